@@ -1,0 +1,174 @@
+"""Pins of the oracle's solve side (Sec. 3): textbook LU against LAPACK, the assembled matrices
+against the un-assembled Galerkin form (eq. matrix_test_varphi), the linear solve against
+manufactured solutions and against an independent finite-difference solve of the same
+boundary value problem, Newton and Picard against their defining properties."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import solve as S
+from paper_2608_07017_b300 import workloads as W
+
+
+def test_lu_matches_lapack():
+    rng = np.random.default_rng(0)
+    for n in (1, 2, 7, 40, 129):
+        M = rng.normal(size=(n, n)) + n * 0.1 * np.eye(n)
+        b = rng.normal(size=n)
+        lu, piv = S.lu_factor(M)
+        x = S.lu_solve(lu, piv, b)
+        ref = np.linalg.solve(M, b)
+        assert np.allclose(x, ref, rtol=1e-10, atol=1e-12)
+    # needs pivoting: zero leading diagonal
+    M = np.array([[0.0, 2.0, 1.0], [1.0, 0.0, 0.0], [3.0, 1.0, 0.0]])
+    lu, piv = S.lu_factor(M)
+    assert np.allclose(S.lu_solve(lu, piv, [1.0, 2.0, 3.0]), np.linalg.solve(M, [1.0, 2.0, 3.0]))
+    # the factors reproduce P M = L U
+    L = np.tril(lu, -1) + np.eye(3); U = np.triu(lu)
+    assert np.allclose(M[piv], L @ U)
+    with pytest.raises(S.SingularMatrix):
+        S.lu_factor(np.array([[1.0, 2.0], [2.0, 4.0]]))
+
+
+def _random_toolbox(rng, n=30, m=30, p=12, d=2):
+    return dict(G=rng.random((n, m)) * 0.01, gradG=rng.normal(size=(d, n, m)) * 0.01,
+                H=rng.random((n, p)) / p, gradH=rng.normal(size=(d, n, p)))
+
+
+def test_assembly_matches_unassembled_galerkin_form():
+    rng = np.random.default_rng(1)
+    for d in (2, 3):
+        n = m = 25
+        tb = _random_toolbox(rng, n, m, 10, d)
+        lam = rng.random(n); lam /= lam.sum()
+        Lr = rng.normal(size=(n, d, d)); A = Lr @ Lr.transpose(0, 2, 1) + np.eye(d)
+        b = rng.normal(size=(n, d)); c = rng.random(n)
+        f = rng.normal(size=n); g = rng.normal(size=10)
+        Lam = S.assemble(tb["G"], tb["gradG"], lam, A, b, c)
+        r = S.rhs(tb["G"], tb["gradG"], tb["H"], tb["gradH"], lam, A, b, c, f, g)
+        for _ in range(3):
+            q, ph = rng.normal(size=m), rng.normal(size=m)
+            lhs = 0.0
+            rr = 0.0
+            for i in range(n):
+                Bi = tb["gradG"][:, i, :]
+                Ki = tb["gradH"][:, i, :]
+                Gi = tb["G"][i]
+                lhs += lam[i] * ((A[i] @ (Bi @ q)) @ (Bi @ ph) + (b[i] @ (Bi @ q)) * (Gi @ ph)
+                                 + c[i] * (Gi @ q) * (Gi @ ph))
+                rr += lam[i] * (f[i] * (Gi @ ph) - (A[i] @ (Ki @ g)) @ (Bi @ ph)
+                                - (b[i] @ (Ki @ g)) * (Gi @ ph) - c[i] * (tb["H"][i] @ g) * (Gi @ ph))
+            assert abs(ph @ Lam @ q - lhs) <= 1e-12 * max(1.0, abs(lhs))
+            assert abs(ph @ r - rr) <= 1e-12 * max(1.0, abs(rr))
+        # R(s) = Lambda s - rhs for the linear problem
+        s = rng.normal(size=m)
+        assert np.allclose(S.residual(tb, lam, A, b, c, f, g, s), Lam @ s - r, rtol=1e-10, atol=1e-13)
+
+
+@pytest.fixture(scope="module")
+def disk_tb(oracle_lib):
+    w = W.disk400()
+    r = oracle_lib.walk_rows(2, "ball", w.domain.params, w.x, w.z, 1000, 1e-3, seed=0)
+    counts = oracle_lib.cell_counts(2, "ball", w.domain.params, w.x, 2_000_000, seed=1)
+    lam = counts / counts.sum()
+    tb = dict(G=r["G"], gradG=r["gradG"], H=r["Hc"] / 1000.0, gradH=r["gradH"])
+    return w, tb, lam
+
+
+def test_linear_solve_disk_manufactured(disk_tb):
+    w, tb, lam = disk_tb
+    pb = w.problem
+    sol = S.solve_linear(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g)
+    e = S.errors(sol["u"], pb.u_star, lam)
+    ref = math.sqrt(np.sum(lam * pb.u_star ** 2))
+    assert e["l2"] < 0.2 * ref                      # the LOT discretisation error (Sec. 3.3: O(1e-2))
+    # without the shift the noise of the toolbox dominates (the reason for the paper's TSVD)
+    raw = S.solve_linear(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, rcond=0.0)
+    assert S.errors(raw["u"], pb.u_star, lam)["l2"] > 2 * e["l2"]
+    # the boundary part alone (s = 0) is far off: the solve does real work
+    assert S.errors(tb["H"] @ pb.g, pb.u_star, lam)["l2"] > 3 * e["l2"]
+    s_t = S.tsvd_solve(sol["Lam"], sol["rhs"], 3e-2)
+    u_t = tb["G"] @ s_t + tb["H"] @ pb.g
+    assert S.errors(u_t, pb.u_star, lam)["l2"] < 0.2 * ref
+
+
+def _fd_solve(a1, a2, f, K):
+    """-d/dx(a1 du/dx) - d/dy(a2 du/dy) = f on (0,1)^2, u = 0 on the boundary: conservative
+    5-point finite differences (face coefficients at midpoints), K x K interior unknowns."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    h = 1.0 / (K + 1)
+    t = np.arange(1, K + 1) * h
+    X, Y = np.meshgrid(t, t, indexing="ij")
+    idx = np.arange(K * K).reshape(K, K)
+    rows, cols, vals = [], [], []
+    for (di, dj, coef) in ((1, 0, lambda: a1(X + h / 2, Y)), (-1, 0, lambda: a1(X - h / 2, Y)),
+                           (0, 1, lambda: a2(X, Y + h / 2)), (0, -1, lambda: a2(X, Y - h / 2))):
+        cf = coef() / h ** 2
+        rows.append(idx.ravel()); cols.append(idx.ravel()); vals.append(cf.ravel())
+        I2, J2 = np.meshgrid(np.arange(K) + di, np.arange(K) + dj, indexing="ij")
+        ok = (I2 >= 0) & (I2 < K) & (J2 >= 0) & (J2 < K)
+        rows.append(idx[ok]); cols.append(idx[I2[ok], J2[ok]]); vals.append(-cf[ok])
+    M = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(K * K, K * K))
+    u = spl.spsolve(M.tocsc(), f(X, Y).ravel())
+    return t, u.reshape(K, K)
+
+
+def test_linear_solve_agrees_with_finite_differences(oracle_lib):
+    k = 12
+    x = W.square_nodes(k)
+    z = W.square_boundary_nodes(24)
+    N = 4000
+    r = oracle_lib.walk_rows(2, "box", [0, 0, 1, 1], x, z, N, 1e-4, seed=4)
+    tb = dict(G=r["G"], gradG=r["gradG"], H=r["Hc"] / N, gradH=r["gradH"])
+    lam = np.full(x.shape[0], 1.0 / x.shape[0])
+    a1 = lambda X, Y: 1.0 + X
+    a2 = lambda X, Y: 1.0 + Y ** 2
+    fsrc = lambda X, Y: 1.0 + 0.0 * X
+    A = np.zeros((x.shape[0], 2, 2)); A[:, 0, 0] = a1(x[:, 0], x[:, 1]); A[:, 1, 1] = a2(x[:, 0], x[:, 1])
+    sol = S.solve_linear(tb, lam, A, None, None, fsrc(x[:, 0], x[:, 1]), np.zeros(z.shape[0]))
+    t, U = _fd_solve(a1, a2, fsrc, 399)
+    from scipy.interpolate import RegularGridInterpolator
+    tt = np.concatenate([[0.0], t, [1.0]])
+    UU = np.pad(U, 1)
+    u_fd = RegularGridInterpolator((tt, tt), UU)(x)
+    rel = np.sqrt(np.sum(lam * (sol["u"] - u_fd) ** 2) / np.sum(lam * u_fd ** 2))
+    assert rel < 0.08
+    # a sign error in the first-order term or a missing factor would be far outside this band
+    bad = S.solve_linear(tb, lam, 2 * A, None, None, fsrc(x[:, 0], x[:, 1]), np.zeros(z.shape[0]))
+    assert np.sqrt(np.sum(lam * (bad["u"] - u_fd) ** 2) / np.sum(lam * u_fd ** 2)) > 0.3
+
+
+def test_newton_semilinear(disk_tb):
+    w, tb, lam = disk_tb
+    pb = w.problem
+    # same manufactured u*, now with N(u) = u^3 added to the operator: f -> f + u*^3
+    f3 = pb.f + pb.u_star ** 3
+    res = S.newton(tb, lam, pb.A, pb.b, pb.c, f3, pb.g, [0, 0, 0, 1])
+    assert res["converged"] and res["iters"] <= 10
+    R = S.residual(tb, lam, pb.A, pb.b, pb.c, f3, pb.g, res["s"], [0, 0, 0, 1]) + res["alpha"] * res["s"]
+    assert np.linalg.norm(R) <= 1e-9 * res["history"][0]
+    lin = S.solve_linear(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g)
+    e_lin = S.errors(lin["u"], pb.u_star, lam)["l2"]
+    assert S.errors(res["u"], pb.u_star, lam)["l2"] < 2 * e_lin + 1e-3
+    # N = 0 reduces Newton to the linear solve
+    res0 = S.newton(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, [0.0], tol=1e-13)
+    assert np.allclose(res0["u"], lin["u"], rtol=1e-8, atol=1e-10)
+
+
+def test_picard_quasilinear(disk_tb):
+    w, tb, lam = disk_tb
+    pb = w.problem
+    lin = S.solve_linear(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g)
+    one = S.picard(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, [1.0])
+    assert np.allclose(one["u"], lin["u"], rtol=1e-10, atol=1e-12) and one["iters"] <= 2
+    st = W.make_problem("star", w.x, w.z)
+    res = S.picard(tb, lam, st.A, st.b, st.c, st.f, st.g, st.kappa, tol=1e-10)
+    assert res["converged"]
+    # fixed point: the linear problem with A(u) frozen at the result returns the result
+    Ak = (1 + res["u"] ** 2)[:, None, None] * st.A
+    again = S.solve_linear(tb, lam, Ak, st.b, st.c, st.f, st.g)
+    assert np.max(np.abs(again["u"] - res["u"])) < 1e-9
+    ref = math.sqrt(np.sum(lam * st.u_star ** 2))
+    assert S.errors(res["u"], st.u_star, lam)["l2"] < 0.15 * ref
