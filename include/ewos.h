@@ -1,0 +1,205 @@
+/*
+ * ewos.h -- C ABI of the B300 extended Walk-on-Spheres operator toolbox.
+ *
+ * The library builds, on one GPU, the Laplacian Operator Toolbox of the paper "Extended
+ * Walk-on-Spheres Algorithm for Linear and Nonlinear Elliptic Problems of Divergence-type"
+ * (the matrices A, B^(j), H, K^(j) of Sec. 2.3, eq. LOT, computed as in Algorithm 5) and
+ * uses it to solve divergence-form Dirichlet problems (Sec. 3).
+ *
+ * Conventions used by every entry point:
+ *   - G := A/2 and gradG := B/2, so that G is the inverse of -Laplace with zero boundary
+ *     values (G 1 = (1-|x|^2)/(2d) on the unit ball).  H and gradH := K are the paper's.
+ *   - d in {2, 3}; n interior nodes x_i (the W and V centres, m = n); p boundary nodes z_j;
+ *     N walks per node; eps the width of the stopping shell.
+ *   - Arrays are dense, row-major, double precision unless stated.  A pointer argument is
+ *     host memory unless the argument's documentation or a flag says it is device memory.
+ *   - The caller owns every input and output buffer.  The library owns a toolbox and its
+ *     device memory until ewos_toolbox_free.
+ *   - Every entry point returns an ewos_status; nothing aborts, traps or prints.  On an
+ *     error the output arguments are left unspecified and ewos_last_error() holds a message.
+ *   - All entry points run on one CUDA device (the current device at build time) and may be
+ *     called from one host thread at a time per toolbox.
+ */
+#ifndef EWOS_API_H_
+#define EWOS_API_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EWOS_OK = 0,
+    EWOS_EINVAL = 1,      /* bad argument: sizes, a node outside the domain, NULL pointer   */
+    EWOS_ENOMEM = 2,      /* device or host allocation failed                              */
+    EWOS_ECUDA = 3,       /* a CUDA runtime call failed (message in ewos_last_error)       */
+    EWOS_ESINGULAR = 4,   /* LU met an exactly zero pivot                                  */
+    EWOS_ENOCONV = 5,     /* Newton / Picard / refinement did not reach the tolerance     */
+    EWOS_ETIMEOUT = 6,    /* a bounded device-side wait gave up                            */
+    EWOS_ESTEPCAP = 7     /* warning: some walks hit max_steps (reported, results valid)   */
+} ewos_status;
+
+typedef enum {
+    EWOS_SDF_BALL = 0,    /* params: centre (d), radius                r = R - |x - c|     */
+    EWOS_SDF_BOX = 1,     /* params: lo (d), hi (d)                    r = min_k min(x-lo, hi-x) */
+    EWOS_SDF_POLYGON = 2  /* d = 2; params: vertices x0,y0,x1,y1,... (closed polygon, <= 256
+                             vertices); r = distance to the nearest edge, signed by an
+                             even-odd inside test (an approximate distance, Rem. 2.14 (i)) */
+} ewos_sdf_kind;
+
+/* Distance to the boundary r(x) of eq. (r), Sec. 2.1. */
+typedef struct {
+    int kind;                 /* ewos_sdf_kind */
+    int dim;                  /* 2 or 3 */
+    const double* params;     /* host */
+    int64_t nparams;
+} ewos_domain;
+
+typedef struct {
+    int precision;            /* 32 (FP32 walks, default) or 64 (FP64 walks)                 */
+    int64_t max_steps;        /* cap on work steps per walk; 0 -> 10000                      */
+    void* stream;             /* cudaStream_t to run on; NULL -> the legacy default stream   */
+    const double* cell_weights; /* optional host n-vector lambda_i; NULL -> Monte Carlo      */
+    int64_t cell_samples;     /* Monte Carlo samples for lambda_i; 0 -> 10^7                 */
+    int threads_per_block;    /* walk kernel block size; 0 -> autotuned/default             */
+    int ctas_per_sm;          /* walk kernel CTAs per SM; 0 -> as many as fit               */
+    int hash_in_smem;         /* -1 auto, 0 keep the Voronoi lookup in global memory, 1 SMEM */
+    int record_walks;         /* 1 -> keep per-walk records (exit cell, steps, G mass)      */
+    uint32_t instance;        /* Philox instance word (separates independent builds)         */
+    int inputs_on_device;     /* 1 -> x and z are device pointers                            */
+} ewos_build_opts;
+
+typedef struct {
+    int64_t walks;            /* n * N                                                       */
+    int64_t steps;            /* WoS steps: 1 (first step) + work steps, summed over walks   */
+    int64_t capped;           /* walks that hit max_steps                                    */
+    double ms_total;          /* device time of the whole build (events on the stream)       */
+    double ms_walk;           /* device time of the walk kernel alone                       */
+    double ms_lookup;         /* Voronoi lookup structures                                   */
+    double ms_cells;          /* lambda_i Monte Carlo                                        */
+    int threads_per_block, ctas_per_sm, grid, hash_in_smem;
+    int64_t smem_bytes;
+} ewos_build_report;
+
+typedef struct ewos_toolbox ewos_toolbox;
+
+/*
+ * Build the toolbox (Algorithm 5 with eqs. Estimator_A, Estimator_B, Estimator_H,
+ * Estimator_K; samplers of Prop. 2.6; Voronoi binning of Sec. 2.3).
+ *   x: n x d interior nodes (walk starts, and V centres), all with r(x_i) > 0.
+ *   z: p x d boundary nodes (Gamma centres).
+ *   walks: N >= 1 per node; eps > 0; seed: Philox key.
+ *   opts may be NULL (defaults).  *out receives the toolbox.
+ * Random numbers: Philox4x32-10, key (seed_lo, seed_hi), counter (walk, step, node,
+ * tag<<24 | instance<<8 | slot); step k >= 0 (k = 0 at x_i) d = 2 slot 0 = (radius of Y,
+ * angle of Y, angle of U, -), d = 3 slot 0 = (median uniforms x3, z of Y), slot 1 = (phi of Y,
+ * z of U, phi of U, -); ball term: step word 0xFFFFFFFF, slot 0 = (S, angle or z, phi, -).
+ * The CPU oracle of the repository replays the same stream.
+ * Returns EWOS_ESTEPCAP (with a valid toolbox) when walks were capped.
+ */
+ewos_status ewos_toolbox_build(const ewos_domain* domain, const double* x, int64_t n,
+                               const double* z, int64_t p, int64_t walks, double eps,
+                               uint64_t seed, const ewos_build_opts* opts, ewos_toolbox** out);
+
+/* Build a toolbox from matrices the caller already has (e.g. a toolbox saved earlier):
+ * G [n][m], gradG [d][n][m], H [n][p] (frequencies), gradH [d][n][p], lambda [n], host
+ * doubles; x [n][d], z [p][d].  precision 32 stores them as FP32 like a built toolbox. */
+ewos_status ewos_toolbox_from_host(int dim, int64_t n, int64_t p, const double* x, const double* z,
+                                   const double* G, const double* gradG, const double* H,
+                                   const double* gradH, const double* lambda, int precision,
+                                   void* stream, ewos_toolbox** out);
+
+typedef enum {
+    EWOS_G = 0,          /* [n][m]       G = A/2                (double)                    */
+    EWOS_GRAD_G = 1,     /* [d][n][m]    gradG = B/2            (double)                    */
+    EWOS_H = 2,          /* [n][p]       H = counts / N         (double)                    */
+    EWOS_GRAD_H = 3,     /* [d][n][p]    gradH = K              (double)                    */
+    EWOS_H_COUNTS = 4,   /* [n][p]       exit counts            (uint32)                    */
+    EWOS_LAMBDA = 5,     /* [n]          cell weights           (double)                    */
+    EWOS_WALK_EXIT = 6,  /* [n][N]       boundary cell of each walk's end (int32; record_walks) */
+    EWOS_WALK_STEPS = 7, /* [n][N]       work steps of each walk (int32; record_walks)      */
+    EWOS_WALK_MASS = 8,  /* [n][N]       unscaled G contribution of each walk (double)      */
+    EWOS_WALK_VHASH = 9  /* [n][N]       XOR over the walk's interior binnings of cellmix(tag, cell),
+                            cellmix = SplitMix64 finaliser of (tag<<32 | cell) folded to 32 bits;
+                            tag = step k (0 for the source at x_i), 0xFFFFFFFF for the ball
+                            term (uint32; record_walks)                                    */
+} ewos_array;
+
+/* Copy one toolbox array to dst (dst_bytes must be at least the array's size in the type
+ * listed above; dst_on_device = 1 for a device pointer). */
+ewos_status ewos_toolbox_get(const ewos_toolbox* tb, int which, void* dst, size_t dst_bytes,
+                             int dst_on_device);
+ewos_status ewos_toolbox_report(const ewos_toolbox* tb, ewos_build_report* rep);
+ewos_status ewos_toolbox_shape(const ewos_toolbox* tb, int* dim, int64_t* n, int64_t* m,
+                               int64_t* p, int* precision);
+void ewos_toolbox_free(ewos_toolbox* tb);
+
+typedef enum { EWOS_NL_NONE = 0, EWOS_NL_SEMILINEAR = 1, EWOS_NL_QUASILINEAR = 2 } ewos_nl_kind;
+typedef enum {
+    EWOS_SOLVE_FP64 = 0,   /* FP64 assembly, FP64 LU                                        */
+    EWOS_SOLVE_MIXED = 1   /* tensor-core assembly + low-precision LU, FP64 refinement      */
+} ewos_solve_mode;
+
+/*
+ * Problem (Sec. 3.1 eq. linearPDE written with b -> -b and f -> -f, and Sec. 3.2):
+ *     -div(kappa(u) A grad u) + b . grad u + c u + N(u) = f  in D,   u = g on the boundary,
+ * with N(u) = sum_k nl_coef[k] u^k (EWOS_NL_SEMILINEAR, Newton), kappa(u) = sum_k nl_coef[k] u^k
+ * (EWOS_NL_QUASILINEAR, Picard), both absent for EWOS_NL_NONE.  All coefficient arrays are
+ * values at the nodes (Rem. 3.3): A [n][d][d] symmetric elliptic, b [n][d] or NULL,
+ * c [n] or NULL, f [nrhs][n], g [nrhs][p].
+ * The linear system is (Lambda + alpha I) s = rhs of eq. linear_q with
+ * alpha = rcond * ||Lambda||_F (the LU counterpart of the paper's TSVD; rcond < 0 -> 3e-2,
+ * rcond = 0 -> no shift), u = G s + H g.  Newton solves R(s) + alpha s = 0 with Jacobian
+ * Lambda + alpha I + G^T diag(lambda N'(u)) G from s = 0; Picard starts at u = H g.
+ */
+typedef struct {
+    const double* A;
+    const double* b;
+    const double* c;
+    const double* f;
+    const double* g;
+    int64_t nrhs;
+    int nl_kind;              /* ewos_nl_kind */
+    const double* nl_coef;
+    int nl_ncoef;
+    int mode;                 /* ewos_solve_mode */
+    double rcond;             /* < 0 -> default 3e-2 */
+    double tol;               /* <= 0 -> 1e-10 (Newton: relative residual; Picard: max |du|) */
+    int max_iter;             /* <= 0 -> 30 (Newton) / 100 (Picard)                       */
+    int inputs_on_device;     /* 1 -> A, b, c, f, g are device pointers                    */
+    void* stream;             /* NULL -> the toolbox's stream                              */
+} ewos_problem;
+
+typedef struct {
+    int iters;                /* Newton / Picard iterations (1 for linear)                  */
+    int refine_iters;         /* FP64 refinement sweeps of the mixed mode (total)            */
+    int converged;
+    double alpha;
+    double residual;          /* final ||R(s) + alpha s||_2 (FP64)                           */
+    double ms_total, ms_assemble, ms_factor, ms_solve;
+} ewos_solve_report;
+
+/* Solve; u_out [nrhs][n] and s_out [nrhs][m] (may be NULL) are host buffers unless
+ * outputs_on_device = 1.  rep may be NULL. */
+ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, double* u_out, double* s_out,
+                       int outputs_on_device, ewos_solve_report* rep);
+
+/* Test hooks (no counterpart in the paper): Philox4x32-10 blocks for count counters
+ * (ctr [count][4], key [2], out [count][4], host uint32), and the d = 2 Green-density radius
+ * R(u) (inverse of F(t) = t^2 - t^2 ln t^2, Prop. 2.6 (i.1)) in FP32 or FP64 for count
+ * uniforms (host arrays of the chosen type).  Both run the device code of the walk kernel. */
+ewos_status ewos_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t count);
+ewos_status ewos_debug_green_radius(const void* u, void* R, int64_t count, int precision);
+
+/* Number of kernels this library has launched in the process so far (all entry points). */
+unsigned long long ewos_launch_count(void);
+
+const char* ewos_status_string(ewos_status s);
+const char* ewos_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EWOS_API_H_ */

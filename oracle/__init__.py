@@ -62,7 +62,8 @@ def lib():
         L.oracle_sdf.restype = ctypes.c_double
         L.oracle_nearest.argtypes = [ctypes.c_int, P, P, ctypes.c_int64]
         L.oracle_nearest.restype = ctypes.c_int64
-        L.oracle_walk_rows.argtypes = [ctypes.POINTER(_Spec), P, ctypes.c_int64] + [P] * 11
+        L.oracle_walk_rows.argtypes = [ctypes.POINTER(_Spec), P, ctypes.c_int64] + [P] * 12
+        L.oracle_philox_batch.argtypes = [P, P, P, ctypes.c_int64]
         L.oracle_walk_rows.restype = ctypes.c_int
         L.oracle_cell_counts.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int64, P,
                                          ctypes.c_int64, P, P, ctypes.c_int64, ctypes.c_uint64,
@@ -85,6 +86,15 @@ def philox4x32_10(ctr, key):
     k = np.ascontiguousarray(key, dtype=np.uint32)
     out = np.zeros(4, dtype=np.uint32)
     lib().oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def philox_batch(ctr, key):
+    """Philox4x32-10 for many counters: ctr [count][4] -> out [count][4]."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros_like(c)
+    lib().oracle_philox_batch(_ptr(c), _ptr(k), _ptr(out), c.shape[0])
     return out
 
 
@@ -118,7 +128,7 @@ def walk_rows(dim, kind, params, x, z, walks, eps, seed, rows=None, y=None, max_
     """Toolbox rows for the node indices ``rows`` (default: all), Algorithm 5 with the
     readings listed in ``wos_oracle.c``.  Returns a dict with G [r][m], gradG [d][r][m],
     Hc [r][p] (int64 exit counts), gradH [d][r][p], steps, capped and, when ``records``,
-    per-walk arrays (exit, steps, capped, gmass, gradmass, w) of shape [r][N](...)."""
+    per-walk arrays (exit, steps, capped, gmass, gradmass, w, vhash) of shape [r][N](...)."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     z = np.ascontiguousarray(z, dtype=np.float64)
     y = x if y is None else np.ascontiguousarray(y, dtype=np.float64)
@@ -134,11 +144,12 @@ def walk_rows(dim, kind, params, x, z, walks, eps, seed, rows=None, y=None, max_
     if records:
         rec = dict(exit=np.zeros((nr, N), np.int32), steps=np.zeros((nr, N), np.int32),
                    capped=np.zeros((nr, N), np.int8), gmass=np.zeros((nr, N)),
-                   gradmass=np.zeros((nr, N, dim)), w=np.zeros((nr, N, dim)))
+                   gradmass=np.zeros((nr, N, dim)), w=np.zeros((nr, N, dim)),
+                   vhash=np.zeros((nr, N), np.uint32))
     rc = lib().oracle_walk_rows(ctypes.byref(spec), _ptr(rows), nr, _ptr(G), _ptr(gG), _ptr(Hc), _ptr(gH),
                                 _ptr(rec.get("exit")), _ptr(rec.get("steps")), _ptr(rec.get("capped")),
                                 _ptr(rec.get("gmass")), _ptr(rec.get("gradmass")), _ptr(rec.get("w")),
-                                _ptr(stats))
+                                _ptr(rec.get("vhash")), _ptr(stats))
     if rc != 0:
         raise ValueError("oracle_walk_rows: invalid input (a node outside the domain or bad dim)")
     out = dict(G=G, gradG=gG, Hc=Hc, gradH=gH, steps=int(stats[0]), capped=int(stats[1]), rows=rows)

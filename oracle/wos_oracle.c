@@ -30,6 +30,9 @@
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11, "Parallel random
  * numbers: as easy as 1, 2, 3"), key = (seed_lo, seed_hi), counter =
  * (walk l, step k, node i, tag<<24 | instance<<8 | slot); uniform u = ((x>>9)+0.5)/2^23.
+ * Step k >= 0 (k = 0 at x_i): d = 2 slot 0 = (radius of Y, angle of Y, angle of U, -);
+ * d = 3 slot 0 = (three uniforms of the median, z of Y), slot 1 = (phi of Y, z of U, phi of U, -).
+ * Ball term: step word 0xFFFFFFFF, slot 0 = (S, angle / z, phi, -).
  */
 #include <math.h>
 #include <stdint.h>
@@ -164,6 +167,21 @@ int64_t oracle_nearest(int dim, const double* q, const double* pts, int64_t np) 
     return orc_nearest(dim, q, pts, np);
 }
 
+/* digest of one interior binning for the per-walk records: Vigna's SplitMix64 output
+ * function applied to (tag << 32 | cell), folded to 32 bits */
+static uint32_t orc_cellmix(uint32_t tag, uint32_t cell) {
+    uint64_t z = ((uint64_t)tag << 32) | (uint64_t)cell;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    z = z ^ (z >> 31);
+    return (uint32_t)(z ^ (z >> 32));
+}
+
+void oracle_philox_batch(const uint32_t* ctr, const uint32_t key[2], uint32_t* out, int64_t count) {
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < count; ++t) oracle_philox4x32_10(ctr + 4 * t, key, out + 4 * t);
+}
+
 /* ---------------------------------------------------------------- toolbox rows */
 typedef struct {
     int dim, sdf_kind;
@@ -197,7 +215,8 @@ static void orc_draw(const oracle_spec* s, uint32_t l, uint32_t k, uint32_t i, u
  * Optional per-walk records (NULL to skip), index r*N + l:
  *   rec_exit (boundary cell), rec_steps (work steps K after the first), rec_capped,
  *   rec_gmass (total G contribution of the walk, unscaled), rec_gradmass [.][dim],
- *   rec_w [.][dim] (X_1 - x_i).
+ *   rec_w [.][dim] (X_1 - x_i), rec_vhash (XOR over the walk's interior binnings of
+ *   cellmix(tag, cell): tag 0xFFFFFFFF for the ball term, k for the source of step k).
  * stats[0] += total WoS steps (1 + K per walk), stats[1] += capped walks.
  * Returns 0, or -1 on invalid input (a node with r(x_i) <= 0).
  */
@@ -205,7 +224,7 @@ int oracle_walk_rows(const oracle_spec* s, const int64_t* rows, int64_t nrows,
                      double* G, double* gradG, int64_t* Hc, double* gradH,
                      int32_t* rec_exit, int32_t* rec_steps, int8_t* rec_capped,
                      double* rec_gmass, double* rec_gradmass, double* rec_w,
-                     int64_t* stats) {
+                     uint32_t* rec_vhash, int64_t* stats) {
     const int d = s->dim;
     const int64_t m = s->m, p = s->p, N = s->walks;
     int bad = 0;
@@ -228,49 +247,32 @@ int oracle_walk_rows(const oracle_spec* s, const int64_t* rows, int64_t nrows,
         double* Grow = G + r * m;
         int64_t* Hrow = Hc + r * p;
         for (int64_t l = 0; l < N; ++l) {
-            double u[4], v[4], q[4], Zb[3] = {0, 0, 0}, Zs[3] = {0, 0, 0}, U[3] = {0, 0, 0};
-            double S, R, wsum, pt[3], X[3], w[3];
+            double u[4], v[4], Zb[3] = {0, 0, 0}, Zs[3] = {0, 0, 0}, U[3] = {0, 0, 0};
+            double S, R, wsum, pt[3], X[3], w[3] = {0, 0, 0};
             double gmass = 0.0, gm[3] = {0, 0, 0};
-            /* step 0: ball term (Prop. 2.6 (ii)), source at x_i (k = 0 term of eq. Estimator_A),
-             * first direction U_0 */
-            if (d == 2) {
-                orc_draw(s, (uint32_t)l, 0u, (uint32_t)i, 0u, u);
-                S = 1.0 - sqrt(u[0]);
-                orc_dir2(u[1], Zb);
-                R = oracle_green_radius_2d(u[2]);
-                orc_dir2(u[3], Zs);
-                orc_draw(s, (uint32_t)l, 0u, (uint32_t)i, 1u, v);
-                orc_dir2(v[0], U);
-                wsum = 1.0 + S;
-            } else {
-                orc_draw(s, (uint32_t)l, 0u, (uint32_t)i, 0u, u);
-                S = 1.0 - sqrt(u[0]);
-                orc_dir3(u[1], u[2], Zb);
-                orc_draw(s, (uint32_t)l, 0u, (uint32_t)i, 1u, v);
-                R = orc_med3(u[3], v[0], v[1]);
-                orc_dir3(v[2], v[3], Zs);
-                orc_draw(s, (uint32_t)l, 0u, (uint32_t)i, 2u, q);
-                orc_dir3(q[0], q[1], U);
-                wsum = 1.0 + S + S * S;
-            }
+            uint32_t vh = 0u;
+            /* ball term of the first sphere (Prop. 2.6 (ii)): its own counter, step tag 0xFFFFFFFF */
+            orc_draw(s, (uint32_t)l, 0xFFFFFFFFu, (uint32_t)i, 0u, u);
+            S = 1.0 - sqrt(u[0]);
+            if (d == 2) { orc_dir2(u[1], Zb); wsum = 1.0 + S; }
+            else { orc_dir3(u[1], u[2], Zb); wsum = 1.0 + S + S * S; }
             for (int c = 0; c < d; ++c) pt[c] = xi[c] + r0 * S * Zb[c];
             int64_t jb = orc_nearest(d, pt, s->y, m);
+            vh ^= orc_cellmix(0xFFFFFFFFu, (uint32_t)jb);
             for (int c = 0; c < d; ++c) {
                 double a = 0.5 * r0 * wsum * Zb[c];
                 gradG[((int64_t)c * nrows + r) * m + jb] += a;
                 gm[c] += a;
             }
-            for (int c = 0; c < d; ++c) pt[c] = xi[c] + r0 * R * Zs[c];
-            int64_t js = orc_nearest(d, pt, s->y, m);
-            Grow[js] += r0 * r0 / (2.0 * d);
-            gmass += r0 * r0 / (2.0 * d);
-            for (int c = 0; c < d; ++c) { w[c] = r0 * U[c]; X[c] = xi[c] + w[c]; }
-
-            int64_t k = 1;
+            /* the chain: step k draws the source Y_k (Green density) and the direction U_k;
+             * step 0 starts at x_i with r = r0 and contributes to G only (k = 0 term of
+             * eq. Estimator_A; eq. Estimator_B sums from s = 1) */
+            for (int c = 0; c < d; ++c) X[c] = xi[c];
+            int64_t k = 0;
             int capped = 0;
             for (;;) {
                 double rk = orc_sdf(d, s->sdf_kind, s->sdf_params, s->n_sdf_params, X);
-                if (rk < s->eps) break;
+                if (k > 0 && rk < s->eps) break;
                 if (k > s->max_steps) { capped = 1; break; }
                 if (d == 2) {
                     orc_draw(s, (uint32_t)l, (uint32_t)k, (uint32_t)i, 0u, u);
@@ -286,13 +288,18 @@ int oracle_walk_rows(const oracle_spec* s, const int64_t* rows, int64_t nrows,
                 }
                 for (int c = 0; c < d; ++c) pt[c] = X[c] + rk * R * Zs[c];
                 int64_t j = orc_nearest(d, pt, s->y, m);
+                vh ^= orc_cellmix((uint32_t)k, (uint32_t)j);
                 double r2 = rk * rk;
                 Grow[j] += r2 / (2.0 * d);
                 gmass += r2 / (2.0 * d);
-                for (int c = 0; c < d; ++c) {
-                    double a = w[c] * r2 / (2.0 * r0 * r0);
-                    gradG[((int64_t)c * nrows + r) * m + j] += a;
-                    gm[c] += a;
+                if (k > 0) {
+                    for (int c = 0; c < d; ++c) {
+                        double a = w[c] * r2 / (2.0 * r0 * r0);
+                        gradG[((int64_t)c * nrows + r) * m + j] += a;
+                        gm[c] += a;
+                    }
+                } else {
+                    for (int c = 0; c < d; ++c) w[c] = rk * U[c];
                 }
                 for (int c = 0; c < d; ++c) X[c] += rk * U[c];
                 ++k;
@@ -301,7 +308,7 @@ int oracle_walk_rows(const oracle_spec* s, const int64_t* rows, int64_t nrows,
             Hrow[jz] += 1;
             for (int c = 0; c < d; ++c)
                 gradH[((int64_t)c * nrows + r) * p + jz] += (double)d / (r0 * r0) * w[c];
-            tot_steps += k;          /* step 0 plus k-1 work steps */
+            tot_steps += k;          /* step 0 plus k-1 further steps */
             tot_capped += capped;
             int64_t ridx = r * N + l;
             if (rec_exit) rec_exit[ridx] = (int32_t)jz;
@@ -310,6 +317,7 @@ int oracle_walk_rows(const oracle_spec* s, const int64_t* rows, int64_t nrows,
             if (rec_gmass) rec_gmass[ridx] = gmass;
             if (rec_gradmass) for (int c = 0; c < d; ++c) rec_gradmass[ridx * d + c] = gm[c];
             if (rec_w) for (int c = 0; c < d; ++c) rec_w[ridx * d + c] = w[c];
+            if (rec_vhash) rec_vhash[ridx] = vh;
         }
     }
     const double invN = 1.0 / (double)N;

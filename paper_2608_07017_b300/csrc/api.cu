@@ -1,0 +1,280 @@
+// api.cu -- the C ABI (include/ewos.h): argument checks, device buffers owned by the toolbox,
+// copies in and out, and the test hooks.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+#include "toolbox.hpp"
+
+namespace ewos {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ewos_status build_toolbox(ewos_toolbox* tb, const ewos_domain* dom, const double* d_x, const double* d_z,
+                          const ewos_build_opts& o);
+ewos_status validate_domain(const ewos_domain* dom, const double* x, int64_t n);
+
+static void release(ewos_toolbox* tb) {
+    if (!tb) return;
+    cudaFree(tb->P); cudaFree(tb->KH); cudaFree(tb->Hc); cudaFree(tb->lambda);
+    cudaFree(tb->x); cudaFree(tb->z);
+    cudaFree(tb->rec_exit); cudaFree(tb->rec_steps); cudaFree(tb->rec_mass); cudaFree(tb->rec_vhash);
+    free_workspace(tb->ws);
+    delete tb;
+}
+
+static ewos_status alloc_matrices(ewos_toolbox* tb, bool counts) {
+    const size_t e = tb->elem();
+    const int64_t d1 = tb->dim + 1;
+    EWOS_CUDA_TRY(cudaMalloc(&tb->P, e * d1 * tb->n * tb->m));
+    EWOS_CUDA_TRY(cudaMalloc(&tb->KH, e * d1 * tb->n * tb->p));
+    if (counts) EWOS_CUDA_TRY(cudaMalloc(&tb->Hc, sizeof(uint32_t) * tb->n * tb->p));
+    EWOS_CUDA_TRY(cudaMalloc(&tb->lambda, sizeof(double) * tb->n));
+    EWOS_CUDA_TRY(cudaMalloc(&tb->x, sizeof(double) * tb->n * tb->dim));
+    EWOS_CUDA_TRY(cudaMalloc(&tb->z, sizeof(double) * tb->p * tb->dim));
+    return EWOS_OK;
+}
+
+template <typename T>
+__global__ void widen_kernel(const T* __restrict__ in, double* __restrict__ out, int64_t count) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = (double)in[t];
+}
+
+template <typename T>
+__global__ void narrow_kernel(const double* __restrict__ in, T* __restrict__ out, int64_t count) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = (T)in[t];
+}
+
+__global__ void philox_debug_kernel(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t k1,
+                                    uint32_t* __restrict__ out, int64_t count) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+        const u32x4 r = philox4x32_10(u32x4{ctr[4 * t], ctr[4 * t + 1], ctr[4 * t + 2], ctr[4 * t + 3]}, k0, k1);
+        out[4 * t] = r.a; out[4 * t + 1] = r.b; out[4 * t + 2] = r.c; out[4 * t + 3] = r.d;
+    }
+}
+
+template <typename T>
+__global__ void green_debug_kernel(const T* __restrict__ u, T* __restrict__ R, int64_t count) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+        R[t] = green_radius_2d<T>(u[t]);
+}
+
+}  // namespace ewos
+
+using namespace ewos;
+
+extern "C" {
+
+const char* ewos_status_string(ewos_status s) {
+    switch (s) {
+        case EWOS_OK: return "ok";
+        case EWOS_EINVAL: return "invalid argument";
+        case EWOS_ENOMEM: return "out of memory";
+        case EWOS_ECUDA: return "CUDA error";
+        case EWOS_ESINGULAR: return "singular matrix";
+        case EWOS_ENOCONV: return "no convergence";
+        case EWOS_ETIMEOUT: return "device wait timed out";
+        case EWOS_ESTEPCAP: return "some walks hit max_steps";
+    }
+    return "unknown status";
+}
+
+const char* ewos_last_error(void) { return g_last_error.c_str(); }
+
+unsigned long long ewos_launch_count(void) { return g_launches.load(); }
+
+ewos_status ewos_toolbox_build(const ewos_domain* domain, const double* x, int64_t n, const double* z, int64_t p,
+                               int64_t walks, double eps, uint64_t seed, const ewos_build_opts* opts,
+                               ewos_toolbox** out) {
+    if (!out || !x || !z || n < 1 || p < 1 || walks < 1 || !(eps > 0) || n > (1 << 30) || p > (1 << 30) ||
+        walks > 0xFFFFFFFFll) {
+        set_error("ewos_toolbox_build: need out, x, z, n >= 1, p >= 1, 1 <= walks < 2^32, eps > 0");
+        return EWOS_EINVAL;
+    }
+    *out = nullptr;
+    ewos_build_opts o{};
+    o.precision = 32;
+    o.hash_in_smem = -1;
+    if (opts) o = *opts;
+    if (o.precision != 32 && o.precision != 64) { set_error("precision must be 32 or 64"); return EWOS_EINVAL; }
+    const double* hx = x;
+    std::vector<double> xh;
+    if (o.inputs_on_device) {
+        xh.resize((size_t)n * domain->dim);
+        if (cudaMemcpy(xh.data(), x, sizeof(double) * xh.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            set_error("cannot read device x");
+            return EWOS_ECUDA;
+        }
+        hx = xh.data();
+    }
+    ewos_status s = validate_domain(domain, hx, n);
+    if (s != EWOS_OK) return s;
+    ewos_toolbox* tb = new ewos_toolbox();
+    tb->dim = domain->dim; tb->precision = o.precision;
+    tb->n = n; tb->m = n; tb->p = p; tb->N = walks; tb->eps = eps; tb->seed = seed; tb->instance = o.instance;
+    tb->stream = (cudaStream_t)o.stream;
+    cudaGetDevice(&tb->device);
+    s = alloc_matrices(tb, true);
+    if (s == EWOS_OK && o.record_walks) {
+        cudaError_t e1 = cudaMalloc(&tb->rec_exit, sizeof(int32_t) * n * walks);
+        cudaError_t e2 = cudaMalloc(&tb->rec_steps, sizeof(int32_t) * n * walks);
+        cudaError_t e3 = cudaMalloc(&tb->rec_mass, tb->elem() * n * walks);
+        cudaError_t e4 = cudaMalloc(&tb->rec_vhash, sizeof(uint32_t) * n * walks);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
+            set_error("records: out of memory");
+            s = EWOS_ENOMEM;
+        }
+    }
+    if (s == EWOS_OK) {
+        const cudaMemcpyKind kind = o.inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        cudaError_t e1 = cudaMemcpyAsync(tb->x, x, sizeof(double) * n * tb->dim, kind, tb->stream);
+        cudaError_t e2 = cudaMemcpyAsync(tb->z, z, sizeof(double) * p * tb->dim, kind, tb->stream);
+        if (e1 != cudaSuccess || e2 != cudaSuccess) { set_error("copy of nodes failed"); s = EWOS_ECUDA; }
+    }
+    if (s == EWOS_OK) s = build_toolbox(tb, domain, tb->x, tb->z, o);
+    if (s != EWOS_OK) { release(tb); return s; }
+    *out = tb;
+    return tb->rep.capped > 0 ? EWOS_ESTEPCAP : EWOS_OK;
+}
+
+ewos_status ewos_toolbox_from_host(int dim, int64_t n, int64_t p, const double* x, const double* z, const double* G,
+                                   const double* gradG, const double* H, const double* gradH, const double* lambda,
+                                   int precision, void* stream, ewos_toolbox** out) {
+    if (!out || (dim != 2 && dim != 3) || n < 1 || p < 1 || !x || !z || !G || !gradG || !H || !gradH || !lambda ||
+        (precision != 32 && precision != 64)) {
+        set_error("ewos_toolbox_from_host: bad arguments");
+        return EWOS_EINVAL;
+    }
+    *out = nullptr;
+    ewos_toolbox* tb = new ewos_toolbox();
+    tb->dim = dim; tb->precision = precision; tb->n = n; tb->m = n; tb->p = p; tb->N = 0;
+    tb->stream = (cudaStream_t)stream;
+    cudaGetDevice(&tb->device);
+    ewos_status s = alloc_matrices(tb, false);
+    if (s != EWOS_OK) { release(tb); return s; }
+    const int64_t nm = n * n, np = n * p;
+    std::vector<double> stage((size_t)(dim + 1) * std::max(nm, np));
+    double* dstage = nullptr;
+    if (cudaMalloc(&dstage, sizeof(double) * stage.size()) != cudaSuccess) { release(tb); set_error("oom"); return EWOS_ENOMEM; }
+    std::memcpy(stage.data(), gradG, sizeof(double) * dim * nm);
+    std::memcpy(stage.data() + dim * nm, G, sizeof(double) * nm);
+    cudaMemcpy(dstage, stage.data(), sizeof(double) * (dim + 1) * nm, cudaMemcpyHostToDevice);
+    if (precision == 64) cudaMemcpy(tb->P, dstage, sizeof(double) * (dim + 1) * nm, cudaMemcpyDeviceToDevice);
+    else ::ewos::note_launch(), narrow_kernel<float><<<1024, 256>>>(dstage, (float*)tb->P, (dim + 1) * nm);
+    std::memcpy(stage.data(), gradH, sizeof(double) * dim * np);
+    std::memcpy(stage.data() + dim * np, H, sizeof(double) * np);
+    cudaMemcpy(dstage, stage.data(), sizeof(double) * (dim + 1) * np, cudaMemcpyHostToDevice);
+    if (precision == 64) cudaMemcpy(tb->KH, dstage, sizeof(double) * (dim + 1) * np, cudaMemcpyDeviceToDevice);
+    else ::ewos::note_launch(), narrow_kernel<float><<<1024, 256>>>(dstage, (float*)tb->KH, (dim + 1) * np);
+    cudaMemcpy(tb->lambda, lambda, sizeof(double) * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(tb->x, x, sizeof(double) * n * dim, cudaMemcpyHostToDevice);
+    cudaMemcpy(tb->z, z, sizeof(double) * p * dim, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaDeviceSynchronize();
+    cudaFree(dstage);
+    if (e != cudaSuccess) { release(tb); set_error(cudaGetErrorString(e)); return EWOS_ECUDA; }
+    *out = tb;
+    return EWOS_OK;
+}
+
+ewos_status ewos_toolbox_get(const ewos_toolbox* tb, int which, void* dst, size_t dst_bytes, int dst_on_device) {
+    if (!tb || !dst) { set_error("ewos_toolbox_get: NULL argument"); return EWOS_EINVAL; }
+    const int64_t d = tb->dim, nm = tb->n * tb->m, np = tb->n * tb->p;
+    const void* src = nullptr;
+    int64_t count = 0;
+    bool widen = false;
+    size_t raw_elem = 0;
+    switch (which) {
+        case EWOS_G: src = (const char*)tb->P + tb->elem() * d * nm; count = nm; widen = true; break;
+        case EWOS_GRAD_G: src = tb->P; count = d * nm; widen = true; break;
+        case EWOS_H: src = (const char*)tb->KH + tb->elem() * d * np; count = np; widen = true; break;
+        case EWOS_GRAD_H: src = tb->KH; count = d * np; widen = true; break;
+        case EWOS_H_COUNTS: src = tb->Hc; count = np; raw_elem = 4; break;
+        case EWOS_LAMBDA: src = tb->lambda; count = tb->n; raw_elem = 8; break;
+        case EWOS_WALK_EXIT: src = tb->rec_exit; count = tb->n * tb->N; raw_elem = 4; break;
+        case EWOS_WALK_STEPS: src = tb->rec_steps; count = tb->n * tb->N; raw_elem = 4; break;
+        case EWOS_WALK_MASS: src = tb->rec_mass; count = tb->n * tb->N; widen = true; break;
+        case EWOS_WALK_VHASH: src = tb->rec_vhash; count = tb->n * tb->N; raw_elem = 4; break;
+        default: set_error("ewos_toolbox_get: unknown array"); return EWOS_EINVAL;
+    }
+    if (!src) { set_error("ewos_toolbox_get: array not available for this toolbox"); return EWOS_EINVAL; }
+    const size_t need = widen ? sizeof(double) * count : raw_elem * count;
+    if (dst_bytes < need) { set_error("ewos_toolbox_get: destination too small"); return EWOS_EINVAL; }
+    const cudaMemcpyKind k = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (!widen || tb->precision == 64) {
+        EWOS_CUDA_TRY(cudaMemcpyAsync(dst, src, need, k, tb->stream));
+        EWOS_CUDA_TRY(cudaStreamSynchronize(tb->stream));
+        return EWOS_OK;
+    }
+    double* tmp = nullptr;
+    if (dst_on_device) tmp = (double*)dst;
+    else EWOS_CUDA_TRY(cudaMalloc(&tmp, need));
+    ::ewos::note_launch(), widen_kernel<float><<<1024, 256, 0, tb->stream>>>((const float*)src, tmp, count);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !dst_on_device) e = cudaMemcpyAsync(dst, tmp, need, cudaMemcpyDeviceToHost, tb->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(tb->stream);
+    if (!dst_on_device) cudaFree(tmp);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return EWOS_ECUDA; }
+    return EWOS_OK;
+}
+
+ewos_status ewos_toolbox_report(const ewos_toolbox* tb, ewos_build_report* rep) {
+    if (!tb || !rep) { set_error("ewos_toolbox_report: NULL argument"); return EWOS_EINVAL; }
+    *rep = tb->rep;
+    return EWOS_OK;
+}
+
+ewos_status ewos_toolbox_shape(const ewos_toolbox* tb, int* dim, int64_t* n, int64_t* m, int64_t* p, int* precision) {
+    if (!tb) { set_error("ewos_toolbox_shape: NULL toolbox"); return EWOS_EINVAL; }
+    if (dim) *dim = tb->dim;
+    if (n) *n = tb->n;
+    if (m) *m = tb->m;
+    if (p) *p = tb->p;
+    if (precision) *precision = tb->precision;
+    return EWOS_OK;
+}
+
+void ewos_toolbox_free(ewos_toolbox* tb) { release(tb); }
+
+ewos_status ewos_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t count) {
+    if (!ctr || !key || !out || count < 0) { set_error("ewos_debug_philox: bad arguments"); return EWOS_EINVAL; }
+    if (count == 0) return EWOS_OK;
+    uint32_t *dc = nullptr, *dout = nullptr;
+    EWOS_CUDA_TRY(cudaMalloc(&dc, 16 * count));
+    EWOS_CUDA_TRY(cudaMalloc(&dout, 16 * count));
+    cudaMemcpy(dc, ctr, 16 * count, cudaMemcpyHostToDevice);
+    ::ewos::note_launch(), philox_debug_kernel<<<256, 256>>>(dc, key[0], key[1], dout, count);
+    cudaError_t e = cudaMemcpy(out, dout, 16 * count, cudaMemcpyDeviceToHost);
+    cudaFree(dc); cudaFree(dout);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return EWOS_ECUDA; }
+    return EWOS_OK;
+}
+
+ewos_status ewos_debug_green_radius(const void* u, void* R, int64_t count, int precision) {
+    if (!u || !R || count < 0 || (precision != 32 && precision != 64)) {
+        set_error("ewos_debug_green_radius: bad arguments");
+        return EWOS_EINVAL;
+    }
+    if (count == 0) return EWOS_OK;
+    const size_t e = precision == 64 ? 8 : 4;
+    void *du = nullptr, *dR = nullptr;
+    EWOS_CUDA_TRY(cudaMalloc(&du, e * count));
+    EWOS_CUDA_TRY(cudaMalloc(&dR, e * count));
+    cudaMemcpy(du, u, e * count, cudaMemcpyHostToDevice);
+    if (precision == 64) ::ewos::note_launch(), green_debug_kernel<double><<<256, 256>>>((const double*)du, (double*)dR, count);
+    else ::ewos::note_launch(), green_debug_kernel<float><<<256, 256>>>((const float*)du, (float*)dR, count);
+    cudaError_t err = cudaMemcpy(R, dR, e * count, cudaMemcpyDeviceToHost);
+    cudaFree(du); cudaFree(dR);
+    if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return EWOS_ECUDA; }
+    return EWOS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,784 @@
+// wos_build.cu -- toolbox build on the GPU: Voronoi lookup structures, Monte Carlo cell
+// weights, and the persistent walk kernel that fuses the four matrix estimators of Sec. 2.3
+// (eqs. Estimator_A, Estimator_B, Estimator_H, Estimator_K) the way Algorithm 5 does, one
+// CTA per node row at a time.
+//
+// Walk of node i, walk l (G := A/2, gradG := B/2; w = X_1 - x_i = r0 U_0):
+//   ball    ball term of Prop. 2.6 (ii): S = 1 - sqrt(u), point x_i + r0 S Z,
+//           gradG += (r0/2) (sum_{k<d} S^k) Z.
+//   step 0  X_0 = x_i, r = r0: source x_i + r0 Y_0 (Green density, Prop. 2.6 (i)):
+//           G += r0^2/(2d);  X_1 = x_i + r0 U_0.
+//   step k  r = r(X_k); stop if r < eps (or k > max_steps); source X_k + r Y_k:
+//           G += r^2/(2d), gradG_c += w_c r^2/(2 r0^2);  X_{k+1} = X_k + r U_k.
+//   exit    boundary cell of the stopping point: H += 1, gradH_c += (d/r0^2) w_c.
+//
+// Layout in HBM: P = [d_1 G, .., d_d G, G] as [(d+1)][n][m] and KH = [d_1 H, .., d_d H, H] as
+// [(d+1)][n][p] (T = float or double), Hc [n][p] uint32 exit counts.  The stacked P is the
+// operand of the Galerkin assembly Lambda = P^T Q (solve.cu).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+#include "toolbox.hpp"
+
+namespace ewos {
+
+constexpr int kMaxPolygonVertices = 256;
+constexpr int kCandidateCap = 96;         // longer lists fall back to a scan of all centres
+
+// ------------------------------------------------------------------ lookup construction
+struct GridSpec {
+    double lo[3];
+    double h;
+    int dims[3];
+    int64_t ncell;
+};
+
+// For grid cell Q: R_Q = min_c maxdist(c, Q); candidates = { c : mindist(c, Q) <= R_Q }.
+// Computed in FP64 with a small relative margin, so the list is a superset of the exact
+// candidates and FP32 queries still see the true nearest centre.
+template <int D>
+__device__ void cell_box(const GridSpec& g, int64_t cell, double* blo, double* bhi) {
+    int64_t rem = cell;
+    for (int c = 0; c < D; ++c) {
+        const int k = (int)(rem % g.dims[c]);
+        rem /= g.dims[c];
+        blo[c] = g.lo[c] + k * g.h;
+        bhi[c] = blo[c] + g.h;
+    }
+}
+
+template <int D>
+__global__ void lookup_count_kernel(const double* __restrict__ pts, int np, GridSpec g,
+                                    int* __restrict__ count, double* __restrict__ radius) {
+    const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= g.ncell) return;
+    double blo[3], bhi[3];
+    cell_box<D>(g, cell, blo, bhi);
+    double R2 = 1e300;
+    for (int j = 0; j < np; ++j) {
+        double mx = 0;
+        for (int c = 0; c < D; ++c) {
+            const double a = fabs(pts[j * D + c] - blo[c]), b = fabs(pts[j * D + c] - bhi[c]);
+            const double t = fmax(a, b);
+            mx += t * t;
+        }
+        R2 = fmin(R2, mx);
+    }
+    const double lim = R2 * (1.0 + 1e-9) + 1e-24;
+    int cnt = 0;
+    for (int j = 0; j < np; ++j) {
+        double mn = 0;
+        for (int c = 0; c < D; ++c) {
+            const double v = pts[j * D + c];
+            const double t = v < blo[c] ? blo[c] - v : (v > bhi[c] ? v - bhi[c] : 0.0);
+            mn += t * t;
+        }
+        cnt += (mn <= lim);
+    }
+    count[cell] = cnt > kCandidateCap ? 0 : cnt;   // empty list = scan all centres
+    radius[cell] = lim;
+}
+
+template <int D>
+__global__ void lookup_fill_kernel(const double* __restrict__ pts, int np, GridSpec g,
+                                   const int* __restrict__ start, const double* __restrict__ radius,
+                                   int* __restrict__ cand) {
+    const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= g.ncell) return;
+    int w = start[cell];
+    const int e = start[cell + 1];
+    if (w == e) return;
+    double blo[3], bhi[3];
+    cell_box<D>(g, cell, blo, bhi);
+    const double lim = radius[cell];
+    for (int j = 0; j < np && w < e; ++j) {
+        double mn = 0;
+        for (int c = 0; c < D; ++c) {
+            const double v = pts[j * D + c];
+            const double t = v < blo[c] ? blo[c] - v : (v > bhi[c] ? v - bhi[c] : 0.0);
+            mn += t * t;
+        }
+        if (mn <= lim) cand[w++] = j;
+    }
+}
+
+// exclusive scan of count[0..len) into start[0..len], single block (len is at most a few 10^5)
+__global__ void exclusive_scan_kernel(const int* __restrict__ count, int64_t len, int* __restrict__ start) {
+    __shared__ int warp_sums[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int64_t base = 0; base < len; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        int v = i < len ? count[i] : 0;
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) warp_sums[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int s = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += t;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        const int before = (wid > 0 ? warp_sums[wid - 1] : 0) + carry;
+        if (i < len) start[i] = before + incl - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) start[len] = carry;
+}
+
+template <typename T, int D>
+__global__ void convert_points_kernel(const double* __restrict__ in, T* __restrict__ out, int64_t count) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) out[t] = (T)in[t];
+}
+
+struct DeviceLookup {
+    void* pts = nullptr;     // T [np][D]
+    int* start = nullptr;
+    int* cand = nullptr;
+    GridSpec grid{};
+    int64_t ncand = 0;
+    int np = 0;
+    void release() {
+        cudaFree(pts); cudaFree(start); cudaFree(cand);
+        pts = nullptr; start = nullptr; cand = nullptr;
+    }
+};
+
+static GridSpec make_grid(int dim, const double* lo, const double* hi, double h) {
+    GridSpec g{};
+    g.h = h;
+    g.ncell = 1;
+    for (int c = 0; c < 3; ++c) {
+        if (c < dim) {
+            const double ext = hi[c] - lo[c];
+            g.dims[c] = std::max(1, (int)std::ceil(ext / h + 1e-9));
+            const double pad = 0.5 * (g.dims[c] * h - ext);
+            g.lo[c] = lo[c] - pad;
+            g.ncell *= g.dims[c];
+        } else {
+            g.dims[c] = 1;
+            g.lo[c] = 0;
+        }
+    }
+    return g;
+}
+
+template <typename T>
+static ewos_status build_lookup(int dim, const double* d_pts, int np, const double* lo, const double* hi,
+                                double h, cudaStream_t st, DeviceLookup& out) {
+    out.np = np;
+    out.grid = make_grid(dim, lo, hi, h);
+    const int64_t nc = out.grid.ncell;
+    int* d_count = nullptr;
+    double* d_rad = nullptr;
+    EWOS_CUDA_TRY(cudaMalloc(&d_count, sizeof(int) * nc));
+    EWOS_CUDA_TRY(cudaMalloc(&d_rad, sizeof(double) * nc));
+    EWOS_CUDA_TRY(cudaMalloc(&out.start, sizeof(int) * (nc + 1)));
+    EWOS_CUDA_TRY(cudaMalloc(&out.pts, sizeof(T) * np * dim));
+    const int tb = 128;
+    const int nb = (int)((nc + tb - 1) / tb);
+    if (dim == 2) ::ewos::note_launch(), lookup_count_kernel<2><<<nb, tb, 0, st>>>(d_pts, np, out.grid, d_count, d_rad);
+    else ::ewos::note_launch(), lookup_count_kernel<3><<<nb, tb, 0, st>>>(d_pts, np, out.grid, d_count, d_rad);
+    ::ewos::note_launch(), exclusive_scan_kernel<<<1, 1024, 0, st>>>(d_count, nc, out.start);
+    int total = 0;
+    EWOS_CUDA_TRY(cudaMemcpyAsync(&total, out.start + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    out.ncand = total;
+    EWOS_CUDA_TRY(cudaMalloc(&out.cand, sizeof(int) * std::max(1, total)));
+    if (dim == 2) ::ewos::note_launch(), lookup_fill_kernel<2><<<nb, tb, 0, st>>>(d_pts, np, out.grid, out.start, d_rad, out.cand);
+    else ::ewos::note_launch(), lookup_fill_kernel<3><<<nb, tb, 0, st>>>(d_pts, np, out.grid, out.start, d_rad, out.cand);
+    const int64_t ne = (int64_t)np * dim;
+    if (dim == 2) ::ewos::note_launch(), convert_points_kernel<T, 2><<<(int)((ne + 255) / 256), 256, 0, st>>>(d_pts, (T*)out.pts, ne);
+    else ::ewos::note_launch(), convert_points_kernel<T, 3><<<(int)((ne + 255) / 256), 256, 0, st>>>(d_pts, (T*)out.pts, ne);
+    EWOS_CUDA_TRY(cudaGetLastError());
+    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(d_count);
+    cudaFree(d_rad);
+    return EWOS_OK;
+}
+
+template <typename T, int D>
+static Lookup<T, D> lookup_view(const DeviceLookup& L) {
+    Lookup<T, D> v{};
+    v.pts = (const T*)L.pts;
+    v.start = L.start;
+    v.cand = L.cand;
+    for (int c = 0; c < D; ++c) { v.lo[c] = (T)L.grid.lo[c]; v.dims[c] = L.grid.dims[c]; }
+    v.inv_h = (T)(1.0 / L.grid.h);
+    return v;
+}
+
+// nearest centre with the fallback scan for cells whose list was too long
+template <typename T, int D>
+__device__ __forceinline__ int nearest_or_scan(const Lookup<T, D>& L, int np, const T* q) {
+    const int cell = lookup_cell(L, q);
+    const int s = L.start[cell], e = L.start[cell + 1];
+    T best = T(3.0e38f);
+    int bi = 0;
+    if (s == e) {
+        for (int j = 0; j < np; ++j) {
+            T d2 = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) { const T dd = q[c] - L.pts[j * D + c]; d2 += dd * dd; }
+            if (d2 < best) { best = d2; bi = j; }
+        }
+        return bi;
+    }
+    for (int t = s; t < e; ++t) {
+        const int j = L.cand[t];
+        T d2 = 0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) { const T dd = q[c] - L.pts[j * D + c]; d2 += dd * dd; }
+        if (d2 < best) { best = d2; bi = j; }
+    }
+    return bi;
+}
+
+// ------------------------------------------------------------------ cell weights
+template <typename T, int D, int KIND>
+__global__ void cell_count_kernel(Lookup<T, D> V, int m, const T* __restrict__ sdf_prm, int nsdf,
+                                  T lo0, T lo1, T lo2, T ex0, T ex1, T ex2, int64_t nsamples,
+                                  uint32_t k0, uint32_t k1, uint32_t inst, unsigned int* __restrict__ counts) {
+    extern __shared__ unsigned int s_cnt[];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) s_cnt[j] = 0;
+    __syncthreads();
+    const T lo[3] = {lo0, lo1, lo2}, ex[3] = {ex0, ex1, ex2};
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nsamples;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const u32x4 q = philox4x32_10(u32x4{(uint32_t)j, (uint32_t)((uint64_t)j >> 32), 0u,
+                                            (1u << 24) | (inst << 8)}, k0, k1);
+        const uint32_t w[4] = {q.a, q.b, q.c, q.d};
+        T pt[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) pt[c] = lo[c] + ex[c] * u01<T>(w[c]);
+        if (Sdf<T, D, KIND>::eval(sdf_prm, nsdf, pt) > T(0)) atomicAdd(&s_cnt[nearest_or_scan(V, m, pt)], 1u);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x)
+        if (s_cnt[j]) atomicAdd(&counts[j], s_cnt[j]);
+}
+
+__global__ void counts_to_lambda_kernel(const unsigned int* __restrict__ counts, int m, double* __restrict__ lam) {
+    __shared__ unsigned long long tot;
+    if (threadIdx.x == 0) tot = 0;
+    __syncthreads();
+    unsigned long long s = 0;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) s += counts[j];
+    atomicAdd(&tot, s);
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) lam[j] = (double)counts[j] / (double)tot;
+}
+
+template <typename T, int D>
+__global__ void node_radius_kernel(const double* __restrict__ x, int n, int kind, const T* __restrict__ prm,
+                                   int nsdf, T* __restrict__ xT, T* __restrict__ r0) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T p[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) { p[c] = (T)x[i * D + c]; xT[i * D + c] = p[c]; }
+    T r;
+    if (kind == SDF_BALL) r = Sdf<T, D, SDF_BALL>::eval(prm, nsdf, p);
+    else if (kind == SDF_BOX) r = Sdf<T, D, SDF_BOX>::eval(prm, nsdf, p);
+    else r = Sdf<T, 2, SDF_POLYGON>::eval(prm, nsdf, p);
+    r0[i] = r;
+}
+
+// ------------------------------------------------------------------ the walk kernel
+template <typename T, int D>
+struct WalkArgs {
+    int n, m, p;
+    int64_t N;
+    T eps;
+    uint32_t k0, k1, inst;
+    int64_t max_steps;
+    const T* x;        // [n][D]
+    const T* r0;       // [n]
+    const T* sdf;      // params
+    int nsdf;          // polygon vertices (else unused)
+    int sdf_len;       // number of T in sdf
+    Lookup<T, D> V;
+    Lookup<T, D> Z;
+    int v_in_smem;
+    int v_ncell;
+    int64_t v_ncand;
+    T* P;              // [(D+1)][n][m]
+    T* KH;             // [(D+1)][n][p]
+    uint32_t* Hc;      // [n][p]
+    int* row_counter;
+    unsigned long long* stat_steps;
+    unsigned long long* stat_capped;
+    int32_t* rec_exit;
+    int32_t* rec_steps;
+    T* rec_mass;
+    uint32_t* rec_vhash;   // XOR over the walk's interior binnings of cellmix(step tag, cell)
+};
+
+// walk-record digest of one interior binning: the splitmix64 output function applied to
+// (tag << 32 | cell), folded to 32 bits (Vigna's SplitMix64 finaliser)
+__device__ __forceinline__ uint32_t cellmix(uint32_t tag, uint32_t cell) {
+    unsigned long long x = ((unsigned long long)tag << 32) | cell;
+    x ^= x >> 30; x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27; x *= 0x94d049bb133111ebull;
+    x ^= x >> 31;
+    return (uint32_t)(x ^ (x >> 32));
+}
+
+// Random-number layout (shared with the oracle through its published definition):
+//   ball term   counter (l, 0xFFFFFFFF, i, inst|0): (S, angle or z, phi, -)
+//   step k >= 0 counter (l, k, i, inst|slot): d = 2 slot 0 = (radius of Y, angle of Y, angle of U, -);
+//               d = 3 slot 0 = (median uniforms x3, z of Y), slot 1 = (phi of Y, z of U, phi of U, -)
+template <typename T, int D>
+__device__ __forceinline__ void draw_ball(uint32_t l, uint32_t row, uint32_t inst, uint32_t k0, uint32_t k1,
+                                          T& S, T* Zb) {
+    const u32x4 q = philox4x32_10(u32x4{l, 0xFFFFFFFFu, row, inst}, k0, k1);
+    S = T(1) - m_sqrt(u01<T>(q.a));
+    if (D == 2) dir2<T>(u01<T>(q.b), Zb);
+    else dir3<T>(u01<T>(q.b), u01<T>(q.c), Zb);
+}
+
+template <typename T, int D>
+__device__ __forceinline__ void draw_step(uint32_t l, uint32_t k, uint32_t row, uint32_t inst, uint32_t k0,
+                                          uint32_t k1, T& R, T* Zs, T* U) {
+    if (D == 2) {
+        const u32x4 q = philox4x32_10(u32x4{l, k, row, inst | 0u}, k0, k1);
+        R = green_radius_2d<T>(u01<T>(q.a));
+        dir2<T>(u01<T>(q.b), Zs);
+        dir2<T>(u01<T>(q.c), U);
+    } else {
+        const u32x4 q = philox4x32_10(u32x4{l, k, row, inst | 0u}, k0, k1);
+        const u32x4 v = philox4x32_10(u32x4{l, k, row, inst | 1u}, k0, k1);
+        R = med3(u01<T>(q.a), u01<T>(q.b), u01<T>(q.c));
+        dir3<T>(u01<T>(q.d), u01<T>(v.a), Zs);
+        dir3<T>(u01<T>(v.b), u01<T>(v.c), U);
+    }
+}
+
+template <typename T, int D, int KIND, bool RECORD>
+__global__ void __launch_bounds__(512, 1) wos_walk_kernel(WalkArgs<T, D> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // shared layout: acc [(D+1)][m] T | accKH [D][p] T | accH [p] u32 | sdf params | V lookup
+    T* acc = reinterpret_cast<T*>(smem_raw);
+    T* accKH = acc + (size_t)(D + 1) * a.m;
+    uint32_t* accH = reinterpret_cast<uint32_t*>(accKH + (size_t)D * a.p);
+    T* s_sdf = reinterpret_cast<T*>(
+        (reinterpret_cast<uintptr_t>(accH + a.p) + 15) & ~uintptr_t(15));
+    unsigned char* s_v = reinterpret_cast<unsigned char*>(s_sdf + ((a.sdf_len + 3) & ~3));
+    __shared__ int s_row;
+    __shared__ unsigned int s_walk;
+
+    for (int t = threadIdx.x; t < a.sdf_len; t += blockDim.x) s_sdf[t] = a.sdf[t];
+    Lookup<T, D> V = a.V;
+    if (a.v_in_smem) {
+        T* vp = reinterpret_cast<T*>(s_v);
+        int* vs = reinterpret_cast<int*>(vp + (size_t)a.m * D);
+        int* vc = vs + a.v_ncell + 1;
+        for (int t = threadIdx.x; t < a.m * D; t += blockDim.x) vp[t] = a.V.pts[t];
+        for (int t = threadIdx.x; t <= a.v_ncell; t += blockDim.x) vs[t] = a.V.start[t];
+        for (int64_t t = threadIdx.x; t < a.v_ncand; t += blockDim.x) vc[t] = a.V.cand[t];
+        V.pts = vp; V.start = vs; V.cand = vc;
+    }
+    const int accN = (D + 1) * a.m;
+    for (int t = threadIdx.x; t < accN; t += blockDim.x) acc[t] = T(0);
+    for (int t = threadIdx.x; t < D * a.p; t += blockDim.x) accKH[t] = T(0);
+    for (int t = threadIdx.x; t < a.p; t += blockDim.x) accH[t] = 0u;
+
+    unsigned long long my_steps = 0, my_capped = 0;
+    const T invN = T(1) / (T)a.N;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) { s_row = atomicAdd(a.row_counter, 1); s_walk = 0u; }
+        __syncthreads();
+        const int row = s_row;
+        if (row >= a.n) break;
+        T xi[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) xi[c] = a.x[(size_t)row * D + c];
+        const T r0 = a.r0[row];
+        const T r02 = r0 * r0;
+
+        // ---- ball term of the first sphere (path independent, Prop. 2.6 (ii))
+        for (int64_t l = threadIdx.x; l < a.N; l += blockDim.x) {
+            T S, Zb[D], pt[D];
+            draw_ball<T, D>((uint32_t)l, (uint32_t)row, a.inst, a.k0, a.k1, S, Zb);
+            const T wsum = (D == 2) ? T(1) + S : T(1) + S + S * S;
+#pragma unroll
+            for (int c = 0; c < D; ++c) pt[c] = xi[c] + r0 * S * Zb[c];
+            const int jb = nearest_or_scan(V, a.m, pt);
+#pragma unroll
+            for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + jb], r02 * wsum * Zb[c]);
+            if (RECORD) atomicXor(&a.rec_vhash[(size_t)row * a.N + l], cellmix(0xFFFFFFFFu, jb));
+        }
+
+        // ---- the chains; a lane whose walk stops takes the next walk of the row and does its
+        // step 0 (at x_i, radius r0) in the same iteration as the other lanes' steps
+        uint32_t l = atomicAdd(&s_walk, 1u);
+        T X[D], U0[D], mass = T(0);
+        uint32_t k = 0, vh = 0u;
+#pragma unroll
+        for (int c = 0; c < D; ++c) { X[c] = xi[c]; U0[c] = T(0); }
+        while (l < (uint64_t)a.N) {
+            T r = k == 0 ? r0 : Sdf<T, D, KIND>::eval(s_sdf, a.nsdf, X);
+            if (k > 0 && (r < a.eps || (int64_t)k > a.max_steps)) {
+                const int jz = nearest_or_scan(a.Z, a.p, X);
+                atomicAdd(&accH[jz], 1u);
+#pragma unroll
+                for (int c = 0; c < D; ++c) atomicAdd(&accKH[(size_t)c * a.p + jz], U0[c]);
+                my_steps += k;
+                my_capped += (r >= a.eps);
+                if (RECORD) {
+                    const size_t ri = (size_t)row * a.N + l;
+                    a.rec_exit[ri] = jz;
+                    a.rec_steps[ri] = (int32_t)(k - 1);
+                    a.rec_mass[ri] = mass / T(2 * D);
+                    atomicXor(&a.rec_vhash[ri], vh);
+                    vh = 0u;
+                    mass = T(0);
+                }
+                l = atomicAdd(&s_walk, 1u);
+                if (l >= (uint64_t)a.N) break;
+#pragma unroll
+                for (int c = 0; c < D; ++c) X[c] = xi[c];
+                k = 0;
+                r = r0;
+            }
+            T R, Zs[D], U[D], pt[D];
+            draw_step<T, D>(l, k, (uint32_t)row, a.inst, a.k0, a.k1, R, Zs, U);
+            const T rR = r * R;
+#pragma unroll
+            for (int c = 0; c < D; ++c) pt[c] = X[c] + rR * Zs[c];
+            const int j = nearest_or_scan(V, a.m, pt);
+            const T r2 = r * r;
+            atomicAdd(&acc[(size_t)D * a.m + j], r2);
+            if (k > 0) {
+#pragma unroll
+                for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + j], U0[c] * r2);
+            } else {
+#pragma unroll
+                for (int c = 0; c < D; ++c) U0[c] = U[c];
+            }
+#pragma unroll
+            for (int c = 0; c < D; ++c) X[c] += r * U[c];
+            if (RECORD) { mass += r2; vh ^= cellmix(k, (uint32_t)j); }
+            ++k;
+        }
+        __syncthreads();
+
+        // ---- flush the row: scale and write coalesced, then clear the accumulators
+        const T sG = invN / T(2 * D);
+        const T sGG = invN / (T(2) * r0);
+        const T sKH = T(D) * invN / r0;
+        const size_t nm = (size_t)a.n * a.m, np = (size_t)a.n * a.p;
+        for (int t = threadIdx.x; t < a.m; t += blockDim.x) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                a.P[c * nm + (size_t)row * a.m + t] = acc[(size_t)c * a.m + t] * sGG;
+                acc[(size_t)c * a.m + t] = T(0);
+            }
+            a.P[D * nm + (size_t)row * a.m + t] = acc[(size_t)D * a.m + t] * sG;
+            acc[(size_t)D * a.m + t] = T(0);
+        }
+        for (int t = threadIdx.x; t < a.p; t += blockDim.x) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                a.KH[c * np + (size_t)row * a.p + t] = accKH[(size_t)c * a.p + t] * sKH;
+                accKH[(size_t)c * a.p + t] = T(0);
+            }
+            const uint32_t h = accH[t];
+            a.KH[D * np + (size_t)row * a.p + t] = (T)h * invN;
+            a.Hc[(size_t)row * a.p + t] = h;
+            accH[t] = 0u;
+        }
+    }
+    // totals
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_steps += __shfl_down_sync(0xffffffffu, my_steps, o);
+        my_capped += __shfl_down_sync(0xffffffffu, my_capped, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(a.stat_steps, my_steps);
+        if (my_capped) atomicAdd(a.stat_capped, my_capped);
+    }
+}
+
+// ------------------------------------------------------------------ host side
+static double host_sdf(int dim, int kind, const double* prm, int64_t nprm, const double* x) {
+    if (kind == SDF_BALL) {
+        double s = 0;
+        for (int c = 0; c < dim; ++c) s += (x[c] - prm[c]) * (x[c] - prm[c]);
+        return prm[dim] - std::sqrt(s);
+    }
+    if (kind == SDF_BOX) {
+        double r = 1e300;
+        for (int c = 0; c < dim; ++c) r = std::min(r, std::min(x[c] - prm[c], prm[dim + c] - x[c]));
+        return r;
+    }
+    const int64_t nv = nprm / 2;
+    double best = 1e300;
+    bool inside = false;
+    for (int64_t e = 0; e < nv; ++e) {
+        const double ax = prm[2 * e], ay = prm[2 * e + 1];
+        const int64_t f = (e + 1) % nv;
+        const double bx = prm[2 * f], by = prm[2 * f + 1];
+        const double ex = bx - ax, ey = by - ay, px = x[0] - ax, py = x[1] - ay;
+        double t = (px * ex + py * ey) / (ex * ex + ey * ey);
+        t = std::min(1.0, std::max(0.0, t));
+        const double dx = px - t * ex, dy = py - t * ey;
+        best = std::min(best, dx * dx + dy * dy);
+        if ((ay > x[1]) != (by > x[1])) {
+            const double xc = ax + (x[1] - ay) / (by - ay) * ex;
+            if (x[0] < xc) inside = !inside;
+        }
+    }
+    return inside ? std::sqrt(best) : -std::sqrt(best);
+}
+
+static void domain_bbox(int dim, int kind, const double* prm, int64_t nprm, double* lo, double* hi) {
+    if (kind == SDF_BALL) {
+        for (int c = 0; c < dim; ++c) { lo[c] = prm[c] - prm[dim]; hi[c] = prm[c] + prm[dim]; }
+    } else if (kind == SDF_BOX) {
+        for (int c = 0; c < dim; ++c) { lo[c] = prm[c]; hi[c] = prm[dim + c]; }
+    } else {
+        lo[0] = lo[1] = 1e300; hi[0] = hi[1] = -1e300;
+        for (int64_t e = 0; e < nprm / 2; ++e)
+            for (int c = 0; c < 2; ++c) {
+                lo[c] = std::min(lo[c], prm[2 * e + c]);
+                hi[c] = std::max(hi[c], prm[2 * e + c]);
+            }
+    }
+}
+
+struct BuildContext {
+    DeviceLookup V, Z;
+    void* d_sdf = nullptr;
+    void* d_xT = nullptr;
+    void* d_r0 = nullptr;
+    int* d_counter = nullptr;
+    unsigned long long* d_stats = nullptr;
+    unsigned int* d_counts = nullptr;
+    ~BuildContext() {
+        V.release(); Z.release();
+        cudaFree(d_sdf); cudaFree(d_xT); cudaFree(d_r0); cudaFree(d_counter); cudaFree(d_stats); cudaFree(d_counts);
+    }
+};
+
+template <typename T, int D, int KIND, bool RECORD>
+static cudaError_t launch_walks(const WalkArgs<T, D>& a, int grid, int tpb, size_t smem, cudaStream_t st) {
+    auto k = wos_walk_kernel<T, D, KIND, RECORD>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ::ewos::note_launch(), k<<<grid, tpb, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int D, int KIND>
+static cudaError_t dispatch_walks(const WalkArgs<T, D>& a, bool rec, int grid, int tpb, size_t smem, cudaStream_t st) {
+    return rec ? launch_walks<T, D, KIND, true>(a, grid, tpb, smem, st)
+               : launch_walks<T, D, KIND, false>(a, grid, tpb, smem, st);
+}
+
+template <typename T, int D, int KIND>
+static int max_ctas_per_sm(int tpb, size_t smem) {
+    int nb = 0;
+    auto k = wos_walk_kernel<T, D, KIND, false>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, tpb, smem);
+    return nb;
+}
+
+template <typename T, int D>
+static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const double* d_x, const double* d_z,
+                               const ewos_build_opts& o) {
+    cudaStream_t st = tb->stream;
+    const int n = (int)tb->n, m = (int)tb->m, p = (int)tb->p;
+    BuildContext ctx;
+    cudaEvent_t ev[5];
+    for (auto& e : ev) cudaEventCreate(&e);
+    struct EvGuard { cudaEvent_t* e; ~EvGuard() { for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]); } } evg{ev};
+    EWOS_CUDA_TRY(cudaEventRecord(ev[0], st));
+
+    // distance parameters and node radii
+    std::vector<T> prmT(dom->nparams);
+    for (int64_t t = 0; t < dom->nparams; ++t) prmT[t] = (T)dom->params[t];
+    const int sdf_len = (int)dom->nparams;
+    const int nsdf = dom->kind == SDF_POLYGON ? (int)(dom->nparams / 2) : 0;
+    EWOS_CUDA_TRY(cudaMalloc(&ctx.d_sdf, sizeof(T) * std::max<int64_t>(1, dom->nparams)));
+    EWOS_CUDA_TRY(cudaMemcpyAsync(ctx.d_sdf, prmT.data(), sizeof(T) * dom->nparams, cudaMemcpyHostToDevice, st));
+    EWOS_CUDA_TRY(cudaMalloc(&ctx.d_xT, sizeof(T) * n * D));
+    EWOS_CUDA_TRY(cudaMalloc(&ctx.d_r0, sizeof(T) * n));
+    ::ewos::note_launch(), node_radius_kernel<T, D><<<(n + 127) / 128, 128, 0, st>>>(d_x, n, dom->kind, (const T*)ctx.d_sdf, nsdf,
+                                                             (T*)ctx.d_xT, (T*)ctx.d_r0);
+    EWOS_CUDA_TRY(cudaGetLastError());
+
+    // Voronoi lookups over the domain's bounding box
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    domain_bbox(D, dom->kind, dom->params, dom->nparams, lo, hi);
+    double vol = 1;
+    for (int c = 0; c < D; ++c) vol *= (hi[c] - lo[c]);
+    const double hv = std::pow(vol / m, 1.0 / D);
+    double surf = 0;           // rough boundary measure for the boundary-centre grid
+    if (D == 2) surf = 2 * ((hi[0] - lo[0]) + (hi[1] - lo[1]));
+    else surf = 2 * ((hi[0] - lo[0]) * (hi[1] - lo[1]) + (hi[1] - lo[1]) * (hi[2] - lo[2]) + (hi[0] - lo[0]) * (hi[2] - lo[2]));
+    const double hz = D == 2 ? surf / p : std::sqrt(surf / p);
+    ewos_status s = build_lookup<T>(D, d_x, m, lo, hi, hv, st, ctx.V);
+    if (s != EWOS_OK) return s;
+    s = build_lookup<T>(D, d_z, p, lo, hi, hz, st, ctx.Z);
+    if (s != EWOS_OK) return s;
+    EWOS_CUDA_TRY(cudaEventRecord(ev[1], st));
+
+    // cell weights
+    if (o.cell_weights) {
+        EWOS_CUDA_TRY(cudaMemcpyAsync(tb->lambda, o.cell_weights, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    } else {
+        const int64_t ns = o.cell_samples > 0 ? o.cell_samples : 10000000;
+        EWOS_CUDA_TRY(cudaMalloc(&ctx.d_counts, sizeof(unsigned int) * m));
+        EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counts, 0, sizeof(unsigned int) * m, st));
+        Lookup<T, D> Vv = lookup_view<T, D>(ctx.V);
+        const T l0 = (T)lo[0], l1 = (T)lo[1], l2 = (T)(D > 2 ? lo[2] : 0);
+        const T e0 = (T)(hi[0] - lo[0]), e1 = (T)(hi[1] - lo[1]), e2 = (T)(D > 2 ? hi[2] - lo[2] : 0);
+        const uint32_t k0 = (uint32_t)tb->seed, k1 = (uint32_t)(tb->seed >> 32), inst = tb->instance & 0xFFFFu;
+        const size_t sm = sizeof(unsigned int) * m;
+        const int blocks = 148 * 4;
+        if (dom->kind == SDF_BALL) cudaFuncSetAttribute(cell_count_kernel<T, D, SDF_BALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        else if (dom->kind == SDF_BOX) cudaFuncSetAttribute(cell_count_kernel<T, D, SDF_BOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        else cudaFuncSetAttribute(cell_count_kernel<T, D, SDF_POLYGON>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (dom->kind == SDF_BALL)
+            ::ewos::note_launch(), cell_count_kernel<T, D, SDF_BALL><<<blocks, 256, sm, st>>>(Vv, m, (const T*)ctx.d_sdf, nsdf, l0, l1, l2, e0, e1, e2, ns, k0, k1, inst, ctx.d_counts);
+        else if (dom->kind == SDF_BOX)
+            ::ewos::note_launch(), cell_count_kernel<T, D, SDF_BOX><<<blocks, 256, sm, st>>>(Vv, m, (const T*)ctx.d_sdf, nsdf, l0, l1, l2, e0, e1, e2, ns, k0, k1, inst, ctx.d_counts);
+        else
+            ::ewos::note_launch(), cell_count_kernel<T, D, SDF_POLYGON><<<blocks, 256, sm, st>>>(Vv, m, (const T*)ctx.d_sdf, nsdf, l0, l1, l2, e0, e1, e2, ns, k0, k1, inst, ctx.d_counts);
+        EWOS_CUDA_TRY(cudaGetLastError());
+        ::ewos::note_launch(), counts_to_lambda_kernel<<<1, 1024, 0, st>>>(ctx.d_counts, m, tb->lambda);
+        EWOS_CUDA_TRY(cudaGetLastError());
+    }
+    EWOS_CUDA_TRY(cudaEventRecord(ev[2], st));
+
+    // walk kernel configuration
+    WalkArgs<T, D> a{};
+    a.n = n; a.m = m; a.p = p; a.N = tb->N; a.eps = (T)tb->eps;
+    a.k0 = (uint32_t)tb->seed; a.k1 = (uint32_t)(tb->seed >> 32);
+    a.inst = (tb->instance & 0xFFFFu) << 8;
+    a.max_steps = o.max_steps > 0 ? o.max_steps : 10000;
+    a.x = (const T*)ctx.d_xT; a.r0 = (const T*)ctx.d_r0;
+    a.sdf = (const T*)ctx.d_sdf; a.nsdf = nsdf; a.sdf_len = sdf_len;
+    a.V = lookup_view<T, D>(ctx.V); a.Z = lookup_view<T, D>(ctx.Z);
+    a.v_ncell = (int)ctx.V.grid.ncell; a.v_ncand = ctx.V.ncand;
+    a.P = (T*)tb->P; a.KH = (T*)tb->KH; a.Hc = tb->Hc;
+    EWOS_CUDA_TRY(cudaMalloc(&ctx.d_counter, sizeof(int)));
+    EWOS_CUDA_TRY(cudaMalloc(&ctx.d_stats, 2 * sizeof(unsigned long long)));
+    EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counter, 0, sizeof(int), st));
+    EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_stats, 0, 2 * sizeof(unsigned long long), st));
+    a.row_counter = ctx.d_counter; a.stat_steps = ctx.d_stats; a.stat_capped = ctx.d_stats + 1;
+    a.rec_exit = tb->rec_exit; a.rec_steps = tb->rec_steps; a.rec_mass = (T*)tb->rec_mass;
+    a.rec_vhash = tb->rec_vhash;
+    if (tb->rec_vhash) EWOS_CUDA_TRY(cudaMemsetAsync(tb->rec_vhash, 0, sizeof(uint32_t) * n * tb->N, st));
+
+    const size_t acc_bytes = sizeof(T) * ((size_t)(D + 1) * m + (size_t)D * p) + sizeof(uint32_t) * p;
+    const size_t sdf_bytes = sizeof(T) * ((sdf_len + 3) & ~3);
+    const size_t base = ((acc_bytes + 15) & ~size_t(15)) + sdf_bytes;
+    const size_t v_bytes = sizeof(T) * (size_t)m * D + sizeof(int) * (ctx.V.grid.ncell + 1 + ctx.V.ncand);
+    int dev = 0, smem_optin = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t budget = (size_t)smem_optin - 1024;
+    if (base > budget) {
+        set_error("toolbox row does not fit in shared memory (m, p too large for one CTA)");
+        return EWOS_EINVAL;
+    }
+    bool v_smem;
+    if (o.hash_in_smem == 0) v_smem = false;
+    else if (o.hash_in_smem == 1) v_smem = base + v_bytes <= budget;
+    else v_smem = base + v_bytes <= budget;
+    a.v_in_smem = v_smem ? 1 : 0;
+    const size_t smem = base + (v_smem ? v_bytes : 0);
+    const int tpb = o.threads_per_block > 0 ? std::min(512, (o.threads_per_block + 31) / 32 * 32) : 512;
+    int per_sm = 0;
+    if (dom->kind == SDF_BALL) per_sm = max_ctas_per_sm<T, D, SDF_BALL>(tpb, smem);
+    else if (dom->kind == SDF_BOX) per_sm = max_ctas_per_sm<T, D, SDF_BOX>(tpb, smem);
+    else per_sm = max_ctas_per_sm<T, D, SDF_POLYGON>(tpb, smem);
+    if (per_sm < 1) {
+        set_error("walk kernel does not fit on an SM with this block size and shared memory");
+        return EWOS_EINVAL;
+    }
+    if (o.ctas_per_sm > 0) per_sm = std::min(per_sm, o.ctas_per_sm);
+    const int grid = std::max(1, std::min(nsm * per_sm, n));
+    const bool rec = o.record_walks != 0;
+    EWOS_CUDA_TRY(cudaEventRecord(ev[3], st));
+    cudaError_t e;
+    if (dom->kind == SDF_BALL) e = dispatch_walks<T, D, SDF_BALL>(a, rec, grid, tpb, smem, st);
+    else if (dom->kind == SDF_BOX) e = dispatch_walks<T, D, SDF_BOX>(a, rec, grid, tpb, smem, st);
+    else e = dispatch_walks<T, D, SDF_POLYGON>(a, rec, grid, tpb, smem, st);
+    EWOS_CUDA_TRY(e);
+    EWOS_CUDA_TRY(cudaEventRecord(ev[4], st));
+    unsigned long long stats[2] = {0, 0};
+    EWOS_CUDA_TRY(cudaMemcpyAsync(stats, ctx.d_stats, sizeof(stats), cudaMemcpyDeviceToHost, st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    float ms[4];
+    cudaEventElapsedTime(&ms[0], ev[0], ev[4]);
+    cudaEventElapsedTime(&ms[1], ev[0], ev[1]);
+    cudaEventElapsedTime(&ms[2], ev[1], ev[2]);
+    cudaEventElapsedTime(&ms[3], ev[3], ev[4]);
+    ewos_build_report& r = tb->rep;
+    r.walks = (int64_t)n * tb->N;
+    r.steps = (int64_t)stats[0];
+    r.capped = (int64_t)stats[1];
+    r.ms_total = ms[0]; r.ms_lookup = ms[1]; r.ms_cells = ms[2]; r.ms_walk = ms[3];
+    r.threads_per_block = tpb; r.ctas_per_sm = per_sm; r.grid = grid; r.hash_in_smem = v_smem;
+    r.smem_bytes = (int64_t)smem;
+    return EWOS_OK;
+}
+
+ewos_status build_toolbox(ewos_toolbox* tb, const ewos_domain* dom, const double* d_x, const double* d_z,
+                          const ewos_build_opts& o) {
+    if (tb->precision == 64)
+        return tb->dim == 2 ? build_typed<double, 2>(tb, dom, d_x, d_z, o) : build_typed<double, 3>(tb, dom, d_x, d_z, o);
+    return tb->dim == 2 ? build_typed<float, 2>(tb, dom, d_x, d_z, o) : build_typed<float, 3>(tb, dom, d_x, d_z, o);
+}
+
+ewos_status validate_domain(const ewos_domain* dom, const double* x, int64_t n) {
+    if (!dom || (dom->dim != 2 && dom->dim != 3) || !dom->params) {
+        set_error("domain: dim must be 2 or 3 and params non-NULL");
+        return EWOS_EINVAL;
+    }
+    if (dom->kind == SDF_BALL && dom->nparams != dom->dim + 1) { set_error("ball: params = centre, radius"); return EWOS_EINVAL; }
+    if (dom->kind == SDF_BOX && dom->nparams != 2 * dom->dim) { set_error("box: params = lo, hi"); return EWOS_EINVAL; }
+    if (dom->kind == SDF_POLYGON &&
+        (dom->dim != 2 || dom->nparams < 6 || (dom->nparams & 1) || dom->nparams / 2 > kMaxPolygonVertices)) {
+        set_error("polygon: d = 2 and 3..256 vertices");
+        return EWOS_EINVAL;
+    }
+    if (dom->kind < 0 || dom->kind > 2) { set_error("unknown domain kind"); return EWOS_EINVAL; }
+    if (x) {
+        for (int64_t i = 0; i < n; ++i)
+            if (!(host_sdf(dom->dim, dom->kind, dom->params, dom->nparams, x + i * dom->dim) > 0.0)) {
+                set_error("interior node " + std::to_string(i) + " is not inside the domain");
+                return EWOS_EINVAL;
+            }
+    }
+    return EWOS_OK;
+}
+
+}  // namespace ewos

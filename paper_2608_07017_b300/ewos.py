@@ -1,0 +1,256 @@
+"""Python binding of the C ABI in include/ewos.h (argument marshalling only).
+
+Every step of the toolbox build and of the solves runs in the CUDA library libewos.so built
+in-tree by ``paper_2608_07017_b300/build.py``; there is no CPU fallback: loading fails loudly
+when the library is missing.  Host arrays are numpy float64; device arrays may be passed as
+torch tensors (their data pointers are handed to the library).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libewos.so")
+_lib = None
+
+OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ENOCONV, ETIMEOUT, ESTEPCAP = range(8)
+SDF = {"ball": 0, "box": 1, "polygon": 2}
+ARR = {"G": 0, "gradG": 1, "H": 2, "gradH": 3, "Hc": 4, "lambda": 5, "walk_exit": 6, "walk_steps": 7,
+       "walk_mass": 8, "walk_vhash": 9}
+NL = {"linear": 0, "semilinear": 1, "quasilinear": 2}
+MODE = {"fp64": 0, "mixed": 1}
+
+
+class EwosError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class _Domain(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dim", ctypes.c_int), ("params", ctypes.c_void_p), ("nparams", ctypes.c_int64)]
+
+
+class BuildOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("max_steps", ctypes.c_int64), ("stream", ctypes.c_void_p),
+                ("cell_weights", ctypes.c_void_p), ("cell_samples", ctypes.c_int64),
+                ("threads_per_block", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("hash_in_smem", ctypes.c_int),
+                ("record_walks", ctypes.c_int), ("instance", ctypes.c_uint32), ("inputs_on_device", ctypes.c_int)]
+
+
+class BuildReport(ctypes.Structure):
+    _fields_ = [("walks", ctypes.c_int64), ("steps", ctypes.c_int64), ("capped", ctypes.c_int64),
+                ("ms_total", ctypes.c_double), ("ms_walk", ctypes.c_double), ("ms_lookup", ctypes.c_double),
+                ("ms_cells", ctypes.c_double), ("threads_per_block", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("grid", ctypes.c_int), ("hash_in_smem", ctypes.c_int), ("smem_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("b", ctypes.c_void_p), ("c", ctypes.c_void_p), ("f", ctypes.c_void_p),
+                ("g", ctypes.c_void_p), ("nrhs", ctypes.c_int64), ("nl_kind", ctypes.c_int),
+                ("nl_coef", ctypes.c_void_p), ("nl_ncoef", ctypes.c_int), ("mode", ctypes.c_int),
+                ("rcond", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("inputs_on_device", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("refine_iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("residual", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("ms_assemble", ctypes.c_double), ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def lib():
+    """Load libewos.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libewos.so not built at {LIB_PATH}: run paper_2608_07017_b300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        L.ewos_status_string.argtypes = [I]
+        L.ewos_status_string.restype = ctypes.c_char_p
+        L.ewos_last_error.restype = ctypes.c_char_p
+        L.ewos_launch_count.restype = ctypes.c_ulonglong
+        L.ewos_toolbox_build.argtypes = [ctypes.POINTER(_Domain), P, I64, P, I64, I64, ctypes.c_double,
+                                         ctypes.c_uint64, ctypes.POINTER(BuildOpts), ctypes.POINTER(P)]
+        L.ewos_toolbox_from_host.argtypes = [I, I64, I64, P, P, P, P, P, P, P, I, P, ctypes.POINTER(P)]
+        L.ewos_toolbox_get.argtypes = [P, I, P, ctypes.c_size_t, I]
+        L.ewos_toolbox_report.argtypes = [P, ctypes.POINTER(BuildReport)]
+        L.ewos_toolbox_shape.argtypes = [P, P, P, P, P, P]
+        L.ewos_toolbox_free.argtypes = [P]
+        L.ewos_toolbox_free.restype = None
+        L.ewos_solve.argtypes = [P, ctypes.POINTER(_Problem), P, P, I, ctypes.POINTER(SolveReport)]
+        L.ewos_debug_philox.argtypes = [P, P, P, I64]
+        L.ewos_debug_green_radius.argtypes = [P, P, I64, I]
+        for fn in ("ewos_toolbox_build", "ewos_toolbox_from_host", "ewos_toolbox_get", "ewos_toolbox_report",
+                   "ewos_toolbox_shape", "ewos_solve", "ewos_debug_philox", "ewos_debug_green_radius"):
+            getattr(L, fn).restype = I
+        _lib = L
+    return _lib
+
+
+def _check(status, what, allow=(OK,)):
+    if status not in allow:
+        raise EwosError(status, f"{what}: {lib().ewos_status_string(status).decode()}: "
+                                f"{lib().ewos_last_error().decode()}")
+    return status
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class Toolbox:
+    """Device-resident toolbox (G, gradG, H, gradH, exit counts, cell weights)."""
+
+    def __init__(self, handle, keep=()):
+        self._h = ctypes.c_void_p(handle)
+        self._keep = keep
+        d, n, m, p, prec = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(lib().ewos_toolbox_shape(self._h, ctypes.byref(d), ctypes.byref(n), ctypes.byref(m),
+                                        ctypes.byref(p), ctypes.byref(prec)), "shape")
+        self.dim, self.n, self.m, self.p, self.precision = d.value, n.value, m.value, p.value, prec.value
+        self.status = OK
+
+    def close(self):
+        if self._h:
+            lib().ewos_toolbox_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def report(self):
+        r = BuildReport()
+        _check(lib().ewos_toolbox_report(self._h, ctypes.byref(r)), "report")
+        return r.as_dict()
+
+    def get(self, which, walks=None):
+        d, n, m, p = self.dim, self.n, self.m, self.p
+        shapes = {"G": (n, m), "gradG": (d, n, m), "H": (n, p), "gradH": (d, n, p), "Hc": (n, p), "lambda": (n,)}
+        dtypes = {"Hc": np.uint32, "walk_exit": np.int32, "walk_steps": np.int32, "walk_vhash": np.uint32}
+        shape = shapes.get(which, (n, walks))
+        out = np.zeros(shape, dtype=dtypes.get(which, np.float64))
+        _check(lib().ewos_toolbox_get(self._h, ARR[which], out.ctypes.data, out.nbytes, 0), f"get {which}")
+        return out
+
+    def get_device(self, which, out):
+        """Copy into a device buffer (a torch tensor of the right size and dtype)."""
+        _check(lib().ewos_toolbox_get(self._h, ARR[which], out.data_ptr(), out.numel() * out.element_size(), 1),
+               f"get {which}")
+        return out
+
+    def matrices(self):
+        return dict(G=self.get("G"), gradG=self.get("gradG"), H=self.get("H"), gradH=self.get("gradH"))
+
+    def solve(self, A, f, g, b=None, c=None, kind="linear", coef=None, mode="fp64", rcond=-1.0, tol=0.0,
+              max_iter=0, want_s=False, on_device=False, out=None, stream=None):
+        """Solve the problem of include/ewos.h; returns (u [nrhs][n] or [n], s or None, report)."""
+        if on_device:
+            Ad, fd, gd, bd, cd = A, f, g, b, c
+            nrhs = f.shape[0] if f.dim() == 2 else 1
+        else:
+            Ad, fd, gd, bd, cd = _f64(A), _f64(f), _f64(g), _f64(b), _f64(c)
+            nrhs = fd.shape[0] if fd.ndim == 2 else 1
+        cf = _f64(coef) if coef is not None else None
+        pb = _Problem(_ptr(Ad), _ptr(bd), _ptr(cd), _ptr(fd), _ptr(gd), nrhs, NL[kind], _ptr(cf),
+                      0 if cf is None else cf.size, MODE[mode], float(rcond), float(tol), int(max_iter),
+                      1 if on_device else 0, stream)
+        if out is not None:
+            u = out
+            optr = out.data_ptr()
+        else:
+            u = np.zeros((nrhs, self.n))
+            optr = u.ctypes.data
+        s = np.zeros((nrhs, self.m)) if want_s else None
+        rep = SolveReport()
+        st = lib().ewos_solve(self._h, ctypes.byref(pb), optr, _ptr(s), 1 if out is not None else 0, ctypes.byref(rep))
+        _check(st, "solve", allow=(OK, ENOCONV))
+        r = rep.as_dict()
+        r["status"] = st
+        if out is None and (fd.ndim if not on_device else f.dim()) == 1:
+            u = u[0]
+            s = None if s is None else s[0]
+        return u, s, r
+
+
+def build_toolbox(domain_kind, dim, params, x, z, walks, eps, seed=0, precision=32, max_steps=0, cell_weights=None,
+                  cell_samples=0, threads_per_block=0, ctas_per_sm=0, hash_in_smem=-1, record_walks=False,
+                  instance=0, stream=None, on_device=False):
+    prm = _f64(params)
+    dom = _Domain(SDF[domain_kind], dim, prm.ctypes.data, prm.size)
+    if on_device:
+        xx, zz = x, z
+        n, p = x.shape[0], z.shape[0]
+    else:
+        xx, zz = _f64(x), _f64(z)
+        n, p = xx.shape[0], zz.shape[0]
+    cw = _f64(cell_weights)
+    o = BuildOpts(precision, max_steps, stream, _ptr(cw), cell_samples, threads_per_block, ctas_per_sm, hash_in_smem,
+                  1 if record_walks else 0, instance, 1 if on_device else 0)
+    h = ctypes.c_void_p()
+    st = lib().ewos_toolbox_build(ctypes.byref(dom), _ptr(xx), n, _ptr(zz), p, int(walks), float(eps), int(seed),
+                                  ctypes.byref(o), ctypes.byref(h))
+    _check(st, "toolbox build", allow=(OK, ESTEPCAP))
+    tb = Toolbox(h.value)
+    tb.status = st
+    return tb
+
+
+def build_workload(w, **kw):
+    """Build the toolbox of a workloads.Workload."""
+    kw.setdefault("precision", w.precision)
+    if w.lam is not None:
+        kw.setdefault("cell_weights", w.lam)
+    return build_toolbox(w.domain.kind, w.domain.dim, w.domain.params, w.x, w.z, w.walks, w.eps, seed=w.seed, **kw)
+
+
+def toolbox_from_host(dim, x, z, G, gradG, H, gradH, lam, precision=64, stream=None):
+    arrs = [_f64(a) for a in (x, z, G, gradG, H, gradH, lam)]
+    h = ctypes.c_void_p()
+    n, p = arrs[0].shape[0], arrs[1].shape[0]
+    _check(lib().ewos_toolbox_from_host(dim, n, p, *[a.ctypes.data for a in arrs], precision, stream, ctypes.byref(h)),
+           "toolbox from host")
+    return Toolbox(h.value, keep=arrs)
+
+
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    return int(lib().ewos_launch_count())
+
+
+def debug_philox(ctr, key):
+    c = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros_like(c)
+    _check(lib().ewos_debug_philox(c.ctypes.data, k.ctypes.data, out.ctypes.data, c.shape[0]), "philox")
+    return out
+
+
+def debug_green_radius(u, precision=32):
+    dt = np.float32 if precision == 32 else np.float64
+    uu = np.ascontiguousarray(u, dtype=dt)
+    R = np.zeros_like(uu)
+    _check(lib().ewos_debug_green_radius(uu.ctypes.data, R.ctypes.data, uu.size, precision), "green radius")
+    return R

@@ -1,0 +1,73 @@
+"""Element-by-element comparison of a GPU toolbox with the oracle's rows (shared by the GPU
+tests; no arithmetic of the method here, only the comparison rule).
+
+Rule (tolerance of matrix entries, 1e-4 relative): a walk is *divergent* when its exit cell,
+its number of steps or its binning digest (XOR of cellmix over every interior binning)
+differs between the two sides -- an FP32/FP64 disagreement at the eps-shell or a Voronoi
+near-tie -- or when its trajectory has drifted: its G mass sum_k r_k^2/(2d) differs by more
+than 1e-5 relative (FP32 positions accumulate rounding along a walk; near corners of the
+box the drift can reach 1e-3 in r^2 without changing any binning).  Every other walk makes
+bit-identical binning decisions along trajectories equal to 1e-5, so its contributions agree
+to that level.  Entries must satisfy
+
+    |gpu - oracle| <= 1e-4 * max(|oracle|, mean_row |oracle|) + bound_row,
+
+for the gradient matrices with max(...) also over the sum of the magnitudes of the entry's terms
+((d/r0) G_ij for gradG, (d/r0) H_ij for gradH), since those entries cancel terms of both signs;
+where bound_row bounds what the divergent walks of that row can move:
+    G      sum_div (mass_gpu + mass_oracle) / N                 (mass = sum r_k^2 / (2d))
+    gradG  sum_div [ (d/r0) (mass_gpu + mass_oracle) + d r0 ] / N
+    Hc     number of divergent walks of the row (integer counts)
+    gradH  2 (d/r0) * (number of divergent walks) / N
+"""
+import numpy as np
+
+
+def compare_rows(gpu, orc, rows, N, dim, r0, rel=1e-4, drift_rel=1e-5):
+    """gpu: dict with G [n][m], gradG [d][n][m], Hc [n][p], gradH [d][n][p] and records
+    exit/steps/vhash/mass [n][N] (full toolbox); orc: oracle.walk_rows(..., records=True) for
+    ``rows``.  Returns a report dict; raises AssertionError on a violation."""
+    rows = np.asarray(rows)
+    rec = orc["records"]
+    ge, gs, gv, gm = (gpu["walk_exit"][rows], gpu["walk_steps"][rows], gpu["walk_vhash"][rows],
+                      gpu["walk_mass"][rows])
+    same_exit = ge == rec["exit"]
+    binning = (~same_exit) | (gs != rec["steps"]) | (gv != rec["vhash"])
+    drift = np.abs(gm - rec["gmass"]) > drift_rel * rec["gmass"]
+    div = binning | drift
+    ndiv = div.sum(1)
+    mass_div = np.where(div, gm + rec["gmass"], 0.0).sum(1)
+    out = dict(exit_equal=float(same_exit.mean()), divergent=float(div.mean()), ndiv=int(ndiv.sum()),
+               binning_divergent=float(binning.mean()), drifted=float((drift & ~binning).mean()))
+
+    def check(name, a, b, bound, extra_scale=None):
+        scale = np.maximum(np.abs(b), np.abs(b).mean(axis=-1, keepdims=True))
+        if extra_scale is not None:
+            scale = np.maximum(scale, extra_scale)
+        lim = rel * scale + bound
+        bad = np.abs(a - b) > lim
+        out[name + "_maxratio"] = float(np.max(np.abs(a - b) / np.maximum(lim, 1e-300)))
+        assert not bad.any(), f"{name}: {int(bad.sum())} entries out of tolerance; worst ratio {out[name + '_maxratio']:.3g}"
+
+    check("G", gpu["G"][rows], orc["G"], (mass_div / N)[:, None])
+    bgg = ((dim / r0) * mass_div + dim * r0 * ndiv) / N
+    # a gradient entry sums terms of both signs; the magnitude its rounding scales with is the sum of
+    # the terms' magnitudes, at most (d/r0) G_ij for the path terms (|U_0| = 1)
+    absg = (dim / r0)[:, None] * orc["G"]
+    for c in range(dim):
+        check(f"gradG{c}", gpu["gradG"][c][rows], orc["gradG"][c], bgg[:, None], absg)
+    dH = np.abs(gpu["Hc"][rows].astype(np.int64) - orc["Hc"])
+    assert np.all(dH <= ndiv[:, None]), "exit counts differ by more than the divergent walks"
+    bgh = 2 * (dim / r0) * ndiv / N
+    absh = (dim / r0)[:, None] * orc["Hc"] / N
+    for c in range(dim):
+        check(f"gradH{c}", gpu["gradH"][c][rows], orc["gradH"][c], bgh[:, None], absh)
+    return out
+
+
+def gpu_arrays(tb, N, records=True):
+    out = dict(G=tb.get("G"), gradG=tb.get("gradG"), Hc=tb.get("Hc"), gradH=tb.get("gradH"), H=tb.get("H"))
+    if records:
+        for k in ("walk_exit", "walk_steps", "walk_vhash", "walk_mass"):
+            out[k] = tb.get(k, walks=N)
+    return out

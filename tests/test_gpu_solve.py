@@ -1,0 +1,148 @@
+"""GPU solves against the oracle's solves (Sec. 3; eq. linear_q with the Tikhonov shift,
+Newton, Picard).
+
+* Same toolbox on both sides (the oracle's FP64 matrices loaded into the library): the FP64
+  path must agree with the oracle to 1e-9 relative (both solve the same FP64 system, only the
+  order of rounding differs; kappa(Lambda + alpha I) <= ~1e3).
+* Whole pipeline (GPU build + GPU solve vs oracle build + oracle solve): the error against the
+  manufactured solution must agree within 1e-3 * max(1e-3, e_oracle) (the stated bar).
+* Full size: the FP64 residual of the GPU solution of the square workload, evaluated with
+  numpy from the downloaded toolbox, is at rounding level.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import solve as S
+from paper_2608_07017_b300 import ewos
+from paper_2608_07017_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def disk():
+    from paper_2608_07017_b300 import build
+    build.build()
+    w = W.disk400()
+    r = oracle.walk_rows(2, "ball", w.domain.params, w.x, w.z, 1000, 1e-3, 0)
+    counts = oracle.cell_counts(2, "ball", w.domain.params, w.x, 1_000_000, seed=1)
+    lam = counts / counts.sum()
+    tb = dict(G=r["G"], gradG=r["gradG"], H=r["Hc"] / 1000.0, gradH=r["gradH"])
+    gtb = ewos.toolbox_from_host(2, w.x, w.z, tb["G"], tb["gradG"], tb["H"], tb["gradH"], lam, precision=64)
+    yield w, tb, lam, gtb
+    gtb.close()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("rcond", [3e-2, 1e-3])
+def test_linear_fp64_matches_oracle_same_toolbox(disk, rcond):
+    w, tb, lam, gtb = disk
+    pb = w.problem
+    ref = S.solve_linear(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, rcond=rcond)
+    u, s, rep = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, c=pb.c, rcond=rcond, want_s=True)
+    assert _rel(u, ref["u"]) < 1e-9
+    assert _rel(s, ref["s"]) < 1e-8
+    assert abs(rep["alpha"] - ref["alpha"]) <= 1e-12 * ref["alpha"]
+    assert rep["residual"] < 1e-10 * np.linalg.norm(ref["rhs"])
+
+
+def test_linear_with_first_and_zeroth_order_terms(disk):
+    w, tb, lam, gtb = disk
+    pb = w.problem
+    rng = np.random.default_rng(2)
+    b = rng.uniform(-1, 1, (w.x.shape[0], 2))
+    c = rng.uniform(0, 2, w.x.shape[0])
+    ref = S.solve_linear(tb, lam, pb.A, b, c, pb.f, pb.g)
+    u, _, _ = gtb.solve(pb.A, pb.f, pb.g, b=b, c=c)
+    assert _rel(u, ref["u"]) < 1e-9
+
+
+def test_multiple_rhs_equal_single_solves(disk):
+    w, tb, lam, gtb = disk
+    pb = w.problem
+    rng = np.random.default_rng(3)
+    F = np.stack([pb.f, pb.f * 0.5 + 1.0, rng.normal(size=pb.f.shape)])
+    Gb = np.stack([pb.g, pb.g * 2.0, rng.normal(size=pb.g.shape)])
+    U, _, _ = gtb.solve(pb.A, F, Gb)
+    for r in range(3):
+        ref = S.solve_linear(tb, lam, pb.A, None, None, F[r], Gb[r])
+        assert _rel(U[r], ref["u"]) < 1e-9
+
+
+def test_newton_matches_oracle(disk):
+    w, tb, lam, gtb = disk
+    pb = w.problem
+    f3 = pb.f + pb.u_star ** 3
+    ref = S.newton(tb, lam, pb.A, None, None, f3, pb.g, [0, 0, 0, 1])
+    u, _, rep = gtb.solve(pb.A, f3, pb.g, kind="semilinear", coef=[0, 0, 0, 1])
+    assert rep["converged"] and rep["iters"] == ref["iters"]
+    assert _rel(u, ref["u"]) < 1e-9
+
+
+def test_picard_matches_oracle(disk):
+    w, tb, lam, gtb = disk
+    st = W.make_problem("star", w.x, w.z)
+    ref = S.picard(tb, lam, st.A, None, None, st.f, st.g, st.kappa)
+    u, _, rep = gtb.solve(st.A, st.f, st.g, kind="quasilinear", coef=st.kappa)
+    assert rep["converged"] and abs(rep["iters"] - ref["iters"]) <= 1
+    assert _rel(u, ref["u"]) < 1e-8
+
+
+def test_ragged_sizes_lu():
+    # m not a multiple of the 64-wide panels (m = 130, 67, 1), FP32 toolbox
+    for k, per in ((11, 3), (8, 2), (1, 1)):
+        x = W.square_nodes(k)
+        x = x[: max(1, x.shape[0] - (3 if k > 1 else 0))]
+        z = W.square_boundary_nodes(per * 2)
+        r = oracle.walk_rows(2, "box", [0, 0, 1, 1], x, z, 400, 1e-4, 7)
+        lam = np.full(x.shape[0], 1.0 / x.shape[0])
+        tb = dict(G=r["G"], gradG=r["gradG"], H=r["Hc"] / 400.0, gradH=r["gradH"])
+        pb = W.make_problem("square", x, z)
+        ref = S.solve_linear(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g)
+        gtb = ewos.toolbox_from_host(2, x, z, tb["G"], tb["gradG"], tb["H"], tb["gradH"], lam, precision=64)
+        u, _, _ = gtb.solve(pb.A, pb.f, pb.g, b=pb.b)
+        gtb.close()
+        assert _rel(u, ref["u"]) < 1e-9, x.shape
+
+
+def test_whole_pipeline_disk400_fp64():
+    w = W.disk400()
+    pb = w.problem
+    gtb = ewos.build_workload(w, cell_samples=1_000_000)
+    lam_g = gtb.get("lambda")
+    u, _, _ = gtb.solve(pb.A, pb.f, pb.g)
+    gtb.close()
+    r = oracle.walk_rows(2, "ball", w.domain.params, w.x, w.z, 1000, 1e-3, 0)
+    counts = oracle.cell_counts(2, "ball", w.domain.params, w.x, 1_000_000, seed=0)
+    lam = counts / counts.sum()
+    tb = dict(G=r["G"], gradG=r["gradG"], H=r["Hc"] / 1000.0, gradH=r["gradH"])
+    ref = S.solve_linear(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g)
+    e_g = S.errors(u, pb.u_star, lam)["l2"]
+    e_o = S.errors(ref["u"], pb.u_star, lam)["l2"]
+    assert abs(e_g - e_o) <= 1e-3 * max(1e-3, e_o)
+    assert np.max(np.abs(lam_g - lam)) < 1e-5
+
+
+def test_square4096_full_size_fp64_residual():
+    w = W.square4096()
+    pb = w.problem
+    gtb = ewos.build_workload(w)
+    u, s, rep = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, want_s=True)
+    mats = gtb.matrices()
+    lam = gtb.get("lambda")
+    gtb.close()
+    Lam = S.assemble(mats["G"], mats["gradG"], lam, pb.A, pb.b, None)
+    r = S.rhs(mats["G"], mats["gradG"], mats["H"], mats["gradH"], lam, pb.A, pb.b, None, pb.f, pb.g)
+    alpha = S.shift(Lam, 3e-2)
+    res = (Lam + alpha * np.eye(Lam.shape[0])) @ s - r
+    assert np.linalg.norm(res) <= 1e-9 * np.linalg.norm(r)
+    u_ref = mats["G"] @ s + mats["H"] @ pb.g
+    assert _rel(u, u_ref) < 1e-10
+    ref_norm = math.sqrt(np.sum(lam * pb.u_star ** 2))
+    assert S.errors(u, pb.u_star, lam)["l2"] < 0.2 * ref_norm
