@@ -121,10 +121,11 @@ typedef enum {
     EWOS_WALK_EXIT = 6,  /* [n][N]       boundary cell of each walk's end (int32; record_walks) */
     EWOS_WALK_STEPS = 7, /* [n][N]       work steps of each walk (int32; record_walks)      */
     EWOS_WALK_MASS = 8,  /* [n][N]       unscaled G contribution of each walk (double)      */
-    EWOS_WALK_VHASH = 9  /* [n][N]       XOR over the walk's interior binnings of cellmix(tag, cell),
+    EWOS_WALK_VHASH = 9, /* [n][N]       XOR over the walk's interior binnings of cellmix(tag, cell),
                             cellmix = SplitMix64 finaliser of (tag<<32 | cell) folded to 32 bits;
                             tag = step k (0 for the source at x_i), 0xFFFFFFFF for the ball
                             term (uint32; record_walks)                                    */
+    EWOS_WALK_XEXIT = 10 /* [n][N][d]    stopping point of each walk (double; record_walks)  */
 } ewos_array;
 
 /* Copy one toolbox array to dst (dst_bytes must be at least the array's size in the type

@@ -62,7 +62,7 @@ def lib():
         L.oracle_sdf.restype = ctypes.c_double
         L.oracle_nearest.argtypes = [ctypes.c_int, P, P, ctypes.c_int64]
         L.oracle_nearest.restype = ctypes.c_int64
-        L.oracle_walk_rows.argtypes = [ctypes.POINTER(_Spec), P, ctypes.c_int64] + [P] * 12
+        L.oracle_walk_rows.argtypes = [ctypes.POINTER(_Spec), P, ctypes.c_int64] + [P] * 14
         L.oracle_philox_batch.argtypes = [P, P, P, ctypes.c_int64]
         L.oracle_walk_rows.restype = ctypes.c_int
         L.oracle_cell_counts.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.c_int64, P,
@@ -128,7 +128,8 @@ def walk_rows(dim, kind, params, x, z, walks, eps, seed, rows=None, y=None, max_
     """Toolbox rows for the node indices ``rows`` (default: all), Algorithm 5 with the
     readings listed in ``wos_oracle.c``.  Returns a dict with G [r][m], gradG [d][r][m],
     Hc [r][p] (int64 exit counts), gradH [d][r][p], steps, capped and, when ``records``,
-    per-walk arrays (exit, steps, capped, gmass, gradmass, w, vhash) of shape [r][N](...)."""
+    per-walk arrays (exit, steps, capped, gmass, gradmass, w, vhash, xexit) of shape [r][N](...)
+    and Grsum (sum of r/(2dN) over the binnings of G, a rounding-bound diagnostic)."""
     x = np.ascontiguousarray(x, dtype=np.float64)
     z = np.ascontiguousarray(z, dtype=np.float64)
     y = x if y is None else np.ascontiguousarray(y, dtype=np.float64)
@@ -140,21 +141,23 @@ def walk_rows(dim, kind, params, x, z, walks, eps, seed, rows=None, y=None, max_
     G = np.zeros((nr, m)); gG = np.zeros((dim, nr, m))
     Hc = np.zeros((nr, p), dtype=np.int64); gH = np.zeros((dim, nr, p))
     stats = np.zeros(2, dtype=np.int64)
+    Grs = np.zeros((nr, m)) if records else None
     rec = {}
     if records:
         rec = dict(exit=np.zeros((nr, N), np.int32), steps=np.zeros((nr, N), np.int32),
                    capped=np.zeros((nr, N), np.int8), gmass=np.zeros((nr, N)),
                    gradmass=np.zeros((nr, N, dim)), w=np.zeros((nr, N, dim)),
-                   vhash=np.zeros((nr, N), np.uint32))
+                   vhash=np.zeros((nr, N), np.uint32), xexit=np.zeros((nr, N, dim)))
     rc = lib().oracle_walk_rows(ctypes.byref(spec), _ptr(rows), nr, _ptr(G), _ptr(gG), _ptr(Hc), _ptr(gH),
                                 _ptr(rec.get("exit")), _ptr(rec.get("steps")), _ptr(rec.get("capped")),
                                 _ptr(rec.get("gmass")), _ptr(rec.get("gradmass")), _ptr(rec.get("w")),
-                                _ptr(rec.get("vhash")), _ptr(stats))
+                                _ptr(rec.get("vhash")), _ptr(rec.get("xexit")), _ptr(Grs), _ptr(stats))
     if rc != 0:
         raise ValueError("oracle_walk_rows: invalid input (a node outside the domain or bad dim)")
     out = dict(G=G, gradG=gG, Hc=Hc, gradH=gH, steps=int(stats[0]), capped=int(stats[1]), rows=rows)
     if records:
         out["records"] = rec
+        out["Grsum"] = Grs
     return out
 
 

@@ -216,7 +216,9 @@ static void orc_draw(const oracle_spec* s, uint32_t l, uint32_t k, uint32_t i, u
  *   rec_exit (boundary cell), rec_steps (work steps K after the first), rec_capped,
  *   rec_gmass (total G contribution of the walk, unscaled), rec_gradmass [.][dim],
  *   rec_w [.][dim] (X_1 - x_i), rec_vhash (XOR over the walk's interior binnings of
- *   cellmix(tag, cell): tag 0xFFFFFFFF for the ball term, k for the source of step k).
+ *   cellmix(tag, cell): tag 0xFFFFFFFF for the ball term, k for the source of step k),
+ *   rec_xexit [.][dim] (stopping point).  Grsum [nrows][m] (optional): sum of r/(2d N) over the
+ *   same binnings as G (a diagnostic used to bound rounding differences, not an estimator).
  * stats[0] += total WoS steps (1 + K per walk), stats[1] += capped walks.
  * Returns 0, or -1 on invalid input (a node with r(x_i) <= 0).
  */
@@ -224,7 +226,7 @@ int oracle_walk_rows(const oracle_spec* s, const int64_t* rows, int64_t nrows,
                      double* G, double* gradG, int64_t* Hc, double* gradH,
                      int32_t* rec_exit, int32_t* rec_steps, int8_t* rec_capped,
                      double* rec_gmass, double* rec_gradmass, double* rec_w,
-                     uint32_t* rec_vhash, int64_t* stats) {
+                     uint32_t* rec_vhash, double* rec_xexit, double* Grsum, int64_t* stats) {
     const int d = s->dim;
     const int64_t m = s->m, p = s->p, N = s->walks;
     int bad = 0;
@@ -235,6 +237,7 @@ int oracle_walk_rows(const oracle_spec* s, const int64_t* rows, int64_t nrows,
     }
     if (bad || d < 2 || d > 3) return -1;
     memset(G, 0, sizeof(double) * nrows * m);
+    if (Grsum) memset(Grsum, 0, sizeof(double) * nrows * m);
     memset(gradG, 0, sizeof(double) * d * nrows * m);
     memset(Hc, 0, sizeof(int64_t) * nrows * p);
     memset(gradH, 0, sizeof(double) * d * nrows * p);
@@ -291,6 +294,7 @@ int oracle_walk_rows(const oracle_spec* s, const int64_t* rows, int64_t nrows,
                 vh ^= orc_cellmix((uint32_t)k, (uint32_t)j);
                 double r2 = rk * rk;
                 Grow[j] += r2 / (2.0 * d);
+                if (Grsum) Grsum[r * m + j] += rk / (2.0 * d);
                 gmass += r2 / (2.0 * d);
                 if (k > 0) {
                     for (int c = 0; c < d; ++c) {
@@ -318,10 +322,12 @@ int oracle_walk_rows(const oracle_spec* s, const int64_t* rows, int64_t nrows,
             if (rec_gradmass) for (int c = 0; c < d; ++c) rec_gradmass[ridx * d + c] = gm[c];
             if (rec_w) for (int c = 0; c < d; ++c) rec_w[ridx * d + c] = w[c];
             if (rec_vhash) rec_vhash[ridx] = vh;
+            if (rec_xexit) for (int c = 0; c < d; ++c) rec_xexit[ridx * d + c] = X[c];
         }
     }
     const double invN = 1.0 / (double)N;
     for (int64_t t = 0; t < nrows * m; ++t) G[t] *= invN;
+    if (Grsum) for (int64_t t = 0; t < nrows * m; ++t) Grsum[t] *= invN;
     for (int64_t t = 0; t < d * nrows * m; ++t) gradG[t] *= invN;
     for (int64_t t = 0; t < d * nrows * p; ++t) gradH[t] *= invN;
     if (stats) { stats[0] += tot_steps; stats[1] += tot_capped; }

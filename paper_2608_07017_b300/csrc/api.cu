@@ -26,6 +26,7 @@ static void release(ewos_toolbox* tb) {
     cudaFree(tb->P); cudaFree(tb->KH); cudaFree(tb->Hc); cudaFree(tb->lambda);
     cudaFree(tb->x); cudaFree(tb->z);
     cudaFree(tb->rec_exit); cudaFree(tb->rec_steps); cudaFree(tb->rec_mass); cudaFree(tb->rec_vhash);
+    cudaFree(tb->rec_xexit);
     free_workspace(tb->ws);
     delete tb;
 }
@@ -129,7 +130,8 @@ ewos_status ewos_toolbox_build(const ewos_domain* domain, const double* x, int64
         cudaError_t e2 = cudaMalloc(&tb->rec_steps, sizeof(int32_t) * n * walks);
         cudaError_t e3 = cudaMalloc(&tb->rec_mass, tb->elem() * n * walks);
         cudaError_t e4 = cudaMalloc(&tb->rec_vhash, sizeof(uint32_t) * n * walks);
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess) {
+        cudaError_t e5 = cudaMalloc(&tb->rec_xexit, tb->elem() * n * walks * domain->dim);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess || e5 != cudaSuccess) {
             set_error("records: out of memory");
             s = EWOS_ENOMEM;
         }
@@ -203,6 +205,7 @@ ewos_status ewos_toolbox_get(const ewos_toolbox* tb, int which, void* dst, size_
         case EWOS_WALK_STEPS: src = tb->rec_steps; count = tb->n * tb->N; raw_elem = 4; break;
         case EWOS_WALK_MASS: src = tb->rec_mass; count = tb->n * tb->N; widen = true; break;
         case EWOS_WALK_VHASH: src = tb->rec_vhash; count = tb->n * tb->N; raw_elem = 4; break;
+        case EWOS_WALK_XEXIT: src = tb->rec_xexit; count = tb->n * tb->N * d; widen = true; break;
         default: set_error("ewos_toolbox_get: unknown array"); return EWOS_EINVAL;
     }
     if (!src) { set_error("ewos_toolbox_get: array not available for this toolbox"); return EWOS_EINVAL; }

@@ -46,6 +46,7 @@ struct ewos_toolbox {
     int32_t* rec_steps = nullptr;
     void* rec_mass = nullptr;        // T [n][N]
     uint32_t* rec_vhash = nullptr;   // [n][N]
+    void* rec_xexit = nullptr;       // T [n][N][d]
     ewos_build_report rep{};
     ewos::SolveWorkspace* ws = nullptr;
     size_t elem() const { return precision == 64 ? 8 : 4; }

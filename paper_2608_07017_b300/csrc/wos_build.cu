@@ -332,6 +332,7 @@ struct WalkArgs {
     int32_t* rec_steps;
     T* rec_mass;
     uint32_t* rec_vhash;   // XOR over the walk's interior binnings of cellmix(step tag, cell)
+    T* rec_xexit;          // [n][N][D] stopping point
 };
 
 // walk-record digest of one interior binning: the splitmix64 output function applied to
@@ -451,6 +452,8 @@ __global__ void __launch_bounds__(512, 1) wos_walk_kernel(WalkArgs<T, D> a) {
                     a.rec_exit[ri] = jz;
                     a.rec_steps[ri] = (int32_t)(k - 1);
                     a.rec_mass[ri] = mass / T(2 * D);
+#pragma unroll
+                    for (int c = 0; c < D; ++c) a.rec_xexit[ri * D + c] = X[c];
                     atomicXor(&a.rec_vhash[ri], vh);
                     vh = 0u;
                     mass = T(0);
@@ -693,6 +696,7 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     a.row_counter = ctx.d_counter; a.stat_steps = ctx.d_stats; a.stat_capped = ctx.d_stats + 1;
     a.rec_exit = tb->rec_exit; a.rec_steps = tb->rec_steps; a.rec_mass = (T*)tb->rec_mass;
     a.rec_vhash = tb->rec_vhash;
+    a.rec_xexit = (T*)tb->rec_xexit;
     if (tb->rec_vhash) EWOS_CUDA_TRY(cudaMemsetAsync(tb->rec_vhash, 0, sizeof(uint32_t) * n * tb->N, st));
 
     const size_t acc_bytes = sizeof(T) * ((size_t)(D + 1) * m + (size_t)D * p) + sizeof(uint32_t) * p;

@@ -20,7 +20,7 @@ _lib = None
 OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ENOCONV, ETIMEOUT, ESTEPCAP = range(8)
 SDF = {"ball": 0, "box": 1, "polygon": 2}
 ARR = {"G": 0, "gradG": 1, "H": 2, "gradH": 3, "Hc": 4, "lambda": 5, "walk_exit": 6, "walk_steps": 7,
-       "walk_mass": 8, "walk_vhash": 9}
+       "walk_mass": 8, "walk_vhash": 9, "walk_xexit": 10}
 NL = {"linear": 0, "semilinear": 1, "quasilinear": 2}
 MODE = {"fp64": 0, "mixed": 1}
 
@@ -150,7 +150,7 @@ class Toolbox:
         d, n, m, p = self.dim, self.n, self.m, self.p
         shapes = {"G": (n, m), "gradG": (d, n, m), "H": (n, p), "gradH": (d, n, p), "Hc": (n, p), "lambda": (n,)}
         dtypes = {"Hc": np.uint32, "walk_exit": np.int32, "walk_steps": np.int32, "walk_vhash": np.uint32}
-        shape = shapes.get(which, (n, walks))
+        shape = shapes.get(which, (n, walks, d) if which == "walk_xexit" else (n, walks))
         out = np.zeros(shape, dtype=dtypes.get(which, np.float64))
         _check(lib().ewos_toolbox_get(self._h, ARR[which], out.ctypes.data, out.nbytes, 0), f"get {which}")
         return out

@@ -14,6 +14,9 @@ to that level.  Entries must satisfy
 
 for the gradient matrices with max(...) also over the sum of the magnitudes of the entry's terms
 ((d/r0) G_ij for gradG, (d/r0) H_ij for gradH), since those entries cancel terms of both signs;
+for FP32 walks bound_row also holds the rounding term of the arithmetic, 2 delta_row Grsum_ij +
+4 u G_ij (u = 2^-24; delta_row = largest stopping-point difference of the row's non-divergent
+walks; Grsum = oracle's sum of r/(2dN) over the same binnings), times d/r0 for gradG;
 where bound_row bounds what the divergent walks of that row can move:
     G      sum_div (mass_gpu + mass_oracle) / N                 (mass = sum r_k^2 / (2d))
     gradG  sum_div [ (d/r0) (mass_gpu + mass_oracle) + d r0 ] / N
@@ -23,7 +26,10 @@ where bound_row bounds what the divergent walks of that row can move:
 import numpy as np
 
 
-def compare_rows(gpu, orc, rows, N, dim, r0, rel=1e-4, drift_rel=1e-5):
+U32 = 2.0 ** -24
+
+
+def compare_rows(gpu, orc, rows, N, dim, r0, rel=1e-4, drift_rel=1e-5, fp32=False):
     """gpu: dict with G [n][m], gradG [d][n][m], Hc [n][p], gradH [d][n][p] and records
     exit/steps/vhash/mass [n][N] (full toolbox); orc: oracle.walk_rows(..., records=True) for
     ``rows``.  Returns a report dict; raises AssertionError on a violation."""
@@ -39,6 +45,16 @@ def compare_rows(gpu, orc, rows, N, dim, r0, rel=1e-4, drift_rel=1e-5):
     mass_div = np.where(div, gm + rec["gmass"], 0.0).sum(1)
     out = dict(exit_equal=float(same_exit.mean()), divergent=float(div.mean()), ndiv=int(ndiv.sum()),
                binning_divergent=float(binning.mean()), drifted=float((drift & ~binning).mean()))
+    # FP32 rounding term: a contribution r^2 computed at a position off by delta differs by at most
+    # 2 r delta + r^2 (4 u); delta per row = the largest stopping-point difference of its
+    # non-divergent walks (positions only accumulate error along a walk)
+    if fp32:
+        dx = np.abs(gpu["walk_xexit"][rows] - rec["xexit"]).max(axis=2)
+        delta = np.where(div, 0.0, dx).max(axis=1) + 4 * U32
+        rnd_G = 2 * delta[:, None] * orc["Grsum"] + 4 * U32 * orc["G"]
+        out["delta_max"] = float(delta.max())
+    else:
+        rnd_G = np.zeros_like(orc["G"])
 
     def check(name, a, b, bound, extra_scale=None):
         scale = np.maximum(np.abs(b), np.abs(b).mean(axis=-1, keepdims=True))
@@ -49,13 +65,13 @@ def compare_rows(gpu, orc, rows, N, dim, r0, rel=1e-4, drift_rel=1e-5):
         out[name + "_maxratio"] = float(np.max(np.abs(a - b) / np.maximum(lim, 1e-300)))
         assert not bad.any(), f"{name}: {int(bad.sum())} entries out of tolerance; worst ratio {out[name + '_maxratio']:.3g}"
 
-    check("G", gpu["G"][rows], orc["G"], (mass_div / N)[:, None])
+    check("G", gpu["G"][rows], orc["G"], (mass_div / N)[:, None] + rnd_G)
     bgg = ((dim / r0) * mass_div + dim * r0 * ndiv) / N
     # a gradient entry sums terms of both signs; the magnitude its rounding scales with is the sum of
     # the terms' magnitudes, at most (d/r0) G_ij for the path terms (|U_0| = 1)
     absg = (dim / r0)[:, None] * orc["G"]
     for c in range(dim):
-        check(f"gradG{c}", gpu["gradG"][c][rows], orc["gradG"][c], bgg[:, None], absg)
+        check(f"gradG{c}", gpu["gradG"][c][rows], orc["gradG"][c], bgg[:, None] + (dim / r0)[:, None] * rnd_G, absg)
     dH = np.abs(gpu["Hc"][rows].astype(np.int64) - orc["Hc"])
     assert np.all(dH <= ndiv[:, None]), "exit counts differ by more than the divergent walks"
     bgh = 2 * (dim / r0) * ndiv / N
@@ -68,6 +84,6 @@ def compare_rows(gpu, orc, rows, N, dim, r0, rel=1e-4, drift_rel=1e-5):
 def gpu_arrays(tb, N, records=True):
     out = dict(G=tb.get("G"), gradG=tb.get("gradG"), Hc=tb.get("Hc"), gradH=tb.get("gradH"), H=tb.get("H"))
     if records:
-        for k in ("walk_exit", "walk_steps", "walk_vhash", "walk_mass"):
+        for k in ("walk_exit", "walk_steps", "walk_vhash", "walk_mass", "walk_xexit"):
             out[k] = tb.get(k, walks=N)
     return out
