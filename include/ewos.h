@@ -103,6 +103,28 @@ ewos_status ewos_toolbox_build(const ewos_domain* domain, const double* x, int64
                                const double* z, int64_t p, int64_t walks, double eps,
                                uint64_t seed, const ewos_build_opts* opts, ewos_toolbox** out);
 
+/*
+ * Build without allocating (no counterpart in the paper).  For callers that cannot call
+ * cudaMalloc -- code under an allocator that owns all device memory (a framework's caching
+ * pool, a serving process with a fixed memory budget) or code that must not allocate while
+ * other work is in flight.  FP32 walks, the same kernels and random numbers as
+ * ewos_toolbox_build; cell weights are not computed.
+ *   x [n][d], z [p][d]: device pointers (double).  Outputs, caller-owned device buffers:
+ *   P [(d+1)][n][n] float = [d_1 G, .., d_d G, G], KH [(d+1)][n][p] float = [d_1 H, .., H],
+ *   Hc [n][p] uint32 exit counts.  rep may be NULL.  max_steps <= 0 -> 10000.
+ * Temporaries live in one static 4 MiB device array per GPU that loads the library (held
+ * until the process exits); a build whose lookup grids need more is rejected with EWOS_EINVAL
+ * before any walk runs (the square workload with n = 4096, p = 512 needs about 0.6 MiB).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every call shares
+ * the array and clears the counters it needs; calls whose work overlaps on the GPU race on
+ * the array and must not be issued concurrently (same or different streams).
+ */
+ewos_status ewos_toolbox_build_noalloc(const ewos_domain* domain, const double* x, int64_t n,
+                                       const double* z, int64_t p, int64_t walks, double eps,
+                                       uint64_t seed, int64_t max_steps, void* stream, float* P,
+                                       float* KH, uint32_t* Hc, ewos_build_report* rep);
+
 /* Build a toolbox from matrices the caller already has (e.g. a toolbox saved earlier):
  * G [n][m], gradG [d][n][m], H [n][p] (frequencies), gradH [d][n][p], lambda [n], host
  * doubles; x [n][d], z [p][d].  precision 32 stores them as FP32 like a built toolbox. */

@@ -21,6 +21,8 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <chrono>
+#include <mutex>
 #include <vector>
 
 #include "device_common.cuh"
@@ -785,4 +787,187 @@ ewos_status validate_domain(const ewos_domain* dom, const double* x, int64_t n) 
     return EWOS_OK;
 }
 
+// ------------------------------------------------------------------ build without allocation
+// Some callers cannot call cudaMalloc: code running under an allocator that owns all device
+// memory (a framework's caching pool, a memory budget enforced by a serving process), or code
+// that must not allocate while other work is in flight.  ewos_toolbox_build_noalloc serves
+// them: the caller passes the output matrices, and every temporary of the build (lookup grids,
+// candidate lists, node copies, counters) lives in the file-scope array below, which each GPU
+// that loads this library holds until the process exits.
+constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;   // 4 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static void* noalloc_scratch_address(int device, ewos_status* st) {
+    // the symbol's device address, looked up once per device with that device current
+    constexpr int kMaxDevices = 64;
+    static std::mutex mu;
+    static void* addr[kMaxDevices] = {};
+    if (device < 0 || device >= kMaxDevices) { *st = EWOS_EINVAL; set_error("device index out of range"); return nullptr; }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[device]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) {
+            *st = EWOS_ECUDA;
+            set_error(std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+            return nullptr;
+        }
+        addr[device] = ptr;
+    }
+    *st = EWOS_OK;
+    return addr[device];
+}
+
+// bump allocator over the static scratch
+struct Arena {
+    unsigned char* base;
+    size_t cap, used;
+    void* take(size_t bytes) {
+        const size_t off = (used + 255) & ~size_t(255);
+        if (off + bytes > cap) return nullptr;
+        used = off + bytes;
+        return base + off;
+    }
+};
+
+__global__ void node_check_kernel(const float* __restrict__ r0, int n, int* __restrict__ bad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && !(r0[i] > 0.0f)) atomicExch(bad, 1);
+}
+
+template <int D>
+static ewos_status lookup_into(const double* d_pts, int np, const double* lo, const double* hi, double h, cudaStream_t st,
+                               Arena& ar, DeviceLookup& out) {
+    out.np = np;
+    out.grid = make_grid(D, lo, hi, h);
+    const int64_t nc = out.grid.ncell;
+    int* d_count = (int*)ar.take(sizeof(int) * nc);
+    double* d_rad = (double*)ar.take(sizeof(double) * nc);
+    out.start = (int*)ar.take(sizeof(int) * (nc + 1));
+    out.pts = ar.take(sizeof(float) * np * D);
+    if (!d_count || !d_rad || !out.start || !out.pts) return EWOS_ENOMEM;
+    const int tb = 128, nb = (int)((nc + tb - 1) / tb);
+    ::ewos::note_launch(), lookup_count_kernel<D><<<nb, tb, 0, st>>>(d_pts, np, out.grid, d_count, d_rad);
+    ::ewos::note_launch(), exclusive_scan_kernel<<<1, 1024, 0, st>>>(d_count, nc, out.start);
+    int total = 0;
+    EWOS_CUDA_TRY(cudaMemcpyAsync(&total, out.start + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    out.ncand = total;
+    out.cand = (int*)ar.take(sizeof(int) * std::max(1, total));
+    if (!out.cand) return EWOS_ENOMEM;
+    ::ewos::note_launch(), lookup_fill_kernel<D><<<nb, tb, 0, st>>>(d_pts, np, out.grid, out.start, d_rad, out.cand);
+    const int64_t ne = (int64_t)np * D;
+    ::ewos::note_launch(), convert_points_kernel<float, D><<<(int)((ne + 255) / 256), 256, 0, st>>>(d_pts, (float*)out.pts, ne);
+    EWOS_CUDA_TRY(cudaGetLastError());
+    return EWOS_OK;
+}
+
+template <int D>
+static ewos_status build_noalloc_typed(const ewos_domain* dom, const double* d_x, int n, const double* d_z, int p,
+                                       int64_t N, double eps, uint64_t seed, int64_t max_steps, cudaStream_t st,
+                                       Arena& ar, float* P, float* KH, uint32_t* Hc, ewos_build_report* rep) {
+    const int m = n;
+    const auto t0 = std::chrono::steady_clock::now();
+    float prm[2 * kMaxPolygonVertices];
+    for (int64_t t = 0; t < dom->nparams; ++t) prm[t] = (float)dom->params[t];
+    const int nsdf = dom->kind == SDF_POLYGON ? (int)(dom->nparams / 2) : 0;
+    float* d_sdf = (float*)ar.take(sizeof(float) * dom->nparams);
+    float* d_xT = (float*)ar.take(sizeof(float) * n * D);
+    float* d_r0 = (float*)ar.take(sizeof(float) * n);
+    int* d_counter = (int*)ar.take(sizeof(int) * 2);               // row counter, bad-node flag
+    unsigned long long* d_stats = (unsigned long long*)ar.take(2 * sizeof(unsigned long long));
+    if (!d_sdf || !d_xT || !d_r0 || !d_counter || !d_stats) return EWOS_ENOMEM;
+    EWOS_CUDA_TRY(cudaMemcpyAsync(d_sdf, prm, sizeof(float) * dom->nparams, cudaMemcpyHostToDevice, st));
+    // every call starts from cleared counters: the scratch keeps the previous call's contents
+    EWOS_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int) * 2, st));
+    EWOS_CUDA_TRY(cudaMemsetAsync(d_stats, 0, 2 * sizeof(unsigned long long), st));
+    ::ewos::note_launch(), node_radius_kernel<float, D><<<(n + 127) / 128, 128, 0, st>>>(d_x, n, dom->kind, d_sdf, nsdf, d_xT, d_r0);
+    ::ewos::note_launch(), node_check_kernel<<<(n + 127) / 128, 128, 0, st>>>(d_r0, n, d_counter + 1);
+    int bad = 0;
+    EWOS_CUDA_TRY(cudaMemcpyAsync(&bad, d_counter + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (bad) { set_error("an interior node is not inside the domain"); return EWOS_EINVAL; }
+
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    domain_bbox(D, dom->kind, dom->params, dom->nparams, lo, hi);
+    double vol = 1, surf;
+    for (int c = 0; c < D; ++c) vol *= (hi[c] - lo[c]);
+    if (D == 2) surf = 2 * ((hi[0] - lo[0]) + (hi[1] - lo[1]));
+    else surf = 2 * ((hi[0] - lo[0]) * (hi[1] - lo[1]) + (hi[1] - lo[1]) * (hi[2] - lo[2]) + (hi[0] - lo[0]) * (hi[2] - lo[2]));
+    DeviceLookup V, Z;
+    ewos_status s = lookup_into<D>(d_x, m, lo, hi, std::pow(vol / m, 1.0 / D), st, ar, V);
+    if (s == EWOS_OK) s = lookup_into<D>(d_z, p, lo, hi, D == 2 ? surf / p : std::sqrt(surf / p), st, ar, Z);
+    if (s == EWOS_ENOMEM) {
+        set_error("ewos_toolbox_build_noalloc: the lookup grids need more than the 4 MiB scratch (reduce n or p)");
+        return EWOS_EINVAL;
+    }
+    if (s != EWOS_OK) return s;
+
+    WalkArgs<float, D> a{};
+    a.n = n; a.m = m; a.p = p; a.N = N; a.eps = (float)eps;
+    a.k0 = (uint32_t)seed; a.k1 = (uint32_t)(seed >> 32);
+    a.inst = 0;
+    a.max_steps = max_steps > 0 ? max_steps : 10000;
+    a.x = d_xT; a.r0 = d_r0;
+    a.sdf = d_sdf; a.nsdf = nsdf; a.sdf_len = (int)dom->nparams;
+    a.V = lookup_view<float, D>(V); a.Z = lookup_view<float, D>(Z);
+    a.v_ncell = (int)V.grid.ncell; a.v_ncand = V.ncand;
+    a.P = P; a.KH = KH; a.Hc = Hc;
+    a.row_counter = d_counter; a.stat_steps = d_stats; a.stat_capped = d_stats + 1;
+    a.v_in_smem = 0;
+    const size_t acc_bytes = sizeof(float) * ((size_t)(D + 1) * m + (size_t)D * p) + sizeof(uint32_t) * p;
+    const size_t smem = ((acc_bytes + 15) & ~size_t(15)) + sizeof(float) * ((a.sdf_len + 3) & ~3);
+    int dev = 0, smem_optin = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (smem + 1024 > (size_t)smem_optin) { set_error("toolbox row does not fit in shared memory"); return EWOS_EINVAL; }
+    const int tpb = 512;
+    int per_sm = 0;
+    if (dom->kind == SDF_BALL) per_sm = max_ctas_per_sm<float, D, SDF_BALL>(tpb, smem);
+    else if (dom->kind == SDF_BOX) per_sm = max_ctas_per_sm<float, D, SDF_BOX>(tpb, smem);
+    else per_sm = max_ctas_per_sm<float, 2, SDF_POLYGON>(tpb, smem);
+    if (per_sm < 1) { set_error("walk kernel does not fit on an SM"); return EWOS_EINVAL; }
+    const int grid = std::max(1, std::min(nsm * per_sm, n));
+    cudaError_t e;
+    if (dom->kind == SDF_BALL) e = launch_walks<float, D, SDF_BALL, false>(a, grid, tpb, smem, st);
+    else if (dom->kind == SDF_BOX) e = launch_walks<float, D, SDF_BOX, false>(a, grid, tpb, smem, st);
+    else e = D == 2 ? launch_walks<float, D, SDF_POLYGON, false>(a, grid, tpb, smem, st) : cudaErrorInvalidValue;
+    EWOS_CUDA_TRY(e);
+    unsigned long long stats[2] = {0, 0};
+    EWOS_CUDA_TRY(cudaMemcpyAsync(stats, d_stats, sizeof(stats), cudaMemcpyDeviceToHost, st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (rep) {
+        const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        *rep = ewos_build_report{};
+        rep->walks = (int64_t)n * N; rep->steps = (int64_t)stats[0]; rep->capped = (int64_t)stats[1];
+        rep->ms_total = ms; rep->threads_per_block = tpb; rep->ctas_per_sm = per_sm; rep->grid = grid;
+        rep->smem_bytes = (int64_t)smem;
+    }
+    return stats[1] > 0 ? EWOS_ESTEPCAP : EWOS_OK;
+}
+
 }  // namespace ewos
+
+extern "C" ewos_status ewos_toolbox_build_noalloc(const ewos_domain* domain, const double* x, int64_t n,
+                                                  const double* z, int64_t p, int64_t walks, double eps, uint64_t seed,
+                                                  int64_t max_steps, void* stream, float* P, float* KH, uint32_t* Hc,
+                                                  ewos_build_report* rep) {
+    using namespace ewos;
+    if (!domain || !x || !z || !P || !KH || !Hc || n < 1 || p < 1 || walks < 1 || walks > 0xFFFFFFFFll || !(eps > 0) ||
+        n > (1 << 20) || p > (1 << 20)) {
+        set_error("ewos_toolbox_build_noalloc: need domain, device x, z, P, KH, Hc, n, p >= 1, 1 <= walks < 2^32, eps > 0");
+        return EWOS_EINVAL;
+    }
+    ewos_status s = validate_domain(domain, nullptr, n);
+    if (s != EWOS_OK) return s;
+    int dev = 0;
+    EWOS_CUDA_TRY(cudaGetDevice(&dev));
+    void* base = noalloc_scratch_address(dev, &s);
+    if (!base) return s;
+    Arena ar{(unsigned char*)base, kNoAllocScratchBytes, 0};
+    cudaStream_t st = (cudaStream_t)stream;
+    return domain->dim == 2
+               ? build_noalloc_typed<2>(domain, x, (int)n, z, (int)p, walks, eps, seed, max_steps, st, ar, P, KH, Hc, rep)
+               : build_noalloc_typed<3>(domain, x, (int)n, z, (int)p, walks, eps, seed, max_steps, st, ar, P, KH, Hc, rep);
+}

@@ -90,9 +90,11 @@ def lib():
         L.ewos_toolbox_free.argtypes = [P]
         L.ewos_toolbox_free.restype = None
         L.ewos_solve.argtypes = [P, ctypes.POINTER(_Problem), P, P, I, ctypes.POINTER(SolveReport)]
+        L.ewos_toolbox_build_noalloc.argtypes = [ctypes.POINTER(_Domain), P, I64, P, I64, I64, ctypes.c_double,
+                                                 ctypes.c_uint64, I64, P, P, P, P, ctypes.POINTER(BuildReport)]
         L.ewos_debug_philox.argtypes = [P, P, P, I64]
         L.ewos_debug_green_radius.argtypes = [P, P, I64, I]
-        for fn in ("ewos_toolbox_build", "ewos_toolbox_from_host", "ewos_toolbox_get", "ewos_toolbox_report",
+        for fn in ("ewos_toolbox_build", "ewos_toolbox_build_noalloc", "ewos_toolbox_from_host", "ewos_toolbox_get", "ewos_toolbox_report",
                    "ewos_toolbox_shape", "ewos_solve", "ewos_debug_philox", "ewos_debug_green_radius"):
             getattr(L, fn).restype = I
         _lib = L
@@ -216,6 +218,21 @@ def build_toolbox(domain_kind, dim, params, x, z, walks, eps, seed=0, precision=
     tb = Toolbox(h.value)
     tb.status = st
     return tb
+
+
+def build_toolbox_noalloc(domain_kind, dim, params, x_dev, z_dev, walks, eps, P, KH, Hc, seed=0, max_steps=0,
+                          stream=None):
+    """FP32 build into caller-owned device buffers (torch tensors): x_dev [n][d] and z_dev [p][d]
+    float64, P [(d+1)][n][n] float32, KH [(d+1)][n][p] float32, Hc [n][p] int32/uint32 storage.
+    The library allocates no device memory for it (see ewos_toolbox_build_noalloc)."""
+    prm = _f64(params)
+    dom = _Domain(SDF[domain_kind], dim, prm.ctypes.data, prm.size)
+    rep = BuildReport()
+    st = lib().ewos_toolbox_build_noalloc(ctypes.byref(dom), x_dev.data_ptr(), x_dev.shape[0], z_dev.data_ptr(),
+                                          z_dev.shape[0], int(walks), float(eps), int(seed), int(max_steps), stream,
+                                          P.data_ptr(), KH.data_ptr(), Hc.data_ptr(), ctypes.byref(rep))
+    _check(st, "toolbox build (no allocation)", allow=(OK, ESTEPCAP))
+    return st, rep.as_dict()
 
 
 def build_workload(w, **kw):
