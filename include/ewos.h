@@ -69,6 +69,7 @@ typedef struct {
     int record_walks;         /* 1 -> keep per-walk records (exit cell, steps, G mass)      */
     uint32_t instance;        /* Philox instance word (separates independent builds)         */
     int inputs_on_device;     /* 1 -> x and z are device pointers                            */
+    double lookup_grid_scale; /* Voronoi grid spacing in units of (volume/n)^(1/d); 0 -> autotuned */
 } ewos_build_opts;
 
 typedef struct {
@@ -81,6 +82,8 @@ typedef struct {
     double ms_cells;          /* lambda_i Monte Carlo                                        */
     int threads_per_block, ctas_per_sm, grid, hash_in_smem;
     int64_t smem_bytes;
+    double lookup_grid_scale; /* V grid spacing used                                            */
+    int lookup_candidates;    /* fixed candidate slots per V grid cell (0: variable lists)      */
 } ewos_build_report;
 
 typedef struct ewos_toolbox ewos_toolbox;

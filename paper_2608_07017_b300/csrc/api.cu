@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -17,16 +18,38 @@ void set_error(const std::string& msg) { g_last_error = msg; }
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+static thread_local cudaStream_t g_alloc_stream = nullptr;
+void set_alloc_stream(cudaStream_t s) { g_alloc_stream = s; }
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    constexpr int kMaxDevices = 64;
+    static std::atomic<int> pool_ready[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kMaxDevices && !pool_ready[dev].exchange(1)) {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;      // keep freed blocks in this process's pool
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+    }
+    return cudaMallocAsync(p, bytes ? bytes : 1, g_alloc_stream);
+}
+
+cudaError_t dev_free(void* p) { return p ? cudaFreeAsync(p, g_alloc_stream) : cudaSuccess; }
+
 ewos_status build_toolbox(ewos_toolbox* tb, const ewos_domain* dom, const double* d_x, const double* d_z,
                           const ewos_build_opts& o);
 ewos_status validate_domain(const ewos_domain* dom, const double* x, int64_t n);
 
 static void release(ewos_toolbox* tb) {
     if (!tb) return;
-    cudaFree(tb->P); cudaFree(tb->KH); cudaFree(tb->Hc); cudaFree(tb->lambda);
-    cudaFree(tb->x); cudaFree(tb->z);
-    cudaFree(tb->rec_exit); cudaFree(tb->rec_steps); cudaFree(tb->rec_mass); cudaFree(tb->rec_vhash);
-    cudaFree(tb->rec_xexit);
+    AllocStream as(tb->stream);
+    ::ewos::dev_free(tb->P); ::ewos::dev_free(tb->KH); ::ewos::dev_free(tb->Hc); ::ewos::dev_free(tb->lambda);
+    ::ewos::dev_free(tb->x); ::ewos::dev_free(tb->z);
+    ::ewos::dev_free(tb->rec_exit); ::ewos::dev_free(tb->rec_steps); ::ewos::dev_free(tb->rec_mass); ::ewos::dev_free(tb->rec_vhash);
+    ::ewos::dev_free(tb->rec_xexit);
     free_workspace(tb->ws);
     delete tb;
 }
@@ -34,12 +57,12 @@ static void release(ewos_toolbox* tb) {
 static ewos_status alloc_matrices(ewos_toolbox* tb, bool counts) {
     const size_t e = tb->elem();
     const int64_t d1 = tb->dim + 1;
-    EWOS_CUDA_TRY(cudaMalloc(&tb->P, e * d1 * tb->n * tb->m));
-    EWOS_CUDA_TRY(cudaMalloc(&tb->KH, e * d1 * tb->n * tb->p));
-    if (counts) EWOS_CUDA_TRY(cudaMalloc(&tb->Hc, sizeof(uint32_t) * tb->n * tb->p));
-    EWOS_CUDA_TRY(cudaMalloc(&tb->lambda, sizeof(double) * tb->n));
-    EWOS_CUDA_TRY(cudaMalloc(&tb->x, sizeof(double) * tb->n * tb->dim));
-    EWOS_CUDA_TRY(cudaMalloc(&tb->z, sizeof(double) * tb->p * tb->dim));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->P, e * d1 * tb->n * tb->m));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->KH, e * d1 * tb->n * tb->p));
+    if (counts) EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->Hc, sizeof(uint32_t) * tb->n * tb->p));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->lambda, sizeof(double) * tb->n));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->x, sizeof(double) * tb->n * tb->dim));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->z, sizeof(double) * tb->p * tb->dim));
     return EWOS_OK;
 }
 
@@ -119,6 +142,7 @@ ewos_status ewos_toolbox_build(const ewos_domain* domain, const double* x, int64
     }
     ewos_status s = validate_domain(domain, hx, n);
     if (s != EWOS_OK) return s;
+    AllocStream as((cudaStream_t)o.stream);
     ewos_toolbox* tb = new ewos_toolbox();
     tb->dim = domain->dim; tb->precision = o.precision;
     tb->n = n; tb->m = n; tb->p = p; tb->N = walks; tb->eps = eps; tb->seed = seed; tb->instance = o.instance;
@@ -126,11 +150,11 @@ ewos_status ewos_toolbox_build(const ewos_domain* domain, const double* x, int64
     cudaGetDevice(&tb->device);
     s = alloc_matrices(tb, true);
     if (s == EWOS_OK && o.record_walks) {
-        cudaError_t e1 = cudaMalloc(&tb->rec_exit, sizeof(int32_t) * n * walks);
-        cudaError_t e2 = cudaMalloc(&tb->rec_steps, sizeof(int32_t) * n * walks);
-        cudaError_t e3 = cudaMalloc(&tb->rec_mass, tb->elem() * n * walks);
-        cudaError_t e4 = cudaMalloc(&tb->rec_vhash, sizeof(uint32_t) * n * walks);
-        cudaError_t e5 = cudaMalloc(&tb->rec_xexit, tb->elem() * n * walks * domain->dim);
+        cudaError_t e1 = ::ewos::dev_alloc((void**)&tb->rec_exit, sizeof(int32_t) * n * walks);
+        cudaError_t e2 = ::ewos::dev_alloc((void**)&tb->rec_steps, sizeof(int32_t) * n * walks);
+        cudaError_t e3 = ::ewos::dev_alloc((void**)&tb->rec_mass, tb->elem() * n * walks);
+        cudaError_t e4 = ::ewos::dev_alloc((void**)&tb->rec_vhash, sizeof(uint32_t) * n * walks);
+        cudaError_t e5 = ::ewos::dev_alloc((void**)&tb->rec_xexit, tb->elem() * n * walks * domain->dim);
         if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e4 != cudaSuccess || e5 != cudaSuccess) {
             set_error("records: out of memory");
             s = EWOS_ENOMEM;
@@ -157,6 +181,7 @@ ewos_status ewos_toolbox_from_host(int dim, int64_t n, int64_t p, const double* 
         return EWOS_EINVAL;
     }
     *out = nullptr;
+    AllocStream as((cudaStream_t)stream);
     ewos_toolbox* tb = new ewos_toolbox();
     tb->dim = dim; tb->precision = precision; tb->n = n; tb->m = n; tb->p = p; tb->N = 0;
     tb->stream = (cudaStream_t)stream;
@@ -166,7 +191,7 @@ ewos_status ewos_toolbox_from_host(int dim, int64_t n, int64_t p, const double* 
     const int64_t nm = n * n, np = n * p;
     std::vector<double> stage((size_t)(dim + 1) * std::max(nm, np));
     double* dstage = nullptr;
-    if (cudaMalloc(&dstage, sizeof(double) * stage.size()) != cudaSuccess) { release(tb); set_error("oom"); return EWOS_ENOMEM; }
+    if (::ewos::dev_alloc((void**)&dstage, sizeof(double) * stage.size()) != cudaSuccess) { release(tb); set_error("oom"); return EWOS_ENOMEM; }
     std::memcpy(stage.data(), gradG, sizeof(double) * dim * nm);
     std::memcpy(stage.data() + dim * nm, G, sizeof(double) * nm);
     cudaMemcpy(dstage, stage.data(), sizeof(double) * (dim + 1) * nm, cudaMemcpyHostToDevice);
@@ -181,7 +206,7 @@ ewos_status ewos_toolbox_from_host(int dim, int64_t n, int64_t p, const double* 
     cudaMemcpy(tb->x, x, sizeof(double) * n * dim, cudaMemcpyHostToDevice);
     cudaMemcpy(tb->z, z, sizeof(double) * p * dim, cudaMemcpyHostToDevice);
     cudaError_t e = cudaDeviceSynchronize();
-    cudaFree(dstage);
+    ::ewos::dev_free(dstage);
     if (e != cudaSuccess) { release(tb); set_error(cudaGetErrorString(e)); return EWOS_ECUDA; }
     *out = tb;
     return EWOS_OK;
@@ -212,6 +237,7 @@ ewos_status ewos_toolbox_get(const ewos_toolbox* tb, int which, void* dst, size_
     const size_t need = widen ? sizeof(double) * count : raw_elem * count;
     if (dst_bytes < need) { set_error("ewos_toolbox_get: destination too small"); return EWOS_EINVAL; }
     const cudaMemcpyKind k = dst_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    AllocStream as(tb->stream);
     if (!widen || tb->precision == 64) {
         EWOS_CUDA_TRY(cudaMemcpyAsync(dst, src, need, k, tb->stream));
         EWOS_CUDA_TRY(cudaStreamSynchronize(tb->stream));
@@ -219,12 +245,12 @@ ewos_status ewos_toolbox_get(const ewos_toolbox* tb, int which, void* dst, size_
     }
     double* tmp = nullptr;
     if (dst_on_device) tmp = (double*)dst;
-    else EWOS_CUDA_TRY(cudaMalloc(&tmp, need));
+    else EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tmp, need));
     ::ewos::note_launch(), widen_kernel<float><<<1024, 256, 0, tb->stream>>>((const float*)src, tmp, count);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && !dst_on_device) e = cudaMemcpyAsync(dst, tmp, need, cudaMemcpyDeviceToHost, tb->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(tb->stream);
-    if (!dst_on_device) cudaFree(tmp);
+    if (!dst_on_device) ::ewos::dev_free(tmp);
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return EWOS_ECUDA; }
     return EWOS_OK;
 }
@@ -251,12 +277,12 @@ ewos_status ewos_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t
     if (!ctr || !key || !out || count < 0) { set_error("ewos_debug_philox: bad arguments"); return EWOS_EINVAL; }
     if (count == 0) return EWOS_OK;
     uint32_t *dc = nullptr, *dout = nullptr;
-    EWOS_CUDA_TRY(cudaMalloc(&dc, 16 * count));
-    EWOS_CUDA_TRY(cudaMalloc(&dout, 16 * count));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&dc, 16 * count));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&dout, 16 * count));
     cudaMemcpy(dc, ctr, 16 * count, cudaMemcpyHostToDevice);
     ::ewos::note_launch(), philox_debug_kernel<<<256, 256>>>(dc, key[0], key[1], dout, count);
     cudaError_t e = cudaMemcpy(out, dout, 16 * count, cudaMemcpyDeviceToHost);
-    cudaFree(dc); cudaFree(dout);
+    ::ewos::dev_free(dc); ::ewos::dev_free(dout);
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return EWOS_ECUDA; }
     return EWOS_OK;
 }
@@ -269,13 +295,13 @@ ewos_status ewos_debug_green_radius(const void* u, void* R, int64_t count, int p
     if (count == 0) return EWOS_OK;
     const size_t e = precision == 64 ? 8 : 4;
     void *du = nullptr, *dR = nullptr;
-    EWOS_CUDA_TRY(cudaMalloc(&du, e * count));
-    EWOS_CUDA_TRY(cudaMalloc(&dR, e * count));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&du, e * count));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&dR, e * count));
     cudaMemcpy(du, u, e * count, cudaMemcpyHostToDevice);
     if (precision == 64) ::ewos::note_launch(), green_debug_kernel<double><<<256, 256>>>((const double*)du, (double*)dR, count);
     else ::ewos::note_launch(), green_debug_kernel<float><<<256, 256>>>((const float*)du, (float*)dR, count);
     cudaError_t err = cudaMemcpy(R, dR, e * count, cudaMemcpyDeviceToHost);
-    cudaFree(du); cudaFree(dR);
+    ::ewos::dev_free(du); ::ewos::dev_free(dR);
     if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return EWOS_ECUDA; }
     return EWOS_OK;
 }

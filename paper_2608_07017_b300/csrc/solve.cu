@@ -581,11 +581,11 @@ struct SolveWorkspace {
 
 void free_workspace(SolveWorkspace* ws) {
     if (!ws) return;
-    cudaFree(ws->Q); cudaFree(ws->Lam); cudaFree(ws->LUm); cudaFree(ws->M); cudaFree(ws->Jx);
-    cudaFree(ws->A); cudaFree(ws->b); cudaFree(ws->c); cudaFree(ws->f); cudaFree(ws->g); cudaFree(ws->nl);
-    cudaFree(ws->s); cudaFree(ws->x); cudaFree(ws->v); cudaFree(ws->w); cudaFree(ws->y); cudaFree(ws->u); cudaFree(ws->u2);
-    cudaFree(ws->scal); cudaFree(ws->umax);
-    cudaFree(ws->lu.pub); cudaFree(ws->lu.bar); cudaFree(ws->lu.ipiv);
+    ::ewos::dev_free(ws->Q); ::ewos::dev_free(ws->Lam); ::ewos::dev_free(ws->LUm); ::ewos::dev_free(ws->M); ::ewos::dev_free(ws->Jx);
+    ::ewos::dev_free(ws->A); ::ewos::dev_free(ws->b); ::ewos::dev_free(ws->c); ::ewos::dev_free(ws->f); ::ewos::dev_free(ws->g); ::ewos::dev_free(ws->nl);
+    ::ewos::dev_free(ws->s); ::ewos::dev_free(ws->x); ::ewos::dev_free(ws->v); ::ewos::dev_free(ws->w); ::ewos::dev_free(ws->y); ::ewos::dev_free(ws->u); ::ewos::dev_free(ws->u2);
+    ::ewos::dev_free(ws->scal); ::ewos::dev_free(ws->umax);
+    ::ewos::dev_free(ws->lu.pub); ::ewos::dev_free(ws->lu.bar); ::ewos::dev_free(ws->lu.ipiv);
     delete ws;
 }
 
@@ -597,33 +597,33 @@ static ewos_status ensure_workspace(ewos_toolbox* tb, int64_t nrhs) {
     const int D = tb->dim, E = D + 1;
     const int64_t n = tb->n, m = tb->m, p = tb->p;
     ws->D = D; ws->n = n; ws->m = m; ws->p = p; ws->cap_rhs = nrhs;
-    EWOS_CUDA_TRY(cudaMalloc(&ws->Q, sizeof(double) * E * n * m));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->Lam, sizeof(double) * m * m));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->LUm, sizeof(double) * m * m));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->Jx, sizeof(double) * n * m));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->M, sizeof(double) * n * E * E));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->A, sizeof(double) * n * D * D));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->b, sizeof(double) * n * D));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->c, sizeof(double) * n));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->f, sizeof(double) * n * nrhs));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->g, sizeof(double) * p * nrhs));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->nl, sizeof(double) * 64));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->s, sizeof(double) * m * nrhs));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->x, sizeof(double) * m * nrhs));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->v, sizeof(double) * E * n));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->w, sizeof(double) * E * n));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->y, sizeof(double) * m));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->u, sizeof(double) * n * nrhs));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->u2, sizeof(double) * n));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->scal, sizeof(double) * 4));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->umax, sizeof(unsigned long long)));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Q, sizeof(double) * E * n * m));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Lam, sizeof(double) * m * m));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->LUm, sizeof(double) * m * m));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Jx, sizeof(double) * n * m));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->M, sizeof(double) * n * E * E));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->A, sizeof(double) * n * D * D));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->b, sizeof(double) * n * D));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->c, sizeof(double) * n));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->f, sizeof(double) * n * nrhs));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->g, sizeof(double) * p * nrhs));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->nl, sizeof(double) * 64));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->s, sizeof(double) * m * nrhs));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->x, sizeof(double) * m * nrhs));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->v, sizeof(double) * E * n));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->w, sizeof(double) * E * n));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->y, sizeof(double) * m));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->u, sizeof(double) * n * nrhs));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->u2, sizeof(double) * n));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->scal, sizeof(double) * 4));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->umax, sizeof(unsigned long long)));
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     ws->lu.pub_bytes = (size_t)2 * nsm * (sizeof(double) + sizeof(int)) + 64 + sizeof(double) * ((size_t)2 * nsm * kNB + 2 * kNB);
-    EWOS_CUDA_TRY(cudaMalloc(&ws->lu.pub, ws->lu.pub_bytes));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->lu.bar, sizeof(GridBarrier)));
-    EWOS_CUDA_TRY(cudaMalloc(&ws->lu.ipiv, sizeof(int) * m));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.pub, ws->lu.pub_bytes));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.bar, sizeof(GridBarrier)));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.ipiv, sizeof(int) * m));
     return EWOS_OK;
 }
 
@@ -898,10 +898,11 @@ extern "C" ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, doub
         return EWOS_EINVAL;
     }
     if (pb->mode != EWOS_SOLVE_FP64 && pb->mode != EWOS_SOLVE_MIXED) { set_error("ewos_solve: unknown mode"); return EWOS_EINVAL; }
+    cudaStream_t st = pb->stream ? (cudaStream_t)pb->stream : tb->stream;
+    AllocStream as(st);
     ewos_status s = ensure_workspace(tb, pb->nrhs);
     if (s != EWOS_OK) return s;
     SolveWorkspace* ws = tb->ws;
-    cudaStream_t st = pb->stream ? (cudaStream_t)pb->stream : tb->stream;
     const cudaMemcpyKind k = pb->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const int D = tb->dim;
     EWOS_CUDA_TRY(cudaMemcpyAsync(ws->A, pb->A, sizeof(double) * tb->n * D * D, k, st));

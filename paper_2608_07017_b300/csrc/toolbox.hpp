@@ -13,6 +13,16 @@ namespace ewos {
 void set_error(const std::string& msg);
 void note_launch();            // counts every kernel launch of the library (ewos_launch_count)
 
+// Device memory of the library comes from the device's stream-ordered pool (cudaMallocAsync),
+// on the stream the current entry point runs on; freed blocks stay in the pool for reuse.
+cudaError_t dev_alloc(void** p, size_t bytes);
+cudaError_t dev_free(void* p);
+void set_alloc_stream(cudaStream_t s);
+struct AllocStream {
+    explicit AllocStream(cudaStream_t s) { set_alloc_stream(s); }
+    ~AllocStream() { set_alloc_stream(nullptr); }
+};
+
 #define EWOS_CUDA_TRY(expr)                                                              \
     do {                                                                                 \
         cudaError_t e__ = (expr);                                                        \

@@ -19,10 +19,10 @@
 
 #include <algorithm>
 #include <cmath>
-#include <cstring>
-#include <string>
 #include <chrono>
+#include <cstring>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "device_common.cuh"
@@ -55,59 +55,169 @@ __device__ void cell_box(const GridSpec& g, int64_t cell, double* blo, double* b
     }
 }
 
+// Candidate lists are computed in FP32 (FP64 is a small fraction of B300's arithmetic) with a
+// margin that keeps them supersets of the exact lists: lim = R_Q^2 (1 + 1e-4) + slack, where
+// slack (host: 1e-6 x squared extent of the domain) dominates the FP32 rounding of squared
+// distances.  One warp per grid cell; lanes scan the centres.
 template <int D>
-__global__ void lookup_count_kernel(const double* __restrict__ pts, int np, GridSpec g,
-                                    int* __restrict__ count, double* __restrict__ radius) {
-    const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= g.ncell) return;
-    double blo[3], bhi[3];
-    cell_box<D>(g, cell, blo, bhi);
-    double R2 = 1e300;
-    for (int j = 0; j < np; ++j) {
-        double mx = 0;
-        for (int c = 0; c < D; ++c) {
-            const double a = fabs(pts[j * D + c] - blo[c]), b = fabs(pts[j * D + c] - bhi[c]);
-            const double t = fmax(a, b);
-            mx += t * t;
-        }
-        R2 = fmin(R2, mx);
+__device__ __forceinline__ void cell_box_f(const GridSpec& g, int64_t cell, float* blo, float* bhi) {
+    int64_t rem = cell;
+    for (int c = 0; c < D; ++c) {
+        const int k = (int)(rem % g.dims[c]);
+        rem /= g.dims[c];
+        blo[c] = (float)(g.lo[c] + k * g.h);
+        bhi[c] = (float)(g.lo[c] + (k + 1) * g.h);
     }
-    const double lim = R2 * (1.0 + 1e-9) + 1e-24;
-    int cnt = 0;
-    for (int j = 0; j < np; ++j) {
-        double mn = 0;
-        for (int c = 0; c < D; ++c) {
-            const double v = pts[j * D + c];
-            const double t = v < blo[c] ? blo[c] - v : (v > bhi[c] ? v - bhi[c] : 0.0);
-            mn += t * t;
-        }
-        cnt += (mn <= lim);
-    }
-    count[cell] = cnt > kCandidateCap ? 0 : cnt;   // empty list = scan all centres
-    radius[cell] = lim;
 }
 
 template <int D>
-__global__ void lookup_fill_kernel(const double* __restrict__ pts, int np, GridSpec g,
-                                   const int* __restrict__ start, const double* __restrict__ radius,
-                                   int* __restrict__ cand) {
-    const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (cell >= g.ncell) return;
-    int w = start[cell];
-    const int e = start[cell + 1];
-    if (w == e) return;
-    double blo[3], bhi[3];
-    cell_box<D>(g, cell, blo, bhi);
-    const double lim = radius[cell];
-    for (int j = 0; j < np && w < e; ++j) {
-        double mn = 0;
-        for (int c = 0; c < D; ++c) {
-            const double v = pts[j * D + c];
-            const double t = v < blo[c] ? blo[c] - v : (v > bhi[c] ? v - bhi[c] : 0.0);
-            mn += t * t;
-        }
-        if (mn <= lim) cand[w++] = j;
+__device__ __forceinline__ float mind2(const float* __restrict__ pts, int j, const float* blo, const float* bhi) {
+    float mn = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+        const float v = pts[j * D + c];
+        const float t = v < blo[c] ? blo[c] - v : (v > bhi[c] ? v - bhi[c] : 0.f);
+        mn += t * t;
     }
+    return mn;
+}
+
+// Per grid cell Q: the centre c_b minimising maxdist(c, Q) and lim = R_Q^2 with margin.  A centre
+// is listed when mindist(c, Q)^2 <= lim and Q does not lie entirely on c_b's side of the bisector
+// of c and c_b (every corner of Q strictly closer to c_b, with a margin): both tests only drop
+// centres that cannot be nearest anywhere in Q, so the lists stay exact supersets.
+template <int D>
+struct CellTest {
+    float blo[3], bhi[3];
+    float lim;
+    float cb[3];
+    float dcb[8];         // squared distance of each corner to c_b
+    float slack;
+};
+
+template <int D>
+__device__ __forceinline__ void corner(const CellTest<D>& t, int k, float* x) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = (k >> c) & 1 ? t.bhi[c] : t.blo[c];
+}
+
+template <int D>
+__device__ __forceinline__ void cell_setup(const float* __restrict__ pts, int np, CellTest<D>& t) {
+    const int lane = threadIdx.x & 31;
+    float R2 = 3.0e38f;
+    int bj = 0x7fffffff;
+    for (int j = lane; j < np; j += 32) {
+        float mx = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const float v = pts[j * D + c];
+            const float u = fmaxf(fabsf(v - t.blo[c]), fabsf(v - t.bhi[c]));
+            mx += u * u;
+        }
+        if (mx < R2 || (mx == R2 && j < bj)) { R2 = mx; bj = j; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oR = __shfl_xor_sync(0xffffffffu, R2, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (oR < R2 || (oR == R2 && oj < bj)) { R2 = oR; bj = oj; }
+    }
+    t.lim = R2 * (1.0f + 1e-4f) + t.slack;
+#pragma unroll
+    for (int c = 0; c < D; ++c) t.cb[c] = pts[bj * D + c];
+#pragma unroll
+    for (int k = 0; k < (1 << D); ++k) {
+        float x[3];
+        corner(t, k, x);
+        float d2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) { const float u = x[c] - t.cb[c]; d2 += u * u; }
+        t.dcb[k] = d2;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ bool cell_candidate(const float* __restrict__ pts, int j, const CellTest<D>& t) {
+    if (mind2<D>(pts, j, t.blo, t.bhi) > t.lim) return false;
+    bool all_closer = true;
+#pragma unroll
+    for (int k = 0; k < (1 << D); ++k) {
+        float x[3];
+        corner(t, k, x);
+        float d2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) { const float u = x[c] - pts[j * D + c]; d2 += u * u; }
+        all_closer = all_closer && (t.dcb[k] < d2 * (1.0f - 1e-4f) - t.slack);
+    }
+    return !all_closer;
+}
+
+template <int D>
+__global__ void lookup_count_kernel(const float* __restrict__ pts, int np, GridSpec g, float slack,
+                                    int* __restrict__ count, float* __restrict__ radius, int* __restrict__ maxcount) {
+    const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (cell >= g.ncell) return;
+    CellTest<D> t;
+    cell_box_f<D>(g, cell, t.blo, t.bhi);
+    t.slack = slack;
+    cell_setup<D>(pts, np, t);
+    int cnt = 0;
+    for (int j = lane; j < np; j += 32) cnt += cell_candidate<D>(pts, j, t);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) {
+        count[cell] = cnt > kCandidateCap ? 0 : cnt;   // empty list = scan all centres
+        radius[cell] = t.lim;
+        if (maxcount) atomicMax(maxcount, cnt);
+    }
+}
+
+// ordered fill: ballot per 32 centres keeps the increasing index order
+template <int D, typename I>
+__device__ __forceinline__ void fill_cell(const float* __restrict__ pts, int np, const CellTest<D>& t,
+                                          I* __restrict__ out, int cap) {
+    const int lane = threadIdx.x & 31;
+    int w = 0;
+    for (int base = 0; base < np && w < cap; base += 32) {
+        const int j = base + lane;
+        const bool in = j < np && cell_candidate<D>(pts, j, t);
+        const unsigned msk = __ballot_sync(0xffffffffu, in);
+        const int off = w + __popc(msk & ((1u << lane) - 1u));
+        if (in && off < cap) out[off] = (I)j;
+        w += __popc(msk);
+    }
+}
+
+template <int D>
+__global__ void lookup_fill_kernel(const float* __restrict__ pts, int np, GridSpec g, float slack,
+                                   const int* __restrict__ start, int* __restrict__ cand) {
+    const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (cell >= g.ncell) return;
+    const int w = start[cell], e = start[cell + 1];
+    if (w == e) return;
+    CellTest<D> t;
+    cell_box_f<D>(g, cell, t.blo, t.bhi);
+    t.slack = slack;
+    cell_setup<D>(pts, np, t);
+    fill_cell<D, int>(pts, np, t, cand + w, e - w);
+}
+
+// fixed-stride candidate table: K slots per cell, candidates in increasing index, padded with
+// the sentinel np (a point placed far away, never nearest)
+template <int D>
+__global__ void lookup_fill_fixed_kernel(const float* __restrict__ pts, int np, GridSpec g, float slack, int K,
+                                         uint16_t* __restrict__ cand) {
+    const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (cell >= g.ncell) return;
+    CellTest<D> t;
+    cell_box_f<D>(g, cell, t.blo, t.bhi);
+    t.slack = slack;
+    cell_setup<D>(pts, np, t);
+    for (int q = lane; q < K; q += 32) cand[cell * K + q] = (uint16_t)np;
+    __syncwarp();
+    fill_cell<D, uint16_t>(pts, np, t, cand + cell * K, K);
 }
 
 // exclusive scan of count[0..len) into start[0..len], single block (len is at most a few 10^5)
@@ -151,20 +261,25 @@ template <typename T, int D>
 __global__ void convert_points_kernel(const double* __restrict__ in, T* __restrict__ out, int64_t count) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < count) out[t] = (T)in[t];
+    if (t < D) out[count + t] = T(1.0e18f);            // sentinel point of the fixed-stride table
 }
 
 struct DeviceLookup {
-    void* pts = nullptr;     // T [np][D]
+    void* pts = nullptr;     // T [np + 1][D] (last: sentinel)
     int* start = nullptr;
     int* cand = nullptr;
+    uint16_t* candK = nullptr;   // [ncell][K] when K > 0
+    int K = 0;
     GridSpec grid{};
     int64_t ncand = 0;
     int np = 0;
     void release() {
-        cudaFree(pts); cudaFree(start); cudaFree(cand);
-        pts = nullptr; start = nullptr; cand = nullptr;
+        ::ewos::dev_free(pts); ::ewos::dev_free(start); ::ewos::dev_free(cand); ::ewos::dev_free(candK);
+        pts = nullptr; start = nullptr; cand = nullptr; candK = nullptr;
     }
 };
+
+constexpr int kFixedCandMax = 16;
 
 static GridSpec make_grid(int dim, const double* lo, const double* hi, double h) {
     GridSpec g{};
@@ -173,7 +288,7 @@ static GridSpec make_grid(int dim, const double* lo, const double* hi, double h)
     for (int c = 0; c < 3; ++c) {
         if (c < dim) {
             const double ext = hi[c] - lo[c];
-            g.dims[c] = std::max(1, (int)std::ceil(ext / h + 1e-9));
+            g.dims[c] = std::max(1, (int)std::ceil(ext / h - 1e-9));
             const double pad = 0.5 * (g.dims[c] * h - ext);
             g.lo[c] = lo[c] - pad;
             g.ncell *= g.dims[c];
@@ -187,35 +302,55 @@ static GridSpec make_grid(int dim, const double* lo, const double* hi, double h)
 
 template <typename T>
 static ewos_status build_lookup(int dim, const double* d_pts, int np, const double* lo, const double* hi,
-                                double h, cudaStream_t st, DeviceLookup& out) {
+                                double h, cudaStream_t st, DeviceLookup& out, bool want_fixed) {
     out.np = np;
     out.grid = make_grid(dim, lo, hi, h);
     const int64_t nc = out.grid.ncell;
+    double ext = 0;
+    for (int c = 0; c < dim; ++c) ext = std::max(ext, std::max(std::fabs(lo[c]), std::fabs(hi[c])) + (hi[c] - lo[c]));
+    const float slack = (float)(1e-6 * ext * ext);
     int* d_count = nullptr;
-    double* d_rad = nullptr;
-    EWOS_CUDA_TRY(cudaMalloc(&d_count, sizeof(int) * nc));
-    EWOS_CUDA_TRY(cudaMalloc(&d_rad, sizeof(double) * nc));
-    EWOS_CUDA_TRY(cudaMalloc(&out.start, sizeof(int) * (nc + 1)));
-    EWOS_CUDA_TRY(cudaMalloc(&out.pts, sizeof(T) * np * dim));
-    const int tb = 128;
-    const int nb = (int)((nc + tb - 1) / tb);
-    if (dim == 2) ::ewos::note_launch(), lookup_count_kernel<2><<<nb, tb, 0, st>>>(d_pts, np, out.grid, d_count, d_rad);
-    else ::ewos::note_launch(), lookup_count_kernel<3><<<nb, tb, 0, st>>>(d_pts, np, out.grid, d_count, d_rad);
-    ::ewos::note_launch(), exclusive_scan_kernel<<<1, 1024, 0, st>>>(d_count, nc, out.start);
-    int total = 0;
-    EWOS_CUDA_TRY(cudaMemcpyAsync(&total, out.start + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
-    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
-    out.ncand = total;
-    EWOS_CUDA_TRY(cudaMalloc(&out.cand, sizeof(int) * std::max(1, total)));
-    if (dim == 2) ::ewos::note_launch(), lookup_fill_kernel<2><<<nb, tb, 0, st>>>(d_pts, np, out.grid, out.start, d_rad, out.cand);
-    else ::ewos::note_launch(), lookup_fill_kernel<3><<<nb, tb, 0, st>>>(d_pts, np, out.grid, out.start, d_rad, out.cand);
+    float* d_rad = nullptr;
+    float* d_pf = nullptr;
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_count, sizeof(int) * (nc + 1)));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_rad, sizeof(float) * nc));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_pf, sizeof(float) * (np + 1) * dim));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&out.start, sizeof(int) * (nc + 1)));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&out.pts, sizeof(T) * (np + 1) * dim));
+    EWOS_CUDA_TRY(cudaMemsetAsync(d_count + nc, 0, sizeof(int), st));
     const int64_t ne = (int64_t)np * dim;
-    if (dim == 2) ::ewos::note_launch(), convert_points_kernel<T, 2><<<(int)((ne + 255) / 256), 256, 0, st>>>(d_pts, (T*)out.pts, ne);
-    else ::ewos::note_launch(), convert_points_kernel<T, 3><<<(int)((ne + 255) / 256), 256, 0, st>>>(d_pts, (T*)out.pts, ne);
-    EWOS_CUDA_TRY(cudaGetLastError());
+    const int cb = (int)((ne + 255) / 256);
+    if (dim == 2) {
+        ::ewos::note_launch(), convert_points_kernel<float, 2><<<cb, 256, 0, st>>>(d_pts, d_pf, ne);
+        ::ewos::note_launch(), convert_points_kernel<T, 2><<<cb, 256, 0, st>>>(d_pts, (T*)out.pts, ne);
+    } else {
+        ::ewos::note_launch(), convert_points_kernel<float, 3><<<cb, 256, 0, st>>>(d_pts, d_pf, ne);
+        ::ewos::note_launch(), convert_points_kernel<T, 3><<<cb, 256, 0, st>>>(d_pts, (T*)out.pts, ne);
+    }
+    const int tb = 256;
+    const int nb = (int)((nc * 32 + tb - 1) / tb);
+    if (dim == 2) ::ewos::note_launch(), lookup_count_kernel<2><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, d_count, d_rad, d_count + nc);
+    else ::ewos::note_launch(), lookup_count_kernel<3><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, d_count, d_rad, d_count + nc);
+    ::ewos::note_launch(), exclusive_scan_kernel<<<1, 1024, 0, st>>>(d_count, nc, out.start);
+    int hv[2] = {0, 0};
+    EWOS_CUDA_TRY(cudaMemcpyAsync(&hv[0], out.start + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EWOS_CUDA_TRY(cudaMemcpyAsync(&hv[1], d_count + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
     EWOS_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(d_count);
-    cudaFree(d_rad);
+    const int total = hv[0], kmax = hv[1];
+    out.ncand = total;
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&out.cand, sizeof(int) * std::max(1, total)));
+    if (dim == 2) ::ewos::note_launch(), lookup_fill_kernel<2><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, out.start, out.cand);
+    else ::ewos::note_launch(), lookup_fill_kernel<3><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, out.start, out.cand);
+    if (want_fixed && kmax >= 1 && kmax <= kFixedCandMax && np < 65535) {
+        out.K = kmax;
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&out.candK, sizeof(uint16_t) * nc * kmax));
+        if (dim == 2) ::ewos::note_launch(), lookup_fill_fixed_kernel<2><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, kmax, out.candK);
+        else ::ewos::note_launch(), lookup_fill_fixed_kernel<3><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, kmax, out.candK);
+    }
+    EWOS_CUDA_TRY(cudaGetLastError());
+    ::ewos::dev_free(d_count);
+    ::ewos::dev_free(d_rad);
+    ::ewos::dev_free(d_pf);
     return EWOS_OK;
 }
 
@@ -324,6 +459,8 @@ struct WalkArgs {
     int v_in_smem;
     int v_ncell;
     int64_t v_ncand;
+    const uint16_t* v_candK;   // fixed-stride table [ncell][v_K] or NULL
+    int v_K;
     T* P;              // [(D+1)][n][m]
     T* KH;             // [(D+1)][n][p]
     uint32_t* Hc;      // [n][p]
@@ -377,34 +514,113 @@ __device__ __forceinline__ void draw_step(uint32_t l, uint32_t k, uint32_t row, 
     }
 }
 
+// nearest V centre through the fixed-stride table (K slots per grid cell, uniform trip count)
+template <typename T, int D>
+__device__ __forceinline__ int nearest_fixed(const Lookup<T, D>& L, const uint16_t* __restrict__ candK, int K,
+                                             const T* q) {
+    const int cell = lookup_cell(L, q);
+    const uint16_t* c = candK + (size_t)cell * K;
+    T best = T(3.0e38f);
+    int bi = 0;
+    for (int t = 0; t < K; ++t) {
+        const int j = c[t];
+        T d2 = 0;
+#pragma unroll
+        for (int cc = 0; cc < D; ++cc) { const T dd = q[cc] - L.pts[j * D + cc]; d2 += dd * dd; }
+        if (d2 < best) { best = d2; bi = j; }
+    }
+    return bi;
+}
+
+constexpr int kQueue = 64;   // per-warp queue of stopped walks awaiting their boundary binning
+
+template <typename T, int D>
+struct WalkQueue {
+    T* X;          // [warps][kQueue][D] stopping point
+    T* U;          // [warps][kQueue][D] first direction U_0
+    uint32_t* L;   // [warps][kQueue] walk index      (records only)
+    uint32_t* vh;  // [warps][kQueue] binning digest  (records only)
+    uint32_t* K;   // [warps][kQueue] steps           (records only)
+    T* mass;       // [warps][kQueue] G mass          (records only)
+};
+
+// bytes of the per-warp queues in shared memory
+template <typename T, int D>
+__host__ __device__ constexpr size_t queue_bytes(int nwarps, bool record) {
+    return (size_t)nwarps * kQueue * (2 * D * sizeof(T) + (record ? 3 * sizeof(uint32_t) + sizeof(T) : 0));
+}
+
+template <typename T, int D, bool RECORD>
+__device__ __forceinline__ void bin_stopped(const WalkArgs<T, D>& a, const WalkQueue<T, D>& q, int slot, int row,
+                                            T* accKH, uint32_t* accH) {
+    T X[D], U[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) { X[c] = q.X[slot * D + c]; U[c] = q.U[slot * D + c]; }
+    const int jz = nearest_or_scan(a.Z, a.p, X);
+    atomicAdd(&accH[jz], 1u);
+#pragma unroll
+    for (int c = 0; c < D; ++c) atomicAdd(&accKH[(size_t)c * a.p + jz], U[c]);
+    if (RECORD) {
+        const size_t ri = (size_t)row * a.N + q.L[slot];
+        a.rec_exit[ri] = jz;
+#pragma unroll
+        for (int c = 0; c < D; ++c) a.rec_xexit[ri * D + c] = X[c];
+        a.rec_mass[ri] = q.mass[slot];
+        a.rec_steps[ri] = (int32_t)q.K[slot];
+        atomicXor(&a.rec_vhash[ri], q.vh[slot]);
+    }
+}
+
 template <typename T, int D, int KIND, bool RECORD>
-__global__ void __launch_bounds__(512, 1) wos_walk_kernel(WalkArgs<T, D> a) {
+__global__ void __launch_bounds__(1024, 1) wos_walk_kernel(WalkArgs<T, D> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // shared layout: acc [(D+1)][m] T | accKH [D][p] T | accH [p] u32 | sdf params | V lookup
+    // shared layout: acc [(D+1)][m] T | accKH [D][p] T | accH [p] u32 | sdf params | per-warp
+    // queues | V lookup (points, then the fixed-stride table or the CSR lists)
     T* acc = reinterpret_cast<T*>(smem_raw);
     T* accKH = acc + (size_t)(D + 1) * a.m;
     uint32_t* accH = reinterpret_cast<uint32_t*>(accKH + (size_t)D * a.p);
-    T* s_sdf = reinterpret_cast<T*>(
-        (reinterpret_cast<uintptr_t>(accH + a.p) + 15) & ~uintptr_t(15));
-    unsigned char* s_v = reinterpret_cast<unsigned char*>(s_sdf + ((a.sdf_len + 3) & ~3));
+    T* s_sdf = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(accH + a.p) + 15) & ~uintptr_t(15));
+    const int nwarps = blockDim.x >> 5;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WalkQueue<T, D> q;
+    q.X = s_sdf + ((a.sdf_len + 3) & ~3);
+    q.U = q.X + (size_t)nwarps * kQueue * D;
+    q.L = reinterpret_cast<uint32_t*>(q.U + (size_t)nwarps * kQueue * D);
+    const size_t qr = RECORD ? (size_t)nwarps * kQueue : 0;
+    q.vh = q.L + qr;
+    q.K = q.vh + qr;
+    q.mass = reinterpret_cast<T*>(q.K + qr);
+    unsigned char* s_v = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(q.mass + qr) + 15) & ~uintptr_t(15));
     __shared__ int s_row;
     __shared__ unsigned int s_walk;
+    __shared__ int s_qn[32];
 
     for (int t = threadIdx.x; t < a.sdf_len; t += blockDim.x) s_sdf[t] = a.sdf[t];
     Lookup<T, D> V = a.V;
+    const uint16_t* candK = a.v_candK;
     if (a.v_in_smem) {
         T* vp = reinterpret_cast<T*>(s_v);
-        int* vs = reinterpret_cast<int*>(vp + (size_t)a.m * D);
-        int* vc = vs + a.v_ncell + 1;
-        for (int t = threadIdx.x; t < a.m * D; t += blockDim.x) vp[t] = a.V.pts[t];
-        for (int t = threadIdx.x; t <= a.v_ncell; t += blockDim.x) vs[t] = a.V.start[t];
-        for (int64_t t = threadIdx.x; t < a.v_ncand; t += blockDim.x) vc[t] = a.V.cand[t];
-        V.pts = vp; V.start = vs; V.cand = vc;
+        for (int t = threadIdx.x; t < (a.m + 1) * D; t += blockDim.x) vp[t] = a.V.pts[t];
+        V.pts = vp;
+        if (a.v_K > 0) {
+            uint16_t* vk = reinterpret_cast<uint16_t*>(vp + (size_t)(a.m + 1) * D);
+            for (int64_t t = threadIdx.x; t < (int64_t)a.v_ncell * a.v_K; t += blockDim.x) vk[t] = a.v_candK[t];
+            candK = vk;
+        } else {
+            int* vs = reinterpret_cast<int*>(vp + (size_t)(a.m + 1) * D);
+            int* vc = vs + a.v_ncell + 1;
+            for (int t = threadIdx.x; t <= a.v_ncell; t += blockDim.x) vs[t] = a.V.start[t];
+            for (int64_t t = threadIdx.x; t < a.v_ncand; t += blockDim.x) vc[t] = a.V.cand[t];
+            V.start = vs; V.cand = vc;
+        }
     }
+    const int K = a.v_K;
     const int accN = (D + 1) * a.m;
     for (int t = threadIdx.x; t < accN; t += blockDim.x) acc[t] = T(0);
     for (int t = threadIdx.x; t < D * a.p; t += blockDim.x) accKH[t] = T(0);
     for (int t = threadIdx.x; t < a.p; t += blockDim.x) accH[t] = 0u;
+    if (threadIdx.x < 32) s_qn[threadIdx.x] = 0;
 
     unsigned long long my_steps = 0, my_capped = 0;
     const T invN = T(1) / (T)a.N;
@@ -427,14 +643,16 @@ __global__ void __launch_bounds__(512, 1) wos_walk_kernel(WalkArgs<T, D> a) {
             const T wsum = (D == 2) ? T(1) + S : T(1) + S + S * S;
 #pragma unroll
             for (int c = 0; c < D; ++c) pt[c] = xi[c] + r0 * S * Zb[c];
-            const int jb = nearest_or_scan(V, a.m, pt);
+            const int jb = K > 0 ? nearest_fixed(V, candK, K, pt) : nearest_or_scan(V, a.m, pt);
 #pragma unroll
             for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + jb], r02 * wsum * Zb[c]);
             if (RECORD) atomicXor(&a.rec_vhash[(size_t)row * a.N + l], cellmix(0xFFFFFFFFu, jb));
         }
 
-        // ---- the chains; a lane whose walk stops takes the next walk of the row and does its
-        // step 0 (at x_i, radius r0) in the same iteration as the other lanes' steps
+        // ---- the chains.  A lane whose walk stops queues its stopping point for boundary
+        // binning and takes the next walk of the row, doing that walk's step 0 (at x_i, radius
+        // r0) in the same iteration as the other lanes' steps; the warp bins queued walks
+        // together once it holds one per active lane.
         uint32_t l = atomicAdd(&s_walk, 1u);
         T X[D], U0[D], mass = T(0);
         uint32_t k = 0, vh = 0u;
@@ -443,23 +661,16 @@ __global__ void __launch_bounds__(512, 1) wos_walk_kernel(WalkArgs<T, D> a) {
         while (l < (uint64_t)a.N) {
             T r = k == 0 ? r0 : Sdf<T, D, KIND>::eval(s_sdf, a.nsdf, X);
             if (k > 0 && (r < a.eps || (int64_t)k > a.max_steps)) {
-                const int jz = nearest_or_scan(a.Z, a.p, X);
-                atomicAdd(&accH[jz], 1u);
+                const int pos = atomicAdd(&s_qn[wid], 1);
+                const int slot = wid * kQueue + pos;
 #pragma unroll
-                for (int c = 0; c < D; ++c) atomicAdd(&accKH[(size_t)c * a.p + jz], U0[c]);
+                for (int c = 0; c < D; ++c) { q.X[slot * D + c] = X[c]; q.U[slot * D + c] = U0[c]; }
+                if (RECORD) {
+                    q.L[slot] = l; q.mass[slot] = mass / T(2 * D); q.vh[slot] = vh; q.K[slot] = k - 1;
+                    vh = 0u; mass = T(0);
+                }
                 my_steps += k;
                 my_capped += (r >= a.eps);
-                if (RECORD) {
-                    const size_t ri = (size_t)row * a.N + l;
-                    a.rec_exit[ri] = jz;
-                    a.rec_steps[ri] = (int32_t)(k - 1);
-                    a.rec_mass[ri] = mass / T(2 * D);
-#pragma unroll
-                    for (int c = 0; c < D; ++c) a.rec_xexit[ri * D + c] = X[c];
-                    atomicXor(&a.rec_vhash[ri], vh);
-                    vh = 0u;
-                    mass = T(0);
-                }
                 l = atomicAdd(&s_walk, 1u);
                 if (l >= (uint64_t)a.N) break;
 #pragma unroll
@@ -472,7 +683,7 @@ __global__ void __launch_bounds__(512, 1) wos_walk_kernel(WalkArgs<T, D> a) {
             const T rR = r * R;
 #pragma unroll
             for (int c = 0; c < D; ++c) pt[c] = X[c] + rR * Zs[c];
-            const int j = nearest_or_scan(V, a.m, pt);
+            const int j = K > 0 ? nearest_fixed(V, candK, K, pt) : nearest_or_scan(V, a.m, pt);
             const T r2 = r * r;
             atomicAdd(&acc[(size_t)D * a.m + j], r2);
             if (k > 0) {
@@ -486,6 +697,27 @@ __global__ void __launch_bounds__(512, 1) wos_walk_kernel(WalkArgs<T, D> a) {
             for (int c = 0; c < D; ++c) X[c] += r * U[c];
             if (RECORD) { mass += r2; vh ^= cellmix(k, (uint32_t)j); }
             ++k;
+            // converged boundary binning of queued walks
+            const unsigned act = __activemask();
+            __syncwarp(act);
+            const int na = __popc(act);
+            const int rank = __popc(act & ((1u << lane) - 1u));
+            int qn = *(volatile int*)&s_qn[wid];
+            while (qn >= na) {
+                bin_stopped<T, D, RECORD>(a, q, wid * kQueue + qn - 1 - rank, row, accKH, accH);
+                qn -= na;
+            }
+            __syncwarp(act);
+            if (rank == 0) s_qn[wid] = qn;
+            __syncwarp(act);
+        }
+        // drain this warp's queue
+        __syncwarp();
+        {
+            const int qn = *(volatile int*)&s_qn[wid];
+            for (int e = lane; e < qn; e += 32) bin_stopped<T, D, RECORD>(a, q, wid * kQueue + e, row, accKH, accH);
+            __syncwarp();
+            if (lane == 0) s_qn[wid] = 0;
         }
         __syncthreads();
 
@@ -575,7 +807,7 @@ static void domain_bbox(int dim, int kind, const double* prm, int64_t nprm, doub
 }
 
 struct BuildContext {
-    DeviceLookup V, Z;
+    DeviceLookup V, Z, V2;       // V2: the V lookup on the alternative grid the autotuner tries
     void* d_sdf = nullptr;
     void* d_xT = nullptr;
     void* d_r0 = nullptr;
@@ -583,8 +815,8 @@ struct BuildContext {
     unsigned long long* d_stats = nullptr;
     unsigned int* d_counts = nullptr;
     ~BuildContext() {
-        V.release(); Z.release();
-        cudaFree(d_sdf); cudaFree(d_xT); cudaFree(d_r0); cudaFree(d_counter); cudaFree(d_stats); cudaFree(d_counts);
+        V.release(); Z.release(); V2.release();
+        ::ewos::dev_free(d_sdf); ::ewos::dev_free(d_xT); ::ewos::dev_free(d_r0); ::ewos::dev_free(d_counter); ::ewos::dev_free(d_stats); ::ewos::dev_free(d_counts);
     }
 };
 
@@ -612,6 +844,30 @@ static int max_ctas_per_sm(int tpb, size_t smem) {
     return nb;
 }
 
+// process-wide cache of the walk kernel configurations chosen by the autotuner
+struct TuneKey {
+    size_t elem; int dim, kind; int m, p; int64_t N; bool rec; int tpb_req, place_req, ctas_req; double grid_req;
+    bool operator==(const TuneKey& o) const {
+        return elem == o.elem && dim == o.dim && kind == o.kind && m == o.m && p == o.p && N == o.N && rec == o.rec &&
+               tpb_req == o.tpb_req && place_req == o.place_req && ctas_req == o.ctas_req && grid_req == o.grid_req;
+    }
+};
+struct TuneVal { int tpb; bool v_smem; int vgrid; };
+static std::mutex g_tune_mu;
+static std::vector<std::pair<TuneKey, TuneVal>> g_tune;
+
+static bool tune_lookup(const TuneKey& k, int& tpb, bool& v_smem, int& vgrid) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (auto& e : g_tune)
+        if (e.first == k) { tpb = e.second.tpb; v_smem = e.second.v_smem; vgrid = e.second.vgrid; return true; }
+    return false;
+}
+
+static void tune_store(const TuneKey& k, int tpb, bool v_smem, int vgrid) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune.push_back({k, TuneVal{tpb, v_smem, vgrid}});
+}
+
 template <typename T, int D>
 static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const double* d_x, const double* d_z,
                                const ewos_build_opts& o) {
@@ -628,10 +884,10 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     for (int64_t t = 0; t < dom->nparams; ++t) prmT[t] = (T)dom->params[t];
     const int sdf_len = (int)dom->nparams;
     const int nsdf = dom->kind == SDF_POLYGON ? (int)(dom->nparams / 2) : 0;
-    EWOS_CUDA_TRY(cudaMalloc(&ctx.d_sdf, sizeof(T) * std::max<int64_t>(1, dom->nparams)));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_sdf, sizeof(T) * std::max<int64_t>(1, dom->nparams)));
     EWOS_CUDA_TRY(cudaMemcpyAsync(ctx.d_sdf, prmT.data(), sizeof(T) * dom->nparams, cudaMemcpyHostToDevice, st));
-    EWOS_CUDA_TRY(cudaMalloc(&ctx.d_xT, sizeof(T) * n * D));
-    EWOS_CUDA_TRY(cudaMalloc(&ctx.d_r0, sizeof(T) * n));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_xT, sizeof(T) * n * D));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_r0, sizeof(T) * n));
     ::ewos::note_launch(), node_radius_kernel<T, D><<<(n + 127) / 128, 128, 0, st>>>(d_x, n, dom->kind, (const T*)ctx.d_sdf, nsdf,
                                                              (T*)ctx.d_xT, (T*)ctx.d_r0);
     EWOS_CUDA_TRY(cudaGetLastError());
@@ -646,10 +902,24 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     if (D == 2) surf = 2 * ((hi[0] - lo[0]) + (hi[1] - lo[1]));
     else surf = 2 * ((hi[0] - lo[0]) * (hi[1] - lo[1]) + (hi[1] - lo[1]) * (hi[2] - lo[2]) + (hi[0] - lo[0]) * (hi[2] - lo[2]));
     const double hz = D == 2 ? surf / p : std::sqrt(surf / p);
-    ewos_status s = build_lookup<T>(D, d_x, m, lo, hi, hv, st, ctx.V);
+    // V grid spacing: factor x (volume / m)^(1/d); the autotuner also tries the other factor
+    const double gf_default = o.lookup_grid_scale > 0 ? o.lookup_grid_scale : (D == 2 ? 1.0 : 0.5);
+    const double gf_alt = D == 2 ? 0.5 : 1.0;
+    const bool tune_grid = o.lookup_grid_scale <= 0 &&
+                           (o.threads_per_block <= 0 || !(o.hash_in_smem == 0 || o.hash_in_smem == 1));
+    ewos_status s = build_lookup<T>(D, d_x, m, lo, hi, hv * gf_default, st, ctx.V, true);
     if (s != EWOS_OK) return s;
-    s = build_lookup<T>(D, d_z, p, lo, hi, hz, st, ctx.Z);
+    s = build_lookup<T>(D, d_z, p, lo, hi, hz, st, ctx.Z, false);
     if (s != EWOS_OK) return s;
+    TuneKey key{sizeof(T), D, dom->kind, m, p, tb->N, o.record_walks != 0, o.threads_per_block, o.hash_in_smem,
+                o.ctas_per_sm, o.lookup_grid_scale};
+    int cached_tpb = 0, cached_grid = 0;
+    bool cached_smem = false;
+    const bool have_cached = tune_lookup(key, cached_tpb, cached_smem, cached_grid);
+    if (tune_grid && (!have_cached || cached_grid == 1)) {
+        s = build_lookup<T>(D, d_x, m, lo, hi, hv * gf_alt, st, ctx.V2, true);
+        if (s != EWOS_OK) return s;
+    }
     EWOS_CUDA_TRY(cudaEventRecord(ev[1], st));
 
     // cell weights
@@ -657,7 +927,7 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
         EWOS_CUDA_TRY(cudaMemcpyAsync(tb->lambda, o.cell_weights, sizeof(double) * n, cudaMemcpyHostToDevice, st));
     } else {
         const int64_t ns = o.cell_samples > 0 ? o.cell_samples : 10000000;
-        EWOS_CUDA_TRY(cudaMalloc(&ctx.d_counts, sizeof(unsigned int) * m));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_counts, sizeof(unsigned int) * m));
         EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counts, 0, sizeof(unsigned int) * m, st));
         Lookup<T, D> Vv = lookup_view<T, D>(ctx.V);
         const T l0 = (T)lo[0], l1 = (T)lo[1], l2 = (T)(D > 2 ? lo[2] : 0);
@@ -688,11 +958,10 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     a.max_steps = o.max_steps > 0 ? o.max_steps : 10000;
     a.x = (const T*)ctx.d_xT; a.r0 = (const T*)ctx.d_r0;
     a.sdf = (const T*)ctx.d_sdf; a.nsdf = nsdf; a.sdf_len = sdf_len;
-    a.V = lookup_view<T, D>(ctx.V); a.Z = lookup_view<T, D>(ctx.Z);
-    a.v_ncell = (int)ctx.V.grid.ncell; a.v_ncand = ctx.V.ncand;
+    a.Z = lookup_view<T, D>(ctx.Z);
     a.P = (T*)tb->P; a.KH = (T*)tb->KH; a.Hc = tb->Hc;
-    EWOS_CUDA_TRY(cudaMalloc(&ctx.d_counter, sizeof(int)));
-    EWOS_CUDA_TRY(cudaMalloc(&ctx.d_stats, 2 * sizeof(unsigned long long)));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_counter, sizeof(int)));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_stats, 2 * sizeof(unsigned long long)));
     EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counter, 0, sizeof(int), st));
     EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_stats, 0, 2 * sizeof(unsigned long long), st));
     a.row_counter = ctx.d_counter; a.stat_steps = ctx.d_stats; a.stat_capped = ctx.d_stats + 1;
@@ -701,43 +970,120 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     a.rec_xexit = (T*)tb->rec_xexit;
     if (tb->rec_vhash) EWOS_CUDA_TRY(cudaMemsetAsync(tb->rec_vhash, 0, sizeof(uint32_t) * n * tb->N, st));
 
+    const bool rec = o.record_walks != 0;
     const size_t acc_bytes = sizeof(T) * ((size_t)(D + 1) * m + (size_t)D * p) + sizeof(uint32_t) * p;
     const size_t sdf_bytes = sizeof(T) * ((sdf_len + 3) & ~3);
-    const size_t base = ((acc_bytes + 15) & ~size_t(15)) + sdf_bytes;
-    const size_t v_bytes = sizeof(T) * (size_t)m * D + sizeof(int) * (ctx.V.grid.ncell + 1 + ctx.V.ncand);
+    const DeviceLookup* Vs[2] = {&ctx.V, &ctx.V2};
+    auto v_bytes_of = [&](const DeviceLookup& L) {
+        return sizeof(T) * (size_t)(m + 1) * D +
+               (L.K > 0 ? sizeof(uint16_t) * L.grid.ncell * L.K : sizeof(int) * (L.grid.ncell + 1 + L.ncand)) + 16;
+    };
     int dev = 0, smem_optin = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const size_t budget = (size_t)smem_optin - 1024;
-    if (base > budget) {
-        set_error("toolbox row does not fit in shared memory (m, p too large for one CTA)");
-        return EWOS_EINVAL;
+    auto base_for = [&](int t) {
+        return (((acc_bytes + 15) & ~size_t(15)) + sdf_bytes + queue_bytes<T, D>(t / 32, rec) + 15) & ~size_t(15);
+    };
+    // a launch configuration: block size, V grid, where the V lookup lives
+    struct Cfg { int tpb; int vg; bool v_smem; size_t smem; int per_sm; int grid; };
+    auto configure = [&](int tpb, int vg, int want_smem, int rows, Cfg& c) -> bool {
+        const DeviceLookup& L = *Vs[vg];
+        if (!L.start) return false;
+        const size_t base = base_for(tpb);
+        if (base > budget) return false;
+        c.tpb = tpb;
+        c.vg = vg;
+        c.v_smem = want_smem != 0 && base + v_bytes_of(L) <= budget;
+        if (want_smem == 1 && !c.v_smem) return false;
+        c.smem = base + (c.v_smem ? v_bytes_of(L) : 0);
+        int ps = 0;
+        if (dom->kind == SDF_BALL) ps = max_ctas_per_sm<T, D, SDF_BALL>(tpb, c.smem);
+        else if (dom->kind == SDF_BOX) ps = max_ctas_per_sm<T, D, SDF_BOX>(tpb, c.smem);
+        else ps = max_ctas_per_sm<T, D, SDF_POLYGON>(tpb, c.smem);
+        if (ps < 1) return false;
+        if (o.ctas_per_sm > 0) ps = std::min(ps, o.ctas_per_sm);
+        c.per_sm = ps;
+        c.grid = std::max(1, std::min(nsm * ps, rows));
+        return true;
+    };
+    auto launch = [&](const Cfg& c, WalkArgs<T, D>& args) -> cudaError_t {
+        const DeviceLookup& L = *Vs[c.vg];
+        args.V = lookup_view<T, D>(L);
+        args.v_ncell = (int)L.grid.ncell; args.v_ncand = L.ncand;
+        args.v_K = L.K; args.v_candK = L.candK;
+        args.v_in_smem = c.v_smem ? 1 : 0;
+        if (dom->kind == SDF_BALL) return dispatch_walks<T, D, SDF_BALL>(args, rec, c.grid, c.tpb, c.smem, st);
+        if (dom->kind == SDF_BOX) return dispatch_walks<T, D, SDF_BOX>(args, rec, c.grid, c.tpb, c.smem, st);
+        return dispatch_walks<T, D, SDF_POLYGON>(args, rec, c.grid, c.tpb, c.smem, st);
+    };
+    Cfg cfg{};
+    const bool fixed_tpb = o.threads_per_block > 0;
+    const bool fixed_place = o.hash_in_smem == 0 || o.hash_in_smem == 1;
+    const int req_tpb = std::min(1024, (o.threads_per_block + 31) / 32 * 32);
+    if (fixed_tpb && fixed_place) {
+        if (!configure(req_tpb, 0, o.hash_in_smem, n, cfg)) {
+            set_error("walk kernel: requested block size / lookup placement does not fit");
+            return EWOS_EINVAL;
+        }
+    } else if (have_cached && configure(cached_tpb, cached_grid, cached_smem ? 1 : 0, n, cfg)) {
+        // configuration chosen earlier for this problem shape
+    } else {
+        // autotuner: time each candidate configuration on a prefix of rows once per problem
+        // shape (cached for the process); the prefix rows are recomputed by the full launch
+        std::vector<Cfg> cands;
+        for (int vg : {0, 1})
+            for (int t : {512, 1024}) {
+                if (fixed_tpb && t != req_tpb) continue;
+                for (int sm : {0, 1}) {
+                    if (fixed_place && sm != o.hash_in_smem) continue;
+                    Cfg c{};
+                    if (configure(t, vg, sm, n, c)) cands.push_back(c);
+                }
+            }
+        if (fixed_tpb && cands.empty()) {
+            Cfg c{};
+            if (configure(req_tpb, 0, 0, n, c)) cands.push_back(c);
+        }
+        if (cands.empty()) {
+            set_error("toolbox row does not fit in shared memory (m, p too large for one CTA)");
+            return EWOS_EINVAL;
+        }
+        if (cands.size() == 1) {
+            cfg = cands[0];
+        } else {
+            const int rows = std::min(n, 2 * nsm);
+            float best = 3.0e38f;
+            cudaEvent_t t0, t1;
+            cudaEventCreate(&t0); cudaEventCreate(&t1);
+            for (Cfg c : cands) {
+                c.grid = std::max(1, std::min(nsm * c.per_sm, rows));
+                WalkArgs<T, D> trial = a;
+                trial.n = rows;
+                EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counter, 0, sizeof(int), st));
+                cudaEventRecord(t0, st);
+                EWOS_CUDA_TRY(launch(c, trial));
+                cudaEventRecord(t1, st);
+                EWOS_CUDA_TRY(cudaEventSynchronize(t1));
+                float ms = 0;
+                cudaEventElapsedTime(&ms, t0, t1);
+                if (ms < best) { best = ms; cfg = c; }
+            }
+            cudaEventDestroy(t0); cudaEventDestroy(t1);
+            cfg.grid = std::max(1, std::min(nsm * cfg.per_sm, n));
+            EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counter, 0, sizeof(int), st));
+            EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_stats, 0, 2 * sizeof(unsigned long long), st));
+            if (tb->rec_vhash) EWOS_CUDA_TRY(cudaMemsetAsync(tb->rec_vhash, 0, sizeof(uint32_t) * n * tb->N, st));
+        }
+        tune_store(key, cfg.tpb, cfg.v_smem, cfg.vg);
     }
-    bool v_smem;
-    if (o.hash_in_smem == 0) v_smem = false;
-    else if (o.hash_in_smem == 1) v_smem = base + v_bytes <= budget;
-    else v_smem = base + v_bytes <= budget;
-    a.v_in_smem = v_smem ? 1 : 0;
-    const size_t smem = base + (v_smem ? v_bytes : 0);
-    const int tpb = o.threads_per_block > 0 ? std::min(512, (o.threads_per_block + 31) / 32 * 32) : 512;
-    int per_sm = 0;
-    if (dom->kind == SDF_BALL) per_sm = max_ctas_per_sm<T, D, SDF_BALL>(tpb, smem);
-    else if (dom->kind == SDF_BOX) per_sm = max_ctas_per_sm<T, D, SDF_BOX>(tpb, smem);
-    else per_sm = max_ctas_per_sm<T, D, SDF_POLYGON>(tpb, smem);
-    if (per_sm < 1) {
-        set_error("walk kernel does not fit on an SM with this block size and shared memory");
-        return EWOS_EINVAL;
-    }
-    if (o.ctas_per_sm > 0) per_sm = std::min(per_sm, o.ctas_per_sm);
-    const int grid = std::max(1, std::min(nsm * per_sm, n));
-    const bool rec = o.record_walks != 0;
     EWOS_CUDA_TRY(cudaEventRecord(ev[3], st));
-    cudaError_t e;
-    if (dom->kind == SDF_BALL) e = dispatch_walks<T, D, SDF_BALL>(a, rec, grid, tpb, smem, st);
-    else if (dom->kind == SDF_BOX) e = dispatch_walks<T, D, SDF_BOX>(a, rec, grid, tpb, smem, st);
-    else e = dispatch_walks<T, D, SDF_POLYGON>(a, rec, grid, tpb, smem, st);
-    EWOS_CUDA_TRY(e);
+    EWOS_CUDA_TRY(launch(cfg, a));
+    const int tpb = cfg.tpb, per_sm = cfg.per_sm, grid = cfg.grid;
+    const bool v_smem = cfg.v_smem;
+    const size_t smem = cfg.smem;
+
     EWOS_CUDA_TRY(cudaEventRecord(ev[4], st));
     unsigned long long stats[2] = {0, 0};
     EWOS_CUDA_TRY(cudaMemcpyAsync(stats, ctx.d_stats, sizeof(stats), cudaMemcpyDeviceToHost, st));
@@ -753,6 +1099,8 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     r.capped = (int64_t)stats[1];
     r.ms_total = ms[0]; r.ms_lookup = ms[1]; r.ms_cells = ms[2]; r.ms_walk = ms[3];
     r.threads_per_block = tpb; r.ctas_per_sm = per_sm; r.grid = grid; r.hash_in_smem = v_smem;
+    r.lookup_grid_scale = cfg.vg == 0 ? gf_default : gf_alt;
+    r.lookup_candidates = Vs[cfg.vg]->K;
     r.smem_bytes = (int64_t)smem;
     return EWOS_OK;
 }
@@ -841,13 +1189,18 @@ static ewos_status lookup_into(const double* d_pts, int np, const double* lo, co
     out.np = np;
     out.grid = make_grid(D, lo, hi, h);
     const int64_t nc = out.grid.ncell;
+    double ext = 0;
+    for (int c = 0; c < D; ++c) ext = std::max(ext, std::max(std::fabs(lo[c]), std::fabs(hi[c])) + (hi[c] - lo[c]));
+    const float slack = (float)(1e-6 * ext * ext);
     int* d_count = (int*)ar.take(sizeof(int) * nc);
-    double* d_rad = (double*)ar.take(sizeof(double) * nc);
+    float* d_rad = (float*)ar.take(sizeof(float) * nc);
     out.start = (int*)ar.take(sizeof(int) * (nc + 1));
-    out.pts = ar.take(sizeof(float) * np * D);
+    out.pts = ar.take(sizeof(float) * (np + 1) * D);
     if (!d_count || !d_rad || !out.start || !out.pts) return EWOS_ENOMEM;
-    const int tb = 128, nb = (int)((nc + tb - 1) / tb);
-    ::ewos::note_launch(), lookup_count_kernel<D><<<nb, tb, 0, st>>>(d_pts, np, out.grid, d_count, d_rad);
+    const int64_t ne = (int64_t)np * D;
+    ::ewos::note_launch(), convert_points_kernel<float, D><<<(int)((ne + 255) / 256), 256, 0, st>>>(d_pts, (float*)out.pts, ne);
+    const int tb = 256, nb = (int)((nc * 32 + tb - 1) / tb);
+    ::ewos::note_launch(), lookup_count_kernel<D><<<nb, tb, 0, st>>>((const float*)out.pts, np, out.grid, slack, d_count, d_rad, nullptr);
     ::ewos::note_launch(), exclusive_scan_kernel<<<1, 1024, 0, st>>>(d_count, nc, out.start);
     int total = 0;
     EWOS_CUDA_TRY(cudaMemcpyAsync(&total, out.start + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -855,9 +1208,7 @@ static ewos_status lookup_into(const double* d_pts, int np, const double* lo, co
     out.ncand = total;
     out.cand = (int*)ar.take(sizeof(int) * std::max(1, total));
     if (!out.cand) return EWOS_ENOMEM;
-    ::ewos::note_launch(), lookup_fill_kernel<D><<<nb, tb, 0, st>>>(d_pts, np, out.grid, out.start, d_rad, out.cand);
-    const int64_t ne = (int64_t)np * D;
-    ::ewos::note_launch(), convert_points_kernel<float, D><<<(int)((ne + 255) / 256), 256, 0, st>>>(d_pts, (float*)out.pts, ne);
+    ::ewos::note_launch(), lookup_fill_kernel<D><<<nb, tb, 0, st>>>((const float*)out.pts, np, out.grid, slack, out.start, out.cand);
     EWOS_CUDA_TRY(cudaGetLastError());
     return EWOS_OK;
 }
@@ -915,14 +1266,16 @@ static ewos_status build_noalloc_typed(const ewos_domain* dom, const double* d_x
     a.P = P; a.KH = KH; a.Hc = Hc;
     a.row_counter = d_counter; a.stat_steps = d_stats; a.stat_capped = d_stats + 1;
     a.v_in_smem = 0;
+    a.v_K = 0; a.v_candK = nullptr;
+    const int tpb = 512;
     const size_t acc_bytes = sizeof(float) * ((size_t)(D + 1) * m + (size_t)D * p) + sizeof(uint32_t) * p;
-    const size_t smem = ((acc_bytes + 15) & ~size_t(15)) + sizeof(float) * ((a.sdf_len + 3) & ~3);
+    const size_t smem = ((((acc_bytes + 15) & ~size_t(15)) + sizeof(float) * ((a.sdf_len + 3) & ~3) +
+                          queue_bytes<float, D>(tpb / 32, false) + 15) & ~size_t(15));
     int dev = 0, smem_optin = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (smem + 1024 > (size_t)smem_optin) { set_error("toolbox row does not fit in shared memory"); return EWOS_EINVAL; }
-    const int tpb = 512;
     int per_sm = 0;
     if (dom->kind == SDF_BALL) per_sm = max_ctas_per_sm<float, D, SDF_BALL>(tpb, smem);
     else if (dom->kind == SDF_BOX) per_sm = max_ctas_per_sm<float, D, SDF_BOX>(tpb, smem);
