@@ -157,7 +157,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--mode", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--serve-solves", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -207,6 +208,7 @@ def main():
     clocks.start()
     ms_total = 0.0
     walk_ms, build_ms, solve_ms, steps_total = [], [], [], 0
+    launches0 = ewos.launch_count()
     for _ in range(args.steps):
         flush.fill_(1.0)                      # L2 flush between timed iterations (outside the events)
         torch.cuda.synchronize()
@@ -223,6 +225,7 @@ def main():
         steps_total += br["steps"]
     torch.cuda.synchronize()
     ck = clocks.stop()
+    launches_per_step = (ewos.launch_count() - launches0) / args.steps
     if ws > 1:
         t = torch.tensor([ms_total], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -230,6 +233,28 @@ def main():
         st = torch.tensor([float(steps_total)], device=dev)
         torch.distributed.all_reduce(st)
         steps_total = int(st.item())
+
+    # served solves on one resident toolbox: mixed precision vs the plain FP64 GPU path
+    tbs = ewos.build_toolbox("box", 2, w.domain.params, xd, zd, w.walks, w.eps, seed=w.seed, precision=32,
+                             cell_weights=w.lam, stream=sp, on_device=True)
+    lam = tbs.get("lambda")
+    served = {}
+    for mode, count in (("mixed", args.serve_solves), ("fp64", max(2, min(3, args.serve_solves)))):
+        tbs.solve(Ad, fd, gd, b=bd, mode=mode, on_device=True, out=ud, stream=sp)      # workspace warm-up
+        lat = []
+        for _ in range(count):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, _, rep = tbs.solve(Ad, fd, gd, b=bd, mode=mode, on_device=True, out=ud, stream=sp)
+            torch.cuda.synchronize()
+            lat.append(1000 * (time.perf_counter() - t0))
+        u_m = ud.cpu().numpy()
+        err = float(np.sqrt(np.sum(lam * (u_m - pb.u_star) ** 2)))
+        lat.sort()
+        served[mode] = {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                        "solves_per_s": 1000.0 / statistics.mean(lat), "l2_error_vs_u_star": err,
+                        "refine_sweeps": rep["refine_iters"], "alpha": rep["alpha"], "solves": count}
+    tbs.close()
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e_ms = []
@@ -273,7 +298,8 @@ def main():
                      "note": f"{OPS_PER_STEP_2D} thread-instructions per WoS step (source count); peak = "
                              f"{nsm} SMs x 4 schedulers x 32 lanes x {peaks.get('sm_max_mhz', 2032.0):.0f} MHz"},
         "clocks": ck,
-        "gpu_launches": None,
+        "served_solve": served,
+        "gpu_launches": launches_per_step,
     }
     if rank == 0:
         if not args.no_cpu_baseline:

@@ -147,24 +147,25 @@ def shift(Lam, rcond):
     return float(rcond) * float(np.sqrt(np.sum(Lam * Lam)))
 
 
-def solve_linear(tb, lam, A, b, c, f, g, rcond=DEFAULT_RCOND):
-    """(Lambda + alpha I) s = rhs by textbook LU, then u = G s + H g."""
+def solve_linear(tb, lam, A, b, c, f, g, rcond=DEFAULT_RCOND, alpha=None):
+    """(Lambda + alpha I) s = rhs by textbook LU, then u = G s + H g.  ``alpha`` overrides the
+    shift (used to compare with a solver that computed its shift from its own Lambda)."""
     Lam = assemble(tb["G"], tb["gradG"], lam, A, b, c)
     r = rhs(tb["G"], tb["gradG"], tb["H"], tb["gradH"], lam, A, b, c, f, g)
-    alpha = shift(Lam, rcond)
+    alpha = shift(Lam, rcond) if alpha is None else float(alpha)
     lu, piv = lu_factor(Lam + alpha * np.eye(Lam.shape[0]))
     s = lu_solve(lu, piv, r)
     u, _ = reconstruct(tb, s, g)
     return dict(s=s, u=u, Lam=Lam, rhs=r, alpha=alpha)
 
 
-def newton(tb, lam, A, b, c, f, g, nl, tol=1e-10, max_iter=30, rcond=DEFAULT_RCOND):
+def newton(tb, lam, A, b, c, f, g, nl, tol=1e-10, max_iter=30, rcond=DEFAULT_RCOND, alpha=None):
     """Newton on R(s) + alpha s = 0 for N(u) = sum nl[k] u^k; Jacobian
     Lambda + alpha I + G^T diag(lam N'(u)) G; s_0 = 0; stop when the residual norm is at most
     tol times the initial one, or after max_iter iterations."""
     G = tb["G"]
     Lam = assemble(G, tb["gradG"], lam, A, b, c)
-    alpha = shift(Lam, rcond)
+    alpha = shift(Lam, rcond) if alpha is None else float(alpha)
     s = np.zeros(G.shape[1])
     R = residual(tb, lam, A, b, c, f, g, s, nl) + alpha * s
     r0 = np.linalg.norm(R)

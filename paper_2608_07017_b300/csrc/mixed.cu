@@ -1,10 +1,11 @@
-// mixed.cu -- mixed-precision solve path (tensor-core assembly, low-precision LU, FP64
-// refinement).  Placeholder until the tensor-core kernels land.
+// mixed.cu -- tensor-core assembly of the Galerkin matrix (placeholder: the FP32 SIMT GEMM of
+// solve.cu is used while no tensor-core kernel is compiled in).
 #include "toolbox.hpp"
 
 namespace ewos {
-ewos_status solve_mixed(ewos_toolbox*, const ewos_problem*, double, double, int, ewos_solve_report*) {
-    set_error("mixed-precision solve is not available in this build");
+bool tc_assemble_available() { return false; }
+ewos_status tc_assemble(const float*, const float*, float*, int, int, int, cudaStream_t) {
+    set_error("tensor-core assembly is not available in this build");
     return EWOS_EINVAL;
 }
 }  // namespace ewos

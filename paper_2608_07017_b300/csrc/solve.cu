@@ -22,6 +22,7 @@
 #include <string>
 #include <vector>
 
+#include "sgemm.cuh"
 #include "toolbox.hpp"
 
 namespace ewos {
@@ -177,6 +178,40 @@ __global__ void sumsq_kernel(const double* __restrict__ X, int64_t count, double
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 
+__global__ void narrow_f32_kernel(const double* __restrict__ in, float* __restrict__ out, int64_t count) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+        out[t] = (float)in[t];
+}
+
+__global__ void sumsq_f32_kernel(const float* __restrict__ X, int64_t count, double* __restrict__ out) {
+    double acc = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)X[t] * (double)X[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+// Jacobian-vector product pieces of the Newton system: w_i = M_i v_i + e_D lam_i N'(u_i) v_{D,i}
+__global__ void formw_jv_kernel(int n, int D, const double* __restrict__ M, const double* __restrict__ v,
+                                const double* __restrict__ lam, const double* __restrict__ u,
+                                const double* __restrict__ nl, int nnl, double* __restrict__ w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int E = D + 1;
+    const double* Mi = M + (size_t)i * E * E;
+    double vi[4];
+    for (int k = 0; k < E; ++k) vi[k] = v[(size_t)k * n + i];
+    for (int j = 0; j < E; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < E; ++k) acc += Mi[j * E + k] * vi[k];
+        w[(size_t)j * n + i] = acc;
+    }
+    double d = 0.0, pw = 1.0;
+    for (int t = 1; t < nnl; ++t) { d += t * nl[t] * pw; pw *= u[i]; }
+    w[(size_t)D * n + i] += lam[i] * d * vi[D];
+}
+
 template <typename T>
 __global__ void add_diag_kernel(T* __restrict__ A, int m, int lda, double alpha) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -268,6 +303,20 @@ template <>
 void gemm_trailing<double>(cudaStream_t st, int M, int N, int K, const double* A, int64_t lda, const double* B,
                            int64_t ldb, double* C, int64_t ldc) {
     gemm64<double, false>(st, M, N, K, -1.0, A, lda, B, ldb, 1.0, C, ldc);
+}
+
+template <bool A_KMAJOR>
+static void sgemm(cudaStream_t st, int M, int N, int K, float alpha, const float* A, int64_t lda, const float* B,
+                  int64_t ldb, float beta, float* C, int64_t ldc) {
+    if (M <= 0 || N <= 0) return;
+    dim3 grid((N + 127) / 128, (M + 127) / 128);
+    ::ewos::note_launch(), sgemm_kernel<A_KMAJOR><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+template <>
+void gemm_trailing<float>(cudaStream_t st, int M, int N, int K, const float* A, int64_t lda, const float* B,
+                          int64_t ldb, float* C, int64_t ldc) {
+    sgemm<false>(st, M, N, K, -1.f, A, lda, B, ldb, 1.f, C, ldc);
 }
 
 // ------------------------------------------------------------------ LU with partial pivoting
@@ -577,6 +626,9 @@ struct SolveWorkspace {
     unsigned long long* umax = nullptr;
     LuScratch lu;
     int64_t cap_rhs = 0;
+    // mixed precision
+    float *Q32 = nullptr, *L32 = nullptr, *LU32 = nullptr, *J32 = nullptr, *Jx32 = nullptr, *P32 = nullptr;
+    double *rhs = nullptr, *r = nullptr, *dx = nullptr;
 };
 
 void free_workspace(SolveWorkspace* ws) {
@@ -586,44 +638,61 @@ void free_workspace(SolveWorkspace* ws) {
     ::ewos::dev_free(ws->s); ::ewos::dev_free(ws->x); ::ewos::dev_free(ws->v); ::ewos::dev_free(ws->w); ::ewos::dev_free(ws->y); ::ewos::dev_free(ws->u); ::ewos::dev_free(ws->u2);
     ::ewos::dev_free(ws->scal); ::ewos::dev_free(ws->umax);
     ::ewos::dev_free(ws->lu.pub); ::ewos::dev_free(ws->lu.bar); ::ewos::dev_free(ws->lu.ipiv);
+    ::ewos::dev_free(ws->Q32); ::ewos::dev_free(ws->L32); ::ewos::dev_free(ws->LU32); ::ewos::dev_free(ws->J32);
+    ::ewos::dev_free(ws->Jx32); ::ewos::dev_free(ws->P32);
+    ::ewos::dev_free(ws->rhs); ::ewos::dev_free(ws->r); ::ewos::dev_free(ws->dx);
     delete ws;
 }
 
-static ewos_status ensure_workspace(ewos_toolbox* tb, int64_t nrhs) {
-    if (tb->ws && tb->ws->cap_rhs >= nrhs) return EWOS_OK;
-    if (tb->ws) { free_workspace(tb->ws); tb->ws = nullptr; }
-    SolveWorkspace* ws = new SolveWorkspace();
-    tb->ws = ws;
+static ewos_status ensure_workspace(ewos_toolbox* tb, int64_t nrhs, bool mixed) {
+    if (tb->ws && tb->ws->cap_rhs < nrhs) { free_workspace(tb->ws); tb->ws = nullptr; }
     const int D = tb->dim, E = D + 1;
     const int64_t n = tb->n, m = tb->m, p = tb->p;
-    ws->D = D; ws->n = n; ws->m = m; ws->p = p; ws->cap_rhs = nrhs;
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Q, sizeof(double) * E * n * m));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Lam, sizeof(double) * m * m));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->LUm, sizeof(double) * m * m));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Jx, sizeof(double) * n * m));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->M, sizeof(double) * n * E * E));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->A, sizeof(double) * n * D * D));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->b, sizeof(double) * n * D));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->c, sizeof(double) * n));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->f, sizeof(double) * n * nrhs));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->g, sizeof(double) * p * nrhs));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->nl, sizeof(double) * 64));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->s, sizeof(double) * m * nrhs));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->x, sizeof(double) * m * nrhs));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->v, sizeof(double) * E * n));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->w, sizeof(double) * E * n));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->y, sizeof(double) * m));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->u, sizeof(double) * n * nrhs));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->u2, sizeof(double) * n));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->scal, sizeof(double) * 4));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->umax, sizeof(unsigned long long)));
-    int dev = 0, nsm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    ws->lu.pub_bytes = (size_t)2 * nsm * (sizeof(double) + sizeof(int)) + 64 + sizeof(double) * ((size_t)2 * nsm * kNB + 2 * kNB);
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.pub, ws->lu.pub_bytes));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.bar, sizeof(GridBarrier)));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.ipiv, sizeof(int) * m));
+    if (!tb->ws) {
+        SolveWorkspace* ws = new SolveWorkspace();
+        tb->ws = ws;
+        ws->D = D; ws->n = n; ws->m = m; ws->p = p; ws->cap_rhs = nrhs;
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->M, sizeof(double) * n * E * E));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->A, sizeof(double) * n * D * D));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->b, sizeof(double) * n * D));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->c, sizeof(double) * n));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->f, sizeof(double) * n * nrhs));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->g, sizeof(double) * p * nrhs));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->nl, sizeof(double) * 64));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->s, sizeof(double) * m * nrhs));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->x, sizeof(double) * m * nrhs));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->rhs, sizeof(double) * m * nrhs));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->r, sizeof(double) * m * nrhs));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->dx, sizeof(double) * m * nrhs));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->v, sizeof(double) * E * n));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->w, sizeof(double) * E * n));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->y, sizeof(double) * m));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->u, sizeof(double) * n * nrhs));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->u2, sizeof(double) * n));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->scal, sizeof(double) * 4));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->umax, sizeof(unsigned long long)));
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        ws->lu.pub_bytes = (size_t)2 * nsm * (sizeof(double) + sizeof(int)) + 64 + sizeof(double) * ((size_t)2 * nsm * kNB + 2 * kNB);
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.pub, ws->lu.pub_bytes));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.bar, sizeof(GridBarrier)));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.ipiv, sizeof(int) * m));
+    }
+    SolveWorkspace* ws = tb->ws;
+    if (!mixed && !ws->Q) {
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Q, sizeof(double) * E * n * m));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Lam, sizeof(double) * m * m));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->LUm, sizeof(double) * m * m));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Jx, sizeof(double) * n * m));
+    }
+    if (mixed && !ws->Q32) {
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Q32, sizeof(float) * E * n * m));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->L32, sizeof(float) * m * m));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->LU32, sizeof(float) * m * m));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Jx32, sizeof(float) * n * m));
+        if (tb->precision == 64) EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->P32, sizeof(float) * E * n * m));
+    }
     return EWOS_OK;
 }
 
@@ -880,8 +949,266 @@ static ewos_status solve_fp64(ewos_toolbox* tb, const ewos_problem* pb, double r
     return rep->converged ? EWOS_OK : EWOS_ENOCONV;
 }
 
+// ------------------------------------------------------------------ mixed precision
+// Low-precision side: Lambda in FP32 (assembled by tc_assemble on the tensor cores, TF32 inputs
+// with FP32 accumulation, or by the FP32 SIMT GEMM), LU of Lambda + alpha I in FP32 (the same
+// blocked kernels, trailing updates in FP32).  FP64 side: the residual of every correction is
+// the matrix-free FP64 operator (two passes over P), so iterative refinement converges to the
+// FP64 solution of the same system while the O(m^3) work runs in 32-bit.
+bool tc_assemble_available();
+ewos_status tc_assemble(const float* A_km, const float* B_km, float* C, int M, int N, int K, cudaStream_t st);
+
+template <typename TP>
+__global__ void jac_scale32_kernel(const TP* __restrict__ Gm, const double* __restrict__ u, const double* __restrict__ lam,
+                                   const double* __restrict__ nl, int nnl, float* __restrict__ out, int n, int m) {
+    const int i = blockIdx.y;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= m) return;
+    double d = 0.0, pw = 1.0;
+    for (int t = 1; t < nnl; ++t) { d += t * nl[t] * pw; pw *= u[i]; }
+    out[(size_t)i * m + col] = (float)(lam[i] * d * (double)Gm[(size_t)i * m + col]);
+}
+
+static double frob32(const Ctx& C, const float* X, int64_t count) {
+    cudaMemsetAsync(C.ws->scal, 0, sizeof(double), C.st);
+    ::ewos::note_launch(), sumsq_f32_kernel<<<1024, 256, 0, C.st>>>(X, count, C.ws->scal);
+    double h = 0;
+    cudaMemcpyAsync(&h, C.ws->scal, sizeof(double), cudaMemcpyDeviceToHost, C.st);
+    cudaStreamSynchronize(C.st);
+    return std::sqrt(h);
+}
+
+template <typename TP>
+static const float* p_f32(const Ctx& C) {
+    if (C.tb->precision == 32) return (const float*)C.tb->P;
+    const int64_t cnt = (int64_t)C.E * C.n * C.m;
+    ::ewos::note_launch(), narrow_f32_kernel<<<1024, 256, 0, C.st>>>((const double*)C.tb->P, C.ws->P32, cnt);
+    return C.ws->P32;
+}
+
+// Lambda32 = P^T Q with Q = M P in FP32
+template <typename TP>
+static void assemble_mixed(const Ctx& C, const float* P32) {
+    dim3 g((unsigned)((C.m + 255) / 256), (unsigned)C.n);
+    ::ewos::note_launch(), formQ_kernel<float, float><<<g, 256, 0, C.st>>>(P32, C.ws->M, C.ws->Q32, (int)C.n, (int)C.m, C.D);
+    sgemm<true>(C.st, (int)C.m, (int)C.m, (int)(C.E * C.n), 1.f, P32, C.m, C.ws->Q32, C.m, 0.f, C.ws->L32, C.m);
+}
+
+// y = (Lambda + alpha I) x with Lambda applied matrix-free in FP64; with u != NULL the Newton
+// Jacobian term G^T diag(lam N'(u)) G is included
+template <typename TP>
+static void apply_op(const Ctx& C, const double* x, double alpha, const double* u, const double* nl, int nnl,
+                     double* y) {
+    const TP* P = (const TP*)C.tb->P;
+    const int64_t rows = (int64_t)C.E * C.n;
+    ::ewos::note_launch(), rowdot_kernel<TP><<<(int)((rows * 32 + 255) / 256), 256, 0, C.st>>>(P, rows, (int)C.m, x, C.ws->v, 0);
+    ::ewos::note_launch(), formw_jv_kernel<<<(int)((C.n + 127) / 128), 128, 0, C.st>>>((int)C.n, C.D, C.ws->M, C.ws->v,
+                                                                                      C.tb->lambda, u, u ? nl : nullptr,
+                                                                                      u ? nnl : 0, C.ws->w);
+    apply_PT<TP>(C, C.ws->w, y);
+    if (alpha != 0.0) ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, alpha, x, y);
+}
+
+// x <- solution of (A) x = b by the FP32 factors plus FP64 refinement; A applied by apply_op
+template <typename TP>
+static ewos_status refine(const Ctx& C, const double* b, double* x, double alpha, const double* u, const double* nl,
+                          int nnl, double rel_tol, int max_sweeps, int* sweeps, double* final_rel) {
+    SolveWorkspace* ws = C.ws;
+    const double nb = norm2(C, b, C.m);
+    cudaMemsetAsync(x, 0, sizeof(double) * C.m, C.st);
+    cudaMemcpyAsync(ws->r, b, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
+    double rel = 1.0;
+    int it = 0;
+    while (it < max_sweeps) {
+        cudaMemcpyAsync(ws->dx, ws->r, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
+        ewos_status st = lu_solve_device<float>(ws->LU32, (int)C.m, (int)C.m, ws->lu, ws->dx, 1, C.st);
+        if (st != EWOS_OK) return st;
+        ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, 1.0, ws->dx, x);
+        apply_op<TP>(C, x, alpha, u, nl, nnl, ws->y);
+        cudaMemcpyAsync(ws->r, b, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
+        ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, -1.0, ws->y, ws->r);
+        ++it;
+        rel = nb > 0 ? norm2(C, ws->r, C.m) / nb : 0.0;
+        if (rel <= rel_tol) break;
+    }
+    *sweeps += it;
+    if (final_rel) *final_rel = rel;
+    return EWOS_OK;
+}
+
+static ewos_status factor32(const Ctx& C, const float* src, double alpha) {
+    cudaMemcpyAsync(C.ws->LU32, src, sizeof(float) * C.m * C.m, cudaMemcpyDeviceToDevice, C.st);
+    ::ewos::note_launch(), add_diag_kernel<float><<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.ws->LU32, (int)C.m, (int)C.m, alpha);
+    bool sing = false;
+    ewos_status s = lu_factor_device<float>(C.ws->LU32, (int)C.m, (int)C.m, C.ws->lu, C.st, &sing);
+    if (s != EWOS_OK) return s;
+    if (sing) { set_error("LU (FP32): zero pivot"); return EWOS_ESINGULAR; }
+    return EWOS_OK;
+}
+
+constexpr double kRefineTol = 1e-12;
+constexpr int kRefineMax = 40;
+
+template <typename TP>
+static ewos_status solve_mixed_t(ewos_toolbox* tb, const ewos_problem* pb, double rcond, double tol, int max_iter,
+                                 ewos_solve_report* rep) {
+    Ctx C{tb, tb->ws, pb->stream ? (cudaStream_t)pb->stream : tb->stream, tb->dim, tb->dim + 1, tb->n, tb->m, tb->p};
+    SolveWorkspace* ws = tb->ws;
+    const int64_t nrhs = pb->nrhs;
+    auto t0 = std::chrono::steady_clock::now();
+    const bool quasi = pb->nl_kind == EWOS_NL_QUASILINEAR, semi = pb->nl_kind == EWOS_NL_SEMILINEAR;
+    const float* P32 = p_f32<TP>(C);
+    ::ewos::note_launch(), coef_kernel<<<(int)((C.n + 127) / 128), 128, 0, C.st>>>((int)C.n, C.D, tb->lambda, ws->A,
+                                                                                pb->b ? ws->b : nullptr,
+                                                                                pb->c ? ws->c : nullptr, nullptr, 0,
+                                                                                nullptr, ws->M);
+    rep->iters = 0;
+    rep->converged = 1;
+    int sweeps = 0;
+    double rel = 0.0;
+    if (!quasi) {
+        auto ta = std::chrono::steady_clock::now();
+        if (tc_assemble_available()) {
+            dim3 g((unsigned)((C.m + 255) / 256), (unsigned)C.n);
+            ::ewos::note_launch(), formQ_kernel<float, float><<<g, 256, 0, C.st>>>(P32, ws->M, ws->Q32, (int)C.n, (int)C.m, C.D);
+            ewos_status st = tc_assemble(P32, ws->Q32, ws->L32, (int)C.m, (int)C.m, (int)(C.E * C.n), C.st);
+            if (st != EWOS_OK) return st;
+        } else {
+            assemble_mixed<TP>(C, P32);
+        }
+        const double alpha = rcond * frob32(C, ws->L32, C.m * C.m);
+        rep->alpha = alpha;
+        rep->ms_assemble = elapsed_ms(ta);
+        if (!semi) {
+            auto t1 = std::chrono::steady_clock::now();
+            ewos_status st = factor32(C, ws->L32, alpha);
+            if (st != EWOS_OK) return st;
+            rep->ms_factor = elapsed_ms(t1);
+            auto t2 = std::chrono::steady_clock::now();
+            for (int64_t r = 0; r < nrhs; ++r) {
+                residual<TP>(C, nullptr, ws->g + r * C.p, ws->f + r * C.n, nullptr, 0, 0.0, ws->y);   // -rhs
+                cudaMemsetAsync(ws->rhs, 0, sizeof(double) * C.m, C.st);
+                ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, -1.0, ws->y, ws->rhs);
+                st = refine<TP>(C, ws->rhs, ws->s + r * C.m, alpha, nullptr, nullptr, 0, kRefineTol, kRefineMax, &sweeps,
+                                &rel);
+                if (st != EWOS_OK) return st;
+                if (!(rel <= kRefineTol)) rep->converged = 0;
+            }
+            rep->iters = 1;
+            rep->ms_solve = elapsed_ms(t2);
+        } else {
+            // Newton on R(s) + alpha s = 0; each step solved by the FP32 factors of the Jacobian
+            // with FP64 refinement of the Jacobian system
+            const double* nl = ws->nl;
+            for (int64_t r = 0; r < nrhs; ++r) {
+                double* s = ws->s + r * C.m;
+                const double* g = ws->g + r * C.p;
+                const double* f = ws->f + r * C.n;
+                cudaMemsetAsync(s, 0, sizeof(double) * C.m, C.st);
+                residual<TP>(C, s, g, f, nl, pb->nl_ncoef, alpha, ws->y);
+                const double r0 = norm2(C, ws->y, C.m);
+                double rn = r0;
+                int it = 0;
+                while (it < max_iter && rn > tol * r0) {
+                    u_from_s(C, tb->P, tb->KH, tb->precision == 64, s, g, ws->u2);
+                    dim3 gj((unsigned)((C.m + 255) / 256), (unsigned)C.n);
+                    const TP* Gm = (const TP*)tb->P + (size_t)C.D * C.n * C.m;
+                    ::ewos::note_launch(), jac_scale32_kernel<TP><<<gj, 256, 0, C.st>>>(Gm, ws->u2, tb->lambda, nl, pb->nl_ncoef,
+                                                                                      ws->Jx32, (int)C.n, (int)C.m);
+                    cudaMemcpyAsync(ws->LU32, ws->L32, sizeof(float) * C.m * C.m, cudaMemcpyDeviceToDevice, C.st);
+                    const float* Gm32 = P32 + (size_t)C.D * C.n * C.m;
+                    sgemm<true>(C.st, (int)C.m, (int)C.m, (int)C.n, 1.f, Gm32, C.m, ws->Jx32, C.m, 1.f, ws->LU32, C.m);
+                    ::ewos::note_launch(), add_diag_kernel<float><<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(ws->LU32, (int)C.m, (int)C.m, alpha);
+                    bool sing = false;
+                    auto t1 = std::chrono::steady_clock::now();
+                    ewos_status st = lu_factor_device<float>(ws->LU32, (int)C.m, (int)C.m, ws->lu, C.st, &sing);
+                    if (st != EWOS_OK) return st;
+                    if (sing) { set_error("LU (FP32): zero pivot"); return EWOS_ESINGULAR; }
+                    rep->ms_factor += elapsed_ms(t1);
+                    cudaMemcpyAsync(ws->rhs, ws->y, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
+                    st = refine<TP>(C, ws->rhs, ws->x, alpha, ws->u2, nl, pb->nl_ncoef, 1e-10, 8, &sweeps, nullptr);
+                    if (st != EWOS_OK) return st;
+                    ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, -1.0, ws->x, s);
+                    residual<TP>(C, s, g, f, nl, pb->nl_ncoef, alpha, ws->y);
+                    rn = norm2(C, ws->y, C.m);
+                    ++it;
+                }
+                rep->iters = std::max(rep->iters, it);
+                if (!(rn <= tol * r0)) rep->converged = 0;
+            }
+        }
+    } else {
+        for (int64_t r = 0; r < nrhs; ++r) {
+            const double* g = ws->g + r * C.p;
+            const double* f = ws->f + r * C.n;
+            double* s = ws->s + r * C.m;
+            double* u = ws->u + r * C.n;
+            cudaMemsetAsync(s, 0, sizeof(double) * C.m, C.st);
+            u_from_s(C, tb->P, tb->KH, tb->precision == 64, s, g, u);
+            int it = 0;
+            bool conv = false;
+            while (it < max_iter) {
+                ::ewos::note_launch(), coef_kernel<<<(int)((C.n + 127) / 128), 128, 0, C.st>>>((int)C.n, C.D, tb->lambda, ws->A,
+                                                                                            pb->b ? ws->b : nullptr,
+                                                                                            pb->c ? ws->c : nullptr,
+                                                                                            ws->nl, pb->nl_ncoef, u, ws->M);
+                auto ta = std::chrono::steady_clock::now();
+                if (tc_assemble_available()) {
+                    dim3 gq((unsigned)((C.m + 255) / 256), (unsigned)C.n);
+                    ::ewos::note_launch(), formQ_kernel<float, float><<<gq, 256, 0, C.st>>>(P32, ws->M, ws->Q32, (int)C.n, (int)C.m, C.D);
+                    ewos_status st = tc_assemble(P32, ws->Q32, ws->L32, (int)C.m, (int)C.m, (int)(C.E * C.n), C.st);
+                    if (st != EWOS_OK) return st;
+                } else {
+                    assemble_mixed<TP>(C, P32);
+                }
+                const double alpha = rcond * frob32(C, ws->L32, C.m * C.m);
+                rep->alpha = alpha;
+                rep->ms_assemble += elapsed_ms(ta);
+                auto t1 = std::chrono::steady_clock::now();
+                ewos_status st = factor32(C, ws->L32, alpha);
+                if (st != EWOS_OK) return st;
+                rep->ms_factor += elapsed_ms(t1);
+                residual<TP>(C, nullptr, g, f, nullptr, 0, 0.0, ws->y);
+                cudaMemsetAsync(ws->rhs, 0, sizeof(double) * C.m, C.st);
+                ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, -1.0, ws->y, ws->rhs);
+                st = refine<TP>(C, ws->rhs, s, alpha, nullptr, nullptr, 0, kRefineTol, kRefineMax, &sweeps, nullptr);
+                if (st != EWOS_OK) return st;
+                u_from_s(C, tb->P, tb->KH, tb->precision == 64, s, g, ws->u2);
+                cudaMemsetAsync(ws->umax, 0, sizeof(unsigned long long), C.st);
+                ::ewos::note_launch(), maxabsdiff_kernel<<<(int)((C.n + 255) / 256), 256, 0, C.st>>>(C.n, ws->u2, u, ws->umax);
+                unsigned long long hm = 0;
+                cudaMemcpyAsync(&hm, ws->umax, sizeof(hm), cudaMemcpyDeviceToHost, C.st);
+                cudaMemcpyAsync(u, ws->u2, sizeof(double) * C.n, cudaMemcpyDeviceToDevice, C.st);
+                cudaStreamSynchronize(C.st);
+                ++it;
+                double du;
+                memcpy(&du, &hm, sizeof(du));
+                if (du <= tol) { conv = true; break; }
+            }
+            rep->iters = std::max(rep->iters, it);
+            if (!conv) rep->converged = 0;
+        }
+    }
+    for (int64_t r = 0; r < nrhs; ++r)
+        u_from_s(C, tb->P, tb->KH, tb->precision == 64, ws->s + r * C.m, ws->g + r * C.p, ws->u + r * C.n);
+    if (!quasi) {
+        const int64_t r = nrhs - 1;
+        residual<TP>(C, ws->s + r * C.m, ws->g + r * C.p, ws->f + r * C.n, semi ? ws->nl : nullptr,
+                     semi ? pb->nl_ncoef : 0, rep->alpha, ws->y);
+        rep->residual = norm2(C, ws->y, C.m);
+    }
+    rep->refine_iters = sweeps;
+    EWOS_CUDA_TRY(cudaStreamSynchronize(C.st));
+    EWOS_CUDA_TRY(cudaGetLastError());
+    rep->ms_total = elapsed_ms(t0);
+    return rep->converged ? EWOS_OK : EWOS_ENOCONV;
+}
+
 ewos_status solve_mixed(ewos_toolbox* tb, const ewos_problem* pb, double rcond, double tol, int max_iter,
-                        ewos_solve_report* rep);
+                        ewos_solve_report* rep) {
+    return tb->precision == 64 ? solve_mixed_t<double>(tb, pb, rcond, tol, max_iter, rep)
+                               : solve_mixed_t<float>(tb, pb, rcond, tol, max_iter, rep);
+}
 
 }  // namespace ewos
 
@@ -900,7 +1227,7 @@ extern "C" ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, doub
     if (pb->mode != EWOS_SOLVE_FP64 && pb->mode != EWOS_SOLVE_MIXED) { set_error("ewos_solve: unknown mode"); return EWOS_EINVAL; }
     cudaStream_t st = pb->stream ? (cudaStream_t)pb->stream : tb->stream;
     AllocStream as(st);
-    ewos_status s = ensure_workspace(tb, pb->nrhs);
+    ewos_status s = ensure_workspace(tb, pb->nrhs, pb->mode == EWOS_SOLVE_MIXED);
     if (s != EWOS_OK) return s;
     SolveWorkspace* ws = tb->ws;
     const cudaMemcpyKind k = pb->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;

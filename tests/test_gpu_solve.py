@@ -146,3 +146,65 @@ def test_square4096_full_size_fp64_residual():
     assert _rel(u, u_ref) < 1e-10
     ref_norm = math.sqrt(np.sum(lam * pb.u_star ** 2))
     assert S.errors(u, pb.u_star, lam)["l2"] < 0.2 * ref_norm
+
+
+# ------------------------------------------------------------------ mixed precision
+# The mixed path assembles Lambda in 32-bit, factors Lambda + alpha I in FP32 and refines with the
+# FP64 matrix-free residual to 1e-12.  Its shift alpha comes from its own 32-bit Lambda, so it is
+# compared with the oracle run with that alpha (1e-9), and with the FP64 GPU path by the R16
+# solution bar.
+
+def test_mixed_linear_matches_oracle(disk):
+    w, tb, lam, gtb = disk
+    pb = w.problem
+    u, s, rep = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, c=pb.c, mode="mixed", want_s=True)
+    assert rep["converged"] and rep["refine_iters"] >= 1
+    ref = S.solve_linear(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, alpha=rep["alpha"])
+    assert _rel(u, ref["u"]) < 1e-9
+    ref_alpha = S.shift(ref["Lam"], 3e-2)
+    assert abs(rep["alpha"] - ref_alpha) <= 1e-3 * ref_alpha
+    u64, _, _ = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, c=pb.c, mode="fp64")
+    e_m = S.errors(u, pb.u_star, lam)["l2"]
+    e_d = S.errors(u64, pb.u_star, lam)["l2"]
+    assert abs(e_m - e_d) <= 1e-3 * max(1e-3, e_d)
+
+
+def test_mixed_newton_matches_oracle(disk):
+    w, tb, lam, gtb = disk
+    pb = w.problem
+    f3 = pb.f + pb.u_star ** 3
+    u, _, rep = gtb.solve(pb.A, f3, pb.g, kind="semilinear", coef=[0, 0, 0, 1], mode="mixed")
+    assert rep["converged"]
+    ref = S.newton(tb, lam, pb.A, None, None, f3, pb.g, [0, 0, 0, 1], alpha=rep["alpha"])
+    assert _rel(u, ref["u"]) < 1e-8
+
+
+def test_mixed_picard_equal_accuracy(disk):
+    w, tb, lam, gtb = disk
+    st = W.make_problem("star", w.x, w.z)
+    um, _, rm = gtb.solve(st.A, st.f, st.g, kind="quasilinear", coef=st.kappa, mode="mixed")
+    ud, _, rd = gtb.solve(st.A, st.f, st.g, kind="quasilinear", coef=st.kappa, mode="fp64")
+    assert rm["converged"] and rd["converged"]
+    e_m = S.errors(um, st.u_star, lam)["l2"]
+    e_d = S.errors(ud, st.u_star, lam)["l2"]
+    assert abs(e_m - e_d) <= 1e-3 * max(1e-3, e_d)
+    assert _rel(um, ud) < 1e-4
+
+
+def test_mixed_square4096_full_size():
+    w = W.square4096()
+    pb = w.problem
+    gtb = ewos.build_workload(w)
+    u, s, rep = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, want_s=True, mode="mixed")
+    u64, s64, rep64 = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, want_s=True, mode="fp64")
+    mats = gtb.matrices()
+    lam = gtb.get("lambda")
+    gtb.close()
+    assert rep["converged"]
+    Lam = S.assemble(mats["G"], mats["gradG"], lam, pb.A, pb.b, None)
+    r = S.rhs(mats["G"], mats["gradG"], mats["H"], mats["gradH"], lam, pb.A, pb.b, None, pb.f, pb.g)
+    res = (Lam + rep["alpha"] * np.eye(Lam.shape[0])) @ s - r
+    assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(r)
+    e_m = S.errors(u, pb.u_star, lam)["l2"]
+    e_d = S.errors(u64, pb.u_star, lam)["l2"]
+    assert abs(e_m - e_d) <= 1e-3 * max(1e-3, e_d)
