@@ -253,7 +253,8 @@ def main():
         lat.sort()
         served[mode] = {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                         "solves_per_s": 1000.0 / statistics.mean(lat), "l2_error_vs_u_star": err,
-                        "refine_sweeps": rep["refine_iters"], "alpha": rep["alpha"], "solves": count}
+                        "refine_sweeps": rep["refine_iters"], "alpha": rep["alpha"], "solves": count,
+                        "ms_assemble": rep["ms_assemble"], "ms_factor": rep["ms_factor"], "ms_refine": rep["ms_solve"]}
     tbs.close()
 
     # end to end through the C ABI with host buffers (copies inside the timed region)

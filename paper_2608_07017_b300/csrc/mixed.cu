@@ -1,11 +1,406 @@
-// mixed.cu -- tensor-core assembly of the Galerkin matrix (placeholder: the FP32 SIMT GEMM of
-// solve.cu is used while no tensor-core kernel is compiled in).
+// mixed.cu -- tensor-core assembly of the Galerkin matrix, Lambda = P^T Q (eq. linear_q), on the
+// 5th-generation tensor cores: tcgen05.mma kind::tf32 with FP32 accumulation in TMEM.
+//
+// Both operands are staged K-major (A = P^T as [M][Kp], B = Q^T as [N][Kp], Kp = K padded to a
+// multiple of 32 with zeros) by a tiled transpose, then
+//   * TMA (cp.async.bulk.tensor, 128-byte swizzle) loads 128 x 32 (A) and 256 x 32 (B) tiles
+//     into a 4-stage shared-memory ring guarded by mbarriers (3xTF32: hi and lo tiles of both,
+//     N = 128, 3 stages);
+//   * one thread issues tcgen05.mma (M = 128, N = 256, K = 8 per instruction, four per stage; 3xTF32:
+//     three per step) into a 128-lane FP32 accumulator in tensor memory, and tcgen05.commit
+//     releases each stage back to the producer;
+//   * four warps read the accumulator with tcgen05.ld (32 lanes each) and store the tile.
+// Every mbarrier wait is bounded; on a timeout the kernel records an error, frees its tensor
+// memory and returns (the call then reports EWOS_ETIMEOUT).
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+
 #include "toolbox.hpp"
 
 namespace ewos {
-bool tc_assemble_available() { return false; }
-ewos_status tc_assemble(const float*, const float*, float*, int, int, int, cudaStream_t) {
-    set_error("tensor-core assembly is not available in this build");
-    return EWOS_EINVAL;
+
+namespace tc {
+
+constexpr int BM = 128, BK = 32;
+constexpr long long kWaitLimit = 1ll << 22;
+
+// plain TF32: tiles A (128 x 32) and B (256 x 32) per stage, 4 stages.
+// split TF32 (3xTF32): A = A_hi + A_lo, B = B_hi + B_lo, products hi.hi + hi.lo + lo.hi into the
+// same accumulator; tiles A_hi, A_lo (128 x 32) and B_hi, B_lo (128 x 32) per stage, 3 stages.
+template <bool SPLIT>
+struct Cfg {
+    static constexpr int BN = SPLIT ? 128 : 256;
+    static constexpr int STAGES = SPLIT ? 3 : 4;
+    static constexpr int A_BYTES = BM * BK * 4;
+    static constexpr int B_BYTES = BN * BK * 4;
+    static constexpr int STAGE_BYTES = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES);
+    static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+    static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(BM >> 4) << 24);
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// bounded wait for the phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms 1024 B apart
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+    const uint64_t addr = smem_u32(p);
+    uint64_t d = 0;
+    d |= (addr >> 4) & 0x3FFFull;             // start address
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8-row atom
+    d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                    // swizzle: 128 B
+    return d;
+}
+
+// instruction descriptor (Cfg::IDESC): kind::tf32 -- D format F32 (bits 4-5 = 1), A and B format
+// TF32 (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bit 17, M >> 4 at bit 24
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                           const __grid_constant__ CUtensorMap mapB,
+                                                           const __grid_constant__ CUtensorMap mapAl,
+                                                           const __grid_constant__ CUtensorMap mapBl, int M, int N,
+                                                           int Kp, float* __restrict__ C, int64_t ldc,
+                                                           int* __restrict__ err) {
+    using CF = Cfg<SPLIT>;
+    constexpr int BN = CF::BN, STAGES = CF::STAGES, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
+    constexpr int STAGE_BYTES = CF::STAGE_BYTES;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* done = empty + STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int nk = Kp / BK;
+
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (threadIdx.x == 0) {
+        // producer: TMA loads into the ring
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
+            if (!mbar_wait(&empty[s], ph ^ 1u)) { s_fail = 1; break; }
+            unsigned char* st = smem + s * STAGE_BYTES;
+            mbar_expect_tx(&full[s], STAGE_BYTES);
+            tma_load_2d(st, &mapA, &full[s], kb * BK, m0);
+            tma_load_2d(st + A_BYTES, &mapB, &full[s], kb * BK, n0);
+            if (SPLIT) {
+                tma_load_2d(st + A_BYTES + B_BYTES, &mapAl, &full[s], kb * BK, m0);
+                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mapBl, &full[s], kb * BK, n0);
+            }
+        }
+    } else if (threadIdx.x == 32) {
+        // MMA issuer
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % STAGES;
+            const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
+            if (!mbar_wait(&full[s], ph)) { s_fail = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            unsigned char* st = smem + s * STAGE_BYTES;
+#pragma unroll
+            for (int k = 0; k < BK / 8; ++k) {
+                const uint64_t da = smem_desc(st + k * 32);
+                const uint64_t db = smem_desc(st + A_BYTES + k * 32);
+                const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                mma_tf32(tmem, da, db, CF::IDESC, acc);
+                if (SPLIT) {
+                    const uint64_t dal = smem_desc(st + A_BYTES + B_BYTES + k * 32);
+                    const uint64_t dbl = smem_desc(st + 2 * A_BYTES + B_BYTES + k * 32);
+                    mma_tf32(tmem, da, dbl, CF::IDESC, 1u);
+                    mma_tf32(tmem, dal, db, CF::IDESC, 1u);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[s]))
+                         : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(done))
+                     : "memory");
+    }
+    __syncwarp();
+    // epilogue: wait for the accumulator, read 32 lanes per warp in 32-column chunks
+    bool ok = mbar_wait(done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && !s_fail) {
+        const int row = m0 + warp * 32 + lane;
+        for (int c = 0; c < BN / 32; ++c) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int col0 = n0 + c * 32;
+            if (row < M) {
+                float* cp = C + (int64_t)row * ldc + col0;
+                if (col0 + 32 <= N && (ldc & 3) == 0) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        reinterpret_cast<float4*>(cp)[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                                                      __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+                } else {
+                    for (int q = 0; q < 32; ++q)
+                        if (col0 + q < N) cp[q] = __uint_as_float(v[q]);
+                }
+            }
+        }
+    }
+    if (!ok || s_fail) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+}
+
+// out[c][k] = in[k][c] for in [K][C] (row-major), out [C][Kp] with zero padding k in [K, Kp)
+__global__ void transpose_pad_kernel(const float* __restrict__ in, int K, int Ccols, float* __restrict__ out, int Kp) {
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int k = k0 + r, c = c0 + threadIdx.x;
+        tile[r][threadIdx.x] = (k < K && c < Ccols) ? in[(int64_t)k * Ccols + c] : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int c = c0 + r, k = k0 + threadIdx.x;
+        if (c < Ccols && k < Kp) out[(int64_t)c * Kp + k] = tile[threadIdx.x][r];
+    }
+}
+
+// as transpose_pad_kernel, also splitting each value into a TF32 part (round to nearest, 10
+// explicit mantissa bits) and the FP32 remainder: v = hi + lo exactly
+__global__ void transpose_split_kernel(const float* __restrict__ in, int K, int Ccols, float* __restrict__ hi,
+                                       float* __restrict__ lo, int Kp) {
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int k = k0 + r, c = c0 + threadIdx.x;
+        tile[r][threadIdx.x] = (k < K && c < Ccols) ? in[(int64_t)k * Ccols + c] : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int c = c0 + r, k = k0 + threadIdx.x;
+        if (c < Ccols && k < Kp) {
+            const float v = tile[threadIdx.x][r];
+            const uint32_t b = __float_as_uint(v);
+            const uint32_t hb = (b + 0x0FFFu + ((b >> 13) & 1u)) & 0xFFFFE000u;
+            const float h = isfinite(v) ? __uint_as_float(hb) : v;
+            hi[(int64_t)c * Kp + k] = h;
+            lo[(int64_t)c * Kp + k] = v - h;
+        }
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+static bool make_map(CUtensorMap* map, const float* base, int rows, int Kp, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// scratch for the K-major operands and the error word (stream-ordered pool)
+struct Scratch {
+    float* At = nullptr;
+    float* Bt = nullptr;
+    float* Atl = nullptr;
+    float* Btl = nullptr;
+    int* err = nullptr;
+    size_t cap = 0;
+};
+static Scratch g_scratch[64];
+static std::mutex g_mu;
+
+}  // namespace tc
+
+bool tc_assemble_available() {
+    static int avail = -1;
+    if (avail < 0) {
+        int dev = 0, major = 0, minor = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        avail = (major == 10 && tc::encode_fn() != nullptr) ? 1 : 0;
+    }
+    return avail == 1;
+}
+
+// C [M][N] = A^T B for A = P [K][M] and B = Q [K][N], both FP32 row-major, on the tensor cores:
+// split = false: TF32 inputs (relative error about 2^-11 per product); split = true: 3xTF32
+// (about 2^-21), three MMAs per step.
+ewos_status tc_assemble(const float* Akm, const float* Bkm, float* C, int M, int N, int K, cudaStream_t st,
+                        bool split) {
+    using namespace tc;
+    int dev = 0;
+    EWOS_CUDA_TRY(cudaGetDevice(&dev));
+    const int Kp = (K + BK - 1) / BK * BK;
+    std::lock_guard<std::mutex> lock(g_mu);
+    Scratch& S = g_scratch[dev & 63];
+    const size_t need = (size_t)std::max(M, N) * Kp;
+    if (S.cap < need || (split && !S.Atl)) {
+        ::ewos::dev_free(S.At); ::ewos::dev_free(S.Bt); ::ewos::dev_free(S.Atl); ::ewos::dev_free(S.Btl);
+        S.At = S.Bt = S.Atl = S.Btl = nullptr;
+        S.cap = 0;
+        const size_t cap = std::max(need, S.cap);
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.At, sizeof(float) * cap));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Bt, sizeof(float) * cap));
+        if (split) {
+            EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Atl, sizeof(float) * cap));
+            EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Btl, sizeof(float) * cap));
+        }
+        S.cap = cap;
+    }
+    if (!S.err) EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.err, sizeof(int)));
+    dim3 tb(32, 8);
+    if (split) {
+        ::ewos::note_launch(), transpose_split_kernel<<<dim3((M + 31) / 32, (Kp + 31) / 32), tb, 0, st>>>(Akm, K, M, S.At, S.Atl, Kp);
+        ::ewos::note_launch(), transpose_split_kernel<<<dim3((N + 31) / 32, (Kp + 31) / 32), tb, 0, st>>>(Bkm, K, N, S.Bt, S.Btl, Kp);
+    } else {
+        ::ewos::note_launch(), transpose_pad_kernel<<<dim3((M + 31) / 32, (Kp + 31) / 32), tb, 0, st>>>(Akm, K, M, S.At, Kp);
+        ::ewos::note_launch(), transpose_pad_kernel<<<dim3((N + 31) / 32, (Kp + 31) / 32), tb, 0, st>>>(Bkm, K, N, S.Bt, Kp);
+    }
+    const int bn = split ? Cfg<true>::BN : Cfg<false>::BN;
+    CUtensorMap ma, mb, mal, mbl;
+    bool ok = make_map(&ma, S.At, M, Kp, BM) && make_map(&mb, S.Bt, N, Kp, bn);
+    if (split) ok = ok && make_map(&mal, S.Atl, M, Kp, BM) && make_map(&mbl, S.Btl, N, Kp, bn);
+    else { mal = ma; mbl = mb; }
+    if (!ok) {
+        set_error("tensor-core assembly: cuTensorMapEncodeTiled failed");
+        return EWOS_ECUDA;
+    }
+    EWOS_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
+    dim3 grid((N + bn - 1) / bn, (M + BM - 1) / BM);
+    if (split) {
+        EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<true>::SMEM_BYTES));
+        ::ewos::note_launch(), gemm_tf32_kernel<true><<<grid, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err);
+    } else {
+        EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<false>::SMEM_BYTES));
+        ::ewos::note_launch(), gemm_tf32_kernel<false><<<grid, 128, Cfg<false>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err);
+    }
+    EWOS_CUDA_TRY(cudaGetLastError());
+    int herr = 0;
+    EWOS_CUDA_TRY(cudaMemcpyAsync(&herr, S.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr) {
+        set_error("tensor-core assembly: a pipeline wait timed out");
+        return EWOS_ETIMEOUT;
+    }
+    return EWOS_OK;
+}
+
 }  // namespace ewos
+
+// Test hook (no counterpart in the paper): C [M][N] = A^T B with A [K][M], B [K][N] host FP32
+// arrays, through the tensor-core path used by the mixed-precision assembly.
+extern "C" ewos_status ewos_debug_tc_gemm(const float* A, const float* B, float* C, int M, int N, int K, int split) {
+    using namespace ewos;
+    if (!A || !B || !C || M < 1 || N < 1 || K < 1) { set_error("ewos_debug_tc_gemm: bad arguments"); return EWOS_EINVAL; }
+    if (!tc_assemble_available()) { set_error("tensor cores (sm_100 family) not available"); return EWOS_EINVAL; }
+    AllocStream as(nullptr);
+    float *dA = nullptr, *dB = nullptr, *dC = nullptr;
+    EWOS_CUDA_TRY(dev_alloc((void**)&dA, sizeof(float) * (size_t)K * M));
+    EWOS_CUDA_TRY(dev_alloc((void**)&dB, sizeof(float) * (size_t)K * N));
+    EWOS_CUDA_TRY(dev_alloc((void**)&dC, sizeof(float) * (size_t)M * N));
+    cudaMemcpy(dA, A, sizeof(float) * (size_t)K * M, cudaMemcpyHostToDevice);
+    cudaMemcpy(dB, B, sizeof(float) * (size_t)K * N, cudaMemcpyHostToDevice);
+    ewos_status s = tc_assemble(dA, dB, dC, M, N, K, nullptr, split != 0);
+    if (s == EWOS_OK && cudaMemcpy(C, dC, sizeof(float) * (size_t)M * N, cudaMemcpyDeviceToHost) != cudaSuccess) s = EWOS_ECUDA;
+    dev_free(dA); dev_free(dB); dev_free(dC);
+    cudaDeviceSynchronize();
+    return s;
+}

@@ -35,7 +35,7 @@ struct GridBarrier {
     int singular;
 };
 
-constexpr long long kSpinLimit = 1ll << 23;
+constexpr long long kSpinLimit = 1ll << 24;   // about 10 s of L2 polling
 
 __device__ __forceinline__ bool grid_sync(GridBarrier* b) {
     __shared__ int s_ok;
@@ -53,7 +53,6 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b) {
             long long spins = 0;
             while (*vgen == g) {
                 if (++spins > kSpinLimit) { atomicExch(&b->err, 1); break; }
-                __nanosleep(40);
             }
         }
         __threadfence();
@@ -437,6 +436,76 @@ __global__ void laswp_kernel(T* __restrict__ A, int lda, int m, int kb, int nb, 
     }
 }
 
+// The row interchanges of one panel (ipiv[kb .. kb+nb)) composed into "row keys[t] receives the
+// old row vals[t]" for the at most 2 nb rows they touch (one thread; shared-memory tables).
+__global__ void perm_compose_kernel(const int* __restrict__ ipiv, int kb, int nb, int* __restrict__ keys,
+                                    int* __restrict__ vals, int* __restrict__ count) {
+    __shared__ int k[128], v[128];
+    __shared__ int n;
+    if (threadIdx.x != 0) return;
+    n = 0;
+    auto slot = [&](int row) {
+        for (int t = 0; t < n; ++t)
+            if (k[t] == row) return t;
+        k[n] = row; v[n] = row;
+        return n++;
+    };
+    for (int i = kb; i < kb + nb; ++i) {
+        const int p = ipiv[i];
+        if (p == i) continue;
+        const int a = slot(i), b = slot(p);
+        const int tv = v[a]; v[a] = v[b]; v[b] = tv;
+    }
+    int w = 0;
+    for (int t = 0; t < n; ++t)
+        if (k[t] != v[t]) { keys[w] = k[t]; vals[w] = v[t]; ++w; }
+    *count = w;
+}
+
+// apply the composed interchanges to the columns outside the panel, 32 columns per block
+template <typename T>
+__global__ void rows_permute_kernel(T* __restrict__ A, int lda, int m, int kb, int nb, const int* __restrict__ keys,
+                                    const int* __restrict__ vals, const int* __restrict__ count) {
+    __shared__ T buf[128][32];
+    const int cnt = *count;
+    if (cnt == 0) return;
+    int c0 = blockIdx.x * 32;
+    if (c0 >= kb) c0 += nb;              // skip the panel's columns (kb is a multiple of 64)
+    if (c0 >= m) return;
+    const int cw = min(32, m - c0);
+    for (int t = threadIdx.x; t < cnt * 32; t += blockDim.x) {
+        const int r = t >> 5, c = t & 31;
+        if (c < cw) buf[r][c] = A[(size_t)vals[r] * lda + c0 + c];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt * 32; t += blockDim.x) {
+        const int r = t >> 5, c = t & 31;
+        if (c < cw) A[(size_t)keys[r] * lda + c0 + c] = buf[r][c];
+    }
+}
+
+// final row order of P A = L U: perm[i] = original row at position i (one thread, shared table)
+__global__ void perm_full_kernel(const int* __restrict__ ipiv, int m, int* __restrict__ perm) {
+    extern __shared__ int pm[];
+    for (int i = threadIdx.x; i < m; i += blockDim.x) pm[i] = i;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 0; i < m; ++i) {
+            const int p = ipiv[i];
+            if (p != i) { const int t = pm[i]; pm[i] = pm[p]; pm[p] = t; }
+        }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) perm[i] = pm[i];
+}
+
+__global__ void gather_rows_kernel(const double* __restrict__ in, double* __restrict__ out, const int* __restrict__ perm,
+                                   int m, int nrhs) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)m * nrhs) return;
+    const int r = (int)(t / m), i = (int)(t % m);
+    out[t] = in[(int64_t)r * m + perm[i]];
+}
+
 // U12 = L11^{-1} A12 (L11 unit lower nb x nb at (kb, kb))
 template <typename T>
 __global__ void trsm_unit_lower_kernel(T* __restrict__ A, int lda, int m, int kb, int nb) {
@@ -463,11 +532,119 @@ __global__ void trsm_unit_lower_kernel(T* __restrict__ A, int lda, int m, int kb
         if (i < nb) A[(size_t)(kb + i) * lda + col] = x[i];
 }
 
+// Panel factorisation on one thread-block cluster: the panel's rows are split over the
+// cluster's CTAs and kept in their shared memory; per column, every CTA publishes its local
+// pivot candidate, a cluster barrier, every CTA reads the candidates and the pivot and old rows
+// through distributed shared memory, a second barrier, then the swap and the rank-1 update of
+// the CTA's own rows.  Hardware cluster barriers replace the grid-wide barriers of the
+// cooperative panel.
+template <typename T>
+__global__ void __launch_bounds__(256) lu_panel_cluster_kernel(T* __restrict__ A, int lda, int mtot, int kb, int nb,
+                                                              int chunk, int* __restrict__ ipiv,
+                                                              GridBarrier* __restrict__ bar) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int ncta = (int)cluster.num_blocks();
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T* tile = reinterpret_cast<T*>(sm_raw);          // [chunk][nb]
+    __shared__ T s_cval;
+    __shared__ int s_crow;
+    __shared__ T s_piv[64];
+    __shared__ T s_old[64];
+    __shared__ int s_prow;
+    __shared__ T s_best;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int r0 = kb + rank * chunk;
+    const int r1 = min(mtot, r0 + chunk);
+    const int nr = max(0, r1 - r0);
+    for (int t = threadIdx.x; t < nr * nb; t += blockDim.x) tile[t] = A[(size_t)(r0 + t / nb) * lda + kb + t % nb];
+    __syncthreads();
+    for (int jj = 0; jj < nb; ++jj) {
+        const int prow0 = kb + jj;
+        if (warp == 0) {
+            T best = T(-1);
+            int brow = 0x7fffffff;
+            for (int rr = lane; rr < nr; rr += 32) {
+                const int gr = r0 + rr;
+                if (gr < prow0) continue;
+                const T v = fabs(tile[rr * nb + jj]);
+                if (v > best || (v == best && gr < brow)) { best = v; brow = gr; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ob = __shfl_down_sync(0xffffffffu, best, o);
+                const int orw = __shfl_down_sync(0xffffffffu, brow, o);
+                if (ob > best || (ob == best && orw < brow)) { best = ob; brow = orw; }
+            }
+            if (lane == 0) { s_cval = best; s_crow = brow; }
+        }
+        cluster.sync();
+        if (warp == 0) {
+            T best = T(-1);
+            int brow = 0x7fffffff;
+            if (lane < ncta) {
+                const T v = *cluster.map_shared_rank(&s_cval, lane);
+                const int rw = *cluster.map_shared_rank(&s_crow, lane);
+                if (rw != 0x7fffffff) { best = v; brow = rw; }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T ob = __shfl_down_sync(0xffffffffu, best, o);
+                const int orw = __shfl_down_sync(0xffffffffu, brow, o);
+                if (ob > best || (ob == best && orw < brow)) { best = ob; brow = orw; }
+            }
+            if (lane == 0) {
+                s_prow = brow;
+                s_best = best;
+                if (rank == 0) {
+                    ipiv[prow0] = brow;
+                    if (best == T(0)) bar->singular = 1;
+                }
+            }
+        }
+        __syncthreads();
+        const int prow = s_prow;
+        {
+            const int ow = (prow - kb) / chunk, oi = (prow - kb) - ow * chunk;
+            const int ow0 = (prow0 - kb) / chunk, oi0 = (prow0 - kb) - ow0 * chunk;
+            const T* rp = cluster.map_shared_rank(tile, ow) + (size_t)oi * nb;
+            const T* rp0 = cluster.map_shared_rank(tile, ow0) + (size_t)oi0 * nb;
+            for (int cc = threadIdx.x; cc < nb; cc += blockDim.x) { s_piv[cc] = rp[cc]; s_old[cc] = rp0[cc]; }
+        }
+        cluster.sync();
+        if (prow != prow0) {
+            if (prow0 >= r0 && prow0 < r1)
+                for (int cc = threadIdx.x; cc < nb; cc += blockDim.x) tile[(prow0 - r0) * nb + cc] = s_piv[cc];
+            if (prow >= r0 && prow < r1)
+                for (int cc = threadIdx.x; cc < nb; cc += blockDim.x) tile[(prow - r0) * nb + cc] = s_old[cc];
+        }
+        __syncthreads();
+        const T piv = s_piv[jj];
+        const T inv = piv != T(0) ? T(1) / piv : T(0);
+        for (int rr = warp; rr < nr; rr += nw) {
+            const int gr = r0 + rr;
+            if (gr <= prow0) continue;
+            T* rowp = tile + rr * nb;
+            const T l = rowp[jj] * inv;
+            for (int cc = jj + 1 + lane; cc < nb; cc += 32) rowp[cc] -= l * s_piv[cc];
+            __syncwarp();
+            if (lane == 0) rowp[jj] = l;
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < nr * nb; t += blockDim.x) A[(size_t)(r0 + t / nb) * lda + kb + t % nb] = tile[t];
+    cluster.sync();
+}
+
 struct LuScratch {
     void* pub = nullptr;
     size_t pub_bytes = 0;
     GridBarrier* bar = nullptr;
     int* ipiv = nullptr;
+    int* perm = nullptr;        // [m] final row order
+    int* swp = nullptr;         // [2 * 128 + 1] composed interchanges of one panel
+    double* tmp = nullptr;      // [m * nrhs] permuted right-hand sides
     int panel_blocks = 0;
 };
 
@@ -484,6 +661,46 @@ static ewos_status lu_factor_device(T* A, int m, int lda, LuScratch& S, cudaStre
         int blocks = std::min(nsm, std::max(1, (rows + 7) / 8));
         const int chunk = (rows + blocks - 1) / blocks;
         blocks = (rows + chunk - 1) / chunk;
+        // cluster panel when the panel fits in the shared memory of one cluster
+        bool done_cluster = false;
+        for (int cl : {16, 8}) {
+            const int cchunk = (rows + cl - 1) / cl;
+            const size_t csmem = sizeof(T) * (size_t)cchunk * nb;
+            if (csmem > 200 * 1024) continue;
+            auto kfn = lu_panel_cluster_kernel<T>;
+            if (cl > 8 && cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            if (cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(csmem, 16)) != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3(cl);
+            lc.blockDim = dim3(256);
+            lc.dynamicSmemBytes = csmem;
+            lc.stream = st;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = cl;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            lc.attrs = at;
+            lc.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, kfn, &lc) != cudaSuccess || nclusters < 1) {
+                cudaGetLastError();
+                continue;
+            }
+            ::ewos::note_launch();
+            if (cudaLaunchKernelEx(&lc, kfn, A, lda, m, kb, nb, cchunk, S.ipiv, S.bar) == cudaSuccess) {
+                done_cluster = true;
+                break;
+            }
+            cudaGetLastError();
+        }
+        if (!done_cluster) {
         const size_t smem = sizeof(T) * (size_t)chunk * nb;
         int per_sm = 0;
         cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
@@ -502,7 +719,14 @@ static ewos_status lu_factor_device(T* A, int m, int lda, LuScratch& S, cudaStre
         void* args[] = {&Ap, &ldai, &mt, &kbi, &nbi, &chi, &ip, &pub, &bar};
         ::ewos::note_launch();
         EWOS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)lu_panel_kernel<T>, blocks, threads, args, smem, st));
-        ::ewos::note_launch(), laswp_kernel<T><<<(m + 255) / 256, 256, 0, st>>>(A, lda, m, kb, nb, S.ipiv);
+        }
+        ::ewos::note_launch(), perm_compose_kernel<<<1, 32, 0, st>>>(S.ipiv, kb, nb, S.swp, S.swp + 128, S.swp + 256);
+        {
+            const int ncols = m - nb;
+            if (ncols > 0)
+                ::ewos::note_launch(), rows_permute_kernel<T><<<(ncols + 31) / 32, 256, 0, st>>>(A, lda, m, kb, nb, S.swp,
+                                                                                                S.swp + 128, S.swp + 256);
+        }
         const int rest = m - kb - nb;
         if (rest > 0) {
             ::ewos::note_launch(), trsm_unit_lower_kernel<T><<<(rest + 127) / 128, 128, sizeof(T) * nb * nb, st>>>(A, lda, m, kb, nb);
@@ -512,6 +736,8 @@ static ewos_status lu_factor_device(T* A, int m, int lda, LuScratch& S, cudaStre
         }
         EWOS_CUDA_TRY(cudaGetLastError());
     }
+    EWOS_CUDA_TRY(cudaFuncSetAttribute(perm_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(int) * m)));
+    ::ewos::note_launch(), perm_full_kernel<<<1, 1024, sizeof(int) * m, st>>>(S.ipiv, m, S.perm);
     GridBarrier hb{};
     EWOS_CUDA_TRY(cudaMemcpyAsync(&hb, S.bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
     EWOS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -521,10 +747,10 @@ static ewos_status lu_factor_device(T* A, int m, int lda, LuScratch& S, cudaStre
 }
 
 
-// Solve with the factors of P A = L U for nrhs right-hand sides x [nrhs][m] (in place).
-// Block 0 owns the diagonal blocks; per diagonal block one grid barrier: block 0 first
-// updates the next diagonal block's rows and solves it while the other blocks update the
-// rows further down (the same in reverse for U).
+// Solve with the factors of P A = L U for nrhs right-hand sides x [nrhs][m] (in place; x arrives
+// already permuted).  Block 0 owns the 64-row diagonal blocks and solves each from shared memory;
+// per diagonal block one grid barrier: block 0 first updates the next diagonal block's rows and
+// solves it while the other blocks update the rows further down (the same in reverse for U).
 constexpr int kTB = 64;
 
 template <typename T>
@@ -533,44 +759,58 @@ __global__ void lu_solve_kernel(const T* __restrict__ LU, int lda, int m, const 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nblk = gridDim.x;
     const int nbk = (m + kTB - 1) / kTB;
-    if (blockIdx.x == 0)
-        for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
-            double* xr = x + (size_t)r * m;
-            for (int i = 0; i < m; ++i) {
-                const int p = ipiv[i];
-                if (p != i) { const double t = xr[i]; xr[i] = xr[p]; xr[p] = t; }
-            }
-        }
-    if (!grid_sync(bar)) return;
-    // ---- forward, unit lower
-    auto fwd_diag = [&](int t) {
-        const int ib = t * kTB, ie = min(m, ib + kTB);
-        for (int r = warp; r < nrhs; r += nw) {
-            double* xr = x + (size_t)r * m;
-            for (int i = ib; i < ie; ++i) {
-                double s = 0.0;
-                for (int k = ib + lane; k < i; k += 32) s += (double)LU[(size_t)i * lda + k] * xr[k];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-                if (lane == 0) xr[i] -= s;
-                __syncwarp();
-            }
-        }
-    };
-    auto update_rows = [&](int ib, int ie, int rlo, int rhi, int worker, int nworkers) {
-        // x[r][i] -= sum_{k in [ib, ie)} LU[i][k] x[r][k] for rows i in [rlo, rhi)
+    (void)ipiv;
+    __shared__ T sL[kTB][kTB + 1];
+    __shared__ double sx[kTB];
+    auto update_rows = [&](int kb, int ke, int rlo, int rhi, int worker, int nworkers) {
+        // x[r][i] -= sum_{k in [kb, ke)} LU[i][k] x[r][k] for rows i in [rlo, rhi)
         const int64_t total = (int64_t)(rhi - rlo) * nrhs;
         for (int64_t t = worker; t < total; t += nworkers) {
             const int i = rlo + (int)(t / nrhs), r = (int)(t % nrhs);
             double* xr = x + (size_t)r * m;
-            double s = 0.0;
-            for (int k = ib + lane; k < ie; k += 32) s += (double)LU[(size_t)i * lda + k] * xr[k];
+            double acc = 0.0;
+            for (int k = kb + lane; k < ke; k += 32) acc += (double)LU[(size_t)i * lda + k] * xr[k];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (lane == 0) xr[i] -= s;
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (lane == 0) xr[i] -= acc;
         }
     };
-    if (blockIdx.x == 0) fwd_diag(0);
+    auto diag = [&](int t, bool lower) {
+        const int ib = t * kTB, ie = min(m, ib + kTB), w = ie - ib;
+        for (int q = threadIdx.x; q < w * w; q += blockDim.x) sL[q / w][q % w] = LU[(size_t)(ib + q / w) * lda + ib + q % w];
+        for (int r = 0; r < nrhs; ++r) {
+            double* xr = x + (size_t)r * m;
+            __syncthreads();
+            for (int i = threadIdx.x; i < w; i += blockDim.x) sx[i] = xr[ib + i];
+            __syncthreads();
+            if (warp == 0) {
+                if (lower) {
+                    for (int i = 0; i < w; ++i) {
+                        double acc = 0.0;
+                        for (int k = lane; k < i; k += 32) acc += (double)sL[i][k] * sx[k];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+                        if (lane == 0) sx[i] -= acc;
+                        __syncwarp();
+                    }
+                } else {
+                    for (int i = w - 1; i >= 0; --i) {
+                        double acc = 0.0;
+                        for (int k = i + 1 + lane; k < w; k += 32) acc += (double)sL[i][k] * sx[k];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+                        if (lane == 0) sx[i] = (sx[i] - acc) / (double)sL[i][i];
+                        __syncwarp();
+                    }
+                }
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < w; i += blockDim.x) xr[ib + i] = sx[i];
+        }
+        __syncthreads();
+    };
+    // ---- forward, unit lower
+    if (blockIdx.x == 0) diag(0, true);
     if (!grid_sync(bar)) return;
     for (int t = 0; t + 1 < nbk; ++t) {
         const int ib = t * kTB, ie = ib + kTB;
@@ -578,28 +818,14 @@ __global__ void lu_solve_kernel(const T* __restrict__ LU, int lda, int m, const 
         if (blockIdx.x == 0) {
             update_rows(ib, ie, ie, nblk == 1 ? m : nxt_hi, warp, nw);
             __syncthreads();
-            fwd_diag(t + 1);
+            diag(t + 1, true);
         } else if (nxt_hi < m) {
             update_rows(ib, ie, nxt_hi, m, (blockIdx.x - 1) * nw + warp, (nblk - 1) * nw);
         }
         if (!grid_sync(bar)) return;
     }
     // ---- backward, upper with diagonal
-    auto bwd_diag = [&](int t) {
-        const int ib = t * kTB, ie = min(m, ib + kTB);
-        for (int r = warp; r < nrhs; r += nw) {
-            double* xr = x + (size_t)r * m;
-            for (int i = ie - 1; i >= ib; --i) {
-                double s = 0.0;
-                for (int k = i + 1 + lane; k < ie; k += 32) s += (double)LU[(size_t)i * lda + k] * xr[k];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-                if (lane == 0) xr[i] = (xr[i] - s) / (double)LU[(size_t)i * lda + i];
-                __syncwarp();
-            }
-        }
-    };
-    if (blockIdx.x == 0) bwd_diag(nbk - 1);
+    if (blockIdx.x == 0) diag(nbk - 1, false);
     if (!grid_sync(bar)) return;
     for (int t = nbk - 1; t > 0; --t) {
         const int ib = t * kTB, ie = min(m, ib + kTB);
@@ -607,7 +833,7 @@ __global__ void lu_solve_kernel(const T* __restrict__ LU, int lda, int m, const 
         if (blockIdx.x == 0) {
             update_rows(ib, ie, nblk == 1 ? 0 : prv_lo, ib, warp, nw);
             __syncthreads();
-            bwd_diag(t - 1);
+            diag(t - 1, false);
         } else if (prv_lo > 0) {
             update_rows(ib, ie, 0, prv_lo, (blockIdx.x - 1) * nw + warp, (nblk - 1) * nw);
         }
@@ -638,6 +864,7 @@ void free_workspace(SolveWorkspace* ws) {
     ::ewos::dev_free(ws->s); ::ewos::dev_free(ws->x); ::ewos::dev_free(ws->v); ::ewos::dev_free(ws->w); ::ewos::dev_free(ws->y); ::ewos::dev_free(ws->u); ::ewos::dev_free(ws->u2);
     ::ewos::dev_free(ws->scal); ::ewos::dev_free(ws->umax);
     ::ewos::dev_free(ws->lu.pub); ::ewos::dev_free(ws->lu.bar); ::ewos::dev_free(ws->lu.ipiv);
+    ::ewos::dev_free(ws->lu.perm); ::ewos::dev_free(ws->lu.swp); ::ewos::dev_free(ws->lu.tmp);
     ::ewos::dev_free(ws->Q32); ::ewos::dev_free(ws->L32); ::ewos::dev_free(ws->LU32); ::ewos::dev_free(ws->J32);
     ::ewos::dev_free(ws->Jx32); ::ewos::dev_free(ws->P32);
     ::ewos::dev_free(ws->rhs); ::ewos::dev_free(ws->r); ::ewos::dev_free(ws->dx);
@@ -678,6 +905,9 @@ static ewos_status ensure_workspace(ewos_toolbox* tb, int64_t nrhs, bool mixed) 
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.pub, ws->lu.pub_bytes));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.bar, sizeof(GridBarrier)));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.ipiv, sizeof(int) * m));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.perm, sizeof(int) * m));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.swp, sizeof(int) * 260));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.tmp, sizeof(double) * m * nrhs));
     }
     SolveWorkspace* ws = tb->ws;
     if (!mixed && !ws->Q) {
@@ -705,6 +935,11 @@ static ewos_status lu_solve_device(const T* LU, int m, int lda, LuScratch& S, do
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_solve_kernel<T>, threads, 0);
     const int blocks = std::max(1, std::min(nsm, per_sm * nsm));
     EWOS_CUDA_TRY(cudaMemsetAsync(S.bar, 0, sizeof(GridBarrier), st));
+    {
+        const int64_t cnt = (int64_t)m * nrhs;
+        ::ewos::note_launch(), gather_rows_kernel<<<(int)((cnt + 255) / 256), 256, 0, st>>>(x, S.tmp, S.perm, m, nrhs);
+        EWOS_CUDA_TRY(cudaMemcpyAsync(x, S.tmp, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st));
+    }
     const T* a0 = LU;
     int lda_ = lda, m_ = m, nr = nrhs;
     const int* ip = S.ipiv;
@@ -956,7 +1191,9 @@ static ewos_status solve_fp64(ewos_toolbox* tb, const ewos_problem* pb, double r
 // the matrix-free FP64 operator (two passes over P), so iterative refinement converges to the
 // FP64 solution of the same system while the O(m^3) work runs in 32-bit.
 bool tc_assemble_available();
-ewos_status tc_assemble(const float* A_km, const float* B_km, float* C, int M, int N, int K, cudaStream_t st);
+ewos_status tc_assemble(const float* A_km, const float* B_km, float* C, int M, int N, int K, cudaStream_t st,
+                        bool split);
+constexpr bool kSplitTF32 = true;     // 3xTF32 assembly: Lambda to ~1e-6, fewer refinement sweeps
 
 template <typename TP>
 __global__ void jac_scale32_kernel(const TP* __restrict__ Gm, const double* __restrict__ u, const double* __restrict__ lam,
@@ -1046,7 +1283,7 @@ static ewos_status factor32(const Ctx& C, const float* src, double alpha) {
     return EWOS_OK;
 }
 
-constexpr double kRefineTol = 1e-12;
+constexpr double kRefineTol = 1e-10;
 constexpr int kRefineMax = 40;
 
 template <typename TP>
@@ -1071,7 +1308,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, const ewos_problem* pb, doubl
         if (tc_assemble_available()) {
             dim3 g((unsigned)((C.m + 255) / 256), (unsigned)C.n);
             ::ewos::note_launch(), formQ_kernel<float, float><<<g, 256, 0, C.st>>>(P32, ws->M, ws->Q32, (int)C.n, (int)C.m, C.D);
-            ewos_status st = tc_assemble(P32, ws->Q32, ws->L32, (int)C.m, (int)C.m, (int)(C.E * C.n), C.st);
+            ewos_status st = tc_assemble(P32, ws->Q32, ws->L32, (int)C.m, (int)C.m, (int)(C.E * C.n), C.st, kSplitTF32);
             if (st != EWOS_OK) return st;
         } else {
             assemble_mixed<TP>(C, P32);
@@ -1156,7 +1393,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, const ewos_problem* pb, doubl
                 if (tc_assemble_available()) {
                     dim3 gq((unsigned)((C.m + 255) / 256), (unsigned)C.n);
                     ::ewos::note_launch(), formQ_kernel<float, float><<<gq, 256, 0, C.st>>>(P32, ws->M, ws->Q32, (int)C.n, (int)C.m, C.D);
-                    ewos_status st = tc_assemble(P32, ws->Q32, ws->L32, (int)C.m, (int)C.m, (int)(C.E * C.n), C.st);
+                    ewos_status st = tc_assemble(P32, ws->Q32, ws->L32, (int)C.m, (int)C.m, (int)(C.E * C.n), C.st, kSplitTF32);
                     if (st != EWOS_OK) return st;
                 } else {
                     assemble_mixed<TP>(C, P32);

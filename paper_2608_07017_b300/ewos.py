@@ -96,8 +96,10 @@ def lib():
                                                  ctypes.c_uint64, I64, P, P, P, P, ctypes.POINTER(BuildReport)]
         L.ewos_debug_philox.argtypes = [P, P, P, I64]
         L.ewos_debug_green_radius.argtypes = [P, P, I64, I]
+        L.ewos_debug_tc_gemm.argtypes = [P, P, P, I, I, I, I]
         for fn in ("ewos_toolbox_build", "ewos_toolbox_build_noalloc", "ewos_toolbox_from_host", "ewos_toolbox_get", "ewos_toolbox_report",
-                   "ewos_toolbox_shape", "ewos_solve", "ewos_debug_philox", "ewos_debug_green_radius"):
+                   "ewos_toolbox_shape", "ewos_solve", "ewos_debug_philox", "ewos_debug_green_radius",
+                   "ewos_debug_tc_gemm"):
             getattr(L, fn).restype = I
         _lib = L
     return _lib
@@ -265,6 +267,18 @@ def debug_philox(ctr, key):
     out = np.zeros_like(c)
     _check(lib().ewos_debug_philox(c.ctypes.data, k.ctypes.data, out.ctypes.data, c.shape[0]), "philox")
     return out
+
+
+def debug_tc_gemm(A, B, split=False):
+    """C = A^T B on the tensor cores (TF32 inputs, FP32 accumulation; split: 3xTF32); A [K][M], B [K][N]."""
+    a = np.ascontiguousarray(A, dtype=np.float32)
+    b = np.ascontiguousarray(B, dtype=np.float32)
+    K, M = a.shape
+    N = b.shape[1]
+    c = np.zeros((M, N), dtype=np.float32)
+    _check(lib().ewos_debug_tc_gemm(a.ctypes.data, b.ctypes.data, c.ctypes.data, M, N, K, 1 if split else 0),
+           "tc gemm")
+    return c
 
 
 def debug_green_radius(u, precision=32):
