@@ -196,6 +196,10 @@ typedef struct {
     int max_iter;             /* <= 0 -> 30 (Newton) / 100 (Picard)                       */
     int inputs_on_device;     /* 1 -> A, b, c, f, g are device pointers                    */
     void* stream;             /* NULL -> the toolbox's stream                              */
+    int pivoting;             /* mixed mode: 0 -> LU with the diagonal pivots, kept only when
+                                 every multiplier has |l| <= 1 (then it is the partial-pivoting
+                                 factorisation) and otherwise redone with row interchanges;
+                                 1 -> always partial pivoting.  FP64 mode always pivots.     */
 } ewos_problem;
 
 typedef struct {
@@ -205,6 +209,8 @@ typedef struct {
     double alpha;
     double residual;          /* final ||R(s) + alpha s||_2 (FP64)                           */
     double ms_total, ms_assemble, ms_factor, ms_solve;
+    int factorizations;       /* LU factorisations run                                       */
+    int pivoted_factorizations; /* of which with row interchanges                            */
 } ewos_solve_report;
 
 /* Solve; u_out [nrhs][n] and s_out [nrhs][m] (may be NULL) are host buffers unless

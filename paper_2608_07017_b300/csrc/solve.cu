@@ -20,6 +20,7 @@
 #include <chrono>
 #include <cmath>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "sgemm.cuh"
@@ -33,6 +34,7 @@ struct GridBarrier {
     unsigned int gen;
     int err;
     int singular;
+    int maxl_bits;    // largest |multiplier| of an unpivoted factorisation (float bits)
 };
 
 constexpr long long kSpinLimit = 1ll << 24;   // about 10 s of L2 polling
@@ -533,11 +535,11 @@ __global__ void trsm_unit_lower_kernel(T* __restrict__ A, int lda, int m, int kb
 }
 
 // Panel factorisation on one thread-block cluster: the panel's rows are split over the
-// cluster's CTAs and kept in their shared memory; per column, every CTA publishes its local
-// pivot candidate, a cluster barrier, every CTA reads the candidates and the pivot and old rows
-// through distributed shared memory, a second barrier, then the swap and the rank-1 update of
-// the CTA's own rows.  Hardware cluster barriers replace the grid-wide barriers of the
-// cooperative panel.
+// cluster's CTAs and kept in their shared memory.  Per column, every CTA publishes (parity double
+// buffered) its pivot candidate, a copy of that candidate row and, for the CTA owning it, a copy
+// of the row the pivot will replace; one hardware cluster barrier; then every CTA reads the
+// candidates and the two rows through distributed shared memory, swaps locally and applies the
+// rank-1 update to its own rows.
 template <typename T>
 __global__ void __launch_bounds__(256) lu_panel_cluster_kernel(T* __restrict__ A, int lda, int mtot, int kb, int nb,
                                                               int chunk, int* __restrict__ ipiv,
@@ -548,12 +550,13 @@ __global__ void __launch_bounds__(256) lu_panel_cluster_kernel(T* __restrict__ A
     const int ncta = (int)cluster.num_blocks();
     extern __shared__ __align__(16) unsigned char sm_raw[];
     T* tile = reinterpret_cast<T*>(sm_raw);          // [chunk][nb]
-    __shared__ T s_cval;
-    __shared__ int s_crow;
+    __shared__ T s_cval[2];
+    __shared__ int s_crow[2];
+    __shared__ T s_pub[2][64];      // published candidate row
+    __shared__ T s_old[2][64];      // published copy of row prow0 (owner only)
     __shared__ T s_piv[64];
-    __shared__ T s_old[64];
+    __shared__ T s_rep[64];
     __shared__ int s_prow;
-    __shared__ T s_best;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int r0 = kb + rank * chunk;
     const int r1 = min(mtot, r0 + chunk);
@@ -561,6 +564,7 @@ __global__ void __launch_bounds__(256) lu_panel_cluster_kernel(T* __restrict__ A
     for (int t = threadIdx.x; t < nr * nb; t += blockDim.x) tile[t] = A[(size_t)(r0 + t / nb) * lda + kb + t % nb];
     __syncthreads();
     for (int jj = 0; jj < nb; ++jj) {
+        const int par = jj & 1;
         const int prow0 = kb + jj;
         if (warp == 0) {
             T best = T(-1);
@@ -577,26 +581,38 @@ __global__ void __launch_bounds__(256) lu_panel_cluster_kernel(T* __restrict__ A
                 const int orw = __shfl_down_sync(0xffffffffu, brow, o);
                 if (ob > best || (ob == best && orw < brow)) { best = ob; brow = orw; }
             }
-            if (lane == 0) { s_cval = best; s_crow = brow; }
+            best = __shfl_sync(0xffffffffu, best, 0);
+            brow = __shfl_sync(0xffffffffu, brow, 0);
+            if (lane == 0) { s_cval[par] = best; s_crow[par] = brow; }
+            if (brow != 0x7fffffff)
+                for (int cc = lane; cc < nb; cc += 32) s_pub[par][cc] = tile[(brow - r0) * nb + cc];
+        } else if (warp == 1 && prow0 >= r0 && prow0 < r1) {
+            for (int cc = lane; cc < nb; cc += 32) s_old[par][cc] = tile[(prow0 - r0) * nb + cc];
         }
         cluster.sync();
         if (warp == 0) {
             T best = T(-1);
-            int brow = 0x7fffffff;
+            int brow = 0x7fffffff, win = 0;
             if (lane < ncta) {
-                const T v = *cluster.map_shared_rank(&s_cval, lane);
-                const int rw = *cluster.map_shared_rank(&s_crow, lane);
-                if (rw != 0x7fffffff) { best = v; brow = rw; }
+                const T v = cluster.map_shared_rank(s_cval, lane)[par];
+                const int rw = cluster.map_shared_rank(s_crow, lane)[par];
+                if (rw != 0x7fffffff) { best = v; brow = rw; win = lane; }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const T ob = __shfl_down_sync(0xffffffffu, best, o);
                 const int orw = __shfl_down_sync(0xffffffffu, brow, o);
-                if (ob > best || (ob == best && orw < brow)) { best = ob; brow = orw; }
+                const int ow = __shfl_down_sync(0xffffffffu, win, o);
+                if (ob > best || (ob == best && orw < brow)) { best = ob; brow = orw; win = ow; }
             }
+            win = __shfl_sync(0xffffffffu, win, 0);
+            brow = __shfl_sync(0xffffffffu, brow, 0);
+            const T* pr = &cluster.map_shared_rank(s_pub, win)[par][0];
+            const int ow0 = (prow0 - kb) / chunk;
+            const T* orow = &cluster.map_shared_rank(s_old, ow0)[par][0];
+            for (int cc = lane; cc < nb; cc += 32) { s_piv[cc] = pr[cc]; s_rep[cc] = orow[cc]; }
             if (lane == 0) {
                 s_prow = brow;
-                s_best = best;
                 if (rank == 0) {
                     ipiv[prow0] = brow;
                     if (best == T(0)) bar->singular = 1;
@@ -605,19 +621,11 @@ __global__ void __launch_bounds__(256) lu_panel_cluster_kernel(T* __restrict__ A
         }
         __syncthreads();
         const int prow = s_prow;
-        {
-            const int ow = (prow - kb) / chunk, oi = (prow - kb) - ow * chunk;
-            const int ow0 = (prow0 - kb) / chunk, oi0 = (prow0 - kb) - ow0 * chunk;
-            const T* rp = cluster.map_shared_rank(tile, ow) + (size_t)oi * nb;
-            const T* rp0 = cluster.map_shared_rank(tile, ow0) + (size_t)oi0 * nb;
-            for (int cc = threadIdx.x; cc < nb; cc += blockDim.x) { s_piv[cc] = rp[cc]; s_old[cc] = rp0[cc]; }
-        }
-        cluster.sync();
         if (prow != prow0) {
             if (prow0 >= r0 && prow0 < r1)
                 for (int cc = threadIdx.x; cc < nb; cc += blockDim.x) tile[(prow0 - r0) * nb + cc] = s_piv[cc];
             if (prow >= r0 && prow < r1)
-                for (int cc = threadIdx.x; cc < nb; cc += blockDim.x) tile[(prow - r0) * nb + cc] = s_old[cc];
+                for (int cc = threadIdx.x; cc < nb; cc += blockDim.x) tile[(prow - r0) * nb + cc] = s_rep[cc];
         }
         __syncthreads();
         const T piv = s_piv[jj];
@@ -637,6 +645,213 @@ __global__ void __launch_bounds__(256) lu_panel_cluster_kernel(T* __restrict__ A
     cluster.sync();
 }
 
+// FP32 panel factorisation with one panel row per thread.  The cluster's CTAs own consecutive
+// chunks of at most kRegThreads rows; each thread holds its row's 64 panel entries in registers.
+// Rows are not moved during the panel: each thread tracks the position its row occupies under
+// the interchanges so far (the interchange of column j swaps the positions j and that of the
+// pivot row), and writes its row to that position at the end.  A row's multipliers go to shared
+// memory as they are formed, so the rank-1 update can run over all 64 registers unmasked (the
+// entries left of the current column are dead).  Per column: arg-max over the warp by shuffles,
+// the warp winners' rows staged in shared memory, arg-max over the warps by warp 0, which pushes
+// its CTA's candidate (value, position, row) into every CTA of the cluster by distributed shared
+// memory stores (parity double buffered); one cluster barrier; every warp then picks the winner
+// from its own shared memory.
+constexpr int kRegThreads = 512;
+constexpr int kRegCluster = 16;
+
+__device__ __forceinline__ void argmax_step(float& v, int& r, int& w, int o) {
+    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int orow = __shfl_xor_sync(0xffffffffu, r, o);
+    const int ow = __shfl_xor_sync(0xffffffffu, w, o);
+    if (ov > v || (ov == v && orow < r)) { v = ov; r = orow; w = ow; }
+}
+
+// row[j] for a run-time j: a binary tree of selects on the bits of j
+__device__ __forceinline__ float pick64(const float (&row)[kNB], int j) {
+    float t32[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) t32[c] = (j & 1) ? row[2 * c + 1] : row[2 * c];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) t32[c] = (j & 2) ? t32[2 * c + 1] : t32[2 * c];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) t32[c] = (j & 4) ? t32[2 * c + 1] : t32[2 * c];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) t32[c] = (j & 8) ? t32[2 * c + 1] : t32[2 * c];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) t32[c] = (j & 16) ? t32[2 * c + 1] : t32[2 * c];
+    return (j & 32) ? t32[1] : t32[0];
+}
+
+constexpr size_t panel_reg_smem(int threads) { return sizeof(float) * (size_t)kNB * threads; }
+
+__global__ void __launch_bounds__(kRegThreads, 1) lu_panel_reg_kernel(float* __restrict__ A, int lda, int mtot, int kb,
+                                                                     int nb, int chunk, int* __restrict__ ipiv,
+                                                                     GridBarrier* __restrict__ bar) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int ncta = (int)cluster.num_blocks();
+    constexpr int kW = kRegThreads / 32;
+    extern __shared__ __align__(16) float s_l[];                    // [64][blockDim] multipliers
+    __shared__ __align__(16) float s_wrow[kW][kNB];                 // warp winners' rows (local)
+    __shared__ float s_wval[kW];
+    __shared__ int s_wrw[kW];
+    __shared__ __align__(16) float s_cand[2][kRegCluster][kNB];     // CTA candidates' rows (pushed)
+    __shared__ float s_cval[2][kRegCluster];
+    __shared__ int s_crow[2][kRegCluster];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5, nt = blockDim.x;
+    const int r0 = kb + rank * chunk;
+    const int gr = r0 + tid;
+    const bool mine = tid < chunk && gr < mtot;
+    float row[kNB];
+#pragma unroll
+    for (int c = 0; c < kNB; ++c) row[c] = (mine && c < nb) ? A[(size_t)gr * lda + kb + c] : 0.f;
+    int pos = gr;          // current position of this thread's row
+    int mycol = nb;        // column at which the row became a pivot row
+    float cur = row[0];    // row[jj] of the current column
+    for (int jj = 0; jj < nb; ++jj) {
+        const int par = jj & 1;
+        const int prow0 = kb + jj;
+        const bool cand = mine && pos >= prow0;
+        float bv = cand ? fabsf(cur) : -1.f;
+        int br = cand ? pos : 0x7fffffff, bw = warp;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) argmax_step(bv, br, bw, o);
+        if (cand && br == pos) {
+            float4* dst = reinterpret_cast<float4*>(&s_wrow[warp][0]);
+#pragma unroll
+            for (int q = 0; q < kNB / 4; ++q) dst[q] = make_float4(row[4 * q], row[4 * q + 1], row[4 * q + 2], row[4 * q + 3]);
+        }
+        if (lane == 0) { s_wval[warp] = bv; s_wrw[warp] = br; }
+        __syncthreads();
+        if (warp == 0) {
+            float v = lane < nw ? s_wval[lane] : -1.f;
+            int r = lane < nw ? s_wrw[lane] : 0x7fffffff, w = lane;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) argmax_step(v, r, w, o);
+            if (lane < ncta) {
+                cluster.map_shared_rank(&s_cval[par][0], lane)[rank] = v;
+                cluster.map_shared_rank(&s_crow[par][0], lane)[rank] = r;
+            }
+            const float4* src = reinterpret_cast<const float4*>(&s_wrow[w < nw ? w : 0][0]);
+            for (int i = lane; i < ncta * (kNB / 4); i += 32) {
+                const int d = i / (kNB / 4), q = i % (kNB / 4);
+                reinterpret_cast<float4*>(cluster.map_shared_rank(&s_cand[par][rank][0], d))[q] = src[q];
+            }
+        }
+        cluster.sync();
+        float v = lane < ncta ? s_cval[par][lane] : -1.f;
+        int r = lane < ncta ? s_crow[par][lane] : 0x7fffffff, src = lane;
+        if (r == 0x7fffffff) v = -1.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) argmax_step(v, r, src, o);
+        if (tid == 0 && rank == 0) {
+            ipiv[prow0] = r;
+            if (v == 0.f) bar->singular = 1;
+        }
+        if (mine) {
+            if (pos == r) { pos = prow0; mycol = jj; }
+            else if (pos == prow0) pos = r;
+        }
+        const float* p = &s_cand[par][src][0];
+        if (mine && pos > prow0) {
+            const float piv = p[jj];
+            const float l = cur * (piv != 0.f ? 1.f / piv : 0.f);
+            s_l[jj * nt + tid] = l;
+            const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+            for (int q = 0; q < kNB / 4; ++q) {
+                const float4 pv = p4[q];
+                row[4 * q] = fmaf(-l, pv.x, row[4 * q]);
+                row[4 * q + 1] = fmaf(-l, pv.y, row[4 * q + 1]);
+                row[4 * q + 2] = fmaf(-l, pv.z, row[4 * q + 2]);
+                row[4 * q + 3] = fmaf(-l, pv.w, row[4 * q + 3]);
+            }
+        }
+        cur = pick64(row, (jj + 1) & (kNB - 1));
+    }
+    __syncthreads();
+    if (mine) {
+        float* out = A + (size_t)pos * lda + kb;
+#pragma unroll
+        for (int c = 0; c < kNB; ++c)
+            if (c < nb) out[c] = c < mycol ? s_l[c * nt + tid] : row[c];
+    }
+    cluster.sync();
+}
+
+static bool launch_panel_reg(float* A, int lda, int m, int kb, int nb, int rows, int* ipiv, GridBarrier* bar,
+                             cudaStream_t st, bool check) {
+    constexpr int cl = kRegCluster;
+    const int chunk = (rows + cl - 1) / cl;
+    const int threads = std::max(32, (chunk + 31) / 32 * 32);
+    const size_t smem = panel_reg_smem(threads);
+    auto kfn = lu_panel_reg_kernel;
+    if (check && (cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+                  cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_reg_smem(kRegThreads)) !=
+                      cudaSuccess)) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(cl);
+    lc.blockDim = dim3(threads);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    int nclusters = 0;
+    if (check && (cudaOccupancyMaxActiveClusters(&nclusters, kfn, &lc) != cudaSuccess || nclusters < 1)) {
+        cudaGetLastError();
+        return false;
+    }
+    ::ewos::note_launch();
+    if (cudaLaunchKernelEx(&lc, kfn, A, lda, m, kb, nb, chunk, ipiv, bar) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// Inverses of the 64 x 64 diagonal blocks of the factors (unit lower part and upper part), one CTA
+// per block: thread j solves the block against e_j.  Dinv [nbk][2][64][64].
+template <typename T>
+__global__ void diag_inverse_kernel(const T* __restrict__ LU, int lda, int m, T* __restrict__ Dinv) {
+    __shared__ T B[64][65];
+    const int t = blockIdx.x, ib = t * 64, w = min(64, m - ib);
+    for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
+        const int i = q >> 6, k = q & 63;
+        B[i][k] = (i < w && k < w) ? LU[(size_t)(ib + i) * lda + ib + k] : T(0);
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    T* Li = Dinv + (size_t)t * 2 * 64 * 64;
+    T* Ui = Li + 64 * 64;
+    if (j < 64) {
+        T col[64];
+        // unit lower: solve L y = e_j
+        for (int i = 0; i < 64; ++i) {
+            T acc = (i == j) ? T(1) : T(0);
+            for (int k = 0; k < i; ++k) acc -= B[i][k] * col[k];
+            col[i] = i < w ? acc : T(0);
+        }
+        for (int i = 0; i < 64; ++i) Li[i * 64 + j] = col[i];
+        // upper with diagonal: solve U y = e_j
+        for (int i = 63; i >= 0; --i) {
+            if (i >= w) { col[i] = T(0); continue; }
+            T acc = (i == j) ? T(1) : T(0);
+            for (int k = i + 1; k < w; ++k) acc -= B[i][k] * col[k];
+            col[i] = acc / B[i][i];
+        }
+        for (int i = 0; i < 64; ++i) Ui[i * 64 + j] = col[i];
+    }
+}
+
 struct LuScratch {
     void* pub = nullptr;
     size_t pub_bytes = 0;
@@ -645,6 +860,8 @@ struct LuScratch {
     int* perm = nullptr;        // [m] final row order
     int* swp = nullptr;         // [2 * 128 + 1] composed interchanges of one panel
     double* tmp = nullptr;      // [m * nrhs] permuted right-hand sides
+    void* dinv = nullptr;       // [nbk][2][64][64] inverses of the diagonal blocks (T)
+    float* diag32 = nullptr;    // [nbk][64][64] factored diagonal blocks of the unpivoted path
     int panel_blocks = 0;
 };
 
@@ -655,15 +872,45 @@ static ewos_status lu_factor_device(T* A, int m, int lda, LuScratch& S, cudaStre
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int threads = 256;
     EWOS_CUDA_TRY(cudaMemsetAsync(S.bar, 0, sizeof(GridBarrier), st));
+    // Panel variant, chosen (attributes set, co-residency checked) on the first and largest panel
+    // and kept for the rest: 0 register panel, 16 / 8 shared-memory cluster panel, -1 cooperative.
+    int plan = -2;
     for (int kb = 0; kb < m; kb += kNB) {
         const int nb = std::min(kNB, m - kb);
         const int rows = m - kb;
         int blocks = std::min(nsm, std::max(1, (rows + 7) / 8));
         const int chunk = (rows + blocks - 1) / blocks;
         blocks = (rows + chunk - 1) / chunk;
-        // cluster panel when the panel fits in the shared memory of one cluster
+        const bool first = plan == -2;
         bool done_cluster = false;
+        if (std::is_same<T, float>::value && (first || plan == 0) &&
+            (rows + kRegCluster - 1) / kRegCluster <= kRegThreads) {
+            done_cluster = launch_panel_reg(reinterpret_cast<float*>(A), lda, m, kb, nb, rows, S.ipiv, S.bar, st, first);
+            if (done_cluster) plan = 0;
+        }
         for (int cl : {16, 8}) {
+            if (done_cluster) break;
+            if (!first && plan != cl) continue;
+            if (!first) {
+                const int cchunk = (rows + cl - 1) / cl;
+                const size_t csmem = sizeof(T) * (size_t)cchunk * nb;
+                cudaLaunchConfig_t lc = {};
+                lc.gridDim = dim3(cl);
+                lc.blockDim = dim3(256);
+                lc.dynamicSmemBytes = csmem;
+                lc.stream = st;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = cl;
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                lc.attrs = at;
+                lc.numAttrs = 1;
+                ::ewos::note_launch();
+                EWOS_CUDA_TRY(cudaLaunchKernelEx(&lc, lu_panel_cluster_kernel<T>, A, lda, m, kb, nb, cchunk, S.ipiv, S.bar));
+                done_cluster = true;
+                break;
+            }
             const int cchunk = (rows + cl - 1) / cl;
             const size_t csmem = sizeof(T) * (size_t)cchunk * nb;
             if (csmem > 200 * 1024) continue;
@@ -696,11 +943,13 @@ static ewos_status lu_factor_device(T* A, int m, int lda, LuScratch& S, cudaStre
             ::ewos::note_launch();
             if (cudaLaunchKernelEx(&lc, kfn, A, lda, m, kb, nb, cchunk, S.ipiv, S.bar) == cudaSuccess) {
                 done_cluster = true;
+                plan = cl;
                 break;
             }
             cudaGetLastError();
         }
         if (!done_cluster) {
+        plan = -1;
         const size_t smem = sizeof(T) * (size_t)chunk * nb;
         int per_sm = 0;
         cudaFuncSetAttribute(lu_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
@@ -738,6 +987,7 @@ static ewos_status lu_factor_device(T* A, int m, int lda, LuScratch& S, cudaStre
     }
     EWOS_CUDA_TRY(cudaFuncSetAttribute(perm_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(int) * m)));
     ::ewos::note_launch(), perm_full_kernel<<<1, 1024, sizeof(int) * m, st>>>(S.ipiv, m, S.perm);
+    ::ewos::note_launch(), diag_inverse_kernel<T><<<(m + 63) / 64, 64, 0, st>>>(A, lda, m, (T*)S.dinv);
     GridBarrier hb{};
     EWOS_CUDA_TRY(cudaMemcpyAsync(&hb, S.bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
     EWOS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -747,97 +997,314 @@ static ewos_status lu_factor_device(T* A, int m, int lda, LuScratch& S, cudaStre
 }
 
 
-// Solve with the factors of P A = L U for nrhs right-hand sides x [nrhs][m] (in place; x arrives
-// already permuted).  Block 0 owns the 64-row diagonal blocks and solves each from shared memory;
-// per diagonal block one grid barrier: block 0 first updates the next diagonal block's rows and
-// solves it while the other blocks update the rows further down (the same in reverse for U).
-constexpr int kTB = 64;
+// ------------------------------------------------------------------ LU without interchanges
+// FP32 blocked LU with the diagonal pivots, accepted only when it equals the partial-pivoting
+// factorisation: partial pivoting picks the diagonal at every column exactly when every
+// multiplier satisfies |l| <= 1, so the largest |l| is tracked and the caller refactors with
+// interchanges when it exceeds 1 (or a pivot is zero).  Per 64-column panel one launch factors
+// the diagonal block (redundantly in every CTA, in shared memory) and then, a thread per row /
+// column, forms L21 = A21 U11^-1 and U12 = L11^-1 A12; the trailing update is the FP32 GEMM.
+// Factored diagonal blocks go to a side buffer (other CTAs still read the original block) and
+// are written into the matrix after the last panel.
+constexpr int kNpThreads = 256;
+constexpr int kNpLd = kNB + 4;   // 16-byte aligned rows; a warp's 32 columns hit distinct banks
 
-template <typename T>
-__global__ void lu_solve_kernel(const T* __restrict__ LU, int lda, int m, const int* __restrict__ ipiv,
-                                double* __restrict__ x, int nrhs, GridBarrier* bar) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nblk = gridDim.x;
-    const int nbk = (m + kTB - 1) / kTB;
-    (void)ipiv;
-    __shared__ T sL[kTB][kTB + 1];
-    __shared__ double sx[kTB];
-    auto update_rows = [&](int kb, int ke, int rlo, int rhi, int worker, int nworkers) {
-        // x[r][i] -= sum_{k in [kb, ke)} LU[i][k] x[r][k] for rows i in [rlo, rhi)
-        const int64_t total = (int64_t)(rhi - rlo) * nrhs;
-        for (int64_t t = worker; t < total; t += nworkers) {
-            const int i = rlo + (int)(t / nrhs), r = (int)(t % nrhs);
-            double* xr = x + (size_t)r * m;
-            double acc = 0.0;
-            for (int k = kb + lane; k < ke; k += 32) acc += (double)LU[(size_t)i * lda + k] * xr[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-            if (lane == 0) xr[i] -= acc;
-        }
-    };
-    auto diag = [&](int t, bool lower) {
-        const int ib = t * kTB, ie = min(m, ib + kTB), w = ie - ib;
-        for (int q = threadIdx.x; q < w * w; q += blockDim.x) sL[q / w][q % w] = LU[(size_t)(ib + q / w) * lda + ib + q % w];
-        for (int r = 0; r < nrhs; ++r) {
-            double* xr = x + (size_t)r * m;
-            __syncthreads();
-            for (int i = threadIdx.x; i < w; i += blockDim.x) sx[i] = xr[ib + i];
-            __syncthreads();
-            if (warp == 0) {
-                if (lower) {
-                    for (int i = 0; i < w; ++i) {
-                        double acc = 0.0;
-                        for (int k = lane; k < i; k += 32) acc += (double)sL[i][k] * sx[k];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-                        if (lane == 0) sx[i] -= acc;
-                        __syncwarp();
-                    }
-                } else {
-                    for (int i = w - 1; i >= 0; --i) {
-                        double acc = 0.0;
-                        for (int k = i + 1 + lane; k < w; k += 32) acc += (double)sL[i][k] * sx[k];
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-                        if (lane == 0) sx[i] = (sx[i] - acc) / (double)sL[i][i];
-                        __syncwarp();
-                    }
-                }
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < w; i += blockDim.x) xr[ib + i] = sx[i];
+__device__ __forceinline__ void atomic_max_pos(int* bits, float v) {
+    // non-negative floats (and NaN, as a large pattern) order like their bit patterns
+    atomicMax(bits, __float_as_int(v));
+}
+
+__global__ void __launch_bounds__(kNpThreads) lu_panel_nopiv_kernel(float* __restrict__ A, int lda, int m, int kb,
+                                                                    int nb, float* __restrict__ diag_out,
+                                                                    GridBarrier* __restrict__ bar) {
+    __shared__ __align__(16) float D[kNB][kNpLd];     // diagonal block: L below, U on and above
+    __shared__ __align__(16) float Lt[kNB][kNB];      // Lt[k][i] = L_ik (i > k), else 0
+    __shared__ __align__(16) float rU[kNB];
+    const int tid = threadIdx.x, c = tid & (kNB - 1), q = tid >> 6;   // 4 threads per column
+    constexpr int kQ = kNpThreads / kNB;
+    float mx = 0.f;
+    int zero = 0;
+    // identity beyond nb
+    for (int i = q; i < kNB; i += kQ)
+        D[i][c] = (i < nb && c < nb) ? A[(size_t)(kb + i) * lda + kb + c] : (i == c ? 1.f : 0.f);
+    __syncthreads();
+    // right-looking elimination, multipliers formed on the fly; column j is scaled at the end
+    for (int j = 0; j < kNB; ++j) {
+        const float piv = D[j][j];
+        const float r = piv != 0.f ? 1.f / piv : 0.f;
+        if (tid == 0) { rU[j] = r; zero |= piv == 0.f; }
+        if (c > j) {
+            const float u = D[j][c] * r;
+            for (int i = j + 1 + q; i < kNB; i += kQ) D[i][c] = fmaf(-D[i][j], u, D[i][c]);
         }
         __syncthreads();
-    };
-    // ---- forward, unit lower
-    if (blockIdx.x == 0) diag(0, true);
-    if (!grid_sync(bar)) return;
-    for (int t = 0; t + 1 < nbk; ++t) {
-        const int ib = t * kTB, ie = ib + kTB;
-        const int nxt_hi = min(m, ie + kTB);
-        if (blockIdx.x == 0) {
-            update_rows(ib, ie, ie, nblk == 1 ? m : nxt_hi, warp, nw);
-            __syncthreads();
-            diag(t + 1, true);
-        } else if (nxt_hi < m) {
-            update_rows(ib, ie, nxt_hi, m, (blockIdx.x - 1) * nw + warp, (nblk - 1) * nw);
-        }
-        if (!grid_sync(bar)) return;
     }
-    // ---- backward, upper with diagonal
-    if (blockIdx.x == 0) diag(nbk - 1, false);
-    if (!grid_sync(bar)) return;
-    for (int t = nbk - 1; t > 0; --t) {
-        const int ib = t * kTB, ie = min(m, ib + kTB);
-        const int prv_lo = ib - kTB;
-        if (blockIdx.x == 0) {
-            update_rows(ib, ie, nblk == 1 ? 0 : prv_lo, ib, warp, nw);
-            __syncthreads();
-            diag(t - 1, false);
-        } else if (prv_lo > 0) {
-            update_rows(ib, ie, 0, prv_lo, (blockIdx.x - 1) * nw + warp, (nblk - 1) * nw);
+    for (int i = c + 1 + q; i < kNB; i += kQ) {
+        const float l = D[i][c] * rU[c];
+        D[i][c] = l;
+        mx = fmaxf(mx, fabsf(l));
+    }
+    __syncthreads();
+    for (int t = tid; t < kNB * kNB; t += kNpThreads) {
+        const int k = t >> 6, i = t & 63;
+        Lt[k][i] = i > k ? D[i][k] : 0.f;
+    }
+    const int rest = m - kb - nb;
+    const int nbl = (rest + kNpThreads - 1) / kNpThreads;
+    if (blockIdx.x == 0) {
+        for (int t = tid; t < nb * nb; t += kNpThreads) diag_out[t] = D[t / nb][t % nb];
+        if (zero) bar->singular = 1;
+    }
+    __syncthreads();
+    if (rest > 0 && blockIdx.x < nbl) {
+        // L21 rows: x U11 = a  (nb == 64 whenever rows remain below the block)
+        const int i = kb + nb + blockIdx.x * kNpThreads + tid;
+        if (i < m) {
+            float x[kNB];
+            const float* src = A + (size_t)i * lda + kb;
+#pragma unroll
+            for (int cc = 0; cc < kNB; ++cc) x[cc] = src[cc];
+#pragma unroll
+            for (int j = 0; j < kNB; ++j) {
+                x[j] *= rU[j];
+                const float4* u4 = reinterpret_cast<const float4*>(&D[j][0]);
+#pragma unroll
+                for (int t = (j + 1) / 4; t < kNB / 4; ++t) {
+                    const float4 u = u4[t];
+                    if (4 * t > j) x[4 * t] = fmaf(-x[j], u.x, x[4 * t]);
+                    if (4 * t + 1 > j) x[4 * t + 1] = fmaf(-x[j], u.y, x[4 * t + 1]);
+                    if (4 * t + 2 > j) x[4 * t + 2] = fmaf(-x[j], u.z, x[4 * t + 2]);
+                    if (4 * t + 3 > j) x[4 * t + 3] = fmaf(-x[j], u.w, x[4 * t + 3]);
+                }
+            }
+            float* dst = A + (size_t)i * lda + kb;
+#pragma unroll
+            for (int cc = 0; cc < kNB; ++cc) {
+                dst[cc] = x[cc];
+                mx = fmaxf(mx, fabsf(x[cc]));
+            }
         }
-        if (!grid_sync(bar)) return;
+    } else if (rest > 0 && blockIdx.x < 2 * nbl) {
+        // U12 columns: L11 y = a  (unit lower)
+        const int col = kb + nb + (blockIdx.x - nbl) * kNpThreads + tid;
+        if (col < m) {
+            float y[kNB];
+#pragma unroll
+            for (int r = 0; r < kNB; ++r) y[r] = A[(size_t)(kb + r) * lda + col];
+#pragma unroll
+            for (int k = 0; k < kNB; ++k) {
+                const float4* l4 = reinterpret_cast<const float4*>(&Lt[k][0]);
+#pragma unroll
+                for (int t = (k + 1) / 4; t < kNB / 4; ++t) {
+                    const float4 l = l4[t];
+                    if (4 * t > k) y[4 * t] = fmaf(-l.x, y[k], y[4 * t]);
+                    if (4 * t + 1 > k) y[4 * t + 1] = fmaf(-l.y, y[k], y[4 * t + 1]);
+                    if (4 * t + 2 > k) y[4 * t + 2] = fmaf(-l.z, y[k], y[4 * t + 2]);
+                    if (4 * t + 3 > k) y[4 * t + 3] = fmaf(-l.w, y[k], y[4 * t + 3]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < kNB; ++r) A[(size_t)(kb + r) * lda + col] = y[r];
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0 && mx > 0.f) atomic_max_pos(&bar->maxl_bits, mx);
+}
+
+__global__ void diag_writeback_kernel(float* __restrict__ A, int lda, int m, const float* __restrict__ diag) {
+    const int t = blockIdx.x, kb = t * kNB, nb = min(kNB, m - kb);
+    const float* d = diag + (size_t)t * kNB * kNB;
+    for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) A[(size_t)(kb + q / nb) * lda + kb + q % nb] = d[q];
+}
+
+__global__ void iota_kernel(int* __restrict__ v, int m) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) v[i] = i;
+}
+
+// Returns EWOS_OK with *accepted false when a multiplier exceeds 1 or a pivot is zero (the
+// caller then refactors the original matrix with interchanges).
+static ewos_status lu_factor_nopiv(float* A, int m, int lda, LuScratch& S, cudaStream_t st, bool* accepted) {
+    EWOS_CUDA_TRY(cudaMemsetAsync(S.bar, 0, sizeof(GridBarrier), st));
+    for (int kb = 0; kb < m; kb += kNB) {
+        const int nb = std::min(kNB, m - kb);
+        const int rest = m - kb - nb;
+        const int nbl = (rest + kNpThreads - 1) / kNpThreads;
+        ::ewos::note_launch(), lu_panel_nopiv_kernel<<<std::max(1, 2 * nbl), kNpThreads, 0, st>>>(
+            A, lda, m, kb, nb, S.diag32 + (size_t)(kb / kNB) * kNB * kNB, S.bar);
+        if (rest > 0)
+            gemm_trailing<float>(st, rest, rest, nb, A + (size_t)(kb + nb) * lda + kb, lda,
+                                 A + (size_t)kb * lda + kb + nb, lda, A + (size_t)(kb + nb) * lda + kb + nb, lda);
+    }
+    const int nbk = (m + kNB - 1) / kNB;
+    ::ewos::note_launch(), diag_writeback_kernel<<<nbk, 256, 0, st>>>(A, lda, m, S.diag32);
+    ::ewos::note_launch(), iota_kernel<<<(m + 255) / 256, 256, 0, st>>>(S.ipiv, m);
+    ::ewos::note_launch(), iota_kernel<<<(m + 255) / 256, 256, 0, st>>>(S.perm, m);
+    ::ewos::note_launch(), diag_inverse_kernel<float><<<nbk, 64, 0, st>>>(A, lda, m, (float*)S.dinv);
+    GridBarrier hb{};
+    EWOS_CUDA_TRY(cudaMemcpyAsync(&hb, S.bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    EWOS_CUDA_TRY(cudaGetLastError());
+    *accepted = !hb.singular && hb.maxl_bits <= __builtin_bit_cast(int, 1.0f);
+    return EWOS_OK;
+}
+
+// Solve with the factors of P A = L U for nrhs right-hand sides x [nrhs][m] (in place; x arrives
+// already permuted), by 64-row steps with one grid barrier each.  Forward step j: block 0 takes
+// the rows of diagonal block j, subtracts the product of their sub-diagonal block with the segment
+// solved at step j - 1 and applies the precomputed inverse of diagonal block j; meanwhile the other
+// blocks (a warp per row) subtract the step j - 1 segment from all rows below block j.  The
+// backward sweep is the same upwards with the upper factor.  Block 0 stages the next step's two
+// 64 x 64 operands in shared memory (cp.async, double buffered) while the barrier is pending, so
+// its critical path per step is one read of the 64 updated entries plus two small products.
+constexpr int kTB = 64;
+constexpr int kTBP = kTB + 1;   // padded shared-memory row
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename T>
+constexpr size_t lu_solve_smem() { return sizeof(T) * 2 * 2 * kTB * kTBP; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) lu_solve_kernel(const T* __restrict__ LU, int lda, int m,
+                                                       const T* __restrict__ Dinv, double* __restrict__ x, int nrhs,
+                                                       GridBarrier* bar) {
+    extern __shared__ __align__(16) unsigned char lu_sm[];
+    T* Ls = reinterpret_cast<T*>(lu_sm);          // [2][64][65] sub-diagonal blocks
+    T* Ds = Ls + 2 * kTB * kTBP;                   // [2][64][65] diagonal-block inverses
+    __shared__ double sx[kTB], sy[kTB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int nblk = gridDim.x;
+    const int nbk = (m + kTB - 1) / kTB;
+    const int total_steps = 2 * nbk;   // per right-hand side: forward 0..nbk-1, backward nbk-1..0
+
+    // step descriptors (block 0): rows [rlo, rlo + h), segment columns [cb, cb + w), inverse index
+    auto step_desc = [&](int s, int& rlo, int& h, int& cb, int& w, const T*& D) {
+        const bool fwd = s < nbk;
+        const int j = fwd ? s : total_steps - 1 - s;
+        rlo = j * kTB;
+        h = min(kTB, m - rlo);
+        if (fwd) { cb = (j - 1) * kTB; w = j > 0 ? kTB : 0; }
+        else { cb = (j + 1) * kTB; w = j + 1 < nbk ? min(kTB, m - cb) : 0; }
+        D = Dinv + (size_t)j * 2 * kTB * kTB + (fwd ? 0 : kTB * kTB);
+    };
+    auto prefetch = [&](int s, int buf) {
+        int rlo, h, cb, w;
+        const T* D;
+        step_desc(s, rlo, h, cb, w, D);
+        T* L = Ls + buf * kTB * kTBP;
+        T* Dd = Ds + buf * kTB * kTBP;
+        for (int q = tid; q < kTB * kTB; q += blockDim.x) {
+            const int i = q >> 6, k = q & 63;
+            if (i < h && k < w) cp_async_elem(&L[i * kTBP + k], LU + (size_t)(rlo + i) * lda + cb + k);
+            else L[i * kTBP + k] = T(0);
+            cp_async_elem(&Dd[i * kTBP + k], D + q);
+        }
+        cp_async_commit();
+    };
+    // workers: xr[i] -= LU[i][cb .. cb + w) . xr[cb .. cb + w) for rows [rlo, rhi)
+    auto update_rows = [&](int cb, int w, int rlo, int rhi, int worker, int nworkers, double* xr) {
+        const int k0 = 2 * lane, k1 = 2 * lane + 1;
+        const double s0 = k0 < w ? __ldcg(xr + cb + k0) : 0.0;
+        const double s1 = k1 < w ? __ldcg(xr + cb + k1) : 0.0;
+        for (int i = rlo + worker; i < rhi; i += 4 * nworkers) {
+            double acc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int r = i + u * nworkers;
+                acc[u] = 0.0;
+                if (r < rhi) {
+                    const T* row = LU + (size_t)r * lda + cb;
+                    acc[u] = (k0 < w ? (double)row[k0] * s0 : 0.0) + (k1 < w ? (double)row[k1] * s1 : 0.0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+                const int r = i + u * nworkers;
+                if (lane == 0 && r < rhi) xr[r] = __ldcg(xr + r) - acc[u];
+            }
+        }
+    };
+    const int i4 = tid >> 2, q4 = tid & 3;   // 4 threads per row for the 64 x 64 products
+    if (blockIdx.x == 0) {
+        prefetch(0, 0);
+        for (int i = tid; i < kTB; i += blockDim.x) sx[i] = 0.0;
+    }
+    for (int r = 0; r < nrhs; ++r) {
+        double* xr = x + (size_t)r * m;
+        for (int s = 0; s < total_steps; ++s) {
+            const int g = r * total_steps + s;
+            const int buf = g & 1;
+            const bool fwd = s < nbk;
+            const int j = fwd ? s : total_steps - 1 - s;
+            if (blockIdx.x == 0) {
+                int rlo, h, cb, w;
+                const T* D;
+                step_desc(s, rlo, h, cb, w, D);
+                const T* L = Ls + buf * kTB * kTBP;
+                const T* Dd = Ds + buf * kTB * kTBP;
+                double xi = 0.0;
+                if (i4 < h && q4 == 0) xi = __ldcg(xr + rlo + i4);
+                cp_async_wait_all();
+                __syncthreads();
+                // y = x[rows] - Lsub . sx   (sx is zero beyond the previous segment's width)
+                if (i4 < kTB) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) acc += (double)L[i4 * kTBP + q4 * 16 + k] * sx[q4 * 16 + k];
+                    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                    if (q4 == 0) sy[i4] = i4 < h ? xi - acc : 0.0;
+                }
+                __syncthreads();
+                // next step's operands go in while this one finishes and the barrier is pending
+                const int gn = g + 1;
+                if (gn < nrhs * total_steps) prefetch(gn % total_steps, gn & 1);
+                if (i4 < kTB) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) acc += (double)Dd[i4 * kTBP + q4 * 16 + k] * sy[q4 * 16 + k];
+                    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                    if (q4 == 0) {
+                        const double v = i4 < h ? acc : 0.0;
+                        sx[i4] = v;
+                        if (i4 < h) xr[rlo + i4] = v;
+                    }
+                }
+                __syncthreads();
+                (void)j;
+            }
+            // the others subtract the segment solved at the previous step from the remaining rows
+            if (s > 0 && s != nbk) {
+                const int jp = fwd ? j - 1 : j + 1;           // segment solved at the previous step
+                const int cb = jp * kTB, w = min(kTB, m - cb);
+                int lo, hi;
+                if (fwd) { lo = (j + 1) * kTB; hi = m; }
+                else { lo = 0; hi = j * kTB; }
+                if (nblk > 1) {
+                    if (blockIdx.x > 0 && lo < hi) update_rows(cb, w, lo, hi, (blockIdx.x - 1) * nw + warp, (nblk - 1) * nw, xr);
+                } else if (lo < hi) {
+                    update_rows(cb, w, lo, hi, warp, nw, xr);
+                }
+            }
+            if (!grid_sync(bar)) {
+                if (blockIdx.x == 0) cp_async_wait_all();
+                return;
+            }
+        }
     }
 }
 
@@ -865,6 +1332,7 @@ void free_workspace(SolveWorkspace* ws) {
     ::ewos::dev_free(ws->scal); ::ewos::dev_free(ws->umax);
     ::ewos::dev_free(ws->lu.pub); ::ewos::dev_free(ws->lu.bar); ::ewos::dev_free(ws->lu.ipiv);
     ::ewos::dev_free(ws->lu.perm); ::ewos::dev_free(ws->lu.swp); ::ewos::dev_free(ws->lu.tmp);
+    ::ewos::dev_free(ws->lu.dinv); ::ewos::dev_free(ws->lu.diag32);
     ::ewos::dev_free(ws->Q32); ::ewos::dev_free(ws->L32); ::ewos::dev_free(ws->LU32); ::ewos::dev_free(ws->J32);
     ::ewos::dev_free(ws->Jx32); ::ewos::dev_free(ws->P32);
     ::ewos::dev_free(ws->rhs); ::ewos::dev_free(ws->r); ::ewos::dev_free(ws->dx);
@@ -908,6 +1376,8 @@ static ewos_status ensure_workspace(ewos_toolbox* tb, int64_t nrhs, bool mixed) 
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.perm, sizeof(int) * m));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.swp, sizeof(int) * 260));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.tmp, sizeof(double) * m * nrhs));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.dinv, sizeof(double) * ((m + 63) / 64) * 2 * 64 * 64));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.diag32, sizeof(float) * ((m + 63) / 64) * 64 * 64));
     }
     SolveWorkspace* ws = tb->ws;
     if (!mixed && !ws->Q) {
@@ -932,7 +1402,9 @@ static ewos_status lu_solve_device(const T* LU, int m, int lda, LuScratch& S, do
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int threads = 256;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_solve_kernel<T>, threads, 0);
+    const size_t smem = lu_solve_smem<T>();
+    EWOS_CUDA_TRY(cudaFuncSetAttribute(lu_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_solve_kernel<T>, threads, smem);
     const int blocks = std::max(1, std::min(nsm, per_sm * nsm));
     EWOS_CUDA_TRY(cudaMemsetAsync(S.bar, 0, sizeof(GridBarrier), st));
     {
@@ -942,11 +1414,11 @@ static ewos_status lu_solve_device(const T* LU, int m, int lda, LuScratch& S, do
     }
     const T* a0 = LU;
     int lda_ = lda, m_ = m, nr = nrhs;
-    const int* ip = S.ipiv;
+    const T* di = (const T*)S.dinv;
     GridBarrier* bar = S.bar;
-    void* args[] = {&a0, &lda_, &m_, &ip, &x, &nr, &bar};
+    void* args[] = {&a0, &lda_, &m_, &di, &x, &nr, &bar};
     ::ewos::note_launch();
-        EWOS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)lu_solve_kernel<T>, blocks, threads, args, 0, st));
+        EWOS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)lu_solve_kernel<T>, blocks, threads, args, smem, st));
     GridBarrier hb{};
     EWOS_CUDA_TRY(cudaMemcpyAsync(&hb, S.bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
     EWOS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1075,6 +1547,7 @@ static ewos_status solve_fp64(ewos_toolbox* tb, const ewos_problem* pb, double r
         rep->ms_assemble = elapsed_ms(t0);
         if (!semi) {
             auto t1 = std::chrono::steady_clock::now();
+            ++rep->factorizations, ++rep->pivoted_factorizations;
             ewos_status s = factor_shifted<TP>(C, alpha, nullptr);
             if (s != EWOS_OK) return s;
             rep->ms_factor = elapsed_ms(t1);
@@ -1108,7 +1581,8 @@ static ewos_status solve_fp64(ewos_toolbox* tb, const ewos_problem* pb, double r
                     const TP* Gm = (const TP*)tb->P + (size_t)C.D * C.n * C.m;
                     ::ewos::note_launch(), jac_scale_kernel<TP><<<gj, 256, 0, C.st>>>(Gm, ws->u2, tb->lambda, nl, pb->nl_ncoef, ws->Jx, (int)C.n, (int)C.m);
                     auto t1 = std::chrono::steady_clock::now();
-                    ewos_status st = factor_shifted<TP>(C, alpha, ws->Jx);
+                    ++rep->factorizations, ++rep->pivoted_factorizations;
+            ewos_status st = factor_shifted<TP>(C, alpha, ws->Jx);
                     if (st != EWOS_OK) return st;
                     rep->ms_factor += elapsed_ms(t1);
                     cudaMemcpyAsync(ws->x, ws->y, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
@@ -1144,7 +1618,8 @@ static ewos_status solve_fp64(ewos_toolbox* tb, const ewos_problem* pb, double r
                 rep->alpha = alpha;
                 rep->ms_assemble += elapsed_ms(ta);
                 auto t1 = std::chrono::steady_clock::now();
-                ewos_status st = factor_shifted<TP>(C, alpha, nullptr);
+                ++rep->factorizations, ++rep->pivoted_factorizations;
+            ewos_status st = factor_shifted<TP>(C, alpha, nullptr);
                 if (st != EWOS_OK) return st;
                 rep->ms_factor += elapsed_ms(t1);
                 residual<TP>(C, nullptr, g, f, nullptr, 0, 0.0, ws->y);
@@ -1273,14 +1748,37 @@ static ewos_status refine(const Ctx& C, const double* b, double* x, double alpha
     return EWOS_OK;
 }
 
-static ewos_status factor32(const Ctx& C, const float* src, double alpha) {
-    cudaMemcpyAsync(C.ws->LU32, src, sizeof(float) * C.m * C.m, cudaMemcpyDeviceToDevice, C.st);
-    ::ewos::note_launch(), add_diag_kernel<float><<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.ws->LU32, (int)C.m, (int)C.m, alpha);
+// FP32 factors of the matrix that build() writes into LU32: first with the diagonal pivots
+// (pivoting == 0; kept when it equals the partial-pivoting factorisation), else rebuilt and
+// factored with row interchanges.
+template <typename Build>
+static ewos_status factor32_with(const Ctx& C, Build build, int pivoting, ewos_solve_report* rep) {
+    build();
+    ++rep->factorizations;
+    if (pivoting == 0) {
+        bool accepted = false;
+        ewos_status s = lu_factor_nopiv(C.ws->LU32, (int)C.m, (int)C.m, C.ws->lu, C.st, &accepted);
+        if (s != EWOS_OK) return s;
+        if (accepted) return EWOS_OK;
+        build();
+    }
+    ++rep->pivoted_factorizations;
     bool sing = false;
     ewos_status s = lu_factor_device<float>(C.ws->LU32, (int)C.m, (int)C.m, C.ws->lu, C.st, &sing);
     if (s != EWOS_OK) return s;
     if (sing) { set_error("LU (FP32): zero pivot"); return EWOS_ESINGULAR; }
     return EWOS_OK;
+}
+
+static ewos_status factor32(const Ctx& C, const float* src, double alpha, int pivoting, ewos_solve_report* rep) {
+    return factor32_with(
+        C,
+        [&] {
+            cudaMemcpyAsync(C.ws->LU32, src, sizeof(float) * C.m * C.m, cudaMemcpyDeviceToDevice, C.st);
+            ::ewos::note_launch(), add_diag_kernel<float><<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.ws->LU32, (int)C.m,
+                                                                                                   (int)C.m, alpha);
+        },
+        pivoting, rep);
 }
 
 constexpr double kRefineTol = 1e-10;
@@ -1318,7 +1816,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, const ewos_problem* pb, doubl
         rep->ms_assemble = elapsed_ms(ta);
         if (!semi) {
             auto t1 = std::chrono::steady_clock::now();
-            ewos_status st = factor32(C, ws->L32, alpha);
+            ewos_status st = factor32(C, ws->L32, alpha, pb->pivoting, rep);
             if (st != EWOS_OK) return st;
             rep->ms_factor = elapsed_ms(t1);
             auto t2 = std::chrono::steady_clock::now();
@@ -1352,15 +1850,18 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, const ewos_problem* pb, doubl
                     const TP* Gm = (const TP*)tb->P + (size_t)C.D * C.n * C.m;
                     ::ewos::note_launch(), jac_scale32_kernel<TP><<<gj, 256, 0, C.st>>>(Gm, ws->u2, tb->lambda, nl, pb->nl_ncoef,
                                                                                       ws->Jx32, (int)C.n, (int)C.m);
-                    cudaMemcpyAsync(ws->LU32, ws->L32, sizeof(float) * C.m * C.m, cudaMemcpyDeviceToDevice, C.st);
                     const float* Gm32 = P32 + (size_t)C.D * C.n * C.m;
-                    sgemm<true>(C.st, (int)C.m, (int)C.m, (int)C.n, 1.f, Gm32, C.m, ws->Jx32, C.m, 1.f, ws->LU32, C.m);
-                    ::ewos::note_launch(), add_diag_kernel<float><<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(ws->LU32, (int)C.m, (int)C.m, alpha);
-                    bool sing = false;
                     auto t1 = std::chrono::steady_clock::now();
-                    ewos_status st = lu_factor_device<float>(ws->LU32, (int)C.m, (int)C.m, ws->lu, C.st, &sing);
+                    ewos_status st = factor32_with(
+                        C,
+                        [&] {
+                            cudaMemcpyAsync(ws->LU32, ws->L32, sizeof(float) * C.m * C.m, cudaMemcpyDeviceToDevice, C.st);
+                            sgemm<true>(C.st, (int)C.m, (int)C.m, (int)C.n, 1.f, Gm32, C.m, ws->Jx32, C.m, 1.f, ws->LU32, C.m);
+                            ::ewos::note_launch(), add_diag_kernel<float><<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(
+                                ws->LU32, (int)C.m, (int)C.m, alpha);
+                        },
+                        pb->pivoting, rep);
                     if (st != EWOS_OK) return st;
-                    if (sing) { set_error("LU (FP32): zero pivot"); return EWOS_ESINGULAR; }
                     rep->ms_factor += elapsed_ms(t1);
                     cudaMemcpyAsync(ws->rhs, ws->y, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
                     st = refine<TP>(C, ws->rhs, ws->x, alpha, ws->u2, nl, pb->nl_ncoef, 1e-10, 8, &sweeps, nullptr);
@@ -1402,7 +1903,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, const ewos_problem* pb, doubl
                 rep->alpha = alpha;
                 rep->ms_assemble += elapsed_ms(ta);
                 auto t1 = std::chrono::steady_clock::now();
-                ewos_status st = factor32(C, ws->L32, alpha);
+                ewos_status st = factor32(C, ws->L32, alpha, pb->pivoting, rep);
                 if (st != EWOS_OK) return st;
                 rep->ms_factor += elapsed_ms(t1);
                 residual<TP>(C, nullptr, g, f, nullptr, 0, 0.0, ws->y);

@@ -59,13 +59,14 @@ class _Problem(ctypes.Structure):
                 ("g", ctypes.c_void_p), ("nrhs", ctypes.c_int64), ("nl_kind", ctypes.c_int),
                 ("nl_coef", ctypes.c_void_p), ("nl_ncoef", ctypes.c_int), ("mode", ctypes.c_int),
                 ("rcond", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("inputs_on_device", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("inputs_on_device", ctypes.c_int), ("stream", ctypes.c_void_p), ("pivoting", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("refine_iters", ctypes.c_int), ("converged", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("residual", ctypes.c_double), ("ms_total", ctypes.c_double),
-                ("ms_assemble", ctypes.c_double), ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double)]
+                ("ms_assemble", ctypes.c_double), ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double),
+                ("factorizations", ctypes.c_int), ("pivoted_factorizations", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -171,8 +172,9 @@ class Toolbox:
         return dict(G=self.get("G"), gradG=self.get("gradG"), H=self.get("H"), gradH=self.get("gradH"))
 
     def solve(self, A, f, g, b=None, c=None, kind="linear", coef=None, mode="fp64", rcond=-1.0, tol=0.0,
-              max_iter=0, want_s=False, on_device=False, out=None, stream=None):
-        """Solve the problem of include/ewos.h; returns (u [nrhs][n] or [n], s or None, report)."""
+              max_iter=0, want_s=False, on_device=False, out=None, stream=None, pivoting=0):
+        """Solve the problem of include/ewos.h; returns (u [nrhs][n] or [n], s or None, report).
+        pivoting=1 forces row interchanges in the mixed-mode LU."""
         if on_device:
             Ad, fd, gd, bd, cd = A, f, g, b, c
             nrhs = f.shape[0] if f.dim() == 2 else 1
@@ -182,7 +184,7 @@ class Toolbox:
         cf = _f64(coef) if coef is not None else None
         pb = _Problem(_ptr(Ad), _ptr(bd), _ptr(cd), _ptr(fd), _ptr(gd), nrhs, NL[kind], _ptr(cf),
                       0 if cf is None else cf.size, MODE[mode], float(rcond), float(tol), int(max_iter),
-                      1 if on_device else 0, stream)
+                      1 if on_device else 0, stream, int(pivoting))
         if out is not None:
             u = out
             optr = out.data_ptr()

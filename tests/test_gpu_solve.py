@@ -208,3 +208,69 @@ def test_mixed_square4096_full_size():
     e_m = S.errors(u, pb.u_star, lam)["l2"]
     e_d = S.errors(u64, pb.u_star, lam)["l2"]
     assert abs(e_m - e_d) <= 1e-3 * max(1e-3, e_d)
+
+
+# ------------------------------------------------------------------ mixed-mode LU variants
+# The mixed mode factors with the diagonal pivots and keeps that factorisation only when every
+# multiplier has |l| <= 1 (it is then the partial-pivoting one); otherwise it refactors with
+# row interchanges.  Both must give the oracle's solution after refinement.
+
+def test_mixed_unpivoted_accepted_and_equal_to_pivoted(disk):
+    w, tb, lam, gtb = disk
+    pb = w.problem
+    u0, _, r0 = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, c=pb.c, mode="mixed")
+    u1, _, r1 = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, c=pb.c, mode="mixed", pivoting=1)
+    assert r0["factorizations"] == 1 and r0["pivoted_factorizations"] == 0
+    assert r1["factorizations"] == 1 and r1["pivoted_factorizations"] == 1
+    assert _rel(u0, u1) < 1e-9
+
+
+def _random_toolbox(seed, n_drop=0):
+    # G ~ N(0, 1), grad G ~ N(0, 1e-4) and a strong drift: Lambda is dominated by its
+    # non-symmetric b . grad G^T G part and needs row interchanges (max |l| ~ 80 without)
+    rng = np.random.default_rng(seed)
+    x = W.disk_nodes(0.15, 0.9)
+    x = x[: x.shape[0] - n_drop]
+    n = m = x.shape[0]
+    z = W.circle_nodes(24)
+    G = rng.normal(size=(n, m))
+    gradG = rng.normal(size=(2, n, m)) * 0.01
+    H = rng.uniform(0, 1, (n, z.shape[0]))
+    H /= H.sum(1, keepdims=True)
+    gradH = rng.normal(size=(2, n, z.shape[0])) * 0.01
+    lam = np.full(n, 1.0 / n)
+    A = np.tile(np.eye(2), (n, 1, 1))
+    b = rng.normal(size=(n, 2)) * 50
+    f = rng.normal(size=n)
+    g = rng.normal(size=z.shape[0])
+    tb = dict(G=G, gradG=gradG, H=H, gradH=gradH)
+    return x, z, tb, lam, A, b, f, g
+
+
+def test_mixed_falls_back_to_interchanges():
+    x, z, tb, lam, A, b, f, g = _random_toolbox(5)
+    gtb = ewos.toolbox_from_host(2, x, z, tb["G"], tb["gradG"], tb["H"], tb["gradH"], lam, precision=64)
+    u, s, rep = gtb.solve(A, f, g, b=b, mode="mixed", want_s=True)
+    gtb.close()
+    assert rep["converged"]
+    assert rep["factorizations"] == 1 and rep["pivoted_factorizations"] == 1
+    ref = S.solve_linear(tb, lam, A, b, None, f, g, alpha=rep["alpha"])
+    assert _rel(u, ref["u"]) < 1e-9
+
+
+@pytest.mark.parametrize("k,per", [(11, 3), (8, 2), (1, 1)])
+def test_mixed_ragged_sizes(k, per):
+    # m = 118, 61, 1 (not multiples of the 64-wide panels), unpivoted FP32 LU
+    x = W.square_nodes(k)
+    x = x[: max(1, x.shape[0] - (3 if k > 1 else 0))]
+    z = W.square_boundary_nodes(per * 2)
+    r = oracle.walk_rows(2, "box", [0, 0, 1, 1], x, z, 400, 1e-4, 7)
+    lam = np.full(x.shape[0], 1.0 / x.shape[0])
+    tb = dict(G=r["G"], gradG=r["gradG"], H=r["Hc"] / 400.0, gradH=r["gradH"])
+    pb = W.make_problem("square", x, z)
+    gtb = ewos.toolbox_from_host(2, x, z, tb["G"], tb["gradG"], tb["H"], tb["gradH"], lam, precision=64)
+    u, _, rep = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, mode="mixed")
+    gtb.close()
+    assert rep["converged"]
+    ref = S.solve_linear(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, alpha=rep["alpha"])
+    assert _rel(u, ref["u"]) < 1e-9, x.shape
