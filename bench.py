@@ -36,10 +36,12 @@ WORKLOAD = ("square4096: unit square (box distance), 4096 interior nodes (64x64 
             "nodes, 10^4 walks/node, eps 1e-4, FP32 walks, seed 0; linear solve A=[[1+x^2,0.3],[0.3,1+y^2]], "
             "b=(1,-0.5), u*=exp(x) sin(2y), Tikhonov rcond 3e-2")
 L2_BYTES = 126 * 2 ** 20
-# walk kernel issue budget per WoS step, counted from the kernel source:
-# thread-level instructions of one step of the 2D walk (Philox, Green radius, two sincospi,
-# box distance, lookup over the candidate list, three shared atomics, updates)
-OPS_PER_STEP_2D = 390
+# Warp instructions the walk kernel issues per WoS step on this workload, and its DRAM bytes
+# per launch, both from one ncu capture of the kernel in the launch configuration this
+# benchmark runs (profiles/wos_walk_square4096.md).  The walk kernel is bound by instruction
+# issue: its roofline is 1 warp instruction per cycle per scheduler.
+WARP_INST_PER_STEP = 21.05
+WALK_DRAM_BYTES = 175.0e6
 
 
 def _peaks():
@@ -239,7 +241,9 @@ def main():
                              cell_weights=w.lam, stream=sp, on_device=True)
     lam = tbs.get("lambda")
     served = {}
-    for mode, count in (("mixed", args.serve_solves), ("fp64", max(2, min(3, args.serve_solves)))):
+    for mode, count in (("mixed", args.serve_solves), ("fp64", min(3, args.serve_solves))):
+        if count <= 0:
+            continue
         tbs.solve(Ad, fd, gd, b=bd, mode=mode, on_device=True, out=ud, stream=sp)      # workspace warm-up
         lat = []
         for _ in range(count):
@@ -278,9 +282,9 @@ def main():
     peaks, peak_src = _peaks()
     sm_mhz = ck.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_ops = nsm * 4 * 32 * (peaks.get("sm_max_mhz", 2032.0) * 1e6)   # thread-instructions/s at max clock
+    peak_ops = nsm * 4 * (peaks.get("sm_max_mhz", 2032.0) * 1e6)   # warp instructions/s at max clock
     wk = statistics.median(walk_ms)
-    achieved = steps_per_run * OPS_PER_STEP_2D / (wk / 1000.0)
+    achieved = steps_per_run * WARP_INST_PER_STEP / (wk / 1000.0)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": max(3, args.warmup),
         "ms_per_step": ms_total / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -288,16 +292,19 @@ def main():
         "config": {"workload": WORKLOAD, "solve_mode": args.mode, "l2": "flushed between timed steps (252 MB write)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "build_s": statistics.median(build_ms) / 1000.0, "walk_kernel_ms": wk,
+        "walk_config": {k: br[k] for k in ("threads_per_block", "ctas_per_sm", "grid", "hash_in_smem",
+                                           "lookup_grid_scale", "lookup_candidates")},
         "solve_ms": statistics.median(solve_ms), "wos_steps_per_step": steps_per_run,
         "walk_steps_per_s": steps_per_run / (wk / 1000.0),
         "e2e": {"value": e2e_steps / (statistics.median(e2e_ms) / 1000.0), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": statistics.median(e2e_ms)},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tinst/s",
-                     "frac": achieved / peak_ops, "traffic": None,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                     "unit": "T warp-instructions/s", "frac": achieved / peak_ops, "traffic": WALK_DRAM_BYTES,
                      "kernel": "wos_walk_kernel<float,2,box>",
-                     "note": f"{OPS_PER_STEP_2D} thread-instructions per WoS step (source count); peak = "
-                             f"{nsm} SMs x 4 schedulers x 32 lanes x {peaks.get('sm_max_mhz', 2032.0):.0f} MHz"},
+                     "note": f"{WARP_INST_PER_STEP} warp instructions per WoS step (ncu count) x WoS steps / "
+                             f"CUDA-event time of the walk kernel; peak = {nsm} SMs x 4 schedulers x 1 issue/cycle x "
+                             f"{peaks.get('sm_max_mhz', 2032.0):.0f} MHz ({peak_src} clock)"},
         "clocks": ck,
         "served_solve": served,
         "gpu_launches": launches_per_step,
