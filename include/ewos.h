@@ -200,6 +200,12 @@ typedef struct {
                                  every multiplier has |l| <= 1 (then it is the partial-pivoting
                                  factorisation) and otherwise redone with row interchanges;
                                  1 -> always partial pivoting.  FP64 mode always pivots.     */
+    int batched;              /* mixed mode: 1 -> all right-hand sides refined together, one
+                                 CUDA-graph launch per sweep; a semilinear problem then runs the
+                                 chord iteration s <- s - (Lambda + alpha I)^-1 (R(s) + alpha s)
+                                 on one factorisation, and exact Newton per right-hand side when
+                                 that does not reach tol (iters = chord sweeps when it does).
+                                 0 -> one right-hand side at a time, Newton for semilinear.   */
 } ewos_problem;
 
 typedef struct {
@@ -217,6 +223,51 @@ typedef struct {
  * outputs_on_device = 1.  rep may be NULL. */
 ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, double* u_out, double* s_out,
                        int outputs_on_device, ewos_solve_report* rep);
+
+/*
+ * Request server (no counterpart in the paper; the serving loop around ewos_solve).  Solve
+ * requests on device-resident toolboxes are queued in arrival order and admitted to worker
+ * slots as slots and device memory free up (continuous batching); each slot is a host thread
+ * with its own non-blocking CUDA stream and solve workspace, so requests in different slots run
+ * concurrently on the GPU.  A request's right-hand sides are refined together in CUDA-graph
+ * sweeps (mixed mode, as ewos_problem.batched = 1).  Memory: the budget is memory_fraction of
+ * the device memory free at creation minus reserve_bytes (and at most budget_bytes when > 0); a
+ * slot's workspace is charged at its estimated size; a request that does not fit waits for a
+ * slot to finish, or fails with EWOS_ENOMEM when nothing is running and it still does not fit.
+ * The caller keeps every toolbox alive until the requests on it have been waited for.  Calls
+ * are thread safe.
+ */
+typedef struct ewos_server ewos_server;
+typedef struct {
+    int max_slots;            /* concurrent requests (<= 0 -> 4, at most 64)                 */
+    double memory_fraction;   /* of the free device memory (<= 0 -> 0.8)                      */
+    int64_t reserve_bytes;    /* kept free for the caller                                     */
+    int64_t budget_bytes;     /* > 0: upper bound of the budget                               */
+} ewos_server_opts;
+typedef struct {
+    uint64_t submitted, completed, failed;
+    int queued, active, peak_active, slots;
+    int64_t budget_bytes, charged_bytes;
+} ewos_server_stats;
+typedef struct {
+    double queue_ms;          /* submission -> admission to a slot                            */
+    double run_ms;            /* admission -> results on the host                             */
+    double total_ms;
+    int slot;
+} ewos_request_timing;
+
+ewos_status ewos_server_create(const ewos_server_opts* opts, ewos_server** out);
+/* Copies the problem's host arrays (inputs_on_device must be 0; stream is ignored: the slot's
+ * stream is used) and queues it; *ticket identifies the request. */
+ewos_status ewos_server_submit(ewos_server* sv, ewos_toolbox* tb, const ewos_problem* pb, uint64_t* ticket);
+/* Waits (timeout_s <= 0: without limit; on expiry EWOS_ETIMEOUT and the request stays queued)
+ * for a request, copies u [nrhs][n] and s [nrhs][m] to the host buffers that are not NULL and
+ * releases it; returns the solve's status. */
+ewos_status ewos_server_wait(ewos_server* sv, uint64_t ticket, double timeout_s, double* u_out, double* s_out,
+                             ewos_solve_report* rep, ewos_request_timing* timing);
+ewos_status ewos_server_query(ewos_server* sv, ewos_server_stats* out);
+/* Finishes the queued requests, stops the slots and frees their workspaces. */
+void ewos_server_destroy(ewos_server* sv);
 
 /* Test hooks (no counterpart in the paper): Philox4x32-10 blocks for count counters
  * (ctr [count][4], key [2], out [count][4], host uint32), and the d = 2 Green-density radius

@@ -323,27 +323,36 @@ bool tc_assemble_available() {
 // C [M][N] = A^T B for A = P [K][M] and B = Q [K][N], both FP32 row-major, on the tensor cores:
 // split = false: TF32 inputs (relative error about 2^-11 per product); split = true: 3xTF32
 // (about 2^-21), three MMAs per step.
-ewos_status tc_assemble(const float* Akm, const float* Bkm, float* C, int M, int N, int K, cudaStream_t st,
-                        bool split) {
+// Scratch of one caller (a solve workspace): operand transposes and the error word.
+struct TcScratch {
+    tc::Scratch s;
+};
+
+void tc_scratch_free(TcScratch* t) {
+    if (!t) return;
+    ::ewos::dev_free(t->s.At); ::ewos::dev_free(t->s.Bt); ::ewos::dev_free(t->s.Atl); ::ewos::dev_free(t->s.Btl);
+    ::ewos::dev_free(t->s.err);
+    delete t;
+}
+
+// Enqueues the transposes and the GEMM on st; the pipeline-timeout word is left in *err_dev
+// for the caller to check after the stream has run (no host synchronisation here).
+static ewos_status tc_enqueue(tc::Scratch& S, const float* Akm, const float* Bkm, float* C, int M, int N, int K,
+                              cudaStream_t st, bool split) {
     using namespace tc;
-    int dev = 0;
-    EWOS_CUDA_TRY(cudaGetDevice(&dev));
     const int Kp = (K + BK - 1) / BK * BK;
-    std::lock_guard<std::mutex> lock(g_mu);
-    Scratch& S = g_scratch[dev & 63];
     const size_t need = (size_t)std::max(M, N) * Kp;
     if (S.cap < need || (split && !S.Atl)) {
         ::ewos::dev_free(S.At); ::ewos::dev_free(S.Bt); ::ewos::dev_free(S.Atl); ::ewos::dev_free(S.Btl);
         S.At = S.Bt = S.Atl = S.Btl = nullptr;
         S.cap = 0;
-        const size_t cap = std::max(need, S.cap);
-        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.At, sizeof(float) * cap));
-        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Bt, sizeof(float) * cap));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.At, sizeof(float) * need));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Bt, sizeof(float) * need));
         if (split) {
-            EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Atl, sizeof(float) * cap));
-            EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Btl, sizeof(float) * cap));
+            EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Atl, sizeof(float) * need));
+            EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Btl, sizeof(float) * need));
         }
-        S.cap = cap;
+        S.cap = need;
     }
     if (!S.err) EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.err, sizeof(int)));
     dim3 tb(32, 8);
@@ -373,6 +382,10 @@ ewos_status tc_assemble(const float* Akm, const float* Bkm, float* C, int M, int
         ::ewos::note_launch(), gemm_tf32_kernel<false><<<grid, 128, Cfg<false>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err);
     }
     EWOS_CUDA_TRY(cudaGetLastError());
+    return EWOS_OK;
+}
+
+static ewos_status tc_check(tc::Scratch& S, cudaStream_t st) {
     int herr = 0;
     EWOS_CUDA_TRY(cudaMemcpyAsync(&herr, S.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     EWOS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -381,6 +394,25 @@ ewos_status tc_assemble(const float* Akm, const float* Bkm, float* C, int M, int
         return EWOS_ETIMEOUT;
     }
     return EWOS_OK;
+}
+
+// C [M][N] = A^T B for K-major FP32 operands A [K][M], B [K][N].  With a caller scratch the
+// call is reentrant across workspaces; without one the per-device scratch is used under a lock.
+ewos_status tc_assemble(const float* Akm, const float* Bkm, float* C, int M, int N, int K, cudaStream_t st,
+                        bool split, TcScratch** owned) {
+    int dev = 0;
+    EWOS_CUDA_TRY(cudaGetDevice(&dev));
+    if (owned) {
+        if (!*owned) *owned = new TcScratch();
+        ewos_status s = tc_enqueue((*owned)->s, Akm, Bkm, C, M, N, K, st, split);
+        if (s != EWOS_OK) return s;
+        return tc_check((*owned)->s, st);
+    }
+    std::lock_guard<std::mutex> lock(tc::g_mu);
+    tc::Scratch& S = tc::g_scratch[dev & 63];
+    ewos_status s = tc_enqueue(S, Akm, Bkm, C, M, N, K, st, split);
+    if (s != EWOS_OK) return s;
+    return tc_check(S, st);
 }
 
 }  // namespace ewos
@@ -398,7 +430,7 @@ extern "C" ewos_status ewos_debug_tc_gemm(const float* A, const float* B, float*
     EWOS_CUDA_TRY(dev_alloc((void**)&dC, sizeof(float) * (size_t)M * N));
     cudaMemcpy(dA, A, sizeof(float) * (size_t)K * M, cudaMemcpyHostToDevice);
     cudaMemcpy(dB, B, sizeof(float) * (size_t)K * N, cudaMemcpyHostToDevice);
-    ewos_status s = tc_assemble(dA, dB, dC, M, N, K, nullptr, split != 0);
+    ewos_status s = tc_assemble(dA, dB, dC, M, N, K, nullptr, split != 0, nullptr);
     if (s == EWOS_OK && cudaMemcpy(C, dC, sizeof(float) * (size_t)M * N, cudaMemcpyDeviceToHost) != cudaSuccess) s = EWOS_ECUDA;
     dev_free(dA); dev_free(dB); dev_free(dC);
     cudaDeviceSynchronize();

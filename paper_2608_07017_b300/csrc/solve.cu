@@ -19,11 +19,13 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
 
 #include "sgemm.cuh"
+#include "solve_internal.hpp"
 #include "toolbox.hpp"
 
 namespace ewos {
@@ -63,6 +65,11 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b) {
     __syncthreads();
     return s_ok != 0;
 }
+
+struct TcScratch;   // mixed.cu: operand transposes of one caller
+void tc_scratch_free(TcScratch* t);
+ewos_status tc_assemble(const float* A_km, const float* B_km, float* C, int M, int N, int K, cudaStream_t st,
+                        bool split, TcScratch** owned);
 
 // ------------------------------------------------------------------ small kernels
 __global__ void coef_kernel(int n, int D, const double* __restrict__ lam, const double* __restrict__ A,
@@ -1150,162 +1157,114 @@ static ewos_status lu_factor_nopiv(float* A, int m, int lda, LuScratch& S, cudaS
     return EWOS_OK;
 }
 
-// Solve with the factors of P A = L U for nrhs right-hand sides x [nrhs][m] (in place; x arrives
-// already permuted), by 64-row steps with one grid barrier each.  Forward step j: block 0 takes
-// the rows of diagonal block j, subtracts the product of their sub-diagonal block with the segment
-// solved at step j - 1 and applies the precomputed inverse of diagonal block j; meanwhile the other
-// blocks (a warp per row) subtract the step j - 1 segment from all rows below block j.  The
-// backward sweep is the same upwards with the upper factor.  Block 0 stages the next step's two
-// 64 x 64 operands in shared memory (cp.async, double buffered) while the barrier is pending, so
-// its critical path per step is one read of the 64 updated entries plus two small products.
-constexpr int kTB = 64;
-constexpr int kTBP = kTB + 1;   // padded shared-memory row
-
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if constexpr (sizeof(T) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+// Triangular solves with the factors of P A = L U, by 64-row block steps, one launch each (no
+// grid barrier, so the sweep can be captured in a CUDA graph and several streams can solve at
+// the same time).  X [m][rc] holds rc right-hand sides per row, in place, rows in pivot order.
+// Forward step j: CTA c owns block t = j + c and subtracts the block-(j-1) segment (final since
+// step j-1); CTA 0 then applies the precomputed inverse of diagonal block j.  Backward step j:
+// t = j - c, segment j + 1, the upper inverse.
+template <typename T, bool LOWER>
+__global__ void __launch_bounds__(256) trsm_step_kernel(const T* __restrict__ LU, int lda, int m,
+                                                       const T* __restrict__ Dinv, T* __restrict__ X, int rc, int j) {
+    extern __shared__ __align__(16) unsigned char trsm_sm[];
+    T (*Ls)[65] = reinterpret_cast<T (*)[65]>(trsm_sm);
+    T (*Xs)[65] = Ls + 64;
+    T (*Xt)[65] = Xs + 64;
+    const int nbk = (m + 63) / 64;
+    const int t = LOWER ? j + (int)blockIdx.x : j - (int)blockIdx.x;
+    if (t < 0 || t >= nbk) return;
+    const int seg = LOWER ? j - 1 : j + 1;
+    const bool has_seg = seg >= 0 && seg < nbk;
+    const int r0 = t * 64, h = min(64, m - r0);
+    const int c0 = seg * 64, w = has_seg ? min(64, m - c0) : 0;
+    const int tid = threadIdx.x, i = tid & 63, rq = tid >> 6;
+    for (int q0 = 0; q0 < rc; q0 += 64) {
+        const int rw = min(64, rc - q0);
+        for (int e = tid; e < 64 * 64; e += 256) {
+            const int a = e >> 6, b = e & 63;
+            Xt[a][b] = (a < h && b < rw) ? X[(size_t)(r0 + a) * rc + q0 + b] : T(0);
+            if (has_seg) {
+                Ls[a][b] = (a < h && b < w) ? LU[(size_t)(r0 + a) * lda + c0 + b] : T(0);
+                Xs[a][b] = (a < w && b < rw) ? X[(size_t)(c0 + a) * rc + q0 + b] : T(0);
+            }
+        }
+        __syncthreads();
+        if (has_seg) {
+            for (int r = rq; r < rw; r += 4) {
+                T acc = Xt[i][r];
+#pragma unroll 16
+                for (int k = 0; k < 64; ++k) acc = fma(-Ls[i][k], Xs[k][r], acc);
+                Xt[i][r] = acc;
+            }
+            __syncthreads();
+        }
+        if (blockIdx.x == 0) {
+            const T* Di = Dinv + (size_t)t * 2 * 64 * 64 + (LOWER ? 0 : 64 * 64);
+            for (int e = tid; e < 64 * 64; e += 256) Ls[e >> 6][e & 63] = Di[e];
+            __syncthreads();
+            T y[16];
+            int cnt = 0;
+            for (int r = rq; r < rw; r += 4) {
+                T acc = T(0);
+#pragma unroll 16
+                for (int k = 0; k < 64; ++k) acc = fma(Ls[i][k], Xt[k][r], acc);
+                y[cnt++] = acc;
+            }
+            __syncthreads();
+            cnt = 0;
+            for (int r = rq; r < rw; r += 4) Xt[i][r] = y[cnt++];
+            __syncthreads();
+        }
+        for (int e = tid; e < 64 * 64; e += 256) {
+            const int a = e >> 6, b = e & 63;
+            if (a < h && b < rw) X[(size_t)(r0 + a) * rc + q0 + b] = Xt[a][b];
+        }
+        __syncthreads();
+    }
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <typename T>
-constexpr size_t lu_solve_smem() { return sizeof(T) * 2 * 2 * kTB * kTBP; }
+constexpr size_t trsm_smem() { return sizeof(T) * 3 * 64 * 65; }
 
 template <typename T>
-__global__ void __launch_bounds__(256) lu_solve_kernel(const T* __restrict__ LU, int lda, int m,
-                                                       const T* __restrict__ Dinv, double* __restrict__ x, int nrhs,
-                                                       GridBarrier* bar) {
-    extern __shared__ __align__(16) unsigned char lu_sm[];
-    T* Ls = reinterpret_cast<T*>(lu_sm);          // [2][64][65] sub-diagonal blocks
-    T* Ds = Ls + 2 * kTB * kTBP;                   // [2][64][65] diagonal-block inverses
-    __shared__ double sx[kTB], sy[kTB];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const int nblk = gridDim.x;
-    const int nbk = (m + kTB - 1) / kTB;
-    const int total_steps = 2 * nbk;   // per right-hand side: forward 0..nbk-1, backward nbk-1..0
+static cudaError_t trsm_prepare() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        err = cudaFuncSetAttribute(trsm_step_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>());
+        if (err == cudaSuccess)
+            err = cudaFuncSetAttribute(trsm_step_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>());
+    });
+    return err;
+}
 
-    // step descriptors (block 0): rows [rlo, rlo + h), segment columns [cb, cb + w), inverse index
-    auto step_desc = [&](int s, int& rlo, int& h, int& cb, int& w, const T*& D) {
-        const bool fwd = s < nbk;
-        const int j = fwd ? s : total_steps - 1 - s;
-        rlo = j * kTB;
-        h = min(kTB, m - rlo);
-        if (fwd) { cb = (j - 1) * kTB; w = j > 0 ? kTB : 0; }
-        else { cb = (j + 1) * kTB; w = j + 1 < nbk ? min(kTB, m - cb) : 0; }
-        D = Dinv + (size_t)j * 2 * kTB * kTB + (fwd ? 0 : kTB * kTB);
-    };
-    auto prefetch = [&](int s, int buf) {
-        int rlo, h, cb, w;
-        const T* D;
-        step_desc(s, rlo, h, cb, w, D);
-        T* L = Ls + buf * kTB * kTBP;
-        T* Dd = Ds + buf * kTB * kTBP;
-        for (int q = tid; q < kTB * kTB; q += blockDim.x) {
-            const int i = q >> 6, k = q & 63;
-            if (i < h && k < w) cp_async_elem(&L[i * kTBP + k], LU + (size_t)(rlo + i) * lda + cb + k);
-            else L[i * kTBP + k] = T(0);
-            cp_async_elem(&Dd[i * kTBP + k], D + q);
-        }
-        cp_async_commit();
-    };
-    // workers: xr[i] -= LU[i][cb .. cb + w) . xr[cb .. cb + w) for rows [rlo, rhi)
-    auto update_rows = [&](int cb, int w, int rlo, int rhi, int worker, int nworkers, double* xr) {
-        const int k0 = 2 * lane, k1 = 2 * lane + 1;
-        const double s0 = k0 < w ? __ldcg(xr + cb + k0) : 0.0;
-        const double s1 = k1 < w ? __ldcg(xr + cb + k1) : 0.0;
-        for (int i = rlo + worker; i < rhi; i += 4 * nworkers) {
-            double acc[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int r = i + u * nworkers;
-                acc[u] = 0.0;
-                if (r < rhi) {
-                    const T* row = LU + (size_t)r * lda + cb;
-                    acc[u] = (k0 < w ? (double)row[k0] * s0 : 0.0) + (k1 < w ? (double)row[k1] * s1 : 0.0);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
-                const int r = i + u * nworkers;
-                if (lane == 0 && r < rhi) xr[r] = __ldcg(xr + r) - acc[u];
-            }
-        }
-    };
-    const int i4 = tid >> 2, q4 = tid & 3;   // 4 threads per row for the 64 x 64 products
-    if (blockIdx.x == 0) {
-        prefetch(0, 0);
-        for (int i = tid; i < kTB; i += blockDim.x) sx[i] = 0.0;
-    }
-    for (int r = 0; r < nrhs; ++r) {
-        double* xr = x + (size_t)r * m;
-        for (int s = 0; s < total_steps; ++s) {
-            const int g = r * total_steps + s;
-            const int buf = g & 1;
-            const bool fwd = s < nbk;
-            const int j = fwd ? s : total_steps - 1 - s;
-            if (blockIdx.x == 0) {
-                int rlo, h, cb, w;
-                const T* D;
-                step_desc(s, rlo, h, cb, w, D);
-                const T* L = Ls + buf * kTB * kTBP;
-                const T* Dd = Ds + buf * kTB * kTBP;
-                double xi = 0.0;
-                if (i4 < h && q4 == 0) xi = __ldcg(xr + rlo + i4);
-                cp_async_wait_all();
-                __syncthreads();
-                // y = x[rows] - Lsub . sx   (sx is zero beyond the previous segment's width)
-                if (i4 < kTB) {
-                    double acc = 0.0;
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) acc += (double)L[i4 * kTBP + q4 * 16 + k] * sx[q4 * 16 + k];
-                    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-                    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-                    if (q4 == 0) sy[i4] = i4 < h ? xi - acc : 0.0;
-                }
-                __syncthreads();
-                // next step's operands go in while this one finishes and the barrier is pending
-                const int gn = g + 1;
-                if (gn < nrhs * total_steps) prefetch(gn % total_steps, gn & 1);
-                if (i4 < kTB) {
-                    double acc = 0.0;
-#pragma unroll
-                    for (int k = 0; k < 16; ++k) acc += (double)Dd[i4 * kTBP + q4 * 16 + k] * sy[q4 * 16 + k];
-                    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-                    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-                    if (q4 == 0) {
-                        const double v = i4 < h ? acc : 0.0;
-                        sx[i4] = v;
-                        if (i4 < h) xr[rlo + i4] = v;
-                    }
-                }
-                __syncthreads();
-                (void)j;
-            }
-            // the others subtract the segment solved at the previous step from the remaining rows
-            if (s > 0 && s != nbk) {
-                const int jp = fwd ? j - 1 : j + 1;           // segment solved at the previous step
-                const int cb = jp * kTB, w = min(kTB, m - cb);
-                int lo, hi;
-                if (fwd) { lo = (j + 1) * kTB; hi = m; }
-                else { lo = 0; hi = j * kTB; }
-                if (nblk > 1) {
-                    if (blockIdx.x > 0 && lo < hi) update_rows(cb, w, lo, hi, (blockIdx.x - 1) * nw + warp, (nblk - 1) * nw, xr);
-                } else if (lo < hi) {
-                    update_rows(cb, w, lo, hi, warp, nw, xr);
-                }
-            }
-            if (!grid_sync(bar)) {
-                if (blockIdx.x == 0) cp_async_wait_all();
-                return;
-            }
-        }
-    }
+// L U X = X (rows already in pivot order), all steps enqueued on st
+template <typename T>
+static void trsm_steps(const T* LU, int m, int lda, const T* Dinv, T* X, int rc, cudaStream_t st) {
+    const int nbk = (m + 63) / 64;
+    const size_t sm = trsm_smem<T>();
+    for (int j = 0; j < nbk; ++j)
+        ::ewos::note_launch(), trsm_step_kernel<T, true><<<j == 0 ? 1 : nbk - j, 256, sm, st>>>(LU, lda, m, Dinv, X, rc, j);
+    for (int j = nbk - 1; j >= 0; --j)
+        ::ewos::note_launch(), trsm_step_kernel<T, false><<<j == nbk - 1 ? 1 : j + 1, 256, sm, st>>>(LU, lda, m, Dinv, X, rc, j);
+}
+
+// out[i][r] = (T) x[r][perm[i]]  /  x[r][i] = out[i][r]
+template <typename T>
+__global__ void gather_cols_kernel(const double* __restrict__ x, const int* __restrict__ perm, T* __restrict__ out,
+                                   int m, int nrhs) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)m * nrhs) return;
+    const int i = (int)(t / nrhs), r = (int)(t % nrhs);
+    out[t] = (T)x[(size_t)r * m + perm[i]];
+}
+
+template <typename T>
+__global__ void scatter_cols_kernel(const T* __restrict__ in, double* __restrict__ x, int m, int nrhs) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)m * nrhs) return;
+    const int r = (int)(t / m), i = (int)(t % m);
+    x[t] = (double)in[(size_t)i * nrhs + r];
 }
 
 // ------------------------------------------------------------------ workspace
@@ -1322,6 +1281,21 @@ struct SolveWorkspace {
     // mixed precision
     float *Q32 = nullptr, *L32 = nullptr, *LU32 = nullptr, *J32 = nullptr, *Jx32 = nullptr, *P32 = nullptr;
     double *rhs = nullptr, *r = nullptr, *dx = nullptr;
+    TcScratch* tc = nullptr;
+    // all right-hand sides at once: [rows][bcap] layouts (bcap = a power-of-two bucket)
+    int64_t bcap = 0;
+    double *Sb = nullptr, *Yb = nullptr, *Vb = nullptr, *Wb = nullptr, *Fb = nullptr, *Gb = nullptr, *Ub = nullptr;
+    double *nrm = nullptr, *alpha_dev = nullptr;
+    float *D32 = nullptr, *D32p = nullptr;
+    struct Graph {
+        const void* tb;
+        int64_t rc;
+        int nl;          // number of nonlinearity coefficients (0: linear)
+        cudaGraphExec_t exec;
+        int launches;
+    };
+    std::vector<Graph> graphs;
+    cudaStream_t cap_st = nullptr;   // capture stream of the graphs
 };
 
 void free_workspace(SolveWorkspace* ws) {
@@ -1336,16 +1310,25 @@ void free_workspace(SolveWorkspace* ws) {
     ::ewos::dev_free(ws->Q32); ::ewos::dev_free(ws->L32); ::ewos::dev_free(ws->LU32); ::ewos::dev_free(ws->J32);
     ::ewos::dev_free(ws->Jx32); ::ewos::dev_free(ws->P32);
     ::ewos::dev_free(ws->rhs); ::ewos::dev_free(ws->r); ::ewos::dev_free(ws->dx);
+    tc_scratch_free(ws->tc);
+    ::ewos::dev_free(ws->Sb); ::ewos::dev_free(ws->Yb); ::ewos::dev_free(ws->Vb); ::ewos::dev_free(ws->Wb);
+    ::ewos::dev_free(ws->Fb); ::ewos::dev_free(ws->Gb); ::ewos::dev_free(ws->Ub); ::ewos::dev_free(ws->nrm);
+    ::ewos::dev_free(ws->alpha_dev); ::ewos::dev_free(ws->D32); ::ewos::dev_free(ws->D32p);
+    for (auto& g : ws->graphs) cudaGraphExecDestroy(g.exec);
+    if (ws->cap_st) cudaStreamDestroy(ws->cap_st);
     delete ws;
 }
 
-static ewos_status ensure_workspace(ewos_toolbox* tb, int64_t nrhs, bool mixed) {
-    if (tb->ws && tb->ws->cap_rhs < nrhs) { free_workspace(tb->ws); tb->ws = nullptr; }
+static ewos_status ensure_workspace(const ewos_toolbox* tb, SolveWorkspace*& slot, int64_t nrhs, bool mixed) {
+    if (slot && (slot->cap_rhs < nrhs || slot->n != tb->n || slot->m != tb->m || slot->p != tb->p || slot->D != tb->dim)) {
+        free_workspace(slot);
+        slot = nullptr;
+    }
     const int D = tb->dim, E = D + 1;
     const int64_t n = tb->n, m = tb->m, p = tb->p;
-    if (!tb->ws) {
+    if (!slot) {
         SolveWorkspace* ws = new SolveWorkspace();
-        tb->ws = ws;
+        slot = ws;
         ws->D = D; ws->n = n; ws->m = m; ws->p = p; ws->cap_rhs = nrhs;
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->M, sizeof(double) * n * E * E));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->A, sizeof(double) * n * D * D));
@@ -1379,7 +1362,7 @@ static ewos_status ensure_workspace(ewos_toolbox* tb, int64_t nrhs, bool mixed) 
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.dinv, sizeof(double) * ((m + 63) / 64) * 2 * 64 * 64));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.diag32, sizeof(float) * ((m + 63) / 64) * 64 * 64));
     }
-    SolveWorkspace* ws = tb->ws;
+    SolveWorkspace* ws = slot;
     if (!mixed && !ws->Q) {
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Q, sizeof(double) * E * n * m));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Lam, sizeof(double) * m * m));
@@ -1398,31 +1381,14 @@ static ewos_status ensure_workspace(ewos_toolbox* tb, int64_t nrhs, bool mixed) 
 
 template <typename T>
 static ewos_status lu_solve_device(const T* LU, int m, int lda, LuScratch& S, double* x, int nrhs, cudaStream_t st) {
-    int dev = 0, nsm = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int threads = 256;
-    const size_t smem = lu_solve_smem<T>();
-    EWOS_CUDA_TRY(cudaFuncSetAttribute(lu_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lu_solve_kernel<T>, threads, smem);
-    const int blocks = std::max(1, std::min(nsm, per_sm * nsm));
-    EWOS_CUDA_TRY(cudaMemsetAsync(S.bar, 0, sizeof(GridBarrier), st));
-    {
-        const int64_t cnt = (int64_t)m * nrhs;
-        ::ewos::note_launch(), gather_rows_kernel<<<(int)((cnt + 255) / 256), 256, 0, st>>>(x, S.tmp, S.perm, m, nrhs);
-        EWOS_CUDA_TRY(cudaMemcpyAsync(x, S.tmp, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, st));
-    }
-    const T* a0 = LU;
-    int lda_ = lda, m_ = m, nr = nrhs;
-    const T* di = (const T*)S.dinv;
-    GridBarrier* bar = S.bar;
-    void* args[] = {&a0, &lda_, &m_, &di, &x, &nr, &bar};
-    ::ewos::note_launch();
-        EWOS_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)lu_solve_kernel<T>, blocks, threads, args, smem, st));
-    GridBarrier hb{};
-    EWOS_CUDA_TRY(cudaMemcpyAsync(&hb, S.bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
-    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
-    if (hb.err) { set_error("LU solve: grid barrier timed out"); return EWOS_ETIMEOUT; }
+    EWOS_CUDA_TRY(trsm_prepare<T>());
+    T* X = reinterpret_cast<T*>(S.tmp);   // [m][nrhs] in the precision of the factors
+    const int64_t cnt = (int64_t)m * nrhs;
+    const int nb = (int)((cnt + 255) / 256);
+    ::ewos::note_launch(), gather_cols_kernel<T><<<nb, 256, 0, st>>>(x, S.perm, X, m, nrhs);
+    trsm_steps<T>(LU, m, lda, (const T*)S.dinv, X, nrhs, st);
+    ::ewos::note_launch(), scatter_cols_kernel<T><<<nb, 256, 0, st>>>(X, x, m, nrhs);
+    EWOS_CUDA_TRY(cudaGetLastError());
     return EWOS_OK;
 }
 
@@ -1529,10 +1495,9 @@ static double elapsed_ms(std::chrono::steady_clock::time_point t0) {
 }
 
 template <typename TP>
-static ewos_status solve_fp64(ewos_toolbox* tb, const ewos_problem* pb, double rcond, double tol, int max_iter,
+static ewos_status solve_fp64(ewos_toolbox* tb, SolveWorkspace* ws, const ewos_problem* pb, double rcond, double tol, int max_iter,
                               ewos_solve_report* rep) {
-    Ctx C{tb, tb->ws, pb->stream ? (cudaStream_t)pb->stream : tb->stream, tb->dim, tb->dim + 1, tb->n, tb->m, tb->p};
-    SolveWorkspace* ws = tb->ws;
+    Ctx C{tb, ws, pb->stream ? (cudaStream_t)pb->stream : tb->stream, tb->dim, tb->dim + 1, tb->n, tb->m, tb->p};
     const int64_t nrhs = pb->nrhs;
     auto t0 = std::chrono::steady_clock::now();
     const bool quasi = pb->nl_kind == EWOS_NL_QUASILINEAR, semi = pb->nl_kind == EWOS_NL_SEMILINEAR;
@@ -1666,8 +1631,6 @@ static ewos_status solve_fp64(ewos_toolbox* tb, const ewos_problem* pb, double r
 // the matrix-free FP64 operator (two passes over P), so iterative refinement converges to the
 // FP64 solution of the same system while the O(m^3) work runs in 32-bit.
 bool tc_assemble_available();
-ewos_status tc_assemble(const float* A_km, const float* B_km, float* C, int M, int N, int K, cudaStream_t st,
-                        bool split);
 constexpr bool kSplitTF32 = true;     // 3xTF32 assembly: Lambda to ~1e-6, fewer refinement sweeps
 
 template <typename TP>
@@ -1781,14 +1744,339 @@ static ewos_status factor32(const Ctx& C, const float* src, double alpha, int pi
         pivoting, rep);
 }
 
+// ------------------------------------------------------------------ all right-hand sides at once
+// Layouts [rows][rc]: the rc right-hand sides of one row are contiguous (rc = the request's
+// count rounded up to a power of two; the padding columns carry zeros).  The FP64 operator is
+// applied to all of them with one pass over P (FP64 FMAs, the residual's precision); the FP32
+// triangular solves run as one launch per 64-row block step (no grid barrier), so that the
+// sweep can be captured in a CUDA graph and several requests can share the GPU.
+
+// in [r][len] (r < R) -> out [len][rc] (zero columns r >= R)
+__global__ void to_cols_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t len, int R, int rc) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= len * rc) return;
+    const int64_t l = t / rc;
+    const int r = (int)(t % rc);
+    out[t] = r < R ? in[(size_t)r * len + l] : 0.0;
+}
+
+__global__ void from_cols_kernel(const double* __restrict__ in, double* __restrict__ out, int64_t len, int R, int rc) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= len * R) return;
+    const int r = (int)(t / len);
+    const int64_t l = t % len;
+    out[t] = in[l * rc + r];
+}
+
+// Vout[row][r] (+)= sum_c X[row][c] Vin[c][r]   (warp per row, 8 right-hand sides per pass)
+template <typename TP>
+__global__ void multi_rowdot_kernel(const TP* __restrict__ X, int64_t rows, int cols, const double* __restrict__ Vin,
+                                    double* __restrict__ Vout, int rc, int accumulate) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const TP* xr = X + row * cols;
+    for (int r0 = 0; r0 < rc; r0 += 8) {
+        const int rw = min(8, rc - r0);
+        double acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+        for (int c = lane; c < cols; c += 32) {
+            const double xv = (double)xr[c];
+            const double* vr = Vin + (size_t)c * rc + r0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < rw) acc[q] = fma(xv, vr[q], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        }
+        if (lane < rw) {
+            double v = acc[0];
+#pragma unroll
+            for (int q = 1; q < 8; ++q)
+                if (lane == q) v = acc[q];
+            double* o = Vout + row * rc + r0 + lane;
+            *o = accumulate ? *o + v : v;
+        }
+    }
+}
+
+// Y[c][r] += sum_{row in chunk} X[row][c] Win[row][r]   (thread per column; Y zeroed before)
+template <typename TP>
+__global__ void multi_coltrans_kernel(const TP* __restrict__ X, int64_t rows, int cols, const double* __restrict__ Win,
+                                      double* __restrict__ Y, int rc, int64_t chunk) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    const int64_t a = (int64_t)blockIdx.y * chunk;
+    const int64_t b = min(rows, a + chunk);
+    for (int r0 = 0; r0 < rc; r0 += 8) {
+        const int rw = min(8, rc - r0);
+        double acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+        for (int64_t row = a; row < b; ++row) {
+            const double xv = (double)X[row * cols + c];
+            const double* wr = Win + row * rc + r0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < rw) acc[q] = fma(xv, wr[q], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < rw) atomicAdd(&Y[(size_t)c * rc + r0 + q], acc[q]);
+    }
+}
+
+// W[e*n + i][r] = sum_k M_i[e][k] V[k*n + i][r] + [e == D] lam_i (N(u_ir) - F[i][r]),
+// u_ir = V[D*n + i][r]   (thread per (i, r))
+__global__ void formw_multi_kernel(int n, int D, const double* __restrict__ M, const double* __restrict__ V,
+                                   const double* __restrict__ lam, const double* __restrict__ F,
+                                   const double* __restrict__ nl, int nnl, double* __restrict__ W, int rc) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * rc) return;
+    const int i = (int)(t / rc), r = (int)(t % rc);
+    const int E = D + 1;
+    const double* Mi = M + (size_t)i * E * E;
+    double vi[4];
+    for (int k = 0; k < E; ++k) vi[k] = V[((size_t)k * n + i) * rc + r];
+    for (int j = 0; j < E; ++j) {
+        double acc = 0.0;
+        for (int k = 0; k < E; ++k) acc += Mi[j * E + k] * vi[k];
+        W[((size_t)j * n + i) * rc + r] = acc;
+    }
+    double extra = -F[(size_t)i * rc + r];
+    if (nl) {
+        double pw = 1.0, sv = 0.0;
+        for (int q = 0; q < nnl; ++q) { sv += nl[q] * pw; pw *= vi[D]; }
+        extra += sv;
+    }
+    W[((size_t)D * n + i) * rc + r] += lam[i] * extra;
+}
+
+__global__ void axpy_dev_kernel(int64_t count, const double* __restrict__ a, const double* __restrict__ x,
+                                double* __restrict__ y) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) y[t] += a[0] * x[t];
+}
+
+// D[i][r] = -(float) Y[perm[i]][r]   (right-hand side of the correction, rows in pivot order)
+__global__ void neg_gather32_kernel(const double* __restrict__ Y, const int* __restrict__ perm, float* __restrict__ D,
+                                    int64_t m, int rc) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m * rc) return;
+    const int64_t i = t / rc;
+    const int r = (int)(t % rc);
+    D[t] = (float)(-Y[(size_t)perm[i] * rc + r]);
+}
+
+__global__ void add_widen_kernel(int64_t count, const float* __restrict__ d, double* __restrict__ s) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) s[t] += (double)d[t];
+}
+
+// nrm[r] = sum_i Y[i][r]^2  (nrm zeroed before)
+__global__ void colsumsq_kernel(const double* __restrict__ Y, int64_t m, int rc, double* __restrict__ nrm) {
+    const int r = blockIdx.y;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = Y[i * rc + r];
+        acc += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&nrm[r], acc);
+}
+
+__global__ void set_scalar_kernel(double* __restrict__ out, double v) {
+    if (threadIdx.x == 0) out[0] = v;
+}
+
+__global__ void alpha_from_sumsq_kernel(const double* __restrict__ sumsq, double rcond, double* __restrict__ alpha) {
+    if (threadIdx.x == 0) alpha[0] = rcond * sqrt(sumsq[0]);
+}
+
+__global__ void add_diag_dev_kernel(float* __restrict__ A, int m, int lda, const double* __restrict__ alpha) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) A[(size_t)i * lda + i] += (float)alpha[0];
+}
+
+static int64_t bucket_of(int64_t R) {
+    int64_t b = 1;
+    while (b < R) b <<= 1;
+    return b;
+}
+
+size_t workspace_bytes(const ewos_toolbox* tb, int64_t nrhs, bool mixed) {
+    const size_t n = (size_t)tb->n, m = (size_t)tb->m, p = (size_t)tb->p, E = (size_t)tb->dim + 1;
+    const size_t rc = (size_t)bucket_of(std::max<int64_t>(1, nrhs));
+    size_t b = 8 * (n * E * E + n * E * E + n * (E + 1) + (n + p + 5 * m) * nrhs + 4 * E * n + 3 * m);   // vectors
+    b += 8 * ((m + 63) / 64) * 2 * 64 * 64 + 4 * ((m + 63) / 64) * 64 * 64 + 16 * m;                  // LU side
+    if (mixed) {
+        const size_t Kp = (E * n + 31) / 32 * 32;
+        b += 4 * (E * n * m + 3 * m * m + n * m);                 // Q32, L32, LU32, Jx32
+        b += 4 * 4 * std::max(m, m) * Kp;                          // TF32 hi/lo transposes
+        if (tb->precision == 64) b += 4 * E * n * m;               // FP32 copy of P
+        b += 8 * rc * (2 * m + 2 * E * n + 2 * n + p + 1) + 8 * rc * m;   // batched columns
+    } else {
+        b += 8 * (E * n * m + 2 * m * m + n * m);                  // Q, Lambda, LU, Jx
+    }
+    return b;
+}
+
+static ewos_status ensure_batched(const Ctx& C, int64_t rc) {
+    SolveWorkspace* ws = C.ws;
+    if (ws->bcap >= rc && ws->Sb) return EWOS_OK;
+    for (auto& g : ws->graphs) cudaGraphExecDestroy(g.exec);
+    ws->graphs.clear();
+    ::ewos::dev_free(ws->Sb); ::ewos::dev_free(ws->Yb); ::ewos::dev_free(ws->Vb); ::ewos::dev_free(ws->Wb);
+    ::ewos::dev_free(ws->Fb); ::ewos::dev_free(ws->Gb); ::ewos::dev_free(ws->Ub); ::ewos::dev_free(ws->nrm);
+    ::ewos::dev_free(ws->D32); ::ewos::dev_free(ws->D32p);
+    const int64_t rows = (int64_t)C.E * C.n;
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Sb, sizeof(double) * C.m * rc));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Yb, sizeof(double) * C.m * rc));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Vb, sizeof(double) * rows * rc));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Wb, sizeof(double) * rows * rc));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Fb, sizeof(double) * C.n * rc));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Gb, sizeof(double) * C.p * rc));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Ub, sizeof(double) * C.n * rc));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->nrm, sizeof(double) * rc));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->D32, sizeof(float) * C.m * rc));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->D32p, sizeof(float) * C.m * rc));
+    if (!ws->alpha_dev) EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->alpha_dev, sizeof(double)));
+    ws->bcap = rc;
+    return EWOS_OK;
+}
+
+static int nblocks(int64_t count, int tpb = 256) { return (int)std::max<int64_t>(1, (count + tpb - 1) / tpb); }
+
+// Yb = R(Sb) + alpha Sb for all columns (f, g of the request in Fb, Gb; nl may be NULL)
+template <typename TP>
+static void residual_multi(const Ctx& C, int64_t rc, int R, const double* nl, int nnl) {
+    SolveWorkspace* ws = C.ws;
+    const TP* P = (const TP*)C.tb->P;
+    const TP* KH = (const TP*)C.tb->KH;
+    const int64_t rows = (int64_t)C.E * C.n;
+    const int rb = nblocks(rows * 32);
+    ::ewos::note_launch(), multi_rowdot_kernel<TP><<<rb, 256, 0, C.st>>>(P, rows, (int)C.m, ws->Sb, ws->Vb, (int)rc, 0);
+    ::ewos::note_launch(), multi_rowdot_kernel<TP><<<rb, 256, 0, C.st>>>(KH, rows, (int)C.p, ws->Gb, ws->Vb, (int)rc, 1);
+    (void)R;   // padding columns are processed like the others (zero data); graphs depend on rc only
+    ::ewos::note_launch(), formw_multi_kernel<<<nblocks(C.n * rc, 128), 128, 0, C.st>>>(
+        (int)C.n, C.D, ws->M, ws->Vb, C.tb->lambda, ws->Fb, nl, nnl, ws->Wb, (int)rc);
+    cudaMemsetAsync(ws->Yb, 0, sizeof(double) * C.m * rc, C.st);
+    const int64_t chunk = 512;
+    dim3 grid((unsigned)((C.m + 127) / 128), (unsigned)((rows + chunk - 1) / chunk));
+    ::ewos::note_launch(), multi_coltrans_kernel<TP><<<grid, 128, 0, C.st>>>(P, rows, (int)C.m, ws->Wb, ws->Yb, (int)rc, chunk);
+    ::ewos::note_launch(), axpy_dev_kernel<<<nblocks(C.m * rc), 256, 0, C.st>>>(C.m * rc, ws->alpha_dev, ws->Sb, ws->Yb);
+}
+
+static void colnorms(const Ctx& C, int64_t rc) {
+    cudaMemsetAsync(C.ws->nrm, 0, sizeof(double) * rc, C.st);
+    dim3 g((unsigned)std::min<int64_t>(64, (C.m + 255) / 256), (unsigned)rc);
+    ::ewos::note_launch(), colsumsq_kernel<<<g, 256, 0, C.st>>>(C.ws->Yb, C.m, (int)rc, C.ws->nrm);
+}
+
+// One sweep: correction from the FP32 factors for every column, s += correction, new residual
+// and its column norms.  Launch count returned for the launch counter of graph replays.
+template <typename TP>
+static int sweep_multi(const Ctx& C, int64_t rc, int R, const double* nl, int nnl) {
+    SolveWorkspace* ws = C.ws;
+    const unsigned long long l0 = ewos_launch_count();
+    const int m = (int)C.m;
+    ::ewos::note_launch(), neg_gather32_kernel<<<nblocks(C.m * rc), 256, 0, C.st>>>(ws->Yb, ws->lu.perm, ws->D32, C.m, (int)rc);
+    trsm_steps<float>(ws->LU32, m, m, (const float*)ws->lu.dinv, ws->D32, (int)rc, C.st);
+    ::ewos::note_launch(), add_widen_kernel<<<nblocks(C.m * rc), 256, 0, C.st>>>(C.m * rc, ws->D32, ws->Sb);
+    residual_multi<TP>(C, rc, R, nl, nnl);
+    colnorms(C, rc);
+    return (int)(ewos_launch_count() - l0);
+}
+
+// Batched refinement (linear) or chord iteration (semilinear) for the R right-hand sides of the
+// request on factors already in LU32; returns false (nothing reported) when it does not reach
+// tol so that the caller takes the per-right-hand-side path.
+template <typename TP>
+static ewos_status solve_batched(const Ctx& C, int R, const double* nl, int nnl, double tol, int max_sweeps,
+                                 int* sweeps, bool* ok, double* final_rel) {
+    SolveWorkspace* ws = C.ws;
+    const int64_t rc = bucket_of(R);
+    *ok = false;
+    ewos_status s = ensure_batched(C, rc);
+    if (s != EWOS_OK) return s;
+    ::ewos::note_launch(), to_cols_kernel<<<nblocks(C.n * rc), 256, 0, C.st>>>(ws->f, ws->Fb, C.n, R, (int)rc);
+    ::ewos::note_launch(), to_cols_kernel<<<nblocks(C.p * rc), 256, 0, C.st>>>(ws->g, ws->Gb, C.p, R, (int)rc);
+    EWOS_CUDA_TRY(cudaMemsetAsync(ws->Sb, 0, sizeof(double) * C.m * rc, C.st));
+    residual_multi<TP>(C, rc, R, nl, nnl);
+    colnorms(C, rc);
+    std::vector<double> r0(rc), rk(rc);
+    EWOS_CUDA_TRY(cudaMemcpyAsync(r0.data(), ws->nrm, sizeof(double) * rc, cudaMemcpyDeviceToHost, C.st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(C.st));
+    // the sweep as a CUDA graph, captured once per (workspace, toolbox, bucket, nonlinearity)
+    const int nlk = nl ? nnl : 0;
+    SolveWorkspace::Graph* gr = nullptr;
+    for (auto& g : ws->graphs)
+        if (g.tb == C.tb && g.rc == rc && g.nl == nlk) gr = &g;
+    EWOS_CUDA_TRY(trsm_prepare<float>());
+    if (!gr) {
+        // captured on the workspace's own stream (the caller's may be the legacy default stream,
+        // which cannot be captured); the graph is then launched on the caller's stream
+        if (!ws->cap_st) EWOS_CUDA_TRY(cudaStreamCreateWithFlags(&ws->cap_st, cudaStreamNonBlocking));
+        Ctx Cc = C;
+        Cc.st = ws->cap_st;
+        cudaGraph_t graph = nullptr;
+        EWOS_CUDA_TRY(cudaStreamBeginCapture(Cc.st, cudaStreamCaptureModeThreadLocal));
+        const int launches = sweep_multi<TP>(Cc, rc, R, nl, nnl);
+        cudaError_t e = cudaStreamEndCapture(Cc.st, &graph);
+        if (e != cudaSuccess) { set_error(std::string("graph capture: ") + cudaGetErrorString(e)); return EWOS_ECUDA; }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { set_error(std::string("graph instantiate: ") + cudaGetErrorString(e)); return EWOS_ECUDA; }
+        ws->graphs.push_back(SolveWorkspace::Graph{C.tb, rc, nlk, exec, launches});
+        gr = &ws->graphs.back();
+    }
+    double worst = 1.0;
+    int it = 0;
+    while (it < max_sweeps) {
+        EWOS_CUDA_TRY(cudaGraphLaunch(gr->exec, C.st));
+        for (int q = 0; q < gr->launches; ++q) ::ewos::note_launch();
+        ++it;
+        EWOS_CUDA_TRY(cudaMemcpyAsync(rk.data(), ws->nrm, sizeof(double) * rc, cudaMemcpyDeviceToHost, C.st));
+        EWOS_CUDA_TRY(cudaStreamSynchronize(C.st));
+        worst = 0.0;
+        bool bad = false;
+        for (int r = 0; r < R; ++r) {
+            const double rel = r0[r] > 0 ? std::sqrt(rk[r] / r0[r]) : 0.0;
+            if (!(rel == rel) || rel > 1e3) bad = true;
+            worst = std::max(worst, rel);
+        }
+        if (bad) break;
+        if (worst <= tol) break;
+    }
+    *sweeps += it;
+    if (final_rel) *final_rel = worst;
+    *ok = worst <= tol;
+    if (!*ok) return EWOS_OK;
+    // s and u = G s + H g for every column
+    ::ewos::note_launch(), from_cols_kernel<<<nblocks(C.m * R), 256, 0, C.st>>>(ws->Sb, ws->s, C.m, R, (int)rc);
+    const TP* Gm = (const TP*)C.tb->P + (size_t)C.D * C.n * C.m;
+    const TP* Hm = (const TP*)C.tb->KH + (size_t)C.D * C.n * C.p;
+    const int rb = nblocks(C.n * 32);
+    ::ewos::note_launch(), multi_rowdot_kernel<TP><<<rb, 256, 0, C.st>>>(Gm, C.n, (int)C.m, ws->Sb, ws->Ub, (int)rc, 0);
+    ::ewos::note_launch(), multi_rowdot_kernel<TP><<<rb, 256, 0, C.st>>>(Hm, C.n, (int)C.p, ws->Gb, ws->Ub, (int)rc, 1);
+    ::ewos::note_launch(), from_cols_kernel<<<nblocks(C.n * R), 256, 0, C.st>>>(ws->Ub, ws->u, C.n, R, (int)rc);
+    return EWOS_OK;
+}
+
 constexpr double kRefineTol = 1e-10;
 constexpr int kRefineMax = 40;
+constexpr int kChordMax = 80;    // chord sweeps before the semilinear batch falls back to Newton
 
 template <typename TP>
-static ewos_status solve_mixed_t(ewos_toolbox* tb, const ewos_problem* pb, double rcond, double tol, int max_iter,
-                                 ewos_solve_report* rep) {
-    Ctx C{tb, tb->ws, pb->stream ? (cudaStream_t)pb->stream : tb->stream, tb->dim, tb->dim + 1, tb->n, tb->m, tb->p};
-    SolveWorkspace* ws = tb->ws;
+static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewos_problem* pb, double rcond, double tol, int max_iter,
+                                 ewos_solve_report* rep, const SolveOptions& opt) {
+    Ctx C{tb, ws, pb->stream ? (cudaStream_t)pb->stream : tb->stream, tb->dim, tb->dim + 1, tb->n, tb->m, tb->p};
     const int64_t nrhs = pb->nrhs;
     auto t0 = std::chrono::steady_clock::now();
     const bool quasi = pb->nl_kind == EWOS_NL_QUASILINEAR, semi = pb->nl_kind == EWOS_NL_SEMILINEAR;
@@ -1801,12 +2089,13 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, const ewos_problem* pb, doubl
     rep->converged = 1;
     int sweeps = 0;
     double rel = 0.0;
+    bool u_done = false;
     if (!quasi) {
         auto ta = std::chrono::steady_clock::now();
         if (tc_assemble_available()) {
             dim3 g((unsigned)((C.m + 255) / 256), (unsigned)C.n);
             ::ewos::note_launch(), formQ_kernel<float, float><<<g, 256, 0, C.st>>>(P32, ws->M, ws->Q32, (int)C.n, (int)C.m, C.D);
-            ewos_status st = tc_assemble(P32, ws->Q32, ws->L32, (int)C.m, (int)C.m, (int)(C.E * C.n), C.st, kSplitTF32);
+            ewos_status st = tc_assemble(P32, ws->Q32, ws->L32, (int)C.m, (int)C.m, (int)(C.E * C.n), C.st, kSplitTF32, &ws->tc);
             if (st != EWOS_OK) return st;
         } else {
             assemble_mixed<TP>(C, P32);
@@ -1814,7 +2103,33 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, const ewos_problem* pb, doubl
         const double alpha = rcond * frob32(C, ws->L32, C.m * C.m);
         rep->alpha = alpha;
         rep->ms_assemble = elapsed_ms(ta);
-        if (!semi) {
+        bool batched_done = false;
+        if (opt.batched) {
+            // one factorisation of Lambda + alpha I; all right-hand sides refined together
+            // (linear) or the chord iteration on R(s) + alpha s = 0 (semilinear)
+            auto t1 = std::chrono::steady_clock::now();
+            ewos_status st = factor32(C, ws->L32, alpha, pb->pivoting, rep);
+            if (st != EWOS_OK) return st;
+            rep->ms_factor = elapsed_ms(t1);
+            auto t2 = std::chrono::steady_clock::now();
+            EWOS_CUDA_TRY(cudaMemsetAsync(ws->scal, 0, sizeof(double), C.st));
+            st = ensure_batched(C, bucket_of(nrhs));
+            if (st != EWOS_OK) return st;
+            ::ewos::note_launch(), set_scalar_kernel<<<1, 32, 0, C.st>>>(ws->alpha_dev, alpha);
+            bool ok = false;
+            double rel = 0.0;
+            st = solve_batched<TP>(C, (int)nrhs, semi ? ws->nl : nullptr, semi ? pb->nl_ncoef : 0,
+                                   semi ? tol : kRefineTol, semi ? kChordMax : kRefineMax, &sweeps, &ok, &rel);
+            if (st != EWOS_OK) return st;
+            rep->ms_solve = elapsed_ms(t2);
+            if (ok) {
+                batched_done = true;
+                u_done = true;
+                rep->iters = semi ? sweeps : 1;
+            }
+        }
+        if (batched_done) {
+        } else if (!semi) {
             auto t1 = std::chrono::steady_clock::now();
             ewos_status st = factor32(C, ws->L32, alpha, pb->pivoting, rep);
             if (st != EWOS_OK) return st;
@@ -1894,7 +2209,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, const ewos_problem* pb, doubl
                 if (tc_assemble_available()) {
                     dim3 gq((unsigned)((C.m + 255) / 256), (unsigned)C.n);
                     ::ewos::note_launch(), formQ_kernel<float, float><<<gq, 256, 0, C.st>>>(P32, ws->M, ws->Q32, (int)C.n, (int)C.m, C.D);
-                    ewos_status st = tc_assemble(P32, ws->Q32, ws->L32, (int)C.m, (int)C.m, (int)(C.E * C.n), C.st, kSplitTF32);
+                    ewos_status st = tc_assemble(P32, ws->Q32, ws->L32, (int)C.m, (int)C.m, (int)(C.E * C.n), C.st, kSplitTF32, &ws->tc);
                     if (st != EWOS_OK) return st;
                 } else {
                     assemble_mixed<TP>(C, P32);
@@ -1927,8 +2242,9 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, const ewos_problem* pb, doubl
             if (!conv) rep->converged = 0;
         }
     }
-    for (int64_t r = 0; r < nrhs; ++r)
-        u_from_s(C, tb->P, tb->KH, tb->precision == 64, ws->s + r * C.m, ws->g + r * C.p, ws->u + r * C.n);
+    if (!u_done)
+        for (int64_t r = 0; r < nrhs; ++r)
+            u_from_s(C, tb->P, tb->KH, tb->precision == 64, ws->s + r * C.m, ws->g + r * C.p, ws->u + r * C.n);
     if (!quasi) {
         const int64_t r = nrhs - 1;
         residual<TP>(C, ws->s + r * C.m, ws->g + r * C.p, ws->f + r * C.n, semi ? ws->nl : nullptr,
@@ -1942,18 +2258,21 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, const ewos_problem* pb, doubl
     return rep->converged ? EWOS_OK : EWOS_ENOCONV;
 }
 
-ewos_status solve_mixed(ewos_toolbox* tb, const ewos_problem* pb, double rcond, double tol, int max_iter,
-                        ewos_solve_report* rep) {
-    return tb->precision == 64 ? solve_mixed_t<double>(tb, pb, rcond, tol, max_iter, rep)
-                               : solve_mixed_t<float>(tb, pb, rcond, tol, max_iter, rep);
+ewos_status solve_mixed(ewos_toolbox* tb, SolveWorkspace* ws, const ewos_problem* pb, double rcond, double tol,
+                        int max_iter, ewos_solve_report* rep, const SolveOptions& opt) {
+    return tb->precision == 64 ? solve_mixed_t<double>(tb, ws, pb, rcond, tol, max_iter, rep, opt)
+                               : solve_mixed_t<float>(tb, ws, pb, rcond, tol, max_iter, rep, opt);
 }
 
 }  // namespace ewos
 
 using namespace ewos;
 
-extern "C" ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, double* u_out, double* s_out,
-                                  int outputs_on_device, ewos_solve_report* rep_out) {
+namespace ewos {
+
+// One solve on a given workspace (the toolbox's own for ewos_solve, a server slot's otherwise).
+ewos_status solve_on(ewos_toolbox* tb, SolveWorkspace*& wslot, const ewos_problem* pb, double* u_out, double* s_out,
+                     int outputs_on_device, ewos_solve_report* rep_out, const SolveOptions& opt) {
     if (!tb || !pb || !u_out || !pb->A || !pb->f || !pb->g || pb->nrhs < 1) {
         set_error("ewos_solve: need toolbox, problem with A, f, g, nrhs >= 1, and u_out");
         return EWOS_EINVAL;
@@ -1965,9 +2284,9 @@ extern "C" ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, doub
     if (pb->mode != EWOS_SOLVE_FP64 && pb->mode != EWOS_SOLVE_MIXED) { set_error("ewos_solve: unknown mode"); return EWOS_EINVAL; }
     cudaStream_t st = pb->stream ? (cudaStream_t)pb->stream : tb->stream;
     AllocStream as(st);
-    ewos_status s = ensure_workspace(tb, pb->nrhs, pb->mode == EWOS_SOLVE_MIXED);
+    ewos_status s = ensure_workspace(tb, wslot, pb->nrhs, pb->mode == EWOS_SOLVE_MIXED);
     if (s != EWOS_OK) return s;
-    SolveWorkspace* ws = tb->ws;
+    SolveWorkspace* ws = wslot;
     const cudaMemcpyKind k = pb->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     const int D = tb->dim;
     EWOS_CUDA_TRY(cudaMemcpyAsync(ws->A, pb->A, sizeof(double) * tb->n * D * D, k, st));
@@ -1982,10 +2301,10 @@ extern "C" ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, doub
     const int max_iter = pb->max_iter > 0 ? pb->max_iter : (pb->nl_kind == EWOS_NL_QUASILINEAR ? 100 : 30);
     ewos_solve_report rep{};
     if (pb->mode == EWOS_SOLVE_FP64)
-        s = tb->precision == 64 ? solve_fp64<double>(tb, pb, rcond, tol, max_iter, &rep)
-                                : solve_fp64<float>(tb, pb, rcond, tol, max_iter, &rep);
+        s = tb->precision == 64 ? solve_fp64<double>(tb, ws, pb, rcond, tol, max_iter, &rep)
+                                : solve_fp64<float>(tb, ws, pb, rcond, tol, max_iter, &rep);
     else
-        s = solve_mixed(tb, pb, rcond, tol, max_iter, &rep);
+        s = solve_mixed(tb, ws, pb, rcond, tol, max_iter, &rep, opt);
     if (s != EWOS_OK && s != EWOS_ENOCONV) return s;
     const cudaMemcpyKind ko = outputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     EWOS_CUDA_TRY(cudaMemcpyAsync(u_out, ws->u, sizeof(double) * tb->n * pb->nrhs, ko, st));
@@ -1993,4 +2312,17 @@ extern "C" ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, doub
     EWOS_CUDA_TRY(cudaStreamSynchronize(st));
     if (rep_out) *rep_out = rep;
     return s;
+}
+
+}  // namespace ewos
+
+extern "C" ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, double* u_out, double* s_out,
+                                  int outputs_on_device, ewos_solve_report* rep_out) {
+    if (!tb) {
+        set_error("ewos_solve: need a toolbox");
+        return EWOS_EINVAL;
+    }
+    ewos::SolveOptions opt;
+    opt.batched = pb && pb->batched != 0;
+    return ewos::solve_on(tb, tb->ws, pb, u_out, s_out, outputs_on_device, rep_out, opt);
 }

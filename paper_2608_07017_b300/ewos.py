@@ -59,7 +59,8 @@ class _Problem(ctypes.Structure):
                 ("g", ctypes.c_void_p), ("nrhs", ctypes.c_int64), ("nl_kind", ctypes.c_int),
                 ("nl_coef", ctypes.c_void_p), ("nl_ncoef", ctypes.c_int), ("mode", ctypes.c_int),
                 ("rcond", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
-                ("inputs_on_device", ctypes.c_int), ("stream", ctypes.c_void_p), ("pivoting", ctypes.c_int)]
+                ("inputs_on_device", ctypes.c_int), ("stream", ctypes.c_void_p), ("pivoting", ctypes.c_int),
+                ("batched", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
@@ -67,6 +68,28 @@ class SolveReport(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("residual", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_assemble", ctypes.c_double), ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double),
                 ("factorizations", ctypes.c_int), ("pivoted_factorizations", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int), ("memory_fraction", ctypes.c_double), ("reserve_bytes", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("queued", ctypes.c_int), ("active", ctypes.c_int), ("peak_active", ctypes.c_int), ("slots", ctypes.c_int),
+                ("budget_bytes", ctypes.c_int64), ("charged_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class RequestTiming(ctypes.Structure):
+    _fields_ = [("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("slot", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -98,9 +121,17 @@ def lib():
         L.ewos_debug_philox.argtypes = [P, P, P, I64]
         L.ewos_debug_green_radius.argtypes = [P, P, I64, I]
         L.ewos_debug_tc_gemm.argtypes = [P, P, P, I, I, I, I]
+        L.ewos_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(P)]
+        L.ewos_server_submit.argtypes = [P, P, ctypes.POINTER(_Problem), ctypes.POINTER(ctypes.c_uint64)]
+        L.ewos_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_double, P, P, ctypes.POINTER(SolveReport),
+                                       ctypes.POINTER(RequestTiming)]
+        L.ewos_server_query.argtypes = [P, ctypes.POINTER(ServerStats)]
+        L.ewos_server_destroy.argtypes = [P]
+        L.ewos_server_destroy.restype = None
         for fn in ("ewos_toolbox_build", "ewos_toolbox_build_noalloc", "ewos_toolbox_from_host", "ewos_toolbox_get", "ewos_toolbox_report",
                    "ewos_toolbox_shape", "ewos_solve", "ewos_debug_philox", "ewos_debug_green_radius",
-                   "ewos_debug_tc_gemm"):
+                   "ewos_debug_tc_gemm", "ewos_server_create", "ewos_server_submit", "ewos_server_wait",
+                   "ewos_server_query"):
             getattr(L, fn).restype = I
         _lib = L
     return _lib
@@ -172,9 +203,10 @@ class Toolbox:
         return dict(G=self.get("G"), gradG=self.get("gradG"), H=self.get("H"), gradH=self.get("gradH"))
 
     def solve(self, A, f, g, b=None, c=None, kind="linear", coef=None, mode="fp64", rcond=-1.0, tol=0.0,
-              max_iter=0, want_s=False, on_device=False, out=None, stream=None, pivoting=0):
+              max_iter=0, want_s=False, on_device=False, out=None, stream=None, pivoting=0, batched=False):
         """Solve the problem of include/ewos.h; returns (u [nrhs][n] or [n], s or None, report).
-        pivoting=1 forces row interchanges in the mixed-mode LU."""
+        pivoting=1 forces row interchanges in the mixed-mode LU; batched=True refines all
+        right-hand sides together (mixed mode; chord iteration for semilinear problems)."""
         if on_device:
             Ad, fd, gd, bd, cd = A, f, g, b, c
             nrhs = f.shape[0] if f.dim() == 2 else 1
@@ -184,7 +216,7 @@ class Toolbox:
         cf = _f64(coef) if coef is not None else None
         pb = _Problem(_ptr(Ad), _ptr(bd), _ptr(cd), _ptr(fd), _ptr(gd), nrhs, NL[kind], _ptr(cf),
                       0 if cf is None else cf.size, MODE[mode], float(rcond), float(tol), int(max_iter),
-                      1 if on_device else 0, stream, int(pivoting))
+                      1 if on_device else 0, stream, int(pivoting), 1 if batched else 0)
         if out is not None:
             u = out
             optr = out.data_ptr()
@@ -289,3 +321,62 @@ def debug_green_radius(u, precision=32):
     R = np.zeros_like(uu)
     _check(lib().ewos_debug_green_radius(uu.ctypes.data, R.ctypes.data, uu.size, precision), "green radius")
     return R
+
+
+class Server:
+    """Request server of include/ewos.h (ewos_server_*): submit() queues a solve on a resident
+    toolbox and returns a ticket; wait() returns (u, s, report, timing)."""
+
+    def __init__(self, max_slots=4, memory_fraction=0.8, reserve_bytes=0, budget_bytes=0):
+        o = ServerOpts(int(max_slots), float(memory_fraction), int(reserve_bytes), int(budget_bytes))
+        h = ctypes.c_void_p()
+        _check(lib().ewos_server_create(ctypes.byref(o), ctypes.byref(h)), "server create")
+        self._h = h
+        self._pending = {}
+
+    def submit(self, tb, A, f, g, b=None, c=None, kind="linear", coef=None, mode="mixed", rcond=-1.0, tol=0.0,
+               max_iter=0, pivoting=0):
+        Ad, fd, gd, bd, cd = _f64(A), _f64(f), _f64(g), _f64(b), _f64(c)
+        nrhs = fd.shape[0] if fd.ndim == 2 else 1
+        cf = _f64(coef) if coef is not None else None
+        pb = _Problem(_ptr(Ad), _ptr(bd), _ptr(cd), _ptr(fd), _ptr(gd), nrhs, NL[kind], _ptr(cf),
+                      0 if cf is None else cf.size, MODE[mode], float(rcond), float(tol), int(max_iter), 0, None,
+                      int(pivoting), 1)
+        t = ctypes.c_uint64()
+        _check(lib().ewos_server_submit(self._h, tb._h, ctypes.byref(pb), ctypes.byref(t)), "server submit")
+        self._pending[t.value] = (tb.n, tb.m, nrhs, fd.ndim == 1)
+        return t.value
+
+    def wait(self, ticket, timeout_s=0.0, want_s=False):
+        n, m, nrhs, single = self._pending.pop(ticket)
+        u = np.zeros((nrhs, n))
+        s = np.zeros((nrhs, m)) if want_s else None
+        rep = SolveReport()
+        tm = RequestTiming()
+        st = lib().ewos_server_wait(self._h, ctypes.c_uint64(ticket), float(timeout_s), u.ctypes.data, _ptr(s),
+                                    ctypes.byref(rep), ctypes.byref(tm))
+        if st == ETIMEOUT:
+            self._pending[ticket] = (n, m, nrhs, single)
+        _check(st, "server wait", allow=(OK, ENOCONV))
+        r = rep.as_dict()
+        r["status"] = st
+        if single:
+            u = u[0]
+            s = None if s is None else s[0]
+        return u, s, r, tm.as_dict()
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().ewos_server_query(self._h, ctypes.byref(st)), "server query")
+        return st.as_dict()
+
+    def close(self):
+        if self._h:
+            lib().ewos_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

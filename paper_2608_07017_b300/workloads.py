@@ -334,3 +334,95 @@ def stars(count=32, nmin=256, nmax=4096, walks=2000, eps=1e-4, seed=2, problem=T
 
 
 WORKLOADS = {"disk400": disk400, "square4096": square4096, "ball8000": ball8000}
+
+
+# ------------------------------------------------------------------ serving requests
+# Random coefficient fields and manufactured solutions for the request server (no counterpart in
+# the paper's experiments).  A = I + S(x), S symmetric, each of its d(d+1)/2 entries a sum of 8
+# modes a_k cos(w_k . x) or a_k sin(w_k . x) with a_k ~ U(-0.3, 0.3)/8 and w_k ~ U(-pi, pi)^d,
+# redrawn until the smallest eigenvalue of A at every node is at least 0.2; b ~ U(-1, 1)^d
+# (constant); each right-hand side is a manufactured u* = sum_j c_j phi_j over a fixed basis
+# (1, x_i, x_i x_j, sin(pi x_0), cos(pi x_1), exp(x_0 / 2)) with c_j ~ U(-1, 1)/sqrt(#basis);
+# f = -div(A grad u*) + b . grad u* (+ u*^3 for semilinear requests), g = u* on the boundary.
+
+_BASIS_CACHE = {}
+
+
+def _basis(dim):
+    if dim in _BASIS_CACHE:
+        return _BASIS_CACHE[dim]
+    import sympy as sp
+    xs = sp.symbols("x0:%d" % dim)
+    exprs = [sp.Integer(1)] + list(xs) + [xs[i] * xs[j] for i in range(dim) for j in range(i, dim)]
+    exprs += [sp.sin(sp.pi * xs[0]), sp.cos(sp.pi * xs[1]), sp.exp(xs[0] / 2)]
+    fns = []
+    for e in exprs:
+        grad = [sp.diff(e, v) for v in xs]
+        hess = [[sp.diff(e, a, b) for b in xs] for a in xs]
+        lam = lambda q: sp.lambdify(xs, q, "numpy")
+        fns.append((lam(e), [lam(g) for g in grad], [[lam(h) for h in row] for row in hess]))
+    _BASIS_CACHE[dim] = fns
+    return fns
+
+
+def _ev(fn, P):
+    return np.broadcast_to(np.asarray(fn(*[P[:, k] for k in range(P.shape[1])]), dtype=np.float64),
+                           (P.shape[0],)).astype(np.float64)
+
+
+def random_field(x, rng, modes=8, return_spec=False):
+    """(A [n][d][d], dA [n][d][d][d] with dA[:, l, i, j] = d_l A_ij) of one random field (and the
+    modes (i, j, a, w, kind) when return_spec)."""
+    n, dim = x.shape
+    while True:
+        A = np.tile(np.eye(dim), (n, 1, 1))
+        dA = np.zeros((n, dim, dim, dim))
+        spec = []
+        for i in range(dim):
+            for j in range(i, dim):
+                a = rng.uniform(-0.3, 0.3, modes) / modes
+                w = rng.uniform(-np.pi, np.pi, (modes, dim))
+                kind = rng.integers(0, 2, modes)
+                spec.append((i, j, a, w, kind))
+                ph = x @ w.T                                    # [n][modes]
+                val = np.where(kind == 0, np.cos(ph), np.sin(ph)) @ a
+                der = np.where(kind == 0, -np.sin(ph), np.cos(ph))   # d/d(phase)
+                A[:, i, j] += val
+                if i != j:
+                    A[:, j, i] += val
+                for l in range(dim):
+                    dl = der @ (a * w[:, l])
+                    dA[:, l, i, j] += dl
+                    if i != j:
+                        dA[:, l, j, i] += dl
+        if np.linalg.eigvalsh(A).min() >= 0.2:
+            return (A, dA, spec) if return_spec else (A, dA)
+
+
+def serving_requests(x, z, count, seed=3, nrhs_max=64, p_semilinear=0.5, nrhs=None):
+    """count requests: dicts with A, b, f [R][n], g [R][p], u_star [R][n], kind, coef."""
+    n, dim = x.shape
+    rng = np.random.default_rng(seed)
+    B = _basis(dim)
+    nb = len(B)
+    phi_x = np.stack([_ev(f, x) for f, _, _ in B])                                  # [nb][n]
+    phi_z = np.stack([_ev(f, z) for f, _, _ in B])                                  # [nb][p]
+    grad = np.stack([np.stack([_ev(g, x) for g in gr], 1) for _, gr, _ in B])        # [nb][n][d]
+    hess = np.stack([np.stack([np.stack([_ev(h, x) for h in row], 1) for row in he], 1) for _, _, he in B])
+    out = []
+    for _ in range(count):
+        A, dA = random_field(x, rng)
+        b = np.tile(rng.uniform(-1, 1, dim), (n, 1))
+        # L phi_j = -(sum_ij d_i A_ij d_j phi + A_ij d_ij phi) + b . grad phi
+        divA = np.einsum("niij->nj", dA)                                            # sum_i d_i A_ij
+        Lphi = -(np.einsum("nj,bnj->bn", divA, grad) + np.einsum("nij,bnij->bn", A, hess)) \
+            + np.einsum("nj,bnj->bn", b, grad)
+        R = int(nrhs) if nrhs is not None else int(np.exp(rng.uniform(0, np.log(nrhs_max + 1))))
+        R = max(1, min(nrhs_max, R))
+        C = rng.uniform(-1, 1, (R, nb)) / np.sqrt(nb)
+        us = C @ phi_x
+        semi = rng.uniform() < p_semilinear
+        f = C @ Lphi + (us ** 3 if semi else 0.0)
+        out.append(dict(A=A, b=b, f=f, g=C @ phi_z, u_star=us, kind="semilinear" if semi else "linear",
+                        coef=[0.0, 0.0, 0.0, 1.0] if semi else None))
+    return out
