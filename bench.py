@@ -153,6 +153,82 @@ def run_reference(args):
     return 0
 
 
+def _stream(sv, items, rate, rng, mode, one_rhs=False):
+    """Submits items [(toolbox, request, lam)] at Poisson arrival times; returns per-request
+    (latency ms, rhs count, lambda-weighted RMS error vs u*) and the makespan."""
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(items)))
+    t0 = time.perf_counter()
+    tickets = []
+    for (tb, q, lam), ta in zip(items, arrivals):
+        dt = t0 + ta - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        f, g = (q["f"][:1], q["g"][:1]) if one_rhs else (q["f"], q["g"])
+        tickets.append(sv.submit(tb, q["A"], f, g, b=q["b"], kind=q["kind"], coef=q["coef"], mode=mode))
+    out = []
+    for (tb, q, lam), t in zip(items, tickets):
+        u, _, rep, tm = sv.wait(t)
+        U = u.reshape(-1, tb.n)
+        us = q["u_star"][:U.shape[0]]
+        err = float(np.mean(np.sqrt((lam[None, :] * (U - us) ** 2).sum(1))))
+        out.append((tm["total_ms"], U.shape[0], err, rep["iters"]))
+    return out, time.perf_counter() - t0
+
+
+def _summary(res, makespan):
+    lat = sorted(r[0] for r in res)
+    rhs = sum(r[1] for r in res)
+    return {"requests": len(res), "rhs": rhs, "p50_ms": lat[len(lat) // 2],
+            "p99_ms": lat[min(len(lat) - 1, int(np.ceil(0.99 * len(lat))) - 1)],
+            "solves_per_s": rhs / makespan, "requests_per_s": len(res) / makespan,
+            "mean_l2_error_vs_u_star": float(np.mean([r[2] for r in res]))}
+
+
+def serve_streams(args, w, xd, zd, sp):
+    from paper_2608_07017_b300 import ewos
+    from paper_2608_07017_b300 import workloads as W
+    wb = W.ball8000(problem=False)
+    tbs = {"square4096": (ewos.build_toolbox("box", 2, w.domain.params, xd, zd, w.walks, w.eps, seed=w.seed,
+                                             precision=32, cell_weights=w.lam, stream=sp, on_device=True), w),
+           "ball8000": (ewos.build_workload(wb, stream=sp), wb)}
+    rng = np.random.default_rng(3)
+    items = []
+    for name, (tb, wk) in tbs.items():
+        lam = tb.get("lambda")
+        for q in W.serving_requests(wk.x, wk.z, args.serve_requests, seed=3 if name == "square4096" else 4):
+            items.append((tb, q, lam, name))
+    order = rng.permutation(len(items))
+    items = [items[i] for i in order]
+    res = {"arrival_rate_per_s": args.serve_rate, "slots": 4,
+           "stream": f"{len(items)} requests over the square4096 and ball8000 toolboxes, 1-64 right-hand sides "
+                     "(log-uniform), linear or semilinear (u^3) 50/50, random fields A = I + S(x)"}
+    sv = ewos.Server(max_slots=4)
+    # warm-up: one request per toolbox and kind (workspaces, graphs)
+    warm = [it for it in items if it[1]["kind"] == "linear"][:2] + [it for it in items if it[1]["kind"] != "linear"][:2]
+    _stream(sv, [(tb, q, lam) for tb, q, lam, _ in warm], 1e6, np.random.default_rng(0), "mixed")
+    out, mk = _stream(sv, [(tb, q, lam) for tb, q, lam, _ in items], args.serve_rate, np.random.default_rng(5), "mixed")
+    res["mixed"] = _summary(out, mk)
+    res["mixed"]["stats"] = sv.stats()
+    # the same first requests of the stream, first right-hand side only, both paths
+    sample = []
+    for name in tbs:
+        sample += [it for it in items if it[3] == name][:args.serve_fp64 if name == "square4096" else 2]
+    sample = [(tb, q, lam) for tb, q, lam, _ in sample]
+    out, mk = _stream(sv, sample, args.serve_rate, np.random.default_rng(6), "mixed", one_rhs=True)
+    res["mixed_on_fp64_sample"] = _summary(out, mk)
+    sv.close()
+    if args.serve_fp64 > 0:
+        sv = ewos.Server(max_slots=4)
+        out, mk = _stream(sv, sample, args.serve_rate, np.random.default_rng(6), "fp64", one_rhs=True)
+        res["fp64_sample"] = _summary(out, mk)
+        sv.close()
+        res["sample"] = (f"first {args.serve_fp64} square4096 and 2 ball8000 requests of the stream, first right-hand "
+                         "side only, same arrival process, mixed and FP64 paths")
+    for tb, _ in tbs.values():
+        tb.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -160,7 +236,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--serve-solves", type=int, default=10)
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="requests per toolbox in the served stream (0: skip serving)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-fp64", type=int, default=6, help="requests of the FP64 sample per toolbox")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -236,30 +315,9 @@ def main():
         torch.distributed.all_reduce(st)
         steps_total = int(st.item())
 
-    # served solves on one resident toolbox: mixed precision vs the plain FP64 GPU path
-    tbs = ewos.build_toolbox("box", 2, w.domain.params, xd, zd, w.walks, w.eps, seed=w.seed, precision=32,
-                             cell_weights=w.lam, stream=sp, on_device=True)
-    lam = tbs.get("lambda")
-    served = {}
-    for mode, count in (("mixed", args.serve_solves), ("fp64", min(3, args.serve_solves))):
-        if count <= 0:
-            continue
-        tbs.solve(Ad, fd, gd, b=bd, mode=mode, on_device=True, out=ud, stream=sp)      # workspace warm-up
-        lat = []
-        for _ in range(count):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            _, _, rep = tbs.solve(Ad, fd, gd, b=bd, mode=mode, on_device=True, out=ud, stream=sp)
-            torch.cuda.synchronize()
-            lat.append(1000 * (time.perf_counter() - t0))
-        u_m = ud.cpu().numpy()
-        err = float(np.sqrt(np.sum(lam * (u_m - pb.u_star) ** 2)))
-        lat.sort()
-        served[mode] = {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                        "solves_per_s": 1000.0 / statistics.mean(lat), "l2_error_vs_u_star": err,
-                        "refine_sweeps": rep["refine_iters"], "alpha": rep["alpha"], "solves": count,
-                        "ms_assemble": rep["ms_assemble"], "ms_factor": rep["ms_factor"], "ms_refine": rep["ms_solve"]}
-    tbs.close()
+    # served solves: Poisson request stream on the resident square and ball toolboxes, mixed
+    # precision (full stream) vs the plain FP64 GPU path (a bounded sample of the same stream)
+    served = serve_streams(args, w, xd, zd, sp) if args.serve_requests > 0 else {}
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e_ms = []

@@ -196,10 +196,10 @@ typedef struct {
     int max_iter;             /* <= 0 -> 30 (Newton) / 100 (Picard)                       */
     int inputs_on_device;     /* 1 -> A, b, c, f, g are device pointers                    */
     void* stream;             /* NULL -> the toolbox's stream                              */
-    int pivoting;             /* mixed mode: 0 -> LU with the diagonal pivots, kept only when
-                                 every multiplier has |l| <= 1 (then it is the partial-pivoting
+    int pivoting;             /* 0 -> LU with the diagonal pivots, kept only when every
+                                 multiplier has |l| <= 1 (then it is the partial-pivoting
                                  factorisation) and otherwise redone with row interchanges;
-                                 1 -> always partial pivoting.  FP64 mode always pivots.     */
+                                 1 -> always partial pivoting.  Both modes.                   */
     int batched;              /* mixed mode: 1 -> all right-hand sides refined together, one
                                  CUDA-graph launch per sweep; a semilinear problem then runs the
                                  chord iteration s <- s - (Lambda + alpha I)^-1 (R(s) + alpha s)

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -38,6 +39,7 @@ struct ServerRequest {
     std::vector<double> u, s;
     ewos_solve_report rep{};
     ewos_status status = EWOS_OK;
+    std::string err;
     bool done = false;
     int slot = -1;
     double t_submit = 0, t_start = 0, t_end = 0;
@@ -84,6 +86,7 @@ static void run_request(ewos_server* sv, ServerSlot* sl, ServerRequest* rq) {
     rq->u.assign((size_t)rq->tb->n * pb.nrhs, 0.0);
     rq->s.assign((size_t)rq->tb->m * pb.nrhs, 0.0);
     rq->status = solve_on(rq->tb, sl->ws, &pb, rq->u.data(), rq->s.data(), 0, &rq->rep, opt);
+    if (rq->status != EWOS_OK) rq->err = ewos_last_error();   // the worker's message, for the waiter
 }
 
 static bool slot_fits(const ServerSlot* sl, const ServerRequest* rq) {
@@ -161,6 +164,7 @@ static void worker(ewos_server* sv, ServerSlot* sl) {
                         sv->queue.pop_front();
                         if (a < 0) {
                             front->status = EWOS_ENOMEM;
+                            front->err = "ewos_server: the request's workspace does not fit in the memory budget";
                             front->done = true;
                             front->t_start = front->t_end = now_ms();
                             ++sv->failed;
@@ -313,6 +317,7 @@ extern "C" ewos_status ewos_server_wait(ewos_server* sv, uint64_t ticket, double
         tm->slot = rq->slot;
     }
     const ewos_status st = rq->status;
+    if (st != EWOS_OK) set_error(rq->err);
     delete rq;
     return st;
 }

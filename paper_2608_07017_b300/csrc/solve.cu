@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <string>
 #include <type_traits>
@@ -36,7 +37,7 @@ struct GridBarrier {
     unsigned int gen;
     int err;
     int singular;
-    int maxl_bits;    // largest |multiplier| of an unpivoted factorisation (float bits)
+    unsigned long long maxl_bits;   // largest |multiplier| of an unpivoted factorisation (double bits)
 };
 
 constexpr long long kSpinLimit = 1ll << 24;   // about 10 s of L2 polling
@@ -868,7 +869,7 @@ struct LuScratch {
     int* swp = nullptr;         // [2 * 128 + 1] composed interchanges of one panel
     double* tmp = nullptr;      // [m * nrhs] permuted right-hand sides
     void* dinv = nullptr;       // [nbk][2][64][64] inverses of the diagonal blocks (T)
-    float* diag32 = nullptr;    // [nbk][64][64] factored diagonal blocks of the unpivoted path
+    void* diagb = nullptr;      // [nbk][64][64] factored diagonal blocks of the unpivoted path (T)
     int panel_blocks = 0;
 };
 
@@ -1016,50 +1017,91 @@ static ewos_status lu_factor_device(T* A, int m, int lda, LuScratch& S, cudaStre
 constexpr int kNpThreads = 256;
 constexpr int kNpLd = kNB + 4;   // 16-byte aligned rows; a warp's 32 columns hit distinct banks
 
-__device__ __forceinline__ void atomic_max_pos(int* bits, float v) {
-    // non-negative floats (and NaN, as a large pattern) order like their bit patterns
-    atomicMax(bits, __float_as_int(v));
-}
+template <typename T>
+constexpr size_t nopiv_smem() { return sizeof(T) * (kNB * kNpLd + kNB * kNB + kNB); }
 
-__global__ void __launch_bounds__(kNpThreads) lu_panel_nopiv_kernel(float* __restrict__ A, int lda, int m, int kb,
-                                                                    int nb, float* __restrict__ diag_out,
+// y[c] -= x * row[c] for c > j (row 16-byte aligned in shared memory)
+template <int J>
+__device__ __forceinline__ void axpy_tail(float (&y)[kNB], float x, const float* row) {
+    const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+    for (int t = (J + 1) / 4; t < kNB / 4; ++t) {
+        const float4 u = r4[t];
+        if (4 * t > J) y[4 * t] = fmaf(-x, u.x, y[4 * t]);
+        if (4 * t + 1 > J) y[4 * t + 1] = fmaf(-x, u.y, y[4 * t + 1]);
+        if (4 * t + 2 > J) y[4 * t + 2] = fmaf(-x, u.z, y[4 * t + 2]);
+        if (4 * t + 3 > J) y[4 * t + 3] = fmaf(-x, u.w, y[4 * t + 3]);
+    }
+}
+template <int J>
+__device__ __forceinline__ void axpy_tail(double (&y)[kNB], double x, const double* row) {
+    const double2* r2 = reinterpret_cast<const double2*>(row);
+#pragma unroll
+    for (int t = (J + 1) / 2; t < kNB / 2; ++t) {
+        const double2 u = r2[t];
+        if (2 * t > J) y[2 * t] = fma(-x, u.x, y[2 * t]);
+        if (2 * t + 1 > J) y[2 * t + 1] = fma(-x, u.y, y[2 * t + 1]);
+    }
+}
+template <typename T, int J>
+struct TailLoop {
+    __device__ __forceinline__ static void fwd(T (&x)[kNB], const T* D, const T* rU) {   // x U = a
+        x[J] *= rU[J];
+        axpy_tail<J>(x, x[J], D + J * kNpLd);
+        TailLoop<T, J + 1>::fwd(x, D, rU);
+    }
+    __device__ __forceinline__ static void low(T (&y)[kNB], const T* Lt) {               // L y = a (unit)
+        axpy_tail<J>(y, y[J], Lt + J * kNB);
+        TailLoop<T, J + 1>::low(y, Lt);
+    }
+};
+template <typename T>
+struct TailLoop<T, kNB> {
+    __device__ __forceinline__ static void fwd(T (&)[kNB], const T*, const T*) {}
+    __device__ __forceinline__ static void low(T (&)[kNB], const T*) {}
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kNpThreads) lu_panel_nopiv_kernel(T* __restrict__ A, int lda, int m, int kb, int nb,
+                                                                    T* __restrict__ diag_out,
                                                                     GridBarrier* __restrict__ bar) {
-    __shared__ __align__(16) float D[kNB][kNpLd];     // diagonal block: L below, U on and above
-    __shared__ __align__(16) float Lt[kNB][kNB];      // Lt[k][i] = L_ik (i > k), else 0
-    __shared__ __align__(16) float rU[kNB];
+    extern __shared__ __align__(16) unsigned char np_sm[];
+    T* D = reinterpret_cast<T*>(np_sm);            // [64][kNpLd] diagonal block: L below, U on and above
+    T* Lt = D + kNB * kNpLd;                       // [64][64] Lt[k][i] = L_ik (i > k), else 0
+    T* rU = Lt + kNB * kNB;                        // [64] reciprocal pivots
     const int tid = threadIdx.x, c = tid & (kNB - 1), q = tid >> 6;   // 4 threads per column
     constexpr int kQ = kNpThreads / kNB;
-    float mx = 0.f;
+    double mx = 0.0;
     int zero = 0;
     // identity beyond nb
     for (int i = q; i < kNB; i += kQ)
-        D[i][c] = (i < nb && c < nb) ? A[(size_t)(kb + i) * lda + kb + c] : (i == c ? 1.f : 0.f);
+        D[i * kNpLd + c] = (i < nb && c < nb) ? A[(size_t)(kb + i) * lda + kb + c] : (i == c ? T(1) : T(0));
     __syncthreads();
     // right-looking elimination, multipliers formed on the fly; column j is scaled at the end
     for (int j = 0; j < kNB; ++j) {
-        const float piv = D[j][j];
-        const float r = piv != 0.f ? 1.f / piv : 0.f;
-        if (tid == 0) { rU[j] = r; zero |= piv == 0.f; }
+        const T piv = D[j * kNpLd + j];
+        const T r = piv != T(0) ? T(1) / piv : T(0);
+        if (tid == 0) { rU[j] = r; zero |= piv == T(0); }
         if (c > j) {
-            const float u = D[j][c] * r;
-            for (int i = j + 1 + q; i < kNB; i += kQ) D[i][c] = fmaf(-D[i][j], u, D[i][c]);
+            const T u = D[j * kNpLd + c] * r;
+            for (int i = j + 1 + q; i < kNB; i += kQ) D[i * kNpLd + c] = fma(-D[i * kNpLd + j], u, D[i * kNpLd + c]);
         }
         __syncthreads();
     }
     for (int i = c + 1 + q; i < kNB; i += kQ) {
-        const float l = D[i][c] * rU[c];
-        D[i][c] = l;
-        mx = fmaxf(mx, fabsf(l));
+        const T l = D[i * kNpLd + c] * rU[c];
+        D[i * kNpLd + c] = l;
+        mx = fmax(mx, fabs((double)l));
     }
     __syncthreads();
     for (int t = tid; t < kNB * kNB; t += kNpThreads) {
         const int k = t >> 6, i = t & 63;
-        Lt[k][i] = i > k ? D[i][k] : 0.f;
+        Lt[k * kNB + i] = i > k ? D[i * kNpLd + k] : T(0);
     }
     const int rest = m - kb - nb;
     const int nbl = (rest + kNpThreads - 1) / kNpThreads;
     if (blockIdx.x == 0) {
-        for (int t = tid; t < nb * nb; t += kNpThreads) diag_out[t] = D[t / nb][t % nb];
+        for (int t = tid; t < nb * nb; t += kNpThreads) diag_out[t] = D[(t / nb) * kNpLd + t % nb];
         if (zero) bar->singular = 1;
     }
     __syncthreads();
@@ -1067,61 +1109,40 @@ __global__ void __launch_bounds__(kNpThreads) lu_panel_nopiv_kernel(float* __res
         // L21 rows: x U11 = a  (nb == 64 whenever rows remain below the block)
         const int i = kb + nb + blockIdx.x * kNpThreads + tid;
         if (i < m) {
-            float x[kNB];
-            const float* src = A + (size_t)i * lda + kb;
+            T x[kNB];
+            const T* src = A + (size_t)i * lda + kb;
 #pragma unroll
             for (int cc = 0; cc < kNB; ++cc) x[cc] = src[cc];
-#pragma unroll
-            for (int j = 0; j < kNB; ++j) {
-                x[j] *= rU[j];
-                const float4* u4 = reinterpret_cast<const float4*>(&D[j][0]);
-#pragma unroll
-                for (int t = (j + 1) / 4; t < kNB / 4; ++t) {
-                    const float4 u = u4[t];
-                    if (4 * t > j) x[4 * t] = fmaf(-x[j], u.x, x[4 * t]);
-                    if (4 * t + 1 > j) x[4 * t + 1] = fmaf(-x[j], u.y, x[4 * t + 1]);
-                    if (4 * t + 2 > j) x[4 * t + 2] = fmaf(-x[j], u.z, x[4 * t + 2]);
-                    if (4 * t + 3 > j) x[4 * t + 3] = fmaf(-x[j], u.w, x[4 * t + 3]);
-                }
-            }
-            float* dst = A + (size_t)i * lda + kb;
+            TailLoop<T, 0>::fwd(x, D, rU);
+            T* dst = A + (size_t)i * lda + kb;
 #pragma unroll
             for (int cc = 0; cc < kNB; ++cc) {
                 dst[cc] = x[cc];
-                mx = fmaxf(mx, fabsf(x[cc]));
+                mx = fmax(mx, fabs((double)x[cc]));
             }
         }
     } else if (rest > 0 && blockIdx.x < 2 * nbl) {
         // U12 columns: L11 y = a  (unit lower)
         const int col = kb + nb + (blockIdx.x - nbl) * kNpThreads + tid;
         if (col < m) {
-            float y[kNB];
+            T y[kNB];
 #pragma unroll
             for (int r = 0; r < kNB; ++r) y[r] = A[(size_t)(kb + r) * lda + col];
-#pragma unroll
-            for (int k = 0; k < kNB; ++k) {
-                const float4* l4 = reinterpret_cast<const float4*>(&Lt[k][0]);
-#pragma unroll
-                for (int t = (k + 1) / 4; t < kNB / 4; ++t) {
-                    const float4 l = l4[t];
-                    if (4 * t > k) y[4 * t] = fmaf(-l.x, y[k], y[4 * t]);
-                    if (4 * t + 1 > k) y[4 * t + 1] = fmaf(-l.y, y[k], y[4 * t + 1]);
-                    if (4 * t + 2 > k) y[4 * t + 2] = fmaf(-l.z, y[k], y[4 * t + 2]);
-                    if (4 * t + 3 > k) y[4 * t + 3] = fmaf(-l.w, y[k], y[4 * t + 3]);
-                }
-            }
+            TailLoop<T, 0>::low(y, Lt);
 #pragma unroll
             for (int r = 0; r < kNB; ++r) A[(size_t)(kb + r) * lda + col] = y[r];
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((tid & 31) == 0 && mx > 0.f) atomic_max_pos(&bar->maxl_bits, mx);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    // non-negative doubles (and NaN, as a large pattern) order like their bit patterns
+    if ((tid & 31) == 0 && mx > 0.0) atomicMax(&bar->maxl_bits, (unsigned long long)__double_as_longlong(mx));
 }
 
-__global__ void diag_writeback_kernel(float* __restrict__ A, int lda, int m, const float* __restrict__ diag) {
+template <typename T>
+__global__ void diag_writeback_kernel(T* __restrict__ A, int lda, int m, const T* __restrict__ diag) {
     const int t = blockIdx.x, kb = t * kNB, nb = min(kNB, m - kb);
-    const float* d = diag + (size_t)t * kNB * kNB;
+    const T* d = diag + (size_t)t * kNB * kNB;
     for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) A[(size_t)(kb + q / nb) * lda + kb + q % nb] = d[q];
 }
 
@@ -1132,28 +1153,40 @@ __global__ void iota_kernel(int* __restrict__ v, int m) {
 
 // Returns EWOS_OK with *accepted false when a multiplier exceeds 1 or a pivot is zero (the
 // caller then refactors the original matrix with interchanges).
-static ewos_status lu_factor_nopiv(float* A, int m, int lda, LuScratch& S, cudaStream_t st, bool* accepted) {
+template <typename T>
+static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStream_t st, bool* accepted) {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(lu_panel_nopiv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)nopiv_smem<T>());
+    });
+    EWOS_CUDA_TRY(attr);
     EWOS_CUDA_TRY(cudaMemsetAsync(S.bar, 0, sizeof(GridBarrier), st));
+    T* diagb = reinterpret_cast<T*>(S.diagb);
     for (int kb = 0; kb < m; kb += kNB) {
         const int nb = std::min(kNB, m - kb);
         const int rest = m - kb - nb;
         const int nbl = (rest + kNpThreads - 1) / kNpThreads;
-        ::ewos::note_launch(), lu_panel_nopiv_kernel<<<std::max(1, 2 * nbl), kNpThreads, 0, st>>>(
-            A, lda, m, kb, nb, S.diag32 + (size_t)(kb / kNB) * kNB * kNB, S.bar);
+        ::ewos::note_launch(), lu_panel_nopiv_kernel<T><<<std::max(1, 2 * nbl), kNpThreads, nopiv_smem<T>(), st>>>(
+            A, lda, m, kb, nb, diagb + (size_t)(kb / kNB) * kNB * kNB, S.bar);
         if (rest > 0)
-            gemm_trailing<float>(st, rest, rest, nb, A + (size_t)(kb + nb) * lda + kb, lda,
-                                 A + (size_t)kb * lda + kb + nb, lda, A + (size_t)(kb + nb) * lda + kb + nb, lda);
+            gemm_trailing<T>(st, rest, rest, nb, A + (size_t)(kb + nb) * lda + kb, lda,
+                             A + (size_t)kb * lda + kb + nb, lda, A + (size_t)(kb + nb) * lda + kb + nb, lda);
     }
     const int nbk = (m + kNB - 1) / kNB;
-    ::ewos::note_launch(), diag_writeback_kernel<<<nbk, 256, 0, st>>>(A, lda, m, S.diag32);
+    ::ewos::note_launch(), diag_writeback_kernel<T><<<nbk, 256, 0, st>>>(A, lda, m, diagb);
     ::ewos::note_launch(), iota_kernel<<<(m + 255) / 256, 256, 0, st>>>(S.ipiv, m);
     ::ewos::note_launch(), iota_kernel<<<(m + 255) / 256, 256, 0, st>>>(S.perm, m);
-    ::ewos::note_launch(), diag_inverse_kernel<float><<<nbk, 64, 0, st>>>(A, lda, m, (float*)S.dinv);
+    ::ewos::note_launch(), diag_inverse_kernel<T><<<nbk, 64, 0, st>>>(A, lda, m, (T*)S.dinv);
     GridBarrier hb{};
     EWOS_CUDA_TRY(cudaMemcpyAsync(&hb, S.bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
     EWOS_CUDA_TRY(cudaStreamSynchronize(st));
     EWOS_CUDA_TRY(cudaGetLastError());
-    *accepted = !hb.singular && hb.maxl_bits <= __builtin_bit_cast(int, 1.0f);
+    const double one = 1.0;
+    unsigned long long one_bits;
+    memcpy(&one_bits, &one, sizeof(one));
+    *accepted = !hb.singular && hb.maxl_bits <= one_bits;
     return EWOS_OK;
 }
 
@@ -1306,7 +1339,7 @@ void free_workspace(SolveWorkspace* ws) {
     ::ewos::dev_free(ws->scal); ::ewos::dev_free(ws->umax);
     ::ewos::dev_free(ws->lu.pub); ::ewos::dev_free(ws->lu.bar); ::ewos::dev_free(ws->lu.ipiv);
     ::ewos::dev_free(ws->lu.perm); ::ewos::dev_free(ws->lu.swp); ::ewos::dev_free(ws->lu.tmp);
-    ::ewos::dev_free(ws->lu.dinv); ::ewos::dev_free(ws->lu.diag32);
+    ::ewos::dev_free(ws->lu.dinv); ::ewos::dev_free(ws->lu.diagb);
     ::ewos::dev_free(ws->Q32); ::ewos::dev_free(ws->L32); ::ewos::dev_free(ws->LU32); ::ewos::dev_free(ws->J32);
     ::ewos::dev_free(ws->Jx32); ::ewos::dev_free(ws->P32);
     ::ewos::dev_free(ws->rhs); ::ewos::dev_free(ws->r); ::ewos::dev_free(ws->dx);
@@ -1360,7 +1393,7 @@ static ewos_status ensure_workspace(const ewos_toolbox* tb, SolveWorkspace*& slo
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.swp, sizeof(int) * 260));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.tmp, sizeof(double) * m * nrhs));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.dinv, sizeof(double) * ((m + 63) / 64) * 2 * 64 * 64));
-        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.diag32, sizeof(float) * ((m + 63) / 64) * 64 * 64));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.diagb, sizeof(double) * ((m + 63) / 64) * 64 * 64));
     }
     SolveWorkspace* ws = slot;
     if (!mixed && !ws->Q) {
@@ -1474,15 +1507,30 @@ static double frob_shift(const Ctx& C, double rcond) {
     return rcond * norm2(C, C.ws->Lam, C.m * C.m);
 }
 
+// LU <- Lambda (+ G^T extra) + alpha I, factorised in place: with the diagonal pivots when that
+// equals partial pivoting (pivoting == 0), else rebuilt and factored with row interchanges.
 template <typename TP>
-static ewos_status factor_shifted(const Ctx& C, double alpha, const double* extra_gemm_B) {
-    // LU <- Lambda (+ G^T extra) + alpha I, factorised in place
-    cudaMemcpyAsync(C.ws->LUm, C.ws->Lam, sizeof(double) * C.m * C.m, cudaMemcpyDeviceToDevice, C.st);
-    if (extra_gemm_B) {
-        const TP* Gm = (const TP*)C.tb->P + (size_t)C.D * C.n * C.m;
-        gemm64<TP, true>(C.st, (int)C.m, (int)C.m, (int)C.n, 1.0, Gm, C.m, extra_gemm_B, C.m, 1.0, C.ws->LUm, C.m);
+static ewos_status factor_shifted(const Ctx& C, double alpha, const double* extra_gemm_B, int pivoting,
+                                  ewos_solve_report* rep) {
+    auto build = [&] {
+        cudaMemcpyAsync(C.ws->LUm, C.ws->Lam, sizeof(double) * C.m * C.m, cudaMemcpyDeviceToDevice, C.st);
+        if (extra_gemm_B) {
+            const TP* Gm = (const TP*)C.tb->P + (size_t)C.D * C.n * C.m;
+            gemm64<TP, true>(C.st, (int)C.m, (int)C.m, (int)C.n, 1.0, Gm, C.m, extra_gemm_B, C.m, 1.0, C.ws->LUm, C.m);
+        }
+        ::ewos::note_launch(), add_diag_kernel<double><<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.ws->LUm, (int)C.m,
+                                                                                                (int)C.m, alpha);
+    };
+    build();
+    ++rep->factorizations;
+    if (pivoting == 0) {
+        bool accepted = false;
+        ewos_status s = lu_factor_nopiv<double>(C.ws->LUm, (int)C.m, (int)C.m, C.ws->lu, C.st, &accepted);
+        if (s != EWOS_OK) return s;
+        if (accepted) return EWOS_OK;
+        build();
     }
-    ::ewos::note_launch(), add_diag_kernel<double><<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.ws->LUm, (int)C.m, (int)C.m, alpha);
+    ++rep->pivoted_factorizations;
     bool sing = false;
     ewos_status s = lu_factor_device<double>(C.ws->LUm, (int)C.m, (int)C.m, C.ws->lu, C.st, &sing);
     if (s != EWOS_OK) return s;
@@ -1512,8 +1560,7 @@ static ewos_status solve_fp64(ewos_toolbox* tb, SolveWorkspace* ws, const ewos_p
         rep->ms_assemble = elapsed_ms(t0);
         if (!semi) {
             auto t1 = std::chrono::steady_clock::now();
-            ++rep->factorizations, ++rep->pivoted_factorizations;
-            ewos_status s = factor_shifted<TP>(C, alpha, nullptr);
+            ewos_status s = factor_shifted<TP>(C, alpha, nullptr, pb->pivoting, rep);
             if (s != EWOS_OK) return s;
             rep->ms_factor = elapsed_ms(t1);
             auto t2 = std::chrono::steady_clock::now();
@@ -1546,8 +1593,7 @@ static ewos_status solve_fp64(ewos_toolbox* tb, SolveWorkspace* ws, const ewos_p
                     const TP* Gm = (const TP*)tb->P + (size_t)C.D * C.n * C.m;
                     ::ewos::note_launch(), jac_scale_kernel<TP><<<gj, 256, 0, C.st>>>(Gm, ws->u2, tb->lambda, nl, pb->nl_ncoef, ws->Jx, (int)C.n, (int)C.m);
                     auto t1 = std::chrono::steady_clock::now();
-                    ++rep->factorizations, ++rep->pivoted_factorizations;
-            ewos_status st = factor_shifted<TP>(C, alpha, ws->Jx);
+                    ewos_status st = factor_shifted<TP>(C, alpha, ws->Jx, pb->pivoting, rep);
                     if (st != EWOS_OK) return st;
                     rep->ms_factor += elapsed_ms(t1);
                     cudaMemcpyAsync(ws->x, ws->y, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
@@ -1583,8 +1629,7 @@ static ewos_status solve_fp64(ewos_toolbox* tb, SolveWorkspace* ws, const ewos_p
                 rep->alpha = alpha;
                 rep->ms_assemble += elapsed_ms(ta);
                 auto t1 = std::chrono::steady_clock::now();
-                ++rep->factorizations, ++rep->pivoted_factorizations;
-            ewos_status st = factor_shifted<TP>(C, alpha, nullptr);
+                ewos_status st = factor_shifted<TP>(C, alpha, nullptr, pb->pivoting, rep);
                 if (st != EWOS_OK) return st;
                 rep->ms_factor += elapsed_ms(t1);
                 residual<TP>(C, nullptr, g, f, nullptr, 0, 0.0, ws->y);
@@ -1720,7 +1765,7 @@ static ewos_status factor32_with(const Ctx& C, Build build, int pivoting, ewos_s
     ++rep->factorizations;
     if (pivoting == 0) {
         bool accepted = false;
-        ewos_status s = lu_factor_nopiv(C.ws->LU32, (int)C.m, (int)C.m, C.ws->lu, C.st, &accepted);
+        ewos_status s = lu_factor_nopiv<float>(C.ws->LU32, (int)C.m, (int)C.m, C.ws->lu, C.st, &accepted);
         if (s != EWOS_OK) return s;
         if (accepted) return EWOS_OK;
         build();

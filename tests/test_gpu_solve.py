@@ -247,15 +247,25 @@ def _random_toolbox(seed, n_drop=0):
     return x, z, tb, lam, A, b, f, g
 
 
-def test_mixed_falls_back_to_interchanges():
+@pytest.mark.parametrize("mode", ["mixed", "fp64"])
+def test_falls_back_to_interchanges(mode):
     x, z, tb, lam, A, b, f, g = _random_toolbox(5)
     gtb = ewos.toolbox_from_host(2, x, z, tb["G"], tb["gradG"], tb["H"], tb["gradH"], lam, precision=64)
-    u, s, rep = gtb.solve(A, f, g, b=b, mode="mixed", want_s=True)
+    u, s, rep = gtb.solve(A, f, g, b=b, mode=mode, want_s=True)
     gtb.close()
     assert rep["converged"]
     assert rep["factorizations"] == 1 and rep["pivoted_factorizations"] == 1
-    ref = S.solve_linear(tb, lam, A, b, None, f, g, alpha=rep["alpha"])
+    ref = S.solve_linear(tb, lam, A, b, None, f, g, alpha=rep["alpha"] if mode == "mixed" else None)
     assert _rel(u, ref["u"]) < 1e-9
+
+
+def test_fp64_unpivoted_accepted(disk):
+    w, tb, lam, gtb = disk
+    pb = w.problem
+    u0, _, r0 = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, c=pb.c)
+    u1, _, r1 = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, c=pb.c, pivoting=1)
+    assert r0["pivoted_factorizations"] == 0 and r1["pivoted_factorizations"] == 1
+    assert _rel(u0, u1) < 1e-11
 
 
 @pytest.mark.parametrize("k,per", [(11, 3), (8, 2), (1, 1)])
