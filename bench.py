@@ -229,6 +229,38 @@ def serve_streams(args, w, xd, zd, sp):
     return res
 
 
+def batched_build():
+    """stars32 (32 star polygons, 64 edges, n log-uniform in [256, 4096], p = n/8, 2000 walks,
+    eps 1e-4): one batched launch against 32 single builds of the same toolboxes."""
+    from paper_2608_07017_b300 import ewos
+    from paper_2608_07017_b300 import workloads as W
+    ws = W.stars(problem=False)
+    args = ([("polygon", 2, w.domain.params) for w in ws], [w.x for w in ws], [w.z for w in ws], ws[0].walks, ws[0].eps)
+    tbs, rep, _ = ewos.build_batch(*args, seed=0)          # autotuner + warm-up
+    for tb in tbs:
+        tb.close()
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tbs, rep, _ = ewos.build_batch(*args, seed=0)
+    wall = 1000 * (time.perf_counter() - t0)
+    for tb in tbs:
+        tb.close()
+    t0 = time.perf_counter()
+    walk_single = 0.0
+    for k, w in enumerate(ws):
+        tb = ewos.build_toolbox("polygon", 2, w.domain.params, w.x, w.z, w.walks, w.eps, seed=0, instance=k)
+        walk_single += tb.report()["ms_walk"]
+        tb.close()
+    wall_single = 1000 * (time.perf_counter() - t0)
+    return {"workload": "stars32: 32 star polygons (64 edges, radius 1+0.2cos(k theta), k in 3..7), n log-uniform "
+                        f"in [256, 4096] (total {sum(w.x.shape[0] for w in ws)}), p = n/8, 2000 walks/node, eps 1e-4, FP32",
+            "walks": rep["walks"], "wos_steps": rep["steps"], "walk_kernel_ms": rep["ms_walk"],
+            "wos_steps_per_s": rep["steps"] / (rep["ms_walk"] / 1000.0), "build_ms": wall,
+            "single_builds_ms": wall_single, "single_walk_kernels_ms": walk_single,
+            "launch": {k: rep[k] for k in ("threads_per_block", "ctas_per_sm", "grid", "smem_bytes")}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -241,6 +273,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serve-fp64", type=int, default=6, help="requests of the FP64 sample per toolbox")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched-build", type=int, default=1, help="1: also time the 32-instance star batch")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -319,6 +352,9 @@ def main():
     # precision (full stream) vs the plain FP64 GPU path (a bounded sample of the same stream)
     served = serve_streams(args, w, xd, zd, sp) if args.serve_requests > 0 else {}
 
+    # many toolboxes in one persistent launch: the 32 star-polygon instances (uneven sizes)
+    batched = batched_build() if args.batched_build else {}
+
     # end to end through the C ABI with host buffers (copies inside the timed region)
     e2e_ms = []
     u_host = np.zeros(w.x.shape[0])
@@ -365,6 +401,7 @@ def main():
                              f"{peaks.get('sm_max_mhz', 2032.0):.0f} MHz ({peak_src} clock)"},
         "clocks": ck,
         "served_solve": served,
+        "batched_build": batched,
         "gpu_launches": launches_per_step,
     }
     if rank == 0:

@@ -153,6 +153,23 @@ typedef enum {
     EWOS_WALK_XEXIT = 10 /* [n][N][d]    stopping point of each walk (double; record_walks)  */
 } ewos_array;
 
+/*
+ * Many toolboxes in one persistent walk launch (uneven node counts): instance k has domain
+ * domains[k] (all of one dimension and distance kind), nodes x[k] [n[k]][d] and z[k]
+ * [p[k]][d] (host arrays); walks, eps, seed and the options are shared, and instance k draws
+ * the Philox stream of opts->instance + k (so each toolbox equals the one ewos_toolbox_build
+ * makes with that instance number).  The rows of all instances are one index space: a CTA takes
+ * the next row of any instance, switching the instance's arguments in shared memory.  The
+ * block size and CTAs per SM are chosen by timing the candidates on a prefix of the rows
+ * (cached per batch shape) unless opts->threads_per_block is set.  record_walks, cell_weights
+ * and inputs_on_device are not supported (EWOS_EINVAL).  out[k] receives toolbox k (free each
+ * with ewos_toolbox_free); batch_report (may be NULL) the totals and the launch shape.
+ */
+ewos_status ewos_toolbox_build_batch(int count, const ewos_domain* domains, const double* const* x, const int64_t* n,
+                                     const double* const* z, const int64_t* p, int64_t walks, double eps,
+                                     uint64_t seed, const ewos_build_opts* opts, ewos_toolbox** out,
+                                     ewos_build_report* batch_report);
+
 /* Copy one toolbox array to dst (dst_bytes must be at least the array's size in the type
  * listed above; dst_on_device = 1 for a device pointer). */
 ewos_status ewos_toolbox_get(const ewos_toolbox* tb, int which, void* dst, size_t dst_bytes,

@@ -42,6 +42,8 @@ cudaError_t dev_free(void* p) { return p ? cudaFreeAsync(p, g_alloc_stream) : cu
 ewos_status build_toolbox(ewos_toolbox* tb, const ewos_domain* dom, const double* d_x, const double* d_z,
                           const ewos_build_opts& o);
 ewos_status validate_domain(const ewos_domain* dom, const double* x, int64_t n);
+ewos_status build_toolbox_batch(std::vector<ewos_toolbox*>& tbs, const std::vector<const ewos_domain*>& doms,
+                                const ewos_build_opts& o, ewos_build_report* brep);
 
 static void release(ewos_toolbox* tb) {
     if (!tb) return;
@@ -170,6 +172,71 @@ ewos_status ewos_toolbox_build(const ewos_domain* domain, const double* x, int64
     if (s != EWOS_OK) { release(tb); return s; }
     *out = tb;
     return tb->rep.capped > 0 ? EWOS_ESTEPCAP : EWOS_OK;
+}
+
+ewos_status ewos_toolbox_build_batch(int count, const ewos_domain* domains, const double* const* x, const int64_t* n,
+                                     const double* const* z, const int64_t* p, int64_t walks, double eps, uint64_t seed,
+                                     const ewos_build_opts* opts, ewos_toolbox** out, ewos_build_report* batch_report) {
+    if (count < 1 || !domains || !x || !n || !z || !p || !out || walks < 1 || !(eps > 0) || walks > 0xFFFFFFFFll) {
+        set_error("ewos_toolbox_build_batch: need count >= 1, domains, x, n, z, p, out, 1 <= walks < 2^32, eps > 0");
+        return EWOS_EINVAL;
+    }
+    ewos_build_opts o{};
+    o.precision = 32;
+    o.hash_in_smem = -1;
+    if (opts) o = *opts;
+    if (o.precision != 32 && o.precision != 64) { set_error("precision must be 32 or 64"); return EWOS_EINVAL; }
+    if (o.record_walks || o.cell_weights || o.inputs_on_device) {
+        set_error("ewos_toolbox_build_batch: record_walks, cell_weights and device inputs are not supported");
+        return EWOS_EINVAL;
+    }
+    int64_t rows = 0;
+    for (int k = 0; k < count; ++k) {
+        if (!x[k] || !z[k] || n[k] < 1 || p[k] < 1 || n[k] > (1 << 30) || p[k] > (1 << 30)) {
+            set_error("ewos_toolbox_build_batch: every instance needs x, z, n >= 1, p >= 1");
+            return EWOS_EINVAL;
+        }
+        if (domains[k].dim != domains[0].dim || domains[k].kind != domains[0].kind) {
+            set_error("ewos_toolbox_build_batch: all domains must have the same dimension and distance kind");
+            return EWOS_EINVAL;
+        }
+        ewos_status s = validate_domain(&domains[k], x[k], n[k]);
+        if (s != EWOS_OK) return s;
+        rows += n[k];
+    }
+    if (rows >= (1ll << 31)) { set_error("ewos_toolbox_build_batch: more than 2^31 rows"); return EWOS_EINVAL; }
+    for (int k = 0; k < count; ++k) out[k] = nullptr;
+    AllocStream as((cudaStream_t)o.stream);
+    std::vector<ewos_toolbox*> tbs;
+    std::vector<const ewos_domain*> doms;
+    ewos_status s = EWOS_OK;
+    for (int k = 0; k < count && s == EWOS_OK; ++k) {
+        ewos_toolbox* tb = new ewos_toolbox();
+        tb->dim = domains[k].dim; tb->precision = o.precision;
+        tb->n = n[k]; tb->m = n[k]; tb->p = p[k]; tb->N = walks; tb->eps = eps; tb->seed = seed;
+        tb->instance = o.instance + (uint32_t)k;
+        tb->stream = (cudaStream_t)o.stream;
+        cudaGetDevice(&tb->device);
+        tbs.push_back(tb);
+        doms.push_back(&domains[k]);
+        s = alloc_matrices(tb, true);
+        if (s == EWOS_OK) {
+            cudaError_t e1 = cudaMemcpyAsync(tb->x, x[k], sizeof(double) * n[k] * tb->dim, cudaMemcpyHostToDevice, tb->stream);
+            cudaError_t e2 = cudaMemcpyAsync(tb->z, z[k], sizeof(double) * p[k] * tb->dim, cudaMemcpyHostToDevice, tb->stream);
+            if (e1 != cudaSuccess || e2 != cudaSuccess) { set_error("copy of nodes failed"); s = EWOS_ECUDA; }
+        }
+    }
+    if (s == EWOS_OK) s = build_toolbox_batch(tbs, doms, o, batch_report);
+    if (s != EWOS_OK) {
+        for (ewos_toolbox* tb : tbs) release(tb);
+        return s;
+    }
+    int64_t capped = 0;
+    for (int k = 0; k < count; ++k) {
+        out[k] = tbs[k];
+        capped += tbs[k]->rep.capped;
+    }
+    return capped > 0 ? EWOS_ESTEPCAP : EWOS_OK;
 }
 
 ewos_status ewos_toolbox_from_host(int dim, int64_t n, int64_t p, const double* x, const double* z, const double* G,

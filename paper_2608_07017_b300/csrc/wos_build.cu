@@ -21,6 +21,7 @@
 #include <cmath>
 #include <chrono>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -571,8 +572,12 @@ __device__ __forceinline__ void bin_stopped(const WalkArgs<T, D>& a, const WalkQ
     }
 }
 
-template <typename T, int D, int KIND, bool RECORD>
-__global__ void __launch_bounds__(1024, 1) wos_walk_kernel(WalkArgs<T, D> a) {
+// The persistent row loop of one toolbox (instance).  Single builds fetch rows from the
+// instance's own counter; batched builds fetch global rows g from one counter shared by all
+// instances (rows of instance k are [gbase, gend)) and return the first fetched row that belongs
+// to a later instance.
+template <typename T, int D, int KIND, bool RECORD, bool BATCH>
+__device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, int gbase, int gend, int* gcounter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // shared layout: acc [(D+1)][m] T | accKH [D][p] T | accH [p] u32 | sdf params | per-warp
     // queues | V lookup (points, then the fixed-stride table or the CSR lists)
@@ -624,12 +629,24 @@ __global__ void __launch_bounds__(1024, 1) wos_walk_kernel(WalkArgs<T, D> a) {
 
     unsigned long long my_steps = 0, my_capped = 0;
     const T invN = T(1) / (T)a.N;
+    bool first = true;
+    int g_next = 0;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) { s_row = atomicAdd(a.row_counter, 1); s_walk = 0u; }
+        if (threadIdx.x == 0) {
+            if (BATCH) s_row = first ? g_first : atomicAdd(gcounter, 1);
+            else s_row = atomicAdd(a.row_counter, 1);
+            s_walk = 0u;
+        }
+        first = false;
         __syncthreads();
-        const int row = s_row;
-        if (row >= a.n) break;
+        int row = s_row;
+        if (BATCH) {
+            if (row >= gend) { g_next = row; break; }
+            row -= gbase;
+        } else if (row >= a.n) {
+            break;
+        }
         T xi[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) xi[c] = a.x[(size_t)row * D + c];
@@ -757,6 +774,41 @@ __global__ void __launch_bounds__(1024, 1) wos_walk_kernel(WalkArgs<T, D> a) {
         atomicAdd(a.stat_steps, my_steps);
         if (my_capped) atomicAdd(a.stat_capped, my_capped);
     }
+    return g_next;
+}
+
+template <typename T, int D, int KIND, bool RECORD>
+__global__ void __launch_bounds__(1024, 1) wos_walk_kernel(WalkArgs<T, D> a) {
+    walk_rows<T, D, KIND, RECORD, false>(a, 0, 0, 0, nullptr);
+}
+
+// Several toolboxes in one persistent launch: the rows of all instances form one index space
+// (instance k owns [row_off[k], row_off[k+1])); a CTA takes the next global row, loads that
+// instance's arguments into shared memory when the instance changes, and runs the instance's
+// row loop until it draws a row of a later instance.
+template <typename T, int D, int KIND>
+__global__ void __launch_bounds__(1024, 1) wos_walk_batch_kernel(const WalkArgs<T, D>* __restrict__ batch,
+                                                                 const int* __restrict__ row_off, int nb,
+                                                                 int* __restrict__ gcounter) {
+    __shared__ WalkArgs<T, D> s_a;
+    __shared__ int s_g;
+    if (threadIdx.x == 0) s_g = atomicAdd(gcounter, 1);
+    __syncthreads();
+    int g = s_g;
+    const int total = row_off[nb];
+    while (g < total) {
+        int lo = 0, hi = nb - 1;              // last instance whose first row is <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (row_off[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_a = batch[lo];
+        __syncthreads();
+        g = walk_rows<T, D, KIND, false, true>(s_a, g, row_off[lo], row_off[lo + 1], gcounter);
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------------ host side
@@ -868,17 +920,24 @@ static void tune_store(const TuneKey& k, int tpb, bool v_smem, int vgrid) {
     g_tune.push_back({k, TuneVal{tpb, v_smem, vgrid}});
 }
 
+// Everything before the walk launch of one toolbox: distances and node radii, the Voronoi
+// lookups (the default V grid; also the alternative grid when alt_grid), cell weights, and the
+// walk arguments (V set to the default grid, in global memory).
+struct PrepOut {
+    double lo[3], hi[3];
+    double gf_default, gf_alt;
+    bool have_cached;
+    int cached_tpb, cached_grid;
+    bool cached_smem;
+    bool tune_grid;
+};
+
 template <typename T, int D>
-static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const double* d_x, const double* d_z,
-                               const ewos_build_opts& o) {
+static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const double* d_x, const double* d_z,
+                                 const ewos_build_opts& o, BuildContext& ctx, WalkArgs<T, D>& a, PrepOut& po,
+                                 cudaEvent_t ev_lookup, cudaEvent_t ev_cells, bool allow_alt) {
     cudaStream_t st = tb->stream;
     const int n = (int)tb->n, m = (int)tb->m, p = (int)tb->p;
-    BuildContext ctx;
-    cudaEvent_t ev[5];
-    for (auto& e : ev) cudaEventCreate(&e);
-    struct EvGuard { cudaEvent_t* e; ~EvGuard() { for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]); } } evg{ev};
-    EWOS_CUDA_TRY(cudaEventRecord(ev[0], st));
-
     // distance parameters and node radii
     std::vector<T> prmT(dom->nparams);
     for (int64_t t = 0; t < dom->nparams; ++t) prmT[t] = (T)dom->params[t];
@@ -893,7 +952,9 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     EWOS_CUDA_TRY(cudaGetLastError());
 
     // Voronoi lookups over the domain's bounding box
-    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    double* lo = po.lo;
+    double* hi = po.hi;
+    for (int c = 0; c < 3; ++c) lo[c] = hi[c] = 0;
     domain_bbox(D, dom->kind, dom->params, dom->nparams, lo, hi);
     double vol = 1;
     for (int c = 0; c < D; ++c) vol *= (hi[c] - lo[c]);
@@ -905,7 +966,7 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     // V grid spacing: factor x (volume / m)^(1/d); the autotuner also tries the other factor
     const double gf_default = o.lookup_grid_scale > 0 ? o.lookup_grid_scale : (D == 2 ? 1.0 : 0.5);
     const double gf_alt = D == 2 ? 0.5 : 1.0;
-    const bool tune_grid = o.lookup_grid_scale <= 0 &&
+    const bool tune_grid = allow_alt && o.lookup_grid_scale <= 0 &&
                            (o.threads_per_block <= 0 || !(o.hash_in_smem == 0 || o.hash_in_smem == 1));
     ewos_status s = build_lookup<T>(D, d_x, m, lo, hi, hv * gf_default, st, ctx.V, true);
     if (s != EWOS_OK) return s;
@@ -920,7 +981,7 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
         s = build_lookup<T>(D, d_x, m, lo, hi, hv * gf_alt, st, ctx.V2, true);
         if (s != EWOS_OK) return s;
     }
-    EWOS_CUDA_TRY(cudaEventRecord(ev[1], st));
+    if (ev_lookup) EWOS_CUDA_TRY(cudaEventRecord(ev_lookup, st));
 
     // cell weights
     if (o.cell_weights) {
@@ -948,10 +1009,9 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
         ::ewos::note_launch(), counts_to_lambda_kernel<<<1, 1024, 0, st>>>(ctx.d_counts, m, tb->lambda);
         EWOS_CUDA_TRY(cudaGetLastError());
     }
-    EWOS_CUDA_TRY(cudaEventRecord(ev[2], st));
+    if (ev_cells) EWOS_CUDA_TRY(cudaEventRecord(ev_cells, st));
 
     // walk kernel configuration
-    WalkArgs<T, D> a{};
     a.n = n; a.m = m; a.p = p; a.N = tb->N; a.eps = (T)tb->eps;
     a.k0 = (uint32_t)tb->seed; a.k1 = (uint32_t)(tb->seed >> 32);
     a.inst = (tb->instance & 0xFFFFu) << 8;
@@ -970,6 +1030,37 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     a.rec_xexit = (T*)tb->rec_xexit;
     if (tb->rec_vhash) EWOS_CUDA_TRY(cudaMemsetAsync(tb->rec_vhash, 0, sizeof(uint32_t) * n * tb->N, st));
 
+    a.V = lookup_view<T, D>(ctx.V);
+    a.v_ncell = (int)ctx.V.grid.ncell; a.v_ncand = ctx.V.ncand;
+    a.v_K = ctx.V.K; a.v_candK = ctx.V.candK;
+    a.v_in_smem = 0;
+    po.gf_default = gf_default; po.gf_alt = gf_alt;
+    po.have_cached = have_cached; po.cached_tpb = cached_tpb; po.cached_grid = cached_grid;
+    po.cached_smem = cached_smem; po.tune_grid = tune_grid;
+    return EWOS_OK;
+}
+
+template <typename T, int D>
+static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const double* d_x, const double* d_z,
+                               const ewos_build_opts& o) {
+    cudaStream_t st = tb->stream;
+    const int n = (int)tb->n, m = (int)tb->m, p = (int)tb->p;
+    BuildContext ctx;
+    cudaEvent_t ev[5];
+    for (auto& e : ev) cudaEventCreate(&e);
+    struct EvGuard { cudaEvent_t* e; ~EvGuard() { for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]); } } evg{ev};
+    EWOS_CUDA_TRY(cudaEventRecord(ev[0], st));
+    WalkArgs<T, D> a{};
+    PrepOut po{};
+    ewos_status s = prepare_walks<T, D>(tb, dom, d_x, d_z, o, ctx, a, po, ev[1], ev[2], true);
+    if (s != EWOS_OK) return s;
+    const double gf_default = po.gf_default, gf_alt = po.gf_alt;
+    const bool have_cached = po.have_cached;
+    const int cached_tpb = po.cached_tpb, cached_grid = po.cached_grid;
+    const bool cached_smem = po.cached_smem;
+    const int sdf_len = a.sdf_len;
+    TuneKey key{sizeof(T), D, dom->kind, m, p, tb->N, o.record_walks != 0, o.threads_per_block, o.hash_in_smem,
+                o.ctas_per_sm, o.lookup_grid_scale};
     const bool rec = o.record_walks != 0;
     const size_t acc_bytes = sizeof(T) * ((size_t)(D + 1) * m + (size_t)D * p) + sizeof(uint32_t) * p;
     const size_t sdf_bytes = sizeof(T) * ((sdf_len + 3) & ~3);
@@ -1103,6 +1194,195 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     r.lookup_candidates = Vs[cfg.vg]->K;
     r.smem_bytes = (int64_t)smem;
     return EWOS_OK;
+}
+
+// ------------------------------------------------------------------ many toolboxes, one launch
+template <typename T, int D, int KIND>
+static cudaError_t launch_batch(const WalkArgs<T, D>* d_args, const int* d_off, int nb, int* d_counter, int grid,
+                                int tpb, size_t smem, cudaStream_t st) {
+    auto k = wos_walk_batch_kernel<T, D, KIND>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ::ewos::note_launch(), k<<<grid, tpb, smem, st>>>(d_args, d_off, nb, d_counter);
+    return cudaGetLastError();
+}
+
+template <typename T, int D, int KIND>
+static int batch_ctas_per_sm(int tpb, size_t smem) {
+    int per = 0;
+    auto k = wos_walk_batch_kernel<T, D, KIND>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, tpb, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per;
+}
+
+// process-wide choices of the batch launch shape, keyed by the batch's shape
+struct BatchTuneKey {
+    int esz, dim, kind, count;
+    int64_t rows, max_m, max_p, N;
+    bool operator==(const BatchTuneKey& o) const {
+        return esz == o.esz && dim == o.dim && kind == o.kind && count == o.count && rows == o.rows &&
+               max_m == o.max_m && max_p == o.max_p && N == o.N;
+    }
+};
+static std::vector<std::pair<BatchTuneKey, std::pair<int, int>>> g_batch_tune;   // -> (tpb, ctas/SM)
+
+template <typename T, int D, int KIND>
+static ewos_status build_batch_kind(std::vector<ewos_toolbox*>& tbs, const std::vector<const ewos_domain*>& doms,
+                                    const ewos_build_opts& o, ewos_build_report* brep) {
+    cudaStream_t st = tbs[0]->stream;
+    const int nb = (int)tbs.size();
+    cudaEvent_t ev[3];
+    for (auto& e : ev) cudaEventCreate(&e);
+    struct EvGuard { cudaEvent_t* e; ~EvGuard() { for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]); } } evg{ev};
+    EWOS_CUDA_TRY(cudaEventRecord(ev[0], st));
+    std::vector<std::unique_ptr<BuildContext>> ctxs;
+    std::vector<WalkArgs<T, D>> args(nb);
+    std::vector<int> off(nb + 1, 0);
+    int64_t max_m = 0, max_p = 0, max_sdf = 0;
+    for (int k = 0; k < nb; ++k) {
+        ctxs.emplace_back(new BuildContext());
+        ewos_build_opts ok = o;
+        ok.instance = o.instance + (uint32_t)k;
+        tbs[k]->instance = ok.instance;
+        PrepOut po{};
+        ewos_status s = prepare_walks<T, D>(tbs[k], doms[k], tbs[k]->x, tbs[k]->z, ok, *ctxs.back(), args[k], po,
+                                            nullptr, nullptr, false);
+        if (s != EWOS_OK) return s;
+        off[k + 1] = off[k] + (int)tbs[k]->n;
+        max_m = std::max<int64_t>(max_m, tbs[k]->m);
+        max_p = std::max<int64_t>(max_p, tbs[k]->p);
+        max_sdf = std::max<int64_t>(max_sdf, args[k].sdf_len);
+    }
+    WalkArgs<T, D>* d_args = nullptr;
+    int *d_off = nullptr, *d_counter = nullptr, *d_off_trial = nullptr;
+    struct Frees { void** p[4]; ~Frees() { for (auto q : p) ::ewos::dev_free(*q); } } fr{{(void**)&d_args, (void**)&d_off, (void**)&d_counter, (void**)&d_off_trial}};
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_args, sizeof(WalkArgs<T, D>) * nb));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_off, sizeof(int) * (nb + 1)));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_off_trial, sizeof(int) * (nb + 1)));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_counter, sizeof(int)));
+    EWOS_CUDA_TRY(cudaMemcpyAsync(d_args, args.data(), sizeof(WalkArgs<T, D>) * nb, cudaMemcpyHostToDevice, st));
+    EWOS_CUDA_TRY(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
+    EWOS_CUDA_TRY(cudaEventRecord(ev[1], st));
+
+    // shared memory for the largest instance
+    const size_t acc_bytes = sizeof(T) * ((size_t)(D + 1) * max_m + (size_t)D * max_p) + sizeof(uint32_t) * max_p;
+    const size_t sdf_bytes = sizeof(T) * ((max_sdf + 3) & ~int64_t(3));
+    auto smem_for = [&](int t) {
+        return (((acc_bytes + 15) & ~size_t(15)) + sdf_bytes + queue_bytes<T, D>(t / 32, false) + 15) & ~size_t(15);
+    };
+    int dev = 0, nsm = 0, smem_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int total = off[nb];
+    // autotuner: block size x CTAs per SM, timed on a prefix of the global rows, cached per shape
+    BatchTuneKey key{(int)sizeof(T), D, KIND, nb, total, max_m, max_p, tbs[0]->N};
+    int tpb = 0, per = 0;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (auto& e : g_batch_tune)
+            if (e.first == key) { tpb = e.second.first; per = e.second.second; }
+    }
+    if (o.threads_per_block > 0) { tpb = std::min(1024, (o.threads_per_block + 31) / 32 * 32); per = 0; }
+    if (tpb == 0) {
+        struct C { int tpb, per; };
+        std::vector<C> cands;
+        for (int t : {256, 512, 1024}) {
+            const size_t sm = smem_for(t);
+            if (sm > (size_t)smem_optin - 1024) continue;
+            const int mx = batch_ctas_per_sm<T, D, KIND>(t, sm);
+            for (int p2 = 1; p2 <= mx && p2 <= 4; p2 *= 2) cands.push_back({t, p2});
+        }
+        if (cands.empty()) { set_error("batch: the largest toolbox row does not fit in shared memory"); return EWOS_EINVAL; }
+        std::vector<int> off_trial(off);
+        const int prefix = std::min(total, 2 * nsm);
+        for (auto& v : off_trial) v = std::min(v, prefix);
+        EWOS_CUDA_TRY(cudaMemcpyAsync(d_off_trial, off_trial.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
+        float best = 3.0e38f;
+        cudaEvent_t t0, t1;
+        cudaEventCreate(&t0); cudaEventCreate(&t1);
+        for (const C& c : cands) {
+            EWOS_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), st));
+            cudaEventRecord(t0, st);
+            const int tgrid = std::max(1, std::min(nsm * c.per, prefix));
+            cudaError_t le = launch_batch<T, D, KIND>(d_args, d_off_trial, nb, d_counter, tgrid, c.tpb, smem_for(c.tpb), st);
+            EWOS_CUDA_TRY(le);
+            cudaEventRecord(t1, st);
+            EWOS_CUDA_TRY(cudaEventSynchronize(t1));
+            float ms = 0;
+            cudaEventElapsedTime(&ms, t0, t1);
+            if (ms < best) { best = ms; tpb = c.tpb; per = c.per; }
+        }
+        cudaEventDestroy(t0); cudaEventDestroy(t1);
+        for (int k = 0; k < nb; ++k) EWOS_CUDA_TRY(cudaMemsetAsync(ctxs[k]->d_stats, 0, 2 * sizeof(unsigned long long), st));
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_batch_tune.push_back({key, {tpb, per}});
+    }
+    const size_t smem = smem_for(tpb);
+    if (per <= 0) per = std::max(1, batch_ctas_per_sm<T, D, KIND>(tpb, smem));
+    if (o.ctas_per_sm > 0) per = std::min(per, o.ctas_per_sm);
+    const int grid = std::max(1, std::min(nsm * per, total));
+    EWOS_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), st));
+    EWOS_CUDA_TRY(cudaEventRecord(ev[1], st));
+    cudaError_t le = launch_batch<T, D, KIND>(d_args, d_off, nb, d_counter, grid, tpb, smem, st);
+    EWOS_CUDA_TRY(le);
+    EWOS_CUDA_TRY(cudaEventRecord(ev[2], st));
+    std::vector<unsigned long long> stats(2 * nb);
+    for (int k = 0; k < nb; ++k)
+        EWOS_CUDA_TRY(cudaMemcpyAsync(&stats[2 * k], ctxs[k]->d_stats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    float ms_all = 0, ms_walk = 0;
+    cudaEventElapsedTime(&ms_all, ev[0], ev[2]);
+    cudaEventElapsedTime(&ms_walk, ev[1], ev[2]);
+    ewos_build_report tot{};
+    for (int k = 0; k < nb; ++k) {
+        ewos_build_report& r = tbs[k]->rep;
+        r = ewos_build_report{};
+        r.walks = tbs[k]->n * tbs[k]->N;
+        r.steps = (int64_t)stats[2 * k];
+        r.capped = (int64_t)stats[2 * k + 1];
+        r.ms_total = ms_all; r.ms_walk = ms_walk;
+        r.threads_per_block = tpb; r.ctas_per_sm = per; r.grid = grid; r.hash_in_smem = 0;
+        r.smem_bytes = (int64_t)smem;
+        r.lookup_candidates = ctxs[k]->V.K;
+        tot.walks += r.walks; tot.steps += r.steps; tot.capped += r.capped;
+    }
+    tot.ms_total = ms_all; tot.ms_walk = ms_walk;
+    tot.threads_per_block = tpb; tot.ctas_per_sm = per; tot.grid = grid; tot.smem_bytes = (int64_t)smem;
+    if (brep) *brep = tot;
+    return EWOS_OK;
+}
+
+ewos_status build_toolbox_batch(std::vector<ewos_toolbox*>& tbs, const std::vector<const ewos_domain*>& doms,
+                                const ewos_build_opts& o, ewos_build_report* brep) {
+    const int kind = doms[0]->kind;
+    const int D = tbs[0]->dim;
+    const bool f64 = tbs[0]->precision == 64;
+#define EWOS_BATCH(TT, DD, KK) return build_batch_kind<TT, DD, KK>(tbs, doms, o, brep)
+    if (f64) {
+        if (D == 2) {
+            if (kind == SDF_BALL) EWOS_BATCH(double, 2, SDF_BALL);
+            if (kind == SDF_BOX) EWOS_BATCH(double, 2, SDF_BOX);
+            EWOS_BATCH(double, 2, SDF_POLYGON);
+        }
+        if (kind == SDF_BALL) EWOS_BATCH(double, 3, SDF_BALL);
+        EWOS_BATCH(double, 3, SDF_BOX);
+    }
+    if (D == 2) {
+        if (kind == SDF_BALL) EWOS_BATCH(float, 2, SDF_BALL);
+        if (kind == SDF_BOX) EWOS_BATCH(float, 2, SDF_BOX);
+        EWOS_BATCH(float, 2, SDF_POLYGON);
+    }
+    if (kind == SDF_BALL) EWOS_BATCH(float, 3, SDF_BALL);
+    EWOS_BATCH(float, 3, SDF_BOX);
+#undef EWOS_BATCH
 }
 
 ewos_status build_toolbox(ewos_toolbox* tb, const ewos_domain* dom, const double* d_x, const double* d_z,

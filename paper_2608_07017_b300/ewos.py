@@ -121,6 +121,8 @@ def lib():
         L.ewos_debug_philox.argtypes = [P, P, P, I64]
         L.ewos_debug_green_radius.argtypes = [P, P, I64, I]
         L.ewos_debug_tc_gemm.argtypes = [P, P, P, I, I, I, I]
+        L.ewos_toolbox_build_batch.argtypes = [I, P, P, P, P, P, I64, ctypes.c_double, ctypes.c_uint64,
+                                               ctypes.POINTER(BuildOpts), P, ctypes.POINTER(BuildReport)]
         L.ewos_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(P)]
         L.ewos_server_submit.argtypes = [P, P, ctypes.POINTER(_Problem), ctypes.POINTER(ctypes.c_uint64)]
         L.ewos_server_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_double, P, P, ctypes.POINTER(SolveReport),
@@ -131,7 +133,7 @@ def lib():
         for fn in ("ewos_toolbox_build", "ewos_toolbox_build_noalloc", "ewos_toolbox_from_host", "ewos_toolbox_get", "ewos_toolbox_report",
                    "ewos_toolbox_shape", "ewos_solve", "ewos_debug_philox", "ewos_debug_green_radius",
                    "ewos_debug_tc_gemm", "ewos_server_create", "ewos_server_submit", "ewos_server_wait",
-                   "ewos_server_query"):
+                   "ewos_server_query", "ewos_toolbox_build_batch"):
             getattr(L, fn).restype = I
         _lib = L
     return _lib
@@ -279,6 +281,39 @@ def build_workload(w, **kw):
     if w.lam is not None:
         kw.setdefault("cell_weights", w.lam)
     return build_toolbox(w.domain.kind, w.domain.dim, w.domain.params, w.x, w.z, w.walks, w.eps, seed=w.seed, **kw)
+
+
+def build_batch(domains, xs, zs, walks, eps, seed=0, precision=32, max_steps=0, instance=0, cell_samples=0,
+                threads_per_block=0, ctas_per_sm=0, stream=None):
+    """Several toolboxes in one persistent walk launch (ewos_toolbox_build_batch).  domains:
+    list of (kind, dim, params); instance k uses Philox instance `instance + k`.  Returns
+    (list of Toolbox, batch report dict, status)."""
+    count = len(domains)
+    prms = [_f64(pr) for _, _, pr in domains]
+    doms = (_Domain * count)(*[_Domain(SDF[k], d, pr.ctypes.data, pr.size) for (k, d, _), pr in zip(domains, prms)])
+    xa = [_f64(x) for x in xs]
+    za = [_f64(z) for z in zs]
+    xp = (ctypes.c_void_p * count)(*[a.ctypes.data for a in xa])
+    zp = (ctypes.c_void_p * count)(*[a.ctypes.data for a in za])
+    ns = (ctypes.c_int64 * count)(*[a.shape[0] for a in xa])
+    ps = (ctypes.c_int64 * count)(*[a.shape[0] for a in za])
+    o = BuildOpts()
+    o.precision = precision
+    o.max_steps = max_steps
+    o.stream = stream
+    o.cell_samples = cell_samples
+    o.threads_per_block = threads_per_block
+    o.ctas_per_sm = ctas_per_sm
+    o.hash_in_smem = -1
+    o.instance = instance
+    out = (ctypes.c_void_p * count)()
+    rep = BuildReport()
+    st = lib().ewos_toolbox_build_batch(count, ctypes.cast(doms, ctypes.c_void_p), ctypes.cast(xp, ctypes.c_void_p),
+                                        ctypes.cast(ns, ctypes.c_void_p), ctypes.cast(zp, ctypes.c_void_p),
+                                        ctypes.cast(ps, ctypes.c_void_p), walks, eps, seed, ctypes.byref(o),
+                                        ctypes.cast(out, ctypes.c_void_p), ctypes.byref(rep))
+    _check(st, "build_batch", allow=(OK, ESTEPCAP))
+    return [Toolbox(out[k]) for k in range(count)], rep.as_dict(), st
 
 
 def toolbox_from_host(dim, x, z, G, gradG, H, gradH, lam, precision=64, stream=None):

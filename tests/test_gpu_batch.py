@@ -1,0 +1,96 @@
+"""Many toolboxes in one persistent launch (uneven star-polygon instances).
+
+* every toolbox of a batch equals the toolbox a single build makes with the same Philox
+  instance: exit counts bit-exact, G and grad G up to the order of the FP32 shared-memory
+  atomics, identical step counts;
+* against the oracle (same stream, instance k): exit counts per row within twice the 0.1 %
+  divergent-walk allowance;
+* the 32-instance star workload at full size: one launch, every row's exit counts sum to N, and
+  the quasilinear problem of each instance solved by Picard through the request server.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import solve as S
+from paper_2608_07017_b300 import ewos
+from paper_2608_07017_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2608_07017_b300 import build
+    build.build()
+    oracle.build()
+
+
+def _small_stars(sizes, walks=400, seed=2):
+    rng = np.random.default_rng(seed)
+    out = []
+    for t, n in enumerate(sizes):
+        V = W.star_polygon(3 + t % 5)
+        x = W.star_nodes(V, n, rng)
+        z = W.polygon_boundary_nodes(V, max(8, n // 8))
+        out.append(W.Workload(f"s{t}", W.Domain(2, "polygon", V.ravel().copy()), x, z, walks, 1e-4, 32, 0))
+    return out
+
+
+def test_batch_equals_single_builds():
+    ws = _small_stars([150, 310, 47, 222])
+    tbs, rep, st = ewos.build_batch([("polygon", 2, w.domain.params) for w in ws], [w.x for w in ws],
+                                    [w.z for w in ws], 400, 1e-4, seed=0, instance=5, cell_samples=100000)
+    assert rep["walks"] == sum(w.x.shape[0] for w in ws) * 400
+    for k, (w, tb) in enumerate(zip(ws, tbs)):
+        single = ewos.build_toolbox("polygon", 2, w.domain.params, w.x, w.z, 400, 1e-4, seed=0, instance=5 + k,
+                                    cell_samples=100000)
+        assert np.array_equal(tb.get("Hc"), single.get("Hc"))
+        for name in ("G", "gradG", "gradH"):
+            a, b = tb.get(name), single.get(name)
+            scale = np.abs(b).max()
+            assert np.max(np.abs(a - b)) <= 1e-5 * scale, name
+        assert tb.report()["steps"] == single.report()["steps"]
+        assert np.array_equal(tb.get("lambda"), single.get("lambda"))
+        single.close()
+        tb.close()
+
+
+def test_batch_exit_counts_against_oracle():
+    ws = _small_stars([120, 260], walks=500)
+    tbs, rep, st = ewos.build_batch([("polygon", 2, w.domain.params) for w in ws], [w.x for w in ws],
+                                    [w.z for w in ws], 500, 1e-4, seed=0, instance=2, cell_samples=100000)
+    for k, (w, tb) in enumerate(zip(ws, tbs)):
+        rows = np.arange(0, w.x.shape[0], 7)
+        orc = oracle.walk_rows(2, "polygon", w.domain.params, w.x, w.z, 500, 1e-4, 0, rows=rows, instance=2 + k)
+        Hc = tb.get("Hc").astype(np.int64)[rows]
+        diff = np.abs(Hc - orc["Hc"]).sum(1)
+        assert np.all(diff <= 2 * math.ceil(0.001 * 500) * 2), diff.max()
+        assert np.all(Hc.sum(1) == 500)
+        tb.close()
+
+
+def test_stars32_full_size_batch_and_picard_serving():
+    ws = W.stars()
+    tbs, rep, st = ewos.build_batch([("polygon", 2, w.domain.params) for w in ws], [w.x for w in ws],
+                                    [w.z for w in ws], ws[0].walks, ws[0].eps, seed=0)
+    assert rep["capped"] == 0 and rep["walks"] == sum(w.x.shape[0] for w in ws) * ws[0].walks
+    sv = ewos.Server(max_slots=4)
+    tickets = []
+    for w, tb in zip(ws, tbs):
+        assert np.all(tb.get("Hc").sum(1) == w.walks)
+        pb = w.problem
+        tickets.append(sv.submit(tb, pb.A, pb.f, pb.g, kind="quasilinear", coef=pb.kappa, mode="mixed"))
+    for w, tb, t in zip(ws, tbs, tickets):
+        u, _, r, _ = sv.wait(t)
+        assert r["converged"], (w.name, r)
+        lam = tb.get("lambda")
+        err = S.errors(u, w.problem.u_star, lam)["l2"]
+        ref = math.sqrt(np.sum(lam * w.problem.u_star ** 2))
+        assert err < 0.1 * ref, (w.name, err, ref)
+    assert sv.stats()["peak_active"] >= 2
+    sv.close()
+    for tb in tbs:
+        tb.close()
