@@ -599,7 +599,6 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
         (reinterpret_cast<uintptr_t>(q.mass + qr) + 15) & ~uintptr_t(15));
     __shared__ int s_row;
     __shared__ unsigned int s_walk;
-    __shared__ int s_qn[32];
 
     for (int t = threadIdx.x; t < a.sdf_len; t += blockDim.x) s_sdf[t] = a.sdf[t];
     Lookup<T, D> V = a.V;
@@ -625,7 +624,6 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
     for (int t = threadIdx.x; t < accN; t += blockDim.x) acc[t] = T(0);
     for (int t = threadIdx.x; t < D * a.p; t += blockDim.x) accKH[t] = T(0);
     for (int t = threadIdx.x; t < a.p; t += blockDim.x) accH[t] = 0u;
-    if (threadIdx.x < 32) s_qn[threadIdx.x] = 0;
 
     unsigned long long my_steps = 0, my_capped = 0;
     const T invN = T(1) / (T)a.N;
@@ -666,20 +664,27 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
             if (RECORD) atomicXor(&a.rec_vhash[(size_t)row * a.N + l], cellmix(0xFFFFFFFFu, jb));
         }
 
-        // ---- the chains.  A lane whose walk stops queues its stopping point for boundary
-        // binning and takes the next walk of the row, doing that walk's step 0 (at x_i, radius
-        // r0) in the same iteration as the other lanes' steps; the warp bins queued walks
-        // together once it holds one per active lane.
+        // ---- the chains.  The warp iterates until none of its lanes holds a walk; a lane whose
+        // walk stops queues its stopping point for boundary binning (slots assigned from a ballot,
+        // the queue length kept warp-uniform in a register) and takes the next walk of the row,
+        // doing that walk's step 0 (at x_i, radius r0) in the same iteration as the other lanes'
+        // steps; the warp bins 32 queued walks together whenever it holds that many.
         uint32_t l = atomicAdd(&s_walk, 1u);
+        bool have = l < (uint64_t)a.N;
         T X[D], U0[D], mass = T(0);
         uint32_t k = 0, vh = 0u;
+        int qn = 0;
+        const unsigned below = (1u << lane) - 1u;
 #pragma unroll
         for (int c = 0; c < D; ++c) { X[c] = xi[c]; U0[c] = T(0); }
-        while (l < (uint64_t)a.N) {
-            T r = k == 0 ? r0 : Sdf<T, D, KIND>::eval(s_sdf, a.nsdf, X);
-            if (k > 0 && (r < a.eps || (int64_t)k > a.max_steps)) {
-                const int pos = atomicAdd(&s_qn[wid], 1);
-                const int slot = wid * kQueue + pos;
+        for (;;) {
+            if (!__any_sync(0xffffffffu, have)) break;
+            T r = r0;
+            if (have && k > 0) r = Sdf<T, D, KIND>::eval(s_sdf, a.nsdf, X);
+            const bool stop = have && k > 0 && (r < a.eps || (int64_t)k > a.max_steps);
+            const unsigned sm = __ballot_sync(0xffffffffu, stop);
+            if (stop) {
+                const int slot = wid * kQueue + qn + __popc(sm & below);
 #pragma unroll
                 for (int c = 0; c < D; ++c) { q.X[slot * D + c] = X[c]; q.U[slot * D + c] = U0[c]; }
                 if (RECORD) {
@@ -689,53 +694,45 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
                 my_steps += k;
                 my_capped += (r >= a.eps);
                 l = atomicAdd(&s_walk, 1u);
-                if (l >= (uint64_t)a.N) break;
+                have = l < (uint64_t)a.N;
 #pragma unroll
                 for (int c = 0; c < D; ++c) X[c] = xi[c];
                 k = 0;
                 r = r0;
             }
-            T R, Zs[D], U[D], pt[D];
-            draw_step<T, D>(l, k, (uint32_t)row, a.inst, a.k0, a.k1, R, Zs, U);
-            const T rR = r * R;
+            qn += __popc(sm);
+            if (have) {
+                T R, Zs[D], U[D], pt[D];
+                draw_step<T, D>(l, k, (uint32_t)row, a.inst, a.k0, a.k1, R, Zs, U);
+                const T rR = r * R;
 #pragma unroll
-            for (int c = 0; c < D; ++c) pt[c] = X[c] + rR * Zs[c];
-            const int j = K > 0 ? nearest_fixed(V, candK, K, pt) : nearest_or_scan(V, a.m, pt);
-            const T r2 = r * r;
-            atomicAdd(&acc[(size_t)D * a.m + j], r2);
-            if (k > 0) {
+                for (int c = 0; c < D; ++c) pt[c] = X[c] + rR * Zs[c];
+                const int j = K > 0 ? nearest_fixed(V, candK, K, pt) : nearest_or_scan(V, a.m, pt);
+                const T r2 = r * r;
+                atomicAdd(&acc[(size_t)D * a.m + j], r2);
+                if (k > 0) {
 #pragma unroll
-                for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + j], U0[c] * r2);
-            } else {
+                    for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + j], U0[c] * r2);
+                } else {
 #pragma unroll
-                for (int c = 0; c < D; ++c) U0[c] = U[c];
+                    for (int c = 0; c < D; ++c) U0[c] = U[c];
+                }
+#pragma unroll
+                for (int c = 0; c < D; ++c) X[c] += r * U[c];
+                if (RECORD) { mass += r2; vh ^= cellmix(k, (uint32_t)j); }
+                ++k;
             }
-#pragma unroll
-            for (int c = 0; c < D; ++c) X[c] += r * U[c];
-            if (RECORD) { mass += r2; vh ^= cellmix(k, (uint32_t)j); }
-            ++k;
-            // converged boundary binning of queued walks
-            const unsigned act = __activemask();
-            __syncwarp(act);
-            const int na = __popc(act);
-            const int rank = __popc(act & ((1u << lane) - 1u));
-            int qn = *(volatile int*)&s_qn[wid];
-            while (qn >= na) {
-                bin_stopped<T, D, RECORD>(a, q, wid * kQueue + qn - 1 - rank, row, accKH, accH);
-                qn -= na;
+            // converged boundary binning of queued walks (queue < 32 + 32 <= kQueue entries)
+            __syncwarp();
+            while (qn >= 32) {
+                bin_stopped<T, D, RECORD>(a, q, wid * kQueue + qn - 1 - lane, row, accKH, accH);
+                qn -= 32;
             }
-            __syncwarp(act);
-            if (rank == 0) s_qn[wid] = qn;
-            __syncwarp(act);
+            __syncwarp();
         }
         // drain this warp's queue
+        for (int e = lane; e < qn; e += 32) bin_stopped<T, D, RECORD>(a, q, wid * kQueue + e, row, accKH, accH);
         __syncwarp();
-        {
-            const int qn = *(volatile int*)&s_qn[wid];
-            for (int e = lane; e < qn; e += 32) bin_stopped<T, D, RECORD>(a, q, wid * kQueue + e, row, accKH, accH);
-            __syncwarp();
-            if (lane == 0) s_qn[wid] = 0;
-        }
         __syncthreads();
 
         // ---- flush the row: scale and write coalesced, then clear the accumulators
