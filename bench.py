@@ -40,8 +40,8 @@ L2_BYTES = 126 * 2 ** 20
 # per launch, both from one ncu capture of the kernel in the launch configuration this
 # benchmark runs (profiles/wos_walk_square4096.md).  The walk kernel is bound by instruction
 # issue: its roofline is 1 warp instruction per cycle per scheduler.
-WARP_INST_PER_STEP = 21.05
-WALK_DRAM_BYTES = 175.0e6
+WARP_INST_PER_STEP = 20.21
+WALK_DRAM_BYTES = 176.05e6
 
 
 def _peaks():

@@ -473,6 +473,12 @@ struct WalkArgs {
     T* rec_mass;
     uint32_t* rec_vhash;   // XOR over the walk's interior binnings of cellmix(step tag, cell)
     T* rec_xexit;          // [n][N][D] stopping point
+    // polygon edge grid (walk steps): candidate edges per cell, records (ax, ay, ex, ey, 1/|e|^2)
+    // at sdf[e_off + 5 e]; NULL for other domains (and the full scan is used)
+    const uint8_t* e_cnt;
+    const uint8_t* e_list;  // [ncell][nsdf]
+    T e_lo0, e_lo1, e_inv_h;
+    int e_nx, e_ny, e_off;
 };
 
 // walk-record digest of one interior binning: the splitmix64 output function applied to
@@ -570,6 +576,32 @@ __device__ __forceinline__ void bin_stopped(const WalkArgs<T, D>& a, const WalkQ
         a.rec_steps[ri] = (int32_t)q.K[slot];
         atomicXor(&a.rec_vhash[ri], q.vh[slot]);
     }
+}
+
+// Distance from a point of the polygon to its boundary through the edge grid: only the cell's
+// candidate edges are measured (a superset of the edges that can be nearest to a point of the
+// cell, with a margin above the rounding of this arithmetic, so the minimum is the full scan's).
+// Walk points lie in the domain, so the distance is returned without the crossing-rule sign.
+template <typename T, int D>
+__device__ __forceinline__ T polygon_dist_grid(const WalkArgs<T, D>& a, const T* s_prm, const T* x) {
+    int cx = (int)floorf((float)((x[0] - a.e_lo0) * a.e_inv_h));
+    int cy = (int)floorf((float)((x[1] - a.e_lo1) * a.e_inv_h));
+    cx = min(max(cx, 0), a.e_nx - 1);
+    cy = min(max(cy, 0), a.e_ny - 1);
+    const int cell = cy * a.e_nx + cx;
+    const int n = a.e_cnt[cell];
+    const uint8_t* L = a.e_list + (size_t)cell * a.nsdf;
+    const T* rec = s_prm + a.e_off;
+    T best = T(3.0e38f);
+    for (int i = 0; i < n; ++i) {
+        const T* r = rec + 5 * L[i];
+        const T px = x[0] - r[0], py = x[1] - r[1];
+        T t = (px * r[2] + py * r[3]) * r[4];
+        t = fmin(fmax(t, T(0)), T(1));
+        const T dx = px - t * r[2], dy = py - t * r[3];
+        best = fmin(best, dx * dx + dy * dy);
+    }
+    return m_sqrt(best);
 }
 
 // The persistent row loop of one toolbox (instance).  Single builds fetch rows from the
@@ -680,7 +712,10 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
         for (;;) {
             if (!__any_sync(0xffffffffu, have)) break;
             T r = r0;
-            if (have && k > 0) r = Sdf<T, D, KIND>::eval(s_sdf, a.nsdf, X);
+            if (have && k > 0) {
+                if (KIND == SDF_POLYGON && a.e_cnt) r = polygon_dist_grid<T, D>(a, s_sdf, X);
+                else r = Sdf<T, D, KIND>::eval(s_sdf, a.nsdf, X);
+            }
             const bool stop = have && k > 0 && (r < a.eps || (int64_t)k > a.max_steps);
             const unsigned sm = __ballot_sync(0xffffffffu, stop);
             if (stop) {
@@ -855,10 +890,86 @@ static void domain_bbox(int dim, int kind, const double* prm, int64_t nprm, doub
     }
 }
 
+// ------------------------------------------------------------------ polygon edge grid
+__device__ __forceinline__ double seg_point_dist(double px, double py, double ax, double ay, double bx, double by) {
+    const double ex = bx - ax, ey = by - ay, ee = ex * ex + ey * ey;
+    double t = ee > 0 ? ((px - ax) * ex + (py - ay) * ey) / ee : 0.0;
+    t = fmin(fmax(t, 0.0), 1.0);
+    const double dx = px - ax - t * ex, dy = py - ay - t * ey;
+    return sqrt(dx * dx + dy * dy);
+}
+
+__device__ __forceinline__ double box_point_dist(double px, double py, double x0, double x1, double y0, double y1) {
+    const double dx = fmax(fmax(x0 - px, px - x1), 0.0), dy = fmax(fmax(y0 - py, py - y1), 0.0);
+    return sqrt(dx * dx + dy * dy);
+}
+
+// the segment meets the closed box (parametric clipping against the four slabs)
+__device__ __forceinline__ bool seg_meets_box(double ax, double ay, double bx, double by, double x0, double x1,
+                                              double y0, double y1) {
+    double t0 = 0.0, t1 = 1.0;
+    const double d[2] = {bx - ax, by - ay}, o[2] = {ax, ay}, lo[2] = {x0, y0}, hi[2] = {x1, y1};
+    for (int c = 0; c < 2; ++c) {
+        if (d[c] == 0.0) {
+            if (o[c] < lo[c] || o[c] > hi[c]) return false;
+        } else {
+            double ta = (lo[c] - o[c]) / d[c], tb = (hi[c] - o[c]) / d[c];
+            if (ta > tb) { const double t = ta; ta = tb; tb = t; }
+            t0 = fmax(t0, ta);
+            t1 = fmin(t1, tb);
+            if (t0 > t1) return false;
+        }
+    }
+    return true;
+}
+
+// Candidate edges of each cell of a uniform grid over the polygon's box: every edge whose
+// distance to the cell is at most R = min_f maxdist(cell, f) + margin (the nearest edge of any
+// point of the cell is at most R away from it).  One CTA per cell, one thread per edge (edge e
+// joins vertex e-1 to vertex e), FP64; the list is written in increasing edge order.
+__global__ void polygon_grid_kernel(const double* __restrict__ V, int nv, double lo0, double lo1, double h, int nx,
+                                   double margin, uint8_t* __restrict__ cnt, uint8_t* __restrict__ list) {
+    __shared__ double s_max[256];
+    __shared__ unsigned char s_flag[256];
+    const int cell = blockIdx.x, cx = cell % nx, cy = cell / nx, e = threadIdx.x;
+    const double x0 = lo0 + cx * h, x1 = x0 + h, y0 = lo1 + cy * h, y1 = y0 + h;
+    double mx = 1e300, mn = 1e300;
+    if (e < nv) {
+        const int a = (e + nv - 1) % nv;
+        const double ax = V[2 * a], ay = V[2 * a + 1], bx = V[2 * e], by = V[2 * e + 1];
+        const double cxs[4] = {x0, x1, x0, x1}, cys[4] = {y0, y0, y1, y1};
+        mx = 0.0;
+        for (int q = 0; q < 4; ++q) mx = fmax(mx, seg_point_dist(cxs[q], cys[q], ax, ay, bx, by));
+        if (seg_meets_box(ax, ay, bx, by, x0, x1, y0, y1)) {
+            mn = 0.0;
+        } else {
+            mn = fmin(box_point_dist(ax, ay, x0, x1, y0, y1), box_point_dist(bx, by, x0, x1, y0, y1));
+            for (int q = 0; q < 4; ++q) mn = fmin(mn, seg_point_dist(cxs[q], cys[q], ax, ay, bx, by));
+        }
+    }
+    s_max[e] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (e < o) s_max[e] = fmin(s_max[e], s_max[e + o]);
+        __syncthreads();
+    }
+    const double R = s_max[0];
+    s_flag[e] = (e < nv && mn <= R + margin) ? 1 : 0;
+    __syncthreads();
+    if (e == 0) {
+        int c = 0;
+        for (int f = 0; f < nv; ++f)
+            if (s_flag[f]) list[(size_t)cell * nv + c++] = (uint8_t)f;
+        cnt[cell] = (uint8_t)c;
+    }
+}
+
 struct BuildContext {
     DeviceLookup V, Z, V2;       // V2: the V lookup on the alternative grid the autotuner tries
     void* d_sdf = nullptr;
     void* d_xT = nullptr;
+    double* d_vtx = nullptr;         // polygon vertices (FP64) for the edge grid
+    uint8_t* d_egrid = nullptr;      // edge grid: counts [ncell] then lists [ncell][nv]
     void* d_r0 = nullptr;
     int* d_counter = nullptr;
     unsigned long long* d_stats = nullptr;
@@ -866,6 +977,7 @@ struct BuildContext {
     ~BuildContext() {
         V.release(); Z.release(); V2.release();
         ::ewos::dev_free(d_sdf); ::ewos::dev_free(d_xT); ::ewos::dev_free(d_r0); ::ewos::dev_free(d_counter); ::ewos::dev_free(d_stats); ::ewos::dev_free(d_counts);
+        ::ewos::dev_free(d_vtx); ::ewos::dev_free(d_egrid);
     }
 };
 
@@ -938,10 +1050,22 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
     // distance parameters and node radii
     std::vector<T> prmT(dom->nparams);
     for (int64_t t = 0; t < dom->nparams; ++t) prmT[t] = (T)dom->params[t];
-    const int sdf_len = (int)dom->nparams;
     const int nsdf = dom->kind == SDF_POLYGON ? (int)(dom->nparams / 2) : 0;
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_sdf, sizeof(T) * std::max<int64_t>(1, dom->nparams)));
-    EWOS_CUDA_TRY(cudaMemcpyAsync(ctx.d_sdf, prmT.data(), sizeof(T) * dom->nparams, cudaMemcpyHostToDevice, st));
+    const bool egrid = dom->kind == SDF_POLYGON && nsdf <= 255;
+    if (egrid) {
+        // edge records (a, b - a, 1/|b - a|^2) of edge e = (vertex e-1, vertex e), for the walks
+        for (int e = 0; e < nsdf; ++e) {
+            const int q = (e + nsdf - 1) % nsdf;
+            const double ax = dom->params[2 * q], ay = dom->params[2 * q + 1];
+            const double ex = dom->params[2 * e] - ax, ey = dom->params[2 * e + 1] - ay;
+            const double ee = ex * ex + ey * ey;
+            prmT.push_back((T)ax); prmT.push_back((T)ay); prmT.push_back((T)ex); prmT.push_back((T)ey);
+            prmT.push_back(ee > 0 ? (T)(1.0 / ee) : T(0));
+        }
+    }
+    const int sdf_len = (int)prmT.size();
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_sdf, sizeof(T) * std::max<size_t>(1, prmT.size())));
+    EWOS_CUDA_TRY(cudaMemcpyAsync(ctx.d_sdf, prmT.data(), sizeof(T) * prmT.size(), cudaMemcpyHostToDevice, st));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_xT, sizeof(T) * n * D));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_r0, sizeof(T) * n));
     ::ewos::note_launch(), node_radius_kernel<T, D><<<(n + 127) / 128, 128, 0, st>>>(d_x, n, dom->kind, (const T*)ctx.d_sdf, nsdf,
@@ -977,6 +1101,26 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
     if (tune_grid && (!have_cached || cached_grid == 1)) {
         s = build_lookup<T>(D, d_x, m, lo, hi, hv * gf_alt, st, ctx.V2, true);
         if (s != EWOS_OK) return s;
+    }
+    int e_nx = 0, e_ny = 0;
+    double e_lo0 = 0, e_lo1 = 0, e_h = 1;
+    if (egrid) {
+        const double ext = std::max(hi[0] - lo[0], hi[1] - lo[1]);
+        e_h = ext / 32.0 * (1.0 + 1e-9);
+        e_lo0 = lo[0] - 1e-9 * ext;
+        e_lo1 = lo[1] - 1e-9 * ext;
+        e_nx = std::max(1, (int)std::ceil((hi[0] - e_lo0) / e_h));
+        e_ny = std::max(1, (int)std::ceil((hi[1] - e_lo1) / e_h));
+        const int ncell = e_nx * e_ny;
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_vtx, sizeof(double) * dom->nparams));
+        EWOS_CUDA_TRY(cudaMemcpyAsync(ctx.d_vtx, dom->params, sizeof(double) * dom->nparams, cudaMemcpyHostToDevice, st));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_egrid, (size_t)ncell * (1 + nsdf)));
+        int tpb = 32;
+        while (tpb < nsdf) tpb <<= 1;        // power of two for the block reduction (<= 256)
+        const double margin = 1e-5 * (1.0 + std::max({std::fabs(lo[0]), std::fabs(lo[1]), std::fabs(hi[0]), std::fabs(hi[1])}));
+        ::ewos::note_launch(), polygon_grid_kernel<<<ncell, tpb, 0, st>>>(ctx.d_vtx, nsdf, e_lo0, e_lo1, e_h, e_nx, margin,
+                                                                        ctx.d_egrid, ctx.d_egrid + ncell);
+        EWOS_CUDA_TRY(cudaGetLastError());
     }
     if (ev_lookup) EWOS_CUDA_TRY(cudaEventRecord(ev_lookup, st));
 
@@ -1015,6 +1159,12 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
     a.max_steps = o.max_steps > 0 ? o.max_steps : 10000;
     a.x = (const T*)ctx.d_xT; a.r0 = (const T*)ctx.d_r0;
     a.sdf = (const T*)ctx.d_sdf; a.nsdf = nsdf; a.sdf_len = sdf_len;
+    if (egrid) {
+        a.e_cnt = ctx.d_egrid;
+        a.e_list = ctx.d_egrid + (size_t)e_nx * e_ny;
+        a.e_lo0 = (T)e_lo0; a.e_lo1 = (T)e_lo1; a.e_inv_h = (T)(1.0 / e_h);
+        a.e_nx = e_nx; a.e_ny = e_ny; a.e_off = 2 * nsdf;
+    }
     a.Z = lookup_view<T, D>(ctx.Z);
     a.P = (T*)tb->P; a.KH = (T*)tb->KH; a.Hc = tb->Hc;
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_counter, sizeof(int)));
