@@ -229,6 +229,40 @@ def serve_streams(args, w, xd, zd, sp):
     return res
 
 
+def ball_newton(args, sp):
+    """ball8000 (unit ball, 8000 jittered-lattice nodes, 2000 Fibonacci boundary nodes, 10^4 walks,
+    eps 1e-4, FP32): build, then -Laplace u + u^3 = f by Newton in both solve modes."""
+    from paper_2608_07017_b300 import ewos
+    from paper_2608_07017_b300 import workloads as W
+    import torch
+    w = W.ball8000()
+    pb = w.problem
+    tb = ewos.build_workload(w, stream=sp)
+    tb.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tb = ewos.build_workload(w, stream=sp)
+    torch.cuda.synchronize()
+    build_ms = 1000 * (time.perf_counter() - t0)
+    br = tb.report()
+    lam = tb.get("lambda")
+    out = {"workload": "ball8000: unit ball, 8000 nodes, 2000 boundary nodes, 10^4 walks/node, eps 1e-4, FP32 walks; "
+                       "-Laplace u + u^3 = f, u* = x^2 - y^2 + 0.5 z sin(pi x), Newton",
+           "build_ms": build_ms, "walk_kernel_ms": br["ms_walk"], "wos_steps": br["steps"],
+           "wos_steps_per_s": br["steps"] / (br["ms_walk"] / 1000.0)}
+    for mode in ("mixed", "fp64"):
+        tb.solve(pb.A, pb.f, pb.g, kind="semilinear", coef=pb.nl, mode=mode, stream=sp) if mode == "mixed" else None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u, _, rep = tb.solve(pb.A, pb.f, pb.g, kind="semilinear", coef=pb.nl, mode=mode, stream=sp)
+        ms = 1000 * (time.perf_counter() - t0)
+        err = float(np.sqrt(np.sum(lam * (u - pb.u_star) ** 2)))
+        out[mode] = {"ms": ms, "newton_iters": rep["iters"], "converged": rep["converged"],
+                     "l2_error_vs_u_star": err, "ms_assemble": rep["ms_assemble"], "ms_factor": rep["ms_factor"]}
+    tb.close()
+    return out
+
+
 def batched_build():
     """stars32 (32 star polygons, 64 edges, n log-uniform in [256, 4096], p = n/8, 2000 walks,
     eps 1e-4): one batched launch against 32 single builds of the same toolboxes."""
@@ -274,6 +308,7 @@ def main():
     ap.add_argument("--serve-fp64", type=int, default=6, help="requests of the FP64 sample per toolbox")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched-build", type=int, default=1, help="1: also time the 32-instance star batch")
+    ap.add_argument("--ball", type=int, default=1, help="1: also time the ball8000 Newton solve (mixed and FP64)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -352,6 +387,9 @@ def main():
     # precision (full stream) vs the plain FP64 GPU path (a bounded sample of the same stream)
     served = serve_streams(args, w, xd, zd, sp) if args.serve_requests > 0 else {}
 
+    # the 3D ball: semilinear -Laplace u + u^3 = f on 8000 unknowns by Newton, mixed vs FP64
+    ball = ball_newton(args, sp) if args.ball else {}
+
     # many toolboxes in one persistent launch: the 32 star-polygon instances (uneven sizes)
     batched = batched_build() if args.batched_build else {}
 
@@ -402,6 +440,7 @@ def main():
         "clocks": ck,
         "served_solve": served,
         "batched_build": batched,
+        "ball8000": ball,
         "gpu_launches": launches_per_step,
     }
     if rank == 0:

@@ -1678,6 +1678,16 @@ static ewos_status solve_fp64(ewos_toolbox* tb, SolveWorkspace* ws, const ewos_p
 bool tc_assemble_available();
 constexpr bool kSplitTF32 = true;     // 3xTF32 assembly: Lambda to ~1e-6, fewer refinement sweeps
 
+// LU = LU + L + alpha I  (m x m, grid-stride)
+__global__ void add_shifted_kernel(float* __restrict__ LU, const float* __restrict__ L, int64_t count, int m,
+                                   double alpha) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+        float v = LU[t] + L[t];
+        if (t / m == t % m) v += (float)alpha;
+        LU[t] = v;
+    }
+}
+
 template <typename TP>
 __global__ void jac_scale32_kernel(const TP* __restrict__ Gm, const double* __restrict__ u, const double* __restrict__ lam,
                                    const double* __restrict__ nl, int nnl, float* __restrict__ out, int n, int m) {
@@ -2212,15 +2222,29 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                                                                                       ws->Jx32, (int)C.n, (int)C.m);
                     const float* Gm32 = P32 + (size_t)C.D * C.n * C.m;
                     auto t1 = std::chrono::steady_clock::now();
+                    // Jacobian Lambda + alpha I + G^T diag(lam N'(u)) G: the product on the tensor
+                    // cores (3 TF32 products) when available
+                    const bool tcj = tc_assemble_available();
+                    ewos_status tst = EWOS_OK;
                     ewos_status st = factor32_with(
                         C,
                         [&] {
-                            cudaMemcpyAsync(ws->LU32, ws->L32, sizeof(float) * C.m * C.m, cudaMemcpyDeviceToDevice, C.st);
-                            sgemm<true>(C.st, (int)C.m, (int)C.m, (int)C.n, 1.f, Gm32, C.m, ws->Jx32, C.m, 1.f, ws->LU32, C.m);
-                            ::ewos::note_launch(), add_diag_kernel<float><<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(
-                                ws->LU32, (int)C.m, (int)C.m, alpha);
+                            if (tcj) {
+                                ewos_status e = tc_assemble(Gm32, ws->Jx32, ws->LU32, (int)C.m, (int)C.m, (int)C.n, C.st,
+                                                            kSplitTF32, &ws->tc);
+                                if (e != EWOS_OK) tst = e;
+                                const int64_t cnt = C.m * C.m;
+                                ::ewos::note_launch(), add_shifted_kernel<<<(int)std::min<int64_t>(65535, (cnt + 255) / 256), 256, 0, C.st>>>(
+                                    ws->LU32, ws->L32, cnt, (int)C.m, alpha);
+                            } else {
+                                cudaMemcpyAsync(ws->LU32, ws->L32, sizeof(float) * C.m * C.m, cudaMemcpyDeviceToDevice, C.st);
+                                sgemm<true>(C.st, (int)C.m, (int)C.m, (int)C.n, 1.f, Gm32, C.m, ws->Jx32, C.m, 1.f, ws->LU32, C.m);
+                                ::ewos::note_launch(), add_diag_kernel<float><<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(
+                                    ws->LU32, (int)C.m, (int)C.m, alpha);
+                            }
                         },
                         pb->pivoting, rep);
+                    if (tst != EWOS_OK) return tst;
                     if (st != EWOS_OK) return st;
                     rep->ms_factor += elapsed_ms(t1);
                     cudaMemcpyAsync(ws->rhs, ws->y, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);

@@ -284,3 +284,21 @@ def test_mixed_ragged_sizes(k, per):
     assert rep["converged"]
     ref = S.solve_linear(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, alpha=rep["alpha"])
     assert _rel(u, ref["u"]) < 1e-9, x.shape
+
+
+def test_ball8000_full_size_newton_mixed_and_fp64():
+    # -Laplace u + u^3 = f on the unit ball, 8000 unknowns: Newton with the tensor-core
+    # assembly, FP32 LU and FP64 refinement against the plain FP64 path (R16 bar)
+    w = W.ball8000()
+    pb = w.problem
+    gtb = ewos.build_workload(w)
+    um, _, rm = gtb.solve(pb.A, pb.f, pb.g, kind="semilinear", coef=pb.nl, mode="mixed")
+    ud, _, rd = gtb.solve(pb.A, pb.f, pb.g, kind="semilinear", coef=pb.nl, mode="fp64")
+    lam = gtb.get("lambda")
+    gtb.close()
+    assert rm["converged"] and rd["converged"]
+    assert rm["iters"] == rd["iters"]
+    e_m = S.errors(um, pb.u_star, lam)["l2"]
+    e_d = S.errors(ud, pb.u_star, lam)["l2"]
+    assert abs(e_m - e_d) <= 1e-3 * max(1e-3, e_d)
+    assert e_m < 0.2 * math.sqrt(np.sum(lam * pb.u_star ** 2))
