@@ -376,12 +376,9 @@ def main():
     ck = clocks.stop()
     launches_per_step = (ewos.launch_count() - launches0) / args.steps
     if ws > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
-        st = torch.tensor([float(steps_total)], device=dev)
-        torch.distributed.all_reduce(st)
-        steps_total = int(st.item())
+        from paper_2608_07017_b300.replicas import combine
+        ms_total, steps_total = combine(ms_total, steps_total, device=dev)
+        steps_total = int(steps_total)
 
     # served solves: Poisson request stream on the resident square and ball toolboxes, mixed
     # precision (full stream) vs the plain FP64 GPU path (a bounded sample of the same stream)

@@ -70,6 +70,12 @@ typedef struct {
     uint32_t instance;        /* Philox instance word (separates independent builds)         */
     int inputs_on_device;     /* 1 -> x and z are device pointers                            */
     double lookup_grid_scale; /* Voronoi grid spacing in units of (volume/n)^(1/d); 0 -> autotuned */
+    const double* v_nodes;    /* V-centres y [m][d] of the source partition (Sec. 2.3: the
+                                 paper's V-cells, a partition independent of the W-cells of the
+                                 nodes x); NULL -> y = x, m = n.  Host or device per
+                                 inputs_on_device.  Rows stay indexed by x (n), columns of G and
+                                 grad G by y (m); the solve's unknown s has m entries.        */
+    int64_t m;                /* number of V-centres when v_nodes is set                     */
 } ewos_build_opts;
 
 typedef struct {

@@ -49,7 +49,7 @@ static void release(ewos_toolbox* tb) {
     if (!tb) return;
     AllocStream as(tb->stream);
     ::ewos::dev_free(tb->P); ::ewos::dev_free(tb->KH); ::ewos::dev_free(tb->Hc); ::ewos::dev_free(tb->lambda);
-    ::ewos::dev_free(tb->x); ::ewos::dev_free(tb->z);
+    ::ewos::dev_free(tb->x); ::ewos::dev_free(tb->z); ::ewos::dev_free(tb->y);
     ::ewos::dev_free(tb->rec_exit); ::ewos::dev_free(tb->rec_steps); ::ewos::dev_free(tb->rec_mass); ::ewos::dev_free(tb->rec_vhash);
     ::ewos::dev_free(tb->rec_xexit);
     free_workspace(tb->ws);
@@ -144,10 +144,27 @@ ewos_status ewos_toolbox_build(const ewos_domain* domain, const double* x, int64
     }
     ewos_status s = validate_domain(domain, hx, n);
     if (s != EWOS_OK) return s;
+    int64_t m = n;
+    if (o.v_nodes) {
+        if (o.m < 1 || o.m > (1 << 30)) { set_error("ewos_toolbox_build: v_nodes needs 1 <= m < 2^30"); return EWOS_EINVAL; }
+        std::vector<double> yh;
+        const double* hy = o.v_nodes;
+        if (o.inputs_on_device) {
+            yh.resize((size_t)o.m * domain->dim);
+            if (cudaMemcpy(yh.data(), o.v_nodes, sizeof(double) * yh.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                set_error("cannot read device v_nodes");
+                return EWOS_ECUDA;
+            }
+            hy = yh.data();
+        }
+        s = validate_domain(domain, hy, o.m);
+        if (s != EWOS_OK) return s;
+        m = o.m;
+    }
     AllocStream as((cudaStream_t)o.stream);
     ewos_toolbox* tb = new ewos_toolbox();
     tb->dim = domain->dim; tb->precision = o.precision;
-    tb->n = n; tb->m = n; tb->p = p; tb->N = walks; tb->eps = eps; tb->seed = seed; tb->instance = o.instance;
+    tb->n = n; tb->m = m; tb->p = p; tb->N = walks; tb->eps = eps; tb->seed = seed; tb->instance = o.instance;
     tb->stream = (cudaStream_t)o.stream;
     cudaGetDevice(&tb->device);
     s = alloc_matrices(tb, true);
@@ -166,7 +183,12 @@ ewos_status ewos_toolbox_build(const ewos_domain* domain, const double* x, int64
         const cudaMemcpyKind kind = o.inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         cudaError_t e1 = cudaMemcpyAsync(tb->x, x, sizeof(double) * n * tb->dim, kind, tb->stream);
         cudaError_t e2 = cudaMemcpyAsync(tb->z, z, sizeof(double) * p * tb->dim, kind, tb->stream);
-        if (e1 != cudaSuccess || e2 != cudaSuccess) { set_error("copy of nodes failed"); s = EWOS_ECUDA; }
+        cudaError_t e3 = cudaSuccess;
+        if (o.v_nodes) {
+            e3 = ::ewos::dev_alloc((void**)&tb->y, sizeof(double) * m * tb->dim);
+            if (e3 == cudaSuccess) e3 = cudaMemcpyAsync(tb->y, o.v_nodes, sizeof(double) * m * tb->dim, kind, tb->stream);
+        }
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) { set_error("copy of nodes failed"); s = EWOS_ECUDA; }
     }
     if (s == EWOS_OK) s = build_toolbox(tb, domain, tb->x, tb->z, o);
     if (s != EWOS_OK) { release(tb); return s; }
@@ -186,8 +208,8 @@ ewos_status ewos_toolbox_build_batch(int count, const ewos_domain* domains, cons
     o.hash_in_smem = -1;
     if (opts) o = *opts;
     if (o.precision != 32 && o.precision != 64) { set_error("precision must be 32 or 64"); return EWOS_EINVAL; }
-    if (o.record_walks || o.cell_weights || o.inputs_on_device) {
-        set_error("ewos_toolbox_build_batch: record_walks, cell_weights and device inputs are not supported");
+    if (o.record_walks || o.cell_weights || o.inputs_on_device || o.v_nodes) {
+        set_error("ewos_toolbox_build_batch: record_walks, cell_weights, v_nodes and device inputs are not supported");
         return EWOS_EINVAL;
     }
     int64_t rows = 0;

@@ -1823,35 +1823,34 @@ __global__ void from_cols_kernel(const double* __restrict__ in, double* __restri
     out[t] = in[l * rc + r];
 }
 
-// Vout[row][r] (+)= sum_c X[row][c] Vin[c][r]   (warp per row, 8 right-hand sides per pass)
-template <typename TP>
+// Vout[row][r] (+)= sum_c X[row][c] Vin[c][r]   (warp per row, RB right-hand sides per pass;
+// rc is a power of two, RB = min(rc, 8))
+template <typename TP, int RB>
 __global__ void multi_rowdot_kernel(const TP* __restrict__ X, int64_t rows, int cols, const double* __restrict__ Vin,
                                     double* __restrict__ Vout, int rc, int accumulate) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= rows) return;
     const TP* xr = X + row * cols;
-    for (int r0 = 0; r0 < rc; r0 += 8) {
-        const int rw = min(8, rc - r0);
-        double acc[8];
+    for (int r0 = 0; r0 < rc; r0 += RB) {
+        double acc[RB];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+        for (int q = 0; q < RB; ++q) acc[q] = 0.0;
         for (int c = lane; c < cols; c += 32) {
             const double xv = (double)xr[c];
             const double* vr = Vin + (size_t)c * rc + r0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (q < rw) acc[q] = fma(xv, vr[q], acc[q]);
+            for (int q = 0; q < RB; ++q) acc[q] = fma(xv, vr[q], acc[q]);
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < RB; ++q) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
         }
-        if (lane < rw) {
+        if (lane < RB) {
             double v = acc[0];
 #pragma unroll
-            for (int q = 1; q < 8; ++q)
+            for (int q = 1; q < RB; ++q)
                 if (lane == q) v = acc[q];
             double* o = Vout + row * rc + r0 + lane;
             *o = accumulate ? *o + v : v;
@@ -1859,29 +1858,27 @@ __global__ void multi_rowdot_kernel(const TP* __restrict__ X, int64_t rows, int 
     }
 }
 
-// Y[c][r] += sum_{row in chunk} X[row][c] Win[row][r]   (thread per column; Y zeroed before)
-template <typename TP>
+// Y[c][r] += sum_{row in chunk} X[row][c] Win[row][r]   (thread per column; Y zeroed before;
+// RB = min(rc, 8) right-hand sides per pass)
+template <typename TP, int RB>
 __global__ void multi_coltrans_kernel(const TP* __restrict__ X, int64_t rows, int cols, const double* __restrict__ Win,
                                       double* __restrict__ Y, int rc, int64_t chunk) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= cols) return;
     const int64_t a = (int64_t)blockIdx.y * chunk;
     const int64_t b = min(rows, a + chunk);
-    for (int r0 = 0; r0 < rc; r0 += 8) {
-        const int rw = min(8, rc - r0);
-        double acc[8];
+    for (int r0 = 0; r0 < rc; r0 += RB) {
+        double acc[RB];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+        for (int q = 0; q < RB; ++q) acc[q] = 0.0;
         for (int64_t row = a; row < b; ++row) {
             const double xv = (double)X[row * cols + c];
             const double* wr = Win + row * rc + r0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (q < rw) acc[q] = fma(xv, wr[q], acc[q]);
+            for (int q = 0; q < RB; ++q) acc[q] = fma(xv, wr[q], acc[q]);
         }
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (q < rw) atomicAdd(&Y[(size_t)c * rc + r0 + q], acc[q]);
+        for (int q = 0; q < RB; ++q) atomicAdd(&Y[(size_t)c * rc + r0 + q], acc[q]);
     }
 }
 
@@ -1958,6 +1955,26 @@ __global__ void add_diag_dev_kernel(float* __restrict__ A, int m, int lda, const
     if (i < m) A[(size_t)i * lda + i] += (float)alpha[0];
 }
 
+template <typename TP>
+static void multi_rowdot(cudaStream_t st, const TP* X, int64_t rows, int cols, const double* Vin, double* Vout, int rc,
+                         int accumulate) {
+    const int rb = (int)std::max<int64_t>(1, (rows * 32 + 255) / 256);
+    if (rc == 1) ::ewos::note_launch(), multi_rowdot_kernel<TP, 1><<<rb, 256, 0, st>>>(X, rows, cols, Vin, Vout, rc, accumulate);
+    else if (rc == 2) ::ewos::note_launch(), multi_rowdot_kernel<TP, 2><<<rb, 256, 0, st>>>(X, rows, cols, Vin, Vout, rc, accumulate);
+    else if (rc == 4) ::ewos::note_launch(), multi_rowdot_kernel<TP, 4><<<rb, 256, 0, st>>>(X, rows, cols, Vin, Vout, rc, accumulate);
+    else ::ewos::note_launch(), multi_rowdot_kernel<TP, 8><<<rb, 256, 0, st>>>(X, rows, cols, Vin, Vout, rc, accumulate);
+}
+
+template <typename TP>
+static void multi_coltrans(cudaStream_t st, const TP* X, int64_t rows, int cols, const double* Win, double* Y, int rc) {
+    const int64_t chunk = 512;
+    dim3 grid((unsigned)((cols + 127) / 128), (unsigned)((rows + chunk - 1) / chunk));
+    if (rc == 1) ::ewos::note_launch(), multi_coltrans_kernel<TP, 1><<<grid, 128, 0, st>>>(X, rows, cols, Win, Y, rc, chunk);
+    else if (rc == 2) ::ewos::note_launch(), multi_coltrans_kernel<TP, 2><<<grid, 128, 0, st>>>(X, rows, cols, Win, Y, rc, chunk);
+    else if (rc == 4) ::ewos::note_launch(), multi_coltrans_kernel<TP, 4><<<grid, 128, 0, st>>>(X, rows, cols, Win, Y, rc, chunk);
+    else ::ewos::note_launch(), multi_coltrans_kernel<TP, 8><<<grid, 128, 0, st>>>(X, rows, cols, Win, Y, rc, chunk);
+}
+
 static int64_t bucket_of(int64_t R) {
     int64_t b = 1;
     while (b < R) b <<= 1;
@@ -2014,16 +2031,13 @@ static void residual_multi(const Ctx& C, int64_t rc, int R, const double* nl, in
     const TP* P = (const TP*)C.tb->P;
     const TP* KH = (const TP*)C.tb->KH;
     const int64_t rows = (int64_t)C.E * C.n;
-    const int rb = nblocks(rows * 32);
-    ::ewos::note_launch(), multi_rowdot_kernel<TP><<<rb, 256, 0, C.st>>>(P, rows, (int)C.m, ws->Sb, ws->Vb, (int)rc, 0);
-    ::ewos::note_launch(), multi_rowdot_kernel<TP><<<rb, 256, 0, C.st>>>(KH, rows, (int)C.p, ws->Gb, ws->Vb, (int)rc, 1);
+    multi_rowdot<TP>(C.st, P, rows, (int)C.m, ws->Sb, ws->Vb, (int)rc, 0);
+    multi_rowdot<TP>(C.st, KH, rows, (int)C.p, ws->Gb, ws->Vb, (int)rc, 1);
     (void)R;   // padding columns are processed like the others (zero data); graphs depend on rc only
     ::ewos::note_launch(), formw_multi_kernel<<<nblocks(C.n * rc, 128), 128, 0, C.st>>>(
         (int)C.n, C.D, ws->M, ws->Vb, C.tb->lambda, ws->Fb, nl, nnl, ws->Wb, (int)rc);
     cudaMemsetAsync(ws->Yb, 0, sizeof(double) * C.m * rc, C.st);
-    const int64_t chunk = 512;
-    dim3 grid((unsigned)((C.m + 127) / 128), (unsigned)((rows + chunk - 1) / chunk));
-    ::ewos::note_launch(), multi_coltrans_kernel<TP><<<grid, 128, 0, C.st>>>(P, rows, (int)C.m, ws->Wb, ws->Yb, (int)rc, chunk);
+    multi_coltrans<TP>(C.st, P, rows, (int)C.m, ws->Wb, ws->Yb, (int)rc);
     ::ewos::note_launch(), axpy_dev_kernel<<<nblocks(C.m * rc), 256, 0, C.st>>>(C.m * rc, ws->alpha_dev, ws->Sb, ws->Yb);
 }
 
@@ -2117,9 +2131,8 @@ static ewos_status solve_batched(const Ctx& C, int R, const double* nl, int nnl,
     ::ewos::note_launch(), from_cols_kernel<<<nblocks(C.m * R), 256, 0, C.st>>>(ws->Sb, ws->s, C.m, R, (int)rc);
     const TP* Gm = (const TP*)C.tb->P + (size_t)C.D * C.n * C.m;
     const TP* Hm = (const TP*)C.tb->KH + (size_t)C.D * C.n * C.p;
-    const int rb = nblocks(C.n * 32);
-    ::ewos::note_launch(), multi_rowdot_kernel<TP><<<rb, 256, 0, C.st>>>(Gm, C.n, (int)C.m, ws->Sb, ws->Ub, (int)rc, 0);
-    ::ewos::note_launch(), multi_rowdot_kernel<TP><<<rb, 256, 0, C.st>>>(Hm, C.n, (int)C.p, ws->Gb, ws->Ub, (int)rc, 1);
+    multi_rowdot<TP>(C.st, Gm, C.n, (int)C.m, ws->Sb, ws->Ub, (int)rc, 0);
+    multi_rowdot<TP>(C.st, Hm, C.n, (int)C.p, ws->Gb, ws->Ub, (int)rc, 1);
     ::ewos::note_launch(), from_cols_kernel<<<nblocks(C.n * R), 256, 0, C.st>>>(ws->Ub, ws->u, C.n, R, (int)rc);
     return EWOS_OK;
 }

@@ -52,6 +52,7 @@ struct ewos_toolbox {
     double* lambda = nullptr;        // [n]
     double* x = nullptr;             // [n][d]
     double* z = nullptr;             // [p][d]
+    double* y = nullptr;             // [m][d] V-centres (NULL: y = x)
     int32_t* rec_exit = nullptr;     // [n][N] optional
     int32_t* rec_steps = nullptr;
     void* rec_mass = nullptr;        // T [n][N]

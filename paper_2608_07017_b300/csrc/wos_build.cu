@@ -966,6 +966,7 @@ __global__ void polygon_grid_kernel(const double* __restrict__ V, int nv, double
 
 struct BuildContext {
     DeviceLookup V, Z, V2;       // V2: the V lookup on the alternative grid the autotuner tries
+    DeviceLookup W;              // the nodes' own cells (cell weights) when V-centres are separate
     void* d_sdf = nullptr;
     void* d_xT = nullptr;
     double* d_vtx = nullptr;         // polygon vertices (FP64) for the edge grid
@@ -975,7 +976,7 @@ struct BuildContext {
     unsigned long long* d_stats = nullptr;
     unsigned int* d_counts = nullptr;
     ~BuildContext() {
-        V.release(); Z.release(); V2.release();
+        V.release(); Z.release(); V2.release(); W.release();
         ::ewos::dev_free(d_sdf); ::ewos::dev_free(d_xT); ::ewos::dev_free(d_r0); ::ewos::dev_free(d_counter); ::ewos::dev_free(d_stats); ::ewos::dev_free(d_counts);
         ::ewos::dev_free(d_vtx); ::ewos::dev_free(d_egrid);
     }
@@ -1089,7 +1090,9 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
     const double gf_alt = D == 2 ? 0.5 : 1.0;
     const bool tune_grid = allow_alt && o.lookup_grid_scale <= 0 &&
                            (o.threads_per_block <= 0 || !(o.hash_in_smem == 0 || o.hash_in_smem == 1));
-    ewos_status s = build_lookup<T>(D, d_x, m, lo, hi, hv * gf_default, st, ctx.V, true);
+    // V-centres: y when the caller gives a separate source partition, else the nodes
+    const double* d_v = tb->y ? tb->y : d_x;
+    ewos_status s = build_lookup<T>(D, d_v, m, lo, hi, hv * gf_default, st, ctx.V, true);
     if (s != EWOS_OK) return s;
     s = build_lookup<T>(D, d_z, p, lo, hi, hz, st, ctx.Z, false);
     if (s != EWOS_OK) return s;
@@ -1099,7 +1102,7 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
     bool cached_smem = false;
     const bool have_cached = tune_lookup(key, cached_tpb, cached_smem, cached_grid);
     if (tune_grid && (!have_cached || cached_grid == 1)) {
-        s = build_lookup<T>(D, d_x, m, lo, hi, hv * gf_alt, st, ctx.V2, true);
+        s = build_lookup<T>(D, d_v, m, lo, hi, hv * gf_alt, st, ctx.V2, true);
         if (s != EWOS_OK) return s;
     }
     int e_nx = 0, e_ny = 0;
@@ -1129,25 +1132,33 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
         EWOS_CUDA_TRY(cudaMemcpyAsync(tb->lambda, o.cell_weights, sizeof(double) * n, cudaMemcpyHostToDevice, st));
     } else {
         const int64_t ns = o.cell_samples > 0 ? o.cell_samples : 10000000;
-        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_counts, sizeof(unsigned int) * m));
-        EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counts, 0, sizeof(unsigned int) * m, st));
-        Lookup<T, D> Vv = lookup_view<T, D>(ctx.V);
+        // lambda_i = |W_i| / |D|: the Voronoi cells of the nodes x (a lookup of its own when the
+        // V-centres are separate)
+        if (tb->y) {
+            const double hw = std::pow(vol / n, 1.0 / D) * gf_default;
+            s = build_lookup<T>(D, d_x, n, lo, hi, hw, st, ctx.W, false);
+            if (s != EWOS_OK) return s;
+        }
+        const DeviceLookup& WL = tb->y ? ctx.W : ctx.V;
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_counts, sizeof(unsigned int) * n));
+        EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counts, 0, sizeof(unsigned int) * n, st));
+        Lookup<T, D> Vv = lookup_view<T, D>(WL);
         const T l0 = (T)lo[0], l1 = (T)lo[1], l2 = (T)(D > 2 ? lo[2] : 0);
         const T e0 = (T)(hi[0] - lo[0]), e1 = (T)(hi[1] - lo[1]), e2 = (T)(D > 2 ? hi[2] - lo[2] : 0);
         const uint32_t k0 = (uint32_t)tb->seed, k1 = (uint32_t)(tb->seed >> 32), inst = tb->instance & 0xFFFFu;
-        const size_t sm = sizeof(unsigned int) * m;
+        const size_t sm = sizeof(unsigned int) * n;
         const int blocks = 148 * 4;
         if (dom->kind == SDF_BALL) cudaFuncSetAttribute(cell_count_kernel<T, D, SDF_BALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         else if (dom->kind == SDF_BOX) cudaFuncSetAttribute(cell_count_kernel<T, D, SDF_BOX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         else cudaFuncSetAttribute(cell_count_kernel<T, D, SDF_POLYGON>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (dom->kind == SDF_BALL)
-            ::ewos::note_launch(), cell_count_kernel<T, D, SDF_BALL><<<blocks, 256, sm, st>>>(Vv, m, (const T*)ctx.d_sdf, nsdf, l0, l1, l2, e0, e1, e2, ns, k0, k1, inst, ctx.d_counts);
+            ::ewos::note_launch(), cell_count_kernel<T, D, SDF_BALL><<<blocks, 256, sm, st>>>(Vv, n, (const T*)ctx.d_sdf, nsdf, l0, l1, l2, e0, e1, e2, ns, k0, k1, inst, ctx.d_counts);
         else if (dom->kind == SDF_BOX)
-            ::ewos::note_launch(), cell_count_kernel<T, D, SDF_BOX><<<blocks, 256, sm, st>>>(Vv, m, (const T*)ctx.d_sdf, nsdf, l0, l1, l2, e0, e1, e2, ns, k0, k1, inst, ctx.d_counts);
+            ::ewos::note_launch(), cell_count_kernel<T, D, SDF_BOX><<<blocks, 256, sm, st>>>(Vv, n, (const T*)ctx.d_sdf, nsdf, l0, l1, l2, e0, e1, e2, ns, k0, k1, inst, ctx.d_counts);
         else
-            ::ewos::note_launch(), cell_count_kernel<T, D, SDF_POLYGON><<<blocks, 256, sm, st>>>(Vv, m, (const T*)ctx.d_sdf, nsdf, l0, l1, l2, e0, e1, e2, ns, k0, k1, inst, ctx.d_counts);
+            ::ewos::note_launch(), cell_count_kernel<T, D, SDF_POLYGON><<<blocks, 256, sm, st>>>(Vv, n, (const T*)ctx.d_sdf, nsdf, l0, l1, l2, e0, e1, e2, ns, k0, k1, inst, ctx.d_counts);
         EWOS_CUDA_TRY(cudaGetLastError());
-        ::ewos::note_launch(), counts_to_lambda_kernel<<<1, 1024, 0, st>>>(ctx.d_counts, m, tb->lambda);
+        ::ewos::note_launch(), counts_to_lambda_kernel<<<1, 1024, 0, st>>>(ctx.d_counts, n, tb->lambda);
         EWOS_CUDA_TRY(cudaGetLastError());
     }
     if (ev_cells) EWOS_CUDA_TRY(cudaEventRecord(ev_cells, st));

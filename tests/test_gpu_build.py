@@ -187,3 +187,35 @@ def test_ball8000_full_size_sampled_rows():
     # G 1 = (1 - |x|^2)/6 on the sampled rows, 4 SE (per-walk masses) + the eps-shell bias
     se = np.sqrt(g["walk_mass"][rows].var(1) / w.walks)
     assert np.all(np.abs(g["G"][rows].sum(1) - (1 - (x ** 2).sum(1)) / 6) <= 4 * se + 1e-4 / 3)
+
+
+def test_separate_v_partition_fp64_parity_and_solve():
+    # V-centres y (the source partition of Sec. 2.3) different from the nodes x: m != n
+    x = W.disk_nodes(0.12, 0.9)
+    y = W.disk_nodes(0.17, 0.88) * 0.97
+    z = W.circle_nodes(40)
+    prm = np.array([0.0, 0, 1])
+    N = 500
+    tb = ewos.build_toolbox("ball", 2, prm, x, z, N, 1e-3, seed=4, precision=64, record_walks=True,
+                            cell_samples=200000, y=y)
+    assert tb.n == x.shape[0] and tb.m == y.shape[0] != x.shape[0]
+    g = gpu_arrays(tb, N)
+    assert g["G"].shape == (x.shape[0], y.shape[0])
+    rows = np.arange(0, x.shape[0], 3)
+    orc = oracle.walk_rows(2, "ball", prm, x, z, N, 1e-3, 4, rows=rows, y=y, records=True)
+    rep = compare_rows(g, orc, rows, N, 2, _r0(2, "ball", prm, x[rows]), fp32=False)
+    assert rep["exit_equal"] >= 0.9999, rep
+    # cell weights are those of the nodes' own cells
+    cnt = oracle.cell_counts(2, "ball", prm, x, 200000, seed=4)
+    lam = tb.get("lambda")
+    assert lam.shape == (x.shape[0],) and np.max(np.abs(lam * cnt.sum() - cnt)) <= 2.0
+    # the solve on the m-column toolbox agrees with the oracle's solve of the same matrices
+    from oracle import solve as S
+    pb = W.make_problem("disk", x, z)
+    mats = dict(G=g["G"], gradG=g["gradG"], H=g["H"], gradH=g["gradH"])
+    for mode in ("fp64", "mixed"):
+        u, s, r = tb.solve(pb.A, pb.f, pb.g, mode=mode, want_s=True)
+        ref = S.solve_linear(mats, lam, pb.A, None, None, pb.f, pb.g, alpha=r["alpha"])
+        assert s.shape == (y.shape[0],)
+        assert np.max(np.abs(u - ref["u"])) <= 1e-9 * np.max(np.abs(ref["u"])), mode
+    tb.close()
