@@ -343,7 +343,8 @@ def main():
     def step():
         tb = ewos.build_toolbox("box", 2, w.domain.params, xd, zd, w.walks, w.eps, seed=w.seed, precision=32,
                                 cell_weights=w.lam, stream=sp, on_device=True)
-        _, _, rep = tb.solve(Ad, fd, gd, b=bd, mode=args.mode, on_device=True, out=ud, stream=sp)
+        _, _, rep = tb.solve(Ad, fd, gd, b=bd, mode=args.mode, on_device=True, out=ud, stream=sp,
+                             batched=args.mode == "mixed")
         br = tb.report()
         tb.close()
         return br, rep
@@ -398,7 +399,7 @@ def main():
         t0 = time.perf_counter()
         tb = ewos.build_toolbox("box", 2, w.domain.params, w.x, w.z, w.walks, w.eps, seed=w.seed, precision=32,
                                 cell_weights=w.lam, stream=sp)
-        u_host, _, _ = tb.solve(pb.A, pb.f, pb.g, b=pb.b, mode=args.mode, stream=sp)
+        u_host, _, _ = tb.solve(pb.A, pb.f, pb.g, b=pb.b, mode=args.mode, stream=sp, batched=args.mode == "mixed")
         torch.cuda.synchronize()
         e2e_ms.append(1000 * (time.perf_counter() - t0))
         e2e_steps = tb.report()["steps"]

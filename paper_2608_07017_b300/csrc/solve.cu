@@ -1320,6 +1320,7 @@ struct SolveWorkspace {
     double *Sb = nullptr, *Yb = nullptr, *Vb = nullptr, *Wb = nullptr, *Fb = nullptr, *Gb = nullptr, *Ub = nullptr;
     double *nrm = nullptr, *alpha_dev = nullptr;
     float *D32 = nullptr, *D32p = nullptr;
+    float* F2buf = nullptr;          // hi/lo FP32 pairs of Sb [m][bcap], Gb [p][bcap], Wb [rows][bcap]
     struct Graph {
         const void* tb;
         int64_t rc;
@@ -1346,7 +1347,7 @@ void free_workspace(SolveWorkspace* ws) {
     tc_scratch_free(ws->tc);
     ::ewos::dev_free(ws->Sb); ::ewos::dev_free(ws->Yb); ::ewos::dev_free(ws->Vb); ::ewos::dev_free(ws->Wb);
     ::ewos::dev_free(ws->Fb); ::ewos::dev_free(ws->Gb); ::ewos::dev_free(ws->Ub); ::ewos::dev_free(ws->nrm);
-    ::ewos::dev_free(ws->alpha_dev); ::ewos::dev_free(ws->D32); ::ewos::dev_free(ws->D32p);
+    ::ewos::dev_free(ws->alpha_dev); ::ewos::dev_free(ws->D32); ::ewos::dev_free(ws->D32p); ::ewos::dev_free(ws->F2buf);
     for (auto& g : ws->graphs) cudaGraphExecDestroy(g.exec);
     if (ws->cap_st) cudaStreamDestroy(ws->cap_st);
     delete ws;
@@ -1955,6 +1956,141 @@ __global__ void add_diag_dev_kernel(float* __restrict__ A, int m, int lda, const
     if (i < m) A[(size_t)i * lda + i] += (float)alpha[0];
 }
 
+// ------------------------------------------------------------------ FP64-accurate FP32 products
+// P is FP32 (exact); a FP64 vector s enters as s_hi + s_lo (FP32 pair, s_lo = fp32(s - s_hi):
+// 48 bits of s).  x * s_hi is split exactly into p + pe by one FMA, x * s_lo is second order;
+// partial sums are unevaluated FP32 pairs (hi + lo, by TwoSum) and become FP64 for the final
+// reduction.  A partial sum of k terms is exact to about k * 2^-48 relative, far below the
+// refinement's 1e-10, at the FP32 issue rate (B300 runs FP64 FMAs at 1/64 of it).
+// (the _rn intrinsics keep the compiler from contracting the error-free steps into FMAs)
+__device__ __forceinline__ void f2_add_prod(float& hi, float& lo, float x, float shi, float slo) {
+    const float p = __fmul_rn(x, shi);
+    const float pe = __fmaf_rn(x, shi, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fmaf_rn(x, slo, __fadd_rn(lo, __fadd_rn(err, pe)));
+}
+
+__global__ void split_f2_kernel(const double* __restrict__ v, float* __restrict__ hi, float* __restrict__ lo,
+                                int64_t count) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+        const double d = v[t];
+        const float h = (float)d;
+        hi[t] = h;
+        lo[t] = (float)(d - (double)h);
+    }
+}
+
+// hi/lo pair of v [cols][rc], stored transposed [rc][cols] (coalesced reads in the row products)
+__global__ void split_f2_t_kernel(const double* __restrict__ v, float* __restrict__ hi, float* __restrict__ lo,
+                                  int64_t cols, int rc) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= cols * rc) return;
+    const int64_t c = t / rc;
+    const int r = (int)(t % rc);
+    const double d = v[t];
+    const float h = (float)d;
+    hi[(size_t)r * cols + c] = h;
+    lo[(size_t)r * cols + c] = (float)(d - (double)h);
+}
+
+// Vout[row][r] (+)= sum_c X[row][c] V[c][r] with V = Vhi + Vlo given as [rc][cols]   (warp per
+// row; lanes walk the columns, so every load is coalesced)
+template <int RB>
+__global__ void multi_rowdot_f2_kernel(const float* __restrict__ X, int64_t rows, int cols, const float* __restrict__ Vhi,
+                                       const float* __restrict__ Vlo, double* __restrict__ Vout, int rc, int accumulate) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const float* xr = X + row * cols;
+    for (int r0 = 0; r0 < rc; r0 += RB) {
+        float hi[RB], lo[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) hi[q] = lo[q] = 0.f;
+        for (int c = lane; c < cols; c += 32) {
+            const float xv = xr[c];
+#pragma unroll
+            for (int q = 0; q < RB; ++q)
+                f2_add_prod(hi[q], lo[q], xv, Vhi[(size_t)(r0 + q) * cols + c], Vlo[(size_t)(r0 + q) * cols + c]);
+        }
+        double acc[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) {
+            acc[q] = (double)hi[q] + (double)lo[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        }
+        if (lane < RB) {
+            double v = acc[0];
+#pragma unroll
+            for (int q = 1; q < RB; ++q)
+                if (lane == q) v = acc[q];
+            double* o = Vout + row * rc + r0 + lane;
+            *o = accumulate ? *o + v : v;
+        }
+    }
+}
+
+// Y[c][r] += sum_{row in chunk} X[row][c] W[row][r] with W = Whi + Wlo   (thread per column)
+template <int RB>
+__global__ void multi_coltrans_f2_kernel(const float* __restrict__ X, int64_t rows, int cols, const float* __restrict__ Whi,
+                                         const float* __restrict__ Wlo, double* __restrict__ Y, int rc, int64_t chunk) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    const int64_t a = (int64_t)blockIdx.y * chunk;
+    const int64_t b = min(rows, a + chunk);
+    for (int r0 = 0; r0 < rc; r0 += RB) {
+        float hi[RB], lo[RB];
+#pragma unroll
+        for (int q = 0; q < RB; ++q) hi[q] = lo[q] = 0.f;
+        for (int64_t row = a; row < b; ++row) {
+            const float xv = X[row * cols + c];
+            float wh[RB], wl[RB];
+            if (RB >= 4) {
+#pragma unroll
+                for (int q = 0; q < RB; q += 4) {
+                    const float4 h4 = *reinterpret_cast<const float4*>(Whi + row * rc + r0 + q);
+                    const float4 l4 = *reinterpret_cast<const float4*>(Wlo + row * rc + r0 + q);
+                    wh[q] = h4.x; wh[q + 1] = h4.y; wh[q + 2] = h4.z; wh[q + 3] = h4.w;
+                    wl[q] = l4.x; wl[q + 1] = l4.y; wl[q + 2] = l4.z; wl[q + 3] = l4.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < RB; ++q) { wh[q] = Whi[row * rc + r0 + q]; wl[q] = Wlo[row * rc + r0 + q]; }
+            }
+#pragma unroll
+            for (int q = 0; q < RB; ++q) f2_add_prod(hi[q], lo[q], xv, wh[q], wl[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < RB; ++q) atomicAdd(&Y[(size_t)c * rc + r0 + q], (double)hi[q] + (double)lo[q]);
+    }
+}
+
+static void multi_rowdot_f2(cudaStream_t st, const float* X, int64_t rows, int cols, const float* Vhi, const float* Vlo,
+                            double* Vout, int rc, int accumulate) {
+    const int rb = (int)std::max<int64_t>(1, (rows * 32 + 255) / 256);
+    if (rc == 1) ::ewos::note_launch(), multi_rowdot_f2_kernel<1><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
+    else if (rc == 2) ::ewos::note_launch(), multi_rowdot_f2_kernel<2><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
+    else if (rc == 4) ::ewos::note_launch(), multi_rowdot_f2_kernel<4><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
+    else ::ewos::note_launch(), multi_rowdot_f2_kernel<8><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
+}
+
+static void multi_coltrans_f2(cudaStream_t st, const float* X, int64_t rows, int cols, const float* Whi, const float* Wlo,
+                              double* Y, int rc) {
+    const int64_t chunk = 512;
+    dim3 grid((unsigned)((cols + 127) / 128), (unsigned)((rows + chunk - 1) / chunk));
+    if (rc == 1) ::ewos::note_launch(), multi_coltrans_f2_kernel<1><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
+    else if (rc == 2) ::ewos::note_launch(), multi_coltrans_f2_kernel<2><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
+    else if (rc == 4) ::ewos::note_launch(), multi_coltrans_f2_kernel<4><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
+    else ::ewos::note_launch(), multi_coltrans_f2_kernel<8><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
+}
+
+static void split_f2(cudaStream_t st, const double* v, float* hi, float* lo, int64_t count) {
+    ::ewos::note_launch(), split_f2_kernel<<<(int)std::min<int64_t>(4096, (count + 255) / 256), 256, 0, st>>>(v, hi, lo, count);
+}
+
 template <typename TP>
 static void multi_rowdot(cudaStream_t st, const TP* X, int64_t rows, int cols, const double* Vin, double* Vout, int rc,
                          int accumulate) {
@@ -2005,8 +2141,9 @@ static ewos_status ensure_batched(const Ctx& C, int64_t rc) {
     ws->graphs.clear();
     ::ewos::dev_free(ws->Sb); ::ewos::dev_free(ws->Yb); ::ewos::dev_free(ws->Vb); ::ewos::dev_free(ws->Wb);
     ::ewos::dev_free(ws->Fb); ::ewos::dev_free(ws->Gb); ::ewos::dev_free(ws->Ub); ::ewos::dev_free(ws->nrm);
-    ::ewos::dev_free(ws->D32); ::ewos::dev_free(ws->D32p);
+    ::ewos::dev_free(ws->D32); ::ewos::dev_free(ws->D32p); ::ewos::dev_free(ws->F2buf);
     const int64_t rows = (int64_t)C.E * C.n;
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->F2buf, sizeof(float) * 2 * (C.m + C.p + rows) * rc));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Sb, sizeof(double) * C.m * rc));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Yb, sizeof(double) * C.m * rc));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Vb, sizeof(double) * rows * rc));
@@ -2031,13 +2168,31 @@ static void residual_multi(const Ctx& C, int64_t rc, int R, const double* nl, in
     const TP* P = (const TP*)C.tb->P;
     const TP* KH = (const TP*)C.tb->KH;
     const int64_t rows = (int64_t)C.E * C.n;
-    multi_rowdot<TP>(C.st, P, rows, (int)C.m, ws->Sb, ws->Vb, (int)rc, 0);
-    multi_rowdot<TP>(C.st, KH, rows, (int)C.p, ws->Gb, ws->Vb, (int)rc, 1);
+    float* Shi = ws->F2buf;
+    float* Slo = Shi + C.m * rc;
+    float* Ghi = Slo + C.m * rc;
+    float* Glo = Ghi + C.p * rc;
+    float* Whi = Glo + C.p * rc;
+    float* Wlo = Whi + rows * rc;
+    if (sizeof(TP) == 4) {
+        ::ewos::note_launch(), split_f2_t_kernel<<<nblocks(C.m * rc), 256, 0, C.st>>>(ws->Sb, Shi, Slo, C.m, (int)rc);
+        ::ewos::note_launch(), split_f2_t_kernel<<<nblocks(C.p * rc), 256, 0, C.st>>>(ws->Gb, Ghi, Glo, C.p, (int)rc);
+        multi_rowdot_f2(C.st, (const float*)P, rows, (int)C.m, Shi, Slo, ws->Vb, (int)rc, 0);
+        multi_rowdot_f2(C.st, (const float*)KH, rows, (int)C.p, Ghi, Glo, ws->Vb, (int)rc, 1);
+    } else {
+        multi_rowdot<TP>(C.st, P, rows, (int)C.m, ws->Sb, ws->Vb, (int)rc, 0);
+        multi_rowdot<TP>(C.st, KH, rows, (int)C.p, ws->Gb, ws->Vb, (int)rc, 1);
+    }
     (void)R;   // padding columns are processed like the others (zero data); graphs depend on rc only
     ::ewos::note_launch(), formw_multi_kernel<<<nblocks(C.n * rc, 128), 128, 0, C.st>>>(
         (int)C.n, C.D, ws->M, ws->Vb, C.tb->lambda, ws->Fb, nl, nnl, ws->Wb, (int)rc);
     cudaMemsetAsync(ws->Yb, 0, sizeof(double) * C.m * rc, C.st);
-    multi_coltrans<TP>(C.st, P, rows, (int)C.m, ws->Wb, ws->Yb, (int)rc);
+    if (sizeof(TP) == 4) {
+        split_f2(C.st, ws->Wb, Whi, Wlo, rows * rc);
+        multi_coltrans_f2(C.st, (const float*)P, rows, (int)C.m, Whi, Wlo, ws->Yb, (int)rc);
+    } else {
+        multi_coltrans<TP>(C.st, P, rows, (int)C.m, ws->Wb, ws->Yb, (int)rc);
+    }
     ::ewos::note_launch(), axpy_dev_kernel<<<nblocks(C.m * rc), 256, 0, C.st>>>(C.m * rc, ws->alpha_dev, ws->Sb, ws->Yb);
 }
 
