@@ -1017,6 +1017,9 @@ static ewos_status lu_factor_device(T* A, int m, int lda, LuScratch& S, cudaStre
 constexpr int kNpThreads = 256;
 constexpr int kNpLd = kNB + 4;   // 16-byte aligned rows; a warp's 32 columns hit distinct banks
 
+// max that keeps a NaN (fmax drops it): a NaN multiplier must reject the unpivoted factors
+__device__ __forceinline__ double nanmax(double m, double v) { return (v > m || v != v) ? v : m; }
+
 template <typename T>
 constexpr size_t nopiv_smem() { return sizeof(T) * (kNB * kNpLd + kNB * kNB + kNB); }
 
@@ -1061,23 +1064,24 @@ struct TailLoop<T, kNB> {
     __device__ __forceinline__ static void low(T (&)[kNB], const T*) {}
 };
 
+// Diagonal block of one panel, factored with the diagonal pivots by one CTA in shared memory
+// (4 threads per column, right-looking, multipliers formed on the fly; column j is scaled at the
+// end).  Writes the factored block to diag_out (the matrix keeps the original block until the
+// end of the factorisation: the triangular-solve CTAs of this panel still read it there).
 template <typename T>
-__global__ void __launch_bounds__(kNpThreads) lu_panel_nopiv_kernel(T* __restrict__ A, int lda, int m, int kb, int nb,
+__global__ void __launch_bounds__(kNpThreads) lu_diag_factor_kernel(const T* __restrict__ A, int lda, int kb, int nb,
                                                                     T* __restrict__ diag_out,
                                                                     GridBarrier* __restrict__ bar) {
     extern __shared__ __align__(16) unsigned char np_sm[];
-    T* D = reinterpret_cast<T*>(np_sm);            // [64][kNpLd] diagonal block: L below, U on and above
-    T* Lt = D + kNB * kNpLd;                       // [64][64] Lt[k][i] = L_ik (i > k), else 0
-    T* rU = Lt + kNB * kNB;                        // [64] reciprocal pivots
-    const int tid = threadIdx.x, c = tid & (kNB - 1), q = tid >> 6;   // 4 threads per column
+    T* D = reinterpret_cast<T*>(np_sm);            // [64][kNpLd]
+    T* rU = D + kNB * kNpLd + kNB * kNB;           // [64]
+    const int tid = threadIdx.x, c = tid & (kNB - 1), q = tid >> 6;
     constexpr int kQ = kNpThreads / kNB;
     double mx = 0.0;
     int zero = 0;
-    // identity beyond nb
     for (int i = q; i < kNB; i += kQ)
         D[i * kNpLd + c] = (i < nb && c < nb) ? A[(size_t)(kb + i) * lda + kb + c] : (i == c ? T(1) : T(0));
     __syncthreads();
-    // right-looking elimination, multipliers formed on the fly; column j is scaled at the end
     for (int j = 0; j < kNB; ++j) {
         const T piv = D[j * kNpLd + j];
         const T r = piv != T(0) ? T(1) / piv : T(0);
@@ -1091,23 +1095,45 @@ __global__ void __launch_bounds__(kNpThreads) lu_panel_nopiv_kernel(T* __restric
     for (int i = c + 1 + q; i < kNB; i += kQ) {
         const T l = D[i * kNpLd + c] * rU[c];
         D[i * kNpLd + c] = l;
-        mx = fmax(mx, fabs((double)l));
+        mx = nanmax(mx, fabs((double)l));
     }
     __syncthreads();
-    for (int t = tid; t < kNB * kNB; t += kNpThreads) {
-        const int k = t >> 6, i = t & 63;
-        Lt[k * kNB + i] = i > k ? D[i * kNpLd + k] : T(0);
-    }
-    const int rest = m - kb - nb;
-    const int nbl = (rest + kNpThreads - 1) / kNpThreads;
-    if (blockIdx.x == 0) {
-        for (int t = tid; t < nb * nb; t += kNpThreads) diag_out[t] = D[(t / nb) * kNpLd + t % nb];
-        if (zero) bar->singular = 1;
+    for (int t = tid; t < kNB * kNB; t += kNpThreads) diag_out[t] = D[(t >> 6) * kNpLd + (t & 63)];
+    if (tid == 0 && zero) bar->singular = 1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = nanmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0 && (mx > 0.0 || mx != mx)) atomicMax(&bar->maxl_bits, (unsigned long long)__double_as_longlong(mx));
+}
+
+// L21 = A21 U11^-1 (a thread per row) and U12 = L11^-1 A12 (a thread per column) of one panel,
+// from the factored diagonal block (64-thread CTAs: the first half of the grid does rows, the
+// second columns); tracks the largest |l| of L21.
+constexpr int kTrsmThreads = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(kTrsmThreads) lu_panel_trsm_kernel(T* __restrict__ A, int lda, int m, int kb,
+                                                                     const T* __restrict__ diag,
+                                                                     GridBarrier* __restrict__ bar) {
+    extern __shared__ __align__(16) unsigned char np_sm[];
+    T* D = reinterpret_cast<T*>(np_sm);            // [64][kNpLd]
+    T* Lt = D + kNB * kNpLd;                       // [64][64]
+    T* rU = Lt + kNB * kNB;                        // [64]
+    const int tid = threadIdx.x;
+    const int rest = m - kb - kNB;
+    const int nbl = (rest + kTrsmThreads - 1) / kTrsmThreads;
+    const bool rows = blockIdx.x < nbl;
+    for (int t = tid; t < kNB * kNB; t += kTrsmThreads) {
+        const int i = t >> 6, k = t & 63;
+        const T v = diag[t];
+        D[i * kNpLd + k] = v;
+        Lt[k * kNB + i] = i > k ? v : T(0);
     }
     __syncthreads();
-    if (rest > 0 && blockIdx.x < nbl) {
-        // L21 rows: x U11 = a  (nb == 64 whenever rows remain below the block)
-        const int i = kb + nb + blockIdx.x * kNpThreads + tid;
+    if (tid < kNB) rU[tid] = T(1) / D[tid * kNpLd + tid];
+    __syncthreads();
+    double mx = 0.0;
+    if (rows) {
+        const int i = kb + kNB + blockIdx.x * kTrsmThreads + tid;
         if (i < m) {
             T x[kNB];
             const T* src = A + (size_t)i * lda + kb;
@@ -1118,12 +1144,11 @@ __global__ void __launch_bounds__(kNpThreads) lu_panel_nopiv_kernel(T* __restric
 #pragma unroll
             for (int cc = 0; cc < kNB; ++cc) {
                 dst[cc] = x[cc];
-                mx = fmax(mx, fabs((double)x[cc]));
+                mx = nanmax(mx, fabs((double)x[cc]));
             }
         }
-    } else if (rest > 0 && blockIdx.x < 2 * nbl) {
-        // U12 columns: L11 y = a  (unit lower)
-        const int col = kb + nb + (blockIdx.x - nbl) * kNpThreads + tid;
+    } else {
+        const int col = kb + kNB + (blockIdx.x - nbl) * kTrsmThreads + tid;
         if (col < m) {
             T y[kNB];
 #pragma unroll
@@ -1134,16 +1159,15 @@ __global__ void __launch_bounds__(kNpThreads) lu_panel_nopiv_kernel(T* __restric
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    // non-negative doubles (and NaN, as a large pattern) order like their bit patterns
-    if ((tid & 31) == 0 && mx > 0.0) atomicMax(&bar->maxl_bits, (unsigned long long)__double_as_longlong(mx));
+    for (int o = 16; o > 0; o >>= 1) mx = nanmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0 && (mx > 0.0 || mx != mx)) atomicMax(&bar->maxl_bits, (unsigned long long)__double_as_longlong(mx));
 }
 
 template <typename T>
 __global__ void diag_writeback_kernel(T* __restrict__ A, int lda, int m, const T* __restrict__ diag) {
     const int t = blockIdx.x, kb = t * kNB, nb = min(kNB, m - kb);
-    const T* d = diag + (size_t)t * kNB * kNB;
-    for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) A[(size_t)(kb + q / nb) * lda + kb + q % nb] = d[q];
+    const T* d = diag + (size_t)t * kNB * kNB;      // [64][64] (rows and columns beyond nb unused)
+    for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) A[(size_t)(kb + q / nb) * lda + kb + q % nb] = d[(q / nb) * kNB + q % nb];
 }
 
 __global__ void iota_kernel(int* __restrict__ v, int m) {
@@ -1158,8 +1182,11 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(lu_panel_nopiv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        attr = cudaFuncSetAttribute(lu_diag_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)nopiv_smem<T>());
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(lu_panel_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)nopiv_smem<T>());
     });
     EWOS_CUDA_TRY(attr);
     EWOS_CUDA_TRY(cudaMemsetAsync(S.bar, 0, sizeof(GridBarrier), st));
@@ -1167,9 +1194,13 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
     for (int kb = 0; kb < m; kb += kNB) {
         const int nb = std::min(kNB, m - kb);
         const int rest = m - kb - nb;
-        const int nbl = (rest + kNpThreads - 1) / kNpThreads;
-        ::ewos::note_launch(), lu_panel_nopiv_kernel<T><<<std::max(1, 2 * nbl), kNpThreads, nopiv_smem<T>(), st>>>(
-            A, lda, m, kb, nb, diagb + (size_t)(kb / kNB) * kNB * kNB, S.bar);
+        T* dblk = diagb + (size_t)(kb / kNB) * kNB * kNB;
+        ::ewos::note_launch(), lu_diag_factor_kernel<T><<<1, kNpThreads, nopiv_smem<T>(), st>>>(A, lda, kb, nb, dblk, S.bar);
+        if (rest > 0) {
+            // nb == 64 whenever rows remain below the diagonal block
+            const int nbl = (rest + kTrsmThreads - 1) / kTrsmThreads;
+            ::ewos::note_launch(), lu_panel_trsm_kernel<T><<<2 * nbl, kTrsmThreads, nopiv_smem<T>(), st>>>(A, lda, m, kb, dblk, S.bar);
+        }
         if (rest > 0)
             gemm_trailing<T>(st, rest, rest, nb, A + (size_t)(kb + nb) * lda + kb, lda,
                              A + (size_t)kb * lda + kb + nb, lda, A + (size_t)(kb + nb) * lda + kb + nb, lda);
