@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
                                                            const __grid_constant__ CUtensorMap mapAl,
                                                            const __grid_constant__ CUtensorMap mapBl, int M, int N,
                                                            int Kp, float* __restrict__ C, int64_t ldc,
-                                                           int* __restrict__ err) {
+                                                           int* __restrict__ err, int sub) {
     using CF = Cfg<SPLIT>;
     constexpr int BN = CF::BN, STAGES = CF::STAGES, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
     constexpr int STAGE_BYTES = CF::STAGE_BYTES;
@@ -206,14 +206,20 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
             const int col0 = n0 + c * 32;
             if (row < M) {
                 float* cp = C + (int64_t)row * ldc + col0;
-                if (col0 + 32 <= N && (ldc & 3) == 0) {
+                if (col0 + 32 <= N && (ldc & 3) == 0 && ((reinterpret_cast<uintptr_t>(cp) & 15) == 0)) {
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        reinterpret_cast<float4*>(cp)[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
-                                                                      __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+                    for (int q = 0; q < 8; ++q) {
+                        float4 o = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                               __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+                        if (sub) {
+                            const float4 c4 = reinterpret_cast<const float4*>(cp)[q];
+                            o = make_float4(c4.x - o.x, c4.y - o.y, c4.z - o.z, c4.w - o.w);
+                        }
+                        reinterpret_cast<float4*>(cp)[q] = o;
+                    }
                 } else {
                     for (int q = 0; q < 32; ++q)
-                        if (col0 + q < N) cp[q] = __uint_as_float(v[q]);
+                        if (col0 + q < N) cp[q] = sub ? cp[q] - __uint_as_float(v[q]) : __uint_as_float(v[q]);
                 }
             }
         }
@@ -261,6 +267,47 @@ __global__ void transpose_split_kernel(const float* __restrict__ in, int K, int 
             const float h = isfinite(v) ? __uint_as_float(hb) : v;
             hi[(int64_t)c * Kp + k] = h;
             lo[(int64_t)c * Kp + k] = v - h;
+        }
+    }
+}
+
+__device__ __forceinline__ void tf32_split(float v, float& h, float& l) {
+    const uint32_t b = __float_as_uint(v);
+    const uint32_t hb = (b + 0x0FFFu + ((b >> 13) & 1u)) & 0xFFFFE000u;
+    h = isfinite(v) ? __uint_as_float(hb) : v;
+    l = v - h;
+}
+
+// hi/lo [M][Kp] from a row-major [M][K] operand with row stride ld (K contiguous), zero padding
+__global__ void rows_split_kernel(const float* __restrict__ in, int64_t ld, int M, int K, float* __restrict__ hi,
+                                  float* __restrict__ lo, int Kp) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)M * Kp) return;
+    const int64_t i = t / Kp;
+    const int k = (int)(t % Kp);
+    float h = 0.f, l = 0.f;
+    if (k < K) tf32_split(in[i * ld + k], h, l);
+    hi[t] = h;
+    lo[t] = l;
+}
+
+// hi/lo [N][Kp] = transpose of a row-major [K][N] operand with row stride ld
+__global__ void cols_split_kernel(const float* __restrict__ in, int64_t ld, int K, int N, float* __restrict__ hi,
+                                  float* __restrict__ lo, int Kp) {
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int k = k0 + r, c = c0 + threadIdx.x;
+        tile[r][threadIdx.x] = (k < K && c < N) ? in[(int64_t)k * ld + c] : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int c = c0 + r, k = k0 + threadIdx.x;
+        if (c < N && k < Kp) {
+            float h, l;
+            tf32_split(tile[threadIdx.x][r], h, l);
+            hi[(int64_t)c * Kp + k] = h;
+            lo[(int64_t)c * Kp + k] = l;
         }
     }
 }
@@ -376,10 +423,10 @@ static ewos_status tc_enqueue(tc::Scratch& S, const float* Akm, const float* Bkm
     dim3 grid((N + bn - 1) / bn, (M + BM - 1) / BM);
     if (split) {
         EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<true>::SMEM_BYTES));
-        ::ewos::note_launch(), gemm_tf32_kernel<true><<<grid, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err);
+        ::ewos::note_launch(), gemm_tf32_kernel<true><<<grid, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err, 0);
     } else {
         EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<false>::SMEM_BYTES));
-        ::ewos::note_launch(), gemm_tf32_kernel<false><<<grid, 128, Cfg<false>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err);
+        ::ewos::note_launch(), gemm_tf32_kernel<false><<<grid, 128, Cfg<false>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err, 0);
     }
     EWOS_CUDA_TRY(cudaGetLastError());
     return EWOS_OK;
@@ -391,6 +438,65 @@ static ewos_status tc_check(tc::Scratch& S, cudaStream_t st) {
     EWOS_CUDA_TRY(cudaStreamSynchronize(st));
     if (herr) {
         set_error("tensor-core assembly: a pipeline wait timed out");
+        return EWOS_ETIMEOUT;
+    }
+    return EWOS_OK;
+}
+
+// C [M][N] (row stride ldc) -= A B for a row-major A [M][K] (stride lda) and B [K][N] (stride
+// ldb): the LU's trailing update on the tensor cores (three TF32 products).  Enqueued only; a
+// pipeline timeout sets the scratch's error word, which tc_update_check reads (and clears).
+ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int M,
+                              int N, int K, cudaStream_t st, TcScratch** owned) {
+    using namespace tc;
+    if (!*owned) *owned = new TcScratch();
+    Scratch& S = (*owned)->s;
+    const int Kp = (K + BK - 1) / BK * BK;
+    const size_t need = (size_t)std::max(M, N) * Kp;
+    if (S.cap < need || !S.Atl) {
+        ::ewos::dev_free(S.At); ::ewos::dev_free(S.Bt); ::ewos::dev_free(S.Atl); ::ewos::dev_free(S.Btl);
+        S.At = S.Bt = S.Atl = S.Btl = nullptr;
+        S.cap = 0;
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.At, sizeof(float) * need));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Bt, sizeof(float) * need));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Atl, sizeof(float) * need));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Btl, sizeof(float) * need));
+        S.cap = need;
+    }
+    if (!S.err) {
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.err, sizeof(int)));
+        EWOS_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
+    }
+    const int64_t na = (int64_t)M * Kp;
+    ::ewos::note_launch(), rows_split_kernel<<<(int)((na + 255) / 256), 256, 0, st>>>(A, lda, M, K, S.At, S.Atl, Kp);
+    ::ewos::note_launch(), cols_split_kernel<<<dim3((N + 31) / 32, (Kp + 31) / 32), dim3(32, 8), 0, st>>>(B, ldb, K, N, S.Bt, S.Btl, Kp);
+    constexpr int bn = Cfg<true>::BN;
+    CUtensorMap ma, mb, mal, mbl;
+    if (!(make_map(&ma, S.At, M, Kp, BM) && make_map(&mb, S.Bt, N, Kp, bn) && make_map(&mal, S.Atl, M, Kp, BM) &&
+          make_map(&mbl, S.Btl, N, Kp, bn))) {
+        set_error("tensor-core update: cuTensorMapEncodeTiled failed");
+        return EWOS_ECUDA;
+    }
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<true>::SMEM_BYTES);
+    });
+    EWOS_CUDA_TRY(attr);
+    dim3 grid((N + bn - 1) / bn, (M + BM - 1) / BM);
+    ::ewos::note_launch(), gemm_tf32_kernel<true><<<grid, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, ldc, S.err, 1);
+    EWOS_CUDA_TRY(cudaGetLastError());
+    return EWOS_OK;
+}
+
+ewos_status tc_update_check(TcScratch* t, cudaStream_t st) {
+    if (!t || !t->s.err) return EWOS_OK;
+    int herr = 0;
+    EWOS_CUDA_TRY(cudaMemcpyAsync(&herr, t->s.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr) {
+        cudaMemsetAsync(t->s.err, 0, sizeof(int), st);
+        set_error("tensor-core update: a pipeline wait timed out");
         return EWOS_ETIMEOUT;
     }
     return EWOS_OK;

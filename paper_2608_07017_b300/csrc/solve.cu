@@ -71,6 +71,10 @@ struct TcScratch;   // mixed.cu: operand transposes of one caller
 void tc_scratch_free(TcScratch* t);
 ewos_status tc_assemble(const float* A_km, const float* B_km, float* C, int M, int N, int K, cudaStream_t st,
                         bool split, TcScratch** owned);
+ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int M,
+                              int N, int K, cudaStream_t st, TcScratch** owned);
+ewos_status tc_update_check(TcScratch* t, cudaStream_t st);
+bool tc_assemble_available();
 
 // ------------------------------------------------------------------ small kernels
 __global__ void coef_kernel(int n, int D, const double* __restrict__ lam, const double* __restrict__ A,
@@ -1177,8 +1181,13 @@ __global__ void iota_kernel(int* __restrict__ v, int m) {
 
 // Returns EWOS_OK with *accepted false when a multiplier exceeds 1 or a pivot is zero (the
 // caller then refactors the original matrix with interchanges).
+// Trailing updates of at least this many rows go to the tensor cores (FP32 factors, three TF32
+// products); smaller ones stay on the FP32 SIMT GEMM.
+constexpr int kTcUpdateMin = 256;
+
 template <typename T>
-static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStream_t st, bool* accepted) {
+static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStream_t st, bool* accepted,
+                                   TcScratch** tc = nullptr) {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
@@ -1201,9 +1210,22 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
             const int nbl = (rest + kTrsmThreads - 1) / kTrsmThreads;
             ::ewos::note_launch(), lu_panel_trsm_kernel<T><<<2 * nbl, kTrsmThreads, nopiv_smem<T>(), st>>>(A, lda, m, kb, dblk, S.bar);
         }
-        if (rest > 0)
-            gemm_trailing<T>(st, rest, rest, nb, A + (size_t)(kb + nb) * lda + kb, lda,
-                             A + (size_t)kb * lda + kb + nb, lda, A + (size_t)(kb + nb) * lda + kb + nb, lda);
+        if (rest > 0) {
+            if (std::is_same<T, float>::value && tc && rest >= kTcUpdateMin) {
+                ewos_status e = tc_update_enqueue(reinterpret_cast<const float*>(A + (size_t)(kb + nb) * lda + kb), lda,
+                                                  reinterpret_cast<const float*>(A + (size_t)kb * lda + kb + nb), lda,
+                                                  reinterpret_cast<float*>(A + (size_t)(kb + nb) * lda + kb + nb), lda,
+                                                  rest, rest, nb, st, tc);
+                if (e != EWOS_OK) return e;
+            } else {
+                gemm_trailing<T>(st, rest, rest, nb, A + (size_t)(kb + nb) * lda + kb, lda,
+                                 A + (size_t)kb * lda + kb + nb, lda, A + (size_t)(kb + nb) * lda + kb + nb, lda);
+            }
+        }
+    }
+    if (tc && *tc) {
+        ewos_status e = tc_update_check(*tc, st);
+        if (e != EWOS_OK) return e;
     }
     const int nbk = (m + kNB - 1) / kNB;
     ::ewos::note_launch(), diag_writeback_kernel<T><<<nbk, 256, 0, st>>>(A, lda, m, diagb);
@@ -1807,7 +1829,8 @@ static ewos_status factor32_with(const Ctx& C, Build build, int pivoting, ewos_s
     ++rep->factorizations;
     if (pivoting == 0) {
         bool accepted = false;
-        ewos_status s = lu_factor_nopiv<float>(C.ws->LU32, (int)C.m, (int)C.m, C.ws->lu, C.st, &accepted);
+        ewos_status s = lu_factor_nopiv<float>(C.ws->LU32, (int)C.m, (int)C.m, C.ws->lu, C.st, &accepted,
+                                               tc_assemble_available() ? &C.ws->tc : nullptr);
         if (s != EWOS_OK) return s;
         if (accepted) return EWOS_OK;
         build();
