@@ -17,6 +17,9 @@ static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void unnote_launches(unsigned long long k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
+static std::atomic<uint64_t> g_toolbox_serial{0};
+uint64_t next_toolbox_serial() { return g_toolbox_serial.fetch_add(1, std::memory_order_relaxed) + 1; }
 
 static thread_local cudaStream_t g_alloc_stream = nullptr;
 void set_alloc_stream(cudaStream_t s) { g_alloc_stream = s; }

@@ -50,7 +50,11 @@ struct ServerSlot {
     cudaStream_t st = nullptr;
     SolveWorkspace* ws = nullptr;
     size_t charged = 0;           // bytes of the budget this slot's workspace holds
-    const ewos_toolbox* shape_of = nullptr;
+    // shape of the toolboxes the workspace was made for, by value (the toolbox itself may be
+    // destroyed while the workspace stays with the slot)
+    bool has_shape = false;
+    int64_t n = 0, m = 0, p = 0;
+    int dim = 0;
     int64_t cap_rhs = 0;
     bool mixed = false, fp64 = false;
     bool busy = false;
@@ -89,11 +93,13 @@ static void run_request(ewos_server* sv, ServerSlot* sl, ServerRequest* rq) {
     if (rq->status != EWOS_OK) rq->err = ewos_last_error();   // the worker's message, for the waiter
 }
 
+static bool same_shape(const ServerSlot* sl, const ewos_toolbox* tb) {
+    return sl->ws && sl->has_shape && sl->n == tb->n && sl->m == tb->m && sl->p == tb->p && sl->dim == tb->dim;
+}
+
 static bool slot_fits(const ServerSlot* sl, const ServerRequest* rq) {
-    const ewos_toolbox* tb = rq->tb;
     const bool mixed = rq->pb.mode == EWOS_SOLVE_MIXED;
-    return sl->ws && sl->shape_of && sl->shape_of->n == tb->n && sl->shape_of->m == tb->m && sl->shape_of->p == tb->p &&
-           sl->shape_of->dim == tb->dim && sl->cap_rhs >= rq->pb.nrhs && (mixed ? sl->mixed : sl->fp64);
+    return same_shape(sl, rq->tb) && sl->cap_rhs >= rq->pb.nrhs && (mixed ? sl->mixed : sl->fp64);
 }
 
 // Frees the workspace of an idle slot (called with sv->mu held; the slot cannot start work
@@ -109,7 +115,7 @@ static void reclaim(ewos_server* sv, ServerSlot* o) {
     o->ws = nullptr;
     sv->charged -= o->charged;
     o->charged = 0;
-    o->shape_of = nullptr;
+    o->has_shape = false;
     o->cap_rhs = 0;
     o->mixed = o->fp64 = false;
 }
@@ -122,11 +128,10 @@ static int admit(ewos_server* sv, ServerSlot* sl, ServerRequest* rq) {
         if (o != sl && !o->busy && slot_fits(o, rq)) return 2;     // an idle slot can take it as it is
     const bool mixed = rq->pb.mode == EWOS_SOLVE_MIXED;
     const ewos_toolbox* tb = rq->tb;
-    const bool same_shape = sl->ws && sl->shape_of && sl->shape_of->n == tb->n && sl->shape_of->m == tb->m &&
-                            sl->shape_of->p == tb->p && sl->shape_of->dim == tb->dim;
-    const int64_t cap = std::max<int64_t>(rq->pb.nrhs, same_shape ? sl->cap_rhs : 0);
-    const bool want_mixed = mixed || (same_shape && sl->mixed);
-    const bool want_fp64 = !mixed || (same_shape && sl->fp64);
+    const bool same = same_shape(sl, tb);
+    const int64_t cap = std::max<int64_t>(rq->pb.nrhs, same ? sl->cap_rhs : 0);
+    const bool want_mixed = mixed || (same && sl->mixed);
+    const bool want_fp64 = !mixed || (same && sl->fp64);
     const size_t need = (want_mixed ? workspace_bytes(tb, cap, true) : 0) + (want_fp64 ? workspace_bytes(tb, cap, false) : 0);
     if (need > sv->budget) return -1;
     // room from the workspaces of idle slots when the budget is short
@@ -138,7 +143,8 @@ static int admit(ewos_server* sv, ServerSlot* sl, ServerRequest* rq) {
         // the slot's old workspace is released or grown by the solve; the new estimate is charged
         sv->charged = sv->charged - sl->charged + need;
         sl->charged = need;
-        sl->shape_of = tb;
+        sl->has_shape = true;
+        sl->n = tb->n; sl->m = tb->m; sl->p = tb->p; sl->dim = tb->dim;
         sl->cap_rhs = cap;
         sl->mixed = want_mixed;
         sl->fp64 = want_fp64;

@@ -1375,7 +1375,7 @@ struct SolveWorkspace {
     float *D32 = nullptr, *D32p = nullptr;
     float* F2buf = nullptr;          // hi/lo FP32 pairs of Sb [m][bcap], Gb [p][bcap], Wb [rows][bcap]
     struct Graph {
-        const void* tb;
+        uint64_t tb;     // serial of the toolbox whose buffers the graph reads
         int64_t rc;
         int nl;          // number of nonlinearity coefficients (0: linear)
         cudaGraphExec_t exec;
@@ -2188,6 +2188,8 @@ size_t workspace_bytes(const ewos_toolbox* tb, int64_t nrhs, bool mixed) {
     return b;
 }
 
+static constexpr size_t kMaxSweepGraphs = 16;
+
 static ewos_status ensure_batched(const Ctx& C, int64_t rc) {
     SolveWorkspace* ws = C.ws;
     if (ws->bcap >= rc && ws->Sb) return EWOS_OK;
@@ -2289,38 +2291,48 @@ static ewos_status solve_batched(const Ctx& C, int R, const double* nl, int nnl,
     colnorms(C, rc);
     std::vector<double> r0(rc), rk(rc);
     EWOS_CUDA_TRY(cudaMemcpyAsync(r0.data(), ws->nrm, sizeof(double) * rc, cudaMemcpyDeviceToHost, C.st));
-    EWOS_CUDA_TRY(cudaStreamSynchronize(C.st));
     // the sweep as a CUDA graph, captured once per (workspace, toolbox, bucket, nonlinearity)
     const int nlk = nl ? nnl : 0;
     SolveWorkspace::Graph* gr = nullptr;
     for (auto& g : ws->graphs)
-        if (g.tb == C.tb && g.rc == rc && g.nl == nlk) gr = &g;
+        if (g.tb == C.tb->serial && g.rc == rc && g.nl == nlk) gr = &g;
     EWOS_CUDA_TRY(trsm_prepare<float>());
-    if (!gr) {
-        // captured on the workspace's own stream (the caller's may be the legacy default stream,
-        // which cannot be captured); the graph is then launched on the caller's stream
-        if (!ws->cap_st) EWOS_CUDA_TRY(cudaStreamCreateWithFlags(&ws->cap_st, cudaStreamNonBlocking));
-        Ctx Cc = C;
-        Cc.st = ws->cap_st;
-        cudaGraph_t graph = nullptr;
-        EWOS_CUDA_TRY(cudaStreamBeginCapture(Cc.st, cudaStreamCaptureModeThreadLocal));
-        const int launches = sweep_multi<TP>(Cc, rc, R, nl, nnl);
-        cudaError_t e = cudaStreamEndCapture(Cc.st, &graph);
-        if (e != cudaSuccess) { set_error(std::string("graph capture: ") + cudaGetErrorString(e)); return EWOS_ECUDA; }
-        cudaGraphExec_t exec = nullptr;
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) { set_error(std::string("graph instantiate: ") + cudaGetErrorString(e)); return EWOS_ECUDA; }
-        ws->graphs.push_back(SolveWorkspace::Graph{C.tb, rc, nlk, exec, launches});
-        gr = &ws->graphs.back();
-    }
     double worst = 1.0;
     int it = 0;
     while (it < max_sweeps) {
-        EWOS_CUDA_TRY(cudaGraphLaunch(gr->exec, C.st));
-        for (int q = 0; q < gr->launches; ++q) ::ewos::note_launch();
+        const bool capture = gr == nullptr;
+        if (capture) {
+            sweep_multi<TP>(C, rc, R, nl, nnl);   // first sweep of a new key: launched directly
+        } else {
+            EWOS_CUDA_TRY(cudaGraphLaunch(gr->exec, C.st));
+            for (int q = 0; q < gr->launches; ++q) ::ewos::note_launch();
+        }
         ++it;
         EWOS_CUDA_TRY(cudaMemcpyAsync(rk.data(), ws->nrm, sizeof(double) * rc, cudaMemcpyDeviceToHost, C.st));
+        if (capture) {
+            // captured while the first sweep runs, on the workspace's own stream (the caller's may
+            // be the legacy default stream, which cannot be captured); launched on the caller's
+            if (!ws->cap_st) EWOS_CUDA_TRY(cudaStreamCreateWithFlags(&ws->cap_st, cudaStreamNonBlocking));
+            Ctx Cc = C;
+            Cc.st = ws->cap_st;
+            cudaGraph_t graph = nullptr;
+            EWOS_CUDA_TRY(cudaStreamBeginCapture(Cc.st, cudaStreamCaptureModeThreadLocal));
+            const int launches = sweep_multi<TP>(Cc, rc, R, nl, nnl);
+            ::ewos::unnote_launches(launches);    // recorded, not run: counted at each replay
+            cudaError_t e = cudaStreamEndCapture(Cc.st, &graph);
+            if (e != cudaSuccess) { set_error(std::string("graph capture: ") + cudaGetErrorString(e)); return EWOS_ECUDA; }
+            cudaGraphExec_t exec = nullptr;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) { set_error(std::string("graph instantiate: ") + cudaGetErrorString(e)); return EWOS_ECUDA; }
+            // a server slot's workspace serves many toolboxes: keep the most recent few graphs
+            if (ws->graphs.size() >= kMaxSweepGraphs) {
+                cudaGraphExecDestroy(ws->graphs.front().exec);
+                ws->graphs.erase(ws->graphs.begin());
+            }
+            ws->graphs.push_back(SolveWorkspace::Graph{C.tb->serial, rc, nlk, exec, launches});
+            gr = &ws->graphs.back();
+        }
         EWOS_CUDA_TRY(cudaStreamSynchronize(C.st));
         worst = 0.0;
         bool bad = false;

@@ -12,6 +12,8 @@ namespace ewos {
 
 void set_error(const std::string& msg);
 void note_launch();            // counts every kernel launch of the library (ewos_launch_count)
+void unnote_launches(unsigned long long k);   // takes back launches recorded into a graph capture
+uint64_t next_toolbox_serial();  // process-wide serial of a new toolbox (never reused)
 
 // Device memory of the library comes from the device's stream-ordered pool (cudaMallocAsync),
 // on the stream the current entry point runs on; freed blocks stay in the pool for reuse.
@@ -60,5 +62,8 @@ struct ewos_toolbox {
     void* rec_xexit = nullptr;       // T [n][N][d]
     ewos_build_report rep{};
     ewos::SolveWorkspace* ws = nullptr;
+    // Identity of this toolbox for caches that outlive it (the sweep graphs of a server slot's
+    // workspace): a host address can be reused by a later toolbox, a serial is not.
+    uint64_t serial = ewos::next_toolbox_serial();
     size_t elem() const { return precision == 64 ? 8 : 4; }
 };

@@ -150,3 +150,35 @@ def test_server_admission_by_memory(disk):
         sv.wait(t)
     assert e.value.status == ewos.ENOMEM
     sv.close()
+
+
+def test_server_slot_reused_by_a_new_toolbox_of_the_same_shape(disk):
+    # One slot: its workspace (and the sweep graph cached in it) outlives the first toolbox.  A
+    # second toolbox of the same shape, made after the first is destroyed (often at the same host
+    # address), must be solved with its own operators, not with a graph of the destroyed one.
+    w, tb, lam, gtb = disk
+    q = W.serving_requests(w.x, w.z, 1, seed=11, nrhs=3, p_semilinear=0.0)[0]
+
+    def scaled(scale):      # FP32-rounded, as the toolbox stores it, so the oracle solves the same system
+        return {k: (np.asarray(scale * v, np.float32).astype(np.float64) if k in ("G", "gradG") else v)
+                for k, v in tb.items()}
+
+    def make(scale):
+        t = scaled(scale)
+        return ewos.toolbox_from_host(2, w.x, w.z, t["G"], t["gradG"], t["H"], t["gradH"], lam, precision=32)
+
+    sv = ewos.Server(max_slots=1)
+    a = make(1.0)
+    sv.wait(_submit_all(sv, a, [q])[0])
+    a.close()
+    b = make(0.8)
+    u_reused, _, rep, _ = sv.wait(_submit_all(sv, b, [q])[0])
+    sv.close()
+    fresh = ewos.Server(max_slots=1)
+    u_fresh, _, _, _ = fresh.wait(_submit_all(fresh, b, [q])[0])
+    fresh.close()
+    b.close()
+    assert rep["converged"]
+    assert _rel(u_reused, u_fresh) < 1e-10
+    ref = S.solve_linear(scaled(0.8), lam, q["A"], q["b"], None, q["f"][0], q["g"][0], alpha=rep["alpha"])
+    assert _rel(u_reused.reshape(3, -1)[0], ref["u"]) < 1e-8
