@@ -10,9 +10,9 @@
 // Dense LU with partial pivoting: blocked right-looking; the panel is a cooperative kernel
 // (rows split over all SMs, one grid barrier per column, row swaps through published copies),
 // then row interchanges, a unit-lower triangular solve for U12 and a GEMM for the trailing
-// matrix.  Triangular solves with the factors are cooperative kernels as well.  Every grid
-// barrier spins a bounded number of times; on a timeout the kernels return and the call
-// reports EWOS_ETIMEOUT.
+// matrix.  Triangular solves with the factors are one dataflow launch (row blocks published
+// through flags, CTAs ordered by tickets).  Every grid barrier and flag wait spins a bounded
+// number of times; on a timeout the kernels return and the call reports EWOS_ETIMEOUT.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -874,6 +874,7 @@ struct LuScratch {
     double* tmp = nullptr;      // [m * nrhs] permuted right-hand sides
     void* dinv = nullptr;       // [nbk][2][64][64] inverses of the diagonal blocks (T)
     void* diagb = nullptr;      // [nbk][64][64] factored diagonal blocks of the unpivoted path (T)
+    unsigned int* flow = nullptr;   // state of the dataflow triangular solve (flow_state_words)
     int panel_blocks = 0;
 };
 
@@ -1243,96 +1244,151 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
     return EWOS_OK;
 }
 
-// Triangular solves with the factors of P A = L U, by 64-row block steps, one launch each (no
-// grid barrier, so the sweep can be captured in a CUDA graph and several streams can solve at
-// the same time).  X [m][rc] holds rc right-hand sides per row, in place, rows in pivot order.
-// Forward step j: CTA c owns block t = j + c and subtracts the block-(j-1) segment (final since
-// step j-1); CTA 0 then applies the precomputed inverse of diagonal block j.  Backward step j:
-// t = j - c, segment j + 1, the upper inverse.
-template <typename T, bool LOWER>
-__global__ void __launch_bounds__(256) trsm_step_kernel(const T* __restrict__ LU, int lda, int m,
-                                                       const T* __restrict__ Dinv, T* __restrict__ X, int rc, int j) {
-    extern __shared__ __align__(16) unsigned char trsm_sm[];
-    T (*Ls)[65] = reinterpret_cast<T (*)[65]>(trsm_sm);
+// Triangular solves with the factors of P A = L U in ONE launch, as a dataflow over 64-row
+// blocks.  X [m][rc] holds rc right-hand sides per row, in place, rows in pivot order.  The
+// CTA with ticket t (tickets are taken in the order the CTAs start) owns block row i = t of
+// the forward solve (t < nbk) or block row i = 2 nbk - 1 - t of the backward solve:
+//   forward   Y_i = L_ii^{-1} (X_i - sum_{j<i} L_ij Y_j)
+//   backward  X_i = U_ii^{-1} (Y_i - sum_{j>i} U_ij X_j)
+// with the inverses of the diagonal blocks precomputed.  A row block publishes its result with
+// a release flag; a CTA waits only on flags of smaller tickets, which belong to CTAs that have
+// already started, so the launch completes whatever else runs on the device (no co-residency
+// assumption; several streams may solve at once).  Every backward write of X_i comes after the
+// last forward read (the backward chain starts from the last forward row block).  Every wait
+// is bounded; a timeout sets the error word, on which all other waits give up too.
+// state: [0] ticket counter, [1] error word, [2, 2 + nbk) forward flags, [2 + nbk, 2 + 2 nbk)
+// backward flags; zeroed before each launch.
+constexpr long long kFlowSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// thread 0 waits for *flag != 0; the result is the CTA's (false: give up and return)
+__device__ __forceinline__ bool flow_wait(const unsigned int* flag, unsigned int* err, int* s_ok) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        long long spins = 0;
+        while (ld_acquire_u32(flag) == 0) {
+            if (ld_acquire_u32(err) != 0) { ok = 0; break; }
+            if (++spins > kFlowSpinLimit) { atomicExch(err, 1u); ok = 0; break; }
+            __nanosleep(64);
+        }
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) trsm_flow_kernel(const T* __restrict__ LU, int lda, int m,
+                                                       const T* __restrict__ Dinv, T* X, int rc,
+                                                       unsigned int* state) {
+    extern __shared__ __align__(16) unsigned char flow_sm[];
+    T (*Ls)[65] = reinterpret_cast<T (*)[65]>(flow_sm);
     T (*Xs)[65] = Ls + 64;
-    T (*Xt)[65] = Xs + 64;
+    T (*Acc)[65] = Xs + 64;
+    T (*Ds)[65] = Acc + 64;
+    __shared__ unsigned int s_ticket;
+    __shared__ int s_ok;
     const int nbk = (m + 63) / 64;
-    const int t = LOWER ? j + (int)blockIdx.x : j - (int)blockIdx.x;
-    if (t < 0 || t >= nbk) return;
-    const int seg = LOWER ? j - 1 : j + 1;
-    const bool has_seg = seg >= 0 && seg < nbk;
-    const int r0 = t * 64, h = min(64, m - r0);
-    const int c0 = seg * 64, w = has_seg ? min(64, m - c0) : 0;
-    const int tid = threadIdx.x, i = tid & 63, rq = tid >> 6;
+    const int tid = threadIdx.x, ii = tid & 63, rq = tid >> 6;
+    if (tid == 0) s_ticket = atomicAdd(state, 1u);
+    __syncthreads();
+    const int t = (int)s_ticket;
+    if (t >= 2 * nbk) return;
+    const bool lower = t < nbk;
+    const int i = lower ? t : 2 * nbk - 1 - t;
+    unsigned int* err = state + 1;
+    unsigned int* const fl = state + 2;
+    unsigned int* const fu = state + 2 + nbk;
+    unsigned int* const mine = lower ? fl : fu;
+    const int r0 = i * 64, h = min(64, m - r0);
+    const T* Di = Dinv + (size_t)i * 2 * 64 * 64 + (lower ? 0 : 64 * 64);
+    for (int e = tid; e < 64 * 64; e += 256) Ds[e >> 6][e & 63] = Di[e];
+    if (!lower && !flow_wait(fl + i, err, &s_ok)) return;      // Y_i from the forward solve
+    const int nj = lower ? i : nbk - 1 - i;
     for (int q0 = 0; q0 < rc; q0 += 64) {
         const int rw = min(64, rc - q0);
         for (int e = tid; e < 64 * 64; e += 256) {
             const int a = e >> 6, b = e & 63;
-            Xt[a][b] = (a < h && b < rw) ? X[(size_t)(r0 + a) * rc + q0 + b] : T(0);
-            if (has_seg) {
+            Acc[a][b] = (a < h && b < rw) ? __ldcg(X + (size_t)(r0 + a) * rc + q0 + b) : T(0);
+        }
+        __syncthreads();                                          // Acc and Ds complete
+        for (int q = 0; q < nj; ++q) {
+            const int j = lower ? q : nbk - 1 - q;
+            const int c0 = j * 64, w = min(64, m - c0);
+            for (int e = tid; e < 64 * 64; e += 256) {
+                const int a = e >> 6, b = e & 63;
                 Ls[a][b] = (a < h && b < w) ? LU[(size_t)(r0 + a) * lda + c0 + b] : T(0);
-                Xs[a][b] = (a < w && b < rw) ? X[(size_t)(c0 + a) * rc + q0 + b] : T(0);
             }
+            if (!flow_wait(mine + j, err, &s_ok)) return;
+            for (int e = tid; e < 64 * 64; e += 256) {
+                const int a = e >> 6, b = e & 63;
+                Xs[a][b] = (a < w && b < rw) ? __ldcg(X + (size_t)(c0 + a) * rc + q0 + b) : T(0);
+            }
+            __syncthreads();
+            for (int r = rq; r < rw; r += 4) {
+                T acc = Acc[ii][r];
+#pragma unroll 16
+                for (int k = 0; k < 64; ++k) acc = fma(-Ls[ii][k], Xs[k][r], acc);
+                Acc[ii][r] = acc;
+            }
+            __syncthreads();
+        }
+        for (int r = rq; r < rw; r += 4) {
+            T acc = T(0);
+#pragma unroll 16
+            for (int k = 0; k < 64; ++k) acc = fma(Ds[ii][k], Acc[k][r], acc);
+            if (ii < h) X[(size_t)(r0 + ii) * rc + q0 + r] = acc;
         }
         __syncthreads();
-        if (has_seg) {
-            for (int r = rq; r < rw; r += 4) {
-                T acc = Xt[i][r];
-#pragma unroll 16
-                for (int k = 0; k < 64; ++k) acc = fma(-Ls[i][k], Xs[k][r], acc);
-                Xt[i][r] = acc;
-            }
-            __syncthreads();
-        }
-        if (blockIdx.x == 0) {
-            const T* Di = Dinv + (size_t)t * 2 * 64 * 64 + (LOWER ? 0 : 64 * 64);
-            for (int e = tid; e < 64 * 64; e += 256) Ls[e >> 6][e & 63] = Di[e];
-            __syncthreads();
-            T y[16];
-            int cnt = 0;
-            for (int r = rq; r < rw; r += 4) {
-                T acc = T(0);
-#pragma unroll 16
-                for (int k = 0; k < 64; ++k) acc = fma(Ls[i][k], Xt[k][r], acc);
-                y[cnt++] = acc;
-            }
-            __syncthreads();
-            cnt = 0;
-            for (int r = rq; r < rw; r += 4) Xt[i][r] = y[cnt++];
-            __syncthreads();
-        }
-        for (int e = tid; e < 64 * 64; e += 256) {
-            const int a = e >> 6, b = e & 63;
-            if (a < h && b < rw) X[(size_t)(r0 + a) * rc + q0 + b] = Xt[a][b];
-        }
-        __syncthreads();
+    }
+    if (tid == 0) {
+        __threadfence();
+        st_release_u32(mine + i, 1u);
     }
 }
 
 template <typename T>
-constexpr size_t trsm_smem() { return sizeof(T) * 3 * 64 * 65; }
+constexpr size_t flow_smem() { return sizeof(T) * 4 * 64 * 65; }
+
+constexpr size_t flow_state_words(int64_t m) { return 2 + 2 * (size_t)((m + 63) / 64); }
 
 template <typename T>
 static cudaError_t trsm_prepare() {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, [] {
-        err = cudaFuncSetAttribute(trsm_step_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>());
-        if (err == cudaSuccess)
-            err = cudaFuncSetAttribute(trsm_step_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem<T>());
+        err = cudaFuncSetAttribute(trsm_flow_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)flow_smem<T>());
     });
     return err;
 }
 
-// L U X = X (rows already in pivot order), all steps enqueued on st
+// L U X = X (rows already in pivot order), enqueued on st: the state reset and the one launch
 template <typename T>
-static void trsm_steps(const T* LU, int m, int lda, const T* Dinv, T* X, int rc, cudaStream_t st) {
+static void trsm_flow(const T* LU, int m, int lda, const T* Dinv, T* X, int rc, unsigned int* state, cudaStream_t st) {
     const int nbk = (m + 63) / 64;
-    const size_t sm = trsm_smem<T>();
-    for (int j = 0; j < nbk; ++j)
-        ::ewos::note_launch(), trsm_step_kernel<T, true><<<j == 0 ? 1 : nbk - j, 256, sm, st>>>(LU, lda, m, Dinv, X, rc, j);
-    for (int j = nbk - 1; j >= 0; --j)
-        ::ewos::note_launch(), trsm_step_kernel<T, false><<<j == nbk - 1 ? 1 : j + 1, 256, sm, st>>>(LU, lda, m, Dinv, X, rc, j);
+    cudaMemsetAsync(state, 0, sizeof(unsigned int) * flow_state_words(m), st);
+    ::ewos::note_launch(), trsm_flow_kernel<T><<<2 * nbk, 256, flow_smem<T>(), st>>>(LU, lda, m, Dinv, X, rc, state);
+}
+
+// the error word of the last triangular solve on st (synchronises st)
+static ewos_status flow_check(const unsigned int* state, cudaStream_t st) {
+    unsigned int herr = 0;
+    EWOS_CUDA_TRY(cudaMemcpyAsync(&herr, state + 1, sizeof(herr), cudaMemcpyDeviceToHost, st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (herr) {
+        set_error("triangular solve: a wait on a preceding row block timed out");
+        return EWOS_ETIMEOUT;
+    }
+    return EWOS_OK;
 }
 
 // out[i][r] = (T) x[r][perm[i]]  /  x[r][i] = out[i][r]
@@ -1393,7 +1449,7 @@ void free_workspace(SolveWorkspace* ws) {
     ::ewos::dev_free(ws->scal); ::ewos::dev_free(ws->umax);
     ::ewos::dev_free(ws->lu.pub); ::ewos::dev_free(ws->lu.bar); ::ewos::dev_free(ws->lu.ipiv);
     ::ewos::dev_free(ws->lu.perm); ::ewos::dev_free(ws->lu.swp); ::ewos::dev_free(ws->lu.tmp);
-    ::ewos::dev_free(ws->lu.dinv); ::ewos::dev_free(ws->lu.diagb);
+    ::ewos::dev_free(ws->lu.dinv); ::ewos::dev_free(ws->lu.diagb); ::ewos::dev_free(ws->lu.flow);
     ::ewos::dev_free(ws->Q32); ::ewos::dev_free(ws->L32); ::ewos::dev_free(ws->LU32); ::ewos::dev_free(ws->J32);
     ::ewos::dev_free(ws->Jx32); ::ewos::dev_free(ws->P32);
     ::ewos::dev_free(ws->rhs); ::ewos::dev_free(ws->r); ::ewos::dev_free(ws->dx);
@@ -1448,6 +1504,7 @@ static ewos_status ensure_workspace(const ewos_toolbox* tb, SolveWorkspace*& slo
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.tmp, sizeof(double) * m * nrhs));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.dinv, sizeof(double) * ((m + 63) / 64) * 2 * 64 * 64));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.diagb, sizeof(double) * ((m + 63) / 64) * 64 * 64));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.flow, sizeof(unsigned int) * flow_state_words(m)));
     }
     SolveWorkspace* ws = slot;
     if (!mixed && !ws->Q) {
@@ -1473,10 +1530,10 @@ static ewos_status lu_solve_device(const T* LU, int m, int lda, LuScratch& S, do
     const int64_t cnt = (int64_t)m * nrhs;
     const int nb = (int)((cnt + 255) / 256);
     ::ewos::note_launch(), gather_cols_kernel<T><<<nb, 256, 0, st>>>(x, S.perm, X, m, nrhs);
-    trsm_steps<T>(LU, m, lda, (const T*)S.dinv, X, nrhs, st);
+    trsm_flow<T>(LU, m, lda, (const T*)S.dinv, X, nrhs, S.flow, st);
     ::ewos::note_launch(), scatter_cols_kernel<T><<<nb, 256, 0, st>>>(X, x, m, nrhs);
     EWOS_CUDA_TRY(cudaGetLastError());
-    return EWOS_OK;
+    return flow_check(S.flow, st);
 }
 
 // ------------------------------------------------------------------ operator pieces
@@ -2175,7 +2232,7 @@ size_t workspace_bytes(const ewos_toolbox* tb, int64_t nrhs, bool mixed) {
     const size_t n = (size_t)tb->n, m = (size_t)tb->m, p = (size_t)tb->p, E = (size_t)tb->dim + 1;
     const size_t rc = (size_t)bucket_of(std::max<int64_t>(1, nrhs));
     size_t b = 8 * (n * E * E + n * E * E + n * (E + 1) + (n + p + 5 * m) * nrhs + 4 * E * n + 3 * m);   // vectors
-    b += 8 * ((m + 63) / 64) * 2 * 64 * 64 + 4 * ((m + 63) / 64) * 64 * 64 + 16 * m;                  // LU side
+    b += 8 * ((m + 63) / 64) * 2 * 64 * 64 + 4 * ((m + 63) / 64) * 64 * 64 + 16 * m + 4 * flow_state_words(m);   // LU side
     if (mixed) {
         const size_t Kp = (E * n + 31) / 32 * 32;
         b += 4 * (E * n * m + 3 * m * m + n * m);                 // Q32, L32, LU32, Jx32
@@ -2266,7 +2323,7 @@ static int sweep_multi(const Ctx& C, int64_t rc, int R, const double* nl, int nn
     const unsigned long long l0 = ewos_launch_count();
     const int m = (int)C.m;
     ::ewos::note_launch(), neg_gather32_kernel<<<nblocks(C.m * rc), 256, 0, C.st>>>(ws->Yb, ws->lu.perm, ws->D32, C.m, (int)rc);
-    trsm_steps<float>(ws->LU32, m, m, (const float*)ws->lu.dinv, ws->D32, (int)rc, C.st);
+    trsm_flow<float>(ws->LU32, m, m, (const float*)ws->lu.dinv, ws->D32, (int)rc, ws->lu.flow, C.st);
     ::ewos::note_launch(), add_widen_kernel<<<nblocks(C.m * rc), 256, 0, C.st>>>(C.m * rc, ws->D32, ws->Sb);
     residual_multi<TP>(C, rc, R, nl, nnl);
     colnorms(C, rc);
@@ -2309,6 +2366,8 @@ static ewos_status solve_batched(const Ctx& C, int R, const double* nl, int nnl,
         }
         ++it;
         EWOS_CUDA_TRY(cudaMemcpyAsync(rk.data(), ws->nrm, sizeof(double) * rc, cudaMemcpyDeviceToHost, C.st));
+        unsigned int flow_err = 0;
+        EWOS_CUDA_TRY(cudaMemcpyAsync(&flow_err, ws->lu.flow + 1, sizeof(flow_err), cudaMemcpyDeviceToHost, C.st));
         if (capture) {
             // captured while the first sweep runs, on the workspace's own stream (the caller's may
             // be the legacy default stream, which cannot be captured); launched on the caller's
@@ -2334,6 +2393,10 @@ static ewos_status solve_batched(const Ctx& C, int R, const double* nl, int nnl,
             gr = &ws->graphs.back();
         }
         EWOS_CUDA_TRY(cudaStreamSynchronize(C.st));
+        if (flow_err) {
+            set_error("triangular solve: a wait on a preceding row block timed out");
+            return EWOS_ETIMEOUT;
+        }
         worst = 0.0;
         bool bad = false;
         for (int r = 0; r < R; ++r) {
