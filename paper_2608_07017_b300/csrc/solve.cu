@@ -1011,161 +1011,203 @@ static ewos_status lu_factor_device(T* A, int m, int lda, LuScratch& S, cudaStre
 
 
 // ------------------------------------------------------------------ LU without interchanges
-// FP32 blocked LU with the diagonal pivots, accepted only when it equals the partial-pivoting
+// Blocked LU with the diagonal pivots, accepted only when it equals the partial-pivoting
 // factorisation: partial pivoting picks the diagonal at every column exactly when every
 // multiplier satisfies |l| <= 1, so the largest |l| is tracked and the caller refactors with
-// interchanges when it exceeds 1 (or a pivot is zero).  Per 64-column panel one launch factors
-// the diagonal block (redundantly in every CTA, in shared memory) and then, a thread per row /
-// column, forms L21 = A21 U11^-1 and U12 = L11^-1 A12; the trailing update is the FP32 GEMM.
-// Factored diagonal blocks go to a side buffer (other CTAs still read the original block) and
-// are written into the matrix after the last panel.
+// interchanges when it exceeds 1 (or a pivot is zero).  Per 64-column panel: one CTA factors the
+// diagonal block and forms the inverses of its two triangles; many CTAs then form
+// L21 = A21 U11^-1 and U12 = L11^-1 A12 as products with those inverses; the trailing update is
+// a GEMM (tensor cores for FP32 from 256 rows).  Factored diagonal blocks go to a side buffer and
+// are written into the matrix after the last panel; their inverses go straight to the buffer
+// the triangular solves use.
 constexpr int kNpThreads = 256;
-constexpr int kNpLd = kNB + 4;   // 16-byte aligned rows; a warp's 32 columns hit distinct banks
 
-// max that keeps a NaN (fmax drops it): a NaN multiplier must reject the unpivoted factors
-__device__ __forceinline__ double nanmax(double m, double v) { return (v > m || v != v) ? v : m; }
+// max that keeps a NaN (fmax drops it): a NaN multiplier must reject the unpivoted factors.
+// Kept in the factors' precision per element (FP64 arithmetic is slow on this part) and widened
+// once per warp for the device-wide maximum.
+template <typename T>
+__device__ __forceinline__ T nanmax(T m, T v) { return (v > m || v != v) ? v : m; }
 
 template <typename T>
-constexpr size_t nopiv_smem() { return sizeof(T) * (kNB * kNpLd + kNB * kNB + kNB); }
-
-// y[c] -= x * row[c] for c > j (row 16-byte aligned in shared memory)
-template <int J>
-__device__ __forceinline__ void axpy_tail(float (&y)[kNB], float x, const float* row) {
-    const float4* r4 = reinterpret_cast<const float4*>(row);
+__device__ __forceinline__ void publish_maxl(T mx, GridBarrier* bar) {
 #pragma unroll
-    for (int t = (J + 1) / 4; t < kNB / 4; ++t) {
-        const float4 u = r4[t];
-        if (4 * t > J) y[4 * t] = fmaf(-x, u.x, y[4 * t]);
-        if (4 * t + 1 > J) y[4 * t + 1] = fmaf(-x, u.y, y[4 * t + 1]);
-        if (4 * t + 2 > J) y[4 * t + 2] = fmaf(-x, u.z, y[4 * t + 2]);
-        if (4 * t + 3 > J) y[4 * t + 3] = fmaf(-x, u.w, y[4 * t + 3]);
-    }
+    for (int o = 16; o > 0; o >>= 1) mx = nanmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const double w = (double)mx;
+    if ((threadIdx.x & 31) == 0 && (w > 0.0 || w != w)) atomicMax(&bar->maxl_bits, (unsigned long long)__double_as_longlong(w));
 }
-template <int J>
-__device__ __forceinline__ void axpy_tail(double (&y)[kNB], double x, const double* row) {
-    const double2* r2 = reinterpret_cast<const double2*>(row);
-#pragma unroll
-    for (int t = (J + 1) / 2; t < kNB / 2; ++t) {
-        const double2 u = r2[t];
-        if (2 * t > J) y[2 * t] = fma(-x, u.x, y[2 * t]);
-        if (2 * t + 1 > J) y[2 * t + 1] = fma(-x, u.y, y[2 * t + 1]);
-    }
-}
-template <typename T, int J>
-struct TailLoop {
-    __device__ __forceinline__ static void fwd(T (&x)[kNB], const T* D, const T* rU) {   // x U = a
-        x[J] *= rU[J];
-        axpy_tail<J>(x, x[J], D + J * kNpLd);
-        TailLoop<T, J + 1>::fwd(x, D, rU);
-    }
-    __device__ __forceinline__ static void low(T (&y)[kNB], const T* Lt) {               // L y = a (unit)
-        axpy_tail<J>(y, y[J], Lt + J * kNB);
-        TailLoop<T, J + 1>::low(y, Lt);
-    }
-};
-template <typename T>
-struct TailLoop<T, kNB> {
-    __device__ __forceinline__ static void fwd(T (&)[kNB], const T*, const T*) {}
-    __device__ __forceinline__ static void low(T (&)[kNB], const T*) {}
-};
 
-// Diagonal block of one panel, factored with the diagonal pivots by one CTA in shared memory
-// (4 threads per column, right-looking, multipliers formed on the fly; column j is scaled at the
-// end).  Writes the factored block to diag_out (the matrix keeps the original block until the
-// end of the factorisation: the triangular-solve CTAs of this panel still read it there).
+// Diagonal block of one panel, factored with the diagonal pivots by one CTA, the block held in
+// registers: thread (c, q) keeps rows q, q + 4, .., q + 60 of column c.  Step j (the 64 steps are
+// unrolled, so every register index is a constant): the owners of row j and of column j publish
+// them through shared memory (double-buffered, one barrier per step), row j is written out with
+// the multipliers left of the diagonal scaled by 1/u_cc, and every thread applies
+// a_ic -= a_ij (a_jc / a_jj) to its rows below j.  The operations on each element are those of
+// the textbook right-looking elimination, in the same order.  Then, in the same layout, the
+// inverses of the unit lower triangle (forward elimination of I) and of the upper triangle
+// (backward elimination of I, row j scaled by 1/u_jj when it is final) are formed together and
+// written to dinv_blk [2][64][64].  Writes the factored block to diag_out.
 template <typename T>
 __global__ void __launch_bounds__(kNpThreads) lu_diag_factor_kernel(const T* __restrict__ A, int lda, int kb, int nb,
-                                                                    T* __restrict__ diag_out,
+                                                                    T* __restrict__ diag_out, T* __restrict__ dinv_blk,
                                                                     GridBarrier* __restrict__ bar) {
-    extern __shared__ __align__(16) unsigned char np_sm[];
-    T* D = reinterpret_cast<T*>(np_sm);            // [64][kNpLd]
-    T* rU = D + kNB * kNpLd + kNB * kNB;           // [64]
-    const int tid = threadIdx.x, c = tid & (kNB - 1), q = tid >> 6;
-    constexpr int kQ = kNpThreads / kNB;
-    double mx = 0.0;
+    constexpr int kQ = kNpThreads / kNB;     // row classes (4)
+    constexpr int kR = kNB / kQ;             // rows per thread (16)
+    __shared__ T rowb[2][kNB];
+    __shared__ T rowu[2][kNB];
+    __shared__ T colb[2][kQ][kR];
+    __shared__ T rU[kNB];
+    __shared__ T F[kNB][kNB + 1];            // the factored block
+    const int tid = threadIdx.x, c = tid & (kNB - 1), q = (tid >> 6) & (kQ - 1);
+    T d[kR];
+#pragma unroll
+    for (int k = 0; k < kR; ++k) {
+        const int i = q + kQ * k;
+        d[k] = (i < nb && c < nb) ? A[(size_t)(kb + i) * lda + kb + c] : (i == c ? T(1) : T(0));
+    }
     int zero = 0;
-    for (int i = q; i < kNB; i += kQ)
-        D[i * kNpLd + c] = (i < nb && c < nb) ? A[(size_t)(kb + i) * lda + kb + c] : (i == c ? T(1) : T(0));
-    __syncthreads();
+    T mx = T(0);
+#pragma unroll
     for (int j = 0; j < kNB; ++j) {
-        const T piv = D[j * kNpLd + j];
+        const int p = j & 1;
+        const bool owner = q == (j & (kQ - 1));   // d[j / 4] is row j
+        if (owner) rowb[p][c] = d[j / kQ];
+        if (c == j) {
+#pragma unroll
+            for (int k = 0; k < kR; ++k)
+                if (q + kQ * k > j) colb[p][q][k] = d[k];
+        }
+        __syncthreads();
+        if (owner) {                          // 1/u_cc of every c < j was set before this barrier
+            T out = d[j / kQ];
+            if (c < j) {
+                out *= rU[c];
+                mx = nanmax(mx, fabs(out));
+            }
+            diag_out[j * kNB + c] = out;
+            F[j][c] = out;
+        }
+        const T piv = rowb[p][j];
         const T r = piv != T(0) ? T(1) / piv : T(0);
         if (tid == 0) { rU[j] = r; zero |= piv == T(0); }
         if (c > j) {
-            const T u = D[j * kNpLd + c] * r;
-            for (int i = j + 1 + q; i < kNB; i += kQ) D[i * kNpLd + c] = fma(-D[i * kNpLd + j], u, D[i * kNpLd + c]);
+            const T u = rowb[p][c] * r;
+#pragma unroll
+            for (int k = 0; k < kR; ++k)
+                if (q + kQ * k > j) d[k] = fma(-colb[p][q][k], u, d[k]);
+        }
+    }
+    __syncthreads();                          // F and rU complete
+    // inverses, same layout: xl rows of L^-1, xu rows of U^-1 (column c, rows q + 4 k)
+    T xl[kR], xu[kR];
+#pragma unroll
+    for (int k = 0; k < kR; ++k) {
+        xl[k] = (q + kQ * k == c) ? T(1) : T(0);
+        xu[k] = xl[k];
+    }
+    T* Li = dinv_blk;
+    T* Ui = dinv_blk + kNB * kNB;
+#pragma unroll
+    for (int j = 0; j < kNB; ++j) {
+        const int p = j & 1;
+        const int ju = kNB - 1 - j;              // row of U^-1 made final at this step
+        if (q == (j & (kQ - 1))) {
+            const T v = xl[j / kQ];
+            rowb[p][c] = v;
+            Li[j * kNB + c] = v;
+        }
+        if (q == (ju & (kQ - 1))) {
+            const T v = xu[ju / kQ] * rU[ju];
+            xu[ju / kQ] = v;
+            rowu[p][c] = v;
+            Ui[ju * kNB + c] = v;
         }
         __syncthreads();
-    }
-    for (int i = c + 1 + q; i < kNB; i += kQ) {
-        const T l = D[i * kNpLd + c] * rU[c];
-        D[i * kNpLd + c] = l;
-        mx = nanmax(mx, fabs((double)l));
-    }
-    __syncthreads();
-    for (int t = tid; t < kNB * kNB; t += kNpThreads) diag_out[t] = D[(t >> 6) * kNpLd + (t & 63)];
-    if (tid == 0 && zero) bar->singular = 1;
+        const T yl = rowb[p][c], yu = rowu[p][c];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = nanmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((tid & 31) == 0 && (mx > 0.0 || mx != mx)) atomicMax(&bar->maxl_bits, (unsigned long long)__double_as_longlong(mx));
+        for (int k = 0; k < kR; ++k) {
+            const int i = q + kQ * k;
+            if (i > j) xl[k] = fma(-F[i][j], yl, xl[k]);
+            if (i < ju) xu[k] = fma(-F[i][ju], yu, xu[k]);
+        }
+    }
+    if (tid == 0 && zero) bar->singular = 1;
+    publish_maxl(mx, bar);
 }
 
-// L21 = A21 U11^-1 (a thread per row) and U12 = L11^-1 A12 (a thread per column) of one panel,
-// from the factored diagonal block (64-thread CTAs: the first half of the grid does rows, the
-// second columns); tracks the largest |l| of L21.
-constexpr int kTrsmThreads = 64;
+// L21 = A21 U11^-1 and U12 = L11^-1 A12 of one panel, as 64 x 64 x 64 products with the
+// inverses of the diagonal block's triangles (the first half of the grid does 64-row tiles of
+// A21, the second 64-column tiles of A12, in place); tracks the largest |l| of L21.  Both tiles
+// are fetched into registers first (all loads in flight together), then staged in shared memory.
+template <typename T>
+constexpr size_t panel_smem() { return sizeof(T) * 2 * kNB * (kNB + 1); }
 
 template <typename T>
-__global__ void __launch_bounds__(kTrsmThreads) lu_panel_trsm_kernel(T* __restrict__ A, int lda, int m, int kb,
-                                                                     const T* __restrict__ diag,
-                                                                     GridBarrier* __restrict__ bar) {
-    extern __shared__ __align__(16) unsigned char np_sm[];
-    T* D = reinterpret_cast<T*>(np_sm);            // [64][kNpLd]
-    T* Lt = D + kNB * kNpLd;                       // [64][64]
-    T* rU = Lt + kNB * kNB;                        // [64]
-    const int tid = threadIdx.x;
+__global__ void __launch_bounds__(kNpThreads) lu_panel_gemm_kernel(T* __restrict__ A, int lda, int m, int kb,
+                                                                   const T* __restrict__ dinv_blk,
+                                                                   GridBarrier* __restrict__ bar) {
+    constexpr int kS = kNB * kNB / kNpThreads;   // elements of a tile per thread (16)
+    extern __shared__ __align__(16) unsigned char pg_sm[];
+    T (*X)[kNB + 1] = reinterpret_cast<T (*)[kNB + 1]>(pg_sm);     // the A21 or A12 tile
+    T (*V)[kNB + 1] = X + kNB;                                       // U11^-1 or L11^-1
+    const int tid = threadIdx.x, a = tid & (kNB - 1), g = (tid >> 6) & 3;
     const int rest = m - kb - kNB;
-    const int nbl = (rest + kTrsmThreads - 1) / kTrsmThreads;
-    const bool rows = blockIdx.x < nbl;
-    for (int t = tid; t < kNB * kNB; t += kTrsmThreads) {
-        const int i = t >> 6, k = t & 63;
-        const T v = diag[t];
-        D[i * kNpLd + k] = v;
-        Lt[k * kNB + i] = i > k ? v : T(0);
+    const int ntl = (rest + kNB - 1) / kNB;
+    const bool rows = (int)blockIdx.x < ntl;
+    const int t0 = kb + kNB + (rows ? (int)blockIdx.x : (int)blockIdx.x - ntl) * kNB;
+    const int ext = min(kNB, m - t0);
+    const T* inv = dinv_blk + (rows ? kNB * kNB : 0);
+    // element e = tid + 256 s of a 64 x 64 tile: row e / 64 = g + 4 s, column a
+    T xv[kS], vv[kS];
+#pragma unroll
+    for (int s = 0; s < kS; ++s) {
+        const int i = g + 4 * s;
+        vv[s] = inv[i * kNB + a];
+        if (rows) xv[s] = i < ext ? A[(size_t)(t0 + i) * lda + kb + a] : T(0);
+        else xv[s] = a < ext ? A[(size_t)(kb + i) * lda + t0 + a] : T(0);
+    }
+#pragma unroll
+    for (int s = 0; s < kS; ++s) {
+        V[g + 4 * s][a] = vv[s];
+        X[g + 4 * s][a] = xv[s];
     }
     __syncthreads();
-    if (tid < kNB) rU[tid] = T(1) / D[tid * kNpLd + tid];
-    __syncthreads();
-    double mx = 0.0;
+    T mx = T(0);
+    T acc[kS];
+#pragma unroll
+    for (int k = 0; k < kS; ++k) acc[k] = T(0);
     if (rows) {
-        const int i = kb + kNB + blockIdx.x * kTrsmThreads + tid;
-        if (i < m) {
-            T x[kNB];
-            const T* src = A + (size_t)i * lda + kb;
+        // row a of the tile, columns g + 4 k:  sum_t X[a][t] U^-1[t][col]
+        for (int t = 0; t < kNB; ++t) {
+            const T x = X[a][t];
 #pragma unroll
-            for (int cc = 0; cc < kNB; ++cc) x[cc] = src[cc];
-            TailLoop<T, 0>::fwd(x, D, rU);
-            T* dst = A + (size_t)i * lda + kb;
+            for (int k = 0; k < kS; ++k) acc[k] = fma(x, V[t][g + 4 * k], acc[k]);
+        }
+        __syncthreads();                      // staged in X for row-contiguous stores
 #pragma unroll
-            for (int cc = 0; cc < kNB; ++cc) {
-                dst[cc] = x[cc];
-                mx = nanmax(mx, fabs((double)x[cc]));
+        for (int k = 0; k < kS; ++k) X[a][g + 4 * k] = acc[k];
+        __syncthreads();
+#pragma unroll
+        for (int s = 0; s < kS; ++s) {
+            const int i = g + 4 * s;
+            if (i < ext) {
+                const T l = X[i][a];
+                A[(size_t)(t0 + i) * lda + kb + a] = l;
+                mx = nanmax(mx, fabs(l));
             }
         }
     } else {
-        const int col = kb + kNB + (blockIdx.x - nbl) * kTrsmThreads + tid;
-        if (col < m) {
-            T y[kNB];
+        // column a of the tile, rows g + 4 k:  sum_t L^-1[row][t] X[t][a]
+        for (int t = 0; t < kNB; ++t) {
+            const T x = X[t][a];
 #pragma unroll
-            for (int r = 0; r < kNB; ++r) y[r] = A[(size_t)(kb + r) * lda + col];
-            TailLoop<T, 0>::low(y, Lt);
+            for (int k = 0; k < kS; ++k) acc[k] = fma(V[g + 4 * k][t], x, acc[k]);
+        }
+        if (a < ext) {
 #pragma unroll
-            for (int r = 0; r < kNB; ++r) A[(size_t)(kb + r) * lda + col] = y[r];
+            for (int k = 0; k < kS; ++k) A[(size_t)(kb + g + 4 * k) * lda + t0 + a] = acc[k];
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = nanmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((tid & 31) == 0 && (mx > 0.0 || mx != mx)) atomicMax(&bar->maxl_bits, (unsigned long long)__double_as_longlong(mx));
+    publish_maxl(mx, bar);
 }
 
 template <typename T>
@@ -1192,24 +1234,23 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(lu_diag_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)nopiv_smem<T>());
-        if (attr == cudaSuccess)
-            attr = cudaFuncSetAttribute(lu_panel_trsm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)nopiv_smem<T>());
+        attr = cudaFuncSetAttribute(lu_panel_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)panel_smem<T>());
     });
     EWOS_CUDA_TRY(attr);
     EWOS_CUDA_TRY(cudaMemsetAsync(S.bar, 0, sizeof(GridBarrier), st));
     T* diagb = reinterpret_cast<T*>(S.diagb);
+    T* dinv = reinterpret_cast<T*>(S.dinv);
     for (int kb = 0; kb < m; kb += kNB) {
         const int nb = std::min(kNB, m - kb);
         const int rest = m - kb - nb;
         T* dblk = diagb + (size_t)(kb / kNB) * kNB * kNB;
-        ::ewos::note_launch(), lu_diag_factor_kernel<T><<<1, kNpThreads, nopiv_smem<T>(), st>>>(A, lda, kb, nb, dblk, S.bar);
+        T* iblk = dinv + (size_t)(kb / kNB) * 2 * kNB * kNB;
+        ::ewos::note_launch(), lu_diag_factor_kernel<T><<<1, kNpThreads, 0, st>>>(A, lda, kb, nb, dblk, iblk, S.bar);
         if (rest > 0) {
             // nb == 64 whenever rows remain below the diagonal block
-            const int nbl = (rest + kTrsmThreads - 1) / kTrsmThreads;
-            ::ewos::note_launch(), lu_panel_trsm_kernel<T><<<2 * nbl, kTrsmThreads, nopiv_smem<T>(), st>>>(A, lda, m, kb, dblk, S.bar);
+            const int ntl = (rest + kNB - 1) / kNB;
+            ::ewos::note_launch(), lu_panel_gemm_kernel<T><<<2 * ntl, kNpThreads, panel_smem<T>(), st>>>(A, lda, m, kb, iblk, S.bar);
         }
         if (rest > 0) {
             if (std::is_same<T, float>::value && tc && rest >= kTcUpdateMin) {
@@ -1232,7 +1273,6 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
     ::ewos::note_launch(), diag_writeback_kernel<T><<<nbk, 256, 0, st>>>(A, lda, m, diagb);
     ::ewos::note_launch(), iota_kernel<<<(m + 255) / 256, 256, 0, st>>>(S.ipiv, m);
     ::ewos::note_launch(), iota_kernel<<<(m + 255) / 256, 256, 0, st>>>(S.perm, m);
-    ::ewos::note_launch(), diag_inverse_kernel<T><<<nbk, 64, 0, st>>>(A, lda, m, (T*)S.dinv);
     GridBarrier hb{};
     EWOS_CUDA_TRY(cudaMemcpyAsync(&hb, S.bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
     EWOS_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1286,6 +1326,21 @@ __device__ __forceinline__ bool flow_wait(const unsigned int* flag, unsigned int
     return *s_ok != 0;
 }
 
+// dst[a][b] = src[a * ld + b] for a < h, b < w, else 0 (a 64 x 64 tile, 256 threads): all 16
+// loads of a thread are issued before the shared-memory stores
+template <typename T, bool L2_ONLY>
+__device__ __forceinline__ void stage_tile(T (*dst)[65], const T* src, size_t ld, int h, int w) {
+    const int b = threadIdx.x & 63, a0 = threadIdx.x >> 6;
+    T v[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const int a = a0 + 4 * s;
+        v[s] = (a < h && b < w) ? (L2_ONLY ? __ldcg(src + a * ld + b) : src[a * ld + b]) : T(0);
+    }
+#pragma unroll
+    for (int s = 0; s < 16; ++s) dst[a0 + 4 * s][b] = v[s];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) trsm_flow_kernel(const T* __restrict__ LU, int lda, int m,
                                                        const T* __restrict__ Dinv, T* X, int rc,
@@ -1311,28 +1366,19 @@ __global__ void __launch_bounds__(256) trsm_flow_kernel(const T* __restrict__ LU
     unsigned int* const mine = lower ? fl : fu;
     const int r0 = i * 64, h = min(64, m - r0);
     const T* Di = Dinv + (size_t)i * 2 * 64 * 64 + (lower ? 0 : 64 * 64);
-    for (int e = tid; e < 64 * 64; e += 256) Ds[e >> 6][e & 63] = Di[e];
+    stage_tile<T, false>(Ds, Di, 64, 64, 64);
     if (!lower && !flow_wait(fl + i, err, &s_ok)) return;      // Y_i from the forward solve
     const int nj = lower ? i : nbk - 1 - i;
     for (int q0 = 0; q0 < rc; q0 += 64) {
         const int rw = min(64, rc - q0);
-        for (int e = tid; e < 64 * 64; e += 256) {
-            const int a = e >> 6, b = e & 63;
-            Acc[a][b] = (a < h && b < rw) ? __ldcg(X + (size_t)(r0 + a) * rc + q0 + b) : T(0);
-        }
+        stage_tile<T, true>(Acc, X + (size_t)r0 * rc + q0, rc, h, rw);
         __syncthreads();                                          // Acc and Ds complete
         for (int q = 0; q < nj; ++q) {
             const int j = lower ? q : nbk - 1 - q;
             const int c0 = j * 64, w = min(64, m - c0);
-            for (int e = tid; e < 64 * 64; e += 256) {
-                const int a = e >> 6, b = e & 63;
-                Ls[a][b] = (a < h && b < w) ? LU[(size_t)(r0 + a) * lda + c0 + b] : T(0);
-            }
+            stage_tile<T, false>(Ls, LU + (size_t)r0 * lda + c0, lda, h, w);
             if (!flow_wait(mine + j, err, &s_ok)) return;
-            for (int e = tid; e < 64 * 64; e += 256) {
-                const int a = e >> 6, b = e & 63;
-                Xs[a][b] = (a < w && b < rw) ? __ldcg(X + (size_t)(c0 + a) * rc + q0 + b) : T(0);
-            }
+            stage_tile<T, true>(Xs, X + (size_t)c0 * rc + q0, rc, w, rw);
             __syncthreads();
             for (int r = rq; r < rw; r += 4) {
                 T acc = Acc[ii][r];
