@@ -99,7 +99,9 @@ __global__ void coef_kernel(int n, int D, const double* __restrict__ lam, const 
     Mi[D * E + D] = c ? lam[i] * c[i] : 0.0;
 }
 
-// Q[j][i][col] = sum_k M_i[j][k] P[k][i][col]
+// Q[j][i][col] = sum_k M_i[j][k] P[k][i][col], computed in TQ: FP64 for the FP64 path; FP32 for
+// the FP32 copy of the mixed path (Q is stored in FP32 there, and FP64 arithmetic would make
+// this pass over P compute-bound on a part whose FP64 rate is a small fraction of its FP32 rate)
 template <typename TP, typename TQ>
 __global__ void formQ_kernel(const TP* __restrict__ P, const double* __restrict__ M, TQ* __restrict__ Q,
                              int n, int m, int D) {
@@ -108,13 +110,13 @@ __global__ void formQ_kernel(const TP* __restrict__ P, const double* __restrict_
     if (col >= m) return;
     const int E = D + 1;
     const size_t nm = (size_t)n * m;
-    double pv[4];
-    for (int k = 0; k < E; ++k) pv[k] = (double)P[k * nm + (size_t)i * m + col];
+    TQ pv[4];
+    for (int k = 0; k < E; ++k) pv[k] = (TQ)P[k * nm + (size_t)i * m + col];
     const double* Mi = M + (size_t)i * E * E;
     for (int j = 0; j < E; ++j) {
-        double acc = 0.0;
-        for (int k = 0; k < E; ++k) acc += Mi[j * E + k] * pv[k];
-        Q[j * nm + (size_t)i * m + col] = (TQ)acc;
+        TQ acc = TQ(0);
+        for (int k = 0; k < E; ++k) acc += (TQ)Mi[j * E + k] * pv[k];
+        Q[j * nm + (size_t)i * m + col] = acc;
     }
 }
 
@@ -1402,6 +1404,116 @@ __global__ void __launch_bounds__(256) trsm_flow_kernel(const T* __restrict__ LU
     }
 }
 
+// The same dataflow for one right-hand side (rc = 1), built for throughput of each CTA: the CTA
+// waits for the next block it needs and then takes every later block whose flag is already set
+// (up to 8 at once), so it never falls behind the chain.  Warp w owns rows w, w + 8, .. of the
+// row block; lanes stride over the columns of the ready blocks (row segments of L or U read
+// contiguously, all loads of a chunk in flight), partial sums are reduced across the warp at
+// the end, and the inverse of the diagonal block is applied from shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) trsm_flow_vec_kernel(const T* __restrict__ LU, int lda, int m,
+                                                           const T* __restrict__ Dinv, T* X, unsigned int* state) {
+    __shared__ T Ds[64][65];
+    __shared__ T ys[64];
+    __shared__ unsigned int s_ticket;
+    __shared__ int s_ok, s_cnt;
+    const int nbk = (m + 63) / 64;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) s_ticket = atomicAdd(state, 1u);
+    __syncthreads();
+    const int t = (int)s_ticket;
+    if (t >= 2 * nbk) return;
+    const bool lower = t < nbk;
+    const int i = lower ? t : 2 * nbk - 1 - t;
+    unsigned int* err = state + 1;
+    unsigned int* const fl = state + 2;
+    unsigned int* const fu = state + 2 + nbk;
+    unsigned int* const mine = lower ? fl : fu;
+    const int r0 = i * 64, h = min(64, m - r0);
+    stage_tile<T, false>(Ds, Dinv + (size_t)i * 2 * 64 * 64 + (lower ? 0 : 64 * 64), 64, 64, 64);
+    if (!lower && !flow_wait(fl + i, err, &s_ok)) return;      // Y_i from the forward solve
+    __syncthreads();                                          // s_ok is rewritten below
+    T acc[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) acc[r] = T(0);
+    const int nj = lower ? i : nbk - 1 - i;
+    int q = 0;
+    while (q < nj) {
+        // the next block this CTA needs: its rows of L (U) are fetched before its flag is polled
+        const int j0 = lower ? q : nbk - 1 - q;
+        const int cj = 64 * j0;
+        T pre[16];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int row = w + 8 * r;
+            const T* src = LU + (size_t)(r0 + row) * lda + cj;
+            pre[2 * r] = (row < h && cj + lane < m) ? src[lane] : T(0);
+            pre[2 * r + 1] = (row < h && cj + lane + 32 < m) ? src[lane + 32] : T(0);
+        }
+        if (tid == 0) {
+            int ok = 1, cnt = 0;
+            const unsigned int* f0 = mine + j0;
+            long long spins = 0;
+            while (ld_acquire_u32(f0) == 0) {
+                if (ld_acquire_u32(err) != 0) { ok = 0; break; }
+                if (++spins > kFlowSpinLimit) { atomicExch(err, 1u); ok = 0; break; }
+                __nanosleep(64);
+            }
+            if (ok) {
+                cnt = 1;
+                while (cnt < 8 && q + cnt < nj && ld_acquire_u32(mine + (lower ? q + cnt : nbk - 1 - q - cnt)) != 0) ++cnt;
+            }
+            s_ok = ok;
+            s_cnt = cnt;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        const int cnt = s_cnt;
+        {
+            const T x0 = cj + lane < m ? __ldcg(X + cj + lane) : T(0);
+            const T x1 = cj + lane + 32 < m ? __ldcg(X + cj + lane + 32) : T(0);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) acc[r] = fma(pre[2 * r + 1], x1, fma(pre[2 * r], x0, acc[r]));
+        }
+        // the other ready blocks: forward j0 + 1 .. j0 + cnt - 1, backward j0 - cnt + 1 .. j0 - 1
+        const int c_lo = lower ? cj + 64 : 64 * (j0 - cnt + 1);
+        const int c_hi = lower ? cj + 64 * cnt : cj;
+#pragma unroll 2
+        for (int k = c_lo + lane; k < c_hi; k += 32) {
+            const T xk = __ldcg(X + k);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int row = w + 8 * r;
+                if (row < h) acc[r] = fma(LU[(size_t)(r0 + row) * lda + k], xk, acc[r]);
+            }
+        }
+        q += cnt;
+        __syncthreads();                      // s_ok and s_cnt are rewritten by the next round
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        T v = acc[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        const int row = w + 8 * r;
+        if (lane == 0) ys[row] = row < h ? __ldcg(X + r0 + row) - v : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int row = w + 8 * r;
+        T v = fma(Ds[row][lane], ys[lane], Ds[row][lane + 32] * ys[lane + 32]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && row < h) X[r0 + row] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        st_release_u32(mine + i, 1u);
+    }
+}
+
 template <typename T>
 constexpr size_t flow_smem() { return sizeof(T) * 4 * 64 * 65; }
 
@@ -1422,7 +1534,10 @@ template <typename T>
 static void trsm_flow(const T* LU, int m, int lda, const T* Dinv, T* X, int rc, unsigned int* state, cudaStream_t st) {
     const int nbk = (m + 63) / 64;
     cudaMemsetAsync(state, 0, sizeof(unsigned int) * flow_state_words(m), st);
-    ::ewos::note_launch(), trsm_flow_kernel<T><<<2 * nbk, 256, flow_smem<T>(), st>>>(LU, lda, m, Dinv, X, rc, state);
+    if (rc == 1)
+        ::ewos::note_launch(), trsm_flow_vec_kernel<T><<<2 * nbk, 256, 0, st>>>(LU, lda, m, Dinv, X, state);
+    else
+        ::ewos::note_launch(), trsm_flow_kernel<T><<<2 * nbk, 256, flow_smem<T>(), st>>>(LU, lda, m, Dinv, X, rc, state);
 }
 
 // the error word of the last triangular solve on st (synchronises st)
