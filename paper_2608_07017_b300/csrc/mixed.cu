@@ -19,6 +19,7 @@
 #include <mutex>
 #include <string>
 
+#include "pdl.cuh"
 #include "toolbox.hpp"
 
 namespace ewos {
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int nk = Kp / BK;
+    ::ewos::pdl_trigger();
 
     if (threadIdx.x == 0) {
         s_fail = 0;
@@ -139,6 +141,7 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    ::ewos::pdl_wait();                       // operands and C come from the preceding launches
 
     if (threadIdx.x == 0) {
         // producer: TMA loads into the ring
@@ -235,6 +238,8 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
 // out[c][k] = in[k][c] for in [K][C] (row-major), out [C][Kp] with zero padding k in [K, Kp)
 __global__ void transpose_pad_kernel(const float* __restrict__ in, int K, int Ccols, float* __restrict__ out, int Kp) {
     __shared__ float tile[32][33];
+    ::ewos::pdl_trigger();
+    ::ewos::pdl_wait();
     const int c0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int k = k0 + r, c = c0 + threadIdx.x;
@@ -252,6 +257,8 @@ __global__ void transpose_pad_kernel(const float* __restrict__ in, int K, int Cc
 __global__ void transpose_split_kernel(const float* __restrict__ in, int K, int Ccols, float* __restrict__ hi,
                                        float* __restrict__ lo, int Kp) {
     __shared__ float tile[32][33];
+    ::ewos::pdl_trigger();
+    ::ewos::pdl_wait();
     const int c0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int k = k0 + r, c = c0 + threadIdx.x;
@@ -281,6 +288,8 @@ __device__ __forceinline__ void tf32_split(float v, float& h, float& l) {
 // hi/lo [M][Kp] from a row-major [M][K] operand with row stride ld (K contiguous), zero padding
 __global__ void rows_split_kernel(const float* __restrict__ in, int64_t ld, int M, int K, float* __restrict__ hi,
                                   float* __restrict__ lo, int Kp) {
+    ::ewos::pdl_trigger();
+    ::ewos::pdl_wait();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)M * Kp) return;
     const int64_t i = t / Kp;
@@ -295,6 +304,8 @@ __global__ void rows_split_kernel(const float* __restrict__ in, int64_t ld, int 
 __global__ void cols_split_kernel(const float* __restrict__ in, int64_t ld, int K, int N, float* __restrict__ hi,
                                   float* __restrict__ lo, int Kp) {
     __shared__ float tile[32][33];
+    ::ewos::pdl_trigger();
+    ::ewos::pdl_wait();
     const int c0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int k = k0 + r, c = c0 + threadIdx.x;
@@ -468,8 +479,12 @@ ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64
         EWOS_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
     }
     const int64_t na = (int64_t)M * Kp;
-    ::ewos::note_launch(), rows_split_kernel<<<(int)((na + 255) / 256), 256, 0, st>>>(A, lda, M, K, S.At, S.Atl, Kp);
-    ::ewos::note_launch(), cols_split_kernel<<<dim3((N + 31) / 32, (Kp + 31) / 32), dim3(32, 8), 0, st>>>(B, ldb, K, N, S.Bt, S.Btl, Kp);
+    ::ewos::note_launch();
+    EWOS_CUDA_TRY(::ewos::launch_pdl(rows_split_kernel, dim3((unsigned)((na + 255) / 256)), dim3(256), 0, st, A, lda, M,
+                                     K, S.At, S.Atl, Kp));
+    ::ewos::note_launch();
+    EWOS_CUDA_TRY(::ewos::launch_pdl(cols_split_kernel, dim3((N + 31) / 32, (Kp + 31) / 32), dim3(32, 8), 0, st, B, ldb,
+                                     K, N, S.Bt, S.Btl, Kp));
     constexpr int bn = Cfg<true>::BN;
     CUtensorMap ma, mb, mal, mbl;
     if (!(make_map(&ma, S.At, M, Kp, BM) && make_map(&mb, S.Bt, N, Kp, bn) && make_map(&mal, S.Atl, M, Kp, BM) &&
@@ -484,8 +499,9 @@ ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64
     });
     EWOS_CUDA_TRY(attr);
     dim3 grid((N + bn - 1) / bn, (M + BM - 1) / BM);
-    ::ewos::note_launch(), gemm_tf32_kernel<true><<<grid, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, ldc, S.err, 1);
-    EWOS_CUDA_TRY(cudaGetLastError());
+    ::ewos::note_launch();
+    EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true>, grid, dim3(128), (size_t)Cfg<true>::SMEM_BYTES, st, ma, mb,
+                                     mal, mbl, M, N, Kp, C, ldc, S.err, 1));
     return EWOS_OK;
 }
 

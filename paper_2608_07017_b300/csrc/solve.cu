@@ -25,6 +25,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "pdl.cuh"
 #include "sgemm.cuh"
 #include "solve_internal.hpp"
 #include "toolbox.hpp"
@@ -1060,6 +1061,8 @@ __global__ void __launch_bounds__(kNpThreads) lu_diag_factor_kernel(const T* __r
     __shared__ T rU[kNB];
     __shared__ T F[kNB][kNB + 1];            // the factored block
     const int tid = threadIdx.x, c = tid & (kNB - 1), q = (tid >> 6) & (kQ - 1);
+    pdl_trigger();
+    pdl_wait();                               // the block comes from the preceding update
     T d[kR];
 #pragma unroll
     for (int k = 0; k < kR; ++k) {
@@ -1152,6 +1155,8 @@ __global__ void __launch_bounds__(kNpThreads) lu_panel_gemm_kernel(T* __restrict
     T (*X)[kNB + 1] = reinterpret_cast<T (*)[kNB + 1]>(pg_sm);     // the A21 or A12 tile
     T (*V)[kNB + 1] = X + kNB;                                       // U11^-1 or L11^-1
     const int tid = threadIdx.x, a = tid & (kNB - 1), g = (tid >> 6) & 3;
+    pdl_trigger();
+    pdl_wait();                               // the inverses come from the diagonal-block launch
     const int rest = m - kb - kNB;
     const int ntl = (rest + kNB - 1) / kNB;
     const bool rows = (int)blockIdx.x < ntl;
@@ -1248,11 +1253,15 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
         const int rest = m - kb - nb;
         T* dblk = diagb + (size_t)(kb / kNB) * kNB * kNB;
         T* iblk = dinv + (size_t)(kb / kNB) * 2 * kNB * kNB;
-        ::ewos::note_launch(), lu_diag_factor_kernel<T><<<1, kNpThreads, 0, st>>>(A, lda, kb, nb, dblk, iblk, S.bar);
+        ::ewos::note_launch();
+        EWOS_CUDA_TRY(launch_pdl(lu_diag_factor_kernel<T>, dim3(1), dim3(kNpThreads), 0, st, (const T*)A, lda, kb, nb, dblk,
+                                 iblk, S.bar));
         if (rest > 0) {
             // nb == 64 whenever rows remain below the diagonal block
             const int ntl = (rest + kNB - 1) / kNB;
-            ::ewos::note_launch(), lu_panel_gemm_kernel<T><<<2 * ntl, kNpThreads, panel_smem<T>(), st>>>(A, lda, m, kb, iblk, S.bar);
+            ::ewos::note_launch();
+            EWOS_CUDA_TRY(launch_pdl(lu_panel_gemm_kernel<T>, dim3(2 * ntl), dim3(kNpThreads), panel_smem<T>(), st, A, lda,
+                                     m, kb, (const T*)iblk, S.bar));
         }
         if (rest > 0) {
             if (std::is_same<T, float>::value && tc && rest >= kTcUpdateMin) {
