@@ -1092,15 +1092,21 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
                            (o.threads_per_block <= 0 || !(o.hash_in_smem == 0 || o.hash_in_smem == 1));
     // V-centres: y when the caller gives a separate source partition, else the nodes
     const double* d_v = tb->y ? tb->y : d_x;
-    ewos_status s = build_lookup<T>(D, d_v, m, lo, hi, hv * gf_default, st, ctx.V, true);
-    if (s != EWOS_OK) return s;
-    s = build_lookup<T>(D, d_z, p, lo, hi, hz, st, ctx.Z, false);
-    if (s != EWOS_OK) return s;
     TuneKey key{sizeof(T), D, dom->kind, m, p, tb->N, o.record_walks != 0, o.threads_per_block, o.hash_in_smem,
                 o.ctas_per_sm, o.lookup_grid_scale};
     int cached_tpb = 0, cached_grid = 0;
     bool cached_smem = false;
     const bool have_cached = tune_lookup(key, cached_tpb, cached_smem, cached_grid);
+    // the default-spacing V grid is skipped when this shape is known to walk on the other one and
+    // the cell weights do not need it (given by the caller, or counted on the nodes' own grid)
+    const bool alt_only = tune_grid && have_cached && cached_grid == 1 && (o.cell_weights || tb->y);
+    ewos_status s = EWOS_OK;
+    if (!alt_only) {
+        s = build_lookup<T>(D, d_v, m, lo, hi, hv * gf_default, st, ctx.V, true);
+        if (s != EWOS_OK) return s;
+    }
+    s = build_lookup<T>(D, d_z, p, lo, hi, hz, st, ctx.Z, false);
+    if (s != EWOS_OK) return s;
     if (tune_grid && (!have_cached || cached_grid == 1)) {
         s = build_lookup<T>(D, d_v, m, lo, hi, hv * gf_alt, st, ctx.V2, true);
         if (s != EWOS_OK) return s;
@@ -1188,9 +1194,10 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
     a.rec_xexit = (T*)tb->rec_xexit;
     if (tb->rec_vhash) EWOS_CUDA_TRY(cudaMemsetAsync(tb->rec_vhash, 0, sizeof(uint32_t) * n * tb->N, st));
 
-    a.V = lookup_view<T, D>(ctx.V);
-    a.v_ncell = (int)ctx.V.grid.ncell; a.v_ncand = ctx.V.ncand;
-    a.v_K = ctx.V.K; a.v_candK = ctx.V.candK;
+    const DeviceLookup& V0 = alt_only ? ctx.V2 : ctx.V;     // replaced by the chosen grid at launch
+    a.V = lookup_view<T, D>(V0);
+    a.v_ncell = (int)V0.grid.ncell; a.v_ncand = V0.ncand;
+    a.v_K = V0.K; a.v_candK = V0.candK;
     a.v_in_smem = 0;
     po.gf_default = gf_default; po.gf_alt = gf_alt;
     po.have_cached = have_cached; po.cached_tpb = cached_tpb; po.cached_grid = cached_grid;
