@@ -20,6 +20,7 @@
 #include <string>
 
 #include "pdl.cuh"
+#include "tf32.cuh"
 #include "toolbox.hpp"
 
 namespace ewos {
@@ -278,13 +279,6 @@ __global__ void transpose_split_kernel(const float* __restrict__ in, int K, int 
     }
 }
 
-__device__ __forceinline__ void tf32_split(float v, float& h, float& l) {
-    const uint32_t b = __float_as_uint(v);
-    const uint32_t hb = (b + 0x0FFFu + ((b >> 13) & 1u)) & 0xFFFFE000u;
-    h = isfinite(v) ? __uint_as_float(hb) : v;
-    l = v - h;
-}
-
 // hi/lo [M][Kp] from a row-major [M][K] operand with row stride ld (K contiguous), zero padding
 __global__ void rows_split_kernel(const float* __restrict__ in, int64_t ld, int M, int K, float* __restrict__ hi,
                                   float* __restrict__ lo, int Kp) {
@@ -454,16 +448,14 @@ static ewos_status tc_check(tc::Scratch& S, cudaStream_t st) {
     return EWOS_OK;
 }
 
-// C [M][N] (row stride ldc) -= A B for a row-major A [M][K] (stride lda) and B [K][N] (stride
-// ldb): the LU's trailing update on the tensor cores (three TF32 products).  Enqueued only; a
-// pipeline timeout sets the scratch's error word, which tc_update_check reads (and clears).
-ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int M,
-                              int N, int K, cudaStream_t st, TcScratch** owned) {
+// Allocates the update scratch for operands of up to max_mn rows and K = k on the calling
+// thread's allocation stream (so a producer kernel can write the split operands into it).
+ewos_status tc_update_reserve(int max_mn, int k, cudaStream_t st, TcScratch** owned) {
     using namespace tc;
     if (!*owned) *owned = new TcScratch();
     Scratch& S = (*owned)->s;
-    const int Kp = (K + BK - 1) / BK * BK;
-    const size_t need = (size_t)std::max(M, N) * Kp;
+    const int Kp = (k + BK - 1) / BK * BK;
+    const size_t need = (size_t)max_mn * Kp;
     if (S.cap < need || !S.Atl) {
         ::ewos::dev_free(S.At); ::ewos::dev_free(S.Bt); ::ewos::dev_free(S.Atl); ::ewos::dev_free(S.Btl);
         S.At = S.Bt = S.Atl = S.Btl = nullptr;
@@ -478,13 +470,54 @@ ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.err, sizeof(int)));
         EWOS_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
     }
-    const int64_t na = (int64_t)M * Kp;
-    ::ewos::note_launch();
-    EWOS_CUDA_TRY(::ewos::launch_pdl(rows_split_kernel, dim3((unsigned)((na + 255) / 256)), dim3(256), 0, st, A, lda, M,
-                                     K, S.At, S.Atl, Kp));
-    ::ewos::note_launch();
-    EWOS_CUDA_TRY(::ewos::launch_pdl(cols_split_kernel, dim3((N + 31) / 32, (Kp + 31) / 32), dim3(32, 8), 0, st, B, ldb,
-                                     K, N, S.Bt, S.Btl, Kp));
+    return EWOS_OK;
+}
+
+// The operand buffers of the update, in the layout tc_update_enqueue reads with presplit set:
+// A hi/lo [M][Kp] (row i of A), B hi/lo [N][Kp] (column j of B), Kp = K rounded up to 32.
+void tc_update_operands(TcScratch* t, float** a_hi, float** a_lo, float** b_hi, float** b_lo) {
+    *a_hi = t->s.At; *a_lo = t->s.Atl; *b_hi = t->s.Bt; *b_lo = t->s.Btl;
+}
+
+// C [M][N] (row stride ldc) -= A B for a row-major A [M][K] (stride lda) and B [K][N] (stride
+// ldb): the LU's trailing update on the tensor cores (three TF32 products).  With presplit the
+// operands are already in the scratch (tc_update_operands; A and B are not read).  Enqueued
+// only; a pipeline timeout sets the scratch's error word, which tc_update_check reads (and
+// clears).
+ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int M,
+                              int N, int K, cudaStream_t st, TcScratch** owned, bool presplit) {
+    using namespace tc;
+    if (!*owned) *owned = new TcScratch();
+    Scratch& S = (*owned)->s;
+    const int Kp = (K + BK - 1) / BK * BK;
+    const size_t need = (size_t)std::max(M, N) * Kp;
+    if (presplit && (S.cap < need || !S.Atl || !S.err)) {
+        set_error("tensor-core update: split operands expected in a scratch that is too small");
+        return EWOS_EINVAL;
+    }
+    if (S.cap < need || !S.Atl) {
+        ::ewos::dev_free(S.At); ::ewos::dev_free(S.Bt); ::ewos::dev_free(S.Atl); ::ewos::dev_free(S.Btl);
+        S.At = S.Bt = S.Atl = S.Btl = nullptr;
+        S.cap = 0;
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.At, sizeof(float) * need));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Bt, sizeof(float) * need));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Atl, sizeof(float) * need));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Btl, sizeof(float) * need));
+        S.cap = need;
+    }
+    if (!S.err) {
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.err, sizeof(int)));
+        EWOS_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
+    }
+    if (!presplit) {
+        const int64_t na = (int64_t)M * Kp;
+        ::ewos::note_launch();
+        EWOS_CUDA_TRY(::ewos::launch_pdl(rows_split_kernel, dim3((unsigned)((na + 255) / 256)), dim3(256), 0, st, A, lda,
+                                         M, K, S.At, S.Atl, Kp));
+        ::ewos::note_launch();
+        EWOS_CUDA_TRY(::ewos::launch_pdl(cols_split_kernel, dim3((N + 31) / 32, (Kp + 31) / 32), dim3(32, 8), 0, st, B,
+                                         ldb, K, N, S.Bt, S.Btl, Kp));
+    }
     constexpr int bn = Cfg<true>::BN;
     CUtensorMap ma, mb, mal, mbl;
     if (!(make_map(&ma, S.At, M, Kp, BM) && make_map(&mb, S.Bt, N, Kp, bn) && make_map(&mal, S.Atl, M, Kp, BM) &&

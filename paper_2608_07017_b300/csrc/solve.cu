@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "pdl.cuh"
+#include "tf32.cuh"
 #include "sgemm.cuh"
 #include "solve_internal.hpp"
 #include "toolbox.hpp"
@@ -73,7 +74,9 @@ void tc_scratch_free(TcScratch* t);
 ewos_status tc_assemble(const float* A_km, const float* B_km, float* C, int M, int N, int K, cudaStream_t st,
                         bool split, TcScratch** owned);
 ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int M,
-                              int N, int K, cudaStream_t st, TcScratch** owned);
+                              int N, int K, cudaStream_t st, TcScratch** owned, bool presplit = false);
+ewos_status tc_update_reserve(int max_mn, int k, cudaStream_t st, TcScratch** owned);
+void tc_update_operands(TcScratch* t, float** a_hi, float** a_lo, float** b_hi, float** b_lo);
 ewos_status tc_update_check(TcScratch* t, cudaStream_t st);
 bool tc_assemble_available();
 
@@ -1143,13 +1146,22 @@ __global__ void __launch_bounds__(kNpThreads) lu_diag_factor_kernel(const T* __r
 // inverses of the diagonal block's triangles (the first half of the grid does 64-row tiles of
 // A21, the second 64-column tiles of A12, in place); tracks the largest |l| of L21.  Both tiles
 // are fetched into registers first (all loads in flight together), then staged in shared memory.
+// When the trailing update runs on the tensor cores (FP32 factors), the kernel also writes L21
+// and U12 split into TF32 hi + lo parts in the update's operand layout (K = 64: A [rest][64] by
+// rows of L21, B [rest][64] by columns of U12), so the update needs no separate split pass.
+struct TcOperands {
+    float* a_hi = nullptr;
+    float* a_lo = nullptr;
+    float* b_hi = nullptr;
+    float* b_lo = nullptr;
+};
 template <typename T>
 constexpr size_t panel_smem() { return sizeof(T) * 2 * kNB * (kNB + 1); }
 
 template <typename T>
 __global__ void __launch_bounds__(kNpThreads) lu_panel_gemm_kernel(T* __restrict__ A, int lda, int m, int kb,
                                                                    const T* __restrict__ dinv_blk,
-                                                                   GridBarrier* __restrict__ bar) {
+                                                                   GridBarrier* __restrict__ bar, TcOperands ops) {
     constexpr int kS = kNB * kNB / kNpThreads;   // elements of a tile per thread (16)
     extern __shared__ __align__(16) unsigned char pg_sm[];
     T (*X)[kNB + 1] = reinterpret_cast<T (*)[kNB + 1]>(pg_sm);     // the A21 or A12 tile
@@ -1193,6 +1205,7 @@ __global__ void __launch_bounds__(kNpThreads) lu_panel_gemm_kernel(T* __restrict
 #pragma unroll
         for (int k = 0; k < kS; ++k) X[a][g + 4 * k] = acc[k];
         __syncthreads();
+        const int64_t o0 = (int64_t)(t0 - kb - kNB) * kNB;        // first operand row of this tile
 #pragma unroll
         for (int s = 0; s < kS; ++s) {
             const int i = g + 4 * s;
@@ -1200,6 +1213,14 @@ __global__ void __launch_bounds__(kNpThreads) lu_panel_gemm_kernel(T* __restrict
                 const T l = X[i][a];
                 A[(size_t)(t0 + i) * lda + kb + a] = l;
                 mx = nanmax(mx, fabs(l));
+                if constexpr (std::is_same<T, float>::value) {
+                    if (ops.a_hi) {
+                        float hv, lv;
+                        tf32_split(l, hv, lv);
+                        ops.a_hi[o0 + (int64_t)i * kNB + a] = hv;
+                        ops.a_lo[o0 + (int64_t)i * kNB + a] = lv;
+                    }
+                }
             }
         }
     } else {
@@ -1212,6 +1233,26 @@ __global__ void __launch_bounds__(kNpThreads) lu_panel_gemm_kernel(T* __restrict
         if (a < ext) {
 #pragma unroll
             for (int k = 0; k < kS; ++k) A[(size_t)(kb + g + 4 * k) * lda + t0 + a] = acc[k];
+        }
+        if constexpr (std::is_same<T, float>::value) {
+            if (ops.b_hi) {
+                // B operand: column t0 + e / 64 of U12, row e % 64, contiguous; staged transposed
+                __syncthreads();                  // every thread is done reading X
+#pragma unroll
+                for (int k = 0; k < kS; ++k) X[g + 4 * k][a] = acc[k];
+                __syncthreads();
+                const int64_t o0 = (int64_t)(t0 - kb - kNB) * kNB;
+#pragma unroll
+                for (int s = 0; s < kS; ++s) {
+                    const int col = g + 4 * s, row = a;
+                    if (col < ext) {
+                        float hv, lv;
+                        tf32_split(X[row][col], hv, lv);
+                        ops.b_hi[o0 + (int64_t)col * kNB + row] = hv;
+                        ops.b_lo[o0 + (int64_t)col * kNB + row] = lv;
+                    }
+                }
+            }
         }
     }
     publish_maxl(mx, bar);
@@ -1248,6 +1289,14 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
     EWOS_CUDA_TRY(cudaMemsetAsync(S.bar, 0, sizeof(GridBarrier), st));
     T* diagb = reinterpret_cast<T*>(S.diagb);
     T* dinv = reinterpret_cast<T*>(S.dinv);
+    // tensor-core updates take their operands split by the panel kernel
+    TcOperands tc_ops;
+    const bool use_tc = std::is_same<T, float>::value && tc != nullptr && m - kNB >= kTcUpdateMin;
+    if (use_tc) {
+        ewos_status e = tc_update_reserve(m - kNB, kNB, st, tc);
+        if (e != EWOS_OK) return e;
+        tc_update_operands(*tc, &tc_ops.a_hi, &tc_ops.a_lo, &tc_ops.b_hi, &tc_ops.b_lo);
+    }
     for (int kb = 0; kb < m; kb += kNB) {
         const int nb = std::min(kNB, m - kb);
         const int rest = m - kb - nb;
@@ -1259,16 +1308,17 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
         if (rest > 0) {
             // nb == 64 whenever rows remain below the diagonal block
             const int ntl = (rest + kNB - 1) / kNB;
+            const bool tc_here = use_tc && rest >= kTcUpdateMin;
             ::ewos::note_launch();
             EWOS_CUDA_TRY(launch_pdl(lu_panel_gemm_kernel<T>, dim3(2 * ntl), dim3(kNpThreads), panel_smem<T>(), st, A, lda,
-                                     m, kb, (const T*)iblk, S.bar));
+                                     m, kb, (const T*)iblk, S.bar, tc_here ? tc_ops : TcOperands{}));
         }
         if (rest > 0) {
-            if (std::is_same<T, float>::value && tc && rest >= kTcUpdateMin) {
+            if (use_tc && rest >= kTcUpdateMin) {
                 ewos_status e = tc_update_enqueue(reinterpret_cast<const float*>(A + (size_t)(kb + nb) * lda + kb), lda,
                                                   reinterpret_cast<const float*>(A + (size_t)kb * lda + kb + nb), lda,
                                                   reinterpret_cast<float*>(A + (size_t)(kb + nb) * lda + kb + nb), lda,
-                                                  rest, rest, nb, st, tc);
+                                                  rest, rest, nb, st, tc, true);
                 if (e != EWOS_OK) return e;
             } else {
                 gemm_trailing<T>(st, rest, rest, nb, A + (size_t)(kb + nb) * lda + kb, lda,
