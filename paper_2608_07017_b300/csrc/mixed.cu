@@ -189,11 +189,27 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
                      : "memory");
     }
     __syncwarp();
-    // epilogue: wait for the accumulator, read 32 lanes per warp in 32-column chunks
+    // epilogue: wait for the accumulator, read 32 lanes per warp in 32-column chunks.  For the
+    // subtracting update the thread's row of C is fetched a chunk ahead: the first chunk while
+    // the MMAs still run, each next one while the current chunk is written.
+    const int row = m0 + warp * 32 + lane;
+    auto c_fast = [&](int c) {
+        const int col0 = n0 + c * 32;
+        return row < M && col0 + 32 <= N && (ldc & 3) == 0 &&
+               ((reinterpret_cast<uintptr_t>(C + (int64_t)row * ldc + col0) & 15) == 0);
+    };
+    float4 cpre[8];
+    auto c_fetch = [&](int c) {
+        if (sub && c_fast(c)) {
+            const float4* cp4 = reinterpret_cast<const float4*>(C + (int64_t)row * ldc + n0 + c * 32);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) cpre[q] = cp4[q];
+        }
+    };
+    c_fetch(0);
     bool ok = mbar_wait(done, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok && !s_fail) {
-        const int row = m0 + warp * 32 + lane;
         for (int c = 0; c < BN / 32; ++c) {
             uint32_t v[32];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32);
@@ -208,15 +224,19 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int col0 = n0 + c * 32;
+            float4 ccur[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) ccur[q] = cpre[q];
+            if (c + 1 < BN / 32) c_fetch(c + 1);
             if (row < M) {
                 float* cp = C + (int64_t)row * ldc + col0;
-                if (col0 + 32 <= N && (ldc & 3) == 0 && ((reinterpret_cast<uintptr_t>(cp) & 15) == 0)) {
+                if (c_fast(c)) {
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         float4 o = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
                                                __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
                         if (sub) {
-                            const float4 c4 = reinterpret_cast<const float4*>(cp)[q];
+                            const float4 c4 = ccur[q];
                             o = make_float4(c4.x - o.x, c4.y - o.y, c4.z - o.z, c4.w - o.w);
                         }
                         reinterpret_cast<float4*>(cp)[q] = o;
