@@ -1042,101 +1042,235 @@ __device__ __forceinline__ void publish_maxl(T mx, GridBarrier* bar) {
     if ((threadIdx.x & 31) == 0 && (w > 0.0 || w != w)) atomicMax(&bar->maxl_bits, (unsigned long long)__double_as_longlong(w));
 }
 
-// Diagonal block of one panel, factored with the diagonal pivots by one CTA, the block held in
-// registers: thread (c, q) keeps rows q, q + 4, .., q + 60 of column c.  Step j (the 64 steps are
-// unrolled, so every register index is a constant): the owners of row j and of column j publish
-// them through shared memory (double-buffered, one barrier per step), row j is written out with
-// the multipliers left of the diagonal scaled by 1/u_cc, and every thread applies
-// a_ic -= a_ij (a_jc / a_jj) to its rows below j.  The operations on each element are those of
-// the textbook right-looking elimination, in the same order.  Then, in the same layout, the
-// inverses of the unit lower triangle (forward elimination of I) and of the upper triangle
-// (backward elimination of I, row j scaled by 1/u_jj when it is final) are formed together and
-// written to dinv_blk [2][64][64].  Writes the factored block to diag_out.
+// Diagonal block of one panel, factored with the diagonal pivots by one CTA in shared memory,
+// blocked by 16 columns so that few CTA-wide barriers sit on this latency-bound path:
+//   for each 16-column sub-panel: one warp eliminates it (rows from the sub-panel's diagonal
+//   down, two rows per lane, pivot rows passed by shuffles; multipliers l = a / u_jj), the
+//   16 x 16 unit lower triangle is applied to the sub-panel's row to the right (U12, a thread
+//   per column), and the rows and columns beyond it get the rank-16 update a -= L21 U12.
+// Then the inverses of the unit lower and of the upper triangle by recursive doubling: each
+// 16 x 16 diagonal tile inverted by substitution (a lane per column), then the off-diagonal
+// blocks at 32 and 64 from  X21 = -inv(L22) L21 inv(L11)  and  X12 = -inv(U11) U12 inv(U22).
+// Writes the factored block to diag_out [64][64] and the inverses to dinv_blk [2][64][64].
+template <typename T>
+constexpr size_t diag_smem() { return sizeof(T) * (3 * kNB * (kNB + 1) + 2 * 32 * 33); }
+
 template <typename T>
 __global__ void __launch_bounds__(kNpThreads) lu_diag_factor_kernel(const T* __restrict__ A, int lda, int kb, int nb,
                                                                     T* __restrict__ diag_out, T* __restrict__ dinv_blk,
                                                                     GridBarrier* __restrict__ bar) {
-    constexpr int kQ = kNpThreads / kNB;     // row classes (4)
-    constexpr int kR = kNB / kQ;             // rows per thread (16)
-    __shared__ T rowb[2][kNB];
-    __shared__ T rowu[2][kNB];
-    __shared__ T colb[2][kQ][kR];
+    constexpr int LD = kNB + 1;              // row stride of the shared tiles
+    extern __shared__ __align__(16) unsigned char df_sm[];
+    T* F = reinterpret_cast<T*>(df_sm);      // [64][65] the block, factored in place
+    T* Li = F + kNB * LD;                    // [64][65] inverse of the unit lower triangle
+    T* Ui = Li + kNB * LD;                   // [64][65] inverse of the upper triangle
+    T* Tb = Ui + kNB * LD;                   // [2][32][33] products of the doubling steps
     __shared__ T rU[kNB];
-    __shared__ T F[kNB][kNB + 1];            // the factored block
-    const int tid = threadIdx.x, c = tid & (kNB - 1), q = (tid >> 6) & (kQ - 1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     pdl_trigger();
     pdl_wait();                               // the block comes from the preceding update
-    T d[kR];
+    {
+        // element e = tid + 256 s: row tid / 64 + 4 s, column tid % 64; all loads in flight first
+        constexpr int kE = kNB * kNB / kNpThreads;
+        const int c = tid & 63, i0 = tid >> 6;
+        T v[kE];
 #pragma unroll
-    for (int k = 0; k < kR; ++k) {
-        const int i = q + kQ * k;
-        d[k] = (i < nb && c < nb) ? A[(size_t)(kb + i) * lda + kb + c] : (i == c ? T(1) : T(0));
+        for (int s2 = 0; s2 < kE; ++s2) {
+            const int i = i0 + 4 * s2;
+            v[s2] = (i < nb && c < nb) ? A[(size_t)(kb + i) * lda + kb + c] : (i == c ? T(1) : T(0));
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < kE; ++s2) {
+            const int i = i0 + 4 * s2;
+            F[i * LD + c] = v[s2];
+            Li[i * LD + c] = T(0);
+            Ui[i * LD + c] = T(0);
+        }
     }
-    int zero = 0;
+    __syncthreads();
     T mx = T(0);
+    int zero = 0;
+    for (int p = 0; p < 4; ++p) {
+        const int c0 = 16 * p, nr = kNB - c0;
+        if (warp == 0) {
+            // rows c0 + lane and c0 + lane + 32 of columns c0 .. c0 + 15
+            const bool v0 = lane < nr, v1 = lane + 32 < nr;
+            T a0[16], a1[16];
 #pragma unroll
-    for (int j = 0; j < kNB; ++j) {
-        const int p = j & 1;
-        const bool owner = q == (j & (kQ - 1));   // d[j / 4] is row j
-        if (owner) rowb[p][c] = d[j / kQ];
-        if (c == j) {
-#pragma unroll
-            for (int k = 0; k < kR; ++k)
-                if (q + kQ * k > j) colb[p][q][k] = d[k];
-        }
-        __syncthreads();
-        if (owner) {                          // 1/u_cc of every c < j was set before this barrier
-            T out = d[j / kQ];
-            if (c < j) {
-                out *= rU[c];
-                mx = nanmax(mx, fabs(out));
+            for (int k = 0; k < 16; ++k) {
+                a0[k] = v0 ? F[(c0 + lane) * LD + c0 + k] : T(0);
+                a1[k] = v1 ? F[(c0 + lane + 32) * LD + c0 + k] : T(0);
             }
-            diag_out[j * kNB + c] = out;
-            F[j][c] = out;
-        }
-        const T piv = rowb[p][j];
-        const T r = piv != T(0) ? T(1) / piv : T(0);
-        if (tid == 0) { rU[j] = r; zero |= piv == T(0); }
-        if (c > j) {
-            const T u = rowb[p][c] * r;
 #pragma unroll
-            for (int k = 0; k < kR; ++k)
-                if (q + kQ * k > j) d[k] = fma(-colb[p][q][k], u, d[k]);
-        }
-    }
-    __syncthreads();                          // F and rU complete
-    // inverses, same layout: xl rows of L^-1, xu rows of U^-1 (column c, rows q + 4 k)
-    T xl[kR], xu[kR];
+            for (int j = 0; j < 16; ++j) {
+                const T piv = __shfl_sync(0xffffffffu, a0[j], j);
+                const T r = piv != T(0) ? T(1) / piv : T(0);
+                if (lane == 0) {
+                    rU[c0 + j] = r;
+                    zero |= piv == T(0);
+                }
+                const bool b0 = v0 && lane > j;
+                if (b0) {
+                    a0[j] *= r;
+                    mx = nanmax(mx, fabs(a0[j]));
+                }
+                if (v1) {
+                    a1[j] *= r;
+                    mx = nanmax(mx, fabs(a1[j]));
+                }
 #pragma unroll
-    for (int k = 0; k < kR; ++k) {
-        xl[k] = (q + kQ * k == c) ? T(1) : T(0);
-        xu[k] = xl[k];
-    }
-    T* Li = dinv_blk;
-    T* Ui = dinv_blk + kNB * kNB;
+                for (int jj = 0; jj < 16; ++jj) {
+                    if (jj > j) {
+                        const T u = __shfl_sync(0xffffffffu, a0[jj], j);
+                        if (b0) a0[jj] = fma(-a0[j], u, a0[jj]);
+                        if (v1) a1[jj] = fma(-a1[j], u, a1[jj]);
+                    }
+                }
+            }
 #pragma unroll
-    for (int j = 0; j < kNB; ++j) {
-        const int p = j & 1;
-        const int ju = kNB - 1 - j;              // row of U^-1 made final at this step
-        if (q == (j & (kQ - 1))) {
-            const T v = xl[j / kQ];
-            rowb[p][c] = v;
-            Li[j * kNB + c] = v;
-        }
-        if (q == (ju & (kQ - 1))) {
-            const T v = xu[ju / kQ] * rU[ju];
-            xu[ju / kQ] = v;
-            rowu[p][c] = v;
-            Ui[ju * kNB + c] = v;
+            for (int k = 0; k < 16; ++k) {
+                if (v0) F[(c0 + lane) * LD + c0 + k] = a0[k];
+                if (v1) F[(c0 + lane + 32) * LD + c0 + k] = a1[k];
+            }
         }
         __syncthreads();
-        const T yl = rowb[p][c], yu = rowu[p][c];
+        const int ncol = kNB - c0 - 16;
+        if (tid < ncol) {                     // U12 = inv(L11) A12, a thread per column
+            const int col = c0 + 16 + tid;
+            T x[16];
 #pragma unroll
-        for (int k = 0; k < kR; ++k) {
-            const int i = q + kQ * k;
-            if (i > j) xl[k] = fma(-F[i][j], yl, xl[k]);
-            if (i < ju) xu[k] = fma(-F[i][ju], yu, xu[k]);
+            for (int k = 0; k < 16; ++k) x[k] = F[(c0 + k) * LD + col];
+#pragma unroll
+            for (int k = 0; k < 16; ++k)
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (i > k) x[i] = fma(-F[(c0 + i) * LD + c0 + k], x[k], x[i]);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) F[(c0 + k) * LD + col] = x[k];
         }
+        __syncthreads();
+        if (ncol > 0) {                       // A22 -= L21 U12 over rows and columns c0 + 16 ..
+            const int col = tid & 63;
+            if (col >= c0 + 16) {
+                T u[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) u[k] = F[(c0 + k) * LD + col];
+                for (int i = c0 + 16 + (tid >> 6); i < kNB; i += kNpThreads / kNB) {
+                    T acc = F[i * LD + col];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) acc = fma(-F[i * LD + c0 + k], u[k], acc);
+                    F[i * LD + col] = acc;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = tid; e < kNB * kNB; e += kNpThreads) diag_out[e] = F[(e >> 6) * LD + (e & 63)];
+    // inverses of the 16 x 16 diagonal tiles: warps 0-3 the lower ones, 4-7 the upper ones
+    {
+        const int t = warp & 3, o = 16 * t, c = lane;
+        if (c < 16) {
+            T x[16];
+            if (warp < 4) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    T sum = (i == c) ? T(1) : T(0);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        if (k < i) sum = fma(-F[(o + i) * LD + o + k], x[k], sum);
+                    x[i] = sum;
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) Li[(o + i) * LD + o + c] = x[i];
+            } else {
+#pragma unroll
+                for (int ii = 0; ii < 16; ++ii) {
+                    const int i = 15 - ii;
+                    T sum = (i == c) ? T(1) : T(0);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k)
+                        if (k > i) sum = fma(-F[(o + i) * LD + o + k], x[k], sum);
+                    x[i] = sum * rU[o + i];
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) Ui[(o + i) * LD + o + c] = x[i];
+            }
+        }
+    }
+    __syncthreads();
+    // doubling to 32: four 16 x 16 tasks (lower pairs 0, 1 and upper pairs 0, 1), four elements
+    // per thread; T = L21 inv(L11) (T = U12 inv(U22)), then X21 = -inv(L22) T (X12 = -inv(U11) T)
+    {
+        const int task = tid >> 6, up = task >> 1, a = 32 * (task & 1), b = a + 16;
+        T* Tt = Tb + task * 16 * 17;
+#pragma unroll
+        for (int s4 = 0; s4 < 4; ++s4) {
+            const int e = (tid & 63) + 64 * s4, r = e >> 4, c = e & 15;
+            T sum = T(0);
+            if (!up) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) sum = fma(F[(b + r) * LD + a + k], Li[(a + k) * LD + a + c], sum);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) sum = fma(F[(a + r) * LD + b + k], Ui[(b + k) * LD + b + c], sum);
+            }
+            Tt[r * 17 + c] = sum;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s4 = 0; s4 < 4; ++s4) {
+            const int e = (tid & 63) + 64 * s4, r = e >> 4, c = e & 15;
+            T sum = T(0);
+            if (!up) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) sum = fma(Li[(b + r) * LD + b + k], Tt[k * 17 + c], sum);
+                Li[(b + r) * LD + a + c] = -sum;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) sum = fma(Ui[(a + r) * LD + a + k], Tt[k * 17 + c], sum);
+                Ui[(a + r) * LD + b + c] = -sum;
+            }
+        }
+        __syncthreads();
+    }
+    // doubling to 64: the lower and the upper 32 x 32 task, eight elements per thread
+    {
+        const int up = tid >> 7, a = 0, b = 32;
+        T* Tt = Tb + up * 32 * 33;
+#pragma unroll
+        for (int s8 = 0; s8 < 8; ++s8) {
+            const int e = (tid & 127) + 128 * s8, r = e >> 5, c = e & 31;
+            T sum = T(0);
+            if (!up) {
+#pragma unroll 8
+                for (int k = 0; k < 32; ++k) sum = fma(F[(b + r) * LD + a + k], Li[(a + k) * LD + a + c], sum);
+            } else {
+#pragma unroll 8
+                for (int k = 0; k < 32; ++k) sum = fma(F[(a + r) * LD + b + k], Ui[(b + k) * LD + b + c], sum);
+            }
+            Tt[r * 33 + c] = sum;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int s8 = 0; s8 < 8; ++s8) {
+            const int e = (tid & 127) + 128 * s8, r = e >> 5, c = e & 31;
+            T sum = T(0);
+            if (!up) {
+#pragma unroll 8
+                for (int k = 0; k < 32; ++k) sum = fma(Li[(b + r) * LD + b + k], Tt[k * 33 + c], sum);
+                Li[(b + r) * LD + a + c] = -sum;
+            } else {
+#pragma unroll 8
+                for (int k = 0; k < 32; ++k) sum = fma(Ui[(a + r) * LD + a + k], Tt[k * 33 + c], sum);
+                Ui[(a + r) * LD + b + c] = -sum;
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < kNB * kNB; e += kNpThreads) {
+        const int i = e >> 6, c = e & 63;
+        dinv_blk[e] = Li[i * LD + c];
+        dinv_blk[kNB * kNB + e] = Ui[i * LD + c];
     }
     if (tid == 0 && zero) bar->singular = 1;
     publish_maxl(mx, bar);
@@ -1284,6 +1418,9 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
     std::call_once(once, [] {
         attr = cudaFuncSetAttribute(lu_panel_gemm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)panel_smem<T>());
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(lu_diag_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)diag_smem<T>());
     });
     EWOS_CUDA_TRY(attr);
     EWOS_CUDA_TRY(cudaMemsetAsync(S.bar, 0, sizeof(GridBarrier), st));
@@ -1303,8 +1440,8 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
         T* dblk = diagb + (size_t)(kb / kNB) * kNB * kNB;
         T* iblk = dinv + (size_t)(kb / kNB) * 2 * kNB * kNB;
         ::ewos::note_launch();
-        EWOS_CUDA_TRY(launch_pdl(lu_diag_factor_kernel<T>, dim3(1), dim3(kNpThreads), 0, st, (const T*)A, lda, kb, nb, dblk,
-                                 iblk, S.bar));
+        EWOS_CUDA_TRY(launch_pdl(lu_diag_factor_kernel<T>, dim3(1), dim3(kNpThreads), diag_smem<T>(), st, (const T*)A, lda,
+                                 kb, nb, dblk, iblk, S.bar));
         if (rest > 0) {
             // nb == 64 whenever rows remain below the diagonal block
             const int ntl = (rest + kNB - 1) / kNB;
