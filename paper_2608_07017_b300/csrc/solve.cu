@@ -1493,7 +1493,10 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
 // already started, so the launch completes whatever else runs on the device (no co-residency
 // assumption; several streams may solve at once).  Every backward write of X_i comes after the
 // last forward read (the backward chain starts from the last forward row block).  Every wait
-// is bounded; a timeout sets the error word, on which all other waits give up too.
+// is bounded; a timeout sets the error word, on which all other waits give up too.  A row block
+// is published by a release store of one thread after a CTA barrier (cumulative over the CTA's
+// writes) and read after an acquire load of one thread followed by a barrier; flags are polled
+// without sleeping (each poll is an L2 round trip).
 // state: [0] ticket counter, [1] error word, [2, 2 + nbk) forward flags, [2 + nbk, 2 + 2 nbk)
 // backward flags; zeroed before each launch.
 constexpr long long kFlowSpinLimit = 1ll << 22;
@@ -1514,9 +1517,8 @@ __device__ __forceinline__ bool flow_wait(const unsigned int* flag, unsigned int
         int ok = 1;
         long long spins = 0;
         while (ld_acquire_u32(flag) == 0) {
-            if (ld_acquire_u32(err) != 0) { ok = 0; break; }
-            if (++spins > kFlowSpinLimit) { atomicExch(err, 1u); ok = 0; break; }
-            __nanosleep(64);
+            if ((++spins & 63) == 0 && ld_acquire_u32(err) != 0) { ok = 0; break; }   // another CTA gave up
+            if (spins > kFlowSpinLimit) { atomicExch(err, 1u); ok = 0; break; }
         }
         *s_ok = ok;
     }
@@ -1594,10 +1596,7 @@ __global__ void __launch_bounds__(256) trsm_flow_kernel(const T* __restrict__ LU
         }
         __syncthreads();
     }
-    if (tid == 0) {
-        __threadfence();
-        st_release_u32(mine + i, 1u);
-    }
+    if (tid == 0) st_release_u32(mine + i, 1u);     // after the barrier: publishes the CTA's writes
 }
 
 // The same dataflow for one right-hand side (rc = 1), built for throughput of each CTA: the CTA
@@ -1651,9 +1650,8 @@ __global__ void __launch_bounds__(256) trsm_flow_vec_kernel(const T* __restrict_
             const unsigned int* f0 = mine + j0;
             long long spins = 0;
             while (ld_acquire_u32(f0) == 0) {
-                if (ld_acquire_u32(err) != 0) { ok = 0; break; }
-                if (++spins > kFlowSpinLimit) { atomicExch(err, 1u); ok = 0; break; }
-                __nanosleep(64);
+                if ((++spins & 63) == 0 && ld_acquire_u32(err) != 0) { ok = 0; break; }
+                if (spins > kFlowSpinLimit) { atomicExch(err, 1u); ok = 0; break; }
             }
             if (ok) {
                 cnt = 1;
@@ -1704,10 +1702,7 @@ __global__ void __launch_bounds__(256) trsm_flow_vec_kernel(const T* __restrict_
         if (lane == 0 && row < h) X[r0 + row] = v;
     }
     __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        st_release_u32(mine + i, 1u);
-    }
+    if (tid == 0) st_release_u32(mine + i, 1u);     // after the barrier: publishes the CTA's writes
 }
 
 template <typename T>
