@@ -468,6 +468,106 @@ static ewos_status tc_check(tc::Scratch& S, cudaStream_t st) {
     return EWOS_OK;
 }
 
+// Operands of Lambda = P^T Q, Q = M P, in one pass over P: P is [(d+1)][n][m] (row k = l n + i
+// of the K x m operand is P[l][i][:]), M [n][d+1][d+1] the per-node coefficient blocks.  A tile
+// of 32 nodes x 32 columns of every P[l] is read once into shared memory; the kernel writes the
+// K-major split operands At/Atl [m][Kp] (from P) and Bt/Btl [m][Kp] (from Q, formed in FP32 as
+// Q[j][i][c] = sum_l M_i[j][l] P[l][i][c]), k = l n + i.
+template <int E>
+__global__ void pq_split_kernel(const float* __restrict__ P, const double* __restrict__ M, int n, int m,
+                                float* __restrict__ at, float* __restrict__ atl, float* __restrict__ bt,
+                                float* __restrict__ btl, int Kp) {
+    __shared__ float Pt[E][32][33];
+    __shared__ float Ms[32][E * E];
+    ::ewos::pdl_trigger();
+    ::ewos::pdl_wait();
+    const int c0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const size_t nm = (size_t)n * m;
+    for (int r = ty; r < 32; r += blockDim.y) {
+        const int i = i0 + r, c = c0 + tx;
+#pragma unroll
+        for (int l = 0; l < E; ++l) Pt[l][r][tx] = (i < n && c < m) ? P[l * nm + (size_t)i * m + c] : 0.f;
+    }
+    for (int t = ty * 32 + tx; t < 32 * E * E; t += 32 * blockDim.y) {
+        const int r = t / (E * E), q = t % (E * E);
+        Ms[r][q] = i0 + r < n ? (float)M[(size_t)(i0 + r) * E * E + q] : 0.f;
+    }
+    __syncthreads();
+    const int i = i0 + tx;
+    if (i >= n) return;
+    for (int cc = ty; cc < 32; cc += blockDim.y) {
+        const int c = c0 + cc;
+        if (c >= m) break;
+        float pv[E];
+#pragma unroll
+        for (int l = 0; l < E; ++l) pv[l] = Pt[l][tx][cc];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            float qv = 0.f;
+#pragma unroll
+            for (int l = 0; l < E; ++l) qv = fmaf(Ms[tx][j * E + l], pv[l], qv);
+            const size_t k = (size_t)j * n + i, o = (size_t)c * Kp + k;
+            float h, lo;
+            tf32_split(pv[j], h, lo);
+            at[o] = h;
+            atl[o] = lo;
+            tf32_split(qv, h, lo);
+            bt[o] = h;
+            btl[o] = lo;
+        }
+    }
+}
+
+// Lambda [m][m] = P^T Q with Q = M P, both operands prepared by pq_split_kernel, then the
+// three-product TF32 GEMM; waits for the launch (pipeline timeouts are reported)
+ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D, float* C, cudaStream_t st,
+                           TcScratch** owned) {
+    using namespace tc;
+    if (!*owned) *owned = new TcScratch();
+    Scratch& S = (*owned)->s;
+    const int E = D + 1, K = E * n;
+    const int Kp = (K + BK - 1) / BK * BK;
+    const size_t need = (size_t)m * Kp;
+    if (S.cap < need || !S.Atl) {
+        ::ewos::dev_free(S.At); ::ewos::dev_free(S.Bt); ::ewos::dev_free(S.Atl); ::ewos::dev_free(S.Btl);
+        S.At = S.Bt = S.Atl = S.Btl = nullptr;
+        S.cap = 0;
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.At, sizeof(float) * need));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Bt, sizeof(float) * need));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Atl, sizeof(float) * need));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Btl, sizeof(float) * need));
+        S.cap = need;
+    }
+    if (!S.err) EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.err, sizeof(int)));
+    if (Kp > K) {   // zero padding of the reduction dimension
+        for (float* b : {S.At, S.Atl, S.Bt, S.Btl})
+            EWOS_CUDA_TRY(cudaMemset2DAsync(b + K, sizeof(float) * Kp, 0, sizeof(float) * (Kp - K), m, st));
+    }
+    const dim3 grid((unsigned)((m + 31) / 32), (unsigned)((n + 31) / 32)), tb(32, 8);
+    ::ewos::note_launch();
+    if (E == 3) pq_split_kernel<3><<<grid, tb, 0, st>>>(P, Mc, n, m, S.At, S.Atl, S.Bt, S.Btl, Kp);
+    else if (E == 4) pq_split_kernel<4><<<grid, tb, 0, st>>>(P, Mc, n, m, S.At, S.Atl, S.Bt, S.Btl, Kp);
+    else {
+        set_error("tensor-core assembly: dimension must be 2 or 3");
+        return EWOS_EINVAL;
+    }
+    EWOS_CUDA_TRY(cudaGetLastError());
+    CUtensorMap ma, mb, mal, mbl;
+    if (!(make_map(&ma, S.At, m, Kp, BM) && make_map(&mb, S.Bt, m, Kp, Cfg<true>::BN) && make_map(&mal, S.Atl, m, Kp, BM) &&
+          make_map(&mbl, S.Btl, m, Kp, Cfg<true>::BN))) {
+        set_error("tensor-core assembly: cuTensorMapEncodeTiled failed");
+        return EWOS_ECUDA;
+    }
+    EWOS_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
+    EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<true>::SMEM_BYTES));
+    const dim3 g2((m + Cfg<true>::BN - 1) / Cfg<true>::BN, (m + BM - 1) / BM);
+    ::ewos::note_launch(), gemm_tf32_kernel<true><<<g2, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, m, m, Kp, C, m, S.err, 0);
+    EWOS_CUDA_TRY(cudaGetLastError());
+    return tc_check(S, st);
+}
+
+
 // Allocates the update scratch for operands of up to max_mn rows and K = k on the calling
 // thread's allocation stream (so a producer kernel can write the split operands into it).
 ewos_status tc_update_reserve(int max_mn, int k, cudaStream_t st, TcScratch** owned) {

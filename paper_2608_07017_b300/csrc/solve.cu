@@ -76,6 +76,8 @@ ewos_status tc_assemble(const float* A_km, const float* B_km, float* C, int M, i
 ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int M,
                               int N, int K, cudaStream_t st, TcScratch** owned, bool presplit = false);
 ewos_status tc_update_reserve(int max_mn, int k, cudaStream_t st, TcScratch** owned);
+ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D, float* C, cudaStream_t st,
+                           TcScratch** owned);
 void tc_update_operands(TcScratch* t, float** a_hi, float** a_lo, float** b_hi, float** b_lo);
 ewos_status tc_update_check(TcScratch* t, cudaStream_t st);
 bool tc_assemble_available();
@@ -2797,9 +2799,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
     if (!quasi) {
         auto ta = std::chrono::steady_clock::now();
         if (tc_assemble_available()) {
-            dim3 g((unsigned)((C.m + 255) / 256), (unsigned)C.n);
-            ::ewos::note_launch(), formQ_kernel<float, float><<<g, 256, 0, C.st>>>(P32, ws->M, ws->Q32, (int)C.n, (int)C.m, C.D);
-            ewos_status st = tc_assemble(P32, ws->Q32, ws->L32, (int)C.m, (int)C.m, (int)(C.E * C.n), C.st, kSplitTF32, &ws->tc);
+            ewos_status st = tc_assemble_pq(P32, ws->M, (int)C.n, (int)C.m, C.D, ws->L32, C.st, &ws->tc);
             if (st != EWOS_OK) return st;
         } else {
             assemble_mixed<TP>(C, P32);
@@ -2925,9 +2925,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                                                                                             ws->nl, pb->nl_ncoef, u, ws->M);
                 auto ta = std::chrono::steady_clock::now();
                 if (tc_assemble_available()) {
-                    dim3 gq((unsigned)((C.m + 255) / 256), (unsigned)C.n);
-                    ::ewos::note_launch(), formQ_kernel<float, float><<<gq, 256, 0, C.st>>>(P32, ws->M, ws->Q32, (int)C.n, (int)C.m, C.D);
-                    ewos_status st = tc_assemble(P32, ws->Q32, ws->L32, (int)C.m, (int)C.m, (int)(C.E * C.n), C.st, kSplitTF32, &ws->tc);
+                    ewos_status st = tc_assemble_pq(P32, ws->M, (int)C.n, (int)C.m, C.D, ws->L32, C.st, &ws->tc);
                     if (st != EWOS_OK) return st;
                 } else {
                     assemble_mixed<TP>(C, P32);
