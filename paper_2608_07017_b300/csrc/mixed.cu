@@ -33,10 +33,11 @@ constexpr long long kWaitLimit = 1ll << 22;
 // plain TF32: tiles A (128 x 32) and B (256 x 32) per stage, 4 stages.
 // split TF32 (3xTF32): A = A_hi + A_lo, B = B_hi + B_lo, products hi.hi + hi.lo + lo.hi into the
 // same accumulator; tiles A_hi, A_lo (128 x 32) and B_hi, B_lo (128 x 32) per stage, 3 stages.
-template <bool SPLIT>
+// ST > 0 sets the ring depth instead (the LU's trailing updates, K = 64, use two stages).
+template <bool SPLIT, int ST = 0>
 struct Cfg {
     static constexpr int BN = SPLIT ? 128 : 256;
-    static constexpr int STAGES = SPLIT ? 3 : 4;
+    static constexpr int STAGES = ST > 0 ? ST : (SPLIT ? 3 : 4);
     static constexpr int A_BYTES = BM * BK * 4;
     static constexpr int B_BYTES = BN * BK * 4;
     static constexpr int STAGE_BYTES = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES);
@@ -103,14 +104,20 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db
         : "memory");
 }
 
-template <bool SPLIT>
+// C tile of the subtracting update staged in shared memory (CSM): 128 rows of BN floats, rows
+// padded to BN + 4 floats so that the row-per-thread float4 reads of the epilogue are free of
+// bank conflicts; filled with cp.async by all threads at kernel start, under the main loop.
+constexpr int kCsmLd = 128 + 4;
+constexpr int kCsmBytes = BM * kCsmLd * 4;
+
+template <bool SPLIT, int ST = 0, bool CSM = false>
 __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant__ CUtensorMap mapA,
                                                            const __grid_constant__ CUtensorMap mapB,
                                                            const __grid_constant__ CUtensorMap mapAl,
                                                            const __grid_constant__ CUtensorMap mapBl, int M, int N,
                                                            int Kp, float* __restrict__ C, int64_t ldc,
                                                            int* __restrict__ err, int sub) {
-    using CF = Cfg<SPLIT>;
+    using CF = Cfg<SPLIT, ST>;
     constexpr int BN = CF::BN, STAGES = CF::STAGES, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
     constexpr int STAGE_BYTES = CF::STAGE_BYTES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -143,6 +150,22 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     ::ewos::pdl_wait();                       // operands and C come from the preceding launches
+    float* Cs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256);
+    if constexpr (CSM) {
+        static_assert(BN == 128, "the staged C tile is 128 columns wide");
+        // 16-byte pieces e = thread + 128 k: row e / 32, columns 4 (e % 32) .. + 3 (the host
+        // checked that C rows start on 16-byte boundaries)
+        for (int e = threadIdx.x; e < BM * BN / 4; e += 128) {
+            const int r = e >> 5, c4 = (e & 31) * 4;
+            if (m0 + r < M && n0 + c4 + 3 < N) {
+                const float* g = C + (int64_t)(m0 + r) * ldc + n0 + c4;
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(Cs + r * kCsmLd + c4)),
+                             "l"(g)
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
 
     if (threadIdx.x == 0) {
         // producer: TMA loads into the ring
@@ -206,9 +229,13 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
             for (int q = 0; q < 8; ++q) cpre[q] = cp4[q];
         }
     };
-    c_fetch(0);
+    if (!CSM) c_fetch(0);
     bool ok = mbar_wait(done, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if constexpr (CSM) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();                      // every thread's pieces of the C tile have landed
+    }
     if (ok && !s_fail) {
         for (int c = 0; c < BN / 32; ++c) {
             uint32_t v[32];
@@ -225,9 +252,15 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int col0 = n0 + c * 32;
             float4 ccur[8];
+            if constexpr (CSM) {
+                const float4* cs4 = reinterpret_cast<const float4*>(Cs + (warp * 32 + lane) * kCsmLd + c * 32);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) ccur[q] = cpre[q];
-            if (c + 1 < BN / 32) c_fetch(c + 1);
+                for (int q = 0; q < 8; ++q) ccur[q] = cs4[q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) ccur[q] = cpre[q];
+                if (c + 1 < BN / 32) c_fetch(c + 1);
+            }
             if (row < M) {
                 float* cp = C + (int64_t)row * ldc + col0;
                 if (c_fast(c)) {
@@ -645,16 +678,28 @@ ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64
         set_error("tensor-core update: cuTensorMapEncodeTiled failed");
         return EWOS_ECUDA;
     }
+    // K = 64 needs two ring stages; the shared memory left holds the C tile (when C's rows start
+    // on 16-byte boundaries), fetched under the main loop instead of by the epilogue
+    constexpr int kUpd = 2;
+    constexpr size_t kCsmSmem = (size_t)Cfg<true, kUpd>::SMEM_BYTES + kCsmBytes;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
         attr = cudaFuncSetAttribute(gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<true>::SMEM_BYTES);
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(gemm_tf32_kernel<true, kUpd, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kCsmSmem);
     });
     EWOS_CUDA_TRY(attr);
     dim3 grid((N + bn - 1) / bn, (M + BM - 1) / BM);
+    const bool csm = Kp <= kUpd * BK && (ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0;
     ::ewos::note_launch();
-    EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true>, grid, dim3(128), (size_t)Cfg<true>::SMEM_BYTES, st, ma, mb,
-                                     mal, mbl, M, N, Kp, C, ldc, S.err, 1));
+    if (csm)
+        EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true, kUpd, true>, grid, dim3(128), kCsmSmem, st, ma, mb, mal, mbl,
+                                         M, N, Kp, C, ldc, S.err, 1));
+    else
+        EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true>, grid, dim3(128), (size_t)Cfg<true>::SMEM_BYTES, st, ma, mb,
+                                         mal, mbl, M, N, Kp, C, ldc, S.err, 1));
     return EWOS_OK;
 }
 
