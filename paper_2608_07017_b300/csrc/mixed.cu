@@ -272,12 +272,27 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
                             const float4 c4 = ccur[q];
                             o = make_float4(c4.x - o.x, c4.y - o.y, c4.z - o.z, c4.w - o.w);
                         }
-                        reinterpret_cast<float4*>(cp)[q] = o;
+                        if constexpr (CSM)      // written back to the tile; stored row-contiguously below
+                            reinterpret_cast<float4*>(Cs + (warp * 32 + lane) * kCsmLd + c * 32)[q] = o;
+                        else
+                            reinterpret_cast<float4*>(cp)[q] = o;
                     }
                 } else {
                     for (int q = 0; q < 32; ++q)
                         if (col0 + q < N) cp[q] = sub ? cp[q] - __uint_as_float(v[q]) : __uint_as_float(v[q]);
                 }
+            }
+        }
+    }
+    if constexpr (CSM) {
+        // every thread reaches this barrier; the tile is stored only when no wait gave up
+        if (__syncthreads_and(ok && !s_fail)) {
+            // the 16-byte pieces of every full 32-column chunk of a row, as they were staged
+            for (int e = threadIdx.x; e < BM * BN / 4; e += 128) {
+                const int r = e >> 5, c4 = (e & 31) * 4, chunk0 = n0 + (c4 & ~31);
+                if (m0 + r < M && chunk0 + 32 <= N)
+                    *reinterpret_cast<float4*>(C + (int64_t)(m0 + r) * ldc + n0 + c4) =
+                        *reinterpret_cast<const float4*>(Cs + r * kCsmLd + c4);
             }
         }
     }
