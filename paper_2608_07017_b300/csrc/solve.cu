@@ -204,10 +204,13 @@ __global__ void narrow_f32_kernel(const double* __restrict__ in, float* __restri
         out[t] = (float)in[t];
 }
 
+// sum of squares of an FP32 array (for alpha = rcond ||Lambda||_F): each thread's partial sum in
+// FP32 (a few dozen terms; FP64 per element made this pass FP64-bound), widened for the reduction
 __global__ void sumsq_f32_kernel(const float* __restrict__ X, int64_t count, double* __restrict__ out) {
-    double acc = 0.0;
+    float part = 0.f;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
-        acc += (double)X[t] * (double)X[t];
+        part = fmaf(X[t], X[t], part);
+    double acc = part;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
@@ -2166,7 +2169,7 @@ __global__ void jac_scale32_kernel(const TP* __restrict__ Gm, const double* __re
 
 static double frob32(const Ctx& C, const float* X, int64_t count) {
     cudaMemsetAsync(C.ws->scal, 0, sizeof(double), C.st);
-    ::ewos::note_launch(), sumsq_f32_kernel<<<1024, 256, 0, C.st>>>(X, count, C.ws->scal);
+    ::ewos::note_launch(), sumsq_f32_kernel<<<4 * 148 * 4, 256, 0, C.st>>>(X, count, C.ws->scal);
     double h = 0;
     cudaMemcpyAsync(&h, C.ws->scal, sizeof(double), cudaMemcpyDeviceToHost, C.st);
     cudaStreamSynchronize(C.st);
