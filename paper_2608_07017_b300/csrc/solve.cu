@@ -2692,7 +2692,7 @@ static int sweep_multi(const Ctx& C, int64_t rc, int R, const double* nl, int nn
 // tol so that the caller takes the per-right-hand-side path.
 template <typename TP>
 static ewos_status solve_batched(const Ctx& C, int R, const double* nl, int nnl, double tol, int max_sweeps,
-                                 int* sweeps, bool* ok, double* final_rel) {
+                                 int* sweeps, bool* ok, double* final_rel, double* last_norm = nullptr) {
     SolveWorkspace* ws = C.ws;
     const int64_t rc = bucket_of(R);
     *ok = false;
@@ -2766,6 +2766,7 @@ static ewos_status solve_batched(const Ctx& C, int R, const double* nl, int nnl,
     }
     *sweeps += it;
     if (final_rel) *final_rel = worst;
+    if (last_norm) *last_norm = std::sqrt(rk[R - 1]);   // ||R(s) + alpha s|| of the last column, from the last sweep
     *ok = worst <= tol;
     if (!*ok) return EWOS_OK;
     // s and u = G s + H g for every column
@@ -2799,6 +2800,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
     int sweeps = 0;
     double rel = 0.0;
     bool u_done = false;
+    double batched_res = -1.0;      // residual norm of the last column from the batched sweeps
     if (!quasi) {
         auto ta = std::chrono::steady_clock::now();
         if (tc_assemble_available()) {
@@ -2826,13 +2828,16 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
             bool ok = false;
             double rel = 0.0;
             st = solve_batched<TP>(C, (int)nrhs, semi ? ws->nl : nullptr, semi ? pb->nl_ncoef : 0,
-                                   semi ? tol : kRefineTol, semi ? kChordMax : kRefineMax, &sweeps, &ok, &rel);
+                                   semi ? tol : kRefineTol, semi ? kChordMax : kRefineMax, &sweeps, &ok, &rel,
+                                   &batched_res);
             if (st != EWOS_OK) return st;
             rep->ms_solve = elapsed_ms(t2);
             if (ok) {
                 batched_done = true;
                 u_done = true;
                 rep->iters = semi ? sweeps : 1;
+            } else {
+                batched_res = -1.0;               // the fallback below computes another s
             }
         }
         if (batched_done) {
@@ -2964,7 +2969,9 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
     if (!u_done)
         for (int64_t r = 0; r < nrhs; ++r)
             u_from_s(C, tb->P, tb->KH, tb->precision == 64, ws->s + r * C.m, ws->g + r * C.p, ws->u + r * C.n);
-    if (!quasi) {
+    if (batched_res >= 0.0) {
+        rep->residual = batched_res;          // the last sweep evaluated it at the final s
+    } else if (!quasi) {
         const int64_t r = nrhs - 1;
         residual<TP>(C, ws->s + r * C.m, ws->g + r * C.p, ws->f + r * C.n, semi ? ws->nl : nullptr,
                      semi ? pb->nl_ncoef : 0, rep->alpha, ws->y);
