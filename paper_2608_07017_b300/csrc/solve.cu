@@ -1787,6 +1787,8 @@ struct SolveWorkspace {
     double *nrm = nullptr, *alpha_dev = nullptr;
     float *D32 = nullptr, *D32p = nullptr;
     float* F2buf = nullptr;          // hi/lo FP32 pairs of Sb [m][bcap], Gb [p][bcap], Wb [rows][bcap]
+    double* Ypart = nullptr;         // per-CTA partials of the fused one-column residual [ypart_grid][m]
+    int ypart_grid = 0;
     struct Graph {
         uint64_t tb;     // serial of the toolbox whose buffers the graph reads
         int64_t rc;
@@ -1814,6 +1816,7 @@ void free_workspace(SolveWorkspace* ws) {
     ::ewos::dev_free(ws->Sb); ::ewos::dev_free(ws->Yb); ::ewos::dev_free(ws->Vb); ::ewos::dev_free(ws->Wb);
     ::ewos::dev_free(ws->Fb); ::ewos::dev_free(ws->Gb); ::ewos::dev_free(ws->Ub); ::ewos::dev_free(ws->nrm);
     ::ewos::dev_free(ws->alpha_dev); ::ewos::dev_free(ws->D32); ::ewos::dev_free(ws->D32p); ::ewos::dev_free(ws->F2buf);
+    ::ewos::dev_free(ws->Ypart);
     for (auto& g : ws->graphs) cudaGraphExecDestroy(g.exec);
     if (ws->cap_st) cudaStreamDestroy(ws->cap_st);
     delete ws;
@@ -2603,6 +2606,8 @@ size_t workspace_bytes(const ewos_toolbox* tb, int64_t nrhs, bool mixed) {
 }
 
 static constexpr size_t kMaxSweepGraphs = 16;
+// columns of m and of p per thread in the fused one-column residual (m <= 4096, p <= 1024)
+constexpr int kFusedCols = 16, kFusedColsH = 4;
 
 static ewos_status ensure_batched(const Ctx& C, int64_t rc) {
     SolveWorkspace* ws = C.ws;
@@ -2625,11 +2630,151 @@ static ewos_status ensure_batched(const Ctx& C, int64_t rc) {
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->D32, sizeof(float) * C.m * rc));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->D32p, sizeof(float) * C.m * rc));
     if (!ws->alpha_dev) EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->alpha_dev, sizeof(double)));
+    if (!ws->Ypart && C.tb->precision == 32 && C.m <= 256 * kFusedCols && C.p <= 256 * kFusedColsH && (C.E == 3 || C.E == 4)) {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        ws->ypart_grid = std::max(1, std::min(nsm, (int)C.n));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Ypart, sizeof(double) * ws->ypart_grid * C.m));
+    }
     ws->bcap = rc;
     return EWOS_OK;
 }
 
 static int nblocks(int64_t count, int tpb = 256) { return (int)std::max<int64_t>(1, (count + tpb - 1) / tpb); }
+
+// (h, l) += (h2, l2) for unevaluated FP32 pairs (two-sum of the high parts)
+__device__ __forceinline__ void f2_merge(float& h, float& l, float h2, float l2) {
+    const float sum = __fadd_rn(h, h2);
+    const float bb = __fsub_rn(sum, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(sum, bb)), __fsub_rn(h2, bb));
+    h = sum;
+    l = __fadd_rn(__fadd_rn(l, l2), err);
+}
+
+// One right-hand side, FP32 toolbox, m <= 4096, p <= 1024: the residual's two passes over P in
+// one.  A CTA takes nodes i = b, b + grid, ..; for each it holds the node's d+1 rows of P in
+// registers (16 columns per thread; the next node's rows are loaded meanwhile), forms v_i = P_i s + KH_i g (FP32 pairs, reduced over the
+// CTA), w_i = M_i v_i + e_d lam_i (N(v_{d,i}) - f_i) (FP64, by d+1 threads), and adds P_i^T w_i
+// to its own partial of Y (FP32 pairs per column); Ypart [grid][m] is summed by
+// reduce_partials_kernel.  s, g arrive split into FP32 pairs.
+template <int E>
+__global__ void __launch_bounds__(256, 1) residual1_f2_kernel(const float* __restrict__ P, const float* __restrict__ KH,
+                                                              int n, int m, int p, const float* __restrict__ Shi,
+                                                              const float* __restrict__ Slo, const float* __restrict__ Ghi,
+                                                              const float* __restrict__ Glo, const double* __restrict__ M,
+                                                              const double* __restrict__ lam, const double* __restrict__ F,
+                                                              const double* __restrict__ nl, int nnl,
+                                                              double* __restrict__ Ypart) {
+    constexpr int D = E - 1;
+    __shared__ float red_h[8][E], red_l[8][E];
+    __shared__ float w_h[E], w_l[E];
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    const size_t nm = (size_t)n * m, np = (size_t)n * p;
+    float sh[kFusedCols], sl[kFusedCols], yh[kFusedCols], yl[kFusedCols];
+#pragma unroll
+    for (int k = 0; k < kFusedCols; ++k) {
+        const int c = tid + 256 * k;
+        sh[k] = c < m ? Shi[c] : 0.f;
+        sl[k] = c < m ? Slo[c] : 0.f;
+        yh[k] = yl[k] = 0.f;
+    }
+    float gh[kFusedColsH], gl[kFusedColsH];
+#pragma unroll
+    for (int k = 0; k < kFusedColsH; ++k) {
+        const int c = tid + 256 * k;
+        gh[k] = c < p ? Ghi[c] : 0.f;
+        gl[k] = c < p ? Glo[c] : 0.f;
+    }
+    // the rows of the next node are loaded while the current one is reduced and applied
+    float pn[E][kFusedCols];
+    auto load_rows = [&](int i) {
+#pragma unroll
+        for (int l = 0; l < E; ++l)
+#pragma unroll
+            for (int k = 0; k < kFusedCols; ++k) {
+                const int c = tid + 256 * k;
+                pn[l][k] = (i < n && c < m) ? P[l * nm + (size_t)i * m + c] : 0.f;
+            }
+    };
+    load_rows(blockIdx.x);
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        float pv[E][kFusedCols];
+#pragma unroll
+        for (int l = 0; l < E; ++l)
+#pragma unroll
+            for (int k = 0; k < kFusedCols; ++k) pv[l][k] = pn[l][k];
+        load_rows(i + gridDim.x);
+        float vh[E], vl[E];
+#pragma unroll
+        for (int l = 0; l < E; ++l) {
+            vh[l] = vl[l] = 0.f;
+#pragma unroll
+            for (int k = 0; k < kFusedCols; ++k) f2_add_prod(vh[l], vl[l], pv[l][k], sh[k], sl[k]);
+#pragma unroll
+            for (int k = 0; k < kFusedColsH; ++k) {
+                const int c = tid + 256 * k;
+                if (c < p) f2_add_prod(vh[l], vl[l], KH[l * np + (size_t)i * p + c], gh[k], gl[k]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                f2_merge(vh[l], vl[l], __shfl_xor_sync(0xffffffffu, vh[l], o), __shfl_xor_sync(0xffffffffu, vl[l], o));
+            if (lane == 0) {
+                red_h[wp][l] = vh[l];
+                red_l[wp][l] = vl[l];
+            }
+        }
+        __syncthreads();
+        if (tid < E) {
+            double vi[E];
+#pragma unroll
+            for (int l = 0; l < E; ++l) {
+                double a = 0.0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) a += (double)red_h[q][l] + (double)red_l[q][l];
+                vi[l] = a;
+            }
+            const double* Mi = M + (size_t)i * E * E;
+            double wj = 0.0;
+#pragma unroll
+            for (int l = 0; l < E; ++l) wj += Mi[tid * E + l] * vi[l];
+            if (tid == D) {
+                double extra = -F[i];
+                if (nl) {
+                    double pw = 1.0, sv = 0.0;
+                    for (int q = 0; q < nnl; ++q) { sv += nl[q] * pw; pw *= vi[D]; }
+                    extra += sv;
+                }
+                wj += lam[i] * extra;
+            }
+            const float h = (float)wj;
+            w_h[tid] = h;
+            w_l[tid] = (float)(wj - (double)h);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < E; ++l) {
+            const float wh = w_h[l], wl = w_l[l];
+#pragma unroll
+            for (int k = 0; k < kFusedCols; ++k) f2_add_prod(yh[k], yl[k], pv[l][k], wh, wl);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kFusedCols; ++k) {
+        const int c = tid + 256 * k;
+        if (c < m) Ypart[(size_t)blockIdx.x * m + c] = (double)yh[k] + (double)yl[k];
+    }
+}
+
+// Y[c] = sum over the parts of Ypart[b][c] + alpha S[c]
+__global__ void reduce_partials_kernel(const double* __restrict__ Ypart, int parts, int m, const double* __restrict__ alpha,
+                                       const double* __restrict__ S, double* __restrict__ Y) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m) return;
+    double a = 0.0;
+    for (int b = 0; b < parts; ++b) a += Ypart[(size_t)b * m + c];
+    Y[c] = a + alpha[0] * S[c];
+}
 
 // Yb = R(Sb) + alpha Sb for all columns (f, g of the request in Fb, Gb; nl may be NULL)
 template <typename TP>
@@ -2644,6 +2789,23 @@ static void residual_multi(const Ctx& C, int64_t rc, int R, const double* nl, in
     float* Glo = Ghi + C.p * rc;
     float* Whi = Glo + C.p * rc;
     float* Wlo = Whi + rows * rc;
+    if (sizeof(TP) == 4 && rc == 1 && ws->Ypart) {
+        ::ewos::note_launch(), split_f2_t_kernel<<<nblocks(C.m), 256, 0, C.st>>>(ws->Sb, Shi, Slo, C.m, 1);
+        ::ewos::note_launch(), split_f2_t_kernel<<<nblocks(C.p), 256, 0, C.st>>>(ws->Gb, Ghi, Glo, C.p, 1);
+        const float* P32 = (const float*)P;
+        const float* KH32 = (const float*)KH;
+        if (C.E == 3)
+            ::ewos::note_launch(), residual1_f2_kernel<3><<<ws->ypart_grid, 256, 0, C.st>>>(
+                                       P32, KH32, (int)C.n, (int)C.m, (int)C.p, Shi, Slo, Ghi, Glo, ws->M, C.tb->lambda,
+                                       ws->Fb, nl, nnl, ws->Ypart);
+        else
+            ::ewos::note_launch(), residual1_f2_kernel<4><<<ws->ypart_grid, 256, 0, C.st>>>(
+                                       P32, KH32, (int)C.n, (int)C.m, (int)C.p, Shi, Slo, Ghi, Glo, ws->M, C.tb->lambda,
+                                       ws->Fb, nl, nnl, ws->Ypart);
+        ::ewos::note_launch(), reduce_partials_kernel<<<nblocks(C.m), 256, 0, C.st>>>(ws->Ypart, ws->ypart_grid, (int)C.m,
+                                                                                    ws->alpha_dev, ws->Sb, ws->Yb);
+        return;
+    }
     if (sizeof(TP) == 4) {
         ::ewos::note_launch(), split_f2_t_kernel<<<nblocks(C.m * rc), 256, 0, C.st>>>(ws->Sb, Shi, Slo, C.m, (int)rc);
         ::ewos::note_launch(), split_f2_t_kernel<<<nblocks(C.p * rc), 256, 0, C.st>>>(ws->Gb, Ghi, Glo, C.p, (int)rc);
