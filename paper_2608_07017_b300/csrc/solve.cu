@@ -1633,6 +1633,12 @@ __global__ void __launch_bounds__(256) trsm_flow_vec_kernel(const T* __restrict_
     stage_tile<T, false>(Ds, Dinv + (size_t)i * 2 * 64 * 64 + (lower ? 0 : 64 * 64), 64, 64, 64);
     if (!lower && !flow_wait(fl + i, err, &s_ok)) return;      // Y_i from the forward solve
     __syncthreads();                                          // s_ok is rewritten below
+    T own[8];                                                 // this block's right-hand side, fetched early
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int row = w + 8 * r;
+        own[r] = (lane == 0 && row < h) ? __ldcg(X + r0 + row) : T(0);
+    }
     T acc[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) acc[r] = T(0);
@@ -1695,7 +1701,7 @@ __global__ void __launch_bounds__(256) trsm_flow_vec_kernel(const T* __restrict_
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         const int row = w + 8 * r;
-        if (lane == 0) ys[row] = row < h ? __ldcg(X + r0 + row) - v : T(0);
+        if (lane == 0) ys[row] = row < h ? own[r] - v : T(0);
     }
     __syncthreads();
 #pragma unroll
