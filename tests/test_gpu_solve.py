@@ -286,6 +286,27 @@ def test_mixed_ragged_sizes(k, per):
     assert _rel(u, ref["u"]) < 1e-9, x.shape
 
 
+@pytest.mark.parametrize("drop", [11, 8])
+def test_mixed_tensor_core_updates_ragged(drop):
+    # m = 389 (rows of the LU not 16-byte aligned: the update's C tile is read from global memory)
+    # and m = 392 (aligned, C staged in shared memory, last tiles ragged): trailing updates of at
+    # least 256 rows run on the tensor cores; K = 3 n is padded to a multiple of 32 in the
+    # one-pass operand preparation of the assembly
+    x = W.square_nodes(20)[:-drop]
+    z = W.square_boundary_nodes(6)
+    r = oracle.walk_rows(2, "box", [0, 0, 1, 1], x, z, 300, 1e-4, 5)
+    lam = np.full(x.shape[0], 1.0 / x.shape[0])
+    tb = dict(G=r["G"], gradG=r["gradG"], H=r["Hc"] / 300.0, gradH=r["gradH"])
+    pb = W.make_problem("square", x, z)
+    gtb = ewos.toolbox_from_host(2, x, z, tb["G"], tb["gradG"], tb["H"], tb["gradH"], lam, precision=32)
+    u, _, rep = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, mode="mixed")
+    gtb.close()
+    assert rep["converged"] and rep["factorizations"] == 1
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    ref = S.solve_linear({k: f32(v) for k, v in tb.items()}, lam, pb.A, pb.b, pb.c, pb.f, pb.g, alpha=rep["alpha"])
+    assert _rel(u, ref["u"]) < 1e-9, x.shape
+
+
 def test_ball8000_full_size_newton_mixed_and_fp64():
     # -Laplace u + u^3 = f on the unit ball, 8000 unknowns: Newton with the tensor-core
     # assembly, FP32 LU and FP64 refinement against the plain FP64 path (R16 bar)
