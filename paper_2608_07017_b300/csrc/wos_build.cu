@@ -91,6 +91,7 @@ template <int D>
 struct CellTest {
     float blo[3], bhi[3];
     float lim;
+    int best;             // index of the centre c_b that bounds the cell
     float cb[3];
     float dcb[8];         // squared distance of each corner to c_b
     float slack;
@@ -124,8 +125,27 @@ __device__ __forceinline__ void cell_setup(const float* __restrict__ pts, int np
         if (oR < R2 || (oR == R2 && oj < bj)) { R2 = oR; bj = oj; }
     }
     t.lim = R2 * (1.0f + 1e-4f) + t.slack;
+    t.best = bj;
 #pragma unroll
     for (int c = 0; c < D; ++c) t.cb[c] = pts[bj * D + c];
+#pragma unroll
+    for (int k = 0; k < (1 << D); ++k) {
+        float x[3];
+        corner(t, k, x);
+        float d2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) { const float u = x[c] - t.cb[c]; d2 += u * u; }
+        t.dcb[k] = d2;
+    }
+}
+
+// the cell test from the bound and centre a previous pass found (same values as cell_setup)
+template <int D>
+__device__ __forceinline__ void cell_setup_stored(const float* __restrict__ pts, int best, float lim, CellTest<D>& t) {
+    t.lim = lim;
+    t.best = best;
+#pragma unroll
+    for (int c = 0; c < D; ++c) t.cb[c] = pts[best * D + c];
 #pragma unroll
     for (int k = 0; k < (1 << D); ++k) {
         float x[3];
@@ -155,7 +175,8 @@ __device__ __forceinline__ bool cell_candidate(const float* __restrict__ pts, in
 
 template <int D>
 __global__ void lookup_count_kernel(const float* __restrict__ pts, int np, GridSpec g, float slack,
-                                    int* __restrict__ count, float* __restrict__ radius, int* __restrict__ maxcount) {
+                                    int* __restrict__ count, float* __restrict__ radius, int* __restrict__ maxcount,
+                                    int* __restrict__ best) {
     const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (cell >= g.ncell) return;
@@ -170,6 +191,7 @@ __global__ void lookup_count_kernel(const float* __restrict__ pts, int np, GridS
     if (lane == 0) {
         count[cell] = cnt > kCandidateCap ? 0 : cnt;   // empty list = scan all centres
         radius[cell] = t.lim;
+        if (best) best[cell] = t.best;
         if (maxcount) atomicMax(maxcount, cnt);
     }
 }
@@ -204,21 +226,39 @@ __global__ void lookup_fill_kernel(const float* __restrict__ pts, int np, GridSp
     fill_cell<D, int>(pts, np, t, cand + w, e - w);
 }
 
-// fixed-stride candidate table: K slots per cell, candidates in increasing index, padded with
-// the sentinel np (a point placed far away, never nearest)
+// Both candidate tables of a cell from one ordered scan, with the bound and centre the count pass
+// stored: the list [start[cell], start[cell + 1]) and, when candK is given, the fixed-stride row
+// of K slots padded with the sentinel np (a point placed far away, never nearest).  Same
+// contents as filling each table on its own.
 template <int D>
-__global__ void lookup_fill_fixed_kernel(const float* __restrict__ pts, int np, GridSpec g, float slack, int K,
-                                         uint16_t* __restrict__ cand) {
+__global__ void lookup_fill_both_kernel(const float* __restrict__ pts, int np, GridSpec g, float slack,
+                                        const float* __restrict__ radius, const int* __restrict__ best,
+                                        const int* __restrict__ start, int* __restrict__ cand, int K,
+                                        uint16_t* __restrict__ candK) {
     const int64_t cell = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (cell >= g.ncell) return;
+    const int s0 = start[cell], cap = start[cell + 1] - s0;
+    const int capK = candK ? K : 0;
+    if (candK)
+        for (int q = lane; q < K; q += 32) candK[cell * K + q] = (uint16_t)np;
+    if (cap == 0 && capK == 0) return;
     CellTest<D> t;
     cell_box_f<D>(g, cell, t.blo, t.bhi);
     t.slack = slack;
-    cell_setup<D>(pts, np, t);
-    for (int q = lane; q < K; q += 32) cand[cell * K + q] = (uint16_t)np;
+    cell_setup_stored<D>(pts, best[cell], radius[cell], t);
     __syncwarp();
-    fill_cell<D, uint16_t>(pts, np, t, cand + cell * K, K);
+    const int lim = max(cap, capK);
+    int w = 0;
+    for (int base = 0; base < np && w < lim; base += 32) {
+        const int j = base + lane;
+        const bool in = j < np && cell_candidate<D>(pts, j, t);
+        const unsigned msk = __ballot_sync(0xffffffffu, in);
+        const int off = w + __popc(msk & ((1u << lane) - 1u));
+        if (in && off < cap) cand[s0 + off] = j;
+        if (in && off < capK) candK[cell * K + off] = (uint16_t)j;
+        w += __popc(msk);
+    }
 }
 
 // exclusive scan of count[0..len) into start[0..len], single block (len is at most a few 10^5)
@@ -313,8 +353,10 @@ static ewos_status build_lookup(int dim, const double* d_pts, int np, const doub
     int* d_count = nullptr;
     float* d_rad = nullptr;
     float* d_pf = nullptr;
+    int* d_best = nullptr;
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_count, sizeof(int) * (nc + 1)));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_rad, sizeof(float) * nc));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_best, sizeof(int) * nc));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_pf, sizeof(float) * (np + 1) * dim));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&out.start, sizeof(int) * (nc + 1)));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&out.pts, sizeof(T) * (np + 1) * dim));
@@ -330,8 +372,8 @@ static ewos_status build_lookup(int dim, const double* d_pts, int np, const doub
     }
     const int tb = 256;
     const int nb = (int)((nc * 32 + tb - 1) / tb);
-    if (dim == 2) ::ewos::note_launch(), lookup_count_kernel<2><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, d_count, d_rad, d_count + nc);
-    else ::ewos::note_launch(), lookup_count_kernel<3><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, d_count, d_rad, d_count + nc);
+    if (dim == 2) ::ewos::note_launch(), lookup_count_kernel<2><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, d_count, d_rad, d_count + nc, d_best);
+    else ::ewos::note_launch(), lookup_count_kernel<3><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, d_count, d_rad, d_count + nc, d_best);
     ::ewos::note_launch(), exclusive_scan_kernel<<<1, 1024, 0, st>>>(d_count, nc, out.start);
     int hv[2] = {0, 0};
     EWOS_CUDA_TRY(cudaMemcpyAsync(&hv[0], out.start + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -340,17 +382,20 @@ static ewos_status build_lookup(int dim, const double* d_pts, int np, const doub
     const int total = hv[0], kmax = hv[1];
     out.ncand = total;
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&out.cand, sizeof(int) * std::max(1, total)));
-    if (dim == 2) ::ewos::note_launch(), lookup_fill_kernel<2><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, out.start, out.cand);
-    else ::ewos::note_launch(), lookup_fill_kernel<3><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, out.start, out.cand);
     if (want_fixed && kmax >= 1 && kmax <= kFixedCandMax && np < 65535) {
         out.K = kmax;
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&out.candK, sizeof(uint16_t) * nc * kmax));
-        if (dim == 2) ::ewos::note_launch(), lookup_fill_fixed_kernel<2><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, kmax, out.candK);
-        else ::ewos::note_launch(), lookup_fill_fixed_kernel<3><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, kmax, out.candK);
     }
+    if (dim == 2)
+        ::ewos::note_launch(), lookup_fill_both_kernel<2><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, d_rad, d_best, out.start,
+                                                                          out.cand, out.K, out.candK);
+    else
+        ::ewos::note_launch(), lookup_fill_both_kernel<3><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, d_rad, d_best, out.start,
+                                                                          out.cand, out.K, out.candK);
     EWOS_CUDA_TRY(cudaGetLastError());
     ::ewos::dev_free(d_count);
     ::ewos::dev_free(d_rad);
+    ::ewos::dev_free(d_best);
     ::ewos::dev_free(d_pf);
     return EWOS_OK;
 }
@@ -1645,7 +1690,8 @@ static ewos_status lookup_into(const double* d_pts, int np, const double* lo, co
     const int64_t ne = (int64_t)np * D;
     ::ewos::note_launch(), convert_points_kernel<float, D><<<(int)((ne + 255) / 256), 256, 0, st>>>(d_pts, (float*)out.pts, ne);
     const int tb = 256, nb = (int)((nc * 32 + tb - 1) / tb);
-    ::ewos::note_launch(), lookup_count_kernel<D><<<nb, tb, 0, st>>>((const float*)out.pts, np, out.grid, slack, d_count, d_rad, nullptr);
+    ::ewos::note_launch(), lookup_count_kernel<D><<<nb, tb, 0, st>>>((const float*)out.pts, np, out.grid, slack, d_count, d_rad, nullptr,
+                                                                   nullptr);
     ::ewos::note_launch(), exclusive_scan_kernel<<<1, 1024, 0, st>>>(d_count, nc, out.start);
     int total = 0;
     EWOS_CUDA_TRY(cudaMemcpyAsync(&total, out.start + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
