@@ -38,7 +38,8 @@ typedef enum {
     EWOS_ESINGULAR = 4,   /* LU met an exactly zero pivot                                  */
     EWOS_ENOCONV = 5,     /* Newton / Picard / refinement did not reach the tolerance     */
     EWOS_ETIMEOUT = 6,    /* a bounded device-side wait gave up                            */
-    EWOS_ESTEPCAP = 7     /* warning: some walks hit max_steps (reported, results valid)   */
+    EWOS_ESTEPCAP = 7,    /* warning: some walks hit max_steps (reported, results valid)   */
+    EWOS_EIO = 8          /* a toolbox file could not be written or read, or is not one    */
 } ewos_status;
 
 typedef enum {
@@ -184,6 +185,20 @@ ewos_status ewos_toolbox_report(const ewos_toolbox* tb, ewos_build_report* rep);
 ewos_status ewos_toolbox_shape(const ewos_toolbox* tb, int* dim, int64_t* n, int64_t* m,
                                int64_t* p, int* precision);
 void ewos_toolbox_free(ewos_toolbox* tb);
+
+/* Resident toolboxes across processes (serving, Sec. 3: the toolbox is built once per node set
+ * and reused for every problem on it).  ewos_toolbox_save writes tb to the file at path: a
+ * versioned header (dimension, precision, n, m, p, N, eps, seed, instance, build report) and the
+ * arrays x, z, the V-centres y (when separate), lambda, P = [grad G, G] and KH = [grad H, H] in the
+ * toolbox's precision, and the exit counts Hc (when present), all little-endian and raw; per-walk
+ * records are not saved.  ewos_toolbox_load reads such a file into a new toolbox on the current
+ * device, allocated on `stream` (NULL: the legacy default stream); the loaded toolbox is
+ * bit-identical to the saved one and is freed with ewos_toolbox_free.  Errors: EWOS_EINVAL for
+ * NULL arguments; EWOS_EIO when the file cannot be opened, written or read, or when its header
+ * is not a toolbox header of this version or does not match the file's size (checked before any
+ * device memory is touched); EWOS_ENOMEM / EWOS_ECUDA for device failures (nothing is returned). */
+ewos_status ewos_toolbox_save(const ewos_toolbox* tb, const char* path);
+ewos_status ewos_toolbox_load(const char* path, void* stream, ewos_toolbox** out);
 
 typedef enum { EWOS_NL_NONE = 0, EWOS_NL_SEMILINEAR = 1, EWOS_NL_QUASILINEAR = 2 } ewos_nl_kind;
 typedef enum {

@@ -2,10 +2,13 @@
 // copies in and out, and the test hooks.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "device_common.cuh"
@@ -113,6 +116,7 @@ const char* ewos_status_string(ewos_status s) {
         case EWOS_ENOCONV: return "no convergence";
         case EWOS_ETIMEOUT: return "device wait timed out";
         case EWOS_ESTEPCAP: return "some walks hit max_steps";
+        case EWOS_EIO: return "toolbox file error";
     }
     return "unknown status";
 }
@@ -364,6 +368,149 @@ ewos_status ewos_toolbox_shape(const ewos_toolbox* tb, int* dim, int64_t* n, int
 }
 
 void ewos_toolbox_free(ewos_toolbox* tb) { release(tb); }
+
+// ------------------------------------------------------------------ toolbox files
+namespace {
+
+constexpr char kTbMagic[8] = {'E', 'W', 'O', 'S', 'T', 'B', 'X', '\0'};
+constexpr uint32_t kTbVersion = 1;
+
+struct TbFileHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t dim, precision;
+    int32_t flags;            // bit 0: exit counts Hc present; bit 1: separate V-centres y present
+    int64_t n, m, p, N;
+    double eps;
+    uint64_t seed;
+    uint32_t instance, reserved;
+    ewos_build_report rep;
+};
+
+// bytes of every array after the header, in file order
+struct TbLayout {
+    int64_t x, z, y, lambda, P, KH, Hc;
+    int64_t total() const { return x + z + y + lambda + P + KH + Hc; }
+};
+
+TbLayout layout_of(const TbFileHeader& h) {
+    const int64_t e = h.precision == 64 ? 8 : 4, d = h.dim;
+    TbLayout L;
+    L.x = 8 * h.n * d;
+    L.z = 8 * h.p * d;
+    L.y = (h.flags & 2) ? 8 * h.m * d : 0;
+    L.lambda = 8 * h.n;
+    L.P = e * (d + 1) * h.n * h.m;
+    L.KH = e * (d + 1) * h.n * h.p;
+    L.Hc = (h.flags & 1) ? 4 * h.n * h.p : 0;
+    return L;
+}
+
+struct FileCloser {
+    FILE* f;
+    ~FileCloser() { if (f) std::fclose(f); }
+};
+
+constexpr size_t kChunk = size_t(64) << 20;    // host staging of the device copies
+
+// device -> file (stream already synchronised by the caller)
+ewos_status write_device(FILE* f, const void* dsrc, int64_t bytes, std::vector<char>& buf) {
+    for (int64_t off = 0; off < bytes; off += (int64_t)buf.size()) {
+        const size_t len = (size_t)std::min<int64_t>((int64_t)buf.size(), bytes - off);
+        EWOS_CUDA_TRY(cudaMemcpy(buf.data(), (const char*)dsrc + off, len, cudaMemcpyDeviceToHost));
+        if (std::fwrite(buf.data(), 1, len, f) != len) { set_error("toolbox file: write failed"); return EWOS_EIO; }
+    }
+    return EWOS_OK;
+}
+
+// file -> device
+ewos_status read_device(FILE* f, void* ddst, int64_t bytes, std::vector<char>& buf) {
+    for (int64_t off = 0; off < bytes; off += (int64_t)buf.size()) {
+        const size_t len = (size_t)std::min<int64_t>((int64_t)buf.size(), bytes - off);
+        if (std::fread(buf.data(), 1, len, f) != len) { set_error("toolbox file: read failed"); return EWOS_EIO; }
+        EWOS_CUDA_TRY(cudaMemcpy((char*)ddst + off, buf.data(), len, cudaMemcpyHostToDevice));
+    }
+    return EWOS_OK;
+}
+
+}  // namespace
+
+ewos_status ewos_toolbox_save(const ewos_toolbox* tb, const char* path) {
+    if (!tb || !path) { set_error("ewos_toolbox_save: NULL argument"); return EWOS_EINVAL; }
+    TbFileHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kTbMagic, sizeof(kTbMagic));
+    h.version = kTbVersion;
+    h.dim = tb->dim; h.precision = tb->precision;
+    h.flags = (tb->Hc ? 1 : 0) | (tb->y ? 2 : 0);
+    h.n = tb->n; h.m = tb->m; h.p = tb->p; h.N = tb->N;
+    h.eps = tb->eps; h.seed = tb->seed; h.instance = tb->instance;
+    h.rep = tb->rep;
+    EWOS_CUDA_TRY(cudaStreamSynchronize(tb->stream));
+    FileCloser fc{std::fopen(path, "wb")};
+    if (!fc.f) { set_error(std::string("toolbox file: cannot open for writing: ") + path); return EWOS_EIO; }
+    if (std::fwrite(&h, sizeof(h), 1, fc.f) != 1) { set_error("toolbox file: write failed"); return EWOS_EIO; }
+    const TbLayout L = layout_of(h);
+    std::vector<char> buf((size_t)std::min<int64_t>((int64_t)kChunk, std::max<int64_t>(1, L.total())));
+    const std::pair<const void*, int64_t> parts[] = {{tb->x, L.x}, {tb->z, L.z}, {tb->y, L.y}, {tb->lambda, L.lambda},
+                                                     {tb->P, L.P}, {tb->KH, L.KH}, {tb->Hc, L.Hc}};
+    for (const auto& pt : parts) {
+        if (pt.second == 0) continue;
+        ewos_status s = write_device(fc.f, pt.first, pt.second, buf);
+        if (s != EWOS_OK) return s;
+    }
+    if (std::fflush(fc.f) != 0) { set_error("toolbox file: write failed"); return EWOS_EIO; }
+    return EWOS_OK;
+}
+
+ewos_status ewos_toolbox_load(const char* path, void* stream, ewos_toolbox** out) {
+    if (!path || !out) { set_error("ewos_toolbox_load: NULL argument"); return EWOS_EINVAL; }
+    *out = nullptr;
+    FileCloser fc{std::fopen(path, "rb")};
+    if (!fc.f) { set_error(std::string("toolbox file: cannot open: ") + path); return EWOS_EIO; }
+    TbFileHeader h;
+    if (std::fread(&h, sizeof(h), 1, fc.f) != 1 || std::memcmp(h.magic, kTbMagic, sizeof(kTbMagic)) != 0) {
+        set_error("toolbox file: not a toolbox file");
+        return EWOS_EIO;
+    }
+    if (h.version != kTbVersion || (h.dim != 2 && h.dim != 3) || (h.precision != 32 && h.precision != 64) ||
+        h.n < 1 || h.m < 1 || h.p < 1 || h.N < 0 || (h.flags & ~3) != 0 || (!(h.flags & 2) && h.m != h.n) ||
+        h.n > (int64_t(1) << 31) || h.m > (int64_t(1) << 31) || h.p > (int64_t(1) << 31)) {
+        set_error("toolbox file: unsupported version or inconsistent header");
+        return EWOS_EIO;
+    }
+    const TbLayout L = layout_of(h);
+    if (std::fseek(fc.f, 0, SEEK_END) != 0) { set_error("toolbox file: cannot seek"); return EWOS_EIO; }
+    const long long size = std::ftell(fc.f);
+    if (size != (long long)sizeof(h) + L.total()) {
+        set_error("toolbox file: size does not match its header");
+        return EWOS_EIO;
+    }
+    std::fseek(fc.f, (long)sizeof(h), SEEK_SET);
+    AllocStream as((cudaStream_t)stream);
+    ewos_toolbox* tb = new ewos_toolbox();
+    tb->dim = h.dim; tb->precision = h.precision; tb->n = h.n; tb->m = h.m; tb->p = h.p; tb->N = h.N;
+    tb->eps = h.eps; tb->seed = h.seed; tb->instance = h.instance; tb->rep = h.rep;
+    tb->stream = (cudaStream_t)stream;
+    cudaGetDevice(&tb->device);
+    ewos_status s = alloc_matrices(tb, (h.flags & 1) != 0);
+    if (s == EWOS_OK && (h.flags & 2) && ::ewos::dev_alloc((void**)&tb->y, sizeof(double) * h.m * h.dim) != cudaSuccess) {
+        set_error("toolbox file: out of device memory");
+        s = EWOS_ENOMEM;
+    }
+    if (s == EWOS_OK) s = cudaStreamSynchronize(tb->stream) == cudaSuccess ? EWOS_OK : EWOS_ECUDA;
+    std::vector<char> buf((size_t)std::min<int64_t>((int64_t)kChunk, std::max<int64_t>(1, L.total())));
+    const std::pair<void*, int64_t> parts[] = {{tb->x, L.x}, {tb->z, L.z}, {tb->y, L.y}, {tb->lambda, L.lambda},
+                                               {tb->P, L.P}, {tb->KH, L.KH}, {tb->Hc, L.Hc}};
+    for (const auto& pt : parts) {
+        if (s != EWOS_OK) break;
+        if (pt.second == 0) continue;
+        s = read_device(fc.f, pt.first, pt.second, buf);
+    }
+    if (s != EWOS_OK) { release(tb); return s; }
+    *out = tb;
+    return EWOS_OK;
+}
 
 ewos_status ewos_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t count) {
     if (!ctr || !key || !out || count < 0) { set_error("ewos_debug_philox: bad arguments"); return EWOS_EINVAL; }

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libewos.so")
 _lib = None
 
-OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ENOCONV, ETIMEOUT, ESTEPCAP = range(8)
+OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ENOCONV, ETIMEOUT, ESTEPCAP, EIO = range(9)
 SDF = {"ball": 0, "box": 1, "polygon": 2}
 ARR = {"G": 0, "gradG": 1, "H": 2, "gradH": 3, "Hc": 4, "lambda": 5, "walk_exit": 6, "walk_steps": 7,
        "walk_mass": 8, "walk_vhash": 9, "walk_xexit": 10}
@@ -130,10 +130,12 @@ def lib():
         L.ewos_server_query.argtypes = [P, ctypes.POINTER(ServerStats)]
         L.ewos_server_destroy.argtypes = [P]
         L.ewos_server_destroy.restype = None
+        L.ewos_toolbox_save.argtypes = [P, ctypes.c_char_p]
+        L.ewos_toolbox_load.argtypes = [ctypes.c_char_p, P, ctypes.POINTER(P)]
         for fn in ("ewos_toolbox_build", "ewos_toolbox_build_noalloc", "ewos_toolbox_from_host", "ewos_toolbox_get", "ewos_toolbox_report",
                    "ewos_toolbox_shape", "ewos_solve", "ewos_debug_philox", "ewos_debug_green_radius",
                    "ewos_debug_tc_gemm", "ewos_server_create", "ewos_server_submit", "ewos_server_wait",
-                   "ewos_server_query", "ewos_toolbox_build_batch"):
+                   "ewos_server_query", "ewos_toolbox_build_batch", "ewos_toolbox_save", "ewos_toolbox_load"):
             getattr(L, fn).restype = I
         _lib = L
     return _lib
@@ -185,6 +187,10 @@ class Toolbox:
         r = BuildReport()
         _check(lib().ewos_toolbox_report(self._h, ctypes.byref(r)), "report")
         return r.as_dict()
+
+    def save(self, path):
+        """Write this toolbox to a file (see save_toolbox)."""
+        save_toolbox(self, path)
 
     def get(self, which, walks=None):
         d, n, m, p = self.dim, self.n, self.m, self.p
@@ -325,6 +331,18 @@ def toolbox_from_host(dim, x, z, G, gradG, H, gradH, lam, precision=64, stream=N
     _check(lib().ewos_toolbox_from_host(dim, n, p, *[a.ctypes.data for a in arrs], precision, stream, ctypes.byref(h)),
            "toolbox from host")
     return Toolbox(h.value, keep=arrs)
+
+
+def save_toolbox(tb, path):
+    """Write a toolbox to a file (ewos_toolbox_save): arrays, shape and build parameters."""
+    _check(lib().ewos_toolbox_save(tb._h, os.fsencode(path)), "toolbox save")
+
+
+def load_toolbox(path, stream=None):
+    """Read a toolbox written by save_toolbox into device memory (ewos_toolbox_load)."""
+    h = ctypes.c_void_p()
+    _check(lib().ewos_toolbox_load(os.fsencode(path), stream, ctypes.byref(h)), "toolbox load")
+    return Toolbox(h.value)
 
 
 def launch_count():
