@@ -31,7 +31,9 @@ Parity pins (tests/test_oracle_*.py): assemble -> the un-assembled bilinear form
 eq. matrix_test_varphi; lu_factor/lu_solve -> LAPACK via numpy.linalg.solve and the residual;
 solve_linear -> manufactured solutions (discretisation-error bound) and a finite-difference
 solve of the same problem; newton -> zero residual and reduction to solve_linear when N = 0;
-picard -> fixed-point property and reduction to solve_linear when A(u) = A.
+picard -> fixed-point property and reduction to solve_linear when A(u) = A; adam_steps -> the
+closed form of the first step and convergence on a separable quadratic (and adam uses residual,
+which is pinned above, as its gradient).
 """
 from __future__ import annotations
 
@@ -207,6 +209,30 @@ def tsvd_solve(M, r, rcond):
     U, sv, Vt = np.linalg.svd(M)
     keep = sv > rcond * sv[0]
     return Vt[keep].T @ ((U[:, keep].T @ r) / sv[keep])
+
+
+def adam_steps(grad, s0, alpha, beta1=0.9, beta2=0.999, eps=1e-10, iters=100):
+    """The Adam algorithm of the paper's appendix ("ADAM"), written from its formulas:
+        m_j = beta1 m_{j-1} + (1 - beta1) grad(s_{j-1}),
+        v_j = beta2 v_{j-1} + (1 - beta2) grad(s_{j-1})^2   (element-wise square),
+        alpha_j = alpha sqrt(1 - beta2^j) / (1 - beta1^j),
+        s_j = s_{j-1} - alpha_j m_j / (sqrt(v_j) + eps),   j >= 1,   m_0 = v_0 = 0.
+    grad is any callable s -> gradient (so the update can be checked on closed forms)."""
+    s = np.array(s0, dtype=np.float64)
+    m = np.zeros_like(s)
+    v = np.zeros_like(s)
+    for j in range(1, iters + 1):
+        gr = grad(s)
+        m = beta1 * m + (1.0 - beta1) * gr
+        v = beta2 * v + (1.0 - beta2) * gr * gr
+        aj = alpha * np.sqrt(1.0 - beta2 ** j) / (1.0 - beta1 ** j)
+        s = s - aj * m / (np.sqrt(v) + eps)
+    return s
+
+
+def adam(tb, lam, A, b, c, f, g, s0, alpha, beta1=0.9, beta2=0.999, eps=1e-10, iters=100, nl=None):
+    """Adam on the discrete functional J of Sec. 3.2: its gradient is R(s) (eq. gradJ)."""
+    return adam_steps(lambda s: residual(tb, lam, A, b, c, f, g, s, nl), s0, alpha, beta1, beta2, eps, iters)
 
 
 def errors(u, u_star, lam):

@@ -172,3 +172,35 @@ def test_picard_quasilinear(disk_tb):
     assert np.max(np.abs(again["u"] - res["u"])) < 1e-9
     ref = math.sqrt(np.sum(lam * st.u_star ** 2))
     assert S.errors(res["u"], st.u_star, lam)["l2"] < 0.15 * ref
+
+
+def test_adam_closed_forms():
+    # first step: m_1 = (1 - b1) g, v_1 = (1 - b2) g^2, so s_1 = s_0 - alpha g / (|g| + eps / sqrt(1 - b2))
+    g = np.array([3.0, -0.5, 2e-3, 0.0])
+    s0 = np.array([1.0, 2.0, -3.0, 4.0])
+    for eps in (1e-10, 1e-3):
+        s1 = S.adam_steps(lambda s: g, s0, 0.1, eps=eps, iters=1)
+        assert np.allclose(s1, s0 - 0.1 * g / (np.abs(g) + eps / math.sqrt(1 - 0.999)), rtol=1e-14, atol=0)
+    # a constant gradient with eps = 0: the bias corrections make every step exactly alpha sign(g)
+    g = np.array([3.0, -0.5, 2e-3])
+    for beta1, beta2 in ((0.9, 0.999), (0.5, 0.9)):
+        sk = S.adam_steps(lambda s: g, np.zeros(3), 0.1, beta1, beta2, eps=0.0, iters=7)
+        assert np.allclose(sk, -0.7 * np.sign(g), rtol=1e-12, atol=0)
+    # a separable convex quadratic: Adam reaches its minimiser
+    D = np.array([1.0, 10.0, 100.0]); st = np.array([1.0, -2.0, 0.5])
+    s = S.adam_steps(lambda s: D * (s - st), np.zeros(3), 0.05, iters=3000)
+    assert np.max(np.abs(s - st)) < 1e-6
+
+
+def test_adam_on_the_discrete_functional(disk_tb):
+    w, tb, lam = disk_tb
+    pb = w.problem
+    s0 = np.zeros(tb["G"].shape[1])
+    R0 = S.residual(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, s0)
+    # first step follows the sign of -R(s_0) = rhs (eq. gradJ: the gradient of J is R)
+    s1 = S.adam(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, s0, 0.1, iters=1)
+    assert np.allclose(s1, -0.1 * R0 / (np.abs(R0) + 1e-10 / math.sqrt(1 - 0.999)), rtol=1e-12, atol=0)
+    # and the iteration drives the gradient of J down
+    s = S.adam(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, s0, 0.1, iters=500)
+    R = S.residual(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, s)
+    assert np.linalg.norm(R) < 0.2 * np.linalg.norm(R0)
