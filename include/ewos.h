@@ -262,6 +262,38 @@ typedef struct {
 ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, double* u_out, double* s_out,
                        int outputs_on_device, ewos_solve_report* rep);
 
+/* Euler-Lagrange route (Sec. 3.2): the gradient of the discrete functional,
+ *   grad J(s) = R(s) = P^T w,  w_i = M_i (P_i s + KH_i g) + e_d lam_i (N(u_i) - f_i)     (eq. gradJ),
+ * for the problem's A, b, c, f, g (first right-hand side) and a semilinear N (a quasilinear
+ * equation is not the Euler-Lagrange equation of a functional: EWOS_EINVAL).  s [m] and grad [m]
+ * are host buffers (device buffers when pb->inputs_on_device = 1); evaluated in FP64 on the
+ * toolbox's P and KH. */
+ewos_status ewos_gradient(ewos_toolbox* tb, const ewos_problem* pb, const double* s, double* grad);
+
+/* Adam on J (the paper's appendix algorithm; its Examples use beta1 = 0.9, beta2 = 0.999,
+ * eps = 1e-10): m_j = beta1 m_{j-1} + (1 - beta1) grad J(s_{j-1}), v_j likewise with the squared
+ * gradient, alpha_j = alpha sqrt(1 - beta2^j) / (1 - beta1^j), s_j = s_{j-1} - alpha_j m_j /
+ * (sqrt(v_j) + eps), all on the device.  Runs max_iter steps, or stops earlier when the weighted
+ * gradient norm (sum_i w_i grad_i^2)^(1/2) <= tol (w = lambda when the V-centres are the nodes,
+ * else 1; checked every check_every steps, default 10; tol <= 0: never).  s_inout [m] holds the
+ * start and receives the result; u_out [n] (may be NULL) receives u = G s + H g. */
+typedef struct {
+    double alpha, beta1, beta2, eps;
+    int64_t max_iter;
+    double tol;
+    int check_every;
+} ewos_adam_opts;
+
+typedef struct {
+    int64_t iters;            /* Adam steps taken                                            */
+    double grad_norm;         /* weighted gradient norm at the returned s                   */
+    int converged;            /* grad_norm <= tol                                            */
+    double ms_total;
+} ewos_adam_report;
+
+ewos_status ewos_minimize_adam(ewos_toolbox* tb, const ewos_problem* pb, const ewos_adam_opts* opts,
+                               double* s_inout, double* u_out, ewos_adam_report* rep);
+
 /*
  * Request server (no counterpart in the paper; the serving loop around ewos_solve).  Solve
  * requests on device-resident toolboxes are queued in arrival order and admitted to worker

@@ -1828,7 +1828,8 @@ void free_workspace(SolveWorkspace* ws) {
     delete ws;
 }
 
-static ewos_status ensure_workspace(const ewos_toolbox* tb, SolveWorkspace*& slot, int64_t nrhs, bool mixed) {
+static ewos_status ensure_workspace(const ewos_toolbox* tb, SolveWorkspace*& slot, int64_t nrhs, bool mixed,
+                                    bool matrices = true) {
     if (slot && (slot->cap_rhs < nrhs || slot->n != tb->n || slot->m != tb->m || slot->p != tb->p || slot->D != tb->dim)) {
         free_workspace(slot);
         slot = nullptr;
@@ -1873,6 +1874,7 @@ static ewos_status ensure_workspace(const ewos_toolbox* tb, SolveWorkspace*& slo
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.flow, sizeof(unsigned int) * flow_state_words(m)));
     }
     SolveWorkspace* ws = slot;
+    if (!matrices) return EWOS_OK;            // the vectors suffice (gradient, Adam)
     if (!mixed && !ws->Q) {
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Q, sizeof(double) * E * n * m));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Lam, sizeof(double) * m * m));
@@ -3208,7 +3210,158 @@ ewos_status solve_on(ewos_toolbox* tb, SolveWorkspace*& wslot, const ewos_proble
     return s;
 }
 
+// ------------------------------------------------------------------ gradient of J and Adam
+// grad J(s) = R(s) (eq. gradJ, Sec. 3.2: the Galerkin residual of the variational form), evaluated
+// matrix-free in FP64 with the coefficient blocks M_i; Adam as in the paper's appendix algorithm:
+//   m_j = b1 m_{j-1} + (1 - b1) grad J,  v_j = b2 v_{j-1} + (1 - b2) (grad J)^2,
+//   alpha_j = alpha sqrt(1 - b2^j) / (1 - b1^j),  s_j = s_{j-1} - alpha_j m_j / (sqrt(v_j) + eps).
+__global__ void adam_kernel(int64_t m, const double* __restrict__ g, double* __restrict__ mo, double* __restrict__ vo,
+                            double* __restrict__ s, double alpha_j, double b1, double b2, double eps) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m) return;
+    const double gt = g[t];
+    const double mj = b1 * mo[t] + (1.0 - b1) * gt;
+    const double vj = b2 * vo[t] + (1.0 - b2) * gt * gt;
+    mo[t] = mj;
+    vo[t] = vj;
+    s[t] -= alpha_j * mj / (sqrt(vj) + eps);
+}
+
+// sum_i w_i y_i^2 (w = NULL: all weights 1)
+__global__ void wsumsq_kernel(const double* __restrict__ y, const double* __restrict__ w, int64_t len,
+                              double* __restrict__ out) {
+    double acc = 0.0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < len; t += (int64_t)gridDim.x * blockDim.x)
+        acc += (w ? w[t] : 1.0) * y[t] * y[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+// the problem's first column and coefficients on the device, M_i formed (semilinear or linear)
+static ewos_status prepare_gradient(ewos_toolbox* tb, SolveWorkspace*& wslot, const ewos_problem* pb, Ctx& C) {
+    if (!pb->A || !pb->f || !pb->g) { set_error("gradient: need a problem with A, f, g"); return EWOS_EINVAL; }
+    if (pb->nl_kind == EWOS_NL_QUASILINEAR) {
+        set_error("gradient: a quasilinear equation is not the Euler-Lagrange equation of a functional");
+        return EWOS_EINVAL;
+    }
+    if (pb->nl_kind == EWOS_NL_SEMILINEAR && (!pb->nl_coef || pb->nl_ncoef < 1 || pb->nl_ncoef > 64)) {
+        set_error("gradient: the nonlinearity needs 1..64 coefficients");
+        return EWOS_EINVAL;
+    }
+    AllocStream as(C.st);
+    ewos_status s = ensure_workspace(tb, wslot, 1, false, false);
+    if (s != EWOS_OK) return s;
+    SolveWorkspace* ws = wslot;
+    C.ws = ws;
+    const cudaMemcpyKind k = pb->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const int D = tb->dim;
+    EWOS_CUDA_TRY(cudaMemcpyAsync(ws->A, pb->A, sizeof(double) * tb->n * D * D, k, C.st));
+    if (pb->b) EWOS_CUDA_TRY(cudaMemcpyAsync(ws->b, pb->b, sizeof(double) * tb->n * D, k, C.st));
+    if (pb->c) EWOS_CUDA_TRY(cudaMemcpyAsync(ws->c, pb->c, sizeof(double) * tb->n, k, C.st));
+    EWOS_CUDA_TRY(cudaMemcpyAsync(ws->f, pb->f, sizeof(double) * tb->n, k, C.st));
+    EWOS_CUDA_TRY(cudaMemcpyAsync(ws->g, pb->g, sizeof(double) * tb->p, k, C.st));
+    if (pb->nl_kind == EWOS_NL_SEMILINEAR)
+        EWOS_CUDA_TRY(cudaMemcpyAsync(ws->nl, pb->nl_coef, sizeof(double) * pb->nl_ncoef, cudaMemcpyHostToDevice, C.st));
+    ::ewos::note_launch(), coef_kernel<<<(int)((C.n + 127) / 128), 128, 0, C.st>>>((int)C.n, C.D, tb->lambda, ws->A,
+                                                                                pb->b ? ws->b : nullptr,
+                                                                                pb->c ? ws->c : nullptr, nullptr, 0,
+                                                                                nullptr, ws->M);
+    return EWOS_OK;
+}
+
+static void gradient_at(const Ctx& C, const ewos_problem* pb, const double* s, double* y) {
+    const double* nl = pb->nl_kind == EWOS_NL_SEMILINEAR ? C.ws->nl : nullptr;
+    const int nnl = pb->nl_kind == EWOS_NL_SEMILINEAR ? pb->nl_ncoef : 0;
+    if (C.tb->precision == 64) residual<double>(C, s, C.ws->g, C.ws->f, nl, nnl, 0.0, y);
+    else residual<float>(C, s, C.ws->g, C.ws->f, nl, nnl, 0.0, y);
+}
+
+// (sum_i w_i y_i^2)^(1/2), w = lambda when the V-centres are the nodes, else 1 (synchronises)
+static double grad_norm(const Ctx& C, const double* y) {
+    cudaMemsetAsync(C.ws->scal, 0, sizeof(double), C.st);
+    const double* w = C.tb->y ? nullptr : C.tb->lambda;
+    ::ewos::note_launch(), wsumsq_kernel<<<std::max<int64_t>(1, std::min<int64_t>(1024, (C.m + 255) / 256)), 256, 0, C.st>>>(
+                               y, w, C.m, C.ws->scal);
+    double h = 0;
+    cudaMemcpyAsync(&h, C.ws->scal, sizeof(double), cudaMemcpyDeviceToHost, C.st);
+    cudaStreamSynchronize(C.st);
+    return std::sqrt(h);
+}
+
 }  // namespace ewos
+
+extern "C" ewos_status ewos_gradient(ewos_toolbox* tb, const ewos_problem* pb, const double* s, double* grad) {
+    using namespace ewos;
+    if (!tb || !pb || !s || !grad) { set_error("ewos_gradient: NULL argument"); return EWOS_EINVAL; }
+    Ctx C{tb, nullptr, pb->stream ? (cudaStream_t)pb->stream : tb->stream, tb->dim, tb->dim + 1, tb->n, tb->m, tb->p};
+    ewos_status st = prepare_gradient(tb, tb->ws, pb, C);
+    if (st != EWOS_OK) return st;
+    const cudaMemcpyKind k = pb->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    EWOS_CUDA_TRY(cudaMemcpyAsync(C.ws->s, s, sizeof(double) * tb->m, k, C.st));
+    gradient_at(C, pb, C.ws->s, C.ws->y);
+    const cudaMemcpyKind ko = pb->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    EWOS_CUDA_TRY(cudaMemcpyAsync(grad, C.ws->y, sizeof(double) * tb->m, ko, C.st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(C.st));
+    return EWOS_OK;
+}
+
+extern "C" ewos_status ewos_minimize_adam(ewos_toolbox* tb, const ewos_problem* pb, const ewos_adam_opts* opts,
+                                         double* s_inout, double* u_out, ewos_adam_report* rep) {
+    using namespace ewos;
+    if (!tb || !pb || !opts || !s_inout) { set_error("ewos_minimize_adam: NULL argument"); return EWOS_EINVAL; }
+    if (!(opts->alpha > 0) || !(opts->beta1 >= 0 && opts->beta1 < 1) || !(opts->beta2 >= 0 && opts->beta2 < 1) ||
+        !(opts->eps > 0) || opts->max_iter < 0) {
+        set_error("ewos_minimize_adam: need alpha > 0, beta1 and beta2 in [0, 1), eps > 0, max_iter >= 0");
+        return EWOS_EINVAL;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    Ctx C{tb, nullptr, pb->stream ? (cudaStream_t)pb->stream : tb->stream, tb->dim, tb->dim + 1, tb->n, tb->m, tb->p};
+    ewos_status st = prepare_gradient(tb, tb->ws, pb, C);
+    if (st != EWOS_OK) return st;
+    SolveWorkspace* ws = C.ws;
+    const cudaMemcpyKind k = pb->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    EWOS_CUDA_TRY(cudaMemcpyAsync(ws->s, s_inout, sizeof(double) * tb->m, k, C.st));
+    EWOS_CUDA_TRY(cudaMemsetAsync(ws->r, 0, sizeof(double) * tb->m, C.st));     // first moment
+    EWOS_CUDA_TRY(cudaMemsetAsync(ws->dx, 0, sizeof(double) * tb->m, C.st));    // second moment
+    const int check = opts->check_every > 0 ? opts->check_every : 10;
+    double p1 = 1.0, p2 = 1.0, gn = 0.0;
+    int64_t j = 0;
+    bool conv = false;
+    while (j < opts->max_iter) {
+        gradient_at(C, pb, ws->s, ws->y);
+        if (opts->tol > 0 && j % check == 0) {
+            gn = grad_norm(C, ws->y);
+            if (gn <= opts->tol) { conv = true; break; }
+        }
+        ++j;
+        p1 *= opts->beta1;
+        p2 *= opts->beta2;
+        const double aj = opts->alpha * std::sqrt(1.0 - p2) / (1.0 - p1);
+        ::ewos::note_launch(), adam_kernel<<<(int)((tb->m + 255) / 256), 256, 0, C.st>>>(tb->m, ws->y, ws->r, ws->dx, ws->s, aj,
+                                                                                       opts->beta1, opts->beta2, opts->eps);
+    }
+    if (!conv) {                              // the gradient at the final iterate
+        gradient_at(C, pb, ws->s, ws->y);
+        gn = grad_norm(C, ws->y);
+        conv = opts->tol > 0 && gn <= opts->tol;
+    }
+    const cudaMemcpyKind ko = pb->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    EWOS_CUDA_TRY(cudaMemcpyAsync(s_inout, ws->s, sizeof(double) * tb->m, ko, C.st));
+    if (u_out) {
+        u_from_s(C, tb->P, tb->KH, tb->precision == 64, ws->s, ws->g, ws->u);
+        EWOS_CUDA_TRY(cudaMemcpyAsync(u_out, ws->u, sizeof(double) * tb->n, ko, C.st));
+    }
+    EWOS_CUDA_TRY(cudaStreamSynchronize(C.st));
+    EWOS_CUDA_TRY(cudaGetLastError());
+    if (rep) {
+        rep->iters = j;
+        rep->grad_norm = gn;
+        rep->converged = conv ? 1 : 0;
+        rep->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return EWOS_OK;
+}
 
 extern "C" ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, double* u_out, double* s_out,
                                   int outputs_on_device, ewos_solve_report* rep_out) {

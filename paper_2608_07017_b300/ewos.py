@@ -73,6 +73,20 @@ class SolveReport(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class AdamOpts(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double), ("max_iter", ctypes.c_int64), ("tol", ctypes.c_double),
+                ("check_every", ctypes.c_int)]
+
+
+class AdamReport(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("grad_norm", ctypes.c_double), ("converged", ctypes.c_int),
+                ("ms_total", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class ServerOpts(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int), ("memory_fraction", ctypes.c_double), ("reserve_bytes", ctypes.c_int64),
                 ("budget_bytes", ctypes.c_int64)]
@@ -132,10 +146,14 @@ def lib():
         L.ewos_server_destroy.restype = None
         L.ewos_toolbox_save.argtypes = [P, ctypes.c_char_p]
         L.ewos_toolbox_load.argtypes = [ctypes.c_char_p, P, ctypes.POINTER(P)]
+        L.ewos_gradient.argtypes = [P, ctypes.POINTER(_Problem), P, P]
+        L.ewos_minimize_adam.argtypes = [P, ctypes.POINTER(_Problem), ctypes.POINTER(AdamOpts), P, P,
+                                         ctypes.POINTER(AdamReport)]
         for fn in ("ewos_toolbox_build", "ewos_toolbox_build_noalloc", "ewos_toolbox_from_host", "ewos_toolbox_get", "ewos_toolbox_report",
                    "ewos_toolbox_shape", "ewos_solve", "ewos_debug_philox", "ewos_debug_green_radius",
                    "ewos_debug_tc_gemm", "ewos_server_create", "ewos_server_submit", "ewos_server_wait",
-                   "ewos_server_query", "ewos_toolbox_build_batch", "ewos_toolbox_save", "ewos_toolbox_load"):
+                   "ewos_server_query", "ewos_toolbox_build_batch", "ewos_toolbox_save", "ewos_toolbox_load",
+                   "ewos_gradient", "ewos_minimize_adam"):
             getattr(L, fn).restype = I
         _lib = L
     return _lib
@@ -241,6 +259,34 @@ class Toolbox:
             u = u[0]
             s = None if s is None else s[0]
         return u, s, r
+
+
+    def _problem1(self, A, f, g, b, c, kind, coef):
+        arrs = [_f64(a) for a in (A, b, c, f, g)]
+        cf = _f64(coef) if coef is not None else None
+        pb = _Problem(*[_ptr(a) for a in arrs], 1, NL[kind], _ptr(cf), 0 if cf is None else cf.size, MODE["fp64"],
+                      0.0, 0.0, 0, 0, None, 0, 0)
+        return pb, (arrs, cf)
+
+    def gradient(self, s, A, f, g, b=None, c=None, kind="linear", coef=None):
+        """grad J(s) = R(s) of the Euler-Lagrange route (ewos_gradient); host arrays."""
+        pb, keep = self._problem1(A, f, g, b, c, kind, coef)
+        ss = _f64(s)
+        out = np.zeros(self.m)
+        _check(lib().ewos_gradient(self._h, ctypes.byref(pb), ss.ctypes.data, out.ctypes.data), "gradient")
+        return out
+
+    def minimize_adam(self, A, f, g, b=None, c=None, kind="linear", coef=None, s0=None, alpha=1e-3, beta1=0.9,
+                      beta2=0.999, eps=1e-10, max_iter=1000, tol=0.0, check_every=0):
+        """Adam on J (ewos_minimize_adam); returns (s, u, report)."""
+        pb, keep = self._problem1(A, f, g, b, c, kind, coef)
+        s = np.zeros(self.m) if s0 is None else _f64(s0).copy()
+        u = np.zeros(self.n)
+        o = AdamOpts(float(alpha), float(beta1), float(beta2), float(eps), int(max_iter), float(tol), int(check_every))
+        rep = AdamReport()
+        _check(lib().ewos_minimize_adam(self._h, ctypes.byref(pb), ctypes.byref(o), s.ctypes.data, u.ctypes.data,
+                                        ctypes.byref(rep)), "minimize_adam")
+        return s, u, rep.as_dict()
 
 
 def build_toolbox(domain_kind, dim, params, x, z, walks, eps, seed=0, precision=32, max_steps=0, cell_weights=None,
