@@ -31,7 +31,10 @@ Parity pins (tests/test_oracle_*.py): assemble -> the un-assembled bilinear form
 eq. matrix_test_varphi; lu_factor/lu_solve -> LAPACK via numpy.linalg.solve and the residual;
 solve_linear -> manufactured solutions (discretisation-error bound) and a finite-difference
 solve of the same problem; newton -> zero residual and reduction to solve_linear when N = 0;
-picard -> fixed-point property and reduction to solve_linear when A(u) = A; adam_steps -> the
+picard -> fixed-point property and reduction to solve_linear when A(u) = A; operators -> they
+reproduce solve_linear for any (f, g) (which checks sigma against rhs), the torsion function
+and the constant 1 on the disk, and the symmetry of GL diag(lam)^(-1) for a self-adjoint
+operator; adam_steps -> the
 closed form of the first step and convergence on a separable quadratic (and adam uses residual,
 which is pinned above, as its gradient).
 """
@@ -209,6 +212,39 @@ def tsvd_solve(M, r, rcond):
     U, sv, Vt = np.linalg.svd(M)
     keep = sv > rcond * sv[0]
     return Vt[keep].T @ ((U[:, keep].T @ r) / sv[keep])
+
+
+def sigma(tb, lam, A, b=None, c=None):
+    """Sigma of eq. linear_q (m x p), from its formula in the header above."""
+    G, gradG, H, gradH = tb["G"], tb["gradG"], tb["H"], tb["gradH"]
+    d = gradG.shape[0]
+    Sig = np.zeros((G.shape[1], H.shape[1]))
+    for k in range(d):
+        for l in range(d):
+            Sig += gradG[k].T @ ((lam * A[:, k, l])[:, None] * gradH[l])
+    if b is not None:
+        Bh = sum(b[:, k][:, None] * gradH[k] for k in range(d))
+        Sig += G.T @ (lam[:, None] * Bh)
+    if c is not None:
+        Sig += G.T @ ((lam * c)[:, None] * H)
+    return Sig
+
+
+def operators(tb, lam, A, b=None, c=None, rcond=DEFAULT_RCOND, alpha=None):
+    """The Monte Carlo operator estimates that follow eq. linear_inversion (Sec. 3.1):
+        Green operator     GL = G (Lambda + alpha I)^(-1) A^lam,       A^lam = G^T diag(lam)  [n x n],
+        elliptic measure   HL = H - G (Lambda + alpha I)^(-1) Sigma                          [n x p],
+    so that the linear solve of the same problem is u = GL f + HL g (the paper's -A and
+    -A^lam are G and G^T diag(lam) here, with f -> -f as in the header).  Lambda + alpha I is
+    the shifted matrix of solve_linear."""
+    G = tb["G"]
+    Lam = assemble(G, tb["gradG"], lam, A, b, c)
+    alpha = shift(Lam, rcond) if alpha is None else float(alpha)
+    lu, piv = lu_factor(Lam + alpha * np.eye(Lam.shape[0]))
+    Alam = G.T * lam[None, :]
+    GL = G @ lu_solve(lu, piv, Alam)
+    HL = tb["H"] - G @ lu_solve(lu, piv, sigma(tb, lam, A, b, c))
+    return dict(GL=GL, HL=HL, alpha=alpha)
 
 
 def adam_steps(grad, s0, alpha, beta1=0.9, beta2=0.999, eps=1e-10, iters=100):

@@ -204,3 +204,30 @@ def test_adam_on_the_discrete_functional(disk_tb):
     s = S.adam(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, s0, 0.1, iters=500)
     R = S.residual(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, s)
     assert np.linalg.norm(R) < 0.2 * np.linalg.norm(R0)
+
+
+def test_operator_estimates(disk_tb):
+    """The Green-operator and elliptic-measure estimates that follow eq. linear_inversion."""
+    w, tb, lam = disk_tb
+    n, p = w.x.shape[0], w.z.shape[0]
+    pb = w.problem
+    # they are the solution map of the linear solve (with first- and zeroth-order terms)
+    b = np.stack([np.sin(3 * w.x[:, 0]), np.cos(2 * w.x[:, 1])], axis=1)
+    c = 1.0 + w.x[:, 0] ** 2
+    op = S.operators(tb, lam, pb.A, b, c)
+    rng = np.random.default_rng(11)
+    for _ in range(2):
+        f, g = rng.normal(size=n), rng.normal(size=p)
+        lin = S.solve_linear(tb, lam, pb.A, b, c, f, g)
+        assert np.max(np.abs(op["GL"] @ f + op["HL"] @ g - lin["u"])) <= 1e-12 * np.max(np.abs(lin["u"]))
+    # L = -Laplacian on the unit disk: G^L 1 is the torsion function (1 - |x|^2)/4 (within the
+    # Tikhonov bias and Monte Carlo error of the default shift), H^L 1 = 1 (mu_x is a
+    # probability measure), and G^L(x, y) = G^L(y, x) makes G diag(lam)^(-1) symmetric
+    eye = np.tile(np.eye(2), (n, 1, 1))
+    op = S.operators(tb, lam, eye)
+    tors = (1.0 - np.sum(w.x ** 2, axis=1)) / 4.0
+    e = op["GL"] @ np.ones(n) - tors
+    assert np.sqrt(np.sum(lam * e * e) / np.sum(lam * tors * tors)) < 0.15
+    assert np.max(np.abs(op["HL"] @ np.ones(p) - 1.0)) < 0.08
+    Sym = op["GL"] / lam[None, :]
+    assert np.max(np.abs(Sym - Sym.T)) <= 1e-12 * np.max(np.abs(Sym))
