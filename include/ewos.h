@@ -294,6 +294,19 @@ typedef struct {
 ewos_status ewos_minimize_adam(ewos_toolbox* tb, const ewos_problem* pb, const ewos_adam_opts* opts,
                                double* s_inout, double* u_out, ewos_adam_report* rep);
 
+/* Operator estimates (Sec. 3.1, after eq. linear_inversion): the matrices of the linear solve
+ * map u = GL f + HL g of ewos_solve for the problem's A, b, c, mode, rcond, pivoting and stream
+ * (f, g, nrhs and batched are ignored; nl_kind must be EWOS_NL_NONE, else EWOS_EINVAL):
+ *   GL [n][n] = G (Lambda + alpha I)^(-1) G^T diag(lambda)      (the Green operator G^L at the nodes),
+ *   HL [n][p] = H - G (Lambda + alpha I)^(-1) Sigma             (the elliptic measure H^L),
+ * both row-major (GL[i][k] weighs f at node k for u at node i).  Computed as one solve with the
+ * n + p unit right-hand sides (f = e_k; g = e_j) on a private workspace of n + p right-hand sides
+ * that is freed before the call returns (device memory about 8 (6 m + 4 n + 2 p)(n + p) bytes on
+ * top of the workspace matrices).  Either output may be NULL; both are host buffers, or device
+ * buffers when outputs_on_device = 1.  rep (may be NULL) as for ewos_solve. */
+ewos_status ewos_operators(ewos_toolbox* tb, const ewos_problem* pb, double* GL, double* HL,
+                           int outputs_on_device, ewos_solve_report* rep);
+
 /*
  * Request server (no counterpart in the paper; the serving loop around ewos_solve).  Solve
  * requests on device-resident toolboxes are queued in arrival order and admitted to worker

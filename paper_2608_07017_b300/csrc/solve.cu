@@ -3373,3 +3373,105 @@ extern "C" ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, doub
     opt.batched = pb && pb->batched != 0;
     return ewos::solve_on(tb, tb->ws, pb, u_out, s_out, outputs_on_device, rep_out, opt);
 }
+
+// ------------------------------------------------------------------ operator estimates
+namespace ewos {
+
+// unit right-hand sides: F [R][n] with F[k][k] = 1 (k < n), Gb [R][p] with Gb[n + j][j] = 1
+__global__ void unit_rhs_kernel(double* __restrict__ F, double* __restrict__ Gb, int64_t n, int64_t p) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) F[t * n + t] = 1.0;
+    else if (t < n + p) Gb[t * p + (t - n)] = 1.0;
+}
+
+// out[i][k - k0] = U[k][i] for k in [k0, k0 + cols), i < n  (32 x 32 tiles through shared memory)
+__global__ void transpose_cols_kernel(const double* __restrict__ U, int64_t n, int64_t k0, int64_t cols,
+                                      double* __restrict__ out) {
+    __shared__ double tile[32][33];
+    const int64_t kb = (int64_t)blockIdx.y * 32, ib = (int64_t)blockIdx.x * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t k = kb + r, i = ib + threadIdx.x;
+        if (k < cols && i < n) tile[r][threadIdx.x] = U[(k0 + k) * n + i];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = ib + r, k = kb + threadIdx.x;
+        if (i < n && k < cols) out[i * cols + k] = tile[threadIdx.x][r];
+    }
+}
+
+static ewos_status transpose_out(const double* U, int64_t n, int64_t k0, int64_t cols, double* dst, bool dst_on_device,
+                                 double* stage, cudaStream_t st) {
+    if (!dst || cols == 0) return EWOS_OK;
+    double* out = dst_on_device ? dst : stage;
+    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((cols + 31) / 32));
+    ::ewos::note_launch(), transpose_cols_kernel<<<grid, dim3(32, 8), 0, st>>>(U, n, k0, cols, out);
+    if (!dst_on_device) EWOS_CUDA_TRY(cudaMemcpyAsync(dst, stage, sizeof(double) * n * cols, cudaMemcpyDeviceToHost, st));
+    return EWOS_OK;
+}
+
+}  // namespace ewos
+
+extern "C" ewos_status ewos_operators(ewos_toolbox* tb, const ewos_problem* pb, double* GL, double* HL,
+                                      int outputs_on_device, ewos_solve_report* rep) {
+    using namespace ewos;
+    if (!tb || !pb || !pb->A || (!GL && !HL)) { set_error("ewos_operators: need toolbox, problem with A, and an output"); return EWOS_EINVAL; }
+    if (pb->nl_kind != EWOS_NL_NONE) { set_error("ewos_operators: the operator estimates are for the linear problem"); return EWOS_EINVAL; }
+    if (pb->mode != EWOS_SOLVE_FP64 && pb->mode != EWOS_SOLVE_MIXED) { set_error("ewos_operators: unknown mode"); return EWOS_EINVAL; }
+    const cudaStream_t st = pb->stream ? (cudaStream_t)pb->stream : tb->stream;
+    const int64_t n = tb->n, p = tb->p, R = n + p, D = tb->dim;
+    double *F = nullptr, *Gb = nullptr, *U = nullptr, *Ad = nullptr, *bd = nullptr, *cd = nullptr, *stage = nullptr;
+    SolveWorkspace* ws = nullptr;
+    ewos_status s = EWOS_OK;
+    auto cleanup = [&]() {
+        AllocStream as(st);
+        ::ewos::dev_free(F); ::ewos::dev_free(Gb); ::ewos::dev_free(U); ::ewos::dev_free(Ad);
+        ::ewos::dev_free(bd); ::ewos::dev_free(cd); ::ewos::dev_free(stage);
+        if (ws) free_workspace(ws);
+    };
+    const bool host = pb->inputs_on_device == 0;
+    {
+        AllocStream as(st);
+        cudaError_t e = ::ewos::dev_alloc((void**)&F, sizeof(double) * R * n);
+        if (e == cudaSuccess) e = ::ewos::dev_alloc((void**)&Gb, sizeof(double) * R * p);
+        if (e == cudaSuccess) e = ::ewos::dev_alloc((void**)&U, sizeof(double) * R * n);
+        if (e == cudaSuccess && !outputs_on_device) e = ::ewos::dev_alloc((void**)&stage, sizeof(double) * n * std::max(n, p));
+        if (e == cudaSuccess && host) e = ::ewos::dev_alloc((void**)&Ad, sizeof(double) * n * D * D);
+        if (e == cudaSuccess && host && pb->b) e = ::ewos::dev_alloc((void**)&bd, sizeof(double) * n * D);
+        if (e == cudaSuccess && host && pb->c) e = ::ewos::dev_alloc((void**)&cd, sizeof(double) * n);
+        if (e != cudaSuccess) {
+            set_error(std::string("ewos_operators: ") + cudaGetErrorString(e));
+            cleanup();
+            return e == cudaErrorMemoryAllocation ? EWOS_ENOMEM : EWOS_ECUDA;
+        }
+        if (host) {
+            e = cudaMemcpyAsync(Ad, pb->A, sizeof(double) * n * D * D, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess && pb->b) e = cudaMemcpyAsync(bd, pb->b, sizeof(double) * n * D, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess && pb->c) e = cudaMemcpyAsync(cd, pb->c, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(F, 0, sizeof(double) * R * n, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(Gb, 0, sizeof(double) * R * p, st);
+        if (e != cudaSuccess) { set_error(std::string("ewos_operators: ") + cudaGetErrorString(e)); cleanup(); return EWOS_ECUDA; }
+        ::ewos::note_launch(), unit_rhs_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(F, Gb, n, p);
+    }
+    ewos_problem q = *pb;
+    q.A = host ? Ad : pb->A;
+    q.b = host ? bd : pb->b;
+    q.c = host ? cd : pb->c;
+    q.f = F;
+    q.g = Gb;
+    q.nrhs = R;
+    q.inputs_on_device = 1;
+    q.stream = st;
+    q.batched = 0;
+    SolveOptions opt;
+    s = solve_on(tb, ws, &q, U, nullptr, 1, rep, opt);
+    if (s == EWOS_OK) {
+        AllocStream as(st);
+        s = transpose_out(U, n, 0, n, GL, outputs_on_device != 0, stage, st);
+        if (s == EWOS_OK) s = transpose_out(U, n, n, p, HL, outputs_on_device != 0, stage, st);
+        if (s == EWOS_OK && cudaStreamSynchronize(st) != cudaSuccess) { set_error("ewos_operators: stream"); s = EWOS_ECUDA; }
+    }
+    cleanup();
+    return s;
+}

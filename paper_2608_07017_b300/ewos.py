@@ -147,13 +147,14 @@ def lib():
         L.ewos_toolbox_save.argtypes = [P, ctypes.c_char_p]
         L.ewos_toolbox_load.argtypes = [ctypes.c_char_p, P, ctypes.POINTER(P)]
         L.ewos_gradient.argtypes = [P, ctypes.POINTER(_Problem), P, P]
+        L.ewos_operators.argtypes = [P, ctypes.POINTER(_Problem), P, P, I, ctypes.POINTER(SolveReport)]
         L.ewos_minimize_adam.argtypes = [P, ctypes.POINTER(_Problem), ctypes.POINTER(AdamOpts), P, P,
                                          ctypes.POINTER(AdamReport)]
         for fn in ("ewos_toolbox_build", "ewos_toolbox_build_noalloc", "ewos_toolbox_from_host", "ewos_toolbox_get", "ewos_toolbox_report",
                    "ewos_toolbox_shape", "ewos_solve", "ewos_debug_philox", "ewos_debug_green_radius",
                    "ewos_debug_tc_gemm", "ewos_server_create", "ewos_server_submit", "ewos_server_wait",
                    "ewos_server_query", "ewos_toolbox_build_batch", "ewos_toolbox_save", "ewos_toolbox_load",
-                   "ewos_gradient", "ewos_minimize_adam"):
+                   "ewos_gradient", "ewos_minimize_adam", "ewos_operators"):
             getattr(L, fn).restype = I
         _lib = L
     return _lib
@@ -275,6 +276,18 @@ class Toolbox:
         out = np.zeros(self.m)
         _check(lib().ewos_gradient(self._h, ctypes.byref(pb), ss.ctypes.data, out.ctypes.data), "gradient")
         return out
+
+    def operators(self, A, b=None, c=None, mode="fp64", rcond=-1.0, pivoting=0, want=("GL", "HL")):
+        """Green-operator and elliptic-measure estimates (ewos_operators): (GL [n][n], HL [n][p],
+        report); an output not in `want` is not computed into (returned as None)."""
+        arrs = [_f64(a) for a in (A, b, c)]
+        pb = _Problem(_ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), None, None, 0, NL["linear"], None, 0, MODE[mode],
+                      float(rcond), 0.0, 0, 0, None, int(pivoting), 0)
+        GL = np.zeros((self.n, self.n)) if "GL" in want else None
+        HL = np.zeros((self.n, self.p)) if "HL" in want else None
+        rep = SolveReport()
+        _check(lib().ewos_operators(self._h, ctypes.byref(pb), _ptr(GL), _ptr(HL), 0, ctypes.byref(rep)), "operators")
+        return GL, HL, rep.as_dict()
 
     def minimize_adam(self, A, f, g, b=None, c=None, kind="linear", coef=None, s0=None, alpha=1e-3, beta1=0.9,
                       beta2=0.999, eps=1e-10, max_iter=1000, tol=0.0, check_every=0):
