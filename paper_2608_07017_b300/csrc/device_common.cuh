@@ -45,6 +45,8 @@ __device__ __forceinline__ float  m_log1p(float v) { return log1pf(v); }
 __device__ __forceinline__ double m_log1p(double v) { return log1p(v); }
 __device__ __forceinline__ float  m_exp(float v) { return expf(v); }
 __device__ __forceinline__ double m_exp(double v) { return exp(v); }
+__device__ __forceinline__ float  m_newton_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double m_newton_div(double a, double b) { return a / b; }
 __device__ __forceinline__ void m_sincos2pi(float u, float* s, float* c) { sincospif(2.0f * u, s, c); }
 __device__ __forceinline__ void m_sincos2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
 
@@ -63,7 +65,7 @@ template <typename T> __device__ __forceinline__ T green_radius_2d(T u) {
 #pragma unroll
     for (int it = 0; it < GreenIters<T>::value; ++it) {
         const T g = m_log1p(L) - L + a;
-        L = L + g * (T(1) + L) / L;
+        L = L + m_newton_div(g * (T(1) + L), L);
     }
     return m_exp(T(-0.5) * L);
 }
