@@ -40,8 +40,8 @@ L2_BYTES = 126 * 2 ** 20
 # per launch, both from one ncu capture of the kernel in the launch configuration this
 # benchmark runs (profiles/wos_walk_square4096.md).  The walk kernel is bound by instruction
 # issue: its roofline is 1 warp instruction per cycle per scheduler.
-WARP_INST_PER_STEP = 20.21
-WALK_DRAM_BYTES = 176.05e6
+WARP_INST_PER_STEP = 19.78
+WALK_DRAM_BYTES = 176.39e6
 
 
 def _peaks():
@@ -307,6 +307,9 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serve-fp64", type=int, default=6, help="requests of the FP64 sample per toolbox")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--walk-config", default="",
+                    help="TPB,CTAS_PER_SM,GRID_SCALE,V_IN_SMEM: a fixed walk launch shape instead of the autotuner's "
+                         "choice (a profiler run replays the shape the plain run chose)")
     ap.add_argument("--batched-build", type=int, default=1, help="1: also time the 32-instance star batch")
     ap.add_argument("--ball", type=int, default=1, help="1: also time the ball8000 Newton solve (mixed and FP64)")
     args = ap.parse_args()
@@ -340,9 +343,15 @@ def main():
     ud = torch.empty(w.x.shape[0], dtype=torch.float64, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
+    shape = {}
+    if args.walk_config:
+        tpb, ctas, scale, smem = args.walk_config.split(",")
+        shape = dict(threads_per_block=int(tpb), ctas_per_sm=int(ctas), lookup_grid_scale=float(scale),
+                     hash_in_smem=int(smem))
+
     def step():
         tb = ewos.build_toolbox("box", 2, w.domain.params, xd, zd, w.walks, w.eps, seed=w.seed, precision=32,
-                                cell_weights=w.lam, stream=sp, on_device=True)
+                                cell_weights=w.lam, stream=sp, on_device=True, **shape)
         _, _, rep = tb.solve(Ad, fd, gd, b=bd, mode=args.mode, on_device=True, out=ud, stream=sp,
                              batched=args.mode == "mixed")
         br = tb.report()
@@ -398,7 +407,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tb = ewos.build_toolbox("box", 2, w.domain.params, w.x, w.z, w.walks, w.eps, seed=w.seed, precision=32,
-                                cell_weights=w.lam, stream=sp)
+                                cell_weights=w.lam, stream=sp, **shape)
         u_host, _, _ = tb.solve(pb.A, pb.f, pb.g, b=pb.b, mode=args.mode, stream=sp, batched=args.mode == "mixed")
         torch.cuda.synchronize()
         e2e_ms.append(1000 * (time.perf_counter() - t0))
