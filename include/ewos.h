@@ -296,14 +296,17 @@ ewos_status ewos_minimize_adam(ewos_toolbox* tb, const ewos_problem* pb, const e
 
 /* Operator estimates (Sec. 3.1, after eq. linear_inversion): the matrices of the linear solve
  * map u = GL f + HL g of ewos_solve for the problem's A, b, c, mode, rcond, pivoting and stream
- * (f, g, nrhs and batched are ignored; nl_kind must be EWOS_NL_NONE, else EWOS_EINVAL):
+ * (f, g, nrhs and batched are ignored; nl_kind must be EWOS_NL_NONE, else EWOS_EINVAL; in mixed
+ * mode all columns are refined together, as with batched = 1):
  *   GL [n][n] = G (Lambda + alpha I)^(-1) G^T diag(lambda)      (the Green operator G^L at the nodes),
  *   HL [n][p] = H - G (Lambda + alpha I)^(-1) Sigma             (the elliptic measure H^L),
- * both row-major (GL[i][k] weighs f at node k for u at node i).  Computed as one solve with the
- * n + p unit right-hand sides (f = e_k; g = e_j) on a private workspace of n + p right-hand sides
- * that is freed before the call returns (device memory about 8 (6 m + 4 n + 2 p)(n + p) bytes on
- * top of the workspace matrices).  Either output may be NULL; both are host buffers, or device
- * buffers when outputs_on_device = 1.  rep (may be NULL) as for ewos_solve. */
+ * both row-major (GL[i][k] weighs f at node k for u at node i).  Computed by solving for the
+ * n + p unit right-hand sides (f = e_k; g = e_j) with one assembly and factorisation, in chunks
+ * of columns sized so that each triangular solve stays well inside its bounded waits (about
+ * 2^31 / m^2 columns in mixed mode, 32 times fewer in FP64 mode; all at once when they fit), on
+ * a private workspace freed before the call returns.  Either output may be NULL; both are host
+ * buffers, or device buffers when outputs_on_device = 1.  rep (may be NULL) as for ewos_solve,
+ * with the times summed over the chunks. */
 ewos_status ewos_operators(ewos_toolbox* tb, const ewos_problem* pb, double* GL, double* HL,
                            int outputs_on_device, ewos_solve_report* rep);
 

@@ -1774,6 +1774,7 @@ __global__ void scatter_cols_kernel(const T* __restrict__ in, double* __restrict
 
 // ------------------------------------------------------------------ workspace
 struct SolveWorkspace {
+    double last_alpha = 0.0;                  // shift of the last linear factorisation (factor reuse)
     int D = 0;
     int64_t n = 0, m = 0, p = 0;
     double *Q = nullptr, *Lam = nullptr, *LUm = nullptr, *M = nullptr, *Jx = nullptr;
@@ -2023,7 +2024,7 @@ static double elapsed_ms(std::chrono::steady_clock::time_point t0) {
 
 template <typename TP>
 static ewos_status solve_fp64(ewos_toolbox* tb, SolveWorkspace* ws, const ewos_problem* pb, double rcond, double tol, int max_iter,
-                              ewos_solve_report* rep) {
+                              ewos_solve_report* rep, bool reuse = false) {
     Ctx C{tb, ws, pb->stream ? (cudaStream_t)pb->stream : tb->stream, tb->dim, tb->dim + 1, tb->n, tb->m, tb->p};
     const int64_t nrhs = pb->nrhs;
     auto t0 = std::chrono::steady_clock::now();
@@ -2033,14 +2034,20 @@ static ewos_status solve_fp64(ewos_toolbox* tb, SolveWorkspace* ws, const ewos_p
     rep->iters = 0;
     rep->converged = 1;
     if (!quasi) {
-        assemble_fp64<TP>(C);
-        const double alpha = frob_shift(C, rcond);
+        const bool keep = reuse && !semi;     // the factors of the previous linear solve
+        if (!keep) {
+            assemble_fp64<TP>(C);
+            ws->last_alpha = frob_shift(C, rcond);
+        }
+        const double alpha = ws->last_alpha;
         rep->alpha = alpha;
         rep->ms_assemble = elapsed_ms(t0);
         if (!semi) {
             auto t1 = std::chrono::steady_clock::now();
-            ewos_status s = factor_shifted<TP>(C, alpha, nullptr, pb->pivoting, rep);
-            if (s != EWOS_OK) return s;
+            if (!keep) {
+                ewos_status s = factor_shifted<TP>(C, alpha, nullptr, pb->pivoting, rep);
+                if (s != EWOS_OK) return s;
+            }
             rep->ms_factor = elapsed_ms(t1);
             auto t2 = std::chrono::steady_clock::now();
             for (int64_t r = 0; r < nrhs; ++r) {       // rhs = -R_0(0)
@@ -2048,7 +2055,7 @@ static ewos_status solve_fp64(ewos_toolbox* tb, SolveWorkspace* ws, const ewos_p
                 cudaMemsetAsync(ws->x + r * C.m, 0, sizeof(double) * C.m, C.st);
                 ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, -1.0, ws->y, ws->x + r * C.m);
             }
-            s = lu_solve_device<double>(ws->LUm, (int)C.m, (int)C.m, ws->lu, ws->x, (int)nrhs, C.st);
+            ewos_status s = lu_solve_device<double>(ws->LUm, (int)C.m, (int)C.m, ws->lu, ws->x, (int)nrhs, C.st);
             if (s != EWOS_OK) return s;
             cudaMemcpyAsync(ws->s, ws->x, sizeof(double) * C.m * nrhs, cudaMemcpyDeviceToDevice, C.st);
             rep->iters = 1;
@@ -2973,13 +2980,17 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
     double batched_res = -1.0;      // residual norm of the last column from the batched sweeps
     if (!quasi) {
         auto ta = std::chrono::steady_clock::now();
-        if (tc_assemble_available()) {
-            ewos_status st = tc_assemble_pq(P32, ws->M, (int)C.n, (int)C.m, C.D, ws->L32, C.st, &ws->tc);
-            if (st != EWOS_OK) return st;
-        } else {
-            assemble_mixed<TP>(C, P32);
+        const bool keep = opt.reuse_factors && !semi;     // the factors of the previous linear solve
+        if (!keep) {
+            if (tc_assemble_available()) {
+                ewos_status st = tc_assemble_pq(P32, ws->M, (int)C.n, (int)C.m, C.D, ws->L32, C.st, &ws->tc);
+                if (st != EWOS_OK) return st;
+            } else {
+                assemble_mixed<TP>(C, P32);
+            }
+            ws->last_alpha = rcond * frob32(C, ws->L32, C.m * C.m);
         }
-        const double alpha = rcond * frob32(C, ws->L32, C.m * C.m);
+        const double alpha = ws->last_alpha;
         rep->alpha = alpha;
         rep->ms_assemble = elapsed_ms(ta);
         bool batched_done = false;
@@ -2987,10 +2998,13 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
             // one factorisation of Lambda + alpha I; all right-hand sides refined together
             // (linear) or the chord iteration on R(s) + alpha s = 0 (semilinear)
             auto t1 = std::chrono::steady_clock::now();
-            ewos_status st = factor32(C, ws->L32, alpha, pb->pivoting, rep);
-            if (st != EWOS_OK) return st;
+            if (!keep) {
+                ewos_status st = factor32(C, ws->L32, alpha, pb->pivoting, rep);
+                if (st != EWOS_OK) return st;
+            }
             rep->ms_factor = elapsed_ms(t1);
             auto t2 = std::chrono::steady_clock::now();
+            ewos_status st = EWOS_OK;
             EWOS_CUDA_TRY(cudaMemsetAsync(ws->scal, 0, sizeof(double), C.st));
             st = ensure_batched(C, bucket_of(nrhs));
             if (st != EWOS_OK) return st;
@@ -3013,8 +3027,11 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
         if (batched_done) {
         } else if (!semi) {
             auto t1 = std::chrono::steady_clock::now();
-            ewos_status st = factor32(C, ws->L32, alpha, pb->pivoting, rep);
-            if (st != EWOS_OK) return st;
+            ewos_status st = EWOS_OK;
+            if (!keep) {
+                st = factor32(C, ws->L32, alpha, pb->pivoting, rep);
+                if (st != EWOS_OK) return st;
+            }
             rep->ms_factor = elapsed_ms(t1);
             auto t2 = std::chrono::steady_clock::now();
             for (int64_t r = 0; r < nrhs; ++r) {
@@ -3197,8 +3214,8 @@ ewos_status solve_on(ewos_toolbox* tb, SolveWorkspace*& wslot, const ewos_proble
     const int max_iter = pb->max_iter > 0 ? pb->max_iter : (pb->nl_kind == EWOS_NL_QUASILINEAR ? 100 : 30);
     ewos_solve_report rep{};
     if (pb->mode == EWOS_SOLVE_FP64)
-        s = tb->precision == 64 ? solve_fp64<double>(tb, ws, pb, rcond, tol, max_iter, &rep)
-                                : solve_fp64<float>(tb, ws, pb, rcond, tol, max_iter, &rep);
+        s = tb->precision == 64 ? solve_fp64<double>(tb, ws, pb, rcond, tol, max_iter, &rep, opt.reuse_factors)
+                                : solve_fp64<float>(tb, ws, pb, rcond, tol, max_iter, &rep, opt.reuse_factors);
     else
         s = solve_mixed(tb, ws, pb, rcond, tol, max_iter, &rep, opt);
     if (s != EWOS_OK && s != EWOS_ENOCONV) return s;
@@ -3377,37 +3394,51 @@ extern "C" ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, doub
 // ------------------------------------------------------------------ operator estimates
 namespace ewos {
 
-// unit right-hand sides: F [R][n] with F[k][k] = 1 (k < n), Gb [R][p] with Gb[n + j][j] = 1
-__global__ void unit_rhs_kernel(double* __restrict__ F, double* __restrict__ Gb, int64_t n, int64_t p) {
+// unit right-hand sides of the columns [k0, k0 + cols) of the solve map: column k < n is f = e_k,
+// column n + j is g = e_j (F [cols][n] and Gb [cols][p] zeroed before)
+__global__ void unit_rhs_kernel(double* __restrict__ F, double* __restrict__ Gb, int64_t n, int64_t p, int64_t k0,
+                                int64_t cols) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) F[t * n + t] = 1.0;
-    else if (t < n + p) Gb[t * p + (t - n)] = 1.0;
+    if (t >= cols) return;
+    const int64_t k = k0 + t;
+    if (k < n) F[t * n + k] = 1.0;
+    else if (k < n + p) Gb[t * p + (k - n)] = 1.0;
 }
 
-// out[i][k - k0] = U[k][i] for k in [k0, k0 + cols), i < n  (32 x 32 tiles through shared memory)
-__global__ void transpose_cols_kernel(const double* __restrict__ U, int64_t n, int64_t k0, int64_t cols,
-                                      double* __restrict__ out) {
+// out[i][col0 + k] = U[t0 + k][i] for k < cols, i < n; out has row length ldo (32 x 32 tiles
+// through shared memory)
+__global__ void transpose_cols_kernel(const double* __restrict__ U, int64_t n, int64_t t0, int64_t cols,
+                                      double* __restrict__ out, int64_t ldo, int64_t col0) {
     __shared__ double tile[32][33];
     const int64_t kb = (int64_t)blockIdx.y * 32, ib = (int64_t)blockIdx.x * 32;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int64_t k = kb + r, i = ib + threadIdx.x;
-        if (k < cols && i < n) tile[r][threadIdx.x] = U[(k0 + k) * n + i];
+        if (k < cols && i < n) tile[r][threadIdx.x] = U[(t0 + k) * n + i];
     }
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int64_t i = ib + r, k = kb + threadIdx.x;
-        if (i < n && k < cols) out[i * cols + k] = tile[threadIdx.x][r];
+        if (i < n && k < cols) out[i * ldo + col0 + k] = tile[threadIdx.x][r];
     }
 }
 
-static ewos_status transpose_out(const double* U, int64_t n, int64_t k0, int64_t cols, double* dst, bool dst_on_device,
-                                 double* stage, cudaStream_t st) {
-    if (!dst || cols == 0) return EWOS_OK;
-    double* out = dst_on_device ? dst : stage;
+static void transpose_cols(const double* U, int64_t n, int64_t t0, int64_t cols, double* out, int64_t ldo,
+                           int64_t col0, cudaStream_t st) {
+    if (!out || cols <= 0) return;
     dim3 grid((unsigned)((n + 31) / 32), (unsigned)((cols + 31) / 32));
-    ::ewos::note_launch(), transpose_cols_kernel<<<grid, dim3(32, 8), 0, st>>>(U, n, k0, cols, out);
-    if (!dst_on_device) EWOS_CUDA_TRY(cudaMemcpyAsync(dst, stage, sizeof(double) * n * cols, cudaMemcpyDeviceToHost, st));
-    return EWOS_OK;
+    ::ewos::note_launch(), transpose_cols_kernel<<<grid, dim3(32, 8), 0, st>>>(U, n, t0, cols, out, ldo, col0);
+}
+
+// right-hand sides per solve of the operator estimates: the dataflow triangular solves give every
+// wait a bounded spin, and their work grows as m^2 per column, so the columns go in chunks of at
+// most ~2^31 multiply-adds per triangular solve (FP64 runs at 1/32 of that; all at once when
+// they fit); the chunks after the first reuse the factors
+static int64_t operator_chunk(int64_t m, int64_t R, bool mixed) {
+    const int64_t cap = std::max<int64_t>(1, (int64_t(1) << 31) / (m * m * (mixed ? 1 : 32)));
+    if (R <= cap) return R;
+    int64_t c = 1;
+    while (c * 2 <= cap) c *= 2;
+    return c;
 }
 
 }  // namespace ewos
@@ -3419,40 +3450,40 @@ extern "C" ewos_status ewos_operators(ewos_toolbox* tb, const ewos_problem* pb, 
     if (pb->nl_kind != EWOS_NL_NONE) { set_error("ewos_operators: the operator estimates are for the linear problem"); return EWOS_EINVAL; }
     if (pb->mode != EWOS_SOLVE_FP64 && pb->mode != EWOS_SOLVE_MIXED) { set_error("ewos_operators: unknown mode"); return EWOS_EINVAL; }
     const cudaStream_t st = pb->stream ? (cudaStream_t)pb->stream : tb->stream;
+    const bool mixed = pb->mode == EWOS_SOLVE_MIXED;
     const int64_t n = tb->n, p = tb->p, R = n + p, D = tb->dim;
-    double *F = nullptr, *Gb = nullptr, *U = nullptr, *Ad = nullptr, *bd = nullptr, *cd = nullptr, *stage = nullptr;
+    const int64_t CH = operator_chunk(tb->m, R, mixed);
+    double *F = nullptr, *Gb = nullptr, *U = nullptr, *Ad = nullptr, *bd = nullptr, *cd = nullptr;
+    double *GLd = outputs_on_device ? GL : nullptr, *HLd = outputs_on_device ? HL : nullptr;
     SolveWorkspace* ws = nullptr;
-    ewos_status s = EWOS_OK;
     auto cleanup = [&]() {
         AllocStream as(st);
         ::ewos::dev_free(F); ::ewos::dev_free(Gb); ::ewos::dev_free(U); ::ewos::dev_free(Ad);
-        ::ewos::dev_free(bd); ::ewos::dev_free(cd); ::ewos::dev_free(stage);
+        ::ewos::dev_free(bd); ::ewos::dev_free(cd);
+        if (!outputs_on_device) { ::ewos::dev_free(GLd); ::ewos::dev_free(HLd); }
         if (ws) free_workspace(ws);
     };
     const bool host = pb->inputs_on_device == 0;
     {
         AllocStream as(st);
-        cudaError_t e = ::ewos::dev_alloc((void**)&F, sizeof(double) * R * n);
-        if (e == cudaSuccess) e = ::ewos::dev_alloc((void**)&Gb, sizeof(double) * R * p);
-        if (e == cudaSuccess) e = ::ewos::dev_alloc((void**)&U, sizeof(double) * R * n);
-        if (e == cudaSuccess && !outputs_on_device) e = ::ewos::dev_alloc((void**)&stage, sizeof(double) * n * std::max(n, p));
+        cudaError_t e = ::ewos::dev_alloc((void**)&F, sizeof(double) * CH * n);
+        if (e == cudaSuccess) e = ::ewos::dev_alloc((void**)&Gb, sizeof(double) * CH * p);
+        if (e == cudaSuccess) e = ::ewos::dev_alloc((void**)&U, sizeof(double) * CH * n);
+        if (e == cudaSuccess && !outputs_on_device && GL) e = ::ewos::dev_alloc((void**)&GLd, sizeof(double) * n * n);
+        if (e == cudaSuccess && !outputs_on_device && HL) e = ::ewos::dev_alloc((void**)&HLd, sizeof(double) * n * p);
         if (e == cudaSuccess && host) e = ::ewos::dev_alloc((void**)&Ad, sizeof(double) * n * D * D);
         if (e == cudaSuccess && host && pb->b) e = ::ewos::dev_alloc((void**)&bd, sizeof(double) * n * D);
         if (e == cudaSuccess && host && pb->c) e = ::ewos::dev_alloc((void**)&cd, sizeof(double) * n);
+        if (e == cudaSuccess && host) {
+            e = cudaMemcpyAsync(Ad, pb->A, sizeof(double) * n * D * D, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess && pb->b) e = cudaMemcpyAsync(bd, pb->b, sizeof(double) * n * D, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess && pb->c) e = cudaMemcpyAsync(cd, pb->c, sizeof(double) * n, cudaMemcpyHostToDevice, st);
+        }
         if (e != cudaSuccess) {
             set_error(std::string("ewos_operators: ") + cudaGetErrorString(e));
             cleanup();
             return e == cudaErrorMemoryAllocation ? EWOS_ENOMEM : EWOS_ECUDA;
         }
-        if (host) {
-            e = cudaMemcpyAsync(Ad, pb->A, sizeof(double) * n * D * D, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess && pb->b) e = cudaMemcpyAsync(bd, pb->b, sizeof(double) * n * D, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess && pb->c) e = cudaMemcpyAsync(cd, pb->c, sizeof(double) * n, cudaMemcpyHostToDevice, st);
-        }
-        if (e == cudaSuccess) e = cudaMemsetAsync(F, 0, sizeof(double) * R * n, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(Gb, 0, sizeof(double) * R * p, st);
-        if (e != cudaSuccess) { set_error(std::string("ewos_operators: ") + cudaGetErrorString(e)); cleanup(); return EWOS_ECUDA; }
-        ::ewos::note_launch(), unit_rhs_kernel<<<(unsigned)((R + 255) / 256), 256, 0, st>>>(F, Gb, n, p);
     }
     ewos_problem q = *pb;
     q.A = host ? Ad : pb->A;
@@ -3460,18 +3491,50 @@ extern "C" ewos_status ewos_operators(ewos_toolbox* tb, const ewos_problem* pb, 
     q.c = host ? cd : pb->c;
     q.f = F;
     q.g = Gb;
-    q.nrhs = R;
     q.inputs_on_device = 1;
     q.stream = st;
-    q.batched = 0;
+    // mixed mode: the columns of a chunk are refined together (graph-captured sweeps)
+    q.batched = mixed ? 1 : 0;
     SolveOptions opt;
-    s = solve_on(tb, ws, &q, U, nullptr, 1, rep, opt);
-    if (s == EWOS_OK) {
-        AllocStream as(st);
-        s = transpose_out(U, n, 0, n, GL, outputs_on_device != 0, stage, st);
-        if (s == EWOS_OK) s = transpose_out(U, n, n, p, HL, outputs_on_device != 0, stage, st);
-        if (s == EWOS_OK && cudaStreamSynchronize(st) != cudaSuccess) { set_error("ewos_operators: stream"); s = EWOS_ECUDA; }
+    opt.batched = mixed;
+    ewos_status s = EWOS_OK;
+    ewos_solve_report r{}, total{};
+    for (int64_t k0 = 0; k0 < R && s == EWOS_OK; k0 += CH) {
+        const int64_t cols = std::min(CH, R - k0);
+        {
+            AllocStream as(st);
+            if (cudaMemsetAsync(F, 0, sizeof(double) * cols * n, st) != cudaSuccess ||
+                cudaMemsetAsync(Gb, 0, sizeof(double) * cols * p, st) != cudaSuccess) {
+                set_error("ewos_operators: memset");
+                s = EWOS_ECUDA;
+                break;
+            }
+            ::ewos::note_launch(), unit_rhs_kernel<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(F, Gb, n, p, k0, cols);
+        }
+        q.nrhs = cols;
+        opt.reuse_factors = k0 > 0;
+        s = solve_on(tb, ws, &q, U, nullptr, 1, &r, opt);
+        if (s != EWOS_OK) break;
+        if (k0 == 0) total = r;
+        else {
+            total.ms_total += r.ms_total;
+            total.ms_solve += r.ms_solve;
+            total.refine_iters = std::max(total.refine_iters, r.refine_iters);
+            total.converged = total.converged && r.converged;
+            total.residual = r.residual;
+        }
+        const int64_t g1 = std::max<int64_t>(0, std::min(cols, n - k0));      // local columns of GL
+        transpose_cols(U, n, 0, g1, GLd, n, k0, st);
+        transpose_cols(U, n, g1, cols - g1, HLd, p, k0 + g1 - n, st);
     }
+    if (s == EWOS_OK && !outputs_on_device) {
+        cudaError_t e = cudaSuccess;
+        if (GL) e = cudaMemcpyAsync(GL, GLd, sizeof(double) * n * n, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && HL) e = cudaMemcpyAsync(HL, HLd, sizeof(double) * n * p, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) { set_error(std::string("ewos_operators: ") + cudaGetErrorString(e)); s = EWOS_ECUDA; }
+    }
+    if (s == EWOS_OK && cudaStreamSynchronize(st) != cudaSuccess) { set_error("ewos_operators: stream"); s = EWOS_ECUDA; }
+    if (rep && s == EWOS_OK) *rep = total;
     cleanup();
     return s;
 }

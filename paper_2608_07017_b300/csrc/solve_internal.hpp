@@ -10,6 +10,10 @@ struct SolveOptions {
     // sweep; semilinear problems by the chord iteration s <- s - (Lambda + alpha I)^-1 (R(s) +
     // alpha s) on the same factors (exact Newton per right-hand side when it does not converge).
     bool batched = false;
+    // Linear problems only: take Lambda + alpha I's factors (and alpha) from the previous solve on
+    // this workspace, for the same toolbox and coefficients, instead of assembling and factoring
+    // again (the operator estimates solve their unit right-hand sides in chunks this way).
+    bool reuse_factors = false;
 };
 
 struct SolveWorkspace;

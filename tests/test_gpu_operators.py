@@ -95,6 +95,29 @@ def test_operators_ragged_sizes():
         assert _rel(GL, ref["GL"]) < 1e-9 and _rel(HL, ref["HL"]) < 1e-9
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_operators_in_chunks_match_oracle(mode):
+    """m = 1400: the columns go in several chunks (1024 in mixed mode, 32 in FP64 mode), the
+    chunks after the first on the first chunk's factors."""
+    from paper_2608_07017_b300 import build
+    build.build()
+    rng = np.random.default_rng(9)
+    n, p = 1400, 100
+    x = rng.uniform(-0.6, 0.6, size=(n, 2))
+    z = rng.normal(size=(p, 2))
+    z /= np.linalg.norm(z, axis=1, keepdims=True)
+    tb = dict(G=rng.random((n, n)) * 1e-3, gradG=rng.normal(size=(2, n, n)) * 0.05,
+              H=rng.random((n, p)) / p, gradH=rng.normal(size=(2, n, p)) * 0.1)
+    lam = rng.random(n) + 0.5
+    lam /= lam.sum()
+    A = np.tile(np.array([[1.2, 0.1], [0.1, 0.9]]), (n, 1, 1))
+    gtb = ewos.toolbox_from_host(2, x, z, tb["G"], tb["gradG"], tb["H"], tb["gradH"], lam, precision=64)
+    GL, HL, rep = gtb.operators(A, mode=mode)
+    gtb.close()
+    ref = S.operators(tb, lam, A, alpha=rep["alpha"])
+    assert _rel(GL, ref["GL"]) < 1e-9 and _rel(HL, ref["HL"]) < 1e-9
+
+
 def test_operators_reject_nonlinear(disk):
     w, tb, lam, gtb = disk
     pb = ewos._Problem(w.problem.A.ctypes.data, None, None, None, None, 0, ewos.NL["semilinear"], None, 0, 0,
