@@ -3284,14 +3284,28 @@ static ewos_status prepare_gradient(ewos_toolbox* tb, SolveWorkspace*& wslot, co
                                                                                 pb->b ? ws->b : nullptr,
                                                                                 pb->c ? ws->c : nullptr, nullptr, 0,
                                                                                 nullptr, ws->M);
+    if (tb->precision == 32) {
+        // FP32 toolbox: the refinement's residual (FP32-pair products, one pass over P where it
+        // fits) on the single-column buffers: s in Sb, the gradient in Yb, shift 0
+        s = ensure_batched(C, 1);
+        if (s != EWOS_OK) return s;
+        EWOS_CUDA_TRY(cudaMemcpyAsync(ws->Fb, ws->f, sizeof(double) * tb->n, cudaMemcpyDeviceToDevice, C.st));
+        EWOS_CUDA_TRY(cudaMemcpyAsync(ws->Gb, ws->g, sizeof(double) * tb->p, cudaMemcpyDeviceToDevice, C.st));
+        ::ewos::note_launch(), set_scalar_kernel<<<1, 32, 0, C.st>>>(ws->alpha_dev, 0.0);
+    }
     return EWOS_OK;
 }
 
-static void gradient_at(const Ctx& C, const ewos_problem* pb, const double* s, double* y) {
+// the iterate and gradient buffers of the gradient evaluation
+static double* grad_s(const Ctx& C) { return C.tb->precision == 32 ? C.ws->Sb : C.ws->s; }
+static double* grad_y(const Ctx& C) { return C.tb->precision == 32 ? C.ws->Yb : C.ws->y; }
+
+// grad_y = R(grad_s)
+static void gradient_at(const Ctx& C, const ewos_problem* pb) {
     const double* nl = pb->nl_kind == EWOS_NL_SEMILINEAR ? C.ws->nl : nullptr;
     const int nnl = pb->nl_kind == EWOS_NL_SEMILINEAR ? pb->nl_ncoef : 0;
-    if (C.tb->precision == 64) residual<double>(C, s, C.ws->g, C.ws->f, nl, nnl, 0.0, y);
-    else residual<float>(C, s, C.ws->g, C.ws->f, nl, nnl, 0.0, y);
+    if (C.tb->precision == 64) residual<double>(C, C.ws->s, C.ws->g, C.ws->f, nl, nnl, 0.0, C.ws->y);
+    else residual_multi<float>(C, 1, 1, nl, nnl);
 }
 
 // (sum_i w_i y_i^2)^(1/2), w = lambda when the V-centres are the nodes, else 1 (synchronises)
@@ -3315,10 +3329,10 @@ extern "C" ewos_status ewos_gradient(ewos_toolbox* tb, const ewos_problem* pb, c
     ewos_status st = prepare_gradient(tb, tb->ws, pb, C);
     if (st != EWOS_OK) return st;
     const cudaMemcpyKind k = pb->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    EWOS_CUDA_TRY(cudaMemcpyAsync(C.ws->s, s, sizeof(double) * tb->m, k, C.st));
-    gradient_at(C, pb, C.ws->s, C.ws->y);
+    EWOS_CUDA_TRY(cudaMemcpyAsync(grad_s(C), s, sizeof(double) * tb->m, k, C.st));
+    gradient_at(C, pb);
     const cudaMemcpyKind ko = pb->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    EWOS_CUDA_TRY(cudaMemcpyAsync(grad, C.ws->y, sizeof(double) * tb->m, ko, C.st));
+    EWOS_CUDA_TRY(cudaMemcpyAsync(grad, grad_y(C), sizeof(double) * tb->m, ko, C.st));
     EWOS_CUDA_TRY(cudaStreamSynchronize(C.st));
     return EWOS_OK;
 }
@@ -3337,8 +3351,10 @@ extern "C" ewos_status ewos_minimize_adam(ewos_toolbox* tb, const ewos_problem* 
     ewos_status st = prepare_gradient(tb, tb->ws, pb, C);
     if (st != EWOS_OK) return st;
     SolveWorkspace* ws = C.ws;
+    double* sv = grad_s(C);
+    double* gv = grad_y(C);
     const cudaMemcpyKind k = pb->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    EWOS_CUDA_TRY(cudaMemcpyAsync(ws->s, s_inout, sizeof(double) * tb->m, k, C.st));
+    EWOS_CUDA_TRY(cudaMemcpyAsync(sv, s_inout, sizeof(double) * tb->m, k, C.st));
     EWOS_CUDA_TRY(cudaMemsetAsync(ws->r, 0, sizeof(double) * tb->m, C.st));     // first moment
     EWOS_CUDA_TRY(cudaMemsetAsync(ws->dx, 0, sizeof(double) * tb->m, C.st));    // second moment
     const int check = opts->check_every > 0 ? opts->check_every : 10;
@@ -3346,27 +3362,27 @@ extern "C" ewos_status ewos_minimize_adam(ewos_toolbox* tb, const ewos_problem* 
     int64_t j = 0;
     bool conv = false;
     while (j < opts->max_iter) {
-        gradient_at(C, pb, ws->s, ws->y);
+        gradient_at(C, pb);
         if (opts->tol > 0 && j % check == 0) {
-            gn = grad_norm(C, ws->y);
+            gn = grad_norm(C, gv);
             if (gn <= opts->tol) { conv = true; break; }
         }
         ++j;
         p1 *= opts->beta1;
         p2 *= opts->beta2;
         const double aj = opts->alpha * std::sqrt(1.0 - p2) / (1.0 - p1);
-        ::ewos::note_launch(), adam_kernel<<<(int)((tb->m + 255) / 256), 256, 0, C.st>>>(tb->m, ws->y, ws->r, ws->dx, ws->s, aj,
+        ::ewos::note_launch(), adam_kernel<<<(int)((tb->m + 255) / 256), 256, 0, C.st>>>(tb->m, gv, ws->r, ws->dx, sv, aj,
                                                                                        opts->beta1, opts->beta2, opts->eps);
     }
     if (!conv) {                              // the gradient at the final iterate
-        gradient_at(C, pb, ws->s, ws->y);
-        gn = grad_norm(C, ws->y);
+        gradient_at(C, pb);
+        gn = grad_norm(C, gv);
         conv = opts->tol > 0 && gn <= opts->tol;
     }
     const cudaMemcpyKind ko = pb->inputs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    EWOS_CUDA_TRY(cudaMemcpyAsync(s_inout, ws->s, sizeof(double) * tb->m, ko, C.st));
+    EWOS_CUDA_TRY(cudaMemcpyAsync(s_inout, sv, sizeof(double) * tb->m, ko, C.st));
     if (u_out) {
-        u_from_s(C, tb->P, tb->KH, tb->precision == 64, ws->s, ws->g, ws->u);
+        u_from_s(C, tb->P, tb->KH, tb->precision == 64, sv, ws->g, ws->u);
         EWOS_CUDA_TRY(cudaMemcpyAsync(u_out, ws->u, sizeof(double) * tb->n, ko, C.st));
     }
     EWOS_CUDA_TRY(cudaStreamSynchronize(C.st));

@@ -5,7 +5,9 @@ algorithm).
   library), linear and semilinear; FP64 on both sides, only the order of rounding differs, so
   1e-11 relative to the largest component.
 * A GPU-built FP32 toolbox: the gradient against the oracle's residual on the downloaded
-  matrices (the library widens the stored FP32 entries and accumulates in FP64): 1e-10.
+  matrices (the library multiplies the stored FP32 entries by a two-float split of the FP64
+  operand and accumulates the pairs, the refinement's residual): 1e-10; and a 30-step Adam
+  trajectory against the oracle's on those matrices.
 * Adam: the GPU trajectory against the oracle's for the same start, steps and hyper-parameters.
   Adam divides m_j by sqrt(v_j), so a rounding difference in a component of the gradient moves
   that component by at most alpha_j |delta m_j| / sqrt(v_j); after tens of steps on this
@@ -62,17 +64,24 @@ def test_gradient_matches_oracle_residual(disk):
     assert got.shape == (gtb.m,)
 
 
-def test_gradient_fp32_built_toolbox():
+def test_gradient_and_adam_fp32_built_toolbox():
+    # FP32 toolbox: the gradient is the refinement's FP32-pair residual
     w = W.disk400()
     pb = w.problem
     gtb = ewos.build_workload(w, cell_samples=200_000)
     tb = gtb.matrices()
     lam = gtb.get("lambda")
-    s = np.random.default_rng(6).normal(size=gtb.m)
+    rng = np.random.default_rng(6)
+    s = rng.normal(size=gtb.m)
     got = gtb.gradient(s, pb.A, pb.f, pb.g)
+    coef = [0.0, 0.0, 0.0, 1.0]
+    got3 = gtb.gradient(s, pb.A, pb.f, pb.g, kind="semilinear", coef=coef)
+    s0 = rng.normal(size=gtb.m)
+    sa, _, rep = gtb.minimize_adam(pb.A, pb.f, pb.g, s0=s0, alpha=0.1, max_iter=30)
     gtb.close()
-    ref = S.residual(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, s)
-    assert _rel(got, ref) < 1e-10
+    assert _rel(got, S.residual(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, s)) < 1e-10
+    assert _rel(got3, S.residual(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, s, coef)) < 1e-10
+    assert _rel(sa, S.adam(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, s0, 0.1, iters=30)) < 1e-8
 
 
 @pytest.mark.parametrize("alpha,iters", [(0.1, 1), (0.1, 40), (0.5, 25)])
