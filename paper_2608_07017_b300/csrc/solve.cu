@@ -2311,7 +2311,7 @@ __global__ void from_cols_kernel(const double* __restrict__ in, double* __restri
 }
 
 // Vout[row][r] (+)= sum_c X[row][c] Vin[c][r]   (warp per row, RB right-hand sides per pass;
-// rc is a power of two, RB = min(rc, 8))
+// rc is a power of two, RB = min(rc, 8); the FP32-pair version below takes RB = min(rc, 16))
 template <typename TP, int RB>
 __global__ void multi_rowdot_kernel(const TP* __restrict__ X, int64_t rows, int cols, const double* __restrict__ Vin,
                                     double* __restrict__ Vout, int rc, int accumulate) {
@@ -2560,7 +2560,8 @@ static void multi_rowdot_f2(cudaStream_t st, const float* X, int64_t rows, int c
     if (rc == 1) ::ewos::note_launch(), multi_rowdot_f2_kernel<1><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
     else if (rc == 2) ::ewos::note_launch(), multi_rowdot_f2_kernel<2><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
     else if (rc == 4) ::ewos::note_launch(), multi_rowdot_f2_kernel<4><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
-    else ::ewos::note_launch(), multi_rowdot_f2_kernel<8><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
+    else if (rc == 8) ::ewos::note_launch(), multi_rowdot_f2_kernel<8><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
+    else ::ewos::note_launch(), multi_rowdot_f2_kernel<16><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
 }
 
 static void multi_coltrans_f2(cudaStream_t st, const float* X, int64_t rows, int cols, const float* Whi, const float* Wlo,
@@ -2570,7 +2571,8 @@ static void multi_coltrans_f2(cudaStream_t st, const float* X, int64_t rows, int
     if (rc == 1) ::ewos::note_launch(), multi_coltrans_f2_kernel<1><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
     else if (rc == 2) ::ewos::note_launch(), multi_coltrans_f2_kernel<2><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
     else if (rc == 4) ::ewos::note_launch(), multi_coltrans_f2_kernel<4><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
-    else ::ewos::note_launch(), multi_coltrans_f2_kernel<8><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
+    else if (rc == 8) ::ewos::note_launch(), multi_coltrans_f2_kernel<8><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
+    else ::ewos::note_launch(), multi_coltrans_f2_kernel<16><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
 }
 
 static void split_f2(cudaStream_t st, const double* v, float* hi, float* lo, int64_t count) {
