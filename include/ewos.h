@@ -266,8 +266,9 @@ ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, double* u_out, 
  *   grad J(s) = R(s) = P^T w,  w_i = M_i (P_i s + KH_i g) + e_d lam_i (N(u_i) - f_i)     (eq. gradJ),
  * for the problem's A, b, c, f, g (first right-hand side) and a semilinear N (a quasilinear
  * equation is not the Euler-Lagrange equation of a functional: EWOS_EINVAL).  s [m] and grad [m]
- * are host buffers (device buffers when pb->inputs_on_device = 1); evaluated in FP64 on the
- * toolbox's P and KH. */
+ * are host buffers (device buffers when pb->inputs_on_device = 1).  FP64 toolbox: FP64
+ * products and sums; FP32 toolbox: the stored FP32 entries times a two-float split of s and g,
+ * summed in float pairs (about 1e-14 relative, the mixed solve's residual). */
 ewos_status ewos_gradient(ewos_toolbox* tb, const ewos_problem* pb, const double* s, double* grad);
 
 /* Adam on J (the paper's appendix algorithm; its Examples use beta1 = 0.9, beta2 = 0.999,
