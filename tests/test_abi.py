@@ -60,6 +60,14 @@ def test_invalid_arguments_are_rejected_before_any_device_work(L):
     assert L.ewos_solve(None, None, None, None, 0, None) == ewos.EINVAL
     assert L.ewos_toolbox_get(None, 0, None, 0, 0) == ewos.EINVAL
     assert L.ewos_debug_philox(None, None, None, 1) == ewos.EINVAL
+    # the Euler-Lagrange route and the operator estimates with NULL handles
+    s = np.zeros(4)
+    pb = ewos._Problem()
+    assert L.ewos_gradient(None, ctypes.byref(pb), s.ctypes.data, s.ctypes.data) == ewos.EINVAL
+    assert L.ewos_gradient(None, None, None, None) == ewos.EINVAL
+    o = ewos.AdamOpts(1e-3, 0.9, 0.999, 1e-10, 10, 0.0, 0)
+    assert L.ewos_minimize_adam(None, ctypes.byref(pb), ctypes.byref(o), s.ctypes.data, None, None) == ewos.EINVAL
+    assert L.ewos_operators(None, ctypes.byref(pb), s.ctypes.data, None, 0, None) == ewos.EINVAL
 
 
 def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
