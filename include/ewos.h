@@ -268,7 +268,9 @@ ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, double* u_out, 
  * equation is not the Euler-Lagrange equation of a functional: EWOS_EINVAL).  s [m] and grad [m]
  * are host buffers (device buffers when pb->inputs_on_device = 1).  FP64 toolbox: FP64
  * products and sums; FP32 toolbox: the stored FP32 entries times a two-float split of s and g,
- * summed in float pairs (about 1e-14 relative, the mixed solve's residual). */
+ * summed in float pairs (about 1e-14 relative, the mixed solve's residual).  Errors:
+ * EWOS_EINVAL (a NULL argument, a quasilinear problem, 0 or more than 64 coefficients),
+ * EWOS_ENOMEM / EWOS_ECUDA from the device; grad is written only on EWOS_OK. */
 ewos_status ewos_gradient(ewos_toolbox* tb, const ewos_problem* pb, const double* s, double* grad);
 
 /* Adam on J (the paper's appendix algorithm; its Examples use beta1 = 0.9, beta2 = 0.999,
@@ -277,7 +279,9 @@ ewos_status ewos_gradient(ewos_toolbox* tb, const ewos_problem* pb, const double
  * (sqrt(v_j) + eps), all on the device.  Runs max_iter steps, or stops earlier when the weighted
  * gradient norm (sum_i w_i grad_i^2)^(1/2) <= tol (w = lambda when the V-centres are the nodes,
  * else 1; checked every check_every steps, default 10; tol <= 0: never).  s_inout [m] holds the
- * start and receives the result; u_out [n] (may be NULL) receives u = G s + H g. */
+ * start and receives the result; u_out [n] (may be NULL) receives u = G s + H g.  Errors: as
+ * ewos_gradient, and EWOS_EINVAL for alpha <= 0, beta1 or beta2 outside [0, 1), eps <= 0 or
+ * max_iter < 0 (checked before any device work); max_iter = 0 returns the start. */
 typedef struct {
     double alpha, beta1, beta2, eps;
     int64_t max_iter;
@@ -307,7 +311,9 @@ ewos_status ewos_minimize_adam(ewos_toolbox* tb, const ewos_problem* pb, const e
  * 2^31 / m^2 columns in mixed mode, 32 times fewer in FP64 mode; all at once when they fit), on
  * a private workspace freed before the call returns.  Either output may be NULL; both are host
  * buffers, or device buffers when outputs_on_device = 1.  rep (may be NULL) as for ewos_solve,
- * with the times summed over the chunks. */
+ * with the times summed over the chunks.  Errors: EWOS_EINVAL (NULL toolbox, problem or A, no
+ * output, a nonlinear problem, an unknown mode), and those of ewos_solve (EWOS_ENOMEM,
+ * EWOS_ESINGULAR, EWOS_ETIMEOUT, EWOS_ECUDA); the outputs are complete only on EWOS_OK. */
 ewos_status ewos_operators(ewos_toolbox* tb, const ewos_problem* pb, double* GL, double* HL,
                            int outputs_on_device, ewos_solve_report* rep);
 
