@@ -30,7 +30,10 @@ from the linear part; Picard recomputes alpha from each iteration's matrix.
 Parity pins (tests/test_oracle_*.py): assemble -> the un-assembled bilinear form of
 eq. matrix_test_varphi; lu_factor/lu_solve -> LAPACK via numpy.linalg.solve and the residual;
 solve_linear -> manufactured solutions (discretisation-error bound) and a finite-difference
-solve of the same problem; newton -> zero residual and reduction to solve_linear when N = 0;
+solve of the same problem; the first- and zeroth-order terms of assemble, rhs, residual and
+sigma -> an independent finite-difference solve of an advection-reaction problem with
+Dirichlet data (b = (8, -4), c = 30), which each function with b -> -b or c -> 2c misses;
+newton -> zero residual and reduction to solve_linear when N = 0;
 picard -> fixed-point property and reduction to solve_linear when A(u) = A; operators -> they
 reproduce solve_linear for any (f, g) (which checks sigma against rhs), the torsion function
 and the constant 1 on the disk, and the symmetry of GL diag(lam)^(-1) for a self-adjoint

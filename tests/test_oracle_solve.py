@@ -135,9 +135,141 @@ def test_linear_solve_agrees_with_finite_differences(oracle_lib):
     u_fd = RegularGridInterpolator((tt, tt), UU)(x)
     rel = np.sqrt(np.sum(lam * (sol["u"] - u_fd) ** 2) / np.sum(lam * u_fd ** 2))
     assert rel < 0.08
-    # a sign error in the first-order term or a missing factor would be far outside this band
+    # a factor-2 error in the diffusion term is far outside this band (this problem has no
+    # first- or zeroth-order term; those are pinned by the tests below)
     bad = S.solve_linear(tb, lam, 2 * A, None, None, fsrc(x[:, 0], x[:, 1]), np.zeros(z.shape[0]))
     assert np.sqrt(np.sum(lam * (bad["u"] - u_fd) ** 2) / np.sum(lam * u_fd ** 2)) > 0.3
+
+
+def _fd_solve_general(a1, a2, bvec, cfun, f, gfun, K):
+    """-d/dx(a1 du/dx) - d/dy(a2 du/dy) + b . grad u + c u = f on (0,1)^2, u = g on the boundary:
+    conservative 5-point diffusion (face coefficients at midpoints), centred differences for the
+    constant advection b, the reaction c at the node; boundary neighbours move to the right-hand
+    side.  Returns an interpolant of the grid solution (boundary values included)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spl
+    from scipy.interpolate import RegularGridInterpolator
+    h = 1.0 / (K + 1)
+    t = np.arange(1, K + 1) * h
+    X, Y = np.meshgrid(t, t, indexing="ij")
+    idx = np.arange(K * K).reshape(K, K)
+    rows, cols, vals = [], [], []
+    rhs = f(X, Y).ravel().copy()
+    diag = cfun(X, Y) + 0.0 * X
+    for (di, dj, diff, adv) in ((1, 0, a1(X + h / 2, Y), bvec[0]), (-1, 0, a1(X - h / 2, Y), -bvec[0]),
+                                (0, 1, a2(X, Y + h / 2), bvec[1]), (0, -1, a2(X, Y - h / 2), -bvec[1])):
+        diag = diag + diff / h ** 2
+        coef = -diff / h ** 2 + adv / (2 * h)
+        I2, J2 = np.meshgrid(np.arange(K) + di, np.arange(K) + dj, indexing="ij")
+        ok = (I2 >= 0) & (I2 < K) & (J2 >= 0) & (J2 < K)
+        rows.append(idx[ok]); cols.append(idx[I2[ok], J2[ok]]); vals.append(coef[ok])
+        out = ~ok
+        rhs[idx[out]] -= coef[out] * gfun((I2[out] + 1) * h, (J2[out] + 1) * h)
+    rows.append(idx.ravel()); cols.append(idx.ravel()); vals.append(diag.ravel())
+    M = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(K * K, K * K))
+    u = spl.spsolve(M.tocsc(), rhs)
+    tt = np.concatenate([[0.0], t, [1.0]])
+    T0, T1 = np.meshgrid(tt, tt, indexing="ij")
+    U = gfun(T0, T1) + 0.0 * T0
+    U[1:-1, 1:-1] = u.reshape(K, K)
+    return RegularGridInterpolator((tt, tt), U)
+
+
+# Advection-reaction problem on the unit square, strong enough that a sign error in b or a
+# factor 2 in c moves the solution well outside the band of the correct solve:
+#   -div(diag(1 + x, 1 + y^2) grad u) + (8, -4) . grad u + 30 u = 1 + 2xy,  u = sin(2x + y)/2 + xy.
+BC_BAND = 0.06
+
+
+@pytest.fixture(scope="module")
+def square_bc(oracle_lib):
+    k, N = 12, 4000
+    x = W.square_nodes(k)
+    z = W.square_boundary_nodes(2 * k)
+    r = oracle_lib.walk_rows(2, "box", [0, 0, 1, 1], x, z, N, 1e-4, seed=4)
+    tb = dict(G=r["G"], gradG=r["gradG"], H=r["Hc"] / N, gradH=r["gradH"])
+    n = x.shape[0]
+    lam = np.full(n, 1.0 / n)
+    a1 = lambda X, Y: 1.0 + X
+    a2 = lambda X, Y: 1.0 + Y ** 2
+    bvec = np.array([8.0, -4.0])
+    cfun = lambda X, Y: 30.0 + 0.0 * X
+    fsrc = lambda X, Y: 1.0 + 2.0 * X * Y
+    gfun = lambda X, Y: 0.5 * np.sin(2.0 * X + Y) + X * Y
+    A = np.zeros((n, 2, 2)); A[:, 0, 0] = a1(x[:, 0], x[:, 1]); A[:, 1, 1] = a2(x[:, 0], x[:, 1])
+    pb = dict(A=A, b=np.tile(bvec, (n, 1)), c=cfun(x[:, 0], x[:, 1]), f=fsrc(x[:, 0], x[:, 1]),
+              g=gfun(z[:, 0], z[:, 1]))
+    u_fd = _fd_solve_general(a1, a2, bvec, cfun, fsrc, gfun, 399)(x)
+    return tb, lam, pb, u_fd
+
+
+def _rel(u, ref, lam):
+    return float(np.sqrt(np.sum(lam * (u - ref) ** 2) / np.sum(lam * ref ** 2)))
+
+
+def _mutants(fn):
+    """Copies of an oracle function with b -> -b, and with c -> 2c, in that function only."""
+    def flip_b(*a, **k):
+        a = list(a)
+        a[_BC_POS[fn.__name__][0]] = -np.asarray(a[_BC_POS[fn.__name__][0]])
+        return fn(*a, **k)
+
+    def double_c(*a, **k):
+        a = list(a)
+        a[_BC_POS[fn.__name__][1]] = 2.0 * np.asarray(a[_BC_POS[fn.__name__][1]])
+        return fn(*a, **k)
+    return {"b -> -b": flip_b, "c -> 2c": double_c}
+
+
+# positional indices of (b, c) in each function's signature
+_BC_POS = {"assemble": (4, 5), "rhs": (7, 8), "residual": (3, 4), "sigma": (3, 4)}
+
+
+def test_lower_order_terms_of_assembly_and_rhs_against_finite_differences(square_bc, monkeypatch):
+    """assemble and rhs (eq. linear_q) with first- and zeroth-order terms: the solve agrees with
+    an independent finite-difference solve of the same boundary value problem within the band,
+    and a sign error in b or a factor 2 in c in either function falls outside it."""
+    tb, lam, pb, u_fd = square_bc
+    args = (tb, lam, pb["A"], pb["b"], pb["c"], pb["f"], pb["g"])
+    e = _rel(S.solve_linear(*args)["u"], u_fd, lam)
+    assert e < BC_BAND / 2
+    for name in ("assemble", "rhs"):
+        fn = getattr(S, name)
+        for what, mut in _mutants(fn).items():
+            with monkeypatch.context() as mp:
+                mp.setattr(S, name, mut)
+                e_bad = _rel(S.solve_linear(*args)["u"], u_fd, lam)
+            assert e_bad > BC_BAND, (name, what, e_bad)
+
+
+def test_lower_order_terms_of_residual_against_finite_differences(square_bc, monkeypatch):
+    """residual R(s) (the Euler-Lagrange residual of Sec. 3.2, eq. gradJ) with first- and
+    zeroth-order terms: Newton on R(s) + alpha s = 0 (N = 0) lands on the finite-difference
+    solution, and lands outside the band (or fails to converge) when residual has b -> -b or
+    c -> 2c."""
+    tb, lam, pb, u_fd = square_bc
+    args = (tb, lam, pb["A"], pb["b"], pb["c"], pb["f"], pb["g"], [0.0])
+    res = S.newton(*args, tol=1e-12)
+    assert res["converged"] and _rel(res["u"], u_fd, lam) < BC_BAND / 2
+    for what, mut in _mutants(S.residual).items():
+        with monkeypatch.context() as mp:
+            mp.setattr(S, "residual", mut)
+            bad = S.newton(*args, tol=1e-12)
+        assert not (bad["converged"] and _rel(bad["u"], u_fd, lam) < BC_BAND), what
+
+
+def test_lower_order_terms_of_sigma_against_finite_differences(square_bc, monkeypatch):
+    """sigma (the boundary matrix of eq. linear_q) with first- and zeroth-order terms: the
+    operator estimates give u = G^L f + H^L g equal to the finite-difference solution within the
+    band (H^L carries sigma), and b -> -b or c -> 2c in sigma moves it outside."""
+    tb, lam, pb, u_fd = square_bc
+    op = S.operators(tb, lam, pb["A"], pb["b"], pb["c"])
+    assert _rel(op["GL"] @ pb["f"] + op["HL"] @ pb["g"], u_fd, lam) < BC_BAND / 2
+    for what, mut in _mutants(S.sigma).items():
+        with monkeypatch.context() as mp:
+            mp.setattr(S, "sigma", mut)
+            op = S.operators(tb, lam, pb["A"], pb["b"], pb["c"])
+        assert _rel(op["GL"] @ pb["f"] + op["HL"] @ pb["g"], u_fd, lam) > BC_BAND, what
 
 
 def test_newton_semilinear(disk_tb):
