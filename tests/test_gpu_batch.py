@@ -4,7 +4,7 @@
   instance: exit counts bit-exact, G and grad G up to the order of the FP32 shared-memory
   atomics, identical step counts;
 * against the oracle (same stream, instance k): exit counts per row within twice the 0.1 %
-  divergent-walk allowance;
+  divergent-walk allowance, and over all compared rows at most 0.1 % of the walks moved;
 * the 32-instance star workload at full size: one launch, every row's exit counts sum to N, and
   the quasilinear problem of each instance solved by Picard through the request server.
 """
@@ -68,6 +68,9 @@ def test_batch_exit_counts_against_oracle():
         Hc = tb.get("Hc").astype(np.int64)[rows]
         diff = np.abs(Hc - orc["Hc"]).sum(1)
         assert np.all(diff <= 2 * math.ceil(0.001 * 500) * 2), diff.max()
+        # over all compared rows: a walk that exits elsewhere moves two counts, and at most
+        # 0.1 % of the walks may do so
+        assert diff.sum() <= 2 * 0.001 * rows.size * 500, diff.sum()
         assert np.all(Hc.sum(1) == 500)
         tb.close()
 

@@ -169,24 +169,39 @@ def _full_size_rows(w, rows, N, ctas_per_sm=0):
     rep = compare_rows(g, orc, rows, N, w.domain.dim, r0, fp32=True)
     assert rep["exit_equal"] >= 0.999, rep
     assert np.all(g["Hc"].sum(1) == N)
-    return rep, g, br
+    # grad H 1 = 0 on every row (E U_0 = 0): 4 SE of the per-walk terms (d/r0^2) w_c
+    d = w.domain.dim
+    per = (d / r0 ** 2)[:, None, None] * orc["records"]["w"]
+    se = per.std(1) / np.sqrt(N)
+    gh1 = np.stack([g["gradH"][c][rows].sum(1) for c in range(d)], axis=1)
+    assert np.all(np.abs(gh1) <= 4 * se + 1e-6), (gh1, se)
+    return rep, g, br, orc, r0
 
 
 def test_square4096_full_size_sampled_rows():
     w = W.square4096(problem=False)
     rows = np.array([0, 63, 2080, 2047, 4032, 4095])
-    rep, g, br = _full_size_rows(w, rows, w.walks)
+    rep, g, br, orc, _ = _full_size_rows(w, rows, w.walks)
     assert br["capped"] == 0
+    # G 1 = the torsion function of the square (its Fourier series), 4 SE + the eps-shell bias
+    from test_oracle_walks import _square_torsion
+    ex = np.array([_square_torsion(*p) for p in w.x[rows]])
+    se = orc["records"]["gmass"].std(1) / np.sqrt(w.walks)
+    assert np.all(np.abs(g["G"][rows].sum(1) - ex) <= 4 * se + 1e-4)
 
 
 def test_ball8000_full_size_sampled_rows():
     w = W.ball8000(problem=False)
     rows = np.array([0, 3999, 7999])
-    rep, g, br = _full_size_rows(w, rows, w.walks)
+    rep, g, br, orc, r0 = _full_size_rows(w, rows, w.walks)
     x = w.x[rows]
     # G 1 = (1 - |x|^2)/6 on the sampled rows, 4 SE (per-walk masses) + the eps-shell bias
     se = np.sqrt(g["walk_mass"][rows].var(1) / w.walks)
     assert np.all(np.abs(g["G"][rows].sum(1) - (1 - (x ** 2).sum(1)) / 6) <= 4 * se + 1e-4 / 3)
+    # grad G 1 = -x/3, 4 SE of the per-walk gradient masses + the eps-shell bias
+    gse = orc["records"]["gradmass"].std(1) / np.sqrt(w.walks)
+    gg1 = np.stack([g["gradG"][c][rows].sum(1) for c in range(3)], axis=1)
+    assert np.all(np.abs(gg1 + x / 3) <= 4 * gse + (1e-4 / (3 * r0))[:, None])
 
 
 def test_separate_v_partition_fp64_parity_and_solve():
