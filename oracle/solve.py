@@ -115,6 +115,29 @@ def lu_solve(lu, piv, b):
     return x
 
 
+# LU backend of the solves.  The textbook LU above is the default; for the full-size systems
+# (m = 4096, 8000) the golden-value script switches to LAPACK's partial-pivoting LU (the same
+# factorisation, getrf/getrs, used as a library primitive; pinned against the textbook LU in
+# tests/test_oracle_solve.py).
+LU_BACKEND = "textbook"
+
+
+def factor(M):
+    if LU_BACKEND == "lapack":
+        import scipy.linalg
+        return ("lapack", scipy.linalg.lu_factor(np.asarray(M, dtype=np.float64)))
+    return ("textbook", lu_factor(M))
+
+
+def factor_solve(F, b):
+    kind, fac = F
+    if kind == "lapack":
+        import scipy.linalg
+        return scipy.linalg.lu_solve(fac, np.asarray(b, dtype=np.float64))
+    lu, piv = fac
+    return lu_solve(lu, piv, b)
+
+
 def _poly(coef, u):
     return sum(a * u ** k for k, a in enumerate(coef))
 
@@ -161,8 +184,7 @@ def solve_linear(tb, lam, A, b, c, f, g, rcond=DEFAULT_RCOND, alpha=None):
     Lam = assemble(tb["G"], tb["gradG"], lam, A, b, c)
     r = rhs(tb["G"], tb["gradG"], tb["H"], tb["gradH"], lam, A, b, c, f, g)
     alpha = shift(Lam, rcond) if alpha is None else float(alpha)
-    lu, piv = lu_factor(Lam + alpha * np.eye(Lam.shape[0]))
-    s = lu_solve(lu, piv, r)
+    s = factor_solve(factor(Lam + alpha * np.eye(Lam.shape[0])), r)
     u, _ = reconstruct(tb, s, g)
     return dict(s=s, u=u, Lam=Lam, rhs=r, alpha=alpha)
 
@@ -182,8 +204,7 @@ def newton(tb, lam, A, b, c, f, g, nl, tol=1e-10, max_iter=30, rcond=DEFAULT_RCO
     while it < max_iter and np.linalg.norm(R) > tol * r0:
         u, _ = reconstruct(tb, s, g)
         J = Lam + alpha * np.eye(Lam.shape[0]) + G.T @ ((lam * _dpoly(nl, u))[:, None] * G)
-        lu, piv = lu_factor(J)
-        s = s - lu_solve(lu, piv, R)
+        s = s - factor_solve(factor(J), R)
         R = residual(tb, lam, A, b, c, f, g, s, nl) + alpha * s
         hist.append(np.linalg.norm(R))
         it += 1
@@ -243,10 +264,10 @@ def operators(tb, lam, A, b=None, c=None, rcond=DEFAULT_RCOND, alpha=None):
     G = tb["G"]
     Lam = assemble(G, tb["gradG"], lam, A, b, c)
     alpha = shift(Lam, rcond) if alpha is None else float(alpha)
-    lu, piv = lu_factor(Lam + alpha * np.eye(Lam.shape[0]))
+    F = factor(Lam + alpha * np.eye(Lam.shape[0]))
     Alam = G.T * lam[None, :]
-    GL = G @ lu_solve(lu, piv, Alam)
-    HL = tb["H"] - G @ lu_solve(lu, piv, sigma(tb, lam, A, b, c))
+    GL = G @ factor_solve(F, Alam)
+    HL = tb["H"] - G @ factor_solve(F, sigma(tb, lam, A, b, c))
     return dict(GL=GL, HL=HL, alpha=alpha)
 
 

@@ -31,6 +31,18 @@ def test_lu_matches_lapack():
         S.lu_factor(np.array([[1.0, 2.0], [2.0, 4.0]]))
 
 
+def test_lapack_backend_matches_textbook_lu(monkeypatch):
+    rng = np.random.default_rng(3)
+    for n in (1, 5, 64):
+        M = rng.normal(size=(n, n)) + 0.5 * np.eye(n)
+        b = rng.normal(size=(n, 3))
+        ref = S.factor_solve(S.factor(M), b)
+        with monkeypatch.context() as mp:
+            mp.setattr(S, "LU_BACKEND", "lapack")
+            got = S.factor_solve(S.factor(M), b)
+        assert np.allclose(got, ref, rtol=1e-10, atol=1e-12)
+
+
 def _random_toolbox(rng, n=30, m=30, p=12, d=2):
     return dict(G=rng.random((n, m)) * 0.01, gradG=rng.normal(size=(d, n, m)) * 0.01,
                 H=rng.random((n, p)) / p, gradH=rng.normal(size=(d, n, p)))
