@@ -29,8 +29,8 @@ def _as_gpu(orc):
                 walk_vhash=rec["vhash"].copy(), walk_mass=rec["gmass"].copy(), walk_xexit=rec["xexit"].copy())
 
 
-def _compare(g, orc, x, r0):
-    return compare_rows(g, orc, np.arange(x.shape[0]), N, 2, r0, fp32=False)
+def _compare(g, orc, x, r0, fp32=False):
+    return compare_rows(g, orc, np.arange(x.shape[0]), N, 2, r0, fp32=fp32)
 
 
 def test_identical_rows_pass_with_no_divergent_walk(rows):
@@ -49,6 +49,22 @@ def test_scaled_r2_weight_fails(rows):
     g["gradG"] *= 1 + 1e-4
     with pytest.raises(AssertionError, match="walks diverge"):
         _compare(g, orc, x, r0)
+
+
+def test_scaled_r2_weight_under_fp32_drift_fails(rows):
+    # the same scale error while every stopping point is off by 2e-5 (FP32-like drift that makes
+    # the per-walk and per-entry rounding bounds loose): the row sums still expose it
+    x, orc, r0 = rows
+    g = _as_gpu(orc)
+    rng = np.random.default_rng(1)
+    g["walk_xexit"] = g["walk_xexit"] + rng.choice([-2e-5, 2e-5], size=g["walk_xexit"].shape)
+    rep = _compare(g, orc, x, r0, fp32=True)
+    assert rep["ndiv"] == 0
+    g["walk_mass"] *= 1 + 1e-4
+    g["G"] *= 1 + 1e-4
+    g["gradG"] *= 1 + 1e-4
+    with pytest.raises(AssertionError, match="walks diverge|row sums"):
+        _compare(g, orc, x, r0, fp32=True)
 
 
 def test_scaled_matrix_fails(rows):
