@@ -123,8 +123,10 @@ ewos_status ewos_toolbox_build(const ewos_domain* domain, const double* x, int64
  *   P [(d+1)][n][n] float = [d_1 G, .., d_d G, G], KH [(d+1)][n][p] float = [d_1 H, .., H],
  *   Hc [n][p] uint32 exit counts.  rep may be NULL.  max_steps <= 0 -> 10000.
  * Temporaries live in one static 4 MiB device array per GPU that loads the library (held
- * until the process exits); a build whose lookup grids need more is rejected with EWOS_EINVAL
- * before any walk runs (the square workload with n = 4096, p = 512 needs about 0.6 MiB).
+ * until the process exits); a build whose node arrays or lookup grids need more is rejected
+ * with EWOS_EINVAL and a message (ewos_last_error) before any walk runs (the square workload
+ * with n = 4096, p = 512 needs about 0.6 MiB).  The call waits on `stream` (it reads the node
+ * check, the lookup sizes and the step counts back) and returns when the build is done.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current; make that first call before any stream capture.  Every call shares
  * the array and clears the counters it needs; calls whose work overlaps on the GPU race on
@@ -255,6 +257,13 @@ typedef struct {
     double ms_total, ms_assemble, ms_factor, ms_solve;
     int factorizations;       /* LU factorisations run                                       */
     int pivoted_factorizations; /* of which with row interchanges                            */
+    /* device time (CUDA events on the solve's stream) of the mixed mode's tensor-core
+     * assembly products (Lambda = P^T Q and the Newton Jacobian products G^T diag G) and of
+     * its FP32 LU factorisations, with the method's floating-point operations of those
+     * products (2 m^2 K each, the three TF32 split products counted once); 0 in FP64 mode */
+    double dev_ms_gemm;
+    double gemm_flop;
+    double dev_ms_lu;
 } ewos_solve_report;
 
 /* Solve; u_out [nrhs][n] and s_out [nrhs][m] (may be NULL) are host buffers unless

@@ -2022,6 +2022,25 @@ static double elapsed_ms(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// device time of a stretch of work on a stream, added to *acc (CUDA events; waits for the end
+// event, which the solve's stages do anyway when they read their results back)
+struct DevSpan {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t st;
+    double* acc;
+    DevSpan(cudaStream_t s, double* a) : st(s), acc(a) {
+        if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) cudaEventRecord(e0, st);
+    }
+    ~DevSpan() {
+        if (e0 && e1 && cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) *acc += ms;
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
 template <typename TP>
 static ewos_status solve_fp64(ewos_toolbox* tb, SolveWorkspace* ws, const ewos_problem* pb, double rcond, double tol, int max_iter,
                               ewos_solve_report* rep, bool reuse = false) {
@@ -2259,6 +2278,7 @@ template <typename Build>
 static ewos_status factor32_with(const Ctx& C, Build build, int pivoting, ewos_solve_report* rep) {
     build();
     ++rep->factorizations;
+    DevSpan span(C.st, &rep->dev_ms_lu);
     if (pivoting == 0) {
         bool accepted = false;
         ewos_status s = lu_factor_nopiv<float>(C.ws->LU32, (int)C.m, (int)C.m, C.ws->lu, C.st, &accepted,
@@ -2985,6 +3005,8 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
         const bool keep = opt.reuse_factors && !semi;     // the factors of the previous linear solve
         if (!keep) {
             if (tc_assemble_available()) {
+                DevSpan span(C.st, &rep->dev_ms_gemm);
+                rep->gemm_flop += 2.0 * (double)C.m * (double)C.m * (double)(C.E * C.n);
                 ewos_status st = tc_assemble_pq(P32, ws->M, (int)C.n, (int)C.m, C.D, ws->L32, C.st, &ws->tc);
                 if (st != EWOS_OK) return st;
             } else {
@@ -3076,6 +3098,8 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                         C,
                         [&] {
                             if (tcj) {
+                                DevSpan span(C.st, &rep->dev_ms_gemm);
+                                rep->gemm_flop += 2.0 * (double)C.m * (double)C.m * (double)C.n;
                                 ewos_status e = tc_assemble(Gm32, ws->Jx32, ws->LU32, (int)C.m, (int)C.m, (int)C.n, C.st,
                                                             kSplitTF32, &ws->tc);
                                 if (e != EWOS_OK) tst = e;
@@ -3122,6 +3146,8 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                                                                                             ws->nl, pb->nl_ncoef, u, ws->M);
                 auto ta = std::chrono::steady_clock::now();
                 if (tc_assemble_available()) {
+                    DevSpan span(C.st, &rep->dev_ms_gemm);
+                    rep->gemm_flop += 2.0 * (double)C.m * (double)C.m * (double)(C.E * C.n);
                     ewos_status st = tc_assemble_pq(P32, ws->M, (int)C.n, (int)C.m, C.D, ws->L32, C.st, &ws->tc);
                     if (st != EWOS_OK) return st;
                 } else {

@@ -1718,7 +1718,10 @@ static ewos_status build_noalloc_typed(const ewos_domain* dom, const double* d_x
     float* d_r0 = (float*)ar.take(sizeof(float) * n);
     int* d_counter = (int*)ar.take(sizeof(int) * 2);               // row counter, bad-node flag
     unsigned long long* d_stats = (unsigned long long*)ar.take(2 * sizeof(unsigned long long));
-    if (!d_sdf || !d_xT || !d_r0 || !d_counter || !d_stats) return EWOS_ENOMEM;
+    if (!d_sdf || !d_xT || !d_r0 || !d_counter || !d_stats) {
+        set_error("ewos_toolbox_build_noalloc: the node arrays need more than the 4 MiB scratch (reduce n)");
+        return EWOS_EINVAL;
+    }
     EWOS_CUDA_TRY(cudaMemcpyAsync(d_sdf, prm, sizeof(float) * dom->nparams, cudaMemcpyHostToDevice, st));
     // every call starts from cleared counters: the scratch keeps the previous call's contents
     EWOS_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int) * 2, st));

@@ -67,7 +67,8 @@ class SolveReport(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("refine_iters", ctypes.c_int), ("converged", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("residual", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("ms_assemble", ctypes.c_double), ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double),
-                ("factorizations", ctypes.c_int), ("pivoted_factorizations", ctypes.c_int)]
+                ("factorizations", ctypes.c_int), ("pivoted_factorizations", ctypes.c_int),
+                ("dev_ms_gemm", ctypes.c_double), ("gemm_flop", ctypes.c_double), ("dev_ms_lu", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
