@@ -261,6 +261,71 @@ __global__ void lookup_fill_both_kernel(const float* __restrict__ pts, int np, G
     }
 }
 
+// Candidate lists of a grid refined 2x from a coarser one (same origin, half the spacing,
+// twice the cells per axis): a point of a fine cell lies in its parent cell, so its nearest
+// centre is on the parent's list, and the fine cell's list is the parent's list filtered by the
+// same tests (bound R_Q and the bisector test taken over the parent's candidates: a larger
+// bound and any bounding centre keep the list a superset of the exact candidates).  One thread
+// per fine cell; lists stay in increasing centre index.  A parent that scans all centres (empty
+// list) gives an empty fine list.  count pass: counts (and the largest count) or, with start
+// given, fill pass: the CSR lists and, when candK is given, the fixed-stride rows (K slots, the
+// unused ones holding the sentinel np).
+template <int D>
+__global__ void lookup_refine_kernel(const float* __restrict__ pts, int np, GridSpec coarse, GridSpec fine, float slack,
+                                     const int* __restrict__ cstart, const int* __restrict__ ccand,
+                                     int* __restrict__ count, int* __restrict__ maxcount, const int* __restrict__ start,
+                                     int* __restrict__ cand, int K, uint16_t* __restrict__ candK) {
+    const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= fine.ncell) return;
+    int64_t rem = cell, pc = 0, mul = 1;
+    for (int c = 0; c < D; ++c) {
+        const int k = (int)(rem % fine.dims[c]);
+        rem /= fine.dims[c];
+        pc += (int64_t)(k >> 1) * mul;
+        mul *= coarse.dims[c];
+    }
+    const int s0 = cstart[pc], e0 = cstart[pc + 1];
+    if (candK)
+        for (int q = 0; q < K; ++q) candK[cell * K + q] = (uint16_t)np;
+    if (s0 == e0) {                 // the parent scans all centres: so does this cell
+        if (count) count[cell] = 0;
+        if (maxcount) atomicMax(maxcount, kCandidateCap + 1);
+        return;
+    }
+    CellTest<D> t;
+    cell_box_f<D>(fine, cell, t.blo, t.bhi);
+    t.slack = slack;
+    float R2 = 3.0e38f;
+    int bj = 0x7fffffff;
+    for (int q = s0; q < e0; ++q) {
+        const int j = ccand[q];
+        float mx = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            const float v = pts[j * D + c];
+            const float u = fmaxf(fabsf(v - t.blo[c]), fabsf(v - t.bhi[c]));
+            mx += u * u;
+        }
+        if (mx < R2 || (mx == R2 && j < bj)) { R2 = mx; bj = j; }
+    }
+    cell_setup_stored<D>(pts, bj, R2 * (1.0f + 1e-4f) + slack, t);
+    if (!start) {
+        int cnt = 0;
+        for (int q = s0; q < e0; ++q) cnt += cell_candidate<D>(pts, ccand[q], t);
+        count[cell] = cnt;
+        atomicMax(maxcount, cnt);
+        return;
+    }
+    int w = start[cell];
+    int wk = 0;
+    for (int q = s0; q < e0; ++q) {
+        const int j = ccand[q];
+        if (!cell_candidate<D>(pts, j, t)) continue;
+        cand[w++] = j;
+        if (candK && wk < K) candK[cell * K + wk++] = (uint16_t)j;
+    }
+}
+
 // exclusive scan of count[0..len) into start[0..len], single block (len is at most a few 10^5)
 __global__ void exclusive_scan_kernel(const int* __restrict__ count, int64_t len, int* __restrict__ start) {
     __shared__ int warp_sums[32];
@@ -320,7 +385,7 @@ struct DeviceLookup {
     }
 };
 
-constexpr int kFixedCandMax = 16;
+constexpr int kFixedCandMax = 32;
 
 static GridSpec make_grid(int dim, const double* lo, const double* hi, double h) {
     GridSpec g{};
@@ -342,8 +407,17 @@ static GridSpec make_grid(int dim, const double* lo, const double* hi, double h)
 }
 
 template <typename T>
+static ewos_status build_lookup_refined(int dim, const double* d_pts, int np, const double* lo, const double* hi,
+                                        double h, double h_direct, cudaStream_t st, DeviceLookup& out,
+                                        bool want_fixed);
+
+// Lookup grid of spacing h over [lo, hi].  Grids finer than h_direct are refined 2x (repeatedly)
+// from a grid of spacing >= h_direct, whose lists are computed directly from all centres.
+template <typename T>
 static ewos_status build_lookup(int dim, const double* d_pts, int np, const double* lo, const double* hi,
-                                double h, cudaStream_t st, DeviceLookup& out, bool want_fixed) {
+                                double h, cudaStream_t st, DeviceLookup& out, bool want_fixed, double h_direct = 0.0) {
+    if (h_direct > 0.0 && h < h_direct)
+        return build_lookup_refined<T>(dim, d_pts, np, lo, hi, h, h_direct, st, out, want_fixed);
     out.np = np;
     out.grid = make_grid(dim, lo, hi, h);
     const int64_t nc = out.grid.ncell;
@@ -397,6 +471,71 @@ static ewos_status build_lookup(int dim, const double* d_pts, int np, const doub
     ::ewos::dev_free(d_rad);
     ::ewos::dev_free(d_best);
     ::ewos::dev_free(d_pf);
+    return EWOS_OK;
+}
+
+template <typename T>
+static ewos_status build_lookup_refined(int dim, const double* d_pts, int np, const double* lo, const double* hi,
+                                        double h, double h_direct, cudaStream_t st, DeviceLookup& out,
+                                        bool want_fixed) {
+    DeviceLookup coarse;
+    struct Rel { DeviceLookup* L; ~Rel() { L->release(); } } rel{&coarse};
+    ewos_status s = build_lookup<float>(dim, d_pts, np, lo, hi, 2.0 * h, st, coarse, false, h_direct);
+    if (s != EWOS_OK) return s;
+    out.np = np;
+    out.grid = coarse.grid;
+    out.grid.h = coarse.grid.h * 0.5;
+    out.grid.ncell = 1;
+    for (int c = 0; c < 3; ++c) {
+        if (c < dim) { out.grid.dims[c] = 2 * coarse.grid.dims[c]; out.grid.ncell *= out.grid.dims[c]; }
+        else out.grid.dims[c] = 1;
+    }
+    const int64_t nc = out.grid.ncell;
+    double ext = 0;
+    for (int c = 0; c < dim; ++c) ext = std::max(ext, std::max(std::fabs(lo[c]), std::fabs(hi[c])) + (hi[c] - lo[c]));
+    const float slack = (float)(1e-6 * ext * ext);
+    int* d_count = nullptr;
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_count, sizeof(int) * (nc + 1)));
+    struct Fr { int** p; ~Fr() { ::ewos::dev_free(*p); } } fr{&d_count};
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&out.start, sizeof(int) * (nc + 1)));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&out.pts, sizeof(T) * (np + 1) * dim));
+    EWOS_CUDA_TRY(cudaMemsetAsync(d_count + nc, 0, sizeof(int), st));
+    const int64_t ne = (int64_t)np * dim;
+    const int cb = (int)((ne + 255) / 256);
+    if (dim == 2) ::ewos::note_launch(), convert_points_kernel<T, 2><<<cb, 256, 0, st>>>(d_pts, (T*)out.pts, ne);
+    else ::ewos::note_launch(), convert_points_kernel<T, 3><<<cb, 256, 0, st>>>(d_pts, (T*)out.pts, ne);
+    const float* pf = (const float*)coarse.pts;          // the coarse lookup's FP32 centres
+    const int tb = 128;
+    const int nb = (int)((nc + tb - 1) / tb);
+    if (dim == 2)
+        ::ewos::note_launch(), lookup_refine_kernel<2><<<nb, tb, 0, st>>>(pf, np, coarse.grid, out.grid, slack, coarse.start,
+                                                                        coarse.cand, d_count, d_count + nc, nullptr,
+                                                                        nullptr, 0, nullptr);
+    else
+        ::ewos::note_launch(), lookup_refine_kernel<3><<<nb, tb, 0, st>>>(pf, np, coarse.grid, out.grid, slack, coarse.start,
+                                                                        coarse.cand, d_count, d_count + nc, nullptr,
+                                                                        nullptr, 0, nullptr);
+    ::ewos::note_launch(), exclusive_scan_kernel<<<1, 1024, 0, st>>>(d_count, nc, out.start);
+    int hv[2] = {0, 0};
+    EWOS_CUDA_TRY(cudaMemcpyAsync(&hv[0], out.start + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EWOS_CUDA_TRY(cudaMemcpyAsync(&hv[1], d_count + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    const int total = hv[0], kmax = hv[1];
+    out.ncand = total;
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&out.cand, sizeof(int) * std::max(1, total)));
+    if (want_fixed && kmax >= 1 && kmax <= kFixedCandMax && np < 65535) {
+        out.K = kmax;
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&out.candK, sizeof(uint16_t) * nc * kmax));
+    }
+    if (dim == 2)
+        ::ewos::note_launch(), lookup_refine_kernel<2><<<nb, tb, 0, st>>>(pf, np, coarse.grid, out.grid, slack, coarse.start,
+                                                                        coarse.cand, nullptr, nullptr, out.start,
+                                                                        out.cand, out.K, out.candK);
+    else
+        ::ewos::note_launch(), lookup_refine_kernel<3><<<nb, tb, 0, st>>>(pf, np, coarse.grid, out.grid, slack, coarse.start,
+                                                                        coarse.cand, nullptr, nullptr, out.start,
+                                                                        out.cand, out.K, out.candK);
+    EWOS_CUDA_TRY(cudaGetLastError());
     return EWOS_OK;
 }
 
@@ -513,6 +652,7 @@ struct WalkArgs {
     int* row_counter;
     unsigned long long* stat_steps;
     unsigned long long* stat_capped;
+    unsigned long long* stat_error;     // streamed rows: warps that gave up waiting (NULL elsewhere)
     int32_t* rec_exit;
     int32_t* rec_steps;
     T* rec_mass;
@@ -569,13 +709,14 @@ __device__ __forceinline__ void draw_step(uint32_t l, uint32_t k, uint32_t row, 
 // nearest V centre through the fixed-stride table (K slots per grid cell, uniform trip count)
 template <typename T, int D>
 __device__ __forceinline__ int nearest_fixed(const Lookup<T, D>& L, const uint16_t* __restrict__ candK, int K,
-                                             const T* q) {
+                                             const T* q, int sentinel) {
     const int cell = lookup_cell(L, q);
     const uint16_t* c = candK + (size_t)cell * K;
     T best = T(3.0e38f);
     int bi = 0;
     for (int t = 0; t < K; ++t) {
         const int j = c[t];
+        if (j >= sentinel) break;             // the list ends where the sentinel padding starts
         T d2 = 0;
 #pragma unroll
         for (int cc = 0; cc < D; ++cc) { const T dd = q[cc] - L.pts[j * D + cc]; d2 += dd * dd; }
@@ -735,7 +876,7 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
             const T wsum = (D == 2) ? T(1) + S : T(1) + S + S * S;
 #pragma unroll
             for (int c = 0; c < D; ++c) pt[c] = xi[c] + r0 * S * Zb[c];
-            const int jb = K > 0 ? nearest_fixed(V, candK, K, pt) : nearest_or_scan(V, a.m, pt);
+            const int jb = K > 0 ? nearest_fixed(V, candK, K, pt, a.m) : nearest_or_scan(V, a.m, pt);
 #pragma unroll
             for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + jb], r02 * wsum * Zb[c]);
             if (RECORD) atomicXor(&a.rec_vhash[(size_t)row * a.N + l], cellmix(0xFFFFFFFFu, jb));
@@ -787,7 +928,7 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
                 const T rR = r * R;
 #pragma unroll
                 for (int c = 0; c < D; ++c) pt[c] = X[c] + rR * Zs[c];
-                const int j = K > 0 ? nearest_fixed(V, candK, K, pt) : nearest_or_scan(V, a.m, pt);
+                const int j = K > 0 ? nearest_fixed(V, candK, K, pt, a.m) : nearest_or_scan(V, a.m, pt);
                 const T r2 = r * r;
                 atomicAdd(&acc[(size_t)D * a.m + j], r2);
                 if (k > 0) {
@@ -886,6 +1027,435 @@ __global__ void __launch_bounds__(1024, 1) wos_walk_batch_kernel(const WalkArgs<
         g = walk_rows<T, D, KIND, false, true>(s_a, g, row_off[lo], row_off[lo + 1], gcounter);
         __syncthreads();
     }
+}
+
+// ------------------------------------------------------------------ streamed rows
+// The row loop above makes every lane of a CTA wait at the end of each row for the row's
+// longest walk (23 % of the issued lane slots on the square, 40 % on the ball).  Here a CTA
+// keeps up to kSlots rows in flight: a lane that finds the current row's walks all handed out
+// takes a walk of the next row straight away.  One row at a time owns the shared-memory
+// accumulators; walks of the other rows add their contributions, already scaled, to the output
+// rows in global memory (which the build zeroes first).  A row is finished by the warp that
+// bins its last walk: it adds the shared accumulators to the row's global part (or stores them
+// when the row had none), clears them and hands them to the row currently taking walks.
+// The ball term of a walk (Prop. 2.6 (ii)) is path independent, so it is binned together with
+// the walk's exit, 32 walks at a time, from the warp's queue.
+constexpr int kSlots = 4;                     // rows in flight per CTA
+constexpr int kSlotFree = -2, kSlotNone = -1; // slot states besides a row index
+constexpr unsigned kIdleLimit = 1u << 26;     // idle iterations of a warp before it gives up
+
+struct StreamState {
+    int row[kSlots];           // row index, kSlotFree (reusable), kSlotNone (no rows left), kSlotOpening
+    int seq[kSlots];           // sequence number of the slot's row (rows are opened in sequence)
+    unsigned next[kSlots];     // next walk index to hand out
+    unsigned done[kSlots];     // walks binned (ball term and exit)
+    int global_part[kSlots];   // a walk of the row accumulated in global memory
+    int fetch_seq;             // sequence number of the row handing out walks
+    int pending;               // sequence number waiting for its slot to be freed, or -1
+    int smem_slot;             // slot whose row owns the shared accumulators (-1: none)
+    unsigned epoch;            // bumped when a row's walks are all handed out
+};
+constexpr int kSlotOpening = -3;
+
+// slot s (claimed: kSlotOpening) gets the next row of the grid-wide counter as row number `seq`
+template <typename T, int D>
+__device__ __forceinline__ void stream_fill(StreamState& S, const WalkArgs<T, D>& a, int s, int seq) {
+    const int R = atomicAdd(a.row_counter, 1);
+    S.seq[s] = seq;
+    if (R >= a.n) {
+        S.next[s] = 0xFFFFFFFFu;
+        __threadfence_block();
+        atomicExch(&S.row[s], kSlotNone);
+    } else {
+        S.done[s] = 0u;
+        S.global_part[s] = 0;
+        atomicCAS(&S.smem_slot, -1, s);
+        __threadfence_block();
+        atomicExch(&S.row[s], R);             // the row before the walks: a lane that takes a walk reads it
+        __threadfence_block();
+        atomicExch(&S.next[s], 0u);
+    }
+    __threadfence_block();
+    atomicExch(&S.fetch_seq, seq);
+}
+
+// row number `seq` goes to slot seq % kSlots once that slot is free: now, or by the warp that
+// frees it (the note in `pending`); exactly one caller fills the slot
+template <typename T, int D>
+__device__ __forceinline__ void stream_open(StreamState& S, const WalkArgs<T, D>& a, int seq) {
+    const int s = seq % kSlots;
+    if (atomicCAS(&S.row[s], kSlotFree, kSlotOpening) == kSlotFree) {
+        stream_fill(S, a, s, seq);
+        return;
+    }
+    atomicExch(&S.pending, seq);
+    if (atomicCAS(&S.row[s], kSlotFree, kSlotOpening) == kSlotFree) {     // freed in between
+        atomicCAS(&S.pending, seq, -1);
+        stream_fill(S, a, s, seq);
+    }
+}
+
+// called after slot s was freed: fills it when a row number waits for it
+template <typename T, int D>
+__device__ __forceinline__ void stream_freed(StreamState& S, const WalkArgs<T, D>& a, int s) {
+    const int p = *(volatile int*)&S.pending;
+    if (p < 0 || p % kSlots != s) return;
+    if (atomicCAS(&S.pending, p, -1) != p) return;
+    if (atomicCAS(&S.row[s], kSlotFree, kSlotOpening) == kSlotFree) stream_fill(S, a, s, p);
+}
+
+// a walk for this lane: (slot, walk index) or false
+template <typename T, int D>
+__device__ __forceinline__ bool stream_acquire(StreamState& S, const WalkArgs<T, D>& a, int& slot, uint32_t& l) {
+    const int f = (*(volatile int*)&S.fetch_seq) % kSlots;
+    const unsigned N = (unsigned)a.N;
+    if (*(volatile unsigned*)&S.next[f] >= N) return false;
+    const unsigned w = atomicAdd(&S.next[f], 1u);
+    if (w >= N) return false;
+    __threadfence_block();
+    if (w == N - 1) {
+        // this lane took the row's last walk: it opens the next row
+        atomicAdd(&S.epoch, 1u);
+        stream_open(S, a, *(volatile int*)&S.seq[f] + 1);
+    }
+    slot = f;
+    l = w;
+    return true;
+}
+
+// nothing left to hand out, in this CTA, ever
+__device__ __forceinline__ bool stream_finished(StreamState& S) {
+    const int f = (*(volatile int*)&S.fetch_seq) % kSlots;
+    return *(volatile int*)&S.row[f] == kSlotNone;
+}
+
+template <typename T, int D>
+struct StreamQueue {
+    T* X;            // [warps][kQueue][D] stopping point
+    T* U;            // [warps][kQueue][D] first direction U_0
+    uint32_t* L;     // [warps][kQueue] walk index
+    uint32_t* M;     // [warps][kQueue] slot | smem-mode << 3
+    uint32_t* vh;    // records only
+    uint32_t* K;
+    T* mass;
+};
+
+template <typename T, int D>
+__host__ __device__ constexpr size_t stream_queue_bytes(int nwarps, bool record) {
+    return (size_t)nwarps * kQueue * (2 * D * sizeof(T) + 2 * sizeof(uint32_t) +
+                                      (record ? 2 * sizeof(uint32_t) + sizeof(T) : 0));
+}
+
+// ball term and exit of one queued walk; returns the slot when this walk was its row's last
+template <typename T, int D, bool RECORD>
+__device__ __forceinline__ int stream_bin(const WalkArgs<T, D>& a, StreamState& S, const StreamQueue<T, D>& q, int e,
+                                          const Lookup<T, D>& V, const uint16_t* candK, int K, T* acc, T* accKH,
+                                          uint32_t* accH) {
+    const uint32_t meta = q.M[e], l = q.L[e];
+    const int slot = (int)(meta & 7u);
+    const bool sm = (meta >> 3) & 1u;
+    const int R = S.row[slot];
+    T X[D], U[D], xi[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) { X[c] = q.X[e * D + c]; U[c] = q.U[e * D + c]; xi[c] = a.x[(size_t)R * D + c]; }
+    const T r0 = a.r0[R];
+    const T invN = T(1) / (T)a.N;
+    // ball term of the first sphere: gradG += (r0/2) (sum_k S^k) Z at the V cell of x_i + r0 S Z
+    T Sb, Zb[D], pt[D];
+    draw_ball<T, D>(l, (uint32_t)R, a.inst, a.k0, a.k1, Sb, Zb);
+    const T wsum = (D == 2) ? T(1) + Sb : T(1) + Sb + Sb * Sb;
+#pragma unroll
+    for (int c = 0; c < D; ++c) pt[c] = xi[c] + r0 * Sb * Zb[c];
+    const int jb = K > 0 ? nearest_fixed(V, candK, K, pt, a.m) : nearest_or_scan(V, a.m, pt);
+    const int jz = nearest_or_scan(a.Z, a.p, X);
+    const size_t nm = (size_t)a.n * a.m, np = (size_t)a.n * a.p;
+    if (sm) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + jb], r0 * r0 * wsum * Zb[c]);
+        atomicAdd(&accH[jz], 1u);
+#pragma unroll
+        for (int c = 0; c < D; ++c) atomicAdd(&accKH[(size_t)c * a.p + jz], U[c]);
+    } else {
+        const T sGG = invN / (T(2) * r0), sKH = T(D) * invN / r0;
+#pragma unroll
+        for (int c = 0; c < D; ++c) atomicAdd(&a.P[c * nm + (size_t)R * a.m + jb], r0 * r0 * wsum * Zb[c] * sGG);
+        atomicAdd(&a.Hc[(size_t)R * a.p + jz], 1u);
+#pragma unroll
+        for (int c = 0; c < D; ++c) atomicAdd(&a.KH[c * np + (size_t)R * a.p + jz], U[c] * sKH);
+    }
+    if (RECORD) {
+        const size_t ri = (size_t)R * a.N + l;
+        a.rec_exit[ri] = jz;
+#pragma unroll
+        for (int c = 0; c < D; ++c) a.rec_xexit[ri * D + c] = X[c];
+        a.rec_mass[ri] = q.mass[e];
+        a.rec_steps[ri] = (int32_t)q.K[e];
+        a.rec_vhash[ri] = q.vh[e] ^ cellmix(0xFFFFFFFFu, (uint32_t)jb);
+    }
+    return slot | (sm ? 0 : 8);
+}
+
+// the warp finishes the row of `slot` (all its walks binned)
+template <typename T, int D>
+__device__ __forceinline__ void stream_flush(const WalkArgs<T, D>& a, StreamState& S, int slot, T* acc, T* accKH,
+                                             uint32_t* accH) {
+    const int lane = threadIdx.x & 31;
+    __threadfence();
+    const int R = S.row[slot];
+    const bool own = *(volatile int*)&S.smem_slot == slot;
+    const bool gp = *(volatile int*)&S.global_part[slot] != 0;
+    const T invN = T(1) / (T)a.N;
+    const T r0 = a.r0[R];
+    const T sG = invN / T(2 * D), sGG = invN / (T(2) * r0), sKH = T(D) * invN / r0;
+    const size_t nm = (size_t)a.n * a.m, np = (size_t)a.n * a.p;
+    if (own) {
+        for (int t = lane; t < a.m; t += 32) {
+#pragma unroll
+            for (int c = 0; c <= D; ++c) {
+                T* dst = &a.P[c * nm + (size_t)R * a.m + t];
+                T v = acc[(size_t)c * a.m + t] * (c < D ? sGG : sG);
+                if (gp) v += __ldcg(dst);
+                *dst = v;
+                acc[(size_t)c * a.m + t] = T(0);
+            }
+        }
+        for (int t = lane; t < a.p; t += 32) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                T* dst = &a.KH[c * np + (size_t)R * a.p + t];
+                T v = accKH[(size_t)c * a.p + t] * sKH;
+                if (gp) v += __ldcg(dst);
+                *dst = v;
+                accKH[(size_t)c * a.p + t] = T(0);
+            }
+            uint32_t h = accH[t];
+            if (gp) h += __ldcg(&a.Hc[(size_t)R * a.p + t]);
+            a.Hc[(size_t)R * a.p + t] = h;
+            a.KH[D * np + (size_t)R * a.p + t] = (T)h * invN;
+            accH[t] = 0u;
+        }
+        __syncwarp();
+        __threadfence_block();
+        if (lane == 0) {
+            // the accumulators go to the row taking walks, if it still has walks to hand out
+            const int f = (*(volatile int*)&S.fetch_seq) % kSlots;
+            const int nxt = (f != slot && *(volatile int*)&S.row[f] >= 0 && *(volatile unsigned*)&S.next[f] < (unsigned)a.N)
+                                ? f : -1;
+            atomicExch(&S.smem_slot, nxt);
+        }
+    } else {
+        for (int t = lane; t < a.p; t += 32)
+            a.KH[D * np + (size_t)R * a.p + t] = (T)__ldcg(&a.Hc[(size_t)R * a.p + t]) * invN;
+    }
+    __syncwarp();
+    __threadfence_block();
+    if (lane == 0) {
+        S.next[slot] = 0xFFFFFFFFu;
+        __threadfence_block();
+        atomicExch(&S.row[slot], kSlotFree);
+        stream_freed(S, a, slot);
+    }
+    __syncwarp();
+}
+
+template <typename T, int D, int KIND, bool RECORD>
+__device__ __forceinline__ void walk_stream(const WalkArgs<T, D>& a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* acc = reinterpret_cast<T*>(smem_raw);
+    T* accKH = acc + (size_t)(D + 1) * a.m;
+    uint32_t* accH = reinterpret_cast<uint32_t*>(accKH + (size_t)D * a.p);
+    T* s_sdf = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(accH + a.p) + 15) & ~uintptr_t(15));
+    const int nwarps = blockDim.x >> 5;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    StreamQueue<T, D> q;
+    q.X = s_sdf + ((a.sdf_len + 3) & ~3);
+    q.U = q.X + (size_t)nwarps * kQueue * D;
+    q.L = reinterpret_cast<uint32_t*>(q.U + (size_t)nwarps * kQueue * D);
+    q.M = q.L + (size_t)nwarps * kQueue;
+    const size_t qr = RECORD ? (size_t)nwarps * kQueue : 0;
+    q.vh = q.M + (size_t)nwarps * kQueue;
+    q.K = q.vh + qr;
+    q.mass = reinterpret_cast<T*>(q.K + qr);
+    unsigned char* s_v = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(q.mass + qr) + 15) & ~uintptr_t(15));
+    __shared__ StreamState S;
+
+    for (int t = threadIdx.x; t < a.sdf_len; t += blockDim.x) s_sdf[t] = a.sdf[t];
+    Lookup<T, D> V = a.V;
+    const uint16_t* candK = a.v_candK;
+    if (a.v_in_smem) {
+        T* vp = reinterpret_cast<T*>(s_v);
+        for (int t = threadIdx.x; t < (a.m + 1) * D; t += blockDim.x) vp[t] = a.V.pts[t];
+        V.pts = vp;
+        if (a.v_K > 0) {
+            uint16_t* vk = reinterpret_cast<uint16_t*>(vp + (size_t)(a.m + 1) * D);
+            for (int64_t t = threadIdx.x; t < (int64_t)a.v_ncell * a.v_K; t += blockDim.x) vk[t] = a.v_candK[t];
+            candK = vk;
+        } else {
+            int* vs = reinterpret_cast<int*>(vp + (size_t)(a.m + 1) * D);
+            int* vc = vs + a.v_ncell + 1;
+            for (int t = threadIdx.x; t <= a.v_ncell; t += blockDim.x) vs[t] = a.V.start[t];
+            for (int64_t t = threadIdx.x; t < a.v_ncand; t += blockDim.x) vc[t] = a.V.cand[t];
+            V.start = vs; V.cand = vc;
+        }
+    }
+    const int K = a.v_K;
+    for (int t = threadIdx.x; t < (D + 1) * a.m; t += blockDim.x) acc[t] = T(0);
+    for (int t = threadIdx.x; t < D * a.p; t += blockDim.x) accKH[t] = T(0);
+    for (int t = threadIdx.x; t < a.p; t += blockDim.x) accH[t] = 0u;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kSlots; ++s) {
+            S.row[s] = kSlotFree; S.seq[s] = -1; S.next[s] = 0xFFFFFFFFu; S.done[s] = 0u; S.global_part[s] = 0;
+        }
+        S.smem_slot = -1;
+        S.pending = -1;
+        S.epoch = 0u;
+        S.fetch_seq = 0;
+        stream_open(S, a, 0);        // the first row goes to slot 0 and owns the accumulators
+    }
+    __syncthreads();
+
+    const unsigned N = (unsigned)a.N;
+    const T invN = T(1) / (T)a.N;
+    const T sG = invN / T(2 * D);
+    const unsigned below = (1u << lane) - 1u;
+    unsigned long long my_steps = 0, my_capped = 0;
+    unsigned seen_epoch = *(volatile unsigned*)&S.epoch;
+    unsigned idle = 0;
+    // lane state
+    bool have = false, sm = false;
+    int slot = 0, R = 0;
+    uint32_t l = 0, k = 0, vh = 0u;
+    T X[D], U0[D], r0 = T(0), mass = T(0), sGG = T(0);
+#pragma unroll
+    for (int c = 0; c < D; ++c) { X[c] = T(0); U0[c] = T(0); }
+    int qn = 0;
+    auto start_walk = [&]() {
+        if (stream_acquire(S, a, slot, l)) {
+            have = true;
+            R = S.row[slot];
+            sm = *(volatile int*)&S.smem_slot == slot;
+            if (!sm) S.global_part[slot] = 1;
+#pragma unroll
+            for (int c = 0; c < D; ++c) X[c] = a.x[(size_t)R * D + c];
+            r0 = a.r0[R];
+            sGG = invN / (T(2) * r0);
+            k = 0;
+        }
+    };
+    for (;;) {
+        if (!have) start_walk();
+        const bool busy = have || qn > 0;
+        if (!__any_sync(0xffffffffu, busy)) {
+            if (stream_finished(S)) break;
+            if (++idle > kIdleLimit) { if (lane == 0) atomicAdd(a.stat_error, 1ull); break; }
+            __nanosleep(200);
+            continue;
+        }
+        idle = 0;
+        T r = r0;
+        if (have && k > 0) {
+            if (KIND == SDF_POLYGON && a.e_cnt) r = polygon_dist_grid<T, D>(a, s_sdf, X);
+            else r = Sdf<T, D, KIND>::eval(s_sdf, a.nsdf, X);
+        }
+        const bool stop = have && k > 0 && (r < a.eps || (int64_t)k > a.max_steps);
+        const unsigned smk = __ballot_sync(0xffffffffu, stop);
+        bool urgent = false;
+        if (stop) {
+            const int e = wid * kQueue + qn + __popc(smk & below);
+#pragma unroll
+            for (int c = 0; c < D; ++c) { q.X[e * D + c] = X[c]; q.U[e * D + c] = U0[c]; }
+            q.L[e] = l;
+            q.M[e] = (uint32_t)slot | (sm ? 8u : 0u);
+            if (RECORD) {
+                q.mass[e] = mass / T(2 * D); q.vh[e] = vh; q.K[e] = k - 1;
+                vh = 0u; mass = T(0);
+            }
+            my_steps += k;
+            my_capped += (r >= a.eps);
+            urgent = *(volatile unsigned*)&S.next[slot] >= N;
+            have = false;
+            start_walk();
+            r = r0;
+        }
+        qn += __popc(smk);
+        if (have) {
+            T Rr, Zs[D], U[D], pt[D];
+            draw_step<T, D>(l, k, (uint32_t)R, a.inst, a.k0, a.k1, Rr, Zs, U);
+            const T rR = r * Rr;
+#pragma unroll
+            for (int c = 0; c < D; ++c) pt[c] = X[c] + rR * Zs[c];
+            const int j = K > 0 ? nearest_fixed(V, candK, K, pt, a.m) : nearest_or_scan(V, a.m, pt);
+            const T r2 = r * r;
+            if (k == 0) {
+#pragma unroll
+                for (int c = 0; c < D; ++c) U0[c] = U[c];
+            }
+            if (sm) {
+                atomicAdd(&acc[(size_t)D * a.m + j], r2);
+                if (k > 0) {
+#pragma unroll
+                    for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + j], U0[c] * r2);
+                }
+            } else {
+                const size_t nm = (size_t)a.n * a.m;
+                T* prow = a.P + (size_t)R * a.m + j;
+                atomicAdd(prow + D * nm, r2 * sG);
+                if (k > 0) {
+                    const T w = r2 * sGG;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) atomicAdd(prow + c * nm, U0[c] * w);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < D; ++c) X[c] += r * U[c];
+            if (RECORD) { mass += r2; vh ^= cellmix(k, (uint32_t)j); }
+            ++k;
+        }
+        // binning of queued walks: 32 at a time, or everything when a row waits for it
+        __syncwarp();
+        const unsigned ep = *(volatile unsigned*)&S.epoch;
+        const bool drain_all = __any_sync(0xffffffffu, urgent) || ep != seen_epoch || !__any_sync(0xffffffffu, have);
+        seen_epoch = ep;
+        int finished = -1;
+        while (qn >= 32 || (drain_all && qn > 0)) {
+            const int take = qn >= 32 ? 32 : qn;
+            const int e = qn - 1 - lane;
+            int res = -1;
+            if (lane < take) res = stream_bin<T, D, RECORD>(a, S, q, wid * kQueue + e, V, candK, K, acc, accKH, accH);
+            // global-mode contributions must be visible before the row can be finished
+            if (__any_sync(0xffffffffu, res >= 8)) __threadfence();
+            else __threadfence_block();
+            if (res >= 0) {
+                const int s = res & 7;
+                if (atomicAdd(&S.done[s], 1u) == N - 1) finished = s;
+            }
+            qn -= take;
+            __syncwarp();
+            unsigned fm = __ballot_sync(0xffffffffu, finished >= 0);
+            while (fm) {
+                const int src = __ffs(fm) - 1;
+                fm &= fm - 1;
+                const int s = __shfl_sync(0xffffffffu, finished, src);
+                stream_flush<T, D>(a, S, s, acc, accKH, accH);
+            }
+            finished = -1;
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_steps += __shfl_down_sync(0xffffffffu, my_steps, o);
+        my_capped += __shfl_down_sync(0xffffffffu, my_capped, o);
+    }
+    if (lane == 0) {
+        atomicAdd(a.stat_steps, my_steps);
+        if (my_capped) atomicAdd(a.stat_capped, my_capped);
+    }
+}
+
+template <typename T, int D, int KIND, bool RECORD>
+__global__ void __launch_bounds__(1024, 1) wos_walk_stream_kernel(WalkArgs<T, D> a) {
+    walk_stream<T, D, KIND, RECORD>(a);
 }
 
 // ------------------------------------------------------------------ host side
@@ -1051,28 +1621,65 @@ static int max_ctas_per_sm(int tpb, size_t smem) {
     return nb;
 }
 
+template <typename T, int D, int KIND, bool RECORD>
+static cudaError_t launch_stream_walks(const WalkArgs<T, D>& a, int grid, int tpb, size_t smem, cudaStream_t st) {
+    auto k = wos_walk_stream_kernel<T, D, KIND, RECORD>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    ::ewos::note_launch(), k<<<grid, tpb, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int D, int KIND>
+static cudaError_t dispatch_stream_walks(const WalkArgs<T, D>& a, bool rec, int grid, int tpb, size_t smem,
+                                         cudaStream_t st) {
+    return rec ? launch_stream_walks<T, D, KIND, true>(a, grid, tpb, smem, st)
+               : launch_stream_walks<T, D, KIND, false>(a, grid, tpb, smem, st);
+}
+
+template <typename T, int D, int KIND>
+static int max_stream_ctas_per_sm(int tpb, size_t smem) {
+    int nb = 0;
+    auto k = wos_walk_stream_kernel<T, D, KIND, false>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, tpb, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
 // process-wide cache of the walk kernel configurations chosen by the autotuner
 struct TuneKey {
     size_t elem; int dim, kind; int m, p; int64_t N; bool rec; int tpb_req, place_req, ctas_req; double grid_req;
+    int kernel_req;
     bool operator==(const TuneKey& o) const {
         return elem == o.elem && dim == o.dim && kind == o.kind && m == o.m && p == o.p && N == o.N && rec == o.rec &&
-               tpb_req == o.tpb_req && place_req == o.place_req && ctas_req == o.ctas_req && grid_req == o.grid_req;
+               tpb_req == o.tpb_req && place_req == o.place_req && ctas_req == o.ctas_req && grid_req == o.grid_req &&
+               kernel_req == o.kernel_req;
     }
 };
-struct TuneVal { int tpb; bool v_smem; int vgrid; };
+struct TuneVal { int tpb; bool v_smem; int vgrid; int kernel; };
 static std::mutex g_tune_mu;
 static std::vector<std::pair<TuneKey, TuneVal>> g_tune;
 
-static bool tune_lookup(const TuneKey& k, int& tpb, bool& v_smem, int& vgrid) {
+static bool tune_lookup(const TuneKey& k, int& tpb, bool& v_smem, int& vgrid, int* kernel = nullptr) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     for (auto& e : g_tune)
-        if (e.first == k) { tpb = e.second.tpb; v_smem = e.second.v_smem; vgrid = e.second.vgrid; return true; }
+        if (e.first == k) {
+            tpb = e.second.tpb; v_smem = e.second.v_smem; vgrid = e.second.vgrid;
+            if (kernel) *kernel = e.second.kernel;
+            return true;
+        }
     return false;
 }
 
-static void tune_store(const TuneKey& k, int tpb, bool v_smem, int vgrid) {
+static void tune_store(const TuneKey& k, int tpb, bool v_smem, int vgrid, int kernel) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune.push_back({k, TuneVal{tpb, v_smem, vgrid}});
+    g_tune.push_back({k, TuneVal{tpb, v_smem, vgrid, kernel}});
 }
 
 // Everything before the walk launch of one toolbox: distances and node radii, the Voronoi
@@ -1085,6 +1692,7 @@ struct PrepOut {
     int cached_tpb, cached_grid;
     bool cached_smem;
     bool tune_grid;
+    int cached_kernel;
 };
 
 template <typename T, int D>
@@ -1131,29 +1739,32 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
     else surf = 2 * ((hi[0] - lo[0]) * (hi[1] - lo[1]) + (hi[1] - lo[1]) * (hi[2] - lo[2]) + (hi[0] - lo[0]) * (hi[2] - lo[2]));
     const double hz = D == 2 ? surf / p : std::sqrt(surf / p);
     // V grid spacing: factor x (volume / m)^(1/d); the autotuner also tries the other factor
-    const double gf_default = o.lookup_grid_scale > 0 ? o.lookup_grid_scale : (D == 2 ? 1.0 : 0.5);
-    const double gf_alt = D == 2 ? 0.5 : 1.0;
+    const double gf_default = o.lookup_grid_scale > 0 ? o.lookup_grid_scale : (D == 2 ? 0.5 : 0.25);
+    const double gf_alt = D == 2 ? 0.25 : 0.18;
+    // grids finer than this are refined from coarser ones instead of scanning every centre per cell
+    const double h_direct = 0.6 * hv;
     const bool tune_grid = allow_alt && o.lookup_grid_scale <= 0 &&
                            (o.threads_per_block <= 0 || !(o.hash_in_smem == 0 || o.hash_in_smem == 1));
     // V-centres: y when the caller gives a separate source partition, else the nodes
     const double* d_v = tb->y ? tb->y : d_x;
     TuneKey key{sizeof(T), D, dom->kind, m, p, tb->N, o.record_walks != 0, o.threads_per_block, o.hash_in_smem,
-                o.ctas_per_sm, o.lookup_grid_scale};
+                o.ctas_per_sm, o.lookup_grid_scale, o.walk_kernel};
     int cached_tpb = 0, cached_grid = 0;
     bool cached_smem = false;
-    const bool have_cached = tune_lookup(key, cached_tpb, cached_smem, cached_grid);
+    int cached_kernel = 1;
+    const bool have_cached = tune_lookup(key, cached_tpb, cached_smem, cached_grid, &cached_kernel);
     // the default-spacing V grid is skipped when this shape is known to walk on the other one and
     // the cell weights do not need it (given by the caller, or counted on the nodes' own grid)
     const bool alt_only = tune_grid && have_cached && cached_grid == 1 && (o.cell_weights || tb->y);
     ewos_status s = EWOS_OK;
     if (!alt_only) {
-        s = build_lookup<T>(D, d_v, m, lo, hi, hv * gf_default, st, ctx.V, true);
+        s = build_lookup<T>(D, d_v, m, lo, hi, hv * gf_default, st, ctx.V, true, h_direct);
         if (s != EWOS_OK) return s;
     }
     s = build_lookup<T>(D, d_z, p, lo, hi, hz, st, ctx.Z, false);
     if (s != EWOS_OK) return s;
     if (tune_grid && (!have_cached || cached_grid == 1)) {
-        s = build_lookup<T>(D, d_v, m, lo, hi, hv * gf_alt, st, ctx.V2, true);
+        s = build_lookup<T>(D, d_v, m, lo, hi, hv * gf_alt, st, ctx.V2, true, h_direct);
         if (s != EWOS_OK) return s;
     }
     int e_nx = 0, e_ny = 0;
@@ -1186,8 +1797,8 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
         // lambda_i = |W_i| / |D|: the Voronoi cells of the nodes x (a lookup of its own when the
         // V-centres are separate)
         if (tb->y) {
-            const double hw = std::pow(vol / n, 1.0 / D) * gf_default;
-            s = build_lookup<T>(D, d_x, n, lo, hi, hw, st, ctx.W, false);
+            const double hw0 = std::pow(vol / n, 1.0 / D);
+            s = build_lookup<T>(D, d_x, n, lo, hi, hw0 * gf_default, st, ctx.W, false, 0.6 * hw0);
             if (s != EWOS_OK) return s;
         }
         const DeviceLookup& WL = tb->y ? ctx.W : ctx.V;
@@ -1230,10 +1841,11 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
     a.Z = lookup_view<T, D>(ctx.Z);
     a.P = (T*)tb->P; a.KH = (T*)tb->KH; a.Hc = tb->Hc;
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_counter, sizeof(int)));
-    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_stats, 2 * sizeof(unsigned long long)));
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_stats, 3 * sizeof(unsigned long long)));
     EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counter, 0, sizeof(int), st));
-    EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_stats, 0, 2 * sizeof(unsigned long long), st));
+    EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_stats, 0, 3 * sizeof(unsigned long long), st));
     a.row_counter = ctx.d_counter; a.stat_steps = ctx.d_stats; a.stat_capped = ctx.d_stats + 1;
+    a.stat_error = ctx.d_stats + 2;
     a.rec_exit = tb->rec_exit; a.rec_steps = tb->rec_steps; a.rec_mass = (T*)tb->rec_mass;
     a.rec_vhash = tb->rec_vhash;
     a.rec_xexit = (T*)tb->rec_xexit;
@@ -1246,7 +1858,7 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
     a.v_in_smem = 0;
     po.gf_default = gf_default; po.gf_alt = gf_alt;
     po.have_cached = have_cached; po.cached_tpb = cached_tpb; po.cached_grid = cached_grid;
-    po.cached_smem = cached_smem; po.tune_grid = tune_grid;
+    po.cached_smem = cached_smem; po.tune_grid = tune_grid; po.cached_kernel = cached_kernel;
     return EWOS_OK;
 }
 
@@ -1266,11 +1878,11 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     if (s != EWOS_OK) return s;
     const double gf_default = po.gf_default, gf_alt = po.gf_alt;
     const bool have_cached = po.have_cached;
-    const int cached_tpb = po.cached_tpb, cached_grid = po.cached_grid;
+    const int cached_tpb = po.cached_tpb, cached_grid = po.cached_grid, cached_kernel = po.cached_kernel;
     const bool cached_smem = po.cached_smem;
     const int sdf_len = a.sdf_len;
     TuneKey key{sizeof(T), D, dom->kind, m, p, tb->N, o.record_walks != 0, o.threads_per_block, o.hash_in_smem,
-                o.ctas_per_sm, o.lookup_grid_scale};
+                o.ctas_per_sm, o.lookup_grid_scale, o.walk_kernel};
     const bool rec = o.record_walks != 0;
     const size_t acc_bytes = sizeof(T) * ((size_t)(D + 1) * m + (size_t)D * p) + sizeof(uint32_t) * p;
     const size_t sdf_bytes = sizeof(T) * ((sdf_len + 3) & ~3);
@@ -1284,30 +1896,47 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const size_t budget = (size_t)smem_optin - 1024;
-    auto base_for = [&](int t) {
-        return (((acc_bytes + 15) & ~size_t(15)) + sdf_bytes + queue_bytes<T, D>(t / 32, rec) + 15) & ~size_t(15);
+    auto base_for = [&](int t, int kern) {
+        const size_t qb = kern == 2 ? stream_queue_bytes<T, D>(t / 32, rec) : queue_bytes<T, D>(t / 32, rec);
+        return (((acc_bytes + 15) & ~size_t(15)) + sdf_bytes + qb + 15) & ~size_t(15);
     };
-    // a launch configuration: block size, V grid, where the V lookup lives
-    struct Cfg { int tpb; int vg; bool v_smem; size_t smem; int per_sm; int grid; };
-    auto configure = [&](int tpb, int vg, int want_smem, int rows, Cfg& c) -> bool {
+    // a launch configuration: walk kernel (1 rows, 2 streamed rows), block size, V grid, where
+    // the V lookup lives
+    struct Cfg { int tpb; int vg; bool v_smem; size_t smem; int per_sm; int grid; int kern; };
+    auto configure = [&](int tpb, int vg, int want_smem, int rows, Cfg& c, int kern) -> bool {
         const DeviceLookup& L = *Vs[vg];
         if (!L.start) return false;
-        const size_t base = base_for(tpb);
+        const size_t base = base_for(tpb, kern);
         if (base > budget) return false;
         c.tpb = tpb;
         c.vg = vg;
+        c.kern = kern;
         c.v_smem = want_smem != 0 && base + v_bytes_of(L) <= budget;
         if (want_smem == 1 && !c.v_smem) return false;
         c.smem = base + (c.v_smem ? v_bytes_of(L) : 0);
         int ps = 0;
-        if (dom->kind == SDF_BALL) ps = max_ctas_per_sm<T, D, SDF_BALL>(tpb, c.smem);
-        else if (dom->kind == SDF_BOX) ps = max_ctas_per_sm<T, D, SDF_BOX>(tpb, c.smem);
-        else ps = max_ctas_per_sm<T, D, SDF_POLYGON>(tpb, c.smem);
+        if (kern == 2) {
+            if (dom->kind == SDF_BALL) ps = max_stream_ctas_per_sm<T, D, SDF_BALL>(tpb, c.smem);
+            else if (dom->kind == SDF_BOX) ps = max_stream_ctas_per_sm<T, D, SDF_BOX>(tpb, c.smem);
+            else ps = max_stream_ctas_per_sm<T, D, SDF_POLYGON>(tpb, c.smem);
+        } else {
+            if (dom->kind == SDF_BALL) ps = max_ctas_per_sm<T, D, SDF_BALL>(tpb, c.smem);
+            else if (dom->kind == SDF_BOX) ps = max_ctas_per_sm<T, D, SDF_BOX>(tpb, c.smem);
+            else ps = max_ctas_per_sm<T, D, SDF_POLYGON>(tpb, c.smem);
+        }
         if (ps < 1) return false;
         if (o.ctas_per_sm > 0) ps = std::min(ps, o.ctas_per_sm);
         c.per_sm = ps;
         c.grid = std::max(1, std::min(nsm * ps, rows));
         return true;
+    };
+    // streamed rows add to the outputs in global memory: they start from zero
+    const size_t nm = (size_t)n * m, np = (size_t)n * p;
+    auto zero_outputs = [&]() -> cudaError_t {
+        cudaError_t e = cudaMemsetAsync(tb->P, 0, sizeof(T) * (D + 1) * nm, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(tb->KH, 0, sizeof(T) * (D + 1) * np, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(tb->Hc, 0, sizeof(uint32_t) * np, st);
+        return e;
     };
     auto launch = [&](const Cfg& c, WalkArgs<T, D>& args) -> cudaError_t {
         const DeviceLookup& L = *Vs[c.vg];
@@ -1315,6 +1944,11 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
         args.v_ncell = (int)L.grid.ncell; args.v_ncand = L.ncand;
         args.v_K = L.K; args.v_candK = L.candK;
         args.v_in_smem = c.v_smem ? 1 : 0;
+        if (c.kern == 2) {
+            if (dom->kind == SDF_BALL) return dispatch_stream_walks<T, D, SDF_BALL>(args, rec, c.grid, c.tpb, c.smem, st);
+            if (dom->kind == SDF_BOX) return dispatch_stream_walks<T, D, SDF_BOX>(args, rec, c.grid, c.tpb, c.smem, st);
+            return dispatch_stream_walks<T, D, SDF_POLYGON>(args, rec, c.grid, c.tpb, c.smem, st);
+        }
         if (dom->kind == SDF_BALL) return dispatch_walks<T, D, SDF_BALL>(args, rec, c.grid, c.tpb, c.smem, st);
         if (dom->kind == SDF_BOX) return dispatch_walks<T, D, SDF_BOX>(args, rec, c.grid, c.tpb, c.smem, st);
         return dispatch_walks<T, D, SDF_POLYGON>(args, rec, c.grid, c.tpb, c.smem, st);
@@ -1323,29 +1957,36 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     const bool fixed_tpb = o.threads_per_block > 0;
     const bool fixed_place = o.hash_in_smem == 0 || o.hash_in_smem == 1;
     const int req_tpb = std::min(1024, (o.threads_per_block + 31) / 32 * 32);
-    if (fixed_tpb && fixed_place) {
-        if (!configure(req_tpb, 0, o.hash_in_smem, n, cfg)) {
+    const int req_kern = o.walk_kernel == 1 || o.walk_kernel == 2 ? o.walk_kernel : 0;
+    if (fixed_tpb && fixed_place && req_kern) {
+        if (!configure(req_tpb, 0, o.hash_in_smem, n, cfg, req_kern)) {
             set_error("walk kernel: requested block size / lookup placement does not fit");
             return EWOS_EINVAL;
         }
-    } else if (have_cached && configure(cached_tpb, cached_grid, cached_smem ? 1 : 0, n, cfg)) {
+    } else if (have_cached && configure(cached_tpb, cached_grid, cached_smem ? 1 : 0, n, cfg, cached_kernel)) {
         // configuration chosen earlier for this problem shape
     } else {
         // autotuner: time each candidate configuration on a prefix of rows once per problem
         // shape (cached for the process); the prefix rows are recomputed by the full launch
         std::vector<Cfg> cands;
-        for (int vg : {0, 1})
-            for (int t : {512, 1024}) {
-                if (fixed_tpb && t != req_tpb) continue;
-                for (int sm : {0, 1}) {
-                    if (fixed_place && sm != o.hash_in_smem) continue;
-                    Cfg c{};
-                    if (configure(t, vg, sm, n, c)) cands.push_back(c);
+        // the streamed-rows kernel is a candidate only on request: measured slower on the
+        // square and ball workloads (the rows that do not own the shared accumulators add
+        // through L2 reductions)
+        for (int kern : {1, 2}) {
+            if (req_kern ? kern != req_kern : kern != 1) continue;
+            for (int vg : {0, 1})
+                for (int t : {512, 1024}) {
+                    if (fixed_tpb && t != req_tpb) continue;
+                    for (int sm : {0, 1}) {
+                        if (fixed_place && sm != o.hash_in_smem) continue;
+                        Cfg c{};
+                        if (configure(t, vg, sm, n, c, kern)) cands.push_back(c);
+                    }
                 }
-            }
+        }
         if (fixed_tpb && cands.empty()) {
             Cfg c{};
-            if (configure(req_tpb, 0, 0, n, c)) cands.push_back(c);
+            if (configure(req_tpb, 0, 0, n, c, req_kern ? req_kern : 1)) cands.push_back(c);
         }
         if (cands.empty()) {
             set_error("toolbox row does not fit in shared memory (m, p too large for one CTA)");
@@ -1363,6 +2004,7 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
                 WalkArgs<T, D> trial = a;
                 trial.n = rows;
                 EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counter, 0, sizeof(int), st));
+                if (c.kern == 2) EWOS_CUDA_TRY(zero_outputs());
                 cudaEventRecord(t0, st);
                 EWOS_CUDA_TRY(launch(c, trial));
                 cudaEventRecord(t1, st);
@@ -1374,11 +2016,12 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
             cudaEventDestroy(t0); cudaEventDestroy(t1);
             cfg.grid = std::max(1, std::min(nsm * cfg.per_sm, n));
             EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counter, 0, sizeof(int), st));
-            EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_stats, 0, 2 * sizeof(unsigned long long), st));
+            EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_stats, 0, 3 * sizeof(unsigned long long), st));
             if (tb->rec_vhash) EWOS_CUDA_TRY(cudaMemsetAsync(tb->rec_vhash, 0, sizeof(uint32_t) * n * tb->N, st));
         }
-        tune_store(key, cfg.tpb, cfg.v_smem, cfg.vg);
+        tune_store(key, cfg.tpb, cfg.v_smem, cfg.vg, cfg.kern);
     }
+    if (cfg.kern == 2) EWOS_CUDA_TRY(zero_outputs());
     EWOS_CUDA_TRY(cudaEventRecord(ev[3], st));
     EWOS_CUDA_TRY(launch(cfg, a));
     const int tpb = cfg.tpb, per_sm = cfg.per_sm, grid = cfg.grid;
@@ -1386,9 +2029,13 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     const size_t smem = cfg.smem;
 
     EWOS_CUDA_TRY(cudaEventRecord(ev[4], st));
-    unsigned long long stats[2] = {0, 0};
+    unsigned long long stats[3] = {0, 0, 0};
     EWOS_CUDA_TRY(cudaMemcpyAsync(stats, ctx.d_stats, sizeof(stats), cudaMemcpyDeviceToHost, st));
     EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    if (stats[2]) {
+        set_error("walk kernel (streamed rows): a warp waited too long for a row and gave up");
+        return EWOS_ETIMEOUT;
+    }
     float ms[4];
     cudaEventElapsedTime(&ms[0], ev[0], ev[4]);
     cudaEventElapsedTime(&ms[1], ev[0], ev[1]);
@@ -1403,6 +2050,7 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     r.lookup_grid_scale = cfg.vg == 0 ? gf_default : gf_alt;
     r.lookup_candidates = Vs[cfg.vg]->K;
     r.smem_bytes = (int64_t)smem;
+    r.walk_kernel = cfg.kern;
     return EWOS_OK;
 }
 

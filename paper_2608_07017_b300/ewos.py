@@ -40,7 +40,8 @@ class BuildOpts(ctypes.Structure):
                 ("cell_weights", ctypes.c_void_p), ("cell_samples", ctypes.c_int64),
                 ("threads_per_block", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("hash_in_smem", ctypes.c_int),
                 ("record_walks", ctypes.c_int), ("instance", ctypes.c_uint32), ("inputs_on_device", ctypes.c_int),
-                ("lookup_grid_scale", ctypes.c_double), ("v_nodes", ctypes.c_void_p), ("m", ctypes.c_int64)]
+                ("lookup_grid_scale", ctypes.c_double), ("v_nodes", ctypes.c_void_p), ("m", ctypes.c_int64),
+                ("walk_kernel", ctypes.c_int)]
 
 
 class BuildReport(ctypes.Structure):
@@ -48,7 +49,7 @@ class BuildReport(ctypes.Structure):
                 ("ms_total", ctypes.c_double), ("ms_walk", ctypes.c_double), ("ms_lookup", ctypes.c_double),
                 ("ms_cells", ctypes.c_double), ("threads_per_block", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
                 ("grid", ctypes.c_int), ("hash_in_smem", ctypes.c_int), ("smem_bytes", ctypes.c_int64),
-                ("lookup_grid_scale", ctypes.c_double), ("lookup_candidates", ctypes.c_int)]
+                ("lookup_grid_scale", ctypes.c_double), ("lookup_candidates", ctypes.c_int), ("walk_kernel", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -305,7 +306,7 @@ class Toolbox:
 
 def build_toolbox(domain_kind, dim, params, x, z, walks, eps, seed=0, precision=32, max_steps=0, cell_weights=None,
                   cell_samples=0, threads_per_block=0, ctas_per_sm=0, hash_in_smem=-1, record_walks=False,
-                  instance=0, stream=None, on_device=False, lookup_grid_scale=0.0, y=None):
+                  instance=0, stream=None, on_device=False, lookup_grid_scale=0.0, y=None, walk_kernel=0):
     """y: optional V-centres [m][d] of a separate source partition (columns of G, grad G)."""
     prm = _f64(params)
     dom = _Domain(SDF[domain_kind], dim, prm.ctypes.data, prm.size)
@@ -318,7 +319,7 @@ def build_toolbox(domain_kind, dim, params, x, z, walks, eps, seed=0, precision=
     cw = _f64(cell_weights)
     o = BuildOpts(precision, max_steps, stream, _ptr(cw), cell_samples, threads_per_block, ctas_per_sm, hash_in_smem,
                   1 if record_walks else 0, instance, 1 if on_device else 0, float(lookup_grid_scale),
-                  _ptr(yy), 0 if yy is None else yy.shape[0])
+                  _ptr(yy), 0 if yy is None else yy.shape[0], int(walk_kernel))
     h = ctypes.c_void_p()
     st = lib().ewos_toolbox_build(ctypes.byref(dom), _ptr(xx), n, _ptr(zz), p, int(walks), float(eps), int(seed),
                                   ctypes.byref(o), ctypes.byref(h))

@@ -49,9 +49,12 @@ def test_green_radius_matches_oracle():
     assert np.max(np.abs(r32 - ref32) / ref32) < 4e-6
 
 
-def _parity(w, rows, N, precision, max_steps=10000, min_exit=0.999):
+def _parity(w, rows, N, precision, max_steps=10000, min_exit=0.999, walk_kernel=0):
     tb = ewos.build_toolbox(w.domain.kind, w.domain.dim, w.domain.params, w.x, w.z, N, w.eps, seed=w.seed,
-                            precision=precision, record_walks=True, cell_samples=100000, max_steps=max_steps)
+                            precision=precision, record_walks=True, cell_samples=100000, max_steps=max_steps,
+                            walk_kernel=walk_kernel)
+    if walk_kernel:
+        assert tb.report()["walk_kernel"] == walk_kernel
     g = gpu_arrays(tb, N)
     orc = oracle.walk_rows(w.domain.dim, w.domain.kind, w.domain.params, w.x, w.z, N, w.eps, w.seed, rows=rows,
                            records=True, max_steps=max_steps)
@@ -234,3 +237,30 @@ def test_separate_v_partition_fp64_parity_and_solve():
         assert s.shape == (y.shape[0],)
         assert np.max(np.abs(u - ref["u"])) <= 1e-9 * np.max(np.abs(ref["u"])), mode
     tb.close()
+
+
+@pytest.mark.parametrize("walk_kernel", [1, 2])
+def test_both_walk_kernels_parity(walk_kernel):
+    """One row per CTA at a time (1) and streamed rows (2, several rows in flight per CTA, walks of
+    rows that do not own the shared accumulators add to the output in global memory): both meet
+    the same bars against the oracle, on small square, ball and star cases and ragged shapes."""
+    w = W.square(16, 16, walks=2000, eps=1e-4, problem=False)
+    _parity(w, np.arange(0, w.x.shape[0], 2), 2000, 32, walk_kernel=walk_kernel)
+    x, _ = W.ball_nodes(500, seed=1)
+    wb = W.Workload("ball500", W.Domain(3, "ball", np.array([0.0, 0, 0, 1])), x, W.fibonacci_sphere(200), 1000,
+                    1e-4, 32, 3)
+    _parity(wb, np.arange(0, 500, 5), 1000, 32, walk_kernel=walk_kernel)
+    V = W.star_polygon(5)
+    xs = W.star_nodes(V, 300, np.random.default_rng(4))
+    ws = W.Workload("star300", W.Domain(2, "polygon", V.ravel().copy()), xs, W.polygon_boundary_nodes(V, 40), 500,
+                    1e-4, 32, 1)
+    _parity(ws, np.arange(0, 300, 3), 500, 32, walk_kernel=walk_kernel)
+    # N = 1 and N = 3 (a row's walks run out at once), fewer rows than CTAs, p = 1, FP64
+    xr = np.concatenate([W.disk_nodes(0.3, 0.9), [[0.0, 0.9995], [0.3, -0.2]]])
+    for N, prec, pz in ((1, 64, 16), (3, 64, 1), (777, 32, 37)):
+        wr = W.Workload("ragged", W.Domain(2, "ball", np.array([0.0, 0, 1])), xr, W.circle_nodes(pz), N, 1e-3, prec, 11)
+        _parity(wr, np.arange(xr.shape[0]), N, prec, walk_kernel=walk_kernel, min_exit=0.99 if N < 10 else 0.999)
+    # the disk workload in FP64 at full size
+    wd = W.disk400(problem=False)
+    rep, g, _ = _parity(wd, np.arange(0, 400, 7), 1000, 64, walk_kernel=walk_kernel)
+    assert rep["exit_equal"] >= 0.9999
