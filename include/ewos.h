@@ -250,6 +250,10 @@ typedef struct {
                                  on one factorisation, and exact Newton per right-hand side when
                                  that does not reach tol (iters = chord sweeps when it does).
                                  0 -> one right-hand side at a time, Newton for semilinear.   */
+    int newton_refactor;      /* mixed-mode Newton: 0 -> each Newton system is refined with the
+                                 FP32 factors of the last Jacobian factored while that refinement
+                                 reaches 1e-10 in 24 sweeps (refactored otherwise); 1 -> the
+                                 Jacobian of every step is factored                           */
 } ewos_problem;
 
 typedef struct {

@@ -87,6 +87,7 @@ static void run_request(ewos_server* sv, ServerSlot* sl, ServerRequest* rq) {
     pb.inputs_on_device = 0;
     SolveOptions opt;
     opt.batched = pb.mode == EWOS_SOLVE_MIXED;
+    opt.newton_reuse = pb.newton_refactor == 0;
     rq->u.assign((size_t)rq->tb->n * pb.nrhs, 0.0);
     rq->s.assign((size_t)rq->tb->m * pb.nrhs, 0.0);
     rq->status = solve_on(rq->tb, sl->ws, &pb, rq->u.data(), rq->s.data(), 0, &rq->rep, opt);

@@ -2980,6 +2980,8 @@ static ewos_status solve_batched(const Ctx& C, int R, const double* nl, int nnl,
 
 constexpr double kRefineTol = 1e-10;
 constexpr int kRefineMax = 40;
+constexpr int kStaleSweeps = 24;     // refinement sweeps allowed on the factors of an older Jacobian
+constexpr double kStaleTol = 1e-10;  // relative residual a Newton system must reach with them
 constexpr int kChordMax = 80;    // chord sweeps before the semilinear batch falls back to Newton
 
 template <typename TP>
@@ -3070,8 +3072,11 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
             rep->iters = 1;
             rep->ms_solve = elapsed_ms(t2);
         } else {
-            // Newton on R(s) + alpha s = 0; each step solved by the FP32 factors of the Jacobian
-            // with FP64 refinement of the Jacobian system
+            // Newton on R(s) + alpha s = 0.  Each Newton system J(u) x = R is solved by FP64
+            // refinement (J applied matrix-free) preconditioned by FP32 factors of a Jacobian:
+            // the current one when factored at this step, else the last one factored, kept while
+            // the refinement still reaches kStaleTol within kStaleSweeps sweeps (the step is the
+            // Newton step either way; only the preconditioner is older), refactored otherwise.
             const double* nl = ws->nl;
             for (int64_t r = 0; r < nrhs; ++r) {
                 double* s = ws->s + r * C.m;
@@ -3082,8 +3087,26 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                 const double r0 = norm2(C, ws->y, C.m);
                 double rn = r0;
                 int it = 0;
+                bool have_factors = false;
                 while (it < max_iter && rn > tol * r0) {
                     u_from_s(C, tb->P, tb->KH, tb->precision == 64, s, g, ws->u2);
+                    if (have_factors && opt.newton_reuse) {
+                        cudaMemcpyAsync(ws->rhs, ws->y, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
+                        double rel = 1.0;
+                        ewos_status st = refine<TP>(C, ws->rhs, ws->x, alpha, ws->u2, nl, pb->nl_ncoef, 1e-10,
+                                                    kStaleSweeps, &sweeps, &rel);
+                        if (st != EWOS_OK) return st;
+                        if (rel <= kStaleTol) {
+                            ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, -1.0, ws->x, s);
+                            residual<TP>(C, s, g, f, nl, pb->nl_ncoef, alpha, ws->y);
+                            rn = norm2(C, ws->y, C.m);
+                            ++it;
+                            continue;
+                        }
+                        // the refinement used y as scratch: put the Newton residual back
+                        cudaMemcpyAsync(ws->y, ws->rhs, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
+                    }
+                    have_factors = true;
                     dim3 gj((unsigned)((C.m + 255) / 256), (unsigned)C.n);
                     const TP* Gm = (const TP*)tb->P + (size_t)C.D * C.n * C.m;
                     ::ewos::note_launch(), jac_scale32_kernel<TP><<<gj, 256, 0, C.st>>>(Gm, ws->u2, tb->lambda, nl, pb->nl_ncoef,
@@ -3432,6 +3455,7 @@ extern "C" ewos_status ewos_solve(ewos_toolbox* tb, const ewos_problem* pb, doub
     }
     ewos::SolveOptions opt;
     opt.batched = pb && pb->batched != 0;
+    opt.newton_reuse = !(pb && pb->newton_refactor != 0);
     return ewos::solve_on(tb, tb->ws, pb, u_out, s_out, outputs_on_device, rep_out, opt);
 }
 

@@ -14,6 +14,9 @@ struct SolveOptions {
     // this workspace, for the same toolbox and coefficients, instead of assembling and factoring
     // again (the operator estimates solve their unit right-hand sides in chunks this way).
     bool reuse_factors = false;
+    // Semilinear mixed solves: keep the FP32 factors of an earlier Newton step's Jacobian as
+    // the refinement's preconditioner while the refinement still converges (refactor otherwise).
+    bool newton_reuse = true;
 };
 
 struct SolveWorkspace;

@@ -61,7 +61,7 @@ class _Problem(ctypes.Structure):
                 ("nl_coef", ctypes.c_void_p), ("nl_ncoef", ctypes.c_int), ("mode", ctypes.c_int),
                 ("rcond", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("inputs_on_device", ctypes.c_int), ("stream", ctypes.c_void_p), ("pivoting", ctypes.c_int),
-                ("batched", ctypes.c_int)]
+                ("batched", ctypes.c_int), ("newton_refactor", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
@@ -232,7 +232,8 @@ class Toolbox:
         return dict(G=self.get("G"), gradG=self.get("gradG"), H=self.get("H"), gradH=self.get("gradH"))
 
     def solve(self, A, f, g, b=None, c=None, kind="linear", coef=None, mode="fp64", rcond=-1.0, tol=0.0,
-              max_iter=0, want_s=False, on_device=False, out=None, stream=None, pivoting=0, batched=False):
+              max_iter=0, want_s=False, on_device=False, out=None, stream=None, pivoting=0, batched=False,
+              newton_refactor=False):
         """Solve the problem of include/ewos.h; returns (u [nrhs][n] or [n], s or None, report).
         pivoting=1 forces row interchanges in the mixed-mode LU; batched=True refines all
         right-hand sides together (mixed mode; chord iteration for semilinear problems)."""
@@ -245,7 +246,7 @@ class Toolbox:
         cf = _f64(coef) if coef is not None else None
         pb = _Problem(_ptr(Ad), _ptr(bd), _ptr(cd), _ptr(fd), _ptr(gd), nrhs, NL[kind], _ptr(cf),
                       0 if cf is None else cf.size, MODE[mode], float(rcond), float(tol), int(max_iter),
-                      1 if on_device else 0, stream, int(pivoting), 1 if batched else 0)
+                      1 if on_device else 0, stream, int(pivoting), 1 if batched else 0, 1 if newton_refactor else 0)
         if out is not None:
             u = out
             optr = out.data_ptr()
