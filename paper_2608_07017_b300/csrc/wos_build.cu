@@ -712,6 +712,9 @@ __device__ __forceinline__ int nearest_fixed(const Lookup<T, D>& L, const uint16
                                              const T* q, int sentinel) {
     const int cell = lookup_cell(L, q);
     const uint16_t* c = candK + (size_t)cell * K;
+    // a cell with one candidate lies inside that centre's Voronoi cell: no distance needed
+    const int j0 = c[0];
+    if (K == 1 || c[1] >= sentinel) return j0;
     T best = T(3.0e38f);
     int bi = 0;
     for (int t = 0; t < K; ++t) {
@@ -1739,7 +1742,7 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
     else surf = 2 * ((hi[0] - lo[0]) * (hi[1] - lo[1]) + (hi[1] - lo[1]) * (hi[2] - lo[2]) + (hi[0] - lo[0]) * (hi[2] - lo[2]));
     const double hz = D == 2 ? surf / p : std::sqrt(surf / p);
     // V grid spacing: factor x (volume / m)^(1/d); the autotuner also tries the other factor
-    const double gf_default = o.lookup_grid_scale > 0 ? o.lookup_grid_scale : (D == 2 ? 0.5 : 0.25);
+    const double gf_default = o.lookup_grid_scale > 0 ? o.lookup_grid_scale : 0.125;
     const double gf_alt = D == 2 ? 0.25 : 0.18;
     // grids finer than this are refined from coarser ones instead of scanning every centre per cell
     const double h_direct = 0.6 * hv;
