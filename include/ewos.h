@@ -387,7 +387,9 @@ ewos_status ewos_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t
 ewos_status ewos_debug_green_radius(const void* u, void* R, int64_t count, int precision);
 /* Test hook (no counterpart in the paper): C [M][N] = A^T B for host FP32 arrays A [K][M],
  * B [K][N], through the tensor-core (tcgen05, TF32) GEMM of the mixed-precision assembly;
- * split = 1 uses three TF32 products per step (hi*hi + hi*lo + lo*hi).  EWOS_EINVAL when the
+ * split = 1 uses three TF32 products per step (hi*hi + hi*lo + lo*hi); split = 2 does the same
+ * with the symmetric launch of the assembly (only the tiles on and below the diagonal are
+ * computed, each also stored transposed: for a symmetric A^T B, M = N).  EWOS_EINVAL when the
  * device has no sm_100-family tensor cores. */
 ewos_status ewos_debug_tc_gemm(const float* A, const float* B, float* C, int M, int N, int K, int split);
 

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
                                                            const __grid_constant__ CUtensorMap mapAl,
                                                            const __grid_constant__ CUtensorMap mapBl, int M, int N,
                                                            int Kp, float* __restrict__ C, int64_t ldc,
-                                                           int* __restrict__ err, int sub) {
+                                                           int* __restrict__ err, int sub, int tri = 0) {
     using CF = Cfg<SPLIT, ST>;
     constexpr int BN = CF::BN, STAGES = CF::STAGES, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
     constexpr int STAGE_BYTES = CF::STAGE_BYTES;
@@ -129,7 +129,19 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
     __shared__ int s_fail;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    // tri: a symmetric result; the 1D grid runs over the tiles on and below the diagonal (ty >= tx)
+    // and each off-diagonal tile is also stored transposed
+    int tile_y = blockIdx.y, tile_x = blockIdx.x;
+    if (tri) {
+        const int t = blockIdx.x;
+        int ty = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while ((ty + 1) * (ty + 2) / 2 <= t) ++ty;
+        while (ty * (ty + 1) / 2 > t) --ty;
+        tile_y = ty;
+        tile_x = t - ty * (ty + 1) / 2;
+    }
+    const int m0 = tile_y * BM, n0 = tile_x * BN;
+    const bool mirror = tri && tile_x != tile_y;
     const int nk = Kp / BK;
     ::ewos::pdl_trigger();
 
@@ -280,6 +292,11 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
                 } else {
                     for (int q = 0; q < 32; ++q)
                         if (col0 + q < N) cp[q] = sub ? cp[q] - __uint_as_float(v[q]) : __uint_as_float(v[q]);
+                }
+                if (mirror) {
+                    // C[col][row]: for each column the warp's 32 rows are 32 consecutive floats
+                    for (int q = 0; q < 32; ++q)
+                        if (col0 + q < N) C[(int64_t)(col0 + q) * ldc + row] = __uint_as_float(v[q]);
                 }
             }
         }
@@ -458,7 +475,7 @@ void tc_scratch_free(TcScratch* t) {
 // Enqueues the transposes and the GEMM on st; the pipeline-timeout word is left in *err_dev
 // for the caller to check after the stream has run (no host synchronisation here).
 static ewos_status tc_enqueue(tc::Scratch& S, const float* Akm, const float* Bkm, float* C, int M, int N, int K,
-                              cudaStream_t st, bool split) {
+                              cudaStream_t st, bool split, bool sym = false) {
     using namespace tc;
     const int Kp = (K + BK - 1) / BK * BK;
     const size_t need = (size_t)std::max(M, N) * Kp;
@@ -495,8 +512,12 @@ static ewos_status tc_enqueue(tc::Scratch& S, const float* Akm, const float* Bkm
     EWOS_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
     dim3 grid((N + bn - 1) / bn, (M + BM - 1) / BM);
     if (split) {
+        const bool tri = sym && M == N;
+        const int nt = (M + BM - 1) / BM;
+        if (tri) grid = dim3((unsigned)(nt * (nt + 1) / 2));
         EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<true>::SMEM_BYTES));
-        ::ewos::note_launch(), gemm_tf32_kernel<true><<<grid, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err, 0);
+        ::ewos::note_launch(), gemm_tf32_kernel<true><<<grid, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err, 0,
+                                                                                            tri ? 1 : 0);
     } else {
         EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<false>::SMEM_BYTES));
         ::ewos::note_launch(), gemm_tf32_kernel<false><<<grid, 128, Cfg<false>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err, 0);
@@ -570,7 +591,7 @@ __global__ void pq_split_kernel(const float* __restrict__ P, const double* __res
 // Lambda [m][m] = P^T Q with Q = M P, both operands prepared by pq_split_kernel, then the
 // three-product TF32 GEMM; waits for the launch (pipeline timeouts are reported)
 ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D, float* C, cudaStream_t st,
-                           TcScratch** owned) {
+                           TcScratch** owned, bool sym = false) {
     using namespace tc;
     if (!*owned) *owned = new TcScratch();
     Scratch& S = (*owned)->s;
@@ -609,8 +630,11 @@ ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D
     }
     EWOS_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
     EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<true>::SMEM_BYTES));
-    const dim3 g2((m + Cfg<true>::BN - 1) / Cfg<true>::BN, (m + BM - 1) / BM);
-    ::ewos::note_launch(), gemm_tf32_kernel<true><<<g2, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, m, m, Kp, C, m, S.err, 0);
+    const int nt = (m + BM - 1) / BM;
+    static_assert(Cfg<true>::BN == BM, "square tiles for the symmetric launch");
+    const dim3 g2 = sym ? dim3((unsigned)(nt * (nt + 1) / 2)) : dim3((m + Cfg<true>::BN - 1) / Cfg<true>::BN, nt);
+    ::ewos::note_launch(), gemm_tf32_kernel<true><<<g2, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, m, m, Kp, C, m, S.err, 0,
+                                                                                       sym ? 1 : 0);
     EWOS_CUDA_TRY(cudaGetLastError());
     return tc_check(S, st);
 }
@@ -711,10 +735,10 @@ ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64
     ::ewos::note_launch();
     if (csm)
         EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true, kUpd, true>, grid, dim3(128), kCsmSmem, st, ma, mb, mal, mbl,
-                                         M, N, Kp, C, ldc, S.err, 1));
+                                         M, N, Kp, C, ldc, S.err, 1, 0));
     else
         EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true>, grid, dim3(128), (size_t)Cfg<true>::SMEM_BYTES, st, ma, mb,
-                                         mal, mbl, M, N, Kp, C, ldc, S.err, 1));
+                                         mal, mbl, M, N, Kp, C, ldc, S.err, 1, 0));
     return EWOS_OK;
 }
 
@@ -734,18 +758,18 @@ ewos_status tc_update_check(TcScratch* t, cudaStream_t st) {
 // C [M][N] = A^T B for K-major FP32 operands A [K][M], B [K][N].  With a caller scratch the
 // call is reentrant across workspaces; without one the per-device scratch is used under a lock.
 ewos_status tc_assemble(const float* Akm, const float* Bkm, float* C, int M, int N, int K, cudaStream_t st,
-                        bool split, TcScratch** owned) {
+                        bool split, TcScratch** owned, bool sym = false) {
     int dev = 0;
     EWOS_CUDA_TRY(cudaGetDevice(&dev));
     if (owned) {
         if (!*owned) *owned = new TcScratch();
-        ewos_status s = tc_enqueue((*owned)->s, Akm, Bkm, C, M, N, K, st, split);
+        ewos_status s = tc_enqueue((*owned)->s, Akm, Bkm, C, M, N, K, st, split, sym);
         if (s != EWOS_OK) return s;
         return tc_check((*owned)->s, st);
     }
     std::lock_guard<std::mutex> lock(tc::g_mu);
     tc::Scratch& S = tc::g_scratch[dev & 63];
-    ewos_status s = tc_enqueue(S, Akm, Bkm, C, M, N, K, st, split);
+    ewos_status s = tc_enqueue(S, Akm, Bkm, C, M, N, K, st, split, sym);
     if (s != EWOS_OK) return s;
     return tc_check(S, st);
 }
@@ -753,7 +777,8 @@ ewos_status tc_assemble(const float* Akm, const float* Bkm, float* C, int M, int
 }  // namespace ewos
 
 // Test hook (no counterpart in the paper): C [M][N] = A^T B with A [K][M], B [K][N] host FP32
-// arrays, through the tensor-core path used by the mixed-precision assembly.
+// arrays, through the tensor-core path used by the mixed-precision assembly; split = 2 takes the
+// symmetric launch (tiles on and below the diagonal, mirrored; for a symmetric A^T B).
 extern "C" ewos_status ewos_debug_tc_gemm(const float* A, const float* B, float* C, int M, int N, int K, int split) {
     using namespace ewos;
     if (!A || !B || !C || M < 1 || N < 1 || K < 1) { set_error("ewos_debug_tc_gemm: bad arguments"); return EWOS_EINVAL; }
@@ -765,7 +790,7 @@ extern "C" ewos_status ewos_debug_tc_gemm(const float* A, const float* B, float*
     EWOS_CUDA_TRY(dev_alloc((void**)&dC, sizeof(float) * (size_t)M * N));
     cudaMemcpy(dA, A, sizeof(float) * (size_t)K * M, cudaMemcpyHostToDevice);
     cudaMemcpy(dB, B, sizeof(float) * (size_t)K * N, cudaMemcpyHostToDevice);
-    ewos_status s = tc_assemble(dA, dB, dC, M, N, K, nullptr, split != 0, nullptr);
+    ewos_status s = tc_assemble(dA, dB, dC, M, N, K, nullptr, split != 0, nullptr, split == 2);
     if (s == EWOS_OK && cudaMemcpy(C, dC, sizeof(float) * (size_t)M * N, cudaMemcpyDeviceToHost) != cudaSuccess) s = EWOS_ECUDA;
     dev_free(dA); dev_free(dB); dev_free(dC);
     cudaDeviceSynchronize();

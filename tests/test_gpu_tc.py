@@ -37,3 +37,23 @@ def test_tc_gemm_split_tf32(M, N, K):
     ref = A.astype(np.float64).T @ B.astype(np.float64)
     bound = (2.0 ** -19 + K * 2.0 ** -23) * (np.abs(A).astype(np.float64).T @ np.abs(B).astype(np.float64))
     assert np.all(np.abs(C - ref) <= bound + 1e-30)
+
+
+@pytest.mark.parametrize("M,K", [(128, 64), (300, 1000), (520, 96), (7, 5)])
+def test_tc_gemm_symmetric_launch(M, K):
+    """The symmetric launch of the assembly (A^T A, or A^T D A): only tiles on and below the
+    diagonal are computed and each off-diagonal one is also stored transposed; the result equals
+    the full 3xTF32 product within its bound, and the mirrored tiles are exact transposes (inside
+    a diagonal tile the two halves come from different MMA lanes and round differently)."""
+    rng = np.random.default_rng(M + K)
+    A = rng.normal(size=(K, M)).astype(np.float32)
+    d = rng.uniform(0.5, 2.0, size=(K, 1)).astype(np.float32)
+    B = (d * A).astype(np.float32)
+    C = ewos.debug_tc_gemm(A, B, sym=True).astype(np.float64)
+    ref = A.astype(np.float64).T @ B.astype(np.float64)
+    bound = (2.0 ** -19 + K * 2.0 ** -23) * (np.abs(A).astype(np.float64).T @ np.abs(B).astype(np.float64))
+    assert np.all(np.abs(C - ref) <= bound + 1e-30)
+    ti = np.arange(M)[:, None] // 128
+    tj = np.arange(M)[None, :] // 128
+    off = ti != tj
+    assert np.array_equal(C[off], C.T[off])
