@@ -268,7 +268,8 @@ typedef struct {
     /* device time (CUDA events on the solve's stream) of the mixed mode's tensor-core
      * assembly products (Lambda = P^T Q and the Newton Jacobian products G^T diag G) and of
      * its FP32 LU factorisations, with the method's floating-point operations of those
-     * products (2 m^2 K each, the three TF32 split products counted once); 0 in FP64 mode */
+     * products (2 m^2 K each, m (m + 1) K for a symmetric one, which is computed as its lower
+     * triangle; the three TF32 split products counted once); 0 in FP64 mode */
     double dev_ms_gemm;
     double gemm_flop;
     double dev_ms_lu;
@@ -392,6 +393,17 @@ ewos_status ewos_debug_green_radius(const void* u, void* R, int64_t count, int p
  * computed, each also stored transposed: for a symmetric A^T B, M = N).  EWOS_EINVAL when the
  * device has no sm_100-family tensor cores. */
 ewos_status ewos_debug_tc_gemm(const float* A, const float* B, float* C, int M, int N, int K, int split);
+
+/* Test hooks for the failure paths (no counterpart in the paper).
+ * ewos_debug_set_flow_wait_limit: the flag waits of the dataflow triangular solves (mixed mode)
+ * give up after `polls` polls on the current device (polls < 0 restores the default, 2^22);
+ * a solve whose waits run out returns EWOS_ETIMEOUT and the device stays usable.  The waits
+ * poll plain flags in global memory: no copy is in flight when they give up.
+ * ewos_debug_fail_allocations: the device allocation of the library that follows `after` more
+ * successful ones fails once, as if the device were out of memory (the entry point returns
+ * EWOS_ENOMEM); after < 0 cancels. */
+ewos_status ewos_debug_set_flow_wait_limit(int64_t polls);
+void ewos_debug_fail_allocations(int64_t after);
 
 /* Number of kernels this library has launched in the process so far (all entry points). */
 unsigned long long ewos_launch_count(void);

@@ -27,7 +27,16 @@ uint64_t next_toolbox_serial() { return g_toolbox_serial.fetch_add(1, std::memor
 static thread_local cudaStream_t g_alloc_stream = nullptr;
 void set_alloc_stream(cudaStream_t s) { g_alloc_stream = s; }
 
+// test hook: the allocation after this many more successful ones fails once (-1: never)
+static std::atomic<long long> g_fail_alloc_after{-1};
+
 cudaError_t dev_alloc(void** p, size_t bytes) {
+    for (long long v = g_fail_alloc_after.load(); v >= 0;) {
+        if (g_fail_alloc_after.compare_exchange_weak(v, v - 1)) {
+            if (v == 0) { *p = nullptr; return cudaErrorMemoryAllocation; }
+            break;
+        }
+    }
     constexpr int kMaxDevices = 64;
     static std::atomic<int> pool_ready[kMaxDevices];
     int dev = 0;
@@ -546,3 +555,7 @@ ewos_status ewos_debug_green_radius(const void* u, void* R, int64_t count, int p
 }
 
 }  // extern "C"
+
+extern "C" void ewos_debug_fail_allocations(int64_t after) {
+    ewos::g_fail_alloc_after.store(after < 0 ? -1 : (long long)after);
+}

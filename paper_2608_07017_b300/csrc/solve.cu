@@ -1505,6 +1505,8 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
 // state: [0] ticket counter, [1] error word, [2, 2 + nbk) forward flags, [2 + nbk, 2 + 2 nbk)
 // backward flags; zeroed before each launch.
 constexpr long long kFlowSpinLimit = 1ll << 22;
+// the limit the kernels use (a test hook lowers it to make the waits run out)
+__device__ long long g_flow_spin_limit = kFlowSpinLimit;
 
 __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
     unsigned int v;
@@ -1521,9 +1523,10 @@ __device__ __forceinline__ bool flow_wait(const unsigned int* flag, unsigned int
     if (threadIdx.x == 0) {
         int ok = 1;
         long long spins = 0;
+        const long long limit = g_flow_spin_limit;
         while (ld_acquire_u32(flag) == 0) {
             if ((++spins & 63) == 0 && ld_acquire_u32(err) != 0) { ok = 0; break; }   // another CTA gave up
-            if (spins > kFlowSpinLimit) { atomicExch(err, 1u); ok = 0; break; }
+            if (spins > limit) { atomicExch(err, 1u); ok = 0; break; }
         }
         *s_ok = ok;
     }
@@ -1660,9 +1663,10 @@ __global__ void __launch_bounds__(256) trsm_flow_vec_kernel(const T* __restrict_
             int ok = 1, cnt = 0;
             const unsigned int* f0 = mine + j0;
             long long spins = 0;
+            const long long limit = g_flow_spin_limit;
             while (ld_acquire_u32(f0) == 0) {
                 if ((++spins & 63) == 0 && ld_acquire_u32(err) != 0) { ok = 0; break; }
-                if (spins > kFlowSpinLimit) { atomicExch(err, 1u); ok = 0; break; }
+                if (spins > limit) { atomicExch(err, 1u); ok = 0; break; }
             }
             if (ok) {
                 cnt = 1;
@@ -1837,9 +1841,16 @@ static ewos_status ensure_workspace(const ewos_toolbox* tb, SolveWorkspace*& slo
     }
     const int D = tb->dim, E = D + 1;
     const int64_t n = tb->n, m = tb->m, p = tb->p;
+    // a failed allocation leaves no half-built workspace behind: the next call starts afresh
+    struct Undo {
+        SolveWorkspace*& slot;
+        bool armed = true;
+        ~Undo() { if (armed && slot) { free_workspace(slot); slot = nullptr; } }
+    };
     if (!slot) {
         SolveWorkspace* ws = new SolveWorkspace();
         slot = ws;
+        Undo undo{slot};
         ws->D = D; ws->n = n; ws->m = m; ws->p = p; ws->cap_rhs = nrhs;
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->M, sizeof(double) * n * E * E));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->A, sizeof(double) * n * D * D));
@@ -1873,21 +1884,26 @@ static ewos_status ensure_workspace(const ewos_toolbox* tb, SolveWorkspace*& slo
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.dinv, sizeof(double) * ((m + 63) / 64) * 2 * 64 * 64));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.diagb, sizeof(double) * ((m + 63) / 64) * 64 * 64));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.flow, sizeof(unsigned int) * flow_state_words(m)));
+        undo.armed = false;
     }
     SolveWorkspace* ws = slot;
     if (!matrices) return EWOS_OK;            // the vectors suffice (gradient, Adam)
     if (!mixed && !ws->Q) {
-        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Q, sizeof(double) * E * n * m));
+        Undo undo{slot};
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Lam, sizeof(double) * m * m));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->LUm, sizeof(double) * m * m));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Jx, sizeof(double) * n * m));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Q, sizeof(double) * E * n * m));     // last: marks the set complete
+        undo.armed = false;
     }
     if (mixed && !ws->Q32) {
-        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Q32, sizeof(float) * E * n * m));
+        Undo undo{slot};
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->L32, sizeof(float) * m * m));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->LU32, sizeof(float) * m * m));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Jx32, sizeof(float) * n * m));
         if (tb->precision == 64) EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->P32, sizeof(float) * E * n * m));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Q32, sizeof(float) * E * n * m));   // last: marks the set complete
+        undo.armed = false;
     }
     return EWOS_OK;
 }
@@ -2651,9 +2667,17 @@ static ewos_status ensure_batched(const Ctx& C, int64_t rc) {
     if (ws->bcap >= rc && ws->Sb) return EWOS_OK;
     for (auto& g : ws->graphs) cudaGraphExecDestroy(g.exec);
     ws->graphs.clear();
-    ::ewos::dev_free(ws->Sb); ::ewos::dev_free(ws->Yb); ::ewos::dev_free(ws->Vb); ::ewos::dev_free(ws->Wb);
-    ::ewos::dev_free(ws->Fb); ::ewos::dev_free(ws->Gb); ::ewos::dev_free(ws->Ub); ::ewos::dev_free(ws->nrm);
-    ::ewos::dev_free(ws->D32); ::ewos::dev_free(ws->D32p); ::ewos::dev_free(ws->F2buf);
+    // every buffer of the set is freed and cleared first, and the capacity is set only once all
+    // of them exist: a failed allocation leaves an empty set that the next call rebuilds
+    ws->bcap = 0;
+    for (double** b : {&ws->Sb, &ws->Yb, &ws->Vb, &ws->Wb, &ws->Fb, &ws->Gb, &ws->Ub, &ws->nrm}) {
+        ::ewos::dev_free(*b);
+        *b = nullptr;
+    }
+    for (float** b : {&ws->D32, &ws->D32p, &ws->F2buf}) {
+        ::ewos::dev_free(*b);
+        *b = nullptr;
+    }
     const int64_t rows = (int64_t)C.E * C.n;
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->F2buf, sizeof(float) * 2 * (C.m + C.p + rows) * rc));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->Sb, sizeof(double) * C.m * rc));
@@ -3008,7 +3032,9 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
         if (!keep) {
             if (tc_assemble_available()) {
                 DevSpan span(C.st, &rep->dev_ms_gemm);
-                rep->gemm_flop += 2.0 * (double)C.m * (double)C.m * (double)(C.E * C.n);
+                // a symmetric system is computed as its lower triangle: m (m + 1) K
+                rep->gemm_flop += (pb->b == nullptr ? (double)C.m * (double)(C.m + 1) : 2.0 * (double)C.m * (double)C.m) *
+                                  (double)(C.E * C.n);
                 ewos_status st = tc_assemble_pq(P32, ws->M, (int)C.n, (int)C.m, C.D, ws->L32, C.st, &ws->tc,
                                                     pb->b == nullptr);
                 if (st != EWOS_OK) return st;
@@ -3123,7 +3149,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                         [&] {
                             if (tcj) {
                                 DevSpan span(C.st, &rep->dev_ms_gemm);
-                                rep->gemm_flop += 2.0 * (double)C.m * (double)C.m * (double)C.n;
+                                rep->gemm_flop += (double)C.m * (double)(C.m + 1) * (double)C.n;   // symmetric: lower triangle
                                 ewos_status e = tc_assemble(Gm32, ws->Jx32, ws->LU32, (int)C.m, (int)C.m, (int)C.n, C.st,
                                                             kSplitTF32, &ws->tc, true);
                                 if (e != EWOS_OK) tst = e;
@@ -3171,7 +3197,9 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                 auto ta = std::chrono::steady_clock::now();
                 if (tc_assemble_available()) {
                     DevSpan span(C.st, &rep->dev_ms_gemm);
-                    rep->gemm_flop += 2.0 * (double)C.m * (double)C.m * (double)(C.E * C.n);
+                    // a symmetric system is computed as its lower triangle: m (m + 1) K
+                rep->gemm_flop += (pb->b == nullptr ? (double)C.m * (double)(C.m + 1) : 2.0 * (double)C.m * (double)C.m) *
+                                  (double)(C.E * C.n);
                     ewos_status st = tc_assemble_pq(P32, ws->M, (int)C.n, (int)C.m, C.D, ws->L32, C.st, &ws->tc,
                                                     pb->b == nullptr);
                     if (st != EWOS_OK) return st;
@@ -3607,4 +3635,14 @@ extern "C" ewos_status ewos_operators(ewos_toolbox* tb, const ewos_problem* pb, 
     if (rep && s == EWOS_OK) *rep = total;
     cleanup();
     return s;
+}
+
+// Test hook (no counterpart in the paper): the dataflow triangular solves' flag waits give up
+// after `polls` polls on the current device (polls < 0: the default, 2^22).
+extern "C" ewos_status ewos_debug_set_flow_wait_limit(int64_t polls) {
+    using namespace ewos;
+    const long long v = polls < 0 ? kFlowSpinLimit : (long long)polls;
+    EWOS_CUDA_TRY(cudaMemcpyToSymbol(g_flow_spin_limit, &v, sizeof(v)));
+    EWOS_CUDA_TRY(cudaDeviceSynchronize());
+    return EWOS_OK;
 }

@@ -137,6 +137,9 @@ def lib():
         L.ewos_debug_philox.argtypes = [P, P, P, I64]
         L.ewos_debug_green_radius.argtypes = [P, P, I64, I]
         L.ewos_debug_tc_gemm.argtypes = [P, P, P, I, I, I, I]
+        L.ewos_debug_set_flow_wait_limit.argtypes = [I64]
+        L.ewos_debug_fail_allocations.argtypes = [I64]
+        L.ewos_debug_fail_allocations.restype = None
         L.ewos_toolbox_build_batch.argtypes = [I, P, P, P, P, P, I64, ctypes.c_double, ctypes.c_uint64,
                                                ctypes.POINTER(BuildOpts), P, ctypes.POINTER(BuildReport)]
         L.ewos_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(P)]
@@ -431,6 +434,16 @@ def debug_tc_gemm(A, B, split=False, sym=False):
     _check(lib().ewos_debug_tc_gemm(a.ctypes.data, b.ctypes.data, c.ctypes.data, M, N, K,
                                     2 if sym else (1 if split else 0)), "tc gemm")
     return c
+
+
+def debug_set_flow_wait_limit(polls):
+    """Test hook: polls before the dataflow solves' flag waits give up (< 0: default)."""
+    _check(lib().ewos_debug_set_flow_wait_limit(int(polls)), "flow wait limit")
+
+
+def debug_fail_allocations(after):
+    """Test hook: the device allocation after `after` more successful ones fails (< 0: cancel)."""
+    lib().ewos_debug_fail_allocations(int(after))
 
 
 def debug_green_radius(u, precision=32):
