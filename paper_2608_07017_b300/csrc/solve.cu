@@ -1799,6 +1799,7 @@ struct SolveWorkspace {
     float *D32 = nullptr, *D32p = nullptr;
     float* F2buf = nullptr;          // hi/lo FP32 pairs of Sb [m][bcap], Gb [p][bcap], Wb [rows][bcap]
     double* Ypart = nullptr;         // per-CTA partials of the fused one-column residual [ypart_grid][m]
+    float* F2one = nullptr;          // FP32 toolboxes: hi/lo pairs of one column of s [m], g [p], w [rows]
     int ypart_grid = 0;
     struct Graph {
         uint64_t tb;     // serial of the toolbox whose buffers the graph reads
@@ -1827,7 +1828,7 @@ void free_workspace(SolveWorkspace* ws) {
     ::ewos::dev_free(ws->Sb); ::ewos::dev_free(ws->Yb); ::ewos::dev_free(ws->Vb); ::ewos::dev_free(ws->Wb);
     ::ewos::dev_free(ws->Fb); ::ewos::dev_free(ws->Gb); ::ewos::dev_free(ws->Ub); ::ewos::dev_free(ws->nrm);
     ::ewos::dev_free(ws->alpha_dev); ::ewos::dev_free(ws->D32); ::ewos::dev_free(ws->D32p); ::ewos::dev_free(ws->F2buf);
-    ::ewos::dev_free(ws->Ypart);
+    ::ewos::dev_free(ws->Ypart); ::ewos::dev_free(ws->F2one);
     for (auto& g : ws->graphs) cudaGraphExecDestroy(g.exec);
     if (ws->cap_st) cudaStreamDestroy(ws->cap_st);
     delete ws;
@@ -1884,6 +1885,8 @@ static ewos_status ensure_workspace(const ewos_toolbox* tb, SolveWorkspace*& slo
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.dinv, sizeof(double) * ((m + 63) / 64) * 2 * 64 * 64));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.diagb, sizeof(double) * ((m + 63) / 64) * 64 * 64));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.flow, sizeof(unsigned int) * flow_state_words(m)));
+        if (tb->precision == 32)
+            EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->F2one, sizeof(float) * 2 * (m + p + (int64_t)E * n)));
         undo.armed = false;
     }
     SolveWorkspace* ws = slot;
@@ -1930,6 +1933,41 @@ struct Ctx {
     int64_t n, m, p;
 };
 
+// FP32-pair products (defined with the batched solves below)
+static void multi_rowdot_f2(cudaStream_t st, const float* X, int64_t rows, int cols, const float* Vhi, const float* Vlo,
+                            double* Vout, int rc, int accumulate);
+static void multi_coltrans_f2(cudaStream_t st, const float* X, int64_t rows, int cols, const float* Whi, const float* Wlo,
+                              double* Y, int rc);
+static void split_f2(cudaStream_t st, const double* v, float* hi, float* lo, int64_t count);
+
+// FP32 toolboxes: v = P s (+ KH g) and y = P^T w with FP64-accurate products on the FP32 pipes:
+// s, g, w split into unevaluated FP32 pairs, products summed in FP32 pairs (two-sum), reduced in
+// FP64 (the same arithmetic as the batched solves' residual; about 1e-14 relative)
+static void apply_v_f2(const Ctx& C, const double* s, const double* g) {
+    float* sh = C.ws->F2one;
+    float* sl = sh + C.m;
+    float* gh = sl + C.m;
+    float* gl = gh + C.p;
+    const int64_t rows = (int64_t)C.E * C.n;
+    if (s) {
+        split_f2(C.st, s, sh, sl, C.m);
+        multi_rowdot_f2(C.st, (const float*)C.tb->P, rows, (int)C.m, sh, sl, C.ws->v, 1, 0);
+    }
+    if (g) {
+        split_f2(C.st, g, gh, gl, C.p);
+        multi_rowdot_f2(C.st, (const float*)C.tb->KH, rows, (int)C.p, gh, gl, C.ws->v, 1, s ? 1 : 0);
+    }
+}
+
+static void apply_PT_f2(const Ctx& C, const double* w, double* y) {
+    float* wh = C.ws->F2one + 2 * (C.m + C.p);
+    float* wl = wh + (int64_t)C.E * C.n;
+    const int64_t rows = (int64_t)C.E * C.n;
+    split_f2(C.st, w, wh, wl, rows);
+    cudaMemsetAsync(y, 0, sizeof(double) * C.m, C.st);
+    multi_coltrans_f2(C.st, (const float*)C.tb->P, rows, (int)C.m, wh, wl, y, 1);
+}
+
 template <typename TP>
 static void apply_v(const Ctx& C, const double* s, const double* g) {
     // v = P s + KH g  ([(D+1)][n]); s may be NULL (= 0)
@@ -1959,10 +1997,13 @@ static void apply_PT(const Ctx& C, const double* w, double* y) {
 template <typename TP>
 static void residual(const Ctx& C, const double* s, const double* g, const double* f, const double* nl, int nnl,
                      double alpha, double* y) {
-    apply_v<TP>(C, s, g);
+    const bool f2 = sizeof(TP) == 4 && C.ws->F2one && g;
+    if (f2) apply_v_f2(C, s, g);
+    else apply_v<TP>(C, s, g);
     ::ewos::note_launch(), formw_kernel<<<(int)((C.n + 127) / 128), 128, 0, C.st>>>((int)C.n, C.D, C.ws->M, C.ws->v, C.tb->lambda, f, nl, nnl,
                                                              C.ws->w);
-    apply_PT<TP>(C, C.ws->w, y);
+    if (f2) apply_PT_f2(C, C.ws->w, y);
+    else apply_PT<TP>(C, C.ws->w, y);
     if (alpha != 0.0 && s) ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, alpha, s, y);
 }
 
@@ -2252,11 +2293,14 @@ static void apply_op(const Ctx& C, const double* x, double alpha, const double* 
                      double* y) {
     const TP* P = (const TP*)C.tb->P;
     const int64_t rows = (int64_t)C.E * C.n;
-    ::ewos::note_launch(), rowdot_kernel<TP><<<(int)((rows * 32 + 255) / 256), 256, 0, C.st>>>(P, rows, (int)C.m, x, C.ws->v, 0);
+    const bool f2 = sizeof(TP) == 4 && C.ws->F2one;
+    if (f2) apply_v_f2(C, x, nullptr);
+    else ::ewos::note_launch(), rowdot_kernel<TP><<<(int)((rows * 32 + 255) / 256), 256, 0, C.st>>>(P, rows, (int)C.m, x, C.ws->v, 0);
     ::ewos::note_launch(), formw_jv_kernel<<<(int)((C.n + 127) / 128), 128, 0, C.st>>>((int)C.n, C.D, C.ws->M, C.ws->v,
                                                                                       C.tb->lambda, u, u ? nl : nullptr,
                                                                                       u ? nnl : 0, C.ws->w);
-    apply_PT<TP>(C, C.ws->w, y);
+    if (f2) apply_PT_f2(C, C.ws->w, y);
+    else apply_PT<TP>(C, C.ws->w, y);
     if (alpha != 0.0) ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, alpha, x, y);
 }
 

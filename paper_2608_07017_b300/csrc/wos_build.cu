@@ -363,6 +363,90 @@ __global__ void exclusive_scan_kernel(const int* __restrict__ count, int64_t len
     if (threadIdx.x == 0) start[len] = carry;
 }
 
+// Exclusive scan over many blocks: per-block sums of `chunk` entries, one block scans the sums,
+// then every block scans its chunk from its offset (fine lookup grids have millions of cells,
+// which the single-block scan above walks through sequentially).
+constexpr int kScanChunk = 4096;      // 1024 threads x 4 entries
+
+__global__ void __launch_bounds__(1024) block_sums_kernel(const int* __restrict__ count, int64_t len,
+                                                          int* __restrict__ sums) {
+    __shared__ int ws[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk;
+    int v = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t i = base + threadIdx.x * 4 + q;
+        if (i < len) v += count[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int t = ws[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) sums[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) block_scan_kernel(const int* __restrict__ count, int64_t len,
+                                                          const int* __restrict__ offs, int* __restrict__ start) {
+    __shared__ int ws[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + threadIdx.x * 4;
+    int v[4];
+    int tsum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        v[q] = base + q < len ? count[base + q] : 0;
+        tsum += v[q];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int t = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        ws[lane] = t;
+    }
+    __syncthreads();
+    int run = offs[blockIdx.x] + (wid > 0 ? ws[wid - 1] : 0) + incl - tsum;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (base + q < len) start[base + q] = run;
+        run += v[q];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) start[len] = offs[gridDim.x];
+}
+
+// start[0..len] = exclusive scan of count[0..len) (start[len] = total) on the stream
+static ewos_status exclusive_scan(const int* count, int64_t len, int* start, cudaStream_t st) {
+    const int64_t nb = (len + kScanChunk - 1) / kScanChunk;
+    if (nb <= 1) {
+        ::ewos::note_launch(), exclusive_scan_kernel<<<1, 1024, 0, st>>>(count, len, start);
+        return EWOS_OK;
+    }
+    int* sums = nullptr;
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&sums, sizeof(int) * (2 * nb + 1)));
+    int* offs = sums + nb;
+    ::ewos::note_launch(), block_sums_kernel<<<(unsigned)nb, 1024, 0, st>>>(count, len, sums);
+    ::ewos::note_launch(), exclusive_scan_kernel<<<1, 1024, 0, st>>>(sums, nb, offs);
+    ::ewos::note_launch(), block_scan_kernel<<<(unsigned)nb, 1024, 0, st>>>(count, len, offs, start);
+    ::ewos::dev_free(sums);
+    EWOS_CUDA_TRY(cudaGetLastError());
+    return EWOS_OK;
+}
+
 template <typename T, int D>
 __global__ void convert_points_kernel(const double* __restrict__ in, T* __restrict__ out, int64_t count) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -448,7 +532,7 @@ static ewos_status build_lookup(int dim, const double* d_pts, int np, const doub
     const int nb = (int)((nc * 32 + tb - 1) / tb);
     if (dim == 2) ::ewos::note_launch(), lookup_count_kernel<2><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, d_count, d_rad, d_count + nc, d_best);
     else ::ewos::note_launch(), lookup_count_kernel<3><<<nb, tb, 0, st>>>(d_pf, np, out.grid, slack, d_count, d_rad, d_count + nc, d_best);
-    ::ewos::note_launch(), exclusive_scan_kernel<<<1, 1024, 0, st>>>(d_count, nc, out.start);
+    if (ewos_status ss = exclusive_scan(d_count, nc, out.start, st); ss != EWOS_OK) return ss;
     int hv[2] = {0, 0};
     EWOS_CUDA_TRY(cudaMemcpyAsync(&hv[0], out.start + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
     EWOS_CUDA_TRY(cudaMemcpyAsync(&hv[1], d_count + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -515,7 +599,7 @@ static ewos_status build_lookup_refined(int dim, const double* d_pts, int np, co
         ::ewos::note_launch(), lookup_refine_kernel<3><<<nb, tb, 0, st>>>(pf, np, coarse.grid, out.grid, slack, coarse.start,
                                                                         coarse.cand, d_count, d_count + nc, nullptr,
                                                                         nullptr, 0, nullptr);
-    ::ewos::note_launch(), exclusive_scan_kernel<<<1, 1024, 0, st>>>(d_count, nc, out.start);
+    if (ewos_status ss = exclusive_scan(d_count, nc, out.start, st); ss != EWOS_OK) return ss;
     int hv[2] = {0, 0};
     EWOS_CUDA_TRY(cudaMemcpyAsync(&hv[0], out.start + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
     EWOS_CUDA_TRY(cudaMemcpyAsync(&hv[1], d_count + nc, sizeof(int), cudaMemcpyDeviceToHost, st));
