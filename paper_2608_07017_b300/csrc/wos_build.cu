@@ -1240,7 +1240,10 @@ __device__ __forceinline__ int stream_bin(const WalkArgs<T, D>& a, StreamState& 
                                           uint32_t* accH) {
     const uint32_t meta = q.M[e], l = q.L[e];
     const int slot = (int)(meta & 7u);
-    const bool sm = (meta >> 3) & 1u;
+    // the row's contributions go where its accumulators are now: the shared ones while the row
+    // owns them (it keeps them until all its walks are binned), else the output in global memory
+    const bool sm = *(volatile int*)&S.smem_slot == (int)(meta & 7u);
+    if (!sm) S.global_part[meta & 7u] = 1;
     const int R = S.row[slot];
     T X[D], U[D], xi[D];
 #pragma unroll
@@ -1326,8 +1329,7 @@ __device__ __forceinline__ void stream_flush(const WalkArgs<T, D>& a, StreamStat
         if (lane == 0) {
             // the accumulators go to the row taking walks, if it still has walks to hand out
             const int f = (*(volatile int*)&S.fetch_seq) % kSlots;
-            const int nxt = (f != slot && *(volatile int*)&S.row[f] >= 0 && *(volatile unsigned*)&S.next[f] < (unsigned)a.N)
-                                ? f : -1;
+            const int nxt = (f != slot && *(volatile int*)&S.row[f] >= 0) ? f : -1;
             atomicExch(&S.smem_slot, nxt);
         }
     } else {
@@ -1420,8 +1422,7 @@ __device__ __forceinline__ void walk_stream(const WalkArgs<T, D>& a) {
         if (stream_acquire(S, a, slot, l)) {
             have = true;
             R = S.row[slot];
-            sm = *(volatile int*)&S.smem_slot == slot;
-            if (!sm) S.global_part[slot] = 1;
+            sm = false;
 #pragma unroll
             for (int c = 0; c < D; ++c) X[c] = a.x[(size_t)R * D + c];
             r0 = a.r0[R];
@@ -1477,6 +1478,8 @@ __device__ __forceinline__ void walk_stream(const WalkArgs<T, D>& a) {
 #pragma unroll
                 for (int c = 0; c < D; ++c) U0[c] = U[c];
             }
+            sm = *(volatile int*)&S.smem_slot == slot;
+            if (!sm) S.global_part[slot] = 1;
             if (sm) {
                 atomicAdd(&acc[(size_t)D * a.m + j], r2);
                 if (k > 0) {
