@@ -18,6 +18,7 @@
 #include <cstdint>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "pdl.cuh"
 #include "tf32.cuh"
@@ -116,7 +117,8 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
                                                            const __grid_constant__ CUtensorMap mapAl,
                                                            const __grid_constant__ CUtensorMap mapBl, int M, int N,
                                                            int Kp, float* __restrict__ C, int64_t ldc,
-                                                           int* __restrict__ err, int sub, int tri = 0) {
+                                                           int* __restrict__ err, int sub, int tri = 0,
+                                                           const int* __restrict__ tiles = nullptr) {
     using CF = Cfg<SPLIT, ST>;
     constexpr int BN = CF::BN, STAGES = CF::STAGES, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
     constexpr int STAGE_BYTES = CF::STAGE_BYTES;
@@ -132,7 +134,11 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
     // tri: a symmetric result; the 1D grid runs over the tiles on and below the diagonal (ty >= tx)
     // and each off-diagonal tile is also stored transposed
     int tile_y = blockIdx.y, tile_x = blockIdx.x;
-    if (tri) {
+    if (tiles) {
+        // blocked order (CTAs that run together share row and column panels in L2)
+        tile_y = tiles[2 * blockIdx.x];
+        tile_x = tiles[2 * blockIdx.x + 1];
+    } else if (tri) {
         const int t = blockIdx.x;
         int ty = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
         while ((ty + 1) * (ty + 2) / 2 <= t) ++ty;
@@ -439,8 +445,41 @@ struct Scratch {
     float* Btl = nullptr;
     int* err = nullptr;
     size_t cap = 0;
+    int* tiles = nullptr;          // (tile row, tile column) per CTA, blocked order
+    long long tiles_key = -1;      // shape the table was made for
+    int tiles_count = 0;
 };
 static Scratch g_scratch[64];
+
+// Output tiles in blocks of kTileBlock x kTileBlock (about one wave of one-CTA-per-SM tiles), block
+// rows in order: the CTAs that run together read kTileBlock row panels and kTileBlock column
+// panels, which L2 then serves to the other CTAs of the block.  tri: only tiles with tx <= ty.
+constexpr int kTileBlock = 12;
+static ewos_status tile_table(Scratch& S, int mt, int nt, bool tri, cudaStream_t st, int* count) {
+    const long long key = ((long long)mt << 32) ^ ((long long)nt << 1) ^ (tri ? 1 : 0);
+    if (S.tiles && S.tiles_key == key) { *count = S.tiles_count; return EWOS_OK; }
+    std::vector<int> t;
+    for (int by = 0; by < mt; by += kTileBlock)
+        for (int bx = 0; bx < nt; bx += kTileBlock) {
+            if (tri && bx > by) break;
+            for (int ty = by; ty < std::min(mt, by + kTileBlock); ++ty)
+                for (int tx = bx; tx < std::min(nt, bx + kTileBlock); ++tx) {
+                    if (tri && tx > ty) break;
+                    t.push_back(ty);
+                    t.push_back(tx);
+                }
+        }
+    ::ewos::dev_free(S.tiles);
+    S.tiles = nullptr;
+    S.tiles_key = -1;
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.tiles, sizeof(int) * t.size()));
+    EWOS_CUDA_TRY(cudaMemcpyAsync(S.tiles, t.data(), sizeof(int) * t.size(), cudaMemcpyHostToDevice, st));
+    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    S.tiles_key = key;
+    S.tiles_count = (int)(t.size() / 2);
+    *count = S.tiles_count;
+    return EWOS_OK;
+}
 static std::mutex g_mu;
 
 }  // namespace tc
@@ -468,7 +507,7 @@ struct TcScratch {
 void tc_scratch_free(TcScratch* t) {
     if (!t) return;
     ::ewos::dev_free(t->s.At); ::ewos::dev_free(t->s.Bt); ::ewos::dev_free(t->s.Atl); ::ewos::dev_free(t->s.Btl);
-    ::ewos::dev_free(t->s.err);
+    ::ewos::dev_free(t->s.err); ::ewos::dev_free(t->s.tiles);
     delete t;
 }
 
@@ -513,11 +552,12 @@ static ewos_status tc_enqueue(tc::Scratch& S, const float* Akm, const float* Bkm
     dim3 grid((N + bn - 1) / bn, (M + BM - 1) / BM);
     if (split) {
         const bool tri = sym && M == N;
-        const int nt = (M + BM - 1) / BM;
-        if (tri) grid = dim3((unsigned)(nt * (nt + 1) / 2));
+        int ntiles = 0;
+        if (ewos_status ts = tile_table(S, (M + BM - 1) / BM, (N + bn - 1) / bn, tri, st, &ntiles); ts != EWOS_OK)
+            return ts;
         EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<true>::SMEM_BYTES));
-        ::ewos::note_launch(), gemm_tf32_kernel<true><<<grid, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err, 0,
-                                                                                            tri ? 1 : 0);
+        ::ewos::note_launch(), gemm_tf32_kernel<true><<<ntiles, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err,
+                                                                                              0, tri ? 1 : 0, S.tiles);
     } else {
         EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<false>::SMEM_BYTES));
         ::ewos::note_launch(), gemm_tf32_kernel<false><<<grid, 128, Cfg<false>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err, 0);
@@ -632,9 +672,11 @@ ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D
     EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<true>::SMEM_BYTES));
     const int nt = (m + BM - 1) / BM;
     static_assert(Cfg<true>::BN == BM, "square tiles for the symmetric launch");
-    const dim3 g2 = sym ? dim3((unsigned)(nt * (nt + 1) / 2)) : dim3((m + Cfg<true>::BN - 1) / Cfg<true>::BN, nt);
-    ::ewos::note_launch(), gemm_tf32_kernel<true><<<g2, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, m, m, Kp, C, m, S.err, 0,
-                                                                                       sym ? 1 : 0);
+    int ntiles = 0;
+    if (ewos_status ts = tile_table(S, nt, (m + Cfg<true>::BN - 1) / Cfg<true>::BN, sym, st, &ntiles); ts != EWOS_OK)
+        return ts;
+    ::ewos::note_launch(), gemm_tf32_kernel<true><<<ntiles, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, m, m, Kp, C, m, S.err,
+                                                                                           0, sym ? 1 : 0, S.tiles);
     EWOS_CUDA_TRY(cudaGetLastError());
     return tc_check(S, st);
 }
@@ -735,10 +777,10 @@ ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64
     ::ewos::note_launch();
     if (csm)
         EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true, kUpd, true>, grid, dim3(128), kCsmSmem, st, ma, mb, mal, mbl,
-                                         M, N, Kp, C, ldc, S.err, 1, 0));
+                                         M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr));
     else
         EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true>, grid, dim3(128), (size_t)Cfg<true>::SMEM_BYTES, st, ma, mb,
-                                         mal, mbl, M, N, Kp, C, ldc, S.err, 1, 0));
+                                         mal, mbl, M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr));
     return EWOS_OK;
 }
 
