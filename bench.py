@@ -129,7 +129,7 @@ def _dist():
 
 
 # ------------------------------------------------------------------ rooflines
-def walk_roofline(workload, steps_per_launch, ms_walk, nsm, peaks, peak_src):
+def walk_roofline(workload, steps_per_launch, ms_walk, nsm, peaks, peak_src, grid_scale=None):
     """Walk-kernel roofline of the survey's measurement section: the kernel is bound by the
     FP32/SFU pipes and instruction issue, so its fraction is max(fma-pipe, xu-pipe) utilisation.
     The instructions per WoS step on each pipe come from the ncu counters committed in
@@ -143,13 +143,14 @@ def walk_roofline(workload, steps_per_launch, ms_walk, nsm, peaks, peak_src):
             table = json.load(fh)
     except OSError:
         table = {}
-    e = table.get(workload)
+    key = f"{workload}@{grid_scale:g}" if grid_scale is not None else workload
+    e = table.get(key)
     clock = peaks.get("sm_max_mhz", 2032.0) * 1e6
     out = {"bound": "alu", "unit": "fraction of pipe peak", "kernel_ms": ms_walk, "source_sha16": sha,
            "peak_clock_mhz": clock / 1e6, "peak_src": peak_src}
     if not e or e.get("source_sha16") != sha:
         out.update({"achieved": None, "peak": None, "frac": None, "traffic": None,
-                    "note": f"no ncu counters for this kernel source ({sha}) in profiles/walk_counters.json"})
+                    "note": f"no ncu counters for {key} with this kernel source ({sha}) in profiles/walk_counters.json"})
         return out
     t = ms_walk / 1000.0
     rates = {}
@@ -488,7 +489,7 @@ def summarize(name, res, workload, peaks, peak_src, nsm, dtype):
            "walk_config": {k: res["builds"][-1][k] for k in ("threads_per_block", "ctas_per_sm", "grid", "hash_in_smem",
                                                              "lookup_grid_scale", "lookup_candidates", "smem_bytes")},
            "gpu_launches": res["launches"]}
-    rl = {"walk": walk_roofline(name, steps, wk, nsm, peaks, peak_src)}
+    rl = {"walk": walk_roofline(name, steps, wk, nsm, peaks, peak_src, res["builds"][-1]["lookup_grid_scale"])}
     g_ms = statistics.median(r["dev_ms_gemm"] for r in solves)
     if g_ms > 0:
         rl["assembly_gemm"] = tensor_roofline("assembly (tcgen05 TF32, 3 split products)",
