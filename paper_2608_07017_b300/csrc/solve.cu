@@ -2253,12 +2253,18 @@ __global__ void add_shifted_kernel(float* __restrict__ LU, const float* __restri
 template <typename TP>
 __global__ void jac_scale32_kernel(const TP* __restrict__ Gm, const double* __restrict__ u, const double* __restrict__ lam,
                                    const double* __restrict__ nl, int nnl, float* __restrict__ out, int n, int m) {
+    // the row's factor lam_i N'(u_i) once per block in FP64, the scaling on the FP32 pipes (the
+    // factors only precondition the FP64-refined Newton systems)
+    __shared__ float s_scale;
     const int i = blockIdx.y;
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= m) return;
-    double d = 0.0, pw = 1.0;
-    for (int t = 1; t < nnl; ++t) { d += t * nl[t] * pw; pw *= u[i]; }
-    out[(size_t)i * m + col] = (float)(lam[i] * d * (double)Gm[(size_t)i * m + col]);
+    if (threadIdx.x == 0) {
+        double d = 0.0, pw = 1.0;
+        for (int t = 1; t < nnl; ++t) { d += t * nl[t] * pw; pw *= u[i]; }
+        s_scale = (float)(lam[i] * d);
+    }
+    __syncthreads();
+    if (col < m) out[(size_t)i * m + col] = s_scale * (float)Gm[(size_t)i * m + col];
 }
 
 static double frob32(const Ctx& C, const float* X, int64_t count) {
