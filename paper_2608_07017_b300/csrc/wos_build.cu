@@ -814,11 +814,13 @@ __device__ __forceinline__ int nearest_fixed(const Lookup<T, D>& L, const uint16
 
 constexpr int kQueue = 64;   // per-warp queue of stopped walks awaiting their boundary binning
 
+// A stopped walk's first direction U_0 is not queued: the binning draws it again from the
+// walk's step-0 counter (one Philox block), which leaves more of the SM's unified L1 / shared
+// memory to the L1 (the ball's queue shrinks from 48 to 32 KB).
 template <typename T, int D>
 struct WalkQueue {
     T* X;          // [warps][kQueue][D] stopping point
-    T* U;          // [warps][kQueue][D] first direction U_0
-    uint32_t* L;   // [warps][kQueue] walk index      (records only)
+    uint32_t* L;   // [warps][kQueue] walk index
     uint32_t* vh;  // [warps][kQueue] binning digest  (records only)
     uint32_t* K;   // [warps][kQueue] steps           (records only)
     T* mass;       // [warps][kQueue] G mass          (records only)
@@ -827,7 +829,20 @@ struct WalkQueue {
 // bytes of the per-warp queues in shared memory
 template <typename T, int D>
 __host__ __device__ constexpr size_t queue_bytes(int nwarps, bool record) {
-    return (size_t)nwarps * kQueue * (2 * D * sizeof(T) + (record ? 3 * sizeof(uint32_t) + sizeof(T) : 0));
+    return (size_t)nwarps * kQueue * (D * sizeof(T) + sizeof(uint32_t) + (record ? 2 * sizeof(uint32_t) + sizeof(T) : 0));
+}
+
+// U_0 of walk l of a row, as draw_step draws it at step 0
+template <typename T, int D>
+__device__ __forceinline__ void draw_first_direction(uint32_t l, uint32_t row, uint32_t inst, uint32_t k0, uint32_t k1,
+                                                     T* U) {
+    if (D == 2) {
+        const u32x4 q = philox4x32_10(u32x4{l, 0u, row, inst | 0u}, k0, k1);
+        dir2<T>(u01<T>(q.c), U);
+    } else {
+        const u32x4 v = philox4x32_10(u32x4{l, 0u, row, inst | 1u}, k0, k1);
+        dir3<T>(u01<T>(v.b), u01<T>(v.c), U);
+    }
 }
 
 template <typename T, int D, bool RECORD>
@@ -835,7 +850,8 @@ __device__ __forceinline__ void bin_stopped(const WalkArgs<T, D>& a, const WalkQ
                                             T* accKH, uint32_t* accH) {
     T X[D], U[D];
 #pragma unroll
-    for (int c = 0; c < D; ++c) { X[c] = q.X[slot * D + c]; U[c] = q.U[slot * D + c]; }
+    for (int c = 0; c < D; ++c) X[c] = q.X[slot * D + c];
+    draw_first_direction<T, D>(q.L[slot], (uint32_t)row, a.inst, a.k0, a.k1, U);
     const int jz = nearest_or_scan(a.Z, a.p, X);
     atomicAdd(&accH[jz], 1u);
 #pragma unroll
@@ -894,10 +910,9 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WalkQueue<T, D> q;
     q.X = s_sdf + ((a.sdf_len + 3) & ~3);
-    q.U = q.X + (size_t)nwarps * kQueue * D;
-    q.L = reinterpret_cast<uint32_t*>(q.U + (size_t)nwarps * kQueue * D);
+    q.L = reinterpret_cast<uint32_t*>(q.X + (size_t)nwarps * kQueue * D);
     const size_t qr = RECORD ? (size_t)nwarps * kQueue : 0;
-    q.vh = q.L + qr;
+    q.vh = q.L + (size_t)nwarps * kQueue;
     q.K = q.vh + qr;
     q.mass = reinterpret_cast<T*>(q.K + qr);
     unsigned char* s_v = reinterpret_cast<unsigned char*>(
@@ -994,9 +1009,10 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
             if (stop) {
                 const int slot = wid * kQueue + qn + __popc(sm & below);
 #pragma unroll
-                for (int c = 0; c < D; ++c) { q.X[slot * D + c] = X[c]; q.U[slot * D + c] = U0[c]; }
+                for (int c = 0; c < D; ++c) q.X[slot * D + c] = X[c];
+                q.L[slot] = l;
                 if (RECORD) {
-                    q.L[slot] = l; q.mass[slot] = mass / T(2 * D); q.vh[slot] = vh; q.K[slot] = k - 1;
+                    q.mass[slot] = mass / T(2 * D); q.vh[slot] = vh; q.K[slot] = k - 1;
                     vh = 0u; mass = T(0);
                 }
                 my_steps += k;
