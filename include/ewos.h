@@ -79,7 +79,10 @@ typedef struct {
     int64_t m;                /* number of V-centres when v_nodes is set                     */
     int walk_kernel;          /* 0 -> autotuned; 1 -> one row per CTA at a time; 2 -> streamed
                                  rows (a CTA keeps several rows in flight; one owns the shared
-                                 accumulators, the others add to the output in global memory) */
+                                 accumulators, the others add to the output in global memory);
+                                 3 -> rows handed over early (the shared accumulators pass to
+                                 the next row once a row's walks are all handed out; its walks
+                                 still in flight add to the output in global memory)          */
 } ewos_build_opts;
 
 typedef struct {
@@ -94,7 +97,8 @@ typedef struct {
     int64_t smem_bytes;
     double lookup_grid_scale; /* V grid spacing used                                            */
     int lookup_candidates;    /* fixed candidate slots per V grid cell (0: variable lists)      */
-    int walk_kernel;          /* walk kernel used: 1 one row at a time, 2 streamed rows        */
+    int walk_kernel;          /* walk kernel used: 1 one row at a time, 2 streamed rows,
+                                 3 rows handed over early                                       */
 } ewos_build_report;
 
 typedef struct ewos_toolbox ewos_toolbox;

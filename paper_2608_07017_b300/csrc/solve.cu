@@ -1777,6 +1777,8 @@ __global__ void scatter_cols_kernel(const T* __restrict__ in, double* __restrict
 }
 
 // ------------------------------------------------------------------ workspace
+static inline int64_t pad4(int64_t x) { return (x + 3) & ~(int64_t)3; }   // 16-byte segments of F2one
+
 struct SolveWorkspace {
     double last_alpha = 0.0;                  // shift of the last linear factorisation (factor reuse)
     int D = 0;
@@ -1886,7 +1888,7 @@ static ewos_status ensure_workspace(const ewos_toolbox* tb, SolveWorkspace*& slo
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.diagb, sizeof(double) * ((m + 63) / 64) * 64 * 64));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->lu.flow, sizeof(unsigned int) * flow_state_words(m)));
         if (tb->precision == 32)
-            EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->F2one, sizeof(float) * 2 * (m + p + (int64_t)E * n)));
+            EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->F2one, sizeof(float) * 2 * (pad4(m) + pad4(p) + pad4((int64_t)E * n))));
         undo.armed = false;
     }
     SolveWorkspace* ws = slot;
@@ -1945,9 +1947,9 @@ static void split_f2(cudaStream_t st, const double* v, float* hi, float* lo, int
 // FP64 (the same arithmetic as the batched solves' residual; about 1e-14 relative)
 static void apply_v_f2(const Ctx& C, const double* s, const double* g) {
     float* sh = C.ws->F2one;
-    float* sl = sh + C.m;
-    float* gh = sl + C.m;
-    float* gl = gh + C.p;
+    float* sl = sh + pad4(C.m);
+    float* gh = sl + pad4(C.m);
+    float* gl = gh + pad4(C.p);
     const int64_t rows = (int64_t)C.E * C.n;
     if (s) {
         split_f2(C.st, s, sh, sl, C.m);
@@ -1960,8 +1962,8 @@ static void apply_v_f2(const Ctx& C, const double* s, const double* g) {
 }
 
 static void apply_PT_f2(const Ctx& C, const double* w, double* y) {
-    float* wh = C.ws->F2one + 2 * (C.m + C.p);
-    float* wl = wh + (int64_t)C.E * C.n;
+    float* wh = C.ws->F2one + 2 * (pad4(C.m) + pad4(C.p));
+    float* wl = wh + pad4((int64_t)C.E * C.n);
     const int64_t rows = (int64_t)C.E * C.n;
     split_f2(C.st, w, wh, wl, rows);
     cudaMemsetAsync(y, 0, sizeof(double) * C.m, C.st);
@@ -2252,19 +2254,32 @@ __global__ void add_shifted_kernel(float* __restrict__ LU, const float* __restri
 
 template <typename TP>
 __global__ void jac_scale32_kernel(const TP* __restrict__ Gm, const double* __restrict__ u, const double* __restrict__ lam,
-                                   const double* __restrict__ nl, int nnl, float* __restrict__ out, int n, int m) {
+                                   const double* __restrict__ nl, int nnl, float* __restrict__ out, int n, int m,
+                                   int vec) {
     // the row's factor lam_i N'(u_i) once per block in FP64, the scaling on the FP32 pipes (the
     // factors only precondition the FP64-refined Newton systems)
+    // (block per row; 16-byte loads and stores when the rows are FP32 and 16-byte aligned)
     __shared__ float s_scale;
-    const int i = blockIdx.y;
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x;
     if (threadIdx.x == 0) {
         double d = 0.0, pw = 1.0;
         for (int t = 1; t < nnl; ++t) { d += t * nl[t] * pw; pw *= u[i]; }
         s_scale = (float)(lam[i] * d);
     }
     __syncthreads();
-    if (col < m) out[(size_t)i * m + col] = s_scale * (float)Gm[(size_t)i * m + col];
+    const float sc = s_scale;
+    const TP* g = Gm + (size_t)i * m;
+    float* o = out + (size_t)i * m;
+    if (std::is_same<TP, float>::value && vec) {
+        const float4* g4 = reinterpret_cast<const float4*>(g);
+        float4* o4 = reinterpret_cast<float4*>(o);
+        for (int c = threadIdx.x; c < (m >> 2); c += blockDim.x) {
+            const float4 v = __ldcs(g4 + c);
+            __stcs(o4 + c, make_float4(sc * v.x, sc * v.y, sc * v.z, sc * v.w));
+        }
+    } else {
+        for (int c = threadIdx.x; c < m; c += blockDim.x) o[c] = sc * (float)g[c];
+    }
 }
 
 static double frob32(const Ctx& C, const float* X, int64_t count) {
@@ -2640,9 +2655,84 @@ __global__ void multi_coltrans_f2_kernel(const float* __restrict__ X, int64_t ro
     }
 }
 
+// Single-column forms for 16-byte aligned operands with cols % 4 == 0.  The kernels above keep
+// one load of X in flight per lane and a single pair chain, which leaves P's stream waiting on
+// HBM latency (about a third of the copy rate); here every lane issues kU 16-byte streaming loads
+// before it uses them and keeps four independent pairs (one per float4 component).
+__device__ __forceinline__ void f2_add_prod4(float* hi, float* lo, const float4 x, const float4 h, const float4 l) {
+    f2_add_prod(hi[0], lo[0], x.x, h.x, l.x);
+    f2_add_prod(hi[1], lo[1], x.y, h.y, l.y);
+    f2_add_prod(hi[2], lo[2], x.z, h.z, l.z);
+    f2_add_prod(hi[3], lo[3], x.w, h.w, l.w);
+}
+
+// Vout[row] (+)= sum_c X[row][c] (Vhi[c] + Vlo[c])   (warp per row)
+template <int kU>
+__global__ void rowdot_f2_vec_kernel(const float* __restrict__ X, int64_t rows, int cols, const float* __restrict__ Vhi,
+                                     const float* __restrict__ Vlo, double* __restrict__ Vout, int accumulate) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= rows) return;
+    const float4* xr = reinterpret_cast<const float4*>(X + row * cols);
+    const float4* vh = reinterpret_cast<const float4*>(Vhi);
+    const float4* vl = reinterpret_cast<const float4*>(Vlo);
+    const int c4 = cols >> 2;
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    int c = lane;
+    for (; c + 32 * (kU - 1) < c4; c += 32 * kU) {
+        float4 x[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) x[u] = __ldcs(xr + c + 32 * u);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) f2_add_prod4(hi, lo, x[u], __ldg(vh + c + 32 * u), __ldg(vl + c + 32 * u));
+    }
+    for (; c < c4; c += 32) f2_add_prod4(hi, lo, __ldcs(xr + c), __ldg(vh + c), __ldg(vl + c));
+    double acc = ((double)hi[0] + (double)lo[0]) + ((double)hi[1] + (double)lo[1]) + ((double)hi[2] + (double)lo[2]) +
+                 ((double)hi[3] + (double)lo[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) Vout[row] = accumulate ? Vout[row] + acc : acc;
+}
+
+// Y[c] += sum_{row in chunk} X[row][c] (Whi[row] + Wlo[row])   (thread per four columns)
+template <int kU>
+__global__ void coltrans_f2_vec_kernel(const float* __restrict__ X, int64_t rows, int cols, const float* __restrict__ Whi,
+                                       const float* __restrict__ Wlo, double* __restrict__ Y, int64_t chunk) {
+    const int c4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c4 >= (cols >> 2)) return;
+    const int64_t a = (int64_t)blockIdx.y * chunk;
+    const int64_t b = min(rows, a + chunk);
+    const float4* xc = reinterpret_cast<const float4*>(X) + c4;
+    const int64_t rs = cols >> 2;
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    int64_t r = a;
+    for (; r + kU <= b; r += kU) {
+        float4 x[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) x[u] = __ldcs(xc + (r + u) * rs);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const float wh = __ldg(Whi + r + u), wl = __ldg(Wlo + r + u);
+            f2_add_prod4(hi, lo, x[u], make_float4(wh, wh, wh, wh), make_float4(wl, wl, wl, wl));
+        }
+    }
+    for (; r < b; ++r) {
+        const float wh = __ldg(Whi + r), wl = __ldg(Wlo + r);
+        f2_add_prod4(hi, lo, __ldcs(xc + r * rs), make_float4(wh, wh, wh, wh), make_float4(wl, wl, wl, wl));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) atomicAdd(&Y[(size_t)c4 * 4 + k], (double)hi[k] + (double)lo[k]);
+}
+
+static inline bool aligned16(const void* q) { return ((uintptr_t)q & 15) == 0; }
+
 static void multi_rowdot_f2(cudaStream_t st, const float* X, int64_t rows, int cols, const float* Vhi, const float* Vlo,
                             double* Vout, int rc, int accumulate) {
     const int rb = (int)std::max<int64_t>(1, (rows * 32 + 255) / 256);
+    if (rc == 1 && cols % 4 == 0 && aligned16(X) && aligned16(Vhi) && aligned16(Vlo)) {
+        ::ewos::note_launch(), rowdot_f2_vec_kernel<4><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, accumulate);
+        return;
+    }
     if (rc == 1) ::ewos::note_launch(), multi_rowdot_f2_kernel<1><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
     else if (rc == 2) ::ewos::note_launch(), multi_rowdot_f2_kernel<2><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
     else if (rc == 4) ::ewos::note_launch(), multi_rowdot_f2_kernel<4><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
@@ -2652,6 +2742,12 @@ static void multi_rowdot_f2(cudaStream_t st, const float* X, int64_t rows, int c
 
 static void multi_coltrans_f2(cudaStream_t st, const float* X, int64_t rows, int cols, const float* Whi, const float* Wlo,
                               double* Y, int rc) {
+    if (rc == 1 && cols % 4 == 0 && aligned16(X)) {
+        const int64_t vchunk = 256;
+        dim3 vgrid((unsigned)((cols / 4 + 127) / 128), (unsigned)((rows + vchunk - 1) / vchunk));
+        ::ewos::note_launch(), coltrans_f2_vec_kernel<8><<<vgrid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, vchunk);
+        return;
+    }
     const int64_t chunk = 512;
     dim3 grid((unsigned)((cols + 127) / 128), (unsigned)((rows + chunk - 1) / chunk));
     if (rc == 1) ::ewos::note_launch(), multi_coltrans_f2_kernel<1><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
@@ -3184,10 +3280,10 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                         cudaMemcpyAsync(ws->y, ws->rhs, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
                     }
                     have_factors = true;
-                    dim3 gj((unsigned)((C.m + 255) / 256), (unsigned)C.n);
                     const TP* Gm = (const TP*)tb->P + (size_t)C.D * C.n * C.m;
-                    ::ewos::note_launch(), jac_scale32_kernel<TP><<<gj, 256, 0, C.st>>>(Gm, ws->u2, tb->lambda, nl, pb->nl_ncoef,
-                                                                                      ws->Jx32, (int)C.n, (int)C.m);
+                    ::ewos::note_launch(), jac_scale32_kernel<TP><<<(unsigned)C.n, 256, 0, C.st>>>(Gm, ws->u2, tb->lambda, nl, pb->nl_ncoef,
+                                                                                      ws->Jx32, (int)C.n, (int)C.m,
+                                                                                      (int)(C.m % 4 == 0 && aligned16(Gm) && aligned16(ws->Jx32)));
                     const float* Gm32 = P32 + (size_t)C.D * C.n * C.m;
                     auto t1 = std::chrono::steady_clock::now();
                     // Jacobian Lambda + alpha I + G^T diag(lam N'(u)) G: the product on the tensor

@@ -1132,6 +1132,297 @@ __global__ void __launch_bounds__(1024, 1) wos_walk_batch_kernel(const WalkArgs<
     }
 }
 
+// ------------------------------------------------------------------ rows handed over early
+// The row loop above keeps a row in the shared accumulators until its last walk stops: once the
+// row's walks are all handed out, lanes whose walk stopped idle while the longest walks finish
+// (simulated on the ball: a quarter of the lane-steps of a row).  Here the CTA hands the shared
+// accumulators to the next row as soon as the row's walks are all handed out: every warp, at the
+// top of its next iteration, bins its queued walks into the shared row and meets the others at a
+// CTA barrier; the row's partial sums are written to the output (scaled, plain stores), the
+// accumulators cleared, and the next row's ball term and walks start at once.  The walks of the
+// earlier row still in flight (about 8 % of a row's steps) keep their row index in a register and
+// add their remaining contributions to the output in global memory (L2 reductions, after the
+// barrier that orders them behind the stores); when one stops it is binned at once, also in
+// global memory.  The exit counts of such walks make KH's H part stale: one pass after the
+// launch sets it from the counts (H = Hc / N) for all rows.
+template <typename T, int D>
+__device__ __forceinline__ void flush_row_scaled(const WalkArgs<T, D>& a, int row, T r0, T* acc, T* accKH,
+                                                 uint32_t* accH) {
+    const T invN = T(1) / (T)a.N;
+    const T sG = invN / T(2 * D), sGG = invN / (T(2) * r0), sKH = T(D) * invN / r0;
+    const size_t nm = (size_t)a.n * a.m, np = (size_t)a.n * a.p;
+    for (int t = threadIdx.x; t < a.m; t += blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            a.P[c * nm + (size_t)row * a.m + t] = acc[(size_t)c * a.m + t] * sGG;
+            acc[(size_t)c * a.m + t] = T(0);
+        }
+        a.P[D * nm + (size_t)row * a.m + t] = acc[(size_t)D * a.m + t] * sG;
+        acc[(size_t)D * a.m + t] = T(0);
+    }
+    for (int t = threadIdx.x; t < a.p; t += blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            a.KH[c * np + (size_t)row * a.p + t] = accKH[(size_t)c * a.p + t] * sKH;
+            accKH[(size_t)c * a.p + t] = T(0);
+        }
+        a.Hc[(size_t)row * a.p + t] = accH[t];
+        accH[t] = 0u;
+    }
+}
+
+// ball term of the first sphere of `row` (all threads of the CTA, into the shared accumulators)
+template <typename T, int D, bool RECORD>
+__device__ __forceinline__ void ball_term(const WalkArgs<T, D>& a, int row, const T* xi, T r0,
+                                          const Lookup<T, D>& V, const uint16_t* candK, int K, T* acc) {
+    const T r02 = r0 * r0;
+    for (int64_t l = threadIdx.x; l < a.N; l += blockDim.x) {
+        T S, Zb[D], pt[D];
+        draw_ball<T, D>((uint32_t)l, (uint32_t)row, a.inst, a.k0, a.k1, S, Zb);
+        const T wsum = (D == 2) ? T(1) + S : T(1) + S + S * S;
+#pragma unroll
+        for (int c = 0; c < D; ++c) pt[c] = xi[c] + r0 * S * Zb[c];
+        const int jb = K > 0 ? nearest_fixed(V, candK, K, pt, a.m) : nearest_or_scan(V, a.m, pt);
+#pragma unroll
+        for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + jb], r02 * wsum * Zb[c]);
+        if (RECORD) atomicXor(&a.rec_vhash[(size_t)row * a.N + l], cellmix(0xFFFFFFFFu, jb));
+    }
+}
+
+template <typename T, int D, int KIND, bool RECORD>
+__device__ __forceinline__ void walk_rows_handover(const WalkArgs<T, D>& a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // shared layout as in walk_rows
+    T* acc = reinterpret_cast<T*>(smem_raw);
+    T* accKH = acc + (size_t)(D + 1) * a.m;
+    uint32_t* accH = reinterpret_cast<uint32_t*>(accKH + (size_t)D * a.p);
+    T* s_sdf = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(accH + a.p) + 15) & ~uintptr_t(15));
+    const int nwarps = blockDim.x >> 5;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WalkQueue<T, D> q;
+    q.X = s_sdf + ((a.sdf_len + 3) & ~3);
+    q.L = reinterpret_cast<uint32_t*>(q.X + (size_t)nwarps * kQueue * D);
+    const size_t qr = RECORD ? (size_t)nwarps * kQueue : 0;
+    q.vh = q.L + (size_t)nwarps * kQueue;
+    q.K = q.vh + qr;
+    q.mass = reinterpret_cast<T*>(q.K + qr);
+    unsigned char* s_v = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(q.mass + qr) + 15) & ~uintptr_t(15));
+    __shared__ int s_row;
+    __shared__ unsigned int s_walk;
+    __shared__ int s_switch;
+
+    for (int t = threadIdx.x; t < a.sdf_len; t += blockDim.x) s_sdf[t] = a.sdf[t];
+    Lookup<T, D> V = a.V;
+    const uint16_t* candK = a.v_candK;
+    if (a.v_in_smem) {
+        T* vp = reinterpret_cast<T*>(s_v);
+        for (int t = threadIdx.x; t < (a.m + 1) * D; t += blockDim.x) vp[t] = a.V.pts[t];
+        V.pts = vp;
+        if (a.v_K > 0) {
+            uint16_t* vk = reinterpret_cast<uint16_t*>(vp + (size_t)(a.m + 1) * D);
+            for (int64_t t = threadIdx.x; t < (int64_t)a.v_ncell * a.v_K; t += blockDim.x) vk[t] = a.v_candK[t];
+            candK = vk;
+        } else {
+            int* vs = reinterpret_cast<int*>(vp + (size_t)(a.m + 1) * D);
+            int* vc = vs + a.v_ncell + 1;
+            for (int t = threadIdx.x; t <= a.v_ncell; t += blockDim.x) vs[t] = a.V.start[t];
+            for (int64_t t = threadIdx.x; t < a.v_ncand; t += blockDim.x) vc[t] = a.V.cand[t];
+            V.start = vs; V.cand = vc;
+        }
+    }
+    const int K = a.v_K;
+    for (int t = threadIdx.x; t < (D + 1) * a.m; t += blockDim.x) acc[t] = T(0);
+    for (int t = threadIdx.x; t < D * a.p; t += blockDim.x) accKH[t] = T(0);
+    for (int t = threadIdx.x; t < a.p; t += blockDim.x) accH[t] = 0u;
+    if (threadIdx.x == 0) {
+        s_row = atomicAdd(a.row_counter, 1);
+        s_walk = 0u;
+        s_switch = 0;
+    }
+    __syncthreads();
+    int row = s_row;
+    if (row >= a.n) return;
+    T xi[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) xi[c] = a.x[(size_t)row * D + c];
+    T r0 = a.r0[row];
+    ball_term<T, D, RECORD>(a, row, xi, r0, V, candK, K, acc);
+
+    unsigned long long my_steps = 0, my_capped = 0;
+    const T invN = T(1) / (T)a.N;
+    const size_t nm = (size_t)a.n * a.m, np = (size_t)a.n * a.p;
+    volatile int* vswitch = &s_switch;
+    bool last = false;                     // no row left to hand the accumulators to
+    uint32_t l = atomicAdd(&s_walk, 1u);
+    bool have = l < (uint64_t)a.N;
+    if (!have) *vswitch = 1;
+    int lrow = row;                        // row of the lane's walk
+    T X[D], U0[D], mass = T(0);
+    uint32_t k = 0, vh = 0u;
+    int qn = 0;
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int c = 0; c < D; ++c) { X[c] = xi[c]; U0[c] = T(0); }
+    for (;;) {
+        const bool any_walk = __any_sync(0xffffffffu, have);
+        if (!last && (!any_walk || __shfl_sync(0xffffffffu, *vswitch, 0))) {
+            // the row's walks are all handed out: hand the accumulators over
+            if (lane == 0) *vswitch = 1;
+            for (int e = lane; e < qn; e += 32) bin_stopped<T, D, RECORD>(a, q, wid * kQueue + e, row, accKH, accH);
+            qn = 0;
+            __syncwarp();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int nxt = atomicAdd(a.row_counter, 1);
+                s_row = nxt;
+                s_walk = 0u;                // (unused once no row is left)
+                s_switch = 0;
+            }
+            __syncthreads();
+            const int nxt = s_row;
+            if (nxt >= a.n) {
+                last = true;                // the walks in flight finish into the shared row
+            } else {
+                flush_row_scaled<T, D>(a, row, r0, acc, accKH, accH);
+                __syncthreads();            // stores and clears before any later addition
+                row = nxt;
+#pragma unroll
+                for (int c = 0; c < D; ++c) xi[c] = a.x[(size_t)row * D + c];
+                r0 = a.r0[row];
+                ball_term<T, D, RECORD>(a, row, xi, r0, V, candK, K, acc);
+                if (!have) {
+                    l = atomicAdd(&s_walk, 1u);
+                    have = l < (uint64_t)a.N;
+                    if (!have) *vswitch = 1;
+                    lrow = row;
+                    k = 0;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) X[c] = xi[c];
+                }
+            }
+            continue;
+        }
+        if (!any_walk) break;               // last row: every walk has stopped
+        T r = r0;
+        if (have && k > 0) {
+            if (KIND == SDF_POLYGON && a.e_cnt) r = polygon_dist_grid<T, D>(a, s_sdf, X);
+            else r = Sdf<T, D, KIND>::eval(s_sdf, a.nsdf, X);
+        } else if (have && lrow != row) {
+            r = a.r0[lrow];                 // taken just before a hand-over (rows of few walks)
+        }
+        const bool stop = have && k > 0 && (r < a.eps || (int64_t)k > a.max_steps);
+        const bool cur = lrow == row;
+        const unsigned sm = __ballot_sync(0xffffffffu, stop && cur);
+        if (stop) {
+            my_steps += k;
+            my_capped += (r >= a.eps);
+            if (cur) {
+                const int slot = wid * kQueue + qn + __popc(sm & below);
+#pragma unroll
+                for (int c = 0; c < D; ++c) q.X[slot * D + c] = X[c];
+                q.L[slot] = l;
+                if (RECORD) { q.mass[slot] = mass / T(2 * D); q.vh[slot] = vh; q.K[slot] = k - 1; }
+            } else {
+                // a walk of an earlier row: binned at once into that row's output
+                T U[D];
+                draw_first_direction<T, D>(l, (uint32_t)lrow, a.inst, a.k0, a.k1, U);
+                const int jz = nearest_or_scan(a.Z, a.p, X);
+                const T sKH = T(D) * invN / a.r0[lrow];
+                atomicAdd(&a.Hc[(size_t)lrow * a.p + jz], 1u);
+#pragma unroll
+                for (int c = 0; c < D; ++c) atomicAdd(&a.KH[c * np + (size_t)lrow * a.p + jz], U[c] * sKH);
+                if (RECORD) {
+                    const size_t ri = (size_t)lrow * a.N + l;
+                    a.rec_exit[ri] = jz;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) a.rec_xexit[ri * D + c] = X[c];
+                    a.rec_mass[ri] = mass / T(2 * D);
+                    a.rec_steps[ri] = (int32_t)(k - 1);
+                    atomicXor(&a.rec_vhash[ri], vh);
+                }
+            }
+            if (RECORD) { vh = 0u; mass = T(0); }
+            if (!last) {
+                l = atomicAdd(&s_walk, 1u);
+                have = l < (uint64_t)a.N;
+                if (!have) *vswitch = 1;
+            } else {
+                have = false;               // no row left: nothing more to hand out
+            }
+            lrow = row;
+#pragma unroll
+            for (int c = 0; c < D; ++c) X[c] = xi[c];
+            k = 0;
+            r = r0;
+        }
+        qn += __popc(sm);
+        if (have) {
+            T R, Zs[D], U[D], pt[D];
+            draw_step<T, D>(l, k, (uint32_t)lrow, a.inst, a.k0, a.k1, R, Zs, U);
+            const T rR = r * R;
+#pragma unroll
+            for (int c = 0; c < D; ++c) pt[c] = X[c] + rR * Zs[c];
+            const int j = K > 0 ? nearest_fixed(V, candK, K, pt, a.m) : nearest_or_scan(V, a.m, pt);
+            const T r2 = r * r;
+            if (lrow == row) {
+                atomicAdd(&acc[(size_t)D * a.m + j], r2);
+                if (k > 0) {
+#pragma unroll
+                    for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + j], U0[c] * r2);
+                }
+            } else {
+                const T sGG = invN / (T(2) * a.r0[lrow]);
+                atomicAdd(&a.P[D * nm + (size_t)lrow * a.m + j], r2 * (invN / T(2 * D)));
+                if (k > 0) {
+#pragma unroll
+                    for (int c = 0; c < D; ++c) atomicAdd(&a.P[c * nm + (size_t)lrow * a.m + j], U0[c] * r2 * sGG);
+                }
+            }
+            if (k == 0) {
+#pragma unroll
+                for (int c = 0; c < D; ++c) U0[c] = U[c];
+            }
+#pragma unroll
+            for (int c = 0; c < D; ++c) X[c] += r * U[c];
+            if (RECORD) { mass += r2; vh ^= cellmix(k, (uint32_t)j); }
+            ++k;
+        }
+        __syncwarp();
+        while (qn >= 32) {
+            bin_stopped<T, D, RECORD>(a, q, wid * kQueue + qn - 1 - lane, row, accKH, accH);
+            qn -= 32;
+        }
+        __syncwarp();
+    }
+    // last row: drain the queues, then write it
+    for (int e = lane; e < qn; e += 32) bin_stopped<T, D, RECORD>(a, q, wid * kQueue + e, row, accKH, accH);
+    __syncwarp();
+    __syncthreads();
+    flush_row_scaled<T, D>(a, row, r0, acc, accKH, accH);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_steps += __shfl_down_sync(0xffffffffu, my_steps, o);
+        my_capped += __shfl_down_sync(0xffffffffu, my_capped, o);
+    }
+    if (lane == 0) {
+        atomicAdd(a.stat_steps, my_steps);
+        if (my_capped) atomicAdd(a.stat_capped, my_capped);
+    }
+}
+
+template <typename T, int D, int KIND, bool RECORD>
+__global__ void __launch_bounds__(1024, 1) wos_walk_handover_kernel(WalkArgs<T, D> a) {
+    walk_rows_handover<T, D, KIND, RECORD>(a);
+}
+
+// KH's H part from the exit counts (after the handover kernel): H = Hc / N
+template <typename T>
+__global__ void h_from_counts_kernel(const uint32_t* __restrict__ Hc, T* __restrict__ H, int64_t count, T invN) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+        H[t] = (T)Hc[t] * invN;
+}
+
 // ------------------------------------------------------------------ streamed rows
 // The row loop above makes every lane of a CTA wait at the end of each row for the row's
 // longest walk (23 % of the issued lane slots on the square, 40 % on the ball).  Here a CTA
@@ -1703,9 +1994,16 @@ struct BuildContext {
     }
 };
 
+// the row kernels: 1 one row per CTA at a time, 3 rows handed over early
 template <typename T, int D, int KIND, bool RECORD>
-static cudaError_t launch_walks(const WalkArgs<T, D>& a, int grid, int tpb, size_t smem, cudaStream_t st) {
-    auto k = wos_walk_kernel<T, D, KIND, RECORD>;
+static void (*row_kernel(int kern))(WalkArgs<T, D>) {
+    if (kern == 3) return wos_walk_handover_kernel<T, D, KIND, RECORD>;
+    return wos_walk_kernel<T, D, KIND, RECORD>;
+}
+
+template <typename T, int D, int KIND, bool RECORD>
+static cudaError_t launch_walks(const WalkArgs<T, D>& a, int grid, int tpb, size_t smem, cudaStream_t st, int kern = 1) {
+    auto k = row_kernel<T, D, KIND, RECORD>(kern);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     ::ewos::note_launch(), k<<<grid, tpb, smem, st>>>(a);
@@ -1713,15 +2011,16 @@ static cudaError_t launch_walks(const WalkArgs<T, D>& a, int grid, int tpb, size
 }
 
 template <typename T, int D, int KIND>
-static cudaError_t dispatch_walks(const WalkArgs<T, D>& a, bool rec, int grid, int tpb, size_t smem, cudaStream_t st) {
-    return rec ? launch_walks<T, D, KIND, true>(a, grid, tpb, smem, st)
-               : launch_walks<T, D, KIND, false>(a, grid, tpb, smem, st);
+static cudaError_t dispatch_walks(const WalkArgs<T, D>& a, bool rec, int grid, int tpb, size_t smem, cudaStream_t st,
+                                  int kern) {
+    return rec ? launch_walks<T, D, KIND, true>(a, grid, tpb, smem, st, kern)
+               : launch_walks<T, D, KIND, false>(a, grid, tpb, smem, st, kern);
 }
 
 template <typename T, int D, int KIND>
-static int max_ctas_per_sm(int tpb, size_t smem) {
+static int max_ctas_per_sm(int tpb, size_t smem, int kern = 1) {
     int nb = 0;
-    auto k = wos_walk_kernel<T, D, KIND, false>;
+    auto k = row_kernel<T, D, KIND, false>(kern);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, tpb, smem);
     return nb;
@@ -2026,9 +2325,9 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
             else if (dom->kind == SDF_BOX) ps = max_stream_ctas_per_sm<T, D, SDF_BOX>(tpb, c.smem);
             else ps = max_stream_ctas_per_sm<T, D, SDF_POLYGON>(tpb, c.smem);
         } else {
-            if (dom->kind == SDF_BALL) ps = max_ctas_per_sm<T, D, SDF_BALL>(tpb, c.smem);
-            else if (dom->kind == SDF_BOX) ps = max_ctas_per_sm<T, D, SDF_BOX>(tpb, c.smem);
-            else ps = max_ctas_per_sm<T, D, SDF_POLYGON>(tpb, c.smem);
+            if (dom->kind == SDF_BALL) ps = max_ctas_per_sm<T, D, SDF_BALL>(tpb, c.smem, kern);
+            else if (dom->kind == SDF_BOX) ps = max_ctas_per_sm<T, D, SDF_BOX>(tpb, c.smem, kern);
+            else ps = max_ctas_per_sm<T, D, SDF_POLYGON>(tpb, c.smem, kern);
         }
         if (ps < 1) return false;
         if (o.ctas_per_sm > 0) ps = std::min(ps, o.ctas_per_sm);
@@ -2055,15 +2354,15 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
             if (dom->kind == SDF_BOX) return dispatch_stream_walks<T, D, SDF_BOX>(args, rec, c.grid, c.tpb, c.smem, st);
             return dispatch_stream_walks<T, D, SDF_POLYGON>(args, rec, c.grid, c.tpb, c.smem, st);
         }
-        if (dom->kind == SDF_BALL) return dispatch_walks<T, D, SDF_BALL>(args, rec, c.grid, c.tpb, c.smem, st);
-        if (dom->kind == SDF_BOX) return dispatch_walks<T, D, SDF_BOX>(args, rec, c.grid, c.tpb, c.smem, st);
-        return dispatch_walks<T, D, SDF_POLYGON>(args, rec, c.grid, c.tpb, c.smem, st);
+        if (dom->kind == SDF_BALL) return dispatch_walks<T, D, SDF_BALL>(args, rec, c.grid, c.tpb, c.smem, st, c.kern);
+        if (dom->kind == SDF_BOX) return dispatch_walks<T, D, SDF_BOX>(args, rec, c.grid, c.tpb, c.smem, st, c.kern);
+        return dispatch_walks<T, D, SDF_POLYGON>(args, rec, c.grid, c.tpb, c.smem, st, c.kern);
     };
     Cfg cfg{};
     const bool fixed_tpb = o.threads_per_block > 0;
     const bool fixed_place = o.hash_in_smem == 0 || o.hash_in_smem == 1;
     const int req_tpb = std::min(1024, (o.threads_per_block + 31) / 32 * 32);
-    const int req_kern = o.walk_kernel == 1 || o.walk_kernel == 2 ? o.walk_kernel : 0;
+    const int req_kern = o.walk_kernel >= 1 && o.walk_kernel <= 3 ? o.walk_kernel : 0;
     if (fixed_tpb && fixed_place && req_kern) {
         if (!configure(req_tpb, 0, o.hash_in_smem, n, cfg, req_kern)) {
             set_error("walk kernel: requested block size / lookup placement does not fit");
@@ -2078,7 +2377,7 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
         // the streamed-rows kernel is a candidate only on request: measured slower on the
         // square and ball workloads (the rows that do not own the shared accumulators add
         // through L2 reductions)
-        for (int kern : {1, 2}) {
+        for (int kern : {1, 2, 3}) {
             if (req_kern ? kern != req_kern : kern != 1) continue;
             for (int vg : {0, 1})
                 for (int t : {512, 1024}) {
@@ -2130,6 +2429,12 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     if (cfg.kern == 2) EWOS_CUDA_TRY(zero_outputs());
     EWOS_CUDA_TRY(cudaEventRecord(ev[3], st));
     EWOS_CUDA_TRY(launch(cfg, a));
+    if (cfg.kern == 3) {
+        ::ewos::note_launch();
+        h_from_counts_kernel<T><<<(int)std::min<int64_t>(4096, ((int64_t)np + 255) / 256), 256, 0, st>>>(
+            tb->Hc, (T*)tb->KH + (size_t)D * np, (int64_t)np, T(1) / (T)tb->N);
+        EWOS_CUDA_TRY(cudaGetLastError());
+    }
     const int tpb = cfg.tpb, per_sm = cfg.per_sm, grid = cfg.grid;
     const bool v_smem = cfg.v_smem;
     const size_t smem = cfg.smem;

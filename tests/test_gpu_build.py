@@ -239,11 +239,14 @@ def test_separate_v_partition_fp64_parity_and_solve():
     tb.close()
 
 
-@pytest.mark.parametrize("walk_kernel", [1, 2])
+@pytest.mark.parametrize("walk_kernel", [1, 2, 3])
 def test_both_walk_kernels_parity(walk_kernel):
-    """One row per CTA at a time (1) and streamed rows (2, several rows in flight per CTA, walks of
-    rows that do not own the shared accumulators add to the output in global memory): both meet
-    the same bars against the oracle, on small square, ball and star cases and ragged shapes."""
+    """One row per CTA at a time (1), streamed rows (2, several rows in flight per CTA, walks of
+    rows that do not own the shared accumulators add to the output in global memory) and rows
+    handed over early (3, the shared accumulators pass to the next row once a row's walks are all
+    handed out; the walks still in flight finish into the output in global memory): all meet the
+    same bars against the oracle, on small square, ball and star cases and ragged shapes (N = 1
+    and N = 3 hand a row over at every step)."""
     w = W.square(16, 16, walks=2000, eps=1e-4, problem=False)
     _parity(w, np.arange(0, w.x.shape[0], 2), 2000, 32, walk_kernel=walk_kernel)
     x, _ = W.ball_nodes(500, seed=1)
