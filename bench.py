@@ -130,8 +130,9 @@ def _dist():
 
 # ------------------------------------------------------------------ rooflines
 def walk_roofline(workload, steps_per_launch, ms_walk, nsm, peaks, peak_src, grid_scale=None):
-    """Walk-kernel roofline of the survey's measurement section: the kernel is bound by the
-    FP32/SFU pipes and instruction issue, so its fraction is max(fma-pipe, xu-pipe) utilisation.
+    """Walk-kernel roofline of the survey's measurement section: its fraction is max(fma-pipe,
+    xu-pipe) utilisation, with issue beside it, and beside those the resource the kernel is
+    measured to be bound by (`binding_resource`: L1 data-pipe wavefronts per WoS step).
     The instructions per WoS step on each pipe come from the ncu counters committed in
     profiles/walk_counters.json for the same kernel source (sha of wos_build.cu and
     device_common.cuh); they are scaled by the WoS steps of this launch and divided by its
@@ -160,6 +161,15 @@ def walk_roofline(workload, steps_per_launch, ms_walk, nsm, peaks, peak_src, gri
         rates[pipe] = {"achieved_per_s": per_step * steps_per_launch / t, "peak_per_s": peak,
                        "frac": per_step * steps_per_launch / t / peak}
     lane = e["thread_inst_per_step"] / 32.0 * steps_per_launch / t / rates["issue"]["peak_per_s"]
+    l1 = e.get("l1_wavefronts_per_step")
+    if l1:
+        # the resource the kernel is bound by: the L1 data pipe (one wavefront per SM cycle),
+        # fed by the shared-memory float atomics of the binning and the lookup's loads
+        l1_peak = e["peak_per_sm_cycle"]["l1_wavefronts"] * nsm * clock
+        out["binding_resource"] = {"name": "L1 data pipe (wavefronts)", "per_step": l1,
+                                   "per_step_by_source": e.get("l1_wavefronts_by_source"),
+                                   "achieved": l1 * steps_per_launch / t / 1e12, "peak": l1_peak / 1e12,
+                                   "unit": "T wavefronts/s", "frac": l1 * steps_per_launch / t / l1_peak}
     best = "fma" if rates["fma"]["frac"] >= rates["xu"]["frac"] else "xu"
     out.update({"pipe": best, "achieved": rates[best]["achieved_per_s"] / 1e12, "peak": rates[best]["peak_per_s"] / 1e12,
                 "unit": "T warp-instructions/s on the " + best + " pipe", "frac": rates[best]["frac"],
