@@ -77,12 +77,11 @@ typedef struct {
                                  inputs_on_device.  Rows stay indexed by x (n), columns of G and
                                  grad G by y (m); the solve's unknown s has m entries.        */
     int64_t m;                /* number of V-centres when v_nodes is set                     */
-    int walk_kernel;          /* 0 -> autotuned; 1 -> one row per CTA at a time; 2 -> streamed
-                                 rows (a CTA keeps several rows in flight; one owns the shared
-                                 accumulators, the others add to the output in global memory);
-                                 3 -> rows handed over early (the shared accumulators pass to
-                                 the next row once a row's walks are all handed out; its walks
-                                 still in flight add to the output in global memory)          */
+    int walk_kernel;          /* 0 -> autotuned; 1 -> the row's G and grad G accumulators in
+                                 global memory (one 16-byte L2 reduction per walk point;
+                                 16 m bytes per CTA of device memory during the build, 32 m
+                                 for FP64 walks);
+                                 2 -> the accumulators in shared memory (one atomic per value) */
 } ewos_build_opts;
 
 typedef struct {
@@ -97,8 +96,8 @@ typedef struct {
     int64_t smem_bytes;
     double lookup_grid_scale; /* V grid spacing used                                            */
     int lookup_candidates;    /* fixed candidate slots per V grid cell (0: variable lists)      */
-    int walk_kernel;          /* walk kernel used: 1 one row at a time, 2 streamed rows,
-                                 3 rows handed over early                                       */
+    int walk_kernel;          /* walk kernel used: 1 accumulators in global memory, 2 in
+                                 shared memory                                                  */
 } ewos_build_report;
 
 typedef struct ewos_toolbox ewos_toolbox;

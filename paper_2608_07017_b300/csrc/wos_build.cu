@@ -736,7 +736,14 @@ struct WalkArgs {
     int* row_counter;
     unsigned long long* stat_steps;
     unsigned long long* stat_capped;
-    unsigned long long* stat_error;     // streamed rows: warps that gave up waiting (NULL elsewhere)
+    // G and grad G accumulators of the rows in flight, in global memory (L2-resident): CTA b owns
+    // acc_g[b * acc_cells * 4 ..) as [cell][4] = (G, d_1 G, .., d_D G) (NULL: the shared-memory form)
+    T* acc_g;
+    int acc_cells;
+    int64_t acc_len;                    // elements of acc_g
+    // indexes the kernel found out of range and skipped (a bin, a row, the accumulator region;
+    // none expected: the host reports any as an error); may be NULL
+    unsigned long long* stat_bad;
     int32_t* rec_exit;
     int32_t* rec_steps;
     T* rec_mass;
@@ -758,6 +765,36 @@ __device__ __forceinline__ uint32_t cellmix(uint32_t tag, uint32_t cell) {
     x ^= x >> 27; x *= 0x94d049bb133111ebull;
     x ^= x >> 31;
     return (uint32_t)(x ^ (x >> 32));
+}
+
+// One walk point's binning (G += G_add, grad G += g[0..D)) into cell j of the CTA's accumulator
+// row.  Global form: the 1 + D values sit together in a 16-byte (FP32) cell and go to L2 as one
+// vector reduction; FP32 atomics in shared memory cost about 20 % of the walk (a
+// compare-and-swap loop per value on the L1 data pipe), the reduction next to nothing.
+// Shared form: one shared-memory atomic per value, planar rows acc[c * m + j].
+template <typename T, int D, bool L2ACC>
+__device__ __forceinline__ void bin_point(T* acc, int m, int j, T G_add, const T* g, bool grad) {
+    if constexpr (L2ACC) {
+        T* dst = acc + (size_t)j * 4;
+        if constexpr (std::is_same<T, float>::value) {
+            const float g0 = grad ? g[0] : 0.0f, g1 = grad ? g[1] : 0.0f, g2 = (grad && D == 3) ? g[D - 1] : 0.0f;
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(G_add), "f"(g0), "f"(g1),
+                         "f"(g2)
+                         : "memory");
+        } else {
+            if (G_add != T(0)) atomicAdd(dst, G_add);
+            if (grad) {
+#pragma unroll
+                for (int c = 0; c < D; ++c) atomicAdd(dst + 1 + c, g[c]);
+            }
+        }
+    } else {
+        if (G_add != T(0)) atomicAdd(&acc[(size_t)D * m + j], G_add);
+        if (grad) {
+#pragma unroll
+            for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * m + j], g[c]);
+        }
+    }
 }
 
 // Random-number layout (shared with the oracle through its published definition):
@@ -897,13 +934,13 @@ __device__ __forceinline__ T polygon_dist_grid(const WalkArgs<T, D>& a, const T*
 // instance's own counter; batched builds fetch global rows g from one counter shared by all
 // instances (rows of instance k are [gbase, gend)) and return the first fetched row that belongs
 // to a later instance.
-template <typename T, int D, int KIND, bool RECORD, bool BATCH>
+template <typename T, int D, int KIND, bool RECORD, bool BATCH, bool L2ACC>
 __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, int gbase, int gend, int* gcounter) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // shared layout: acc [(D+1)][m] T | accKH [D][p] T | accH [p] u32 | sdf params | per-warp
-    // queues | V lookup (points, then the fixed-stride table or the CSR lists)
-    T* acc = reinterpret_cast<T*>(smem_raw);
-    T* accKH = acc + (size_t)(D + 1) * a.m;
+    // shared layout: [acc [(D+1)][m] T, shared form only] | accKH [D][p] T | accH [p] u32 | sdf
+    // params | per-warp queues | V lookup (points, then the fixed-stride table or the CSR lists)
+    T* acc = L2ACC ? a.acc_g + (size_t)blockIdx.x * a.acc_cells * 4 : reinterpret_cast<T*>(smem_raw);
+    T* accKH = L2ACC ? reinterpret_cast<T*>(smem_raw) : acc + (size_t)(D + 1) * a.m;
     uint32_t* accH = reinterpret_cast<uint32_t*>(accKH + (size_t)D * a.p);
     T* s_sdf = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(accH + a.p) + 15) & ~uintptr_t(15));
     const int nwarps = blockDim.x >> 5;
@@ -940,7 +977,11 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
         }
     }
     const int K = a.v_K;
-    const int accN = (D + 1) * a.m;
+    if (L2ACC && ((int64_t)(blockIdx.x + 1) * a.acc_cells * 4 > a.acc_len || a.m > a.acc_cells)) {
+        if (threadIdx.x == 0 && a.stat_bad) atomicAdd(a.stat_bad, 1ull);
+        return BATCH ? gend : 0;              // (the CTA as a whole, before any barrier)
+    }
+    const int accN = L2ACC ? 4 * a.acc_cells : (D + 1) * a.m;
     for (int t = threadIdx.x; t < accN; t += blockDim.x) acc[t] = T(0);
     for (int t = threadIdx.x; t < D * a.p; t += blockDim.x) accKH[t] = T(0);
     for (int t = threadIdx.x; t < a.p; t += blockDim.x) accH[t] = 0u;
@@ -962,6 +1003,11 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
         if (BATCH) {
             if (row >= gend) { g_next = row; break; }
             row -= gbase;
+            if (row < 0 || row >= a.n) {
+                if (threadIdx.x == 0 && a.stat_bad) atomicAdd(a.stat_bad, 1ull);
+                g_next = gend;
+                break;
+            }
         } else if (row >= a.n) {
             break;
         }
@@ -979,8 +1025,11 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
 #pragma unroll
             for (int c = 0; c < D; ++c) pt[c] = xi[c] + r0 * S * Zb[c];
             const int jb = K > 0 ? nearest_fixed(V, candK, K, pt, a.m) : nearest_or_scan(V, a.m, pt);
+            T gb[D];
 #pragma unroll
-            for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + jb], r02 * wsum * Zb[c]);
+            for (int c = 0; c < D; ++c) gb[c] = r02 * wsum * Zb[c];
+            if ((unsigned)jb < (unsigned)a.m) bin_point<T, D, L2ACC>(acc, a.m, jb, T(0), gb, true);
+            else if (a.stat_bad) atomicAdd(a.stat_bad, 1ull);
             if (RECORD) atomicXor(&a.rec_vhash[(size_t)row * a.N + l], cellmix(0xFFFFFFFFu, jb));
         }
 
@@ -1033,11 +1082,12 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
                 for (int c = 0; c < D; ++c) pt[c] = X[c] + rR * Zs[c];
                 const int j = K > 0 ? nearest_fixed(V, candK, K, pt, a.m) : nearest_or_scan(V, a.m, pt);
                 const T r2 = r * r;
-                atomicAdd(&acc[(size_t)D * a.m + j], r2);
-                if (k > 0) {
+                T gs[D];
 #pragma unroll
-                    for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + j], U0[c] * r2);
-                } else {
+                for (int c = 0; c < D; ++c) gs[c] = U0[c] * r2;     // (not added at step 0)
+                if ((unsigned)j < (unsigned)a.m) bin_point<T, D, L2ACC>(acc, a.m, j, r2, gs, k > 0);
+                else if (a.stat_bad) atomicAdd(a.stat_bad, 1ull);
+                if (k == 0) {
 #pragma unroll
                     for (int c = 0; c < D; ++c) U0[c] = U[c];
                 }
@@ -1065,13 +1115,29 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
         const T sKH = T(D) * invN / r0;
         const size_t nm = (size_t)a.n * a.m, np = (size_t)a.n * a.p;
         for (int t = threadIdx.x; t < a.m; t += blockDim.x) {
+            if constexpr (L2ACC) {
+                // the reductions of the row are complete at the barrier above; read past L1
+                T v[4];
+                if constexpr (std::is_same<T, float>::value) {
+                    const float4 q4 = __ldcg(reinterpret_cast<const float4*>(acc) + t);
+                    v[0] = q4.x; v[1] = q4.y; v[2] = q4.z; v[3] = q4.w;
+                    __stcg(reinterpret_cast<float4*>(acc) + t, make_float4(0.f, 0.f, 0.f, 0.f));
+                } else {
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                a.P[c * nm + (size_t)row * a.m + t] = acc[(size_t)c * a.m + t] * sGG;
-                acc[(size_t)c * a.m + t] = T(0);
+                    for (int c = 0; c < 4; ++c) { v[c] = __ldcg(acc + (size_t)t * 4 + c); acc[(size_t)t * 4 + c] = T(0); }
+                }
+#pragma unroll
+                for (int c = 0; c < D; ++c) a.P[c * nm + (size_t)row * a.m + t] = v[1 + c] * sGG;
+                a.P[D * nm + (size_t)row * a.m + t] = v[0] * sG;
+            } else {
+#pragma unroll
+                for (int c = 0; c < D; ++c) {
+                    a.P[c * nm + (size_t)row * a.m + t] = acc[(size_t)c * a.m + t] * sGG;
+                    acc[(size_t)c * a.m + t] = T(0);
+                }
+                a.P[D * nm + (size_t)row * a.m + t] = acc[(size_t)D * a.m + t] * sG;
+                acc[(size_t)D * a.m + t] = T(0);
             }
-            a.P[D * nm + (size_t)row * a.m + t] = acc[(size_t)D * a.m + t] * sG;
-            acc[(size_t)D * a.m + t] = T(0);
         }
         for (int t = threadIdx.x; t < a.p; t += blockDim.x) {
 #pragma unroll
@@ -1098,9 +1164,16 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
     return g_next;
 }
 
+// the row kernel with its G / grad G accumulators in global memory (walk_kernel 1, the default)
 template <typename T, int D, int KIND, bool RECORD>
 __global__ void __launch_bounds__(1024, 1) wos_walk_kernel(WalkArgs<T, D> a) {
-    walk_rows<T, D, KIND, RECORD, false>(a, 0, 0, 0, nullptr);
+    walk_rows<T, D, KIND, RECORD, false, true>(a, 0, 0, 0, nullptr);
+}
+
+// the same with the accumulators in shared memory (walk_kernel 2; the build without allocation)
+template <typename T, int D, int KIND, bool RECORD>
+__global__ void __launch_bounds__(1024, 1) wos_walk_smem_kernel(WalkArgs<T, D> a) {
+    walk_rows<T, D, KIND, RECORD, false, false>(a, 0, 0, 0, nullptr);
 }
 
 // Several toolboxes in one persistent launch: the rows of all instances form one index space
@@ -1127,732 +1200,9 @@ __global__ void __launch_bounds__(1024, 1) wos_walk_batch_kernel(const WalkArgs<
         __syncthreads();
         if (threadIdx.x == 0) s_a = batch[lo];
         __syncthreads();
-        g = walk_rows<T, D, KIND, false, true>(s_a, g, row_off[lo], row_off[lo + 1], gcounter);
+        g = walk_rows<T, D, KIND, false, true, true>(s_a, g, row_off[lo], row_off[lo + 1], gcounter);
         __syncthreads();
     }
-}
-
-// ------------------------------------------------------------------ rows handed over early
-// The row loop above keeps a row in the shared accumulators until its last walk stops: once the
-// row's walks are all handed out, lanes whose walk stopped idle while the longest walks finish
-// (simulated on the ball: a quarter of the lane-steps of a row).  Here the CTA hands the shared
-// accumulators to the next row as soon as the row's walks are all handed out: every warp, at the
-// top of its next iteration, bins its queued walks into the shared row and meets the others at a
-// CTA barrier; the row's partial sums are written to the output (scaled, plain stores), the
-// accumulators cleared, and the next row's ball term and walks start at once.  The walks of the
-// earlier row still in flight (about 8 % of a row's steps) keep their row index in a register and
-// add their remaining contributions to the output in global memory (L2 reductions, after the
-// barrier that orders them behind the stores); when one stops it is binned at once, also in
-// global memory.  The exit counts of such walks make KH's H part stale: one pass after the
-// launch sets it from the counts (H = Hc / N) for all rows.
-template <typename T, int D>
-__device__ __forceinline__ void flush_row_scaled(const WalkArgs<T, D>& a, int row, T r0, T* acc, T* accKH,
-                                                 uint32_t* accH) {
-    const T invN = T(1) / (T)a.N;
-    const T sG = invN / T(2 * D), sGG = invN / (T(2) * r0), sKH = T(D) * invN / r0;
-    const size_t nm = (size_t)a.n * a.m, np = (size_t)a.n * a.p;
-    for (int t = threadIdx.x; t < a.m; t += blockDim.x) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            a.P[c * nm + (size_t)row * a.m + t] = acc[(size_t)c * a.m + t] * sGG;
-            acc[(size_t)c * a.m + t] = T(0);
-        }
-        a.P[D * nm + (size_t)row * a.m + t] = acc[(size_t)D * a.m + t] * sG;
-        acc[(size_t)D * a.m + t] = T(0);
-    }
-    for (int t = threadIdx.x; t < a.p; t += blockDim.x) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-            a.KH[c * np + (size_t)row * a.p + t] = accKH[(size_t)c * a.p + t] * sKH;
-            accKH[(size_t)c * a.p + t] = T(0);
-        }
-        a.Hc[(size_t)row * a.p + t] = accH[t];
-        accH[t] = 0u;
-    }
-}
-
-// ball term of the first sphere of `row` (all threads of the CTA, into the shared accumulators)
-template <typename T, int D, bool RECORD>
-__device__ __forceinline__ void ball_term(const WalkArgs<T, D>& a, int row, const T* xi, T r0,
-                                          const Lookup<T, D>& V, const uint16_t* candK, int K, T* acc) {
-    const T r02 = r0 * r0;
-    for (int64_t l = threadIdx.x; l < a.N; l += blockDim.x) {
-        T S, Zb[D], pt[D];
-        draw_ball<T, D>((uint32_t)l, (uint32_t)row, a.inst, a.k0, a.k1, S, Zb);
-        const T wsum = (D == 2) ? T(1) + S : T(1) + S + S * S;
-#pragma unroll
-        for (int c = 0; c < D; ++c) pt[c] = xi[c] + r0 * S * Zb[c];
-        const int jb = K > 0 ? nearest_fixed(V, candK, K, pt, a.m) : nearest_or_scan(V, a.m, pt);
-#pragma unroll
-        for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + jb], r02 * wsum * Zb[c]);
-        if (RECORD) atomicXor(&a.rec_vhash[(size_t)row * a.N + l], cellmix(0xFFFFFFFFu, jb));
-    }
-}
-
-template <typename T, int D, int KIND, bool RECORD>
-__device__ __forceinline__ void walk_rows_handover(const WalkArgs<T, D>& a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    // shared layout as in walk_rows
-    T* acc = reinterpret_cast<T*>(smem_raw);
-    T* accKH = acc + (size_t)(D + 1) * a.m;
-    uint32_t* accH = reinterpret_cast<uint32_t*>(accKH + (size_t)D * a.p);
-    T* s_sdf = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(accH + a.p) + 15) & ~uintptr_t(15));
-    const int nwarps = blockDim.x >> 5;
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WalkQueue<T, D> q;
-    q.X = s_sdf + ((a.sdf_len + 3) & ~3);
-    q.L = reinterpret_cast<uint32_t*>(q.X + (size_t)nwarps * kQueue * D);
-    const size_t qr = RECORD ? (size_t)nwarps * kQueue : 0;
-    q.vh = q.L + (size_t)nwarps * kQueue;
-    q.K = q.vh + qr;
-    q.mass = reinterpret_cast<T*>(q.K + qr);
-    unsigned char* s_v = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(q.mass + qr) + 15) & ~uintptr_t(15));
-    __shared__ int s_row;
-    __shared__ unsigned int s_walk;
-    __shared__ int s_switch;
-
-    for (int t = threadIdx.x; t < a.sdf_len; t += blockDim.x) s_sdf[t] = a.sdf[t];
-    Lookup<T, D> V = a.V;
-    const uint16_t* candK = a.v_candK;
-    if (a.v_in_smem) {
-        T* vp = reinterpret_cast<T*>(s_v);
-        for (int t = threadIdx.x; t < (a.m + 1) * D; t += blockDim.x) vp[t] = a.V.pts[t];
-        V.pts = vp;
-        if (a.v_K > 0) {
-            uint16_t* vk = reinterpret_cast<uint16_t*>(vp + (size_t)(a.m + 1) * D);
-            for (int64_t t = threadIdx.x; t < (int64_t)a.v_ncell * a.v_K; t += blockDim.x) vk[t] = a.v_candK[t];
-            candK = vk;
-        } else {
-            int* vs = reinterpret_cast<int*>(vp + (size_t)(a.m + 1) * D);
-            int* vc = vs + a.v_ncell + 1;
-            for (int t = threadIdx.x; t <= a.v_ncell; t += blockDim.x) vs[t] = a.V.start[t];
-            for (int64_t t = threadIdx.x; t < a.v_ncand; t += blockDim.x) vc[t] = a.V.cand[t];
-            V.start = vs; V.cand = vc;
-        }
-    }
-    const int K = a.v_K;
-    for (int t = threadIdx.x; t < (D + 1) * a.m; t += blockDim.x) acc[t] = T(0);
-    for (int t = threadIdx.x; t < D * a.p; t += blockDim.x) accKH[t] = T(0);
-    for (int t = threadIdx.x; t < a.p; t += blockDim.x) accH[t] = 0u;
-    if (threadIdx.x == 0) {
-        s_row = atomicAdd(a.row_counter, 1);
-        s_walk = 0u;
-        s_switch = 0;
-    }
-    __syncthreads();
-    int row = s_row;
-    if (row >= a.n) return;
-    T xi[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) xi[c] = a.x[(size_t)row * D + c];
-    T r0 = a.r0[row];
-    ball_term<T, D, RECORD>(a, row, xi, r0, V, candK, K, acc);
-
-    unsigned long long my_steps = 0, my_capped = 0;
-    const T invN = T(1) / (T)a.N;
-    const size_t nm = (size_t)a.n * a.m, np = (size_t)a.n * a.p;
-    volatile int* vswitch = &s_switch;
-    bool last = false;                     // no row left to hand the accumulators to
-    uint32_t l = atomicAdd(&s_walk, 1u);
-    bool have = l < (uint64_t)a.N;
-    if (!have) *vswitch = 1;
-    int lrow = row;                        // row of the lane's walk
-    T X[D], U0[D], mass = T(0);
-    uint32_t k = 0, vh = 0u;
-    int qn = 0;
-    const unsigned below = (1u << lane) - 1u;
-#pragma unroll
-    for (int c = 0; c < D; ++c) { X[c] = xi[c]; U0[c] = T(0); }
-    for (;;) {
-        const bool any_walk = __any_sync(0xffffffffu, have);
-        if (!last && (!any_walk || __shfl_sync(0xffffffffu, *vswitch, 0))) {
-            // the row's walks are all handed out: hand the accumulators over
-            if (lane == 0) *vswitch = 1;
-            for (int e = lane; e < qn; e += 32) bin_stopped<T, D, RECORD>(a, q, wid * kQueue + e, row, accKH, accH);
-            qn = 0;
-            __syncwarp();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                const int nxt = atomicAdd(a.row_counter, 1);
-                s_row = nxt;
-                s_walk = 0u;                // (unused once no row is left)
-                s_switch = 0;
-            }
-            __syncthreads();
-            const int nxt = s_row;
-            if (nxt >= a.n) {
-                last = true;                // the walks in flight finish into the shared row
-            } else {
-                flush_row_scaled<T, D>(a, row, r0, acc, accKH, accH);
-                __syncthreads();            // stores and clears before any later addition
-                row = nxt;
-#pragma unroll
-                for (int c = 0; c < D; ++c) xi[c] = a.x[(size_t)row * D + c];
-                r0 = a.r0[row];
-                ball_term<T, D, RECORD>(a, row, xi, r0, V, candK, K, acc);
-                if (!have) {
-                    l = atomicAdd(&s_walk, 1u);
-                    have = l < (uint64_t)a.N;
-                    if (!have) *vswitch = 1;
-                    lrow = row;
-                    k = 0;
-#pragma unroll
-                    for (int c = 0; c < D; ++c) X[c] = xi[c];
-                }
-            }
-            continue;
-        }
-        if (!any_walk) break;               // last row: every walk has stopped
-        T r = r0;
-        if (have && k > 0) {
-            if (KIND == SDF_POLYGON && a.e_cnt) r = polygon_dist_grid<T, D>(a, s_sdf, X);
-            else r = Sdf<T, D, KIND>::eval(s_sdf, a.nsdf, X);
-        } else if (have && lrow != row) {
-            r = a.r0[lrow];                 // taken just before a hand-over (rows of few walks)
-        }
-        const bool stop = have && k > 0 && (r < a.eps || (int64_t)k > a.max_steps);
-        const bool cur = lrow == row;
-        const unsigned sm = __ballot_sync(0xffffffffu, stop && cur);
-        if (stop) {
-            my_steps += k;
-            my_capped += (r >= a.eps);
-            if (cur) {
-                const int slot = wid * kQueue + qn + __popc(sm & below);
-#pragma unroll
-                for (int c = 0; c < D; ++c) q.X[slot * D + c] = X[c];
-                q.L[slot] = l;
-                if (RECORD) { q.mass[slot] = mass / T(2 * D); q.vh[slot] = vh; q.K[slot] = k - 1; }
-            } else {
-                // a walk of an earlier row: binned at once into that row's output
-                T U[D];
-                draw_first_direction<T, D>(l, (uint32_t)lrow, a.inst, a.k0, a.k1, U);
-                const int jz = nearest_or_scan(a.Z, a.p, X);
-                const T sKH = T(D) * invN / a.r0[lrow];
-                atomicAdd(&a.Hc[(size_t)lrow * a.p + jz], 1u);
-#pragma unroll
-                for (int c = 0; c < D; ++c) atomicAdd(&a.KH[c * np + (size_t)lrow * a.p + jz], U[c] * sKH);
-                if (RECORD) {
-                    const size_t ri = (size_t)lrow * a.N + l;
-                    a.rec_exit[ri] = jz;
-#pragma unroll
-                    for (int c = 0; c < D; ++c) a.rec_xexit[ri * D + c] = X[c];
-                    a.rec_mass[ri] = mass / T(2 * D);
-                    a.rec_steps[ri] = (int32_t)(k - 1);
-                    atomicXor(&a.rec_vhash[ri], vh);
-                }
-            }
-            if (RECORD) { vh = 0u; mass = T(0); }
-            if (!last) {
-                l = atomicAdd(&s_walk, 1u);
-                have = l < (uint64_t)a.N;
-                if (!have) *vswitch = 1;
-            } else {
-                have = false;               // no row left: nothing more to hand out
-            }
-            lrow = row;
-#pragma unroll
-            for (int c = 0; c < D; ++c) X[c] = xi[c];
-            k = 0;
-            r = r0;
-        }
-        qn += __popc(sm);
-        if (have) {
-            T R, Zs[D], U[D], pt[D];
-            draw_step<T, D>(l, k, (uint32_t)lrow, a.inst, a.k0, a.k1, R, Zs, U);
-            const T rR = r * R;
-#pragma unroll
-            for (int c = 0; c < D; ++c) pt[c] = X[c] + rR * Zs[c];
-            const int j = K > 0 ? nearest_fixed(V, candK, K, pt, a.m) : nearest_or_scan(V, a.m, pt);
-            const T r2 = r * r;
-            if (lrow == row) {
-                atomicAdd(&acc[(size_t)D * a.m + j], r2);
-                if (k > 0) {
-#pragma unroll
-                    for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + j], U0[c] * r2);
-                }
-            } else {
-                const T sGG = invN / (T(2) * a.r0[lrow]);
-                atomicAdd(&a.P[D * nm + (size_t)lrow * a.m + j], r2 * (invN / T(2 * D)));
-                if (k > 0) {
-#pragma unroll
-                    for (int c = 0; c < D; ++c) atomicAdd(&a.P[c * nm + (size_t)lrow * a.m + j], U0[c] * r2 * sGG);
-                }
-            }
-            if (k == 0) {
-#pragma unroll
-                for (int c = 0; c < D; ++c) U0[c] = U[c];
-            }
-#pragma unroll
-            for (int c = 0; c < D; ++c) X[c] += r * U[c];
-            if (RECORD) { mass += r2; vh ^= cellmix(k, (uint32_t)j); }
-            ++k;
-        }
-        __syncwarp();
-        while (qn >= 32) {
-            bin_stopped<T, D, RECORD>(a, q, wid * kQueue + qn - 1 - lane, row, accKH, accH);
-            qn -= 32;
-        }
-        __syncwarp();
-    }
-    // last row: drain the queues, then write it
-    for (int e = lane; e < qn; e += 32) bin_stopped<T, D, RECORD>(a, q, wid * kQueue + e, row, accKH, accH);
-    __syncwarp();
-    __syncthreads();
-    flush_row_scaled<T, D>(a, row, r0, acc, accKH, accH);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_steps += __shfl_down_sync(0xffffffffu, my_steps, o);
-        my_capped += __shfl_down_sync(0xffffffffu, my_capped, o);
-    }
-    if (lane == 0) {
-        atomicAdd(a.stat_steps, my_steps);
-        if (my_capped) atomicAdd(a.stat_capped, my_capped);
-    }
-}
-
-template <typename T, int D, int KIND, bool RECORD>
-__global__ void __launch_bounds__(1024, 1) wos_walk_handover_kernel(WalkArgs<T, D> a) {
-    walk_rows_handover<T, D, KIND, RECORD>(a);
-}
-
-// KH's H part from the exit counts (after the handover kernel): H = Hc / N
-template <typename T>
-__global__ void h_from_counts_kernel(const uint32_t* __restrict__ Hc, T* __restrict__ H, int64_t count, T invN) {
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
-        H[t] = (T)Hc[t] * invN;
-}
-
-// ------------------------------------------------------------------ streamed rows
-// The row loop above makes every lane of a CTA wait at the end of each row for the row's
-// longest walk (23 % of the issued lane slots on the square, 40 % on the ball).  Here a CTA
-// keeps up to kSlots rows in flight: a lane that finds the current row's walks all handed out
-// takes a walk of the next row straight away.  One row at a time owns the shared-memory
-// accumulators; walks of the other rows add their contributions, already scaled, to the output
-// rows in global memory (which the build zeroes first).  A row is finished by the warp that
-// bins its last walk: it adds the shared accumulators to the row's global part (or stores them
-// when the row had none), clears them and hands them to the row currently taking walks.
-// The ball term of a walk (Prop. 2.6 (ii)) is path independent, so it is binned together with
-// the walk's exit, 32 walks at a time, from the warp's queue.
-constexpr int kSlots = 4;                     // rows in flight per CTA
-constexpr int kSlotFree = -2, kSlotNone = -1; // slot states besides a row index
-constexpr unsigned kIdleLimit = 1u << 26;     // idle iterations of a warp before it gives up
-
-struct StreamState {
-    int row[kSlots];           // row index, kSlotFree (reusable), kSlotNone (no rows left), kSlotOpening
-    int seq[kSlots];           // sequence number of the slot's row (rows are opened in sequence)
-    unsigned next[kSlots];     // next walk index to hand out
-    unsigned done[kSlots];     // walks binned (ball term and exit)
-    int global_part[kSlots];   // a walk of the row accumulated in global memory
-    int fetch_seq;             // sequence number of the row handing out walks
-    int pending;               // sequence number waiting for its slot to be freed, or -1
-    int smem_slot;             // slot whose row owns the shared accumulators (-1: none)
-    unsigned epoch;            // bumped when a row's walks are all handed out
-};
-constexpr int kSlotOpening = -3;
-
-// slot s (claimed: kSlotOpening) gets the next row of the grid-wide counter as row number `seq`
-template <typename T, int D>
-__device__ __forceinline__ void stream_fill(StreamState& S, const WalkArgs<T, D>& a, int s, int seq) {
-    const int R = atomicAdd(a.row_counter, 1);
-    S.seq[s] = seq;
-    if (R >= a.n) {
-        S.next[s] = 0xFFFFFFFFu;
-        __threadfence_block();
-        atomicExch(&S.row[s], kSlotNone);
-    } else {
-        S.done[s] = 0u;
-        S.global_part[s] = 0;
-        atomicCAS(&S.smem_slot, -1, s);
-        __threadfence_block();
-        atomicExch(&S.row[s], R);             // the row before the walks: a lane that takes a walk reads it
-        __threadfence_block();
-        atomicExch(&S.next[s], 0u);
-    }
-    __threadfence_block();
-    atomicExch(&S.fetch_seq, seq);
-}
-
-// row number `seq` goes to slot seq % kSlots once that slot is free: now, or by the warp that
-// frees it (the note in `pending`); exactly one caller fills the slot
-template <typename T, int D>
-__device__ __forceinline__ void stream_open(StreamState& S, const WalkArgs<T, D>& a, int seq) {
-    const int s = seq % kSlots;
-    if (atomicCAS(&S.row[s], kSlotFree, kSlotOpening) == kSlotFree) {
-        stream_fill(S, a, s, seq);
-        return;
-    }
-    atomicExch(&S.pending, seq);
-    if (atomicCAS(&S.row[s], kSlotFree, kSlotOpening) == kSlotFree) {     // freed in between
-        atomicCAS(&S.pending, seq, -1);
-        stream_fill(S, a, s, seq);
-    }
-}
-
-// called after slot s was freed: fills it when a row number waits for it
-template <typename T, int D>
-__device__ __forceinline__ void stream_freed(StreamState& S, const WalkArgs<T, D>& a, int s) {
-    const int p = *(volatile int*)&S.pending;
-    if (p < 0 || p % kSlots != s) return;
-    if (atomicCAS(&S.pending, p, -1) != p) return;
-    if (atomicCAS(&S.row[s], kSlotFree, kSlotOpening) == kSlotFree) stream_fill(S, a, s, p);
-}
-
-// a walk for this lane: (slot, walk index) or false
-template <typename T, int D>
-__device__ __forceinline__ bool stream_acquire(StreamState& S, const WalkArgs<T, D>& a, int& slot, uint32_t& l) {
-    const int f = (*(volatile int*)&S.fetch_seq) % kSlots;
-    const unsigned N = (unsigned)a.N;
-    if (*(volatile unsigned*)&S.next[f] >= N) return false;
-    const unsigned w = atomicAdd(&S.next[f], 1u);
-    if (w >= N) return false;
-    __threadfence_block();
-    if (w == N - 1) {
-        // this lane took the row's last walk: it opens the next row
-        atomicAdd(&S.epoch, 1u);
-        stream_open(S, a, *(volatile int*)&S.seq[f] + 1);
-    }
-    slot = f;
-    l = w;
-    return true;
-}
-
-// nothing left to hand out, in this CTA, ever
-__device__ __forceinline__ bool stream_finished(StreamState& S) {
-    const int f = (*(volatile int*)&S.fetch_seq) % kSlots;
-    return *(volatile int*)&S.row[f] == kSlotNone;
-}
-
-template <typename T, int D>
-struct StreamQueue {
-    T* X;            // [warps][kQueue][D] stopping point
-    T* U;            // [warps][kQueue][D] first direction U_0
-    uint32_t* L;     // [warps][kQueue] walk index
-    uint32_t* M;     // [warps][kQueue] slot | smem-mode << 3
-    uint32_t* vh;    // records only
-    uint32_t* K;
-    T* mass;
-};
-
-template <typename T, int D>
-__host__ __device__ constexpr size_t stream_queue_bytes(int nwarps, bool record) {
-    return (size_t)nwarps * kQueue * (2 * D * sizeof(T) + 2 * sizeof(uint32_t) +
-                                      (record ? 2 * sizeof(uint32_t) + sizeof(T) : 0));
-}
-
-// ball term and exit of one queued walk; returns the slot when this walk was its row's last
-template <typename T, int D, bool RECORD>
-__device__ __forceinline__ int stream_bin(const WalkArgs<T, D>& a, StreamState& S, const StreamQueue<T, D>& q, int e,
-                                          const Lookup<T, D>& V, const uint16_t* candK, int K, T* acc, T* accKH,
-                                          uint32_t* accH) {
-    const uint32_t meta = q.M[e], l = q.L[e];
-    const int slot = (int)(meta & 7u);
-    // the row's contributions go where its accumulators are now: the shared ones while the row
-    // owns them (it keeps them until all its walks are binned), else the output in global memory
-    const bool sm = *(volatile int*)&S.smem_slot == (int)(meta & 7u);
-    if (!sm) S.global_part[meta & 7u] = 1;
-    const int R = S.row[slot];
-    T X[D], U[D], xi[D];
-#pragma unroll
-    for (int c = 0; c < D; ++c) { X[c] = q.X[e * D + c]; U[c] = q.U[e * D + c]; xi[c] = a.x[(size_t)R * D + c]; }
-    const T r0 = a.r0[R];
-    const T invN = T(1) / (T)a.N;
-    // ball term of the first sphere: gradG += (r0/2) (sum_k S^k) Z at the V cell of x_i + r0 S Z
-    T Sb, Zb[D], pt[D];
-    draw_ball<T, D>(l, (uint32_t)R, a.inst, a.k0, a.k1, Sb, Zb);
-    const T wsum = (D == 2) ? T(1) + Sb : T(1) + Sb + Sb * Sb;
-#pragma unroll
-    for (int c = 0; c < D; ++c) pt[c] = xi[c] + r0 * Sb * Zb[c];
-    const int jb = K > 0 ? nearest_fixed(V, candK, K, pt, a.m) : nearest_or_scan(V, a.m, pt);
-    const int jz = nearest_or_scan(a.Z, a.p, X);
-    const size_t nm = (size_t)a.n * a.m, np = (size_t)a.n * a.p;
-    if (sm) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + jb], r0 * r0 * wsum * Zb[c]);
-        atomicAdd(&accH[jz], 1u);
-#pragma unroll
-        for (int c = 0; c < D; ++c) atomicAdd(&accKH[(size_t)c * a.p + jz], U[c]);
-    } else {
-        const T sGG = invN / (T(2) * r0), sKH = T(D) * invN / r0;
-#pragma unroll
-        for (int c = 0; c < D; ++c) atomicAdd(&a.P[c * nm + (size_t)R * a.m + jb], r0 * r0 * wsum * Zb[c] * sGG);
-        atomicAdd(&a.Hc[(size_t)R * a.p + jz], 1u);
-#pragma unroll
-        for (int c = 0; c < D; ++c) atomicAdd(&a.KH[c * np + (size_t)R * a.p + jz], U[c] * sKH);
-    }
-    if (RECORD) {
-        const size_t ri = (size_t)R * a.N + l;
-        a.rec_exit[ri] = jz;
-#pragma unroll
-        for (int c = 0; c < D; ++c) a.rec_xexit[ri * D + c] = X[c];
-        a.rec_mass[ri] = q.mass[e];
-        a.rec_steps[ri] = (int32_t)q.K[e];
-        a.rec_vhash[ri] = q.vh[e] ^ cellmix(0xFFFFFFFFu, (uint32_t)jb);
-    }
-    return slot | (sm ? 0 : 8);
-}
-
-// the warp finishes the row of `slot` (all its walks binned)
-template <typename T, int D>
-__device__ __forceinline__ void stream_flush(const WalkArgs<T, D>& a, StreamState& S, int slot, T* acc, T* accKH,
-                                             uint32_t* accH) {
-    const int lane = threadIdx.x & 31;
-    __threadfence();
-    const int R = S.row[slot];
-    const bool own = *(volatile int*)&S.smem_slot == slot;
-    const bool gp = *(volatile int*)&S.global_part[slot] != 0;
-    const T invN = T(1) / (T)a.N;
-    const T r0 = a.r0[R];
-    const T sG = invN / T(2 * D), sGG = invN / (T(2) * r0), sKH = T(D) * invN / r0;
-    const size_t nm = (size_t)a.n * a.m, np = (size_t)a.n * a.p;
-    if (own) {
-        for (int t = lane; t < a.m; t += 32) {
-#pragma unroll
-            for (int c = 0; c <= D; ++c) {
-                T* dst = &a.P[c * nm + (size_t)R * a.m + t];
-                T v = acc[(size_t)c * a.m + t] * (c < D ? sGG : sG);
-                if (gp) v += __ldcg(dst);
-                *dst = v;
-                acc[(size_t)c * a.m + t] = T(0);
-            }
-        }
-        for (int t = lane; t < a.p; t += 32) {
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-                T* dst = &a.KH[c * np + (size_t)R * a.p + t];
-                T v = accKH[(size_t)c * a.p + t] * sKH;
-                if (gp) v += __ldcg(dst);
-                *dst = v;
-                accKH[(size_t)c * a.p + t] = T(0);
-            }
-            uint32_t h = accH[t];
-            if (gp) h += __ldcg(&a.Hc[(size_t)R * a.p + t]);
-            a.Hc[(size_t)R * a.p + t] = h;
-            a.KH[D * np + (size_t)R * a.p + t] = (T)h * invN;
-            accH[t] = 0u;
-        }
-        __syncwarp();
-        __threadfence_block();
-        if (lane == 0) {
-            // the accumulators go to the row taking walks, if it still has walks to hand out
-            const int f = (*(volatile int*)&S.fetch_seq) % kSlots;
-            const int nxt = (f != slot && *(volatile int*)&S.row[f] >= 0) ? f : -1;
-            atomicExch(&S.smem_slot, nxt);
-        }
-    } else {
-        for (int t = lane; t < a.p; t += 32)
-            a.KH[D * np + (size_t)R * a.p + t] = (T)__ldcg(&a.Hc[(size_t)R * a.p + t]) * invN;
-    }
-    __syncwarp();
-    __threadfence_block();
-    if (lane == 0) {
-        S.next[slot] = 0xFFFFFFFFu;
-        __threadfence_block();
-        atomicExch(&S.row[slot], kSlotFree);
-        stream_freed(S, a, slot);
-    }
-    __syncwarp();
-}
-
-template <typename T, int D, int KIND, bool RECORD>
-__device__ __forceinline__ void walk_stream(const WalkArgs<T, D>& a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* acc = reinterpret_cast<T*>(smem_raw);
-    T* accKH = acc + (size_t)(D + 1) * a.m;
-    uint32_t* accH = reinterpret_cast<uint32_t*>(accKH + (size_t)D * a.p);
-    T* s_sdf = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(accH + a.p) + 15) & ~uintptr_t(15));
-    const int nwarps = blockDim.x >> 5;
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    StreamQueue<T, D> q;
-    q.X = s_sdf + ((a.sdf_len + 3) & ~3);
-    q.U = q.X + (size_t)nwarps * kQueue * D;
-    q.L = reinterpret_cast<uint32_t*>(q.U + (size_t)nwarps * kQueue * D);
-    q.M = q.L + (size_t)nwarps * kQueue;
-    const size_t qr = RECORD ? (size_t)nwarps * kQueue : 0;
-    q.vh = q.M + (size_t)nwarps * kQueue;
-    q.K = q.vh + qr;
-    q.mass = reinterpret_cast<T*>(q.K + qr);
-    unsigned char* s_v = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(q.mass + qr) + 15) & ~uintptr_t(15));
-    __shared__ StreamState S;
-
-    for (int t = threadIdx.x; t < a.sdf_len; t += blockDim.x) s_sdf[t] = a.sdf[t];
-    Lookup<T, D> V = a.V;
-    const uint16_t* candK = a.v_candK;
-    if (a.v_in_smem) {
-        T* vp = reinterpret_cast<T*>(s_v);
-        for (int t = threadIdx.x; t < (a.m + 1) * D; t += blockDim.x) vp[t] = a.V.pts[t];
-        V.pts = vp;
-        if (a.v_K > 0) {
-            uint16_t* vk = reinterpret_cast<uint16_t*>(vp + (size_t)(a.m + 1) * D);
-            for (int64_t t = threadIdx.x; t < (int64_t)a.v_ncell * a.v_K; t += blockDim.x) vk[t] = a.v_candK[t];
-            candK = vk;
-        } else {
-            int* vs = reinterpret_cast<int*>(vp + (size_t)(a.m + 1) * D);
-            int* vc = vs + a.v_ncell + 1;
-            for (int t = threadIdx.x; t <= a.v_ncell; t += blockDim.x) vs[t] = a.V.start[t];
-            for (int64_t t = threadIdx.x; t < a.v_ncand; t += blockDim.x) vc[t] = a.V.cand[t];
-            V.start = vs; V.cand = vc;
-        }
-    }
-    const int K = a.v_K;
-    for (int t = threadIdx.x; t < (D + 1) * a.m; t += blockDim.x) acc[t] = T(0);
-    for (int t = threadIdx.x; t < D * a.p; t += blockDim.x) accKH[t] = T(0);
-    for (int t = threadIdx.x; t < a.p; t += blockDim.x) accH[t] = 0u;
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kSlots; ++s) {
-            S.row[s] = kSlotFree; S.seq[s] = -1; S.next[s] = 0xFFFFFFFFu; S.done[s] = 0u; S.global_part[s] = 0;
-        }
-        S.smem_slot = -1;
-        S.pending = -1;
-        S.epoch = 0u;
-        S.fetch_seq = 0;
-        stream_open(S, a, 0);        // the first row goes to slot 0 and owns the accumulators
-    }
-    __syncthreads();
-
-    const unsigned N = (unsigned)a.N;
-    const T invN = T(1) / (T)a.N;
-    const T sG = invN / T(2 * D);
-    const unsigned below = (1u << lane) - 1u;
-    unsigned long long my_steps = 0, my_capped = 0;
-    unsigned seen_epoch = *(volatile unsigned*)&S.epoch;
-    unsigned idle = 0;
-    // lane state
-    bool have = false, sm = false;
-    int slot = 0, R = 0;
-    uint32_t l = 0, k = 0, vh = 0u;
-    T X[D], U0[D], r0 = T(0), mass = T(0), sGG = T(0);
-#pragma unroll
-    for (int c = 0; c < D; ++c) { X[c] = T(0); U0[c] = T(0); }
-    int qn = 0;
-    auto start_walk = [&]() {
-        if (stream_acquire(S, a, slot, l)) {
-            have = true;
-            R = S.row[slot];
-            sm = false;
-#pragma unroll
-            for (int c = 0; c < D; ++c) X[c] = a.x[(size_t)R * D + c];
-            r0 = a.r0[R];
-            sGG = invN / (T(2) * r0);
-            k = 0;
-        }
-    };
-    for (;;) {
-        if (!have) start_walk();
-        const bool busy = have || qn > 0;
-        if (!__any_sync(0xffffffffu, busy)) {
-            if (stream_finished(S)) break;
-            if (++idle > kIdleLimit) { if (lane == 0) atomicAdd(a.stat_error, 1ull); break; }
-            __nanosleep(200);
-            continue;
-        }
-        idle = 0;
-        T r = r0;
-        if (have && k > 0) {
-            if (KIND == SDF_POLYGON && a.e_cnt) r = polygon_dist_grid<T, D>(a, s_sdf, X);
-            else r = Sdf<T, D, KIND>::eval(s_sdf, a.nsdf, X);
-        }
-        const bool stop = have && k > 0 && (r < a.eps || (int64_t)k > a.max_steps);
-        const unsigned smk = __ballot_sync(0xffffffffu, stop);
-        bool urgent = false;
-        if (stop) {
-            const int e = wid * kQueue + qn + __popc(smk & below);
-#pragma unroll
-            for (int c = 0; c < D; ++c) { q.X[e * D + c] = X[c]; q.U[e * D + c] = U0[c]; }
-            q.L[e] = l;
-            q.M[e] = (uint32_t)slot | (sm ? 8u : 0u);
-            if (RECORD) {
-                q.mass[e] = mass / T(2 * D); q.vh[e] = vh; q.K[e] = k - 1;
-                vh = 0u; mass = T(0);
-            }
-            my_steps += k;
-            my_capped += (r >= a.eps);
-            urgent = *(volatile unsigned*)&S.next[slot] >= N;
-            have = false;
-            start_walk();
-            r = r0;
-        }
-        qn += __popc(smk);
-        if (have) {
-            T Rr, Zs[D], U[D], pt[D];
-            draw_step<T, D>(l, k, (uint32_t)R, a.inst, a.k0, a.k1, Rr, Zs, U);
-            const T rR = r * Rr;
-#pragma unroll
-            for (int c = 0; c < D; ++c) pt[c] = X[c] + rR * Zs[c];
-            const int j = K > 0 ? nearest_fixed(V, candK, K, pt, a.m) : nearest_or_scan(V, a.m, pt);
-            const T r2 = r * r;
-            if (k == 0) {
-#pragma unroll
-                for (int c = 0; c < D; ++c) U0[c] = U[c];
-            }
-            sm = *(volatile int*)&S.smem_slot == slot;
-            if (!sm) S.global_part[slot] = 1;
-            if (sm) {
-                atomicAdd(&acc[(size_t)D * a.m + j], r2);
-                if (k > 0) {
-#pragma unroll
-                    for (int c = 0; c < D; ++c) atomicAdd(&acc[(size_t)c * a.m + j], U0[c] * r2);
-                }
-            } else {
-                const size_t nm = (size_t)a.n * a.m;
-                T* prow = a.P + (size_t)R * a.m + j;
-                atomicAdd(prow + D * nm, r2 * sG);
-                if (k > 0) {
-                    const T w = r2 * sGG;
-#pragma unroll
-                    for (int c = 0; c < D; ++c) atomicAdd(prow + c * nm, U0[c] * w);
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < D; ++c) X[c] += r * U[c];
-            if (RECORD) { mass += r2; vh ^= cellmix(k, (uint32_t)j); }
-            ++k;
-        }
-        // binning of queued walks: 32 at a time, or everything when a row waits for it
-        __syncwarp();
-        const unsigned ep = *(volatile unsigned*)&S.epoch;
-        const bool drain_all = __any_sync(0xffffffffu, urgent) || ep != seen_epoch || !__any_sync(0xffffffffu, have);
-        seen_epoch = ep;
-        int finished = -1;
-        while (qn >= 32 || (drain_all && qn > 0)) {
-            const int take = qn >= 32 ? 32 : qn;
-            const int e = qn - 1 - lane;
-            int res = -1;
-            if (lane < take) res = stream_bin<T, D, RECORD>(a, S, q, wid * kQueue + e, V, candK, K, acc, accKH, accH);
-            // global-mode contributions must be visible before the row can be finished
-            if (__any_sync(0xffffffffu, res >= 8)) __threadfence();
-            else __threadfence_block();
-            if (res >= 0) {
-                const int s = res & 7;
-                if (atomicAdd(&S.done[s], 1u) == N - 1) finished = s;
-            }
-            qn -= take;
-            __syncwarp();
-            unsigned fm = __ballot_sync(0xffffffffu, finished >= 0);
-            while (fm) {
-                const int src = __ffs(fm) - 1;
-                fm &= fm - 1;
-                const int s = __shfl_sync(0xffffffffu, finished, src);
-                stream_flush<T, D>(a, S, s, acc, accKH, accH);
-            }
-            finished = -1;
-        }
-        __syncwarp();
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        my_steps += __shfl_down_sync(0xffffffffu, my_steps, o);
-        my_capped += __shfl_down_sync(0xffffffffu, my_capped, o);
-    }
-    if (lane == 0) {
-        atomicAdd(a.stat_steps, my_steps);
-        if (my_capped) atomicAdd(a.stat_capped, my_capped);
-    }
-}
-
-template <typename T, int D, int KIND, bool RECORD>
-__global__ void __launch_bounds__(1024, 1) wos_walk_stream_kernel(WalkArgs<T, D> a) {
-    walk_stream<T, D, KIND, RECORD>(a);
 }
 
 // ------------------------------------------------------------------ host side
@@ -1987,17 +1337,29 @@ struct BuildContext {
     int* d_counter = nullptr;
     unsigned long long* d_stats = nullptr;
     unsigned int* d_counts = nullptr;
+    void* d_acc = nullptr;           // G / grad G accumulators of the rows in flight (walk_kernel 1)
+    size_t acc_cap = 0;
     ~BuildContext() {
         V.release(); Z.release(); V2.release(); W.release();
         ::ewos::dev_free(d_sdf); ::ewos::dev_free(d_xT); ::ewos::dev_free(d_r0); ::ewos::dev_free(d_counter); ::ewos::dev_free(d_stats); ::ewos::dev_free(d_counts);
-        ::ewos::dev_free(d_vtx); ::ewos::dev_free(d_egrid);
+        ::ewos::dev_free(d_vtx); ::ewos::dev_free(d_egrid); ::ewos::dev_free(d_acc);
+    }
+    // at least `bytes` of accumulator space (kept for the rest of the build)
+    cudaError_t ensure_acc(size_t bytes) {
+        if (acc_cap >= bytes) return cudaSuccess;
+        ::ewos::dev_free(d_acc);
+        d_acc = nullptr;
+        acc_cap = 0;
+        cudaError_t e = ::ewos::dev_alloc(&d_acc, bytes);
+        if (e == cudaSuccess) acc_cap = bytes;
+        return e;
     }
 };
 
-// the row kernels: 1 one row per CTA at a time, 3 rows handed over early
+// the row kernels: 1 accumulators in global memory, 2 in shared memory
 template <typename T, int D, int KIND, bool RECORD>
 static void (*row_kernel(int kern))(WalkArgs<T, D>) {
-    if (kern == 3) return wos_walk_handover_kernel<T, D, KIND, RECORD>;
+    if (kern == 2) return wos_walk_smem_kernel<T, D, KIND, RECORD>;
     return wos_walk_kernel<T, D, KIND, RECORD>;
 }
 
@@ -2023,37 +1385,6 @@ static int max_ctas_per_sm(int tpb, size_t smem, int kern = 1) {
     auto k = row_kernel<T, D, KIND, false>(kern);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, tpb, smem);
-    return nb;
-}
-
-template <typename T, int D, int KIND, bool RECORD>
-static cudaError_t launch_stream_walks(const WalkArgs<T, D>& a, int grid, int tpb, size_t smem, cudaStream_t st) {
-    auto k = wos_walk_stream_kernel<T, D, KIND, RECORD>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    ::ewos::note_launch(), k<<<grid, tpb, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename T, int D, int KIND>
-static cudaError_t dispatch_stream_walks(const WalkArgs<T, D>& a, bool rec, int grid, int tpb, size_t smem,
-                                         cudaStream_t st) {
-    return rec ? launch_stream_walks<T, D, KIND, true>(a, grid, tpb, smem, st)
-               : launch_stream_walks<T, D, KIND, false>(a, grid, tpb, smem, st);
-}
-
-template <typename T, int D, int KIND>
-static int max_stream_ctas_per_sm(int tpb, size_t smem) {
-    int nb = 0;
-    auto k = wos_walk_stream_kernel<T, D, KIND, false>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, tpb, smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
     return nb;
 }
 
@@ -2250,7 +1581,7 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
     EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counter, 0, sizeof(int), st));
     EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_stats, 0, 3 * sizeof(unsigned long long), st));
     a.row_counter = ctx.d_counter; a.stat_steps = ctx.d_stats; a.stat_capped = ctx.d_stats + 1;
-    a.stat_error = ctx.d_stats + 2;
+    a.stat_bad = ctx.d_stats + 2;
     a.rec_exit = tb->rec_exit; a.rec_steps = tb->rec_steps; a.rec_mass = (T*)tb->rec_mass;
     a.rec_vhash = tb->rec_vhash;
     a.rec_xexit = (T*)tb->rec_xexit;
@@ -2289,7 +1620,9 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     TuneKey key{sizeof(T), D, dom->kind, m, p, tb->N, o.record_walks != 0, o.threads_per_block, o.hash_in_smem,
                 o.ctas_per_sm, o.lookup_grid_scale, o.walk_kernel};
     const bool rec = o.record_walks != 0;
-    const size_t acc_bytes = sizeof(T) * ((size_t)(D + 1) * m + (size_t)D * p) + sizeof(uint32_t) * p;
+    // shared memory: the KH / H accumulators, and G / grad G as well for walk_kernel 2
+    const size_t kh_bytes = sizeof(T) * (size_t)D * p + sizeof(uint32_t) * p;
+    const size_t g_bytes = sizeof(T) * (size_t)(D + 1) * m;
     const size_t sdf_bytes = sizeof(T) * ((sdf_len + 3) & ~3);
     const DeviceLookup* Vs[2] = {&ctx.V, &ctx.V2};
     auto v_bytes_of = [&](const DeviceLookup& L) {
@@ -2302,11 +1635,11 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const size_t budget = (size_t)smem_optin - 1024;
     auto base_for = [&](int t, int kern) {
-        const size_t qb = kern == 2 ? stream_queue_bytes<T, D>(t / 32, rec) : queue_bytes<T, D>(t / 32, rec);
-        return (((acc_bytes + 15) & ~size_t(15)) + sdf_bytes + qb + 15) & ~size_t(15);
+        const size_t acc_bytes = kh_bytes + (kern == 2 ? g_bytes : 0);
+        return (((acc_bytes + 15) & ~size_t(15)) + sdf_bytes + queue_bytes<T, D>(t / 32, rec) + 15) & ~size_t(15);
     };
-    // a launch configuration: walk kernel (1 rows, 2 streamed rows), block size, V grid, where
-    // the V lookup lives
+    // a launch configuration: walk kernel (1 accumulators in global memory, 2 in shared memory),
+    // block size, V grid, where the V lookup lives
     struct Cfg { int tpb; int vg; bool v_smem; size_t smem; int per_sm; int grid; int kern; };
     auto configure = [&](int tpb, int vg, int want_smem, int rows, Cfg& c, int kern) -> bool {
         const DeviceLookup& L = *Vs[vg];
@@ -2320,28 +1653,14 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
         if (want_smem == 1 && !c.v_smem) return false;
         c.smem = base + (c.v_smem ? v_bytes_of(L) : 0);
         int ps = 0;
-        if (kern == 2) {
-            if (dom->kind == SDF_BALL) ps = max_stream_ctas_per_sm<T, D, SDF_BALL>(tpb, c.smem);
-            else if (dom->kind == SDF_BOX) ps = max_stream_ctas_per_sm<T, D, SDF_BOX>(tpb, c.smem);
-            else ps = max_stream_ctas_per_sm<T, D, SDF_POLYGON>(tpb, c.smem);
-        } else {
-            if (dom->kind == SDF_BALL) ps = max_ctas_per_sm<T, D, SDF_BALL>(tpb, c.smem, kern);
-            else if (dom->kind == SDF_BOX) ps = max_ctas_per_sm<T, D, SDF_BOX>(tpb, c.smem, kern);
-            else ps = max_ctas_per_sm<T, D, SDF_POLYGON>(tpb, c.smem, kern);
-        }
+        if (dom->kind == SDF_BALL) ps = max_ctas_per_sm<T, D, SDF_BALL>(tpb, c.smem, kern);
+        else if (dom->kind == SDF_BOX) ps = max_ctas_per_sm<T, D, SDF_BOX>(tpb, c.smem, kern);
+        else ps = max_ctas_per_sm<T, D, SDF_POLYGON>(tpb, c.smem, kern);
         if (ps < 1) return false;
         if (o.ctas_per_sm > 0) ps = std::min(ps, o.ctas_per_sm);
         c.per_sm = ps;
         c.grid = std::max(1, std::min(nsm * ps, rows));
         return true;
-    };
-    // streamed rows add to the outputs in global memory: they start from zero
-    const size_t nm = (size_t)n * m, np = (size_t)n * p;
-    auto zero_outputs = [&]() -> cudaError_t {
-        cudaError_t e = cudaMemsetAsync(tb->P, 0, sizeof(T) * (D + 1) * nm, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(tb->KH, 0, sizeof(T) * (D + 1) * np, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(tb->Hc, 0, sizeof(uint32_t) * np, st);
-        return e;
     };
     auto launch = [&](const Cfg& c, WalkArgs<T, D>& args) -> cudaError_t {
         const DeviceLookup& L = *Vs[c.vg];
@@ -2349,10 +1668,14 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
         args.v_ncell = (int)L.grid.ncell; args.v_ncand = L.ncand;
         args.v_K = L.K; args.v_candK = L.candK;
         args.v_in_smem = c.v_smem ? 1 : 0;
-        if (c.kern == 2) {
-            if (dom->kind == SDF_BALL) return dispatch_stream_walks<T, D, SDF_BALL>(args, rec, c.grid, c.tpb, c.smem, st);
-            if (dom->kind == SDF_BOX) return dispatch_stream_walks<T, D, SDF_BOX>(args, rec, c.grid, c.tpb, c.smem, st);
-            return dispatch_stream_walks<T, D, SDF_POLYGON>(args, rec, c.grid, c.tpb, c.smem, st);
+        args.acc_g = nullptr;
+        args.acc_cells = m;
+        if (c.kern == 1) {
+            // one accumulator row per CTA, zeroed by the kernel
+            cudaError_t e = ctx.ensure_acc(sizeof(T) * 4 * (size_t)m * c.grid);
+            if (e != cudaSuccess) return e;
+            args.acc_g = (T*)ctx.d_acc;
+            args.acc_len = (int64_t)(ctx.acc_cap / sizeof(T));
         }
         if (dom->kind == SDF_BALL) return dispatch_walks<T, D, SDF_BALL>(args, rec, c.grid, c.tpb, c.smem, st, c.kern);
         if (dom->kind == SDF_BOX) return dispatch_walks<T, D, SDF_BOX>(args, rec, c.grid, c.tpb, c.smem, st, c.kern);
@@ -2362,7 +1685,7 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     const bool fixed_tpb = o.threads_per_block > 0;
     const bool fixed_place = o.hash_in_smem == 0 || o.hash_in_smem == 1;
     const int req_tpb = std::min(1024, (o.threads_per_block + 31) / 32 * 32);
-    const int req_kern = o.walk_kernel >= 1 && o.walk_kernel <= 3 ? o.walk_kernel : 0;
+    const int req_kern = o.walk_kernel == 1 || o.walk_kernel == 2 ? o.walk_kernel : 0;
     if (fixed_tpb && fixed_place && req_kern) {
         if (!configure(req_tpb, 0, o.hash_in_smem, n, cfg, req_kern)) {
             set_error("walk kernel: requested block size / lookup placement does not fit");
@@ -2374,11 +1697,8 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
         // autotuner: time each candidate configuration on a prefix of rows once per problem
         // shape (cached for the process); the prefix rows are recomputed by the full launch
         std::vector<Cfg> cands;
-        // the streamed-rows kernel is a candidate only on request: measured slower on the
-        // square and ball workloads (the rows that do not own the shared accumulators add
-        // through L2 reductions)
-        for (int kern : {1, 2, 3}) {
-            if (req_kern ? kern != req_kern : kern != 1) continue;
+        for (int kern : {1, 2}) {
+            if (req_kern && kern != req_kern) continue;
             for (int vg : {0, 1})
                 for (int t : {512, 1024}) {
                     if (fixed_tpb && t != req_tpb) continue;
@@ -2409,7 +1729,6 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
                 WalkArgs<T, D> trial = a;
                 trial.n = rows;
                 EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counter, 0, sizeof(int), st));
-                if (c.kern == 2) EWOS_CUDA_TRY(zero_outputs());
                 cudaEventRecord(t0, st);
                 EWOS_CUDA_TRY(launch(c, trial));
                 cudaEventRecord(t1, st);
@@ -2426,15 +1745,9 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
         }
         tune_store(key, cfg.tpb, cfg.v_smem, cfg.vg, cfg.kern);
     }
-    if (cfg.kern == 2) EWOS_CUDA_TRY(zero_outputs());
+    if (cfg.kern == 1) EWOS_CUDA_TRY(ctx.ensure_acc(sizeof(T) * 4 * (size_t)m * cfg.grid));
     EWOS_CUDA_TRY(cudaEventRecord(ev[3], st));
     EWOS_CUDA_TRY(launch(cfg, a));
-    if (cfg.kern == 3) {
-        ::ewos::note_launch();
-        h_from_counts_kernel<T><<<(int)std::min<int64_t>(4096, ((int64_t)np + 255) / 256), 256, 0, st>>>(
-            tb->Hc, (T*)tb->KH + (size_t)D * np, (int64_t)np, T(1) / (T)tb->N);
-        EWOS_CUDA_TRY(cudaGetLastError());
-    }
     const int tpb = cfg.tpb, per_sm = cfg.per_sm, grid = cfg.grid;
     const bool v_smem = cfg.v_smem;
     const size_t smem = cfg.smem;
@@ -2444,8 +1757,8 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     EWOS_CUDA_TRY(cudaMemcpyAsync(stats, ctx.d_stats, sizeof(stats), cudaMemcpyDeviceToHost, st));
     EWOS_CUDA_TRY(cudaStreamSynchronize(st));
     if (stats[2]) {
-        set_error("walk kernel (streamed rows): a warp waited too long for a row and gave up");
-        return EWOS_ETIMEOUT;
+        set_error("walk kernel: " + std::to_string(stats[2]) + " out-of-range indexes found and skipped");
+        return EWOS_ECUDA;
     }
     float ms[4];
     cudaEventElapsedTime(&ms[0], ev[0], ev[4]);
@@ -2531,7 +1844,21 @@ static ewos_status build_batch_kind(std::vector<ewos_toolbox*>& tbs, const std::
     }
     WalkArgs<T, D>* d_args = nullptr;
     int *d_off = nullptr, *d_counter = nullptr, *d_off_trial = nullptr;
-    struct Frees { void** p[4]; ~Frees() { for (auto q : p) ::ewos::dev_free(*q); } } fr{{(void**)&d_args, (void**)&d_off, (void**)&d_counter, (void**)&d_off_trial}};
+    T* d_acc = nullptr;
+    struct Frees { void** p[5]; ~Frees() { for (auto q : p) ::ewos::dev_free(*q); } } fr{{(void**)&d_args, (void**)&d_off, (void**)&d_counter, (void**)&d_off_trial, (void**)&d_acc}};
+    int dev = 0, nsm = 0, smem_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // G / grad G accumulators in global memory: one row of the largest instance per CTA, for up
+    // to kMaxBatchCtasPerSm CTAs per SM
+    constexpr int kMaxBatchCtasPerSm = 8;
+    EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_acc, sizeof(T) * 4 * (size_t)max_m * nsm * kMaxBatchCtasPerSm));
+    for (int k = 0; k < nb; ++k) {
+        args[k].acc_g = d_acc;
+        args[k].acc_cells = (int)max_m;
+        args[k].acc_len = (int64_t)4 * max_m * nsm * kMaxBatchCtasPerSm;
+    }
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_args, sizeof(WalkArgs<T, D>) * nb));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_off, sizeof(int) * (nb + 1)));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&d_off_trial, sizeof(int) * (nb + 1)));
@@ -2540,16 +1867,12 @@ static ewos_status build_batch_kind(std::vector<ewos_toolbox*>& tbs, const std::
     EWOS_CUDA_TRY(cudaMemcpyAsync(d_off, off.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
     EWOS_CUDA_TRY(cudaEventRecord(ev[1], st));
 
-    // shared memory for the largest instance
-    const size_t acc_bytes = sizeof(T) * ((size_t)(D + 1) * max_m + (size_t)D * max_p) + sizeof(uint32_t) * max_p;
+    // shared memory for the largest instance (the KH / H accumulators, sdf parameters, queues)
+    const size_t acc_bytes = sizeof(T) * (size_t)D * max_p + sizeof(uint32_t) * max_p;
     const size_t sdf_bytes = sizeof(T) * ((max_sdf + 3) & ~int64_t(3));
     auto smem_for = [&](int t) {
         return (((acc_bytes + 15) & ~size_t(15)) + sdf_bytes + queue_bytes<T, D>(t / 32, false) + 15) & ~size_t(15);
     };
-    int dev = 0, nsm = 0, smem_optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int total = off[nb];
     // autotuner: block size x CTAs per SM, timed on a prefix of the global rows, cached per shape
     BatchTuneKey key{(int)sizeof(T), D, KIND, nb, total, max_m, max_p, tbs[0]->N};
@@ -2566,7 +1889,7 @@ static ewos_status build_batch_kind(std::vector<ewos_toolbox*>& tbs, const std::
         for (int t : {256, 512, 1024}) {
             const size_t sm = smem_for(t);
             if (sm > (size_t)smem_optin - 1024) continue;
-            const int mx = batch_ctas_per_sm<T, D, KIND>(t, sm);
+            const int mx = std::min(kMaxBatchCtasPerSm, batch_ctas_per_sm<T, D, KIND>(t, sm));
             for (int p2 = 1; p2 <= mx && p2 <= 4; p2 *= 2) cands.push_back({t, p2});
         }
         if (cands.empty()) { set_error("batch: the largest toolbox row does not fit in shared memory"); return EWOS_EINVAL; }
@@ -2590,12 +1913,12 @@ static ewos_status build_batch_kind(std::vector<ewos_toolbox*>& tbs, const std::
             if (ms < best) { best = ms; tpb = c.tpb; per = c.per; }
         }
         cudaEventDestroy(t0); cudaEventDestroy(t1);
-        for (int k = 0; k < nb; ++k) EWOS_CUDA_TRY(cudaMemsetAsync(ctxs[k]->d_stats, 0, 2 * sizeof(unsigned long long), st));
+        for (int k = 0; k < nb; ++k) EWOS_CUDA_TRY(cudaMemsetAsync(ctxs[k]->d_stats, 0, 3 * sizeof(unsigned long long), st));
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_batch_tune.push_back({key, {tpb, per}});
     }
     const size_t smem = smem_for(tpb);
-    if (per <= 0) per = std::max(1, batch_ctas_per_sm<T, D, KIND>(tpb, smem));
+    if (per <= 0) per = std::max(1, std::min(kMaxBatchCtasPerSm, batch_ctas_per_sm<T, D, KIND>(tpb, smem)));
     if (o.ctas_per_sm > 0) per = std::min(per, o.ctas_per_sm);
     const int grid = std::max(1, std::min(nsm * per, total));
     EWOS_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), st));
@@ -2603,10 +1926,15 @@ static ewos_status build_batch_kind(std::vector<ewos_toolbox*>& tbs, const std::
     cudaError_t le = launch_batch<T, D, KIND>(d_args, d_off, nb, d_counter, grid, tpb, smem, st);
     EWOS_CUDA_TRY(le);
     EWOS_CUDA_TRY(cudaEventRecord(ev[2], st));
-    std::vector<unsigned long long> stats(2 * nb);
+    std::vector<unsigned long long> stats(3 * nb);
     for (int k = 0; k < nb; ++k)
-        EWOS_CUDA_TRY(cudaMemcpyAsync(&stats[2 * k], ctxs[k]->d_stats, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        EWOS_CUDA_TRY(cudaMemcpyAsync(&stats[3 * k], ctxs[k]->d_stats, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int k = 0; k < nb; ++k)
+        if (stats[3 * k + 2]) {
+            set_error("batch walk kernel: " + std::to_string(stats[3 * k + 2]) + " out-of-range indexes found and skipped");
+            return EWOS_ECUDA;
+        }
     float ms_all = 0, ms_walk = 0;
     cudaEventElapsedTime(&ms_all, ev[0], ev[2]);
     cudaEventElapsedTime(&ms_walk, ev[1], ev[2]);
@@ -2615,8 +1943,8 @@ static ewos_status build_batch_kind(std::vector<ewos_toolbox*>& tbs, const std::
         ewos_build_report& r = tbs[k]->rep;
         r = ewos_build_report{};
         r.walks = tbs[k]->n * tbs[k]->N;
-        r.steps = (int64_t)stats[2 * k];
-        r.capped = (int64_t)stats[2 * k + 1];
+        r.steps = (int64_t)stats[3 * k];
+        r.capped = (int64_t)stats[3 * k + 1];
         r.ms_total = ms_all; r.ms_walk = ms_walk;
         r.threads_per_block = tpb; r.ctas_per_sm = per; r.grid = grid; r.hash_in_smem = 0;
         r.smem_bytes = (int64_t)smem;
@@ -2830,15 +2158,15 @@ static ewos_status build_noalloc_typed(const ewos_domain* dom, const double* d_x
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (smem + 1024 > (size_t)smem_optin) { set_error("toolbox row does not fit in shared memory"); return EWOS_EINVAL; }
     int per_sm = 0;
-    if (dom->kind == SDF_BALL) per_sm = max_ctas_per_sm<float, D, SDF_BALL>(tpb, smem);
-    else if (dom->kind == SDF_BOX) per_sm = max_ctas_per_sm<float, D, SDF_BOX>(tpb, smem);
-    else per_sm = max_ctas_per_sm<float, 2, SDF_POLYGON>(tpb, smem);
+    if (dom->kind == SDF_BALL) per_sm = max_ctas_per_sm<float, D, SDF_BALL>(tpb, smem, 2);
+    else if (dom->kind == SDF_BOX) per_sm = max_ctas_per_sm<float, D, SDF_BOX>(tpb, smem, 2);
+    else per_sm = max_ctas_per_sm<float, 2, SDF_POLYGON>(tpb, smem, 2);
     if (per_sm < 1) { set_error("walk kernel does not fit on an SM"); return EWOS_EINVAL; }
     const int grid = std::max(1, std::min(nsm * per_sm, n));
     cudaError_t e;
-    if (dom->kind == SDF_BALL) e = launch_walks<float, D, SDF_BALL, false>(a, grid, tpb, smem, st);
-    else if (dom->kind == SDF_BOX) e = launch_walks<float, D, SDF_BOX, false>(a, grid, tpb, smem, st);
-    else e = D == 2 ? launch_walks<float, D, SDF_POLYGON, false>(a, grid, tpb, smem, st) : cudaErrorInvalidValue;
+    if (dom->kind == SDF_BALL) e = launch_walks<float, D, SDF_BALL, false>(a, grid, tpb, smem, st, 2);
+    else if (dom->kind == SDF_BOX) e = launch_walks<float, D, SDF_BOX, false>(a, grid, tpb, smem, st, 2);
+    else e = D == 2 ? launch_walks<float, D, SDF_POLYGON, false>(a, grid, tpb, smem, st, 2) : cudaErrorInvalidValue;
     EWOS_CUDA_TRY(e);
     unsigned long long stats[2] = {0, 0};
     EWOS_CUDA_TRY(cudaMemcpyAsync(stats, d_stats, sizeof(stats), cudaMemcpyDeviceToHost, st));
