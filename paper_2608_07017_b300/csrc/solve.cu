@@ -2035,6 +2035,16 @@ static void u_from_s(const Ctx& C, const void* P, const void* KH, bool fp64, con
     if (fp64) {
         ::ewos::note_launch(), rowdot_kernel<double><<<blocks, 256, 0, C.st>>>((const double*)Gm, C.n, (int)C.m, s, u, 0);
         ::ewos::note_launch(), rowdot_kernel<double><<<blocks, 256, 0, C.st>>>((const double*)Hm, C.n, (int)C.p, g, u, 1);
+    } else if (C.ws->F2one) {
+        // FP32 matrices, FP64 vectors: the FP32-pair products (as in the residual)
+        float* sh = C.ws->F2one;
+        float* sl = sh + pad4(C.m);
+        float* gh = sl + pad4(C.m);
+        float* gl = gh + pad4(C.p);
+        split_f2(C.st, s, sh, sl, C.m);
+        multi_rowdot_f2(C.st, (const float*)Gm, C.n, (int)C.m, sh, sl, u, 1, 0);
+        split_f2(C.st, g, gh, gl, C.p);
+        multi_rowdot_f2(C.st, (const float*)Hm, C.n, (int)C.p, gh, gl, u, 1, 1);
     } else {
         ::ewos::note_launch(), rowdot_kernel<float><<<blocks, 256, 0, C.st>>>((const float*)Gm, C.n, (int)C.m, s, u, 0);
         ::ewos::note_launch(), rowdot_kernel<float><<<blocks, 256, 0, C.st>>>((const float*)Hm, C.n, (int)C.p, g, u, 1);
