@@ -715,17 +715,18 @@ void tc_update_operands(TcScratch* t, float** a_hi, float** a_lo, float** b_hi, 
 
 // C [M][N] (row stride ldc) -= A B for a row-major A [M][K] (stride lda) and B [K][N] (stride
 // ldb): the LU's trailing update on the tensor cores (three TF32 products).  With presplit the
-// operands are already in the scratch (tc_update_operands; A and B are not read).  Enqueued
-// only; a pipeline timeout sets the scratch's error word, which tc_update_check reads (and
-// clears).
+// operands are already in the scratch (tc_update_operands; A and B are not read), starting at
+// operand row a_off of A and b_off of B.  Enqueued only; a pipeline timeout sets the scratch's
+// error word, which tc_update_check reads (and clears).
 ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int M,
-                              int N, int K, cudaStream_t st, TcScratch** owned, bool presplit) {
+                              int N, int K, cudaStream_t st, TcScratch** owned, bool presplit, int a_off, int b_off) {
     using namespace tc;
     if (!*owned) *owned = new TcScratch();
     Scratch& S = (*owned)->s;
     const int Kp = (K + BK - 1) / BK * BK;
     const size_t need = (size_t)std::max(M, N) * Kp;
-    if (presplit && (S.cap < need || !S.Atl || !S.err)) {
+    if (!presplit) a_off = b_off = 0;
+    if (presplit && (S.cap < (size_t)std::max(a_off + M, b_off + N) * Kp || !S.Atl || !S.err || a_off < 0 || b_off < 0)) {
         set_error("tensor-core update: split operands expected in a scratch that is too small");
         return EWOS_EINVAL;
     }
@@ -754,8 +755,9 @@ ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64
     }
     constexpr int bn = Cfg<true>::BN;
     CUtensorMap ma, mb, mal, mbl;
-    if (!(make_map(&ma, S.At, M, Kp, BM) && make_map(&mb, S.Bt, N, Kp, bn) && make_map(&mal, S.Atl, M, Kp, BM) &&
-          make_map(&mbl, S.Btl, N, Kp, bn))) {
+    const size_t ao = (size_t)a_off * Kp, bo = (size_t)b_off * Kp;
+    if (!(make_map(&ma, S.At + ao, M, Kp, BM) && make_map(&mb, S.Bt + bo, N, Kp, bn) &&
+          make_map(&mal, S.Atl + ao, M, Kp, BM) && make_map(&mbl, S.Btl + bo, N, Kp, bn))) {
         set_error("tensor-core update: cuTensorMapEncodeTiled failed");
         return EWOS_ECUDA;
     }

@@ -74,7 +74,8 @@ void tc_scratch_free(TcScratch* t);
 ewos_status tc_assemble(const float* A_km, const float* B_km, float* C, int M, int N, int K, cudaStream_t st,
                         bool split, TcScratch** owned, bool sym = false);
 ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int M,
-                              int N, int K, cudaStream_t st, TcScratch** owned, bool presplit = false);
+                              int N, int K, cudaStream_t st, TcScratch** owned, bool presplit = false, int a_off = 0,
+                              int b_off = 0);
 ewos_status tc_update_reserve(int max_mn, int k, cudaStream_t st, TcScratch** owned);
 ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D, float* C, cudaStream_t st,
                            TcScratch** owned, bool sym = false);
@@ -1414,6 +1415,7 @@ __global__ void iota_kernel(int* __restrict__ v, int m) {
 // Trailing updates of at least this many rows go to the tensor cores (FP32 factors, three TF32
 // products); smaller ones stay on the FP32 SIMT GEMM.
 constexpr int kTcUpdateMin = 256;
+constexpr int kSuper = 4;           // 64-column panels per super panel of the unpivoted LU
 
 template <typename T>
 static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStream_t st, bool* accepted,
@@ -1435,38 +1437,58 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
     TcOperands tc_ops;
     const bool use_tc = std::is_same<T, float>::value && tc != nullptr && m - kNB >= kTcUpdateMin;
     if (use_tc) {
-        ewos_status e = tc_update_reserve(m - kNB, kNB, st, tc);
+        // room for the rank-kSuper*64 updates' operands too (split by the update itself)
+        ewos_status e = tc_update_reserve(m - kNB, kSuper * kNB, st, tc);
         if (e != EWOS_OK) return e;
         tc_update_operands(*tc, &tc_ops.a_hi, &tc_ops.a_lo, &tc_ops.b_hi, &tc_ops.b_lo);
     }
-    for (int kb = 0; kb < m; kb += kNB) {
-        const int nb = std::min(kNB, m - kb);
-        const int rest = m - kb - nb;
-        T* dblk = diagb + (size_t)(kb / kNB) * kNB * kNB;
-        T* iblk = dinv + (size_t)(kb / kNB) * 2 * kNB * kNB;
-        ::ewos::note_launch();
-        EWOS_CUDA_TRY(launch_pdl(lu_diag_factor_kernel<T>, dim3(1), dim3(kNpThreads), diag_smem<T>(), st, (const T*)A, lda,
-                                 kb, nb, dblk, iblk, S.bar));
-        if (rest > 0) {
-            // nb == 64 whenever rows remain below the diagonal block
-            const int ntl = (rest + kNB - 1) / kNB;
-            const bool tc_here = use_tc && rest >= kTcUpdateMin;
-            ::ewos::note_launch();
-            EWOS_CUDA_TRY(launch_pdl(lu_panel_gemm_kernel<T>, dim3(2 * ntl), dim3(kNpThreads), panel_smem<T>(), st, A, lda,
-                                     m, kb, (const T*)iblk, S.bar, tc_here ? tc_ops : TcOperands{}));
+    // C[row0 .., col0 ..] (M x N) -= L[row0 .., kcol .. kcol + K] U[krow .. krow + K, col0 ..], in place;
+    // with `split` the operands are the panel's split ones, starting at operand rows a_off, b_off
+    auto update = [&](int M, int N, int K, int row0, int col0, int kcol, int krow, bool split, int a_off,
+                      int b_off) -> ewos_status {
+        if (M <= 0 || N <= 0 || K <= 0) return EWOS_OK;
+        T* C = A + (size_t)row0 * lda + col0;
+        const T* L = A + (size_t)row0 * lda + kcol;
+        const T* U = A + (size_t)krow * lda + col0;
+        if constexpr (std::is_same<T, float>::value) {
+            if (split || (use_tc && M >= kTcUpdateMin && N >= kTcUpdateMin))
+                return tc_update_enqueue(reinterpret_cast<const float*>(L), lda, reinterpret_cast<const float*>(U), lda,
+                                         reinterpret_cast<float*>(C), lda, M, N, K, st, tc, split, a_off, b_off);
         }
-        if (rest > 0) {
-            if (use_tc && rest >= kTcUpdateMin) {
-                ewos_status e = tc_update_enqueue(reinterpret_cast<const float*>(A + (size_t)(kb + nb) * lda + kb), lda,
-                                                  reinterpret_cast<const float*>(A + (size_t)kb * lda + kb + nb), lda,
-                                                  reinterpret_cast<float*>(A + (size_t)(kb + nb) * lda + kb + nb), lda,
-                                                  rest, rest, nb, st, tc, true);
+        gemm_trailing<T>(st, M, N, K, L, lda, U, lda, C, lda);
+        return EWOS_OK;
+    };
+    // Super panels of kSuper 64-column panels.  Inside a super panel each panel updates only the
+    // rows of the super panel's later panels (across every column to its right: the band) and the
+    // super panel's later columns (for every row below the super panel); the trailing matrix
+    // below and right of the super panel gets one rank-(kSuper * 64) update at its end, which
+    // reads and writes that matrix once instead of kSuper times.
+    for (int KB = 0; KB < m; KB += kSuper * kNB) {
+        const int KE = std::min(m, KB + kSuper * kNB);
+        for (int kb = KB; kb < KE; kb += kNB) {
+            const int nb = std::min(kNB, m - kb);
+            const int rest = m - kb - nb;
+            T* dblk = diagb + (size_t)(kb / kNB) * kNB * kNB;
+            T* iblk = dinv + (size_t)(kb / kNB) * 2 * kNB * kNB;
+            ::ewos::note_launch();
+            EWOS_CUDA_TRY(launch_pdl(lu_diag_factor_kernel<T>, dim3(1), dim3(kNpThreads), diag_smem<T>(), st, (const T*)A,
+                                     lda, kb, nb, dblk, iblk, S.bar));
+            if (rest > 0) {
+                // nb == 64 whenever rows remain below the diagonal block
+                const int ntl = (rest + kNB - 1) / kNB;
+                const bool tc_here = use_tc && rest >= kTcUpdateMin;
+                ::ewos::note_launch();
+                EWOS_CUDA_TRY(launch_pdl(lu_panel_gemm_kernel<T>, dim3(2 * ntl), dim3(kNpThreads), panel_smem<T>(), st, A,
+                                         lda, m, kb, (const T*)iblk, S.bar, tc_here ? tc_ops : TcOperands{}));
+                const int band = KE - (kb + nb);       // rows (and columns) of the super panel's later panels
+                const int below = m - KE;
+                ewos_status e = update(band, rest, nb, kb + nb, kb + nb, kb, kb, tc_here, 0, 0);
+                if (e == EWOS_OK) e = update(below, band, nb, KE, kb + nb, kb, kb, tc_here, band, 0);
                 if (e != EWOS_OK) return e;
-            } else {
-                gemm_trailing<T>(st, rest, rest, nb, A + (size_t)(kb + nb) * lda + kb, lda,
-                                 A + (size_t)kb * lda + kb + nb, lda, A + (size_t)(kb + nb) * lda + kb + nb, lda);
             }
         }
+        ewos_status e = update(m - KE, m - KE, KE - KB, KE, KE, KB, KB, false, 0, 0);
+        if (e != EWOS_OK) return e;
     }
     if (tc && *tc) {
         ewos_status e = tc_update_check(*tc, st);
