@@ -1415,7 +1415,7 @@ __global__ void iota_kernel(int* __restrict__ v, int m) {
 // Trailing updates of at least this many rows go to the tensor cores (FP32 factors, three TF32
 // products); smaller ones stay on the FP32 SIMT GEMM.
 constexpr int kTcUpdateMin = 256;
-constexpr int kSuper = 4;           // 64-column panels per super panel of the unpivoted LU
+constexpr int kSuper = 8;           // 64-column panels per super panel of the unpivoted LU
 
 template <typename T>
 static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStream_t st, bool* accepted,
