@@ -2758,6 +2758,160 @@ __global__ void coltrans_f2_vec_kernel(const float* __restrict__ X, int64_t rows
 
 static inline bool aligned16(const void* q) { return ((uintptr_t)q & 15) == 0; }
 
+// Many columns (rc >= 8): the products are small GEMMs on the FP32 pipes in FP32 pairs.  A CTA
+// stages 32-column (32-row) slices of X and of the vector block in shared memory and every
+// thread accumulates RW x 4 outputs as FP32 pairs, so each element of X is read once from HBM
+// for all the CTA's columns (the kernels above read the vectors from L1/L2 once per product).
+template <int RCT>
+struct F2Tile {
+    static constexpr int TX = RCT / 4;                 // threads across vector columns (4 each)
+    static constexpr int TY = 256 / TX;                // threads across matrix rows (columns)
+    static constexpr int RW = TY >= 64 ? 1 : 64 / TY;  // rows per thread
+    static constexpr int TR = TY * RW;                 // rows per CTA
+    static constexpr int CK = 32;                      // slice depth
+};
+
+// Vout[row][r] (+)= sum_c X[row][c] V[r][c], V = Vhi + Vlo given as [rc][cols]
+template <int RCT>
+__global__ void __launch_bounds__(256) rowdot_f2_tile_kernel(const float* __restrict__ X, int64_t rows, int cols,
+                                                            const float* __restrict__ Vhi, const float* __restrict__ Vlo,
+                                                            double* __restrict__ Vout, int rc, int accumulate) {
+    using F = F2Tile<RCT>;
+    constexpr int TX = F::TX, TY = F::TY, RW = F::RW, TR = F::TR, CK = F::CK;
+    __shared__ float Xs[CK][TR + 1];
+    __shared__ __align__(16) float Hs[CK][RCT + 4];
+    __shared__ __align__(16) float Ls[CK][RCT + 4];
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int64_t row0 = (int64_t)blockIdx.x * TR;
+    const int r0 = blockIdx.y * RCT;
+    float hi[RW][4], lo[RW][4];
+#pragma unroll
+    for (int i = 0; i < RW; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) hi[i][j] = lo[i][j] = 0.f;
+    for (int c0 = 0; c0 < cols; c0 += CK) {
+        for (int e = threadIdx.x; e < TR * CK; e += 256) {
+            const int r = e / CK, c = e % CK;
+            const int64_t gr = row0 + r;
+            Xs[c][r] = (gr < rows && c0 + c < cols) ? __ldcs(X + gr * cols + c0 + c) : 0.f;
+        }
+        for (int e = threadIdx.x; e < RCT * CK; e += 256) {
+            const int j = e / CK, c = e % CK;
+            const bool ok = r0 + j < rc && c0 + c < cols;
+            Hs[c][j] = ok ? Vhi[(size_t)(r0 + j) * cols + c0 + c] : 0.f;
+            Ls[c][j] = ok ? Vlo[(size_t)(r0 + j) * cols + c0 + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int c = 0; c < CK; ++c) {
+            float x[RW];
+#pragma unroll
+            for (int i = 0; i < RW; ++i) x[i] = Xs[c][ty + TY * i];
+            const float4 h = *reinterpret_cast<const float4*>(&Hs[c][tx * 4]);
+            const float4 l = *reinterpret_cast<const float4*>(&Ls[c][tx * 4]);
+#pragma unroll
+            for (int i = 0; i < RW; ++i) {
+                f2_add_prod(hi[i][0], lo[i][0], x[i], h.x, l.x);
+                f2_add_prod(hi[i][1], lo[i][1], x[i], h.y, l.y);
+                f2_add_prod(hi[i][2], lo[i][2], x[i], h.z, l.z);
+                f2_add_prod(hi[i][3], lo[i][3], x[i], h.w, l.w);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < RW; ++i) {
+        const int64_t row = row0 + ty + TY * i;
+        if (row >= rows) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = r0 + tx * 4 + j;
+            if (r >= rc) continue;
+            const double v = (double)hi[i][j] + (double)lo[i][j];
+            double* o = Vout + row * rc + r;
+            *o = accumulate ? *o + v : v;
+        }
+    }
+}
+
+// Y[c][r] += sum_{row in chunk} X[row][c] W[row][r], W = Whi + Wlo given as [rows][rc]
+template <int RCT>
+__global__ void __launch_bounds__(256) coltrans_f2_tile_kernel(const float* __restrict__ X, int64_t rows, int cols,
+                                                              const float* __restrict__ Whi, const float* __restrict__ Wlo,
+                                                              double* __restrict__ Y, int rc, int64_t chunk) {
+    using F = F2Tile<RCT>;
+    constexpr int TX = F::TX, TY = F::TY, RW = F::RW, TR = F::TR, CK = F::CK;
+    __shared__ float Xs[CK][TR + 1];
+    __shared__ __align__(16) float Hs[CK][RCT + 4];
+    __shared__ __align__(16) float Ls[CK][RCT + 4];
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int col0 = blockIdx.x * TR;
+    const int r0 = blockIdx.y * RCT;
+    const int64_t a = (int64_t)blockIdx.z * chunk;
+    const int64_t b = min(rows, a + chunk);
+    float hi[RW][4], lo[RW][4];
+#pragma unroll
+    for (int i = 0; i < RW; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) hi[i][j] = lo[i][j] = 0.f;
+    for (int64_t k0 = a; k0 < b; k0 += CK) {
+        for (int e = threadIdx.x; e < TR * CK; e += 256) {
+            const int k = e / TR, c = e % TR;
+            Xs[k][c] = (k0 + k < b && col0 + c < cols) ? __ldcs(X + (k0 + k) * cols + col0 + c) : 0.f;
+        }
+        for (int e = threadIdx.x; e < RCT * CK; e += 256) {
+            const int k = e / RCT, j = e % RCT;
+            const bool ok = k0 + k < b && r0 + j < rc;
+            Hs[k][j] = ok ? Whi[(k0 + k) * rc + r0 + j] : 0.f;
+            Ls[k][j] = ok ? Wlo[(k0 + k) * rc + r0 + j] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < CK; ++k) {
+            float x[RW];
+#pragma unroll
+            for (int i = 0; i < RW; ++i) x[i] = Xs[k][ty + TY * i];
+            const float4 h = *reinterpret_cast<const float4*>(&Hs[k][tx * 4]);
+            const float4 l = *reinterpret_cast<const float4*>(&Ls[k][tx * 4]);
+#pragma unroll
+            for (int i = 0; i < RW; ++i) {
+                f2_add_prod(hi[i][0], lo[i][0], x[i], h.x, l.x);
+                f2_add_prod(hi[i][1], lo[i][1], x[i], h.y, l.y);
+                f2_add_prod(hi[i][2], lo[i][2], x[i], h.z, l.z);
+                f2_add_prod(hi[i][3], lo[i][3], x[i], h.w, l.w);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < RW; ++i) {
+        const int c = col0 + ty + TY * i;
+        if (c >= cols) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = r0 + tx * 4 + j;
+            if (r < rc) atomicAdd(&Y[(size_t)c * rc + r], (double)hi[i][j] + (double)lo[i][j]);
+        }
+    }
+}
+
+template <int RCT>
+static void rowdot_f2_tile(cudaStream_t st, const float* X, int64_t rows, int cols, const float* Vhi, const float* Vlo,
+                           double* Vout, int rc, int accumulate) {
+    using F = F2Tile<RCT>;
+    dim3 grid((unsigned)((rows + F::TR - 1) / F::TR), (unsigned)((rc + RCT - 1) / RCT));
+    ::ewos::note_launch(), rowdot_f2_tile_kernel<RCT><<<grid, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
+}
+
+template <int RCT>
+static void coltrans_f2_tile(cudaStream_t st, const float* X, int64_t rows, int cols, const float* Whi, const float* Wlo,
+                             double* Y, int rc) {
+    using F = F2Tile<RCT>;
+    const int64_t chunk = 1024;
+    dim3 grid((unsigned)((cols + F::TR - 1) / F::TR), (unsigned)((rc + RCT - 1) / RCT), (unsigned)((rows + chunk - 1) / chunk));
+    ::ewos::note_launch(), coltrans_f2_tile_kernel<RCT><<<grid, 256, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
+}
+
 static void multi_rowdot_f2(cudaStream_t st, const float* X, int64_t rows, int cols, const float* Vhi, const float* Vlo,
                             double* Vout, int rc, int accumulate) {
     const int rb = (int)std::max<int64_t>(1, (rows * 32 + 255) / 256);
@@ -2765,6 +2919,10 @@ static void multi_rowdot_f2(cudaStream_t st, const float* X, int64_t rows, int c
         ::ewos::note_launch(), rowdot_f2_vec_kernel<4><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, accumulate);
         return;
     }
+    if (rc >= 64) return rowdot_f2_tile<64>(st, X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
+    if (rc >= 32) return rowdot_f2_tile<32>(st, X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
+    if (rc >= 16) return rowdot_f2_tile<16>(st, X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
+    if (rc >= 8) return rowdot_f2_tile<8>(st, X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
     if (rc == 1) ::ewos::note_launch(), multi_rowdot_f2_kernel<1><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
     else if (rc == 2) ::ewos::note_launch(), multi_rowdot_f2_kernel<2><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
     else if (rc == 4) ::ewos::note_launch(), multi_rowdot_f2_kernel<4><<<rb, 256, 0, st>>>(X, rows, cols, Vhi, Vlo, Vout, rc, accumulate);
@@ -2774,6 +2932,10 @@ static void multi_rowdot_f2(cudaStream_t st, const float* X, int64_t rows, int c
 
 static void multi_coltrans_f2(cudaStream_t st, const float* X, int64_t rows, int cols, const float* Whi, const float* Wlo,
                               double* Y, int rc) {
+    if (rc >= 64) return coltrans_f2_tile<64>(st, X, rows, cols, Whi, Wlo, Y, rc);
+    if (rc >= 32) return coltrans_f2_tile<32>(st, X, rows, cols, Whi, Wlo, Y, rc);
+    if (rc >= 16) return coltrans_f2_tile<16>(st, X, rows, cols, Whi, Wlo, Y, rc);
+    if (rc >= 8) return coltrans_f2_tile<8>(st, X, rows, cols, Whi, Wlo, Y, rc);
     if (rc == 1 && cols % 4 == 0 && aligned16(X)) {
         const int64_t vchunk = 256;
         dim3 vgrid((unsigned)((cols / 4 + 127) / 128), (unsigned)((rows + vchunk - 1) / vchunk));
@@ -3174,8 +3336,20 @@ static ewos_status solve_batched(const Ctx& C, int R, const double* nl, int nnl,
     ::ewos::note_launch(), from_cols_kernel<<<nblocks(C.m * R), 256, 0, C.st>>>(ws->Sb, ws->s, C.m, R, (int)rc);
     const TP* Gm = (const TP*)C.tb->P + (size_t)C.D * C.n * C.m;
     const TP* Hm = (const TP*)C.tb->KH + (size_t)C.D * C.n * C.p;
-    multi_rowdot<TP>(C.st, Gm, C.n, (int)C.m, ws->Sb, ws->Ub, (int)rc, 0);
-    multi_rowdot<TP>(C.st, Hm, C.n, (int)C.p, ws->Gb, ws->Ub, (int)rc, 1);
+    if (sizeof(TP) == 4) {
+        // FP32 matrices: the FP32-pair products, as in the sweeps
+        float* Shi = ws->F2buf;
+        float* Slo = Shi + C.m * rc;
+        float* Ghi = Slo + C.m * rc;
+        float* Glo = Ghi + C.p * rc;
+        ::ewos::note_launch(), split_f2_t_kernel<<<nblocks(C.m * rc), 256, 0, C.st>>>(ws->Sb, Shi, Slo, C.m, (int)rc);
+        ::ewos::note_launch(), split_f2_t_kernel<<<nblocks(C.p * rc), 256, 0, C.st>>>(ws->Gb, Ghi, Glo, C.p, (int)rc);
+        multi_rowdot_f2(C.st, (const float*)Gm, C.n, (int)C.m, Shi, Slo, ws->Ub, (int)rc, 0);
+        multi_rowdot_f2(C.st, (const float*)Hm, C.n, (int)C.p, Ghi, Glo, ws->Ub, (int)rc, 1);
+    } else {
+        multi_rowdot<TP>(C.st, Gm, C.n, (int)C.m, ws->Sb, ws->Ub, (int)rc, 0);
+        multi_rowdot<TP>(C.st, Hm, C.n, (int)C.p, ws->Gb, ws->Ub, (int)rc, 1);
+    }
     ::ewos::note_launch(), from_cols_kernel<<<nblocks(C.n * R), 256, 0, C.st>>>(ws->Ub, ws->u, C.n, R, (int)rc);
     return EWOS_OK;
 }
