@@ -1571,19 +1571,37 @@ __device__ __forceinline__ void stage_tile(T (*dst)[65], const T* src, size_t ld
     for (int s = 0; s < 16; ++s) dst[a0 + 4 * s][b] = v[s];
 }
 
+// 4 consecutive values of a shared-memory row (16-byte aligned for FP32)
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T* v) {
+    if constexpr (std::is_same<T, float>::value) {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = p[e];
+    }
+}
+
+// Many right-hand sides: the same dataflow over 64-row blocks, 64 right-hand sides at a time.
+// A thread owns a 4 x 4 piece of the block's 64 x 64 accumulator in registers; each preceding
+// block's contribution L_ij X_j is a 64 x 64 x 64 product from shared memory (L_ij staged
+// transposed), 16 multiply-adds per two 4-wide loads, and the diagonal inverse is applied the
+// same way at the end.
+constexpr int kFlowLd = 68;                   // shared row stride (16-byte aligned rows)
 template <typename T>
 __global__ void __launch_bounds__(256) trsm_flow_kernel(const T* __restrict__ LU, int lda, int m,
                                                        const T* __restrict__ Dinv, T* X, int rc,
                                                        unsigned int* state) {
     extern __shared__ __align__(16) unsigned char flow_sm[];
-    T (*Ls)[65] = reinterpret_cast<T (*)[65]>(flow_sm);
-    T (*Xs)[65] = Ls + 64;
-    T (*Acc)[65] = Xs + 64;
-    T (*Ds)[65] = Acc + 64;
+    T (*Lt)[kFlowLd] = reinterpret_cast<T (*)[kFlowLd]>(flow_sm);   // [k][row]: L_ij (U_ij) transposed
+    T (*Xs)[kFlowLd] = Lt + 64;                                       // [k][col]: X_j
+    T (*Dt)[kFlowLd] = Xs + 64;                                       // [k][row]: the diagonal inverse, transposed
+    T (*As)[kFlowLd] = Dt + 64;                                       // [row][col]: the accumulator
     __shared__ unsigned int s_ticket;
     __shared__ int s_ok;
     const int nbk = (m + 63) / 64;
-    const int tid = threadIdx.x, ii = tid & 63, rq = tid >> 6;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;     // rows 4 ty .. 4 ty + 3, columns 4 tx ..
     if (tid == 0) s_ticket = atomicAdd(state, 1u);
     __syncthreads();
     const int t = (int)s_ticket;
@@ -1596,34 +1614,74 @@ __global__ void __launch_bounds__(256) trsm_flow_kernel(const T* __restrict__ LU
     unsigned int* const mine = lower ? fl : fu;
     const int r0 = i * 64, h = min(64, m - r0);
     const T* Di = Dinv + (size_t)i * 2 * 64 * 64 + (lower ? 0 : 64 * 64);
-    stage_tile<T, false>(Ds, Di, 64, 64, 64);
+    // the diagonal inverse, transposed: Dt[k][a] = D[a][k]
+    for (int e = tid; e < 64 * 64; e += 256) Dt[e & 63][e >> 6] = Di[e];
     if (!lower && !flow_wait(fl + i, err, &s_ok)) return;      // Y_i from the forward solve
     const int nj = lower ? i : nbk - 1 - i;
     for (int q0 = 0; q0 < rc; q0 += 64) {
         const int rw = min(64, rc - q0);
-        stage_tile<T, true>(Acc, X + (size_t)r0 * rc + q0, rc, h, rw);
-        __syncthreads();                                          // Acc and Ds complete
+        T acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int row = 4 * ty + a, col = 4 * tx + c;
+                acc[a][c] = (row < h && col < rw) ? __ldcg(X + (size_t)(r0 + row) * rc + q0 + col) : T(0);
+            }
         for (int q = 0; q < nj; ++q) {
             const int j = lower ? q : nbk - 1 - q;
             const int c0 = j * 64, w = min(64, m - c0);
-            stage_tile<T, false>(Ls, LU + (size_t)r0 * lda + c0, lda, h, w);
+            // L_ij transposed (rows of the block, columns of block j), fetched before the flag wait
+            for (int e = tid; e < 64 * 64; e += 256) {
+                const int a = e >> 6, k = e & 63;
+                Lt[k][a] = (a < h && k < w) ? LU[(size_t)(r0 + a) * lda + c0 + k] : T(0);
+            }
             if (!flow_wait(mine + j, err, &s_ok)) return;
-            stage_tile<T, true>(Xs, X + (size_t)c0 * rc + q0, rc, w, rw);
+            for (int e = tid; e < 64 * 64; e += 256) {
+                const int k = e >> 6, c = e & 63;
+                Xs[k][c] = (k < w && c < rw) ? __ldcg(X + (size_t)(c0 + k) * rc + q0 + c) : T(0);
+            }
             __syncthreads();
-            for (int r = rq; r < rw; r += 4) {
-                T acc = Acc[ii][r];
-#pragma unroll 16
-                for (int k = 0; k < 64; ++k) acc = fma(-Ls[ii][k], Xs[k][r], acc);
-                Acc[ii][r] = acc;
+#pragma unroll 8
+            for (int k = 0; k < 64; ++k) {
+                T l4[4], x4[4];
+                ld4(&Lt[k][4 * ty], l4);
+                ld4(&Xs[k][4 * tx], x4);
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[a][c] = fma(-l4[a], x4[c], acc[a][c]);
             }
             __syncthreads();
         }
-        for (int r = rq; r < rw; r += 4) {
-            T acc = T(0);
-#pragma unroll 16
-            for (int k = 0; k < 64; ++k) acc = fma(Ds[ii][k], Acc[k][r], acc);
-            if (ii < h) X[(size_t)(r0 + ii) * rc + q0 + r] = acc;
+        // X_i = D (B_i - sum_j L_ij X_j)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) As[4 * ty + a][4 * tx + c] = acc[a][c];
+        __syncthreads();
+        T out[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) out[a][c] = T(0);
+#pragma unroll 8
+        for (int k = 0; k < 64; ++k) {
+            T d4[4], a4[4];
+            ld4(&Dt[k][4 * ty], d4);
+            ld4(&As[k][4 * tx], a4);
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) out[a][c] = fma(d4[a], a4[c], out[a][c]);
         }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int row = 4 * ty + a, col = 4 * tx + c;
+                if (row < h && col < rw) X[(size_t)(r0 + row) * rc + q0 + col] = out[a][c];
+            }
         __syncthreads();
     }
     if (tid == 0) st_release_u32(mine + i, 1u);     // after the barrier: publishes the CTA's writes
@@ -1743,7 +1801,7 @@ __global__ void __launch_bounds__(256) trsm_flow_vec_kernel(const T* __restrict_
 }
 
 template <typename T>
-constexpr size_t flow_smem() { return sizeof(T) * 4 * 64 * 65; }
+constexpr size_t flow_smem() { return sizeof(T) * 4 * 64 * kFlowLd; }
 
 constexpr size_t flow_state_words(int64_t m) { return 2 + 2 * (size_t)((m + 63) / 64); }
 
