@@ -255,8 +255,12 @@ typedef struct {
                                  0 -> one right-hand side at a time, Newton for semilinear.   */
     int newton_refactor;      /* mixed-mode Newton: 0 -> each Newton system is refined with the
                                  FP32 factors of the last Jacobian factored while that refinement
-                                 reaches 1e-10 in 24 sweeps (refactored otherwise); 1 -> the
-                                 Jacobian of every step is factored                           */
+                                 reaches its inexact-Newton forcing term in 24 sweeps (refactored
+                                 otherwise); 1 -> the Jacobian of every step is factored        */
+    int assembly;             /* mixed mode, assembly of Lambda on the tensor cores: 0 -> FP16
+                                 (P and Q scaled by powers of two, each split into two FP16
+                                 halves, three products: twice the TF32 rate); 1 -> TF32 (each
+                                 FP32 operand split into two TF32 parts, three products)        */
 } ewos_problem;
 
 typedef struct {
@@ -396,6 +400,13 @@ ewos_status ewos_debug_green_radius(const void* u, void* R, int64_t count, int p
  * computed, each also stored transposed: for a symmetric A^T B, M = N).  EWOS_EINVAL when the
  * device has no sm_100-family tensor cores. */
 ewos_status ewos_debug_tc_gemm(const float* A, const float* B, float* C, int M, int N, int K, int split);
+/* Test hook (no counterpart in the paper): the tensor-core assembly of the mixed-precision solve,
+ * C [m][m] = Lambda = P^T Q with Q_i = M_i P_i (eq. linear_q), for host arrays P [D+1][n][m] (FP32),
+ * M [n][D+1][D+1] (FP64; row-major blocks) and C (FP32); D = 2 or 3.  f16 != 0 takes the FP16
+ * form (operands scaled by powers of two and split into FP16 halves), f16 = 0 the TF32 form
+ * (three TF32 products); sym != 0 computes the tiles on and below the diagonal and mirrors them
+ * (for symmetric M_i).  EWOS_EINVAL when the device has no sm_100-family tensor cores. */
+ewos_status ewos_debug_tc_assemble(const float* P, const double* M, int n, int m, int D, float* C, int sym, int f16);
 
 /* Test hooks for the failure paths (no counterpart in the paper).
  * ewos_debug_set_flow_wait_limit: the flag waits of the dataflow triangular solves (mixed mode)

@@ -13,9 +13,11 @@
 // Every mbarrier wait is bounded; on a timeout the kernel records an error, frees its tensor
 // memory and returns (the call then reports EWOS_ETIMEOUT).
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -35,7 +37,10 @@ constexpr long long kWaitLimit = 1ll << 22;
 // split TF32 (3xTF32): A = A_hi + A_lo, B = B_hi + B_lo, products hi.hi + hi.lo + lo.hi into the
 // same accumulator; tiles A_hi, A_lo (128 x 32) and B_hi, B_lo (128 x 32) per stage, 3 stages.
 // ST > 0 sets the ring depth instead (the LU's trailing updates, K = 64, use two stages).
-template <bool SPLIT, int ST = 0>
+// F16: the operands are FP16 (the split of a scaled FP32 value into an FP16 part and an FP16
+// remainder) and each stage holds 64 of them per row (the same 128 bytes); kind::f16 runs at twice
+// the TF32 rate.
+template <bool SPLIT, int ST = 0, bool F16 = false>
 struct Cfg {
     static constexpr int BN = SPLIT ? 128 : 256;
     static constexpr int STAGES = ST > 0 ? ST : (SPLIT ? 3 : 4);
@@ -43,8 +48,9 @@ struct Cfg {
     static constexpr int B_BYTES = BN * BK * 4;
     static constexpr int STAGE_BYTES = (SPLIT ? 2 : 1) * (A_BYTES + B_BYTES);
     static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-    static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                      ((uint32_t)(BM >> 4) << 24);
+    static constexpr int KSTAGE = F16 ? 2 * BK : BK;      // operand elements per row and stage
+    static constexpr uint32_t IDESC = (1u << 4) | ((F16 ? 0u : 2u) << 7) | ((F16 ? 0u : 2u) << 10) |
+                                      ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -105,21 +111,30 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db
         : "memory");
 }
 
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 // C tile of the subtracting update staged in shared memory (CSM): 128 rows of BN floats, rows
 // padded to BN + 4 floats so that the row-per-thread float4 reads of the epilogue are free of
 // bank conflicts; filled with cp.async by all threads at kernel start, under the main loop.
 constexpr int kCsmLd = 128 + 4;
 constexpr int kCsmBytes = BM * kCsmLd * 4;
 
-template <bool SPLIT, int ST = 0, bool CSM = false>
+template <bool SPLIT, int ST = 0, bool CSM = false, bool F16 = false>
 __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant__ CUtensorMap mapA,
                                                            const __grid_constant__ CUtensorMap mapB,
                                                            const __grid_constant__ CUtensorMap mapAl,
                                                            const __grid_constant__ CUtensorMap mapBl, int M, int N,
                                                            int Kp, float* __restrict__ C, int64_t ldc,
                                                            int* __restrict__ err, int sub, int tri = 0,
-                                                           const int* __restrict__ tiles = nullptr) {
-    using CF = Cfg<SPLIT, ST>;
+                                                           const int* __restrict__ tiles = nullptr,
+                                                           const float* __restrict__ cscale = nullptr) {
+    using CF = Cfg<SPLIT, ST, F16>;
     constexpr int BN = CF::BN, STAGES = CF::STAGES, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
     constexpr int STAGE_BYTES = CF::STAGE_BYTES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -148,7 +163,7 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
     }
     const int m0 = tile_y * BM, n0 = tile_x * BN;
     const bool mirror = tri && tile_x != tile_y;
-    const int nk = Kp / BK;
+    const int nk = Kp / CF::KSTAGE;                // (Kp counts operand elements)
     ::ewos::pdl_trigger();
 
     if (threadIdx.x == 0) {
@@ -193,11 +208,11 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
             if (!mbar_wait(&empty[s], ph ^ 1u)) { s_fail = 1; break; }
             unsigned char* st = smem + s * STAGE_BYTES;
             mbar_expect_tx(&full[s], STAGE_BYTES);
-            tma_load_2d(st, &mapA, &full[s], kb * BK, m0);
-            tma_load_2d(st + A_BYTES, &mapB, &full[s], kb * BK, n0);
+            tma_load_2d(st, &mapA, &full[s], kb * CF::KSTAGE, m0);
+            tma_load_2d(st + A_BYTES, &mapB, &full[s], kb * CF::KSTAGE, n0);
             if (SPLIT) {
-                tma_load_2d(st + A_BYTES + B_BYTES, &mapAl, &full[s], kb * BK, m0);
-                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mapBl, &full[s], kb * BK, n0);
+                tma_load_2d(st + A_BYTES + B_BYTES, &mapAl, &full[s], kb * CF::KSTAGE, m0);
+                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mapBl, &full[s], kb * CF::KSTAGE, n0);
             }
         }
     } else if (threadIdx.x == 32) {
@@ -209,16 +224,22 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             unsigned char* st = smem + s * STAGE_BYTES;
 #pragma unroll
-            for (int k = 0; k < BK / 8; ++k) {
+            for (int k = 0; k < BK / 8; ++k) {      // 32-byte steps: K = 8 TF32 or 16 FP16 per MMA
                 const uint64_t da = smem_desc(st + k * 32);
                 const uint64_t db = smem_desc(st + A_BYTES + k * 32);
                 const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
-                mma_tf32(tmem, da, db, CF::IDESC, acc);
+                if constexpr (F16) mma_f16(tmem, da, db, CF::IDESC, acc);
+                else mma_tf32(tmem, da, db, CF::IDESC, acc);
                 if (SPLIT) {
                     const uint64_t dal = smem_desc(st + A_BYTES + B_BYTES + k * 32);
                     const uint64_t dbl = smem_desc(st + 2 * A_BYTES + B_BYTES + k * 32);
-                    mma_tf32(tmem, da, dbl, CF::IDESC, 1u);
-                    mma_tf32(tmem, dal, db, CF::IDESC, 1u);
+                    if constexpr (F16) {
+                        mma_f16(tmem, da, dbl, CF::IDESC, 1u);
+                        mma_f16(tmem, dal, db, CF::IDESC, 1u);
+                    } else {
+                        mma_tf32(tmem, da, dbl, CF::IDESC, 1u);
+                        mma_tf32(tmem, dal, db, CF::IDESC, 1u);
+                    }
                 }
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -268,6 +289,12 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if constexpr (F16) {
+                // the operands were scaled by powers of two: undo it (exact)
+                const float sc = cscale ? *cscale : 1.0f;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) * sc);
+            }
             const int col0 = n0 + c * 32;
             float4 ccur[8];
             if constexpr (CSM) {
@@ -437,6 +464,19 @@ static bool make_map(CUtensorMap* map, const float* base, int rows, int Kp, int 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// FP16 operand: [rows][Kp] halves, box of 64 halves (128 bytes) by box_rows
+static bool make_map16(CUtensorMap* map, const void* base, int rows, int Kp, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * BK), (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // scratch for the K-major operands and the error word (stream-ordered pool)
 struct Scratch {
     float* At = nullptr;
@@ -445,6 +485,7 @@ struct Scratch {
     float* Btl = nullptr;
     int* err = nullptr;
     size_t cap = 0;
+    float* scale = nullptr;        // FP16 assembly: [0] max |P|, [1] max row sum of |M|, [2] s_P, [3] s_Q, [4] 1/(s_P s_Q)
     int* tiles = nullptr;          // (tile row, tile column) per CTA, blocked order
     long long tiles_key = -1;      // shape the table was made for
     int tiles_count = 0;
@@ -507,7 +548,7 @@ struct TcScratch {
 void tc_scratch_free(TcScratch* t) {
     if (!t) return;
     ::ewos::dev_free(t->s.At); ::ewos::dev_free(t->s.Bt); ::ewos::dev_free(t->s.Atl); ::ewos::dev_free(t->s.Btl);
-    ::ewos::dev_free(t->s.err); ::ewos::dev_free(t->s.tiles);
+    ::ewos::dev_free(t->s.err); ::ewos::dev_free(t->s.tiles); ::ewos::dev_free(t->s.scale);
     delete t;
 }
 
@@ -628,13 +669,175 @@ __global__ void pq_split_kernel(const float* __restrict__ P, const double* __res
     }
 }
 
+// The FP16 form of the assembly.  FP16 has the 11-bit significand of TF32 and twice its tensor-core
+// rate, but a narrow exponent range, so P and Q enter scaled by powers of two s_P, s_Q that put
+// their largest magnitudes in [2^13, 2^14); v s = h + l with h = fp16(v s) and l = fp16(v s - h),
+// and the three products hi.hi + hi.lo + lo.hi are unscaled by 1 / (s_P s_Q) in the epilogue
+// (exact).  Entries below 2^-3 after scaling keep an absolute error of 2^-25 (the low part is an
+// FP16 subnormal there), 2^-39 of the largest entry.
+__device__ __forceinline__ void f16_split(float v, __half& h, __half& l) {
+    h = __float2half_rn(v);
+    l = __float2half_rn(v - __half2float(h));
+}
+
+// scale[0] = max |P| over `count` values, scale[1] = max over the nodes of the largest row sum of |M_i|
+__global__ void pq_absmax_kernel(const float* __restrict__ P, int64_t count, const double* __restrict__ M, int n,
+                                 int E, float* __restrict__ scale) {
+    float mx = 0.f;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x)
+        mx = fmaxf(mx, fabsf(P[t]));
+    float mm = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int j = 0; j < E; ++j) {
+            double r = 0.0;
+            for (int l = 0; l < E; ++l) r += fabs(M[(size_t)i * E * E + j * E + l]);
+            mm = fmaxf(mm, (float)r);
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(reinterpret_cast<unsigned int*>(scale), __float_as_uint(mx));       // (non-negative floats)
+        atomicMax(reinterpret_cast<unsigned int*>(scale + 1), __float_as_uint(mm));
+    }
+}
+
+// powers of two s_P, s_Q with max |P| s_P and max |Q| s_Q in [2^13, 2^14) (|Q| <= max |P| times the
+// largest row sum of |M|, with a little room for the rounding of Q), and their inverse product
+__global__ void pq_scale_kernel(float* scale) {
+    if (threadIdx.x != 0) return;
+    const float mp = scale[0], mq = scale[0] * scale[1] * 1.0001f;
+    auto pw = [](float mxv) {
+        if (!(mxv > 0.f) || !isfinite(mxv)) return 1.0f;
+        int e;
+        frexpf(mxv, &e);               // mxv in [2^(e-1), 2^e)
+        return ldexpf(1.0f, 14 - e);
+    };
+    const float sp = pw(mp), sq = pw(mq);
+    scale[2] = sp;
+    scale[3] = sq;
+    scale[4] = 1.0f / (sp * sq);
+}
+
+template <int E>
+__global__ void pq_split16_kernel(const float* __restrict__ P, const double* __restrict__ M, int n, int m,
+                                  __half* __restrict__ at, __half* __restrict__ atl, __half* __restrict__ bt,
+                                  __half* __restrict__ btl, int Kp, const float* __restrict__ scale) {
+    __shared__ float Pt[E][32][33];
+    __shared__ float Ms[32][E * E];
+    ::ewos::pdl_trigger();
+    ::ewos::pdl_wait();
+    const float sp = scale[2], sq = scale[3];
+    const int c0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const size_t nm = (size_t)n * m;
+    for (int r = ty; r < 32; r += blockDim.y) {
+        const int i = i0 + r, c = c0 + tx;
+#pragma unroll
+        for (int l = 0; l < E; ++l) Pt[l][r][tx] = (i < n && c < m) ? P[l * nm + (size_t)i * m + c] : 0.f;
+    }
+    for (int t = ty * 32 + tx; t < 32 * E * E; t += 32 * blockDim.y) {
+        const int r = t / (E * E), q = t % (E * E);
+        Ms[r][q] = i0 + r < n ? (float)M[(size_t)(i0 + r) * E * E + q] : 0.f;
+    }
+    __syncthreads();
+    const int i = i0 + tx;
+    if (i >= n) return;
+    for (int cc = ty; cc < 32; cc += blockDim.y) {
+        const int c = c0 + cc;
+        if (c >= m) break;
+        float pv[E];
+#pragma unroll
+        for (int l = 0; l < E; ++l) pv[l] = Pt[l][tx][cc];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            float qv = 0.f;
+#pragma unroll
+            for (int l = 0; l < E; ++l) qv = fmaf(Ms[tx][j * E + l], pv[l], qv);
+            const size_t k = (size_t)j * n + i, o = (size_t)c * Kp + k;
+            __half h, lo;
+            f16_split(pv[j] * sp, h, lo);
+            at[o] = h;
+            atl[o] = lo;
+            f16_split(qv * sq, h, lo);
+            bt[o] = h;
+            btl[o] = lo;
+        }
+    }
+}
+
 // Lambda [m][m] = P^T Q with Q = M P, both operands prepared by pq_split_kernel, then the
 // three-product TF32 GEMM; waits for the launch (pipeline timeouts are reported)
+// The FP16 form of tc_assemble_pq (same operands in FP16 halves, twice the tensor-core rate)
+static ewos_status tc_assemble_pq16(tc::Scratch& S, const float* P, const double* Mc, int n, int m, int D, float* C,
+                                    cudaStream_t st, bool sym) {
+    using namespace tc;
+    const int E = D + 1, K = E * n;
+    const int Kp = (K + 2 * BK - 1) / (2 * BK) * (2 * BK);          // halves, 128-byte rows
+    const size_t need_f = ((size_t)m * Kp + 1) / 2;                   // floats of scratch per operand
+    if (S.cap < need_f || !S.Atl) {
+        ::ewos::dev_free(S.At); ::ewos::dev_free(S.Bt); ::ewos::dev_free(S.Atl); ::ewos::dev_free(S.Btl);
+        S.At = S.Bt = S.Atl = S.Btl = nullptr;
+        S.cap = 0;
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.At, sizeof(float) * need_f));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Bt, sizeof(float) * need_f));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Atl, sizeof(float) * need_f));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Btl, sizeof(float) * need_f));
+        S.cap = need_f;
+    }
+    if (!S.err) EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.err, sizeof(int)));
+    if (!S.scale) EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.scale, sizeof(float) * 8));
+    __half* at = reinterpret_cast<__half*>(S.At);
+    __half* atl = reinterpret_cast<__half*>(S.Atl);
+    __half* bt = reinterpret_cast<__half*>(S.Bt);
+    __half* btl = reinterpret_cast<__half*>(S.Btl);
+    if (Kp > K) {   // zero padding of the reduction dimension
+        for (__half* b : {at, atl, bt, btl})
+            EWOS_CUDA_TRY(cudaMemset2DAsync(b + K, sizeof(__half) * Kp, 0, sizeof(__half) * (Kp - K), m, st));
+    }
+    EWOS_CUDA_TRY(cudaMemsetAsync(S.scale, 0, sizeof(float) * 8, st));
+    if (E != 3 && E != 4) {
+        set_error("tensor-core assembly: dimension must be 2 or 3");
+        return EWOS_EINVAL;
+    }
+    ::ewos::note_launch(), pq_absmax_kernel<<<4 * 148, 256, 0, st>>>(P, (int64_t)E * n * m, Mc, n, E, S.scale);
+    ::ewos::note_launch(), pq_scale_kernel<<<1, 32, 0, st>>>(S.scale);
+    const dim3 grid((unsigned)((m + 31) / 32), (unsigned)((n + 31) / 32)), tb(32, 8);
+    ::ewos::note_launch();
+    if (E == 3) pq_split16_kernel<3><<<grid, tb, 0, st>>>(P, Mc, n, m, at, atl, bt, btl, Kp, S.scale);
+    else if (E == 4) pq_split16_kernel<4><<<grid, tb, 0, st>>>(P, Mc, n, m, at, atl, bt, btl, Kp, S.scale);
+    else {
+        set_error("tensor-core assembly: dimension must be 2 or 3");
+        return EWOS_EINVAL;
+    }
+    EWOS_CUDA_TRY(cudaGetLastError());
+    using CF = Cfg<true, 0, true>;
+    CUtensorMap ma, mb, mal, mbl;
+    if (!(make_map16(&ma, at, m, Kp, BM) && make_map16(&mb, bt, m, Kp, CF::BN) && make_map16(&mal, atl, m, Kp, BM) &&
+          make_map16(&mbl, btl, m, Kp, CF::BN))) {
+        set_error("tensor-core assembly: cuTensorMapEncodeTiled failed");
+        return EWOS_ECUDA;
+    }
+    EWOS_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
+    auto k = gemm_tf32_kernel<true, 0, false, true>;
+    EWOS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM_BYTES));
+    const int nt = (m + BM - 1) / BM;
+    int ntiles = 0;
+    if (ewos_status ts = tile_table(S, nt, (m + CF::BN - 1) / CF::BN, sym, st, &ntiles); ts != EWOS_OK) return ts;
+    ::ewos::note_launch(), k<<<ntiles, 128, CF::SMEM_BYTES, st>>>(ma, mb, mal, mbl, m, m, Kp, C, m, S.err, 0, sym ? 1 : 0,
+                                                                  S.tiles, S.scale + 4);
+    EWOS_CUDA_TRY(cudaGetLastError());
+    return tc_check(S, st);
+}
+
 ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D, float* C, cudaStream_t st,
-                           TcScratch** owned, bool sym = false) {
+                           TcScratch** owned, bool sym = false, bool f16 = true) {
     using namespace tc;
     if (!*owned) *owned = new TcScratch();
     Scratch& S = (*owned)->s;
+    if (f16) return tc_assemble_pq16(S, P, Mc, n, m, D, C, st, sym);
     const int E = D + 1, K = E * n;
     const int Kp = (K + BK - 1) / BK * BK;
     const size_t need = (size_t)m * Kp;
@@ -779,10 +982,10 @@ ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64
     ::ewos::note_launch();
     if (csm)
         EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true, kUpd, true>, grid, dim3(128), kCsmSmem, st, ma, mb, mal, mbl,
-                                         M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr));
+                                         M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr));
     else
         EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true>, grid, dim3(128), (size_t)Cfg<true>::SMEM_BYTES, st, ma, mb,
-                                         mal, mbl, M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr));
+                                         mal, mbl, M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr));
     return EWOS_OK;
 }
 
@@ -838,5 +1041,36 @@ extern "C" ewos_status ewos_debug_tc_gemm(const float* A, const float* B, float*
     if (s == EWOS_OK && cudaMemcpy(C, dC, sizeof(float) * (size_t)M * N, cudaMemcpyDeviceToHost) != cudaSuccess) s = EWOS_ECUDA;
     dev_free(dA); dev_free(dB); dev_free(dC);
     cudaDeviceSynchronize();
+    return s;
+}
+
+extern "C" ewos_status ewos_debug_tc_assemble(const float* P, const double* M, int n, int m, int D, float* C, int sym,
+                                              int f16) {
+    using namespace ewos;
+    if (!P || !M || !C || n < 1 || m < 1 || (D != 2 && D != 3)) {
+        set_error("ewos_debug_tc_assemble: bad arguments");
+        return EWOS_EINVAL;
+    }
+    if (!tc_assemble_available()) { set_error("tensor cores (sm_100 family) not available"); return EWOS_EINVAL; }
+    const size_t E = (size_t)D + 1, np_ = E * (size_t)n * m, nm_ = (size_t)n * E * E, nc = (size_t)m * m;
+    AllocStream as(nullptr);
+    float *dP = nullptr, *dC = nullptr;
+    double* dM = nullptr;
+    TcScratch* owned = nullptr;
+    ewos_status s = EWOS_OK;
+    if (dev_alloc((void**)&dP, sizeof(float) * np_) != cudaSuccess || dev_alloc((void**)&dM, sizeof(double) * nm_) != cudaSuccess ||
+        dev_alloc((void**)&dC, sizeof(float) * nc) != cudaSuccess) {
+        set_error("ewos_debug_tc_assemble: out of device memory");
+        s = EWOS_ENOMEM;
+    }
+    if (s == EWOS_OK && (cudaMemcpy(dP, P, sizeof(float) * np_, cudaMemcpyHostToDevice) != cudaSuccess ||
+                         cudaMemcpy(dM, M, sizeof(double) * nm_, cudaMemcpyHostToDevice) != cudaSuccess ||
+                         cudaMemset(dC, 0, sizeof(float) * nc) != cudaSuccess))
+        s = EWOS_ECUDA;
+    if (s == EWOS_OK) s = tc_assemble_pq(dP, dM, n, m, D, dC, nullptr, &owned, sym != 0, f16 != 0);
+    if (s == EWOS_OK && cudaMemcpy(C, dC, sizeof(float) * nc, cudaMemcpyDeviceToHost) != cudaSuccess) s = EWOS_ECUDA;
+    cudaDeviceSynchronize();
+    tc_scratch_free(owned);
+    dev_free(dP); dev_free(dM); dev_free(dC);
     return s;
 }

@@ -78,7 +78,7 @@ ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64
                               int b_off = 0);
 ewos_status tc_update_reserve(int max_mn, int k, cudaStream_t st, TcScratch** owned);
 ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D, float* C, cudaStream_t st,
-                           TcScratch** owned, bool sym = false);
+                           TcScratch** owned, bool sym = false, bool f16 = true);
 void tc_update_operands(TcScratch* t, float** a_hi, float** a_lo, float** b_hi, float** b_lo);
 ewos_status tc_update_check(TcScratch* t, cudaStream_t st);
 bool tc_assemble_available();
@@ -3451,7 +3451,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                 rep->gemm_flop += (pb->b == nullptr ? (double)C.m * (double)(C.m + 1) : 2.0 * (double)C.m * (double)C.m) *
                                   (double)(C.E * C.n);
                 ewos_status st = tc_assemble_pq(P32, ws->M, (int)C.n, (int)C.m, C.D, ws->L32, C.st, &ws->tc,
-                                                    pb->b == nullptr);
+                                                    pb->b == nullptr, pb->assembly != 1);
                 if (st != EWOS_OK) return st;
             } else {
                 assemble_mixed<TP>(C, P32);
@@ -3621,7 +3621,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                 rep->gemm_flop += (pb->b == nullptr ? (double)C.m * (double)(C.m + 1) : 2.0 * (double)C.m * (double)C.m) *
                                   (double)(C.E * C.n);
                     ewos_status st = tc_assemble_pq(P32, ws->M, (int)C.n, (int)C.m, C.D, ws->L32, C.st, &ws->tc,
-                                                    pb->b == nullptr);
+                                                    pb->b == nullptr, pb->assembly != 1);
                     if (st != EWOS_OK) return st;
                 } else {
                     assemble_mixed<TP>(C, P32);

@@ -23,6 +23,7 @@ ARR = {"G": 0, "gradG": 1, "H": 2, "gradH": 3, "Hc": 4, "lambda": 5, "walk_exit"
        "walk_mass": 8, "walk_vhash": 9, "walk_xexit": 10}
 NL = {"linear": 0, "semilinear": 1, "quasilinear": 2}
 MODE = {"fp64": 0, "mixed": 1}
+ASSEMBLY = {"fp16": 0, "tf32": 1}
 
 
 class EwosError(RuntimeError):
@@ -61,7 +62,7 @@ class _Problem(ctypes.Structure):
                 ("nl_coef", ctypes.c_void_p), ("nl_ncoef", ctypes.c_int), ("mode", ctypes.c_int),
                 ("rcond", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("inputs_on_device", ctypes.c_int), ("stream", ctypes.c_void_p), ("pivoting", ctypes.c_int),
-                ("batched", ctypes.c_int), ("newton_refactor", ctypes.c_int)]
+                ("batched", ctypes.c_int), ("newton_refactor", ctypes.c_int), ("assembly", ctypes.c_int)]
 
 
 class SolveReport(ctypes.Structure):
@@ -137,6 +138,7 @@ def lib():
         L.ewos_debug_philox.argtypes = [P, P, P, I64]
         L.ewos_debug_green_radius.argtypes = [P, P, I64, I]
         L.ewos_debug_tc_gemm.argtypes = [P, P, P, I, I, I, I]
+        L.ewos_debug_tc_assemble.argtypes = [P, P, I, I, I, P, I, I]
         L.ewos_debug_set_flow_wait_limit.argtypes = [I64]
         L.ewos_debug_fail_allocations.argtypes = [I64]
         L.ewos_debug_fail_allocations.restype = None
@@ -157,7 +159,7 @@ def lib():
                                          ctypes.POINTER(AdamReport)]
         for fn in ("ewos_toolbox_build", "ewos_toolbox_build_noalloc", "ewos_toolbox_from_host", "ewos_toolbox_get", "ewos_toolbox_report",
                    "ewos_toolbox_shape", "ewos_solve", "ewos_debug_philox", "ewos_debug_green_radius",
-                   "ewos_debug_tc_gemm", "ewos_server_create", "ewos_server_submit", "ewos_server_wait",
+                   "ewos_debug_tc_gemm", "ewos_debug_tc_assemble", "ewos_server_create", "ewos_server_submit", "ewos_server_wait",
                    "ewos_server_query", "ewos_toolbox_build_batch", "ewos_toolbox_save", "ewos_toolbox_load",
                    "ewos_gradient", "ewos_minimize_adam", "ewos_operators"):
             getattr(L, fn).restype = I
@@ -236,10 +238,11 @@ class Toolbox:
 
     def solve(self, A, f, g, b=None, c=None, kind="linear", coef=None, mode="fp64", rcond=-1.0, tol=0.0,
               max_iter=0, want_s=False, on_device=False, out=None, stream=None, pivoting=0, batched=False,
-              newton_refactor=False):
+              newton_refactor=False, assembly="fp16"):
         """Solve the problem of include/ewos.h; returns (u [nrhs][n] or [n], s or None, report).
         pivoting=1 forces row interchanges in the mixed-mode LU; batched=True refines all
-        right-hand sides together (mixed mode; chord iteration for semilinear problems)."""
+        right-hand sides together (mixed mode; chord iteration for semilinear problems);
+        assembly="tf32" assembles Lambda from TF32 parts instead of scaled FP16 halves."""
         if on_device:
             Ad, fd, gd, bd, cd = A, f, g, b, c
             nrhs = f.shape[0] if f.dim() == 2 else 1
@@ -249,7 +252,8 @@ class Toolbox:
         cf = _f64(coef) if coef is not None else None
         pb = _Problem(_ptr(Ad), _ptr(bd), _ptr(cd), _ptr(fd), _ptr(gd), nrhs, NL[kind], _ptr(cf),
                       0 if cf is None else cf.size, MODE[mode], float(rcond), float(tol), int(max_iter),
-                      1 if on_device else 0, stream, int(pivoting), 1 if batched else 0, 1 if newton_refactor else 0)
+                      1 if on_device else 0, stream, int(pivoting), 1 if batched else 0, 1 if newton_refactor else 0,
+                      ASSEMBLY[assembly])
         if out is not None:
             u = out
             optr = out.data_ptr()
@@ -433,6 +437,19 @@ def debug_tc_gemm(A, B, split=False, sym=False):
     c = np.zeros((M, N), dtype=np.float32)
     _check(lib().ewos_debug_tc_gemm(a.ctypes.data, b.ctypes.data, c.ctypes.data, M, N, K,
                                     2 if sym else (1 if split else 0)), "tc gemm")
+    return c
+
+
+def debug_tc_assemble(P, M, sym=False, f16=True):
+    """Lambda = P^T Q, Q_i = M_i P_i, by the tensor-core assembly of the mixed solve: P [D+1][n][m],
+    M [n][D+1][D+1]; f16: scaled FP16 halves (else three TF32 products); sym: mirrored lower half."""
+    p = np.ascontiguousarray(P, dtype=np.float32)
+    mm = np.ascontiguousarray(M, dtype=np.float64)
+    E, n, m = p.shape
+    assert mm.shape == (n, E, E)
+    c = np.zeros((m, m), dtype=np.float32)
+    _check(lib().ewos_debug_tc_assemble(p.ctypes.data, mm.ctypes.data, n, m, E - 1, c.ctypes.data,
+                                        1 if sym else 0, 1 if f16 else 0), "tc assemble")
     return c
 
 

@@ -154,10 +154,13 @@ def test_square4096_full_size_fp64_residual():
 # compared with the oracle run with that alpha (1e-9), and with the FP64 GPU path by the R16
 # solution bar.
 
-def test_mixed_linear_matches_oracle(disk):
+@pytest.mark.parametrize("assembly", ["fp16", "tf32"])
+def test_mixed_linear_matches_oracle(disk, assembly):
+    # Lambda assembled on the tensor cores from scaled FP16 halves (the default) or TF32 parts:
+    # either way the refined solution is the oracle's for the same shift alpha
     w, tb, lam, gtb = disk
     pb = w.problem
-    u, s, rep = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, c=pb.c, mode="mixed", want_s=True)
+    u, s, rep = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, c=pb.c, mode="mixed", want_s=True, assembly=assembly)
     assert rep["converged"] and rep["refine_iters"] >= 1
     ref = S.solve_linear(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, alpha=rep["alpha"])
     assert _rel(u, ref["u"]) < 1e-9
@@ -196,6 +199,13 @@ def test_mixed_square4096_full_size():
     pb = w.problem
     gtb = ewos.build_workload(w)
     u, s, rep = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, want_s=True, mode="mixed")
+    # the two tensor-core assemblies reach the same refined solution, in as many sweeps; the shift
+    # alpha = rcond ||Lambda_32||_F comes from each assembly's own FP32 matrix, whose norm the
+    # tensor cores' truncating accumulation lowers by about 5e-9 K relative (K = 3 n = 12288 here)
+    ut, _, rept = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, mode="mixed", assembly="tf32")
+    assert rept["converged"] and abs(rept["refine_iters"] - rep["refine_iters"]) <= 1
+    assert abs(rept["alpha"] - rep["alpha"]) <= 2e-4 * rep["alpha"]
+    assert _rel(u, ut) < 1e-4
     u64, s64, rep64 = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, want_s=True, mode="fp64")
     mats = gtb.matrices()
     lam = gtb.get("lambda")

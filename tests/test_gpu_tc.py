@@ -57,3 +57,62 @@ def test_tc_gemm_symmetric_launch(M, K):
     tj = np.arange(M)[None, :] // 128
     off = ti != tj
     assert np.array_equal(C[off], C.T[off])
+
+
+def _pq_case(n, m, D, seed, spread, sym=False):
+    """P [D+1][n][m] with magnitudes log-uniform over `spread` decades below 1e-2 and random
+    signs (the bins of G and grad G range over several decades); M_i = lam_i [[A_i, 0], [b_i^T, c_i]]
+    with A_i symmetric positive definite (sym: b_i = 0, so Q_i = M_i P_i gives a symmetric Lambda)."""
+    rng = np.random.default_rng(seed)
+    E = D + 1
+    mag = 10.0 ** rng.uniform(-2.0 - spread, -2.0, size=(E, n, m))
+    P = (mag * rng.choice([-1.0, 1.0], size=(E, n, m))).astype(np.float32)
+    lam = rng.uniform(0.5, 1.5, size=n) / n
+    R = rng.normal(size=(n, D, D))
+    A = np.einsum("nij,nkj->nik", R, R) + np.eye(D)[None]
+    M = np.zeros((n, E, E))
+    M[:, :D, :D] = lam[:, None, None] * A
+    M[:, D, D] = lam * rng.uniform(0.0, 2.0, size=n)
+    if not sym:
+        M[:, D, :D] = lam[:, None] * rng.normal(size=(n, D))
+    return P, M
+
+
+def _pq_ref(P, M):
+    """Lambda = sum_{l, i} P[l][i]^T Q[l][i] with Q_i = M_i P_i in FP64, and sum |P|^T |Q|"""
+    P64 = P.astype(np.float64)
+    Q = np.einsum("ijk,kic->jic", M, P64)
+    E, n, m = P.shape
+    P2, Q2 = P64.reshape(E * n, m), Q.reshape(E * n, m)
+    return P2.T @ Q2, np.abs(P2).T @ np.abs(Q2)
+
+
+@pytest.mark.parametrize("f16", [True, False])
+@pytest.mark.parametrize("n,m,D,sym,spread", [(200, 150, 2, False, 3.0), (300, 260, 3, True, 6.0),
+                                              (1000, 520, 2, False, 9.0), (64, 33, 3, False, 1.0)])
+def test_tc_assemble_pq(n, m, D, sym, spread, f16):
+    """Lambda = P^T (M P) as the mixed solve assembles it: FP16 halves of the scaled operands or
+    three TF32 products.  Both keep about 22 significand bits per operand; with Q formed in FP32
+    and FP32 accumulation each entry is within (2^-19 + K 2^-23) sum |P||Q|; in the FP16 form the
+    entries far below the largest keep an absolute error of 2^-25 / s (s the power of two that
+    scaled the operand), which adds 2^-24 / s_P sum |Q| + 2^-24 / s_Q sum |P|.  The tensor cores
+    round their FP32 accumulation toward zero, so the error of the whole matrix is a bias that grows
+    with K (measured: ||C - Lambda||_F / ||Lambda||_F about 5e-9 K for both forms); the test allows
+    2e-8 K, and checks the sign of the bias (||C||_F below ||Lambda||_F)."""
+    P, M = _pq_case(n, m, D, n + m + D, spread, sym)
+    C = ewos.debug_tc_assemble(P, M, sym=sym, f16=f16).astype(np.float64)
+    ref, absref = _pq_ref(P, M)
+    K = (D + 1) * n
+    bound = (2.0 ** -19 + K * 2.0 ** -23) * absref
+    if f16:
+        E = D + 1
+        Q = np.einsum("ijk,kic->jic", M, P.astype(np.float64)).reshape(E * n, m)
+        P2 = np.abs(P.astype(np.float64)).reshape(E * n, m)
+        s_p = 2.0 ** (13 - np.floor(np.log2(P2.max())))
+        s_q = 2.0 ** (13 - np.floor(np.log2(np.abs(Q).max())))
+        bound += 2.0 ** -24 / s_p * np.abs(Q).sum(axis=0)[None, :] + 2.0 ** -24 / s_q * P2.sum(axis=0)[:, None]
+    err = np.abs(C - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    rel = np.linalg.norm(C - ref) / np.linalg.norm(ref)
+    assert rel < 2e-8 * K
+    assert np.linalg.norm(C) < np.linalg.norm(ref)

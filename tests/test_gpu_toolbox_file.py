@@ -40,7 +40,9 @@ def test_built_fp32_toolbox_round_trip(tmp_path):
     pb = W.make_problem("square", x, z)
     u1, _, _ = tb.solve(pb.A, pb.f, pb.g, b=pb.b, mode="mixed")
     u2, _, _ = tb2.solve(pb.A, pb.f, pb.g, b=pb.b, mode="mixed")
-    assert np.array_equal(u1, u2)
+    # (the refinement's FP64 reductions add their partial sums by atomics in no fixed order, so
+    # two solves agree to rounding, well inside the refinement tolerance)
+    assert np.linalg.norm(u1 - u2) <= 1e-9 * np.linalg.norm(u1)
     tb.close()
     tb2.close()
 
