@@ -80,6 +80,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
+// as mbar_wait, sleeping `ns` nanoseconds between polls: for warps that wait long and share their
+// SM sub-partition with the TMA and MMA threads (a hot poll takes issue slots from them)
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, int ns) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        __nanosleep(ns);
+    }
+    return false;
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
@@ -354,6 +371,214 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
 }
 
+#ifndef EWOS_DRAIN_SLEEP
+#define EWOS_DRAIN_SLEEP 128
+#endif
+
+// The long-K products of the assembly (Lambda = P^T Q and the Jacobian's G^T D G, K up to 4 n)
+// with two-level accumulation.  The tensor cores round the FP32 accumulation of each MMA toward
+// zero, so one accumulator run over all of K loses about 5e-9 K of every entry's magnitude (a bias,
+// not noise: 6e-5 at K = 12288).  Here the MMAs accumulate chunks of `dk` k-blocks (256 operand
+// elements by default) into one of two TMEM accumulators in turn, while four drain warps add the
+// finished chunks into FP32 registers (round to nearest): the bias is then that of one chunk,
+// about 1e-6 (measured: 6.5e-7 for chunks of 128, 2e-6 for 512).  Each drain reads 64 KB of TMEM
+// and costs the MMAs about 125 ns (more accumulators, to give the drains slack, did not change
+// that), so the chunk stays long: 4 % over one accumulator for all of K at 256.  Warp roles: warps 0-3 drain (warp w reads TMEM lanes 32 w .. 32 w + 31, its 32 rows of
+// the 128-row tile) and store the tile; warp 4 loads operands by TMA; warp 5 issues the MMAs.
+template <bool F16>
+__global__ void __launch_bounds__(192, 1) gemm_drain_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                            const __grid_constant__ CUtensorMap mapB,
+                                                            const __grid_constant__ CUtensorMap mapAl,
+                                                            const __grid_constant__ CUtensorMap mapBl, int M, int N,
+                                                            int Kp, float* __restrict__ C, int64_t ldc,
+                                                            int* __restrict__ err, int tri,
+                                                            const int* __restrict__ tiles,
+                                                            const float* __restrict__ cscale, int dk) {
+    using CF = Cfg<true, 0, F16>;
+    constexpr int BN = CF::BN, STAGES = CF::STAGES, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
+    constexpr int STAGE_BYTES = CF::STAGE_BYTES;
+    constexpr int NACC = 2;
+    static_assert(BN == 128, "128-column accumulators");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;        // [NACC]: a chunk's MMAs have completed into accumulator b
+    uint64_t* tempty = tfull + NACC;         // [NACC]: the drain warps have read accumulator b
+    uint64_t* done = tempty + NACC;          // every MMA of the CTA has completed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int tile_y = blockIdx.y, tile_x = blockIdx.x;
+    if (tiles) {
+        tile_y = tiles[2 * blockIdx.x];
+        tile_x = tiles[2 * blockIdx.x + 1];
+    }
+    const int m0 = tile_y * BM, n0 = tile_x * BN;
+    const bool mirror = tri && tile_x != tile_y;
+    const int nk = Kp / CF::KSTAGE;
+    const int nchunk = (nk + dk - 1) / dk;
+    ::ewos::pdl_trigger();
+
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < NACC; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(NACC * BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    ::ewos::pdl_wait();
+
+    if (warp == 4) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)((kb / STAGES) & 1);
+                if (!mbar_wait(&empty[s], ph ^ 1u)) { s_fail = 1; break; }
+                unsigned char* st = smem + s * STAGE_BYTES;
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+                tma_load_2d(st, &mapA, &full[s], kb * CF::KSTAGE, m0);
+                tma_load_2d(st + A_BYTES, &mapB, &full[s], kb * CF::KSTAGE, n0);
+                tma_load_2d(st + A_BYTES + B_BYTES, &mapAl, &full[s], kb * CF::KSTAGE, m0);
+                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mapBl, &full[s], kb * CF::KSTAGE, n0);
+                issued = kb + 1;
+            }
+            // after a failed wait, let the loads still in flight land before the CTA exits
+            if (issued < nk)
+                for (int kb = issued > STAGES ? issued - STAGES : 0; kb < issued; ++kb)
+                    mbar_wait(&full[kb % STAGES], (uint32_t)((kb / STAGES) & 1));
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // the issue loop is on the critical path (the tensor pipe waits for it whenever the
+            // ring runs dry): no divisions, descriptors of stage 0 computed once (a stage, and a
+            // 32-byte step inside one, move the descriptor's address field by bytes / 16)
+            const uint64_t d0a = smem_desc(smem), d0b = smem_desc(smem + A_BYTES);
+            const uint64_t d0al = smem_desc(smem + A_BYTES + B_BYTES), d0bl = smem_desc(smem + 2 * A_BYTES + B_BYTES);
+            int chunk = 0, kin = 0, s = 0;
+            uint32_t ph = 0;
+            for (int kb = 0; kb < nk; ++kb) {
+                const int b = chunk & (NACC - 1);
+                const bool first = kin == 0, last = kin == dk - 1 || kb == nk - 1;
+                // accumulator b is free again once the chunk NACC back has been drained
+                if (first && chunk >= NACC && !mbar_wait(&tempty[b], (uint32_t)(((chunk >> 1) - 1) & 1))) {
+                    s_fail = 1;
+                    break;
+                }
+                if (!mbar_wait(&full[s], ph)) { s_fail = 1; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t so = (uint64_t)(s * (STAGE_BYTES >> 4));
+                const uint32_t d = tmem + (uint32_t)(b * BN);
+#pragma unroll
+                for (int k = 0; k < BK / 8; ++k) {
+                    const uint64_t ko = so + (uint64_t)(k * 2);
+                    const uint32_t acc = (!first || k > 0) ? 1u : 0u;
+                    if constexpr (F16) {
+                        mma_f16(d, d0a + ko, d0b + ko, CF::IDESC, acc);
+                        mma_f16(d, d0a + ko, d0bl + ko, CF::IDESC, 1u);
+                        mma_f16(d, d0al + ko, d0b + ko, CF::IDESC, 1u);
+                    } else {
+                        mma_tf32(d, d0a + ko, d0b + ko, CF::IDESC, acc);
+                        mma_tf32(d, d0a + ko, d0bl + ko, CF::IDESC, 1u);
+                        mma_tf32(d, d0al + ko, d0b + ko, CF::IDESC, 1u);
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&empty[s]))
+                             : "memory");
+                if (last)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&tfull[b]))
+                                 : "memory");
+                if (++kin == dk) { kin = 0; ++chunk; }
+                if (++s == STAGES) { s = 0; ph ^= 1u; }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(done))
+                         : "memory");
+        }
+    } else {
+        float acc[BN];
+#pragma unroll
+        for (int q = 0; q < BN; ++q) acc[q] = 0.f;
+        bool ok = true;
+        for (int chunk = 0; chunk < nchunk; ++chunk) {
+            const int b = chunk & (NACC - 1);
+            if (!mbar_wait_sleep(&tfull[b], (uint32_t)((chunk >> 1) & 1), EWOS_DRAIN_SLEEP) || s_fail) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * BN + c * 32);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                    "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 32; ++q) acc[c * 32 + q] += __uint_as_float(v[q]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[b])) : "memory");
+        }
+        // every MMA has completed (also after a failed wait) before TMEM is released
+        if (!mbar_wait_sleep(done, 0, EWOS_DRAIN_SLEEP)) ok = false;
+        if (ok && !s_fail) {
+            const float sc = (F16 && cscale) ? *cscale : 1.0f;
+            const int row = m0 + warp * 32 + lane;
+            if (row < M) {
+#pragma unroll
+                for (int c = 0; c < BN / 32; ++c) {
+                    const int col0 = n0 + c * 32;
+                    float* cp = C + (int64_t)row * ldc + col0;
+                    const bool fast = col0 + 32 <= N && (ldc & 3) == 0 && ((reinterpret_cast<uintptr_t>(cp) & 15) == 0);
+                    if (fast) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            reinterpret_cast<float4*>(cp)[q] = make_float4(acc[c * 32 + 4 * q] * sc, acc[c * 32 + 4 * q + 1] * sc,
+                                                                           acc[c * 32 + 4 * q + 2] * sc, acc[c * 32 + 4 * q + 3] * sc);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q)
+                            if (col0 + q < N) cp[q] = acc[c * 32 + q] * sc;
+                    }
+                    if (mirror) {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q)
+                            if (col0 + q < N) C[(int64_t)(col0 + q) * ldc + row] = acc[c * 32 + q] * sc;
+                    }
+                }
+            }
+        } else {
+            s_fail = 1;
+        }
+    }
+    __syncwarp();
+    __syncthreads();
+    if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * BN));
+}
+
 // out[c][k] = in[k][c] for in [K][C] (row-major), out [C][Kp] with zero padding k in [K, Kp)
 __global__ void transpose_pad_kernel(const float* __restrict__ in, int K, int Ccols, float* __restrict__ out, int Kp) {
     __shared__ float tile[32][33];
@@ -523,6 +748,25 @@ static ewos_status tile_table(Scratch& S, int mt, int nt, bool tri, cudaStream_t
 }
 static std::mutex g_mu;
 
+// operand elements per chunk of the two-level accumulation (gemm_drain_kernel)
+#ifndef EWOS_DRAIN_ELEMS
+#define EWOS_DRAIN_ELEMS 256
+#endif
+
+template <bool F16>
+static ewos_status launch_drain(Scratch& S, const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mal,
+                                const CUtensorMap& mbl, int M, int N, int Kp, float* C, int64_t ldc, bool tri,
+                                int ntiles, const float* cscale, cudaStream_t st) {
+    using CF = Cfg<true, 0, F16>;
+    auto k = gemm_drain_kernel<F16>;
+    EWOS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM_BYTES));
+    const int dk = EWOS_DRAIN_ELEMS / CF::KSTAGE > 0 ? EWOS_DRAIN_ELEMS / CF::KSTAGE : 1;
+    ::ewos::note_launch(), k<<<ntiles, 192, CF::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, ldc, S.err, tri ? 1 : 0,
+                                                                  S.tiles, cscale, dk);
+    EWOS_CUDA_TRY(cudaGetLastError());
+    return EWOS_OK;
+}
+
 }  // namespace tc
 
 bool tc_assemble_available() {
@@ -596,9 +840,9 @@ static ewos_status tc_enqueue(tc::Scratch& S, const float* Akm, const float* Bkm
         int ntiles = 0;
         if (ewos_status ts = tile_table(S, (M + BM - 1) / BM, (N + bn - 1) / bn, tri, st, &ntiles); ts != EWOS_OK)
             return ts;
-        EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<true>::SMEM_BYTES));
-        ::ewos::note_launch(), gemm_tf32_kernel<true><<<ntiles, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err,
-                                                                                              0, tri ? 1 : 0, S.tiles);
+        if (ewos_status ls = launch_drain<false>(S, ma, mb, mal, mbl, M, N, Kp, C, N, tri, ntiles, nullptr, st);
+            ls != EWOS_OK)
+            return ls;
     } else {
         EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<false>::SMEM_BYTES));
         ::ewos::note_launch(), gemm_tf32_kernel<false><<<grid, 128, Cfg<false>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, M, N, Kp, C, N, S.err, 0);
@@ -821,14 +1065,11 @@ static ewos_status tc_assemble_pq16(tc::Scratch& S, const float* P, const double
         return EWOS_ECUDA;
     }
     EWOS_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
-    auto k = gemm_tf32_kernel<true, 0, false, true>;
-    EWOS_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM_BYTES));
     const int nt = (m + BM - 1) / BM;
     int ntiles = 0;
     if (ewos_status ts = tile_table(S, nt, (m + CF::BN - 1) / CF::BN, sym, st, &ntiles); ts != EWOS_OK) return ts;
-    ::ewos::note_launch(), k<<<ntiles, 128, CF::SMEM_BYTES, st>>>(ma, mb, mal, mbl, m, m, Kp, C, m, S.err, 0, sym ? 1 : 0,
-                                                                  S.tiles, S.scale + 4);
-    EWOS_CUDA_TRY(cudaGetLastError());
+    if (ewos_status ls = launch_drain<true>(S, ma, mb, mal, mbl, m, m, Kp, C, m, sym, ntiles, S.scale + 4, st); ls != EWOS_OK)
+        return ls;
     return tc_check(S, st);
 }
 
@@ -872,15 +1113,13 @@ ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D
         return EWOS_ECUDA;
     }
     EWOS_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
-    EWOS_CUDA_TRY(cudaFuncSetAttribute(gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<true>::SMEM_BYTES));
     const int nt = (m + BM - 1) / BM;
     static_assert(Cfg<true>::BN == BM, "square tiles for the symmetric launch");
     int ntiles = 0;
     if (ewos_status ts = tile_table(S, nt, (m + Cfg<true>::BN - 1) / Cfg<true>::BN, sym, st, &ntiles); ts != EWOS_OK)
         return ts;
-    ::ewos::note_launch(), gemm_tf32_kernel<true><<<ntiles, 128, Cfg<true>::SMEM_BYTES, st>>>(ma, mb, mal, mbl, m, m, Kp, C, m, S.err,
-                                                                                           0, sym ? 1 : 0, S.tiles);
-    EWOS_CUDA_TRY(cudaGetLastError());
+    if (ewos_status ls = launch_drain<false>(S, ma, mb, mal, mbl, m, m, Kp, C, m, sym, ntiles, nullptr, st); ls != EWOS_OK)
+        return ls;
     return tc_check(S, st);
 }
 

@@ -165,7 +165,7 @@ def test_mixed_linear_matches_oracle(disk, assembly):
     ref = S.solve_linear(tb, lam, pb.A, pb.b, pb.c, pb.f, pb.g, alpha=rep["alpha"])
     assert _rel(u, ref["u"]) < 1e-9
     ref_alpha = S.shift(ref["Lam"], 3e-2)
-    assert abs(rep["alpha"] - ref_alpha) <= 1e-3 * ref_alpha
+    assert abs(rep["alpha"] - ref_alpha) <= 1e-5 * ref_alpha
     u64, _, _ = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, c=pb.c, mode="fp64")
     e_m = S.errors(u, pb.u_star, lam)["l2"]
     e_d = S.errors(u64, pb.u_star, lam)["l2"]
@@ -200,12 +200,12 @@ def test_mixed_square4096_full_size():
     gtb = ewos.build_workload(w)
     u, s, rep = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, want_s=True, mode="mixed")
     # the two tensor-core assemblies reach the same refined solution, in as many sweeps; the shift
-    # alpha = rcond ||Lambda_32||_F comes from each assembly's own FP32 matrix, whose norm the
-    # tensor cores' truncating accumulation lowers by about 5e-9 K relative (K = 3 n = 12288 here)
+    # alpha = rcond ||Lambda_32||_F comes from each assembly's own FP32 matrix (within a few 1e-6
+    # of the exact norm: the tensor cores truncate, the chunked accumulation bounds that)
     ut, _, rept = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, mode="mixed", assembly="tf32")
     assert rept["converged"] and abs(rept["refine_iters"] - rep["refine_iters"]) <= 1
-    assert abs(rept["alpha"] - rep["alpha"]) <= 2e-4 * rep["alpha"]
-    assert _rel(u, ut) < 1e-4
+    assert abs(rept["alpha"] - rep["alpha"]) <= 1e-5 * rep["alpha"]
+    assert _rel(u, ut) < 1e-5
     u64, s64, rep64 = gtb.solve(pb.A, pb.f, pb.g, b=pb.b, want_s=True, mode="fp64")
     mats = gtb.matrices()
     lam = gtb.get("lambda")

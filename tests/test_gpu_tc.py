@@ -89,21 +89,23 @@ def _pq_ref(P, M):
 
 @pytest.mark.parametrize("f16", [True, False])
 @pytest.mark.parametrize("n,m,D,sym,spread", [(200, 150, 2, False, 3.0), (300, 260, 3, True, 6.0),
-                                              (1000, 520, 2, False, 9.0), (64, 33, 3, False, 1.0)])
+                                              (1000, 520, 2, False, 9.0), (64, 33, 3, False, 1.0),
+                                              (8000, 260, 3, True, 3.0)])
 def test_tc_assemble_pq(n, m, D, sym, spread, f16):
     """Lambda = P^T (M P) as the mixed solve assembles it: FP16 halves of the scaled operands or
-    three TF32 products.  Both keep about 22 significand bits per operand; with Q formed in FP32
-    and FP32 accumulation each entry is within (2^-19 + K 2^-23) sum |P||Q|; in the FP16 form the
-    entries far below the largest keep an absolute error of 2^-25 / s (s the power of two that
-    scaled the operand), which adds 2^-24 / s_P sum |Q| + 2^-24 / s_Q sum |P|.  The tensor cores
-    round their FP32 accumulation toward zero, so the error of the whole matrix is a bias that grows
-    with K (measured: ||C - Lambda||_F / ||Lambda||_F about 5e-9 K for both forms); the test allows
-    2e-8 K, and checks the sign of the bias (||C||_F below ||Lambda||_F)."""
+    three TF32 products.  Both keep about 22 significand bits per operand.  The tensor cores round
+    their FP32 accumulation toward zero; the assembly accumulates chunks of 256 operand elements
+    and adds the chunks in FP32 registers, so an entry carries the truncation of one chunk (at most
+    48 MMAs of 2^-23 each, under 2^-16 of sum |P||Q|) and the rounding of the chunk sums (K 2^-24).
+    In the FP16 form the entries far below the largest keep an absolute error of 2^-25 / s (s the
+    power of two that scaled the operand): 2^-24 / s_P sum |Q| + 2^-24 / s_Q sum |P| more.  The
+    matrix as a whole: ||C - Lambda||_F / ||Lambda||_F below 4e-6 at every K (measured 1e-6 to
+    2e-6; one accumulator for all of K gave 5e-9 K), still a bias toward zero."""
     P, M = _pq_case(n, m, D, n + m + D, spread, sym)
     C = ewos.debug_tc_assemble(P, M, sym=sym, f16=f16).astype(np.float64)
     ref, absref = _pq_ref(P, M)
     K = (D + 1) * n
-    bound = (2.0 ** -19 + K * 2.0 ** -23) * absref
+    bound = (2.0 ** -18 + 2.0 ** -16 + K * 2.0 ** -24) * absref
     if f16:
         E = D + 1
         Q = np.einsum("ijk,kic->jic", M, P.astype(np.float64)).reshape(E * n, m)
@@ -114,5 +116,5 @@ def test_tc_assemble_pq(n, m, D, sym, spread, f16):
     err = np.abs(C - ref)
     assert np.all(err <= bound), float(np.max(err / bound))
     rel = np.linalg.norm(C - ref) / np.linalg.norm(ref)
-    assert rel < 2e-8 * K
+    assert rel < 4e-6
     assert np.linalg.norm(C) < np.linalg.norm(ref)
