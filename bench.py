@@ -181,15 +181,17 @@ def walk_roofline(workload, steps_per_launch, ms_walk, nsm, peaks, peak_src, gri
     return out
 
 
-def tensor_roofline(name, flop, ms, peaks, peak_src, sustained=True):
-    """Tensor-core stage: the method's FLOPs (the three TF32 split products counted once) over
-    the stage's device time, against the TF32 peak derived from the measured BF16 GEMM peak."""
+def tensor_roofline(name, flop, ms, peaks, peak_src, sustained=True, dtype="tf32"):
+    """Tensor-core stage: the method's FLOPs (the three split products counted once) over the
+    stage's device time, against the peak of the operand type: FP16 runs at the BF16 rate (the
+    measured BF16 GEMM peak), TF32 at 1.1/2.25 of it."""
     bf16 = peaks.get("bf16_tflops_sustained" if sustained else "bf16_tflops", 1400.0)
-    peak = bf16 * TF32_OVER_BF16
+    peak = bf16 * (TF32_OVER_BF16 if dtype == "tf32" else 1.0)
     ach = flop / (ms / 1000.0) / 1e12 if ms > 0 else None
+    kind = "sustained" if sustained else "burst"
+    note = f"TF32 = {kind} bf16 ({peak_src}) x 1.1/2.25" if dtype == "tf32" else f"FP16 = {kind} bf16 ({peak_src})"
     return {"stage": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": None if ach is None else ach / peak, "traffic": None,
-            "peak_note": f"TF32 = {'sustained' if sustained else 'burst'} bf16 ({peak_src}) x 1.1/2.25"}
+            "frac": None if ach is None else ach / peak, "traffic": None, "peak_note": note}
 
 
 # ------------------------------------------------------------------ CPU oracle (reference arm)
@@ -502,8 +504,10 @@ def summarize(name, res, workload, peaks, peak_src, nsm, dtype):
     rl = {"walk": walk_roofline(name, steps, wk, nsm, peaks, peak_src, res["builds"][-1]["lookup_grid_scale"])}
     g_ms = statistics.median(r["dev_ms_gemm"] for r in solves)
     if g_ms > 0:
-        rl["assembly_gemm"] = tensor_roofline("assembly (tcgen05 TF32, 3 split products)",
-                                              statistics.median(r["gemm_flop"] for r in solves), g_ms, peaks, peak_src)
+        rl["assembly_gemm"] = tensor_roofline("assembly and Jacobian products (tcgen05 kind::f16, three products of "
+                                              "scaled FP16 halves, chunked accumulation)",
+                                              statistics.median(r["gemm_flop"] for r in solves), g_ms, peaks, peak_src,
+                                              dtype="f16")
     lu_ms = statistics.median(r["dev_ms_lu"] for r in solves)
     if lu_ms > 0:
         mm = line_m(name)

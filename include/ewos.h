@@ -394,11 +394,13 @@ void ewos_server_destroy(ewos_server* sv);
 ewos_status ewos_debug_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t count);
 ewos_status ewos_debug_green_radius(const void* u, void* R, int64_t count, int precision);
 /* Test hook (no counterpart in the paper): C [M][N] = A^T B for host FP32 arrays A [K][M],
- * B [K][N], through the tensor-core (tcgen05, TF32) GEMM of the mixed-precision assembly;
- * split = 1 uses three TF32 products per step (hi*hi + hi*lo + lo*hi); split = 2 does the same
- * with the symmetric launch of the assembly (only the tiles on and below the diagonal are
- * computed, each also stored transposed: for a symmetric A^T B, M = N).  EWOS_EINVAL when the
- * device has no sm_100-family tensor cores. */
+ * B [K][N], through the tensor-core (tcgen05) GEMMs of the mixed-precision solve: split = 0
+ * plain TF32; split = 1 three TF32 products per step (hi*hi + hi*lo + lo*hi), accumulated in
+ * chunks (the long-K product of the assembly); split = 3 the same with A and B scaled by powers
+ * of two and split into FP16 halves (kind::f16); split = 2 and 4 are 1 and 3 with the symmetric
+ * launch (only the tiles on and below the diagonal are computed, each also stored transposed: for
+ * a symmetric A^T B, M = N).  EWOS_EINVAL for another split, and when the device has no
+ * sm_100-family tensor cores. */
 ewos_status ewos_debug_tc_gemm(const float* A, const float* B, float* C, int M, int N, int K, int split);
 /* Test hook (no counterpart in the paper): the tensor-core assembly of the mixed-precision solve,
  * C [m][m] = Lambda = P^T Q with Q_i = M_i P_i (eq. linear_q), for host arrays P [D+1][n][m] (FP32),

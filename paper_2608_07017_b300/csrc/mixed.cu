@@ -710,7 +710,7 @@ struct Scratch {
     float* Btl = nullptr;
     int* err = nullptr;
     size_t cap = 0;
-    float* scale = nullptr;        // FP16 assembly: [0] max |P|, [1] max row sum of |M|, [2] s_P, [3] s_Q, [4] 1/(s_P s_Q)
+    float* scale = nullptr;        // FP16 forms: [0], [1] the maxima that set [2] s_A (s_P), [3] s_B (s_Q); [4] 1/(s_A s_B)
     int* tiles = nullptr;          // (tile row, tile column) per CTA, blocked order
     long long tiles_key = -1;      // shape the table was made for
     int tiles_count = 0;
@@ -798,6 +798,67 @@ void tc_scratch_free(TcScratch* t) {
 
 // Enqueues the transposes and the GEMM on st; the pipeline-timeout word is left in *err_dev
 // for the caller to check after the stream has run (no host synchronisation here).
+// scale[0] = max |A|, scale[1] = max |B| over na and nb values (the FP16 form of tc_enqueue)
+__global__ void absmax2_kernel(const float* __restrict__ A, int64_t na, const float* __restrict__ B, int64_t nb,
+                               float* __restrict__ scale) {
+    float ma = 0.f, mb = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < na; t += stride) ma = fmaxf(ma, fabsf(A[t]));
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nb; t += stride) mb = fmaxf(mb, fabsf(B[t]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+        mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(reinterpret_cast<unsigned int*>(scale), __float_as_uint(ma));       // (non-negative floats)
+        atomicMax(reinterpret_cast<unsigned int*>(scale + 1), __float_as_uint(mb));
+    }
+}
+
+// powers of two s_A, s_B with max |A| s_A and max |B| s_B in [2^13, 2^14), and 1 / (s_A s_B)
+__global__ void ab_scale_kernel(float* scale) {
+    if (threadIdx.x != 0) return;
+    auto pw = [](float mxv) {
+        if (!(mxv > 0.f) || !isfinite(mxv)) return 1.0f;
+        int e;
+        frexpf(mxv, &e);
+        return ldexpf(1.0f, 14 - e);
+    };
+    const float sa = pw(scale[0]), sb = pw(scale[1]);
+    scale[2] = sa;
+    scale[3] = sb;
+    scale[4] = 1.0f / (sa * sb);
+}
+
+__device__ __forceinline__ void f16_split_tc(float v, __half& h, __half& l) {
+    h = __float2half_rn(v);
+    l = __float2half_rn(v - __half2float(h));
+}
+
+// hi/lo [C][Kp] halves of s * in^T for in [K][C] FP32 (row-major), zero padding k in [K, Kp);
+// s = scale[which]
+__global__ void transpose_split16_kernel(const float* __restrict__ in, int K, int Ccols, __half* __restrict__ hi,
+                                         __half* __restrict__ lo, int Kp, const float* __restrict__ scale, int which) {
+    __shared__ float tile[32][33];
+    const float sc = scale[which];
+    const int c0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int k = k0 + r, c = c0 + threadIdx.x;
+        tile[r][threadIdx.x] = (k < K && c < Ccols) ? in[(int64_t)k * Ccols + c] : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int c = c0 + r, k = k0 + threadIdx.x;
+        if (c < Ccols && k < Kp) {
+            __half h, l;
+            f16_split_tc(tile[threadIdx.x][r] * sc, h, l);
+            hi[(int64_t)c * Kp + k] = h;
+            lo[(int64_t)c * Kp + k] = l;
+        }
+    }
+}
+
 static ewos_status tc_enqueue(tc::Scratch& S, const float* Akm, const float* Bkm, float* C, int M, int N, int K,
                               cudaStream_t st, bool split, bool sym = false) {
     using namespace tc;
@@ -849,6 +910,55 @@ static ewos_status tc_enqueue(tc::Scratch& S, const float* Akm, const float* Bkm
     }
     EWOS_CUDA_TRY(cudaGetLastError());
     return EWOS_OK;
+}
+
+// The FP16 form of tc_enqueue's split product (C = A^T B, FP32 operands scaled by powers of two
+// and split into FP16 halves, three kind::f16 products, unscaled in the epilogue): twice the TF32
+// rate; as accurate as the TF32 split while max |A| and max |B| do not exceed the other entries
+// by more than about 2^17 (below that an entry keeps an absolute error of 2^-39 of the largest).
+static ewos_status tc_enqueue16(tc::Scratch& S, const float* Akm, const float* Bkm, float* C, int M, int N, int K,
+                                cudaStream_t st, bool sym) {
+    using namespace tc;
+    using CF = Cfg<true, 0, true>;
+    const int Kp = (K + 2 * BK - 1) / (2 * BK) * (2 * BK);
+    const size_t need_f = ((size_t)std::max(M, N) * Kp + 1) / 2;
+    if (S.cap < need_f || !S.Atl) {
+        ::ewos::dev_free(S.At); ::ewos::dev_free(S.Bt); ::ewos::dev_free(S.Atl); ::ewos::dev_free(S.Btl);
+        S.At = S.Bt = S.Atl = S.Btl = nullptr;
+        S.cap = 0;
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.At, sizeof(float) * need_f));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Bt, sizeof(float) * need_f));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Atl, sizeof(float) * need_f));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Btl, sizeof(float) * need_f));
+        S.cap = need_f;
+    }
+    if (!S.err) EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.err, sizeof(int)));
+    if (!S.scale) EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.scale, sizeof(float) * 8));
+    __half* at = reinterpret_cast<__half*>(S.At);
+    __half* atl = reinterpret_cast<__half*>(S.Atl);
+    __half* bt = reinterpret_cast<__half*>(S.Bt);
+    __half* btl = reinterpret_cast<__half*>(S.Btl);
+    EWOS_CUDA_TRY(cudaMemsetAsync(S.scale, 0, sizeof(float) * 8, st));
+    ::ewos::note_launch(), absmax2_kernel<<<4 * 148, 256, 0, st>>>(Akm, (int64_t)K * M, Bkm, (int64_t)K * N, S.scale);
+    ::ewos::note_launch(), ab_scale_kernel<<<1, 32, 0, st>>>(S.scale);
+    const dim3 tb(32, 8);
+    ::ewos::note_launch(), transpose_split16_kernel<<<dim3((M + 31) / 32, (Kp + 31) / 32), tb, 0, st>>>(Akm, K, M, at, atl, Kp,
+                                                                                                     S.scale, 2);
+    ::ewos::note_launch(), transpose_split16_kernel<<<dim3((N + 31) / 32, (Kp + 31) / 32), tb, 0, st>>>(Bkm, K, N, bt, btl, Kp,
+                                                                                                     S.scale, 3);
+    EWOS_CUDA_TRY(cudaGetLastError());
+    CUtensorMap ma, mb, mal, mbl;
+    if (!(make_map16(&ma, at, M, Kp, BM) && make_map16(&mb, bt, N, Kp, CF::BN) && make_map16(&mal, atl, M, Kp, BM) &&
+          make_map16(&mbl, btl, N, Kp, CF::BN))) {
+        set_error("tensor-core assembly: cuTensorMapEncodeTiled failed");
+        return EWOS_ECUDA;
+    }
+    EWOS_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
+    const bool tri = sym && M == N;
+    int ntiles = 0;
+    if (ewos_status ts = tile_table(S, (M + BM - 1) / BM, (N + CF::BN - 1) / CF::BN, tri, st, &ntiles); ts != EWOS_OK)
+        return ts;
+    return launch_drain<true>(S, ma, mb, mal, mbl, M, N, Kp, C, N, tri, ntiles, S.scale + 4, st);
 }
 
 static ewos_status tc_check(tc::Scratch& S, cudaStream_t st) {
@@ -1244,18 +1354,19 @@ ewos_status tc_update_check(TcScratch* t, cudaStream_t st) {
 // C [M][N] = A^T B for K-major FP32 operands A [K][M], B [K][N].  With a caller scratch the
 // call is reentrant across workspaces; without one the per-device scratch is used under a lock.
 ewos_status tc_assemble(const float* Akm, const float* Bkm, float* C, int M, int N, int K, cudaStream_t st,
-                        bool split, TcScratch** owned, bool sym = false) {
+                        bool split, TcScratch** owned, bool sym = false, bool f16 = false) {
     int dev = 0;
     EWOS_CUDA_TRY(cudaGetDevice(&dev));
     if (owned) {
         if (!*owned) *owned = new TcScratch();
-        ewos_status s = tc_enqueue((*owned)->s, Akm, Bkm, C, M, N, K, st, split, sym);
+        ewos_status s = f16 ? tc_enqueue16((*owned)->s, Akm, Bkm, C, M, N, K, st, sym)
+                            : tc_enqueue((*owned)->s, Akm, Bkm, C, M, N, K, st, split, sym);
         if (s != EWOS_OK) return s;
         return tc_check((*owned)->s, st);
     }
     std::lock_guard<std::mutex> lock(tc::g_mu);
     tc::Scratch& S = tc::g_scratch[dev & 63];
-    ewos_status s = tc_enqueue(S, Akm, Bkm, C, M, N, K, st, split, sym);
+    ewos_status s = f16 ? tc_enqueue16(S, Akm, Bkm, C, M, N, K, st, sym) : tc_enqueue(S, Akm, Bkm, C, M, N, K, st, split, sym);
     if (s != EWOS_OK) return s;
     return tc_check(S, st);
 }
@@ -1267,7 +1378,10 @@ ewos_status tc_assemble(const float* Akm, const float* Bkm, float* C, int M, int
 // symmetric launch (tiles on and below the diagonal, mirrored; for a symmetric A^T B).
 extern "C" ewos_status ewos_debug_tc_gemm(const float* A, const float* B, float* C, int M, int N, int K, int split) {
     using namespace ewos;
-    if (!A || !B || !C || M < 1 || N < 1 || K < 1) { set_error("ewos_debug_tc_gemm: bad arguments"); return EWOS_EINVAL; }
+    if (!A || !B || !C || M < 1 || N < 1 || K < 1 || split < 0 || split > 4) {
+        set_error("ewos_debug_tc_gemm: bad arguments");
+        return EWOS_EINVAL;
+    }
     if (!tc_assemble_available()) { set_error("tensor cores (sm_100 family) not available"); return EWOS_EINVAL; }
     AllocStream as(nullptr);
     float *dA = nullptr, *dB = nullptr, *dC = nullptr;
@@ -1276,7 +1390,7 @@ extern "C" ewos_status ewos_debug_tc_gemm(const float* A, const float* B, float*
     EWOS_CUDA_TRY(dev_alloc((void**)&dC, sizeof(float) * (size_t)M * N));
     cudaMemcpy(dA, A, sizeof(float) * (size_t)K * M, cudaMemcpyHostToDevice);
     cudaMemcpy(dB, B, sizeof(float) * (size_t)K * N, cudaMemcpyHostToDevice);
-    ewos_status s = tc_assemble(dA, dB, dC, M, N, K, nullptr, split != 0, nullptr, split == 2);
+    ewos_status s = tc_assemble(dA, dB, dC, M, N, K, nullptr, split != 0, nullptr, split == 2 || split == 4, split >= 3);
     if (s == EWOS_OK && cudaMemcpy(C, dC, sizeof(float) * (size_t)M * N, cudaMemcpyDeviceToHost) != cudaSuccess) s = EWOS_ECUDA;
     dev_free(dA); dev_free(dB); dev_free(dC);
     cudaDeviceSynchronize();

@@ -72,7 +72,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b) {
 struct TcScratch;   // mixed.cu: operand transposes of one caller
 void tc_scratch_free(TcScratch* t);
 ewos_status tc_assemble(const float* A_km, const float* B_km, float* C, int M, int N, int K, cudaStream_t st,
-                        bool split, TcScratch** owned, bool sym = false);
+                        bool split, TcScratch** owned, bool sym = false, bool f16 = false);
 ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int M,
                               int N, int K, cudaStream_t st, TcScratch** owned, bool presplit = false, int a_off = 0,
                               int b_off = 0);
@@ -3561,7 +3561,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                     const float* Gm32 = P32 + (size_t)C.D * C.n * C.m;
                     auto t1 = std::chrono::steady_clock::now();
                     // Jacobian Lambda + alpha I + G^T diag(lam N'(u)) G: the product on the tensor
-                    // cores (3 TF32 products) when available
+                    // cores (three products of FP16 halves, or of TF32 parts) when available
                     const bool tcj = tc_assemble_available();
                     ewos_status tst = EWOS_OK;
                     ewos_status st = factor32_with(
@@ -3571,7 +3571,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                                 DevSpan span(C.st, &rep->dev_ms_gemm);
                                 rep->gemm_flop += (double)C.m * (double)(C.m + 1) * (double)C.n;   // symmetric: lower triangle
                                 ewos_status e = tc_assemble(Gm32, ws->Jx32, ws->LU32, (int)C.m, (int)C.m, (int)C.n, C.st,
-                                                            kSplitTF32, &ws->tc, true);
+                                                            kSplitTF32, &ws->tc, true, pb->assembly != 1);
                                 if (e != EWOS_OK) tst = e;
                                 const int64_t cnt = C.m * C.m;
                                 ::ewos::note_launch(), add_shifted_kernel<<<(int)std::min<int64_t>(65535, (cnt + 255) / 256), 256, 0, C.st>>>(

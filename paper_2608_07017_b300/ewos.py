@@ -427,16 +427,17 @@ def debug_philox(ctr, key):
     return out
 
 
-def debug_tc_gemm(A, B, split=False, sym=False):
-    """C = A^T B on the tensor cores (TF32 inputs, FP32 accumulation; split: 3xTF32); A [K][M], B [K][N].
-    sym: 3xTF32 with the symmetric launch (tiles on and below the diagonal, mirrored)."""
+def debug_tc_gemm(A, B, split=False, sym=False, f16=False):
+    """C = A^T B on the tensor cores (TF32 inputs, FP32 accumulation; split: 3xTF32; f16: three
+    products of scaled FP16 halves); A [K][M], B [K][N].  sym: a split form with the symmetric
+    launch (tiles on and below the diagonal, mirrored)."""
     a = np.ascontiguousarray(A, dtype=np.float32)
     b = np.ascontiguousarray(B, dtype=np.float32)
     K, M = a.shape
     N = b.shape[1]
     c = np.zeros((M, N), dtype=np.float32)
     _check(lib().ewos_debug_tc_gemm(a.ctypes.data, b.ctypes.data, c.ctypes.data, M, N, K,
-                                    2 if sym else (1 if split else 0)), "tc gemm")
+                                    (4 if sym else 3) if f16 else (2 if sym else (1 if split else 0))), "tc gemm")
     return c
 
 

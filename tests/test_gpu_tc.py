@@ -39,6 +39,31 @@ def test_tc_gemm_split_tf32(M, N, K):
     assert np.all(np.abs(C - ref) <= bound + 1e-30)
 
 
+@pytest.mark.parametrize("M,N,K,sym", [(128, 128, 64, False), (300, 260, 5000, False), (520, 520, 9000, True),
+                                       (7, 5, 3, False)])
+def test_tc_gemm_f16_split(M, N, K, sym):
+    """The FP16 form of the long-K product (the Jacobian's G^T D G): A and B scaled by powers of two
+    that put their largest entries in [2^13, 2^14), split into FP16 halves, three kind::f16
+    products accumulated in chunks.  On normal data every operand entry keeps 22 bits (2^-21
+    relative per product, plus the FP16 subnormal floor of 2^-25 / s per entry) and the chunked
+    accumulation adds 2^-16 + K 2^-24 of sum |a b|."""
+    rng = np.random.default_rng(M + N + K)
+    A = rng.normal(size=(K, M)).astype(np.float32)
+    B = (rng.uniform(0.5, 2.0, size=(K, 1)) * A[:, :N]).astype(np.float32) if sym else \
+        rng.normal(size=(K, N)).astype(np.float32) * 1e-3
+    C = ewos.debug_tc_gemm(A, B, f16=True, sym=sym).astype(np.float64)
+    ref = A.astype(np.float64).T @ B.astype(np.float64)
+    absref = np.abs(A).astype(np.float64).T @ np.abs(B).astype(np.float64)
+    s_a = 2.0 ** (13 - np.floor(np.log2(np.abs(A).max())))
+    s_b = 2.0 ** (13 - np.floor(np.log2(np.abs(B).max())))
+    bound = (2.0 ** -19 + 2.0 ** -16 + K * 2.0 ** -24) * absref + \
+        2.0 ** -24 / s_a * np.abs(B).astype(np.float64).sum(axis=0)[None, :] + \
+        2.0 ** -24 / s_b * np.abs(A).astype(np.float64).sum(axis=0)[:, None]
+    assert np.all(np.abs(C - ref) <= bound)
+    if K >= 1000:
+        assert np.linalg.norm(C - ref) < 4e-6 * np.linalg.norm(absref)
+
+
 @pytest.mark.parametrize("M,K", [(128, 64), (300, 1000), (520, 96), (7, 5)])
 def test_tc_gemm_symmetric_launch(M, K):
     """The symmetric launch of the assembly (A^T A, or A^T D A): only tiles on and below the
