@@ -749,6 +749,9 @@ struct WalkArgs {
     T* rec_mass;
     uint32_t* rec_vhash;   // XOR over the walk's interior binnings of cellmix(step tag, cell)
     T* rec_xexit;          // [n][N][D] stopping point
+    // autotuner trials: fetched row t < trial_rows is row (t * trial_step) mod n (0: all rows in order)
+    int trial_rows;
+    int trial_step;
     // polygon edge grid (walk steps): candidate edges per cell, records (ax, ay, ex, ey, 1/|e|^2)
     // at sdf[e_off + 5 e]; NULL for other domains (and the full scan is used)
     const uint8_t* e_cnt;
@@ -1008,6 +1011,9 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
                 g_next = gend;
                 break;
             }
+        } else if (a.trial_rows > 0) {
+            if (row >= a.trial_rows) break;
+            row = (int)(((int64_t)row * a.trial_step) % a.n);
         } else if (row >= a.n) {
             break;
         }
@@ -1388,6 +1394,15 @@ static int max_ctas_per_sm(int tpb, size_t smem, int kern = 1) {
     return nb;
 }
 
+// a step s coprime with n near n / rows: rows t s mod n (t < rows) are distinct and spread out
+static int trial_step_for(int n, int rows) {
+    if (rows >= n) return 1;
+    int s = std::max(1, n / std::max(1, rows));
+    auto gcd = [](int a, int b) { while (b) { const int t = a % b; a = b; b = t; } return a; };
+    while (gcd(s, n) != 1) ++s;
+    return s;
+}
+
 // process-wide cache of the walk kernel configurations chosen by the autotuner
 struct TuneKey {
     size_t elem; int dim, kind; int m, p; int64_t N; bool rec; int tpb_req, place_req, ctas_req; double grid_req;
@@ -1696,9 +1711,11 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
     } else {
         // autotuner: time each candidate configuration on a prefix of rows once per problem
         // shape (cached for the process); the prefix rows are recomputed by the full launch
+        // (the shared-memory accumulator form, kernel 2, measured 1.6 to 3 times slower on every
+        // workload; it is tried only when asked for)
         std::vector<Cfg> cands;
         for (int kern : {1, 2}) {
-            if (req_kern && kern != req_kern) continue;
+            if (req_kern ? kern != req_kern : kern != 1) continue;
             for (int vg : {0, 1})
                 for (int t : {512, 1024}) {
                     if (fixed_tpb && t != req_tpb) continue;
@@ -1720,14 +1737,30 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
         if (cands.size() == 1) {
             cfg = cands[0];
         } else {
-            const int rows = std::min(n, 2 * nsm);
+            // every candidate runs the same rows, 16 per SM spread over the domain: as in the
+            // whole build, a shape with more CTAs runs fewer rows per CTA (two rows per SM
+            // favoured the shapes with fewer, larger CTAs: the square's 512 x 2 measured 6 %
+            // faster than 1024 x 1 over the whole build, slower on that prefix)
             float best = 3.0e38f;
             cudaEvent_t t0, t1;
             cudaEventCreate(&t0); cudaEventCreate(&t1);
             for (Cfg c : cands) {
+                // an untimed one-row launch first: the kernel's first launch loads its module
+                Cfg c1 = c;
+                c1.grid = 1;
+                WalkArgs<T, D> warm = a;
+                warm.trial_rows = 1;
+                warm.trial_step = 1;
+                EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counter, 0, sizeof(int), st));
+                EWOS_CUDA_TRY(launch(c1, warm));
+                const int rows = std::min(n, 16 * nsm);
                 c.grid = std::max(1, std::min(nsm * c.per_sm, rows));
+                if (c.kern == 1) EWOS_CUDA_TRY(ctx.ensure_acc(sizeof(T) * 4 * (size_t)m * c.grid));   // (outside the timing)
                 WalkArgs<T, D> trial = a;
-                trial.n = rows;
+                // rows spread over the domain (a prefix of the node order can be all near the
+                // boundary, where walks are short): a step coprime with n
+                trial.trial_rows = rows;
+                trial.trial_step = trial_step_for(n, rows);
                 EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counter, 0, sizeof(int), st));
                 cudaEventRecord(t0, st);
                 EWOS_CUDA_TRY(launch(c, trial));
@@ -1893,14 +1926,22 @@ static ewos_status build_batch_kind(std::vector<ewos_toolbox*>& tbs, const std::
             for (int p2 = 1; p2 <= mx && p2 <= 4; p2 *= 2) cands.push_back({t, p2});
         }
         if (cands.empty()) { set_error("batch: the largest toolbox row does not fit in shared memory"); return EWOS_EINVAL; }
+        // each candidate runs a prefix of three global rows per CTA of its grid, compared by time
+        // per row (as the single-build autotuner)
         std::vector<int> off_trial(off);
-        const int prefix = std::min(total, 2 * nsm);
-        for (auto& v : off_trial) v = std::min(v, prefix);
-        EWOS_CUDA_TRY(cudaMemcpyAsync(d_off_trial, off_trial.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
         float best = 3.0e38f;
         cudaEvent_t t0, t1;
         cudaEventCreate(&t0); cudaEventCreate(&t1);
         for (const C& c : cands) {
+            // an untimed one-row launch first (the kernel's first launch loads its module)
+            for (int k = 0; k <= nb; ++k) off_trial[k] = std::min(off[k], 1);
+            EWOS_CUDA_TRY(cudaMemcpyAsync(d_off_trial, off_trial.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
+            EWOS_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), st));
+            cudaError_t we = launch_batch<T, D, KIND>(d_args, d_off_trial, nb, d_counter, 1, c.tpb, smem_for(c.tpb), st);
+            EWOS_CUDA_TRY(we);
+            const int prefix = std::min(total, 3 * nsm * c.per);
+            for (int k = 0; k <= nb; ++k) off_trial[k] = std::min(off[k], prefix);
+            EWOS_CUDA_TRY(cudaMemcpyAsync(d_off_trial, off_trial.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, st));
             EWOS_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(int), st));
             cudaEventRecord(t0, st);
             const int tgrid = std::max(1, std::min(nsm * c.per, prefix));
@@ -1910,6 +1951,7 @@ static ewos_status build_batch_kind(std::vector<ewos_toolbox*>& tbs, const std::
             EWOS_CUDA_TRY(cudaEventSynchronize(t1));
             float ms = 0;
             cudaEventElapsedTime(&ms, t0, t1);
+            ms /= (float)prefix;
             if (ms < best) { best = ms; tpb = c.tpb; per = c.per; }
         }
         cudaEventDestroy(t0); cudaEventDestroy(t1);
