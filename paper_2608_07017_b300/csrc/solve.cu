@@ -1866,6 +1866,11 @@ struct SolveWorkspace {
     double *Q = nullptr, *Lam = nullptr, *LUm = nullptr, *M = nullptr, *Jx = nullptr;
     double *A = nullptr, *b = nullptr, *c = nullptr, *f = nullptr, *g = nullptr, *nl = nullptr;
     double *s = nullptr, *x = nullptr, *v = nullptr, *w = nullptr, *y = nullptr, *u = nullptr, *u2 = nullptr;
+    // KH g of the right-hand side being solved ([(D+1)][n]), valid while vg_for == that g (set and
+    // cleared around one right-hand side's iteration by VgScope): the residuals of Newton and
+    // Picard iterations start from it instead of reading KH again
+    double* vg = nullptr;
+    const double* vg_for = nullptr;
     double* scal = nullptr;                   // [4] reductions
     unsigned long long* umax = nullptr;
     LuScratch lu;
@@ -1898,6 +1903,7 @@ void free_workspace(SolveWorkspace* ws) {
     if (!ws) return;
     ::ewos::dev_free(ws->Q); ::ewos::dev_free(ws->Lam); ::ewos::dev_free(ws->LUm); ::ewos::dev_free(ws->M); ::ewos::dev_free(ws->Jx);
     ::ewos::dev_free(ws->A); ::ewos::dev_free(ws->b); ::ewos::dev_free(ws->c); ::ewos::dev_free(ws->f); ::ewos::dev_free(ws->g); ::ewos::dev_free(ws->nl);
+    ::ewos::dev_free(ws->vg);
     ::ewos::dev_free(ws->s); ::ewos::dev_free(ws->x); ::ewos::dev_free(ws->v); ::ewos::dev_free(ws->w); ::ewos::dev_free(ws->y); ::ewos::dev_free(ws->u); ::ewos::dev_free(ws->u2);
     ::ewos::dev_free(ws->scal); ::ewos::dev_free(ws->umax);
     ::ewos::dev_free(ws->lu.pub); ::ewos::dev_free(ws->lu.bar); ::ewos::dev_free(ws->lu.ipiv);
@@ -1948,6 +1954,7 @@ static ewos_status ensure_workspace(const ewos_toolbox* tb, SolveWorkspace*& slo
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->r, sizeof(double) * m * nrhs));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->dx, sizeof(double) * m * nrhs));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->v, sizeof(double) * E * n));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->vg, sizeof(double) * E * n));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->w, sizeof(double) * E * n));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->y, sizeof(double) * m));
         EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ws->u, sizeof(double) * n * nrhs));
@@ -2031,6 +2038,15 @@ static void apply_v_f2(const Ctx& C, const double* s, const double* g) {
     float* gh = sl + pad4(C.m);
     float* gl = gh + pad4(C.p);
     const int64_t rows = (int64_t)C.E * C.n;
+    if (g && g == C.ws->vg_for) {
+        // v = KH g + P s: the same two sums as P s + KH g, in the other (exact) order
+        cudaMemcpyAsync(C.ws->v, C.ws->vg, sizeof(double) * rows, cudaMemcpyDeviceToDevice, C.st);
+        if (s) {
+            split_f2(C.st, s, sh, sl, C.m);
+            multi_rowdot_f2(C.st, (const float*)C.tb->P, rows, (int)C.m, sh, sl, C.ws->v, 1, 1);
+        }
+        return;
+    }
     if (s) {
         split_f2(C.st, s, sh, sl, C.m);
         multi_rowdot_f2(C.st, (const float*)C.tb->P, rows, (int)C.m, sh, sl, C.ws->v, 1, 0);
@@ -2057,6 +2073,11 @@ static void apply_v(const Ctx& C, const double* s, const double* g) {
     const TP* KH = (const TP*)C.tb->KH;
     const int64_t rows = (int64_t)C.E * C.n;
     const int blocks = (int)((rows * 32 + 255) / 256);
+    if (g && g == C.ws->vg_for) {
+        cudaMemcpyAsync(C.ws->v, C.ws->vg, sizeof(double) * rows, cudaMemcpyDeviceToDevice, C.st);
+        if (s) ::ewos::note_launch(), rowdot_kernel<TP><<<blocks, 256, 0, C.st>>>(P, rows, (int)C.m, s, C.ws->v, 1);
+        return;
+    }
     if (s) {
         ::ewos::note_launch(), rowdot_kernel<TP><<<blocks, 256, 0, C.st>>>(P, rows, (int)C.m, s, C.ws->v, 0);
         ::ewos::note_launch(), rowdot_kernel<TP><<<blocks, 256, 0, C.st>>>(KH, rows, (int)C.p, g, C.ws->v, 1);
@@ -2087,6 +2108,28 @@ static void residual(const Ctx& C, const double* s, const double* g, const doubl
     if (f2) apply_PT_f2(C, C.ws->w, y);
     else apply_PT<TP>(C, C.ws->w, y);
     if (alpha != 0.0 && s) ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, alpha, s, y);
+}
+
+// KH g of one right-hand side kept for the residuals of its iterations (ws->vg), cleared when the
+// scope ends: computed here as the residual's own v with s = 0
+template <typename TP>
+struct VgScope {
+    const Ctx& C;
+    VgScope(const Ctx& c, const double* g) : C(c) {
+        C.ws->vg_for = nullptr;
+        if (sizeof(TP) == 4 && C.ws->F2one) apply_v_f2(C, nullptr, g);
+        else apply_v<TP>(C, nullptr, g);
+        cudaMemcpyAsync(C.ws->vg, C.ws->v, sizeof(double) * C.E * C.n, cudaMemcpyDeviceToDevice, C.st);
+        C.ws->vg_for = g;
+    }
+    ~VgScope() { C.ws->vg_for = nullptr; }
+};
+
+// u = G s + H g after a residual at s: the last plane of that residual's v = P s + KH g (the
+// same FP32-pair or FP64 row products, in the same order, as u_from_s), while nothing else has
+// written ws->v since
+static void u_from_v(const Ctx& C, double* u) {
+    cudaMemcpyAsync(u, C.ws->v + (size_t)C.D * C.n, sizeof(double) * C.n, cudaMemcpyDeviceToDevice, C.st);
 }
 
 static double norm2(const Ctx& C, const double* v, int64_t len) {
@@ -2236,13 +2279,15 @@ static ewos_status solve_fp64(ewos_toolbox* tb, SolveWorkspace* ws, const ewos_p
                 const double* g = ws->g + r * C.p;
                 const double* f = ws->f + r * C.n;
                 cudaMemsetAsync(s, 0, sizeof(double) * C.m, C.st);
+                VgScope<TP> vgs(C, g);
                 residual<TP>(C, s, g, f, nl, pb->nl_ncoef, alpha, ws->y);
                 const double r0 = norm2(C, ws->y, C.m);
                 double rn = r0;
                 int it = 0;
                 while (it < max_iter && rn > tol * r0) {
-                    // u at the current s, Jacobian term G^T diag(lam N'(u)) G
-                    u_from_s(C, tb->P, tb->KH, tb->precision == 64, s, g, ws->u2);
+                    // u at the current s (from the residual just evaluated there), Jacobian term
+                    // G^T diag(lam N'(u)) G
+                    u_from_v(C, ws->u2);
                     dim3 gj((unsigned)((C.m + 255) / 256), (unsigned)C.n);
                     const TP* Gm = (const TP*)tb->P + (size_t)C.D * C.n * C.m;
                     ::ewos::note_launch(), jac_scale_kernel<TP><<<gj, 256, 0, C.st>>>(Gm, ws->u2, tb->lambda, nl, pb->nl_ncoef, ws->Jx, (int)C.n, (int)C.m);
@@ -2271,6 +2316,7 @@ static ewos_status solve_fp64(ewos_toolbox* tb, SolveWorkspace* ws, const ewos_p
             double* u = ws->u + r * C.n;
             cudaMemsetAsync(s, 0, sizeof(double) * C.m, C.st);
             u_from_s(C, tb->P, tb->KH, tb->precision == 64, s, g, u);
+            VgScope<TP> vgs(C, g);               // the residual at s = 0 of every iteration
             int it = 0;
             bool conv = false;
             while (it < max_iter) {
@@ -3526,6 +3572,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                 const double* g = ws->g + r * C.p;
                 const double* f = ws->f + r * C.n;
                 cudaMemsetAsync(s, 0, sizeof(double) * C.m, C.st);
+                VgScope<TP> vgs(C, g);
                 residual<TP>(C, s, g, f, nl, pb->nl_ncoef, alpha, ws->y);
                 const double r0 = norm2(C, ws->y, C.m);
                 double rn = r0, rn_prev = r0;
@@ -3536,7 +3583,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                     if (it > 0) eta = std::min(kEtaMax, 0.9 * (rn / rn_prev) * (rn / rn_prev));
                     eta = std::max(eta, std::max(kEtaMin, 0.5 * tol * r0 / rn));
                     rn_prev = rn;
-                    u_from_s(C, tb->P, tb->KH, tb->precision == 64, s, g, ws->u2);
+                    u_from_v(C, ws->u2);         // u at the current s, from the residual just evaluated
                     if (have_factors && opt.newton_reuse) {
                         cudaMemcpyAsync(ws->rhs, ws->y, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
                         double rel = 1.0;
@@ -3607,6 +3654,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
             double* u = ws->u + r * C.n;
             cudaMemsetAsync(s, 0, sizeof(double) * C.m, C.st);
             u_from_s(C, tb->P, tb->KH, tb->precision == 64, s, g, u);
+            VgScope<TP> vgs(C, g);               // the residual at s = 0 of every iteration
             int it = 0;
             bool conv = false;
             while (it < max_iter) {
