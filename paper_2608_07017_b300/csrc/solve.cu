@@ -1205,71 +1205,79 @@ __global__ void __launch_bounds__(kNpThreads) lu_diag_factor_kernel(const T* __r
     }
     __syncthreads();
     // doubling to 32: four 16 x 16 tasks (lower pairs 0, 1 and upper pairs 0, 1), four elements
-    // per thread; T = L21 inv(L11) (T = U12 inv(U22)), then X21 = -inv(L22) T (X12 = -inv(U11) T)
+    // per thread (rows r0 + 4 s of column c); T = L21 inv(L11) (T = U12 inv(U22)), then
+    // X21 = -inv(L22) T (X12 = -inv(U11) T).  The k loop is outside the thread's rows, so each
+    // value of the right factor is read once for all of them (the row values are broadcasts):
+    // these products are bound by shared-memory reads.  Each sum keeps its order over k.
     {
         const int task = tid >> 6, up = task >> 1, a = 32 * (task & 1), b = a + 16;
+        const int r0 = (tid & 63) >> 4, c = tid & 15;
         T* Tt = Tb + task * 16 * 17;
+        {
+            const T* Fr = up ? F + a * LD + b : F + b * LD + a;          // rows of L21 (U12)
+            const T* Xc = up ? Ui + b * LD + b + c : Li + a * LD + a + c; // column c of inv(L11) (inv(U22))
+            T sum[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-        for (int s4 = 0; s4 < 4; ++s4) {
-            const int e = (tid & 63) + 64 * s4, r = e >> 4, c = e & 15;
-            T sum = T(0);
-            if (!up) {
+            for (int k = 0; k < 16; ++k) {
+                const T x = Xc[k * LD];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) sum = fma(F[(b + r) * LD + a + k], Li[(a + k) * LD + a + c], sum);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 16; ++k) sum = fma(F[(a + r) * LD + b + k], Ui[(b + k) * LD + b + c], sum);
+                for (int s4 = 0; s4 < 4; ++s4) sum[s4] = fma(Fr[(r0 + 4 * s4) * LD + k], x, sum[s4]);
             }
-            Tt[r * 17 + c] = sum;
+#pragma unroll
+            for (int s4 = 0; s4 < 4; ++s4) Tt[(r0 + 4 * s4) * 17 + c] = sum[s4];
         }
         __syncthreads();
+        {
+            T* Xi = up ? Ui + a * LD + a : Li + b * LD + b;                // inv(U11) (inv(L22))
+            T* Xo = up ? Ui + a * LD + b + c : Li + b * LD + a + c;        // the block written
+            T sum[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-        for (int s4 = 0; s4 < 4; ++s4) {
-            const int e = (tid & 63) + 64 * s4, r = e >> 4, c = e & 15;
-            T sum = T(0);
-            if (!up) {
+            for (int k = 0; k < 16; ++k) {
+                const T t = Tt[k * 17 + c];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) sum = fma(Li[(b + r) * LD + b + k], Tt[k * 17 + c], sum);
-                Li[(b + r) * LD + a + c] = -sum;
-            } else {
-#pragma unroll
-                for (int k = 0; k < 16; ++k) sum = fma(Ui[(a + r) * LD + a + k], Tt[k * 17 + c], sum);
-                Ui[(a + r) * LD + b + c] = -sum;
+                for (int s4 = 0; s4 < 4; ++s4) sum[s4] = fma(Xi[(r0 + 4 * s4) * LD + k], t, sum[s4]);
             }
+#pragma unroll
+            for (int s4 = 0; s4 < 4; ++s4) Xo[(r0 + 4 * s4) * LD] = -sum[s4];
         }
         __syncthreads();
     }
-    // doubling to 64: the lower and the upper 32 x 32 task, eight elements per thread
+    // doubling to 64: the lower and the upper 32 x 32 task, eight elements per thread (rows
+    // r0 + 4 s of column c), as above
     {
         const int up = tid >> 7, a = 0, b = 32;
+        const int r0 = (tid & 127) >> 5, c = tid & 31;
         T* Tt = Tb + up * 32 * 33;
+        {
+            const T* Fr = up ? F + a * LD + b : F + b * LD + a;
+            const T* Xc = up ? Ui + b * LD + b + c : Li + a * LD + a + c;
+            T sum[8];
 #pragma unroll
-        for (int s8 = 0; s8 < 8; ++s8) {
-            const int e = (tid & 127) + 128 * s8, r = e >> 5, c = e & 31;
-            T sum = T(0);
-            if (!up) {
+            for (int s8 = 0; s8 < 8; ++s8) sum[s8] = T(0);
 #pragma unroll 8
-                for (int k = 0; k < 32; ++k) sum = fma(F[(b + r) * LD + a + k], Li[(a + k) * LD + a + c], sum);
-            } else {
-#pragma unroll 8
-                for (int k = 0; k < 32; ++k) sum = fma(F[(a + r) * LD + b + k], Ui[(b + k) * LD + b + c], sum);
+            for (int k = 0; k < 32; ++k) {
+                const T x = Xc[k * LD];
+#pragma unroll
+                for (int s8 = 0; s8 < 8; ++s8) sum[s8] = fma(Fr[(r0 + 4 * s8) * LD + k], x, sum[s8]);
             }
-            Tt[r * 33 + c] = sum;
+#pragma unroll
+            for (int s8 = 0; s8 < 8; ++s8) Tt[(r0 + 4 * s8) * 33 + c] = sum[s8];
         }
         __syncthreads();
+        {
+            T* Xi = up ? Ui + a * LD + a : Li + b * LD + b;
+            T* Xo = up ? Ui + a * LD + b + c : Li + b * LD + a + c;
+            T sum[8];
 #pragma unroll
-        for (int s8 = 0; s8 < 8; ++s8) {
-            const int e = (tid & 127) + 128 * s8, r = e >> 5, c = e & 31;
-            T sum = T(0);
-            if (!up) {
+            for (int s8 = 0; s8 < 8; ++s8) sum[s8] = T(0);
 #pragma unroll 8
-                for (int k = 0; k < 32; ++k) sum = fma(Li[(b + r) * LD + b + k], Tt[k * 33 + c], sum);
-                Li[(b + r) * LD + a + c] = -sum;
-            } else {
-#pragma unroll 8
-                for (int k = 0; k < 32; ++k) sum = fma(Ui[(a + r) * LD + a + k], Tt[k * 33 + c], sum);
-                Ui[(a + r) * LD + b + c] = -sum;
+            for (int k = 0; k < 32; ++k) {
+                const T t = Tt[k * 33 + c];
+#pragma unroll
+                for (int s8 = 0; s8 < 8; ++s8) sum[s8] = fma(Xi[(r0 + 4 * s8) * LD + k], t, sum[s8]);
             }
+#pragma unroll
+            for (int s8 = 0; s8 < 8; ++s8) Xo[(r0 + 4 * s8) * LD] = -sum[s8];
         }
         __syncthreads();
     }
@@ -1886,6 +1894,8 @@ struct SolveWorkspace {
     float *D32 = nullptr, *D32p = nullptr;
     float* F2buf = nullptr;          // hi/lo FP32 pairs of Sb [m][bcap], Gb [p][bcap], Wb [rows][bcap]
     double* Ypart = nullptr;         // per-CTA partials of the fused one-column residual [ypart_grid][m]
+    double* ctpart = nullptr;        // per-CTA partials of the whole-row column products [parts][m]
+    int64_t ctpart_cap = 0;          // doubles
     float* F2one = nullptr;          // FP32 toolboxes: hi/lo pairs of one column of s [m], g [p], w [rows]
     int ypart_grid = 0;
     struct Graph {
@@ -1916,7 +1926,7 @@ void free_workspace(SolveWorkspace* ws) {
     ::ewos::dev_free(ws->Sb); ::ewos::dev_free(ws->Yb); ::ewos::dev_free(ws->Vb); ::ewos::dev_free(ws->Wb);
     ::ewos::dev_free(ws->Fb); ::ewos::dev_free(ws->Gb); ::ewos::dev_free(ws->Ub); ::ewos::dev_free(ws->nrm);
     ::ewos::dev_free(ws->alpha_dev); ::ewos::dev_free(ws->D32); ::ewos::dev_free(ws->D32p); ::ewos::dev_free(ws->F2buf);
-    ::ewos::dev_free(ws->Ypart); ::ewos::dev_free(ws->F2one);
+    ::ewos::dev_free(ws->Ypart); ::ewos::dev_free(ws->F2one); ::ewos::dev_free(ws->ctpart);
     for (auto& g : ws->graphs) cudaGraphExecDestroy(g.exec);
     if (ws->cap_st) cudaStreamDestroy(ws->cap_st);
     delete ws;
@@ -2028,6 +2038,8 @@ static void multi_rowdot_f2(cudaStream_t st, const float* X, int64_t rows, int c
 static void multi_coltrans_f2(cudaStream_t st, const float* X, int64_t rows, int cols, const float* Whi, const float* Wlo,
                               double* Y, int rc);
 static void split_f2(cudaStream_t st, const double* v, float* hi, float* lo, int64_t count);
+static bool coltrans_rows(const Ctx& C, const float* X, int64_t rows, int cols, const float* Whi, const float* Wlo,
+                          double* Y);
 
 // FP32 toolboxes: v = P s (+ KH g) and y = P^T w with FP64-accurate products on the FP32 pipes:
 // s, g, w split into unevaluated FP32 pairs, products summed in FP32 pairs (two-sum), reduced in
@@ -2062,6 +2074,7 @@ static void apply_PT_f2(const Ctx& C, const double* w, double* y) {
     float* wl = wh + pad4((int64_t)C.E * C.n);
     const int64_t rows = (int64_t)C.E * C.n;
     split_f2(C.st, w, wh, wl, rows);
+    if (coltrans_rows(C, (const float*)C.tb->P, rows, (int)C.m, wh, wl, y)) return;
     cudaMemsetAsync(y, 0, sizeof(double) * C.m, C.st);
     multi_coltrans_f2(C.st, (const float*)C.tb->P, rows, (int)C.m, wh, wl, y, 1);
 }
@@ -2830,10 +2843,13 @@ __global__ void rowdot_f2_vec_kernel(const float* __restrict__ X, int64_t rows, 
     if (lane == 0) Vout[row] = accumulate ? Vout[row] + acc : acc;
 }
 
-// Y[c] += sum_{row in chunk} X[row][c] (Whi[row] + Wlo[row])   (thread per four columns)
+// Y[c] += sum_{row in chunk} X[row][c] (Whi[row] + Wlo[row])   (thread per four columns); with
+// Ypart the chunk's sums are stored to row blockIdx.y of Ypart [chunks][cols] instead (summed in
+// order by sum_parts_kernel: no atomics, the result independent of the order the CTAs run in)
 template <int kU>
 __global__ void coltrans_f2_vec_kernel(const float* __restrict__ X, int64_t rows, int cols, const float* __restrict__ Whi,
-                                       const float* __restrict__ Wlo, double* __restrict__ Y, int64_t chunk) {
+                                       const float* __restrict__ Wlo, double* __restrict__ Y, int64_t chunk,
+                                       double* __restrict__ Ypart = nullptr) {
     const int c4 = blockIdx.x * blockDim.x + threadIdx.x;
     if (c4 >= (cols >> 2)) return;
     const int64_t a = (int64_t)blockIdx.y * chunk;
@@ -2856,8 +2872,43 @@ __global__ void coltrans_f2_vec_kernel(const float* __restrict__ X, int64_t rows
         const float wh = __ldg(Whi + r), wl = __ldg(Wlo + r);
         f2_add_prod4(hi, lo, __ldcs(xc + r * rs), make_float4(wh, wh, wh, wh), make_float4(wl, wl, wl, wl));
     }
+    if (Ypart) {
+        double* yp = Ypart + (size_t)blockIdx.y * cols + (size_t)c4 * 4;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) yp[k] = (double)hi[k] + (double)lo[k];
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 4; ++k) atomicAdd(&Y[(size_t)c4 * 4 + k], (double)hi[k] + (double)lo[k]);
+}
+
+// Y[c] = sum over b of Ypart[b][c] in a fixed order: a CTA takes 32 columns, warp w sums parts
+// w, w + 8, .. (eight loads in flight), and the eight warp sums are added in warp order
+__global__ void __launch_bounds__(256) sum_parts_kernel(const double* __restrict__ Ypart, int parts, int cols,
+                                                        double* __restrict__ Y) {
+    __shared__ double red[8][33];
+    const int tx = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + tx;
+    double a = 0.0;
+    if (c < cols) {
+        int b = w;
+        for (; b + 56 < parts; b += 64) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = Ypart[(size_t)(b + 8 * u) * cols + c];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a += v[u];
+        }
+        for (; b < parts; b += 8) a += Ypart[(size_t)b * cols + c];
+    }
+    red[w][tx] = a;
+    __syncthreads();
+    if (w == 0 && c < cols) {
+        double t = red[0][tx];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) t += red[k][tx];
+        Y[c] = t;
+    }
 }
 
 static inline bool aligned16(const void* q) { return ((uintptr_t)q & 15) == 0; }
@@ -3053,6 +3104,32 @@ static void multi_coltrans_f2(cudaStream_t st, const float* X, int64_t rows, int
     else if (rc == 4) ::ewos::note_launch(), multi_coltrans_f2_kernel<4><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
     else if (rc == 8) ::ewos::note_launch(), multi_coltrans_f2_kernel<8><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
     else ::ewos::note_launch(), multi_coltrans_f2_kernel<16><<<grid, 128, 0, st>>>(X, rows, cols, Whi, Wlo, Y, rc, chunk);
+}
+
+// Y = X^T (Whi + Wlo) for one column: the 256-row x 512-column tiles of coltrans_f2_vec_kernel
+// with their sums stored as partials and added in order (no atomics); X 16-byte aligned, cols a
+// multiple of 4; false when it does not apply or the partials cannot be allocated (the caller
+// then takes the atomic form)
+static bool coltrans_rows(const Ctx& C, const float* X, int64_t rows, int cols, const float* Whi, const float* Wlo,
+                          double* Y) {
+    if (cols % 4 != 0 || !aligned16(X) || rows < 1) return false;
+    const int64_t vchunk = 256;
+    const int parts = (int)((rows + vchunk - 1) / vchunk);
+    SolveWorkspace* ws = C.ws;
+    if (ws->ctpart_cap < (int64_t)parts * cols) {
+        ::ewos::dev_free(ws->ctpart);
+        ws->ctpart = nullptr;
+        ws->ctpart_cap = 0;
+        if (::ewos::dev_alloc((void**)&ws->ctpart, sizeof(double) * (size_t)parts * cols) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        ws->ctpart_cap = (int64_t)parts * cols;
+    }
+    dim3 vgrid((unsigned)((cols / 4 + 127) / 128), (unsigned)parts);
+    ::ewos::note_launch(), coltrans_f2_vec_kernel<8><<<vgrid, 128, 0, C.st>>>(X, rows, cols, Whi, Wlo, Y, vchunk, ws->ctpart);
+    ::ewos::note_launch(), sum_parts_kernel<<<(cols + 31) / 32, 256, 0, C.st>>>(ws->ctpart, parts, cols, Y);
+    return true;
 }
 
 static void split_f2(cudaStream_t st, const double* v, float* hi, float* lo, int64_t count) {
