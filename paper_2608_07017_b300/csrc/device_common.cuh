@@ -31,6 +31,19 @@ __host__ __device__ __forceinline__ u32x4 philox4x32_10(u32x4 x, uint32_t k0, ui
     return x;
 }
 
+// The same rounds with the key schedule precomputed: rk[r] = k0 + r 0x9E3779B9, rk[10 + r] =
+// k1 + r 0xBB67AE85 (r < 10).  Read from the kernel's parameter space the keys are operands of the
+// XORs themselves, which saves the schedule's two additions per round.
+__device__ __forceinline__ u32x4 philox4x32_10_rk(u32x4 x, const uint32_t* rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * x.a, hi0 = __umulhi(0xD2511F53u, x.a);
+        const uint32_t lo1 = 0xCD9E8D57u * x.c, hi1 = __umulhi(0xCD9E8D57u, x.c);
+        x = u32x4{hi1 ^ x.b ^ rk[r], lo1, hi0 ^ x.d ^ rk[10 + r], lo0};
+    }
+    return x;
+}
+
 // uniform in (0,1): ((x >> 9) + 1/2) / 2^23 -- exact in FP32 and FP64 alike
 template <typename T> __device__ __forceinline__ T u01(uint32_t x) {
     return (T)((float)(x >> 9) * 1.1920928955078125e-07f + 5.9604644775390625e-08f);
