@@ -717,6 +717,7 @@ struct WalkArgs {
     int64_t N;
     T eps;
     uint32_t k0, k1, inst;
+    uint32_t rk[20];   // Philox key schedule of (k0, k1): rk[r] = k0 + r W0, rk[10 + r] = k1 + r W1
     int64_t max_steps;
     const T* x;        // [n][D]
     const T* r0;       // [n]
@@ -804,26 +805,35 @@ __device__ __forceinline__ void bin_point(T* acc, int m, int j, T G_add, const T
 //   ball term   counter (l, 0xFFFFFFFF, i, inst|0): (S, angle or z, phi, -)
 //   step k >= 0 counter (l, k, i, inst|slot): d = 2 slot 0 = (radius of Y, angle of Y, angle of U, -);
 //               d = 3 slot 0 = (median uniforms x3, z of Y), slot 1 = (phi of Y, z of U, phi of U, -)
-template <typename T, int D>
+// Philox block of counter c: from the precomputed key schedule rk (single builds: the schedule sits
+// in the kernel's parameters) or from the key (batched builds read their arguments from shared
+// memory, where the schedule would cost loads)
+template <bool PRK>
+__device__ __forceinline__ u32x4 walk_philox(u32x4 c, uint32_t k0, uint32_t k1, const uint32_t* rk) {
+    if constexpr (PRK) return philox4x32_10_rk(c, rk);
+    else return philox4x32_10(c, k0, k1);
+}
+
+template <typename T, int D, bool PRK = false>
 __device__ __forceinline__ void draw_ball(uint32_t l, uint32_t row, uint32_t inst, uint32_t k0, uint32_t k1,
-                                          T& S, T* Zb) {
-    const u32x4 q = philox4x32_10(u32x4{l, 0xFFFFFFFFu, row, inst}, k0, k1);
+                                          T& S, T* Zb, const uint32_t* rk = nullptr) {
+    const u32x4 q = walk_philox<PRK>(u32x4{l, 0xFFFFFFFFu, row, inst}, k0, k1, rk);
     S = T(1) - m_sqrt(u01<T>(q.a));
     if (D == 2) dir2<T>(u01<T>(q.b), Zb);
     else dir3<T>(u01<T>(q.b), u01<T>(q.c), Zb);
 }
 
-template <typename T, int D>
+template <typename T, int D, bool PRK = false>
 __device__ __forceinline__ void draw_step(uint32_t l, uint32_t k, uint32_t row, uint32_t inst, uint32_t k0,
-                                          uint32_t k1, T& R, T* Zs, T* U) {
+                                          uint32_t k1, T& R, T* Zs, T* U, const uint32_t* rk = nullptr) {
     if (D == 2) {
-        const u32x4 q = philox4x32_10(u32x4{l, k, row, inst | 0u}, k0, k1);
+        const u32x4 q = walk_philox<PRK>(u32x4{l, k, row, inst | 0u}, k0, k1, rk);
         R = green_radius_2d<T>(u01<T>(q.a));
         dir2<T>(u01<T>(q.b), Zs);
         dir2<T>(u01<T>(q.c), U);
     } else {
-        const u32x4 q = philox4x32_10(u32x4{l, k, row, inst | 0u}, k0, k1);
-        const u32x4 v = philox4x32_10(u32x4{l, k, row, inst | 1u}, k0, k1);
+        const u32x4 q = walk_philox<PRK>(u32x4{l, k, row, inst | 0u}, k0, k1, rk);
+        const u32x4 v = walk_philox<PRK>(u32x4{l, k, row, inst | 1u}, k0, k1, rk);
         R = med3(u01<T>(q.a), u01<T>(q.b), u01<T>(q.c));
         dir3<T>(u01<T>(q.d), u01<T>(v.a), Zs);
         dir3<T>(u01<T>(v.b), u01<T>(v.c), U);
@@ -873,25 +883,25 @@ __host__ __device__ constexpr size_t queue_bytes(int nwarps, bool record) {
 }
 
 // U_0 of walk l of a row, as draw_step draws it at step 0
-template <typename T, int D>
+template <typename T, int D, bool PRK = false>
 __device__ __forceinline__ void draw_first_direction(uint32_t l, uint32_t row, uint32_t inst, uint32_t k0, uint32_t k1,
-                                                     T* U) {
+                                                     T* U, const uint32_t* rk = nullptr) {
     if (D == 2) {
-        const u32x4 q = philox4x32_10(u32x4{l, 0u, row, inst | 0u}, k0, k1);
+        const u32x4 q = walk_philox<PRK>(u32x4{l, 0u, row, inst | 0u}, k0, k1, rk);
         dir2<T>(u01<T>(q.c), U);
     } else {
-        const u32x4 v = philox4x32_10(u32x4{l, 0u, row, inst | 1u}, k0, k1);
+        const u32x4 v = walk_philox<PRK>(u32x4{l, 0u, row, inst | 1u}, k0, k1, rk);
         dir3<T>(u01<T>(v.b), u01<T>(v.c), U);
     }
 }
 
-template <typename T, int D, bool RECORD>
+template <typename T, int D, bool RECORD, bool PRK>
 __device__ __forceinline__ void bin_stopped(const WalkArgs<T, D>& a, const WalkQueue<T, D>& q, int slot, int row,
                                             T* accKH, uint32_t* accH) {
     T X[D], U[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) X[c] = q.X[slot * D + c];
-    draw_first_direction<T, D>(q.L[slot], (uint32_t)row, a.inst, a.k0, a.k1, U);
+    draw_first_direction<T, D, PRK>(q.L[slot], (uint32_t)row, a.inst, a.k0, a.k1, U, a.rk);
     const int jz = nearest_or_scan(a.Z, a.p, X);
     atomicAdd(&accH[jz], 1u);
 #pragma unroll
@@ -1026,7 +1036,7 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
         // ---- ball term of the first sphere (path independent, Prop. 2.6 (ii))
         for (int64_t l = threadIdx.x; l < a.N; l += blockDim.x) {
             T S, Zb[D], pt[D];
-            draw_ball<T, D>((uint32_t)l, (uint32_t)row, a.inst, a.k0, a.k1, S, Zb);
+            draw_ball<T, D, !BATCH>((uint32_t)l, (uint32_t)row, a.inst, a.k0, a.k1, S, Zb, a.rk);
             const T wsum = (D == 2) ? T(1) + S : T(1) + S + S * S;
 #pragma unroll
             for (int c = 0; c < D; ++c) pt[c] = xi[c] + r0 * S * Zb[c];
@@ -1082,7 +1092,7 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
             qn += __popc(sm);
             if (have) {
                 T R, Zs[D], U[D], pt[D];
-                draw_step<T, D>(l, k, (uint32_t)row, a.inst, a.k0, a.k1, R, Zs, U);
+                draw_step<T, D, !BATCH>(l, k, (uint32_t)row, a.inst, a.k0, a.k1, R, Zs, U, a.rk);
                 const T rR = r * R;
 #pragma unroll
                 for (int c = 0; c < D; ++c) pt[c] = X[c] + rR * Zs[c];
@@ -1105,13 +1115,13 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
             // converged boundary binning of queued walks (queue < 32 + 32 <= kQueue entries)
             __syncwarp();
             while (qn >= 32) {
-                bin_stopped<T, D, RECORD>(a, q, wid * kQueue + qn - 1 - lane, row, accKH, accH);
+                bin_stopped<T, D, RECORD, !BATCH>(a, q, wid * kQueue + qn - 1 - lane, row, accKH, accH);
                 qn -= 32;
             }
             __syncwarp();
         }
         // drain this warp's queue
-        for (int e = lane; e < qn; e += 32) bin_stopped<T, D, RECORD>(a, q, wid * kQueue + e, row, accKH, accH);
+        for (int e = lane; e < qn; e += 32) bin_stopped<T, D, RECORD, !BATCH>(a, q, wid * kQueue + e, row, accKH, accH);
         __syncwarp();
         __syncthreads();
 
@@ -1579,6 +1589,10 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
     // walk kernel configuration
     a.n = n; a.m = m; a.p = p; a.N = tb->N; a.eps = (T)tb->eps;
     a.k0 = (uint32_t)tb->seed; a.k1 = (uint32_t)(tb->seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        a.rk[r] = a.k0 + (uint32_t)r * 0x9E3779B9u;
+        a.rk[10 + r] = a.k1 + (uint32_t)r * 0xBB67AE85u;
+    }
     a.inst = (tb->instance & 0xFFFFu) << 8;
     a.max_steps = o.max_steps > 0 ? o.max_steps : 10000;
     a.x = (const T*)ctx.d_xT; a.r0 = (const T*)ctx.d_r0;
@@ -2180,6 +2194,10 @@ static ewos_status build_noalloc_typed(const ewos_domain* dom, const double* d_x
     WalkArgs<float, D> a{};
     a.n = n; a.m = m; a.p = p; a.N = N; a.eps = (float)eps;
     a.k0 = (uint32_t)seed; a.k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        a.rk[r] = a.k0 + (uint32_t)r * 0x9E3779B9u;
+        a.rk[10 + r] = a.k1 + (uint32_t)r * 0xBB67AE85u;
+    }
     a.inst = 0;
     a.max_steps = max_steps > 0 ? max_steps : 10000;
     a.x = d_xT; a.r0 = d_r0;
