@@ -1125,7 +1125,9 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
         __syncwarp();
         __syncthreads();
 
-        // ---- flush the row: scale and write coalesced, then clear the accumulators
+        // ---- flush the row: scale and write coalesced, then clear the accumulators.  The output
+        // rows (1.3 GB per ball launch) are written with the streaming (evict-first) policy, so
+        // that they do not push the V lookup's candidate table (74 MB) out of L2
         const T sG = invN / T(2 * D);
         const T sGG = invN / (T(2) * r0);
         const T sKH = T(D) * invN / r0;
@@ -1143,27 +1145,27 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
                     for (int c = 0; c < 4; ++c) { v[c] = __ldcg(acc + (size_t)t * 4 + c); acc[(size_t)t * 4 + c] = T(0); }
                 }
 #pragma unroll
-                for (int c = 0; c < D; ++c) a.P[c * nm + (size_t)row * a.m + t] = v[1 + c] * sGG;
-                a.P[D * nm + (size_t)row * a.m + t] = v[0] * sG;
+                for (int c = 0; c < D; ++c) __stcs(a.P + c * nm + (size_t)row * a.m + t, v[1 + c] * sGG);
+                __stcs(a.P + D * nm + (size_t)row * a.m + t, v[0] * sG);
             } else {
 #pragma unroll
                 for (int c = 0; c < D; ++c) {
-                    a.P[c * nm + (size_t)row * a.m + t] = acc[(size_t)c * a.m + t] * sGG;
+                    __stcs(a.P + c * nm + (size_t)row * a.m + t, acc[(size_t)c * a.m + t] * sGG);
                     acc[(size_t)c * a.m + t] = T(0);
                 }
-                a.P[D * nm + (size_t)row * a.m + t] = acc[(size_t)D * a.m + t] * sG;
+                __stcs(a.P + D * nm + (size_t)row * a.m + t, acc[(size_t)D * a.m + t] * sG);
                 acc[(size_t)D * a.m + t] = T(0);
             }
         }
         for (int t = threadIdx.x; t < a.p; t += blockDim.x) {
 #pragma unroll
             for (int c = 0; c < D; ++c) {
-                a.KH[c * np + (size_t)row * a.p + t] = accKH[(size_t)c * a.p + t] * sKH;
+                __stcs(a.KH + c * np + (size_t)row * a.p + t, accKH[(size_t)c * a.p + t] * sKH);
                 accKH[(size_t)c * a.p + t] = T(0);
             }
             const uint32_t h = accH[t];
-            a.KH[D * np + (size_t)row * a.p + t] = (T)h * invN;
-            a.Hc[(size_t)row * a.p + t] = h;
+            __stcs(a.KH + D * np + (size_t)row * a.p + t, (T)h * invN);
+            __stcs(a.Hc + (size_t)row * a.p + t, h);
             accH[t] = 0u;
         }
     }
