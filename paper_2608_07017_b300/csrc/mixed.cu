@@ -710,7 +710,9 @@ struct Scratch {
     float* Btl = nullptr;
     int* err = nullptr;
     size_t cap = 0;
-    float* scale = nullptr;        // FP16 forms: [0], [1] the maxima that set [2] s_A (s_P), [3] s_B (s_Q); [4] 1/(s_A s_B)
+    float* scale = nullptr;        // FP16 forms: [0], [1] the maxima that set [2] s_A (s_P), [3] s_B (s_Q); [4] 1/(s_A s_B);
+                                   // [5] max |P|, [6] max |A| kept for the operand of key pkey, akey
+    uint64_t pkey = 0, akey = 0;   // (a toolbox's serial: its P, and the G plane of P, never change)
     int* tiles = nullptr;          // (tile row, tile column) per CTA, blocked order
     long long tiles_key = -1;      // shape the table was made for
     int tiles_count = 0;
@@ -816,9 +818,12 @@ __global__ void absmax2_kernel(const float* __restrict__ A, int64_t na, const fl
     }
 }
 
-// powers of two s_A, s_B with max |A| s_A and max |B| s_B in [2^13, 2^14), and 1 / (s_A s_B)
-__global__ void ab_scale_kernel(float* scale) {
+// powers of two s_A, s_B with max |A| s_A and max |B| s_B in [2^13, 2^14), and 1 / (s_A s_B);
+// max |A| from scale[0], or from the kept scale[6] (cached), and kept there (keep)
+__global__ void ab_scale_kernel(float* scale, int cached, int keep) {
     if (threadIdx.x != 0) return;
+    if (cached) scale[0] = scale[6];
+    else if (keep) scale[6] = scale[0];
     auto pw = [](float mxv) {
         if (!(mxv > 0.f) || !isfinite(mxv)) return 1.0f;
         int e;
@@ -917,7 +922,7 @@ static ewos_status tc_enqueue(tc::Scratch& S, const float* Akm, const float* Bkm
 // rate; as accurate as the TF32 split while max |A| and max |B| do not exceed the other entries
 // by more than about 2^17 (below that an entry keeps an absolute error of 2^-39 of the largest).
 static ewos_status tc_enqueue16(tc::Scratch& S, const float* Akm, const float* Bkm, float* C, int M, int N, int K,
-                                cudaStream_t st, bool sym) {
+                                cudaStream_t st, bool sym, uint64_t akey = 0) {
     using namespace tc;
     using CF = Cfg<true, 0, true>;
     const int Kp = (K + 2 * BK - 1) / (2 * BK) * (2 * BK);
@@ -938,9 +943,13 @@ static ewos_status tc_enqueue16(tc::Scratch& S, const float* Akm, const float* B
     __half* atl = reinterpret_cast<__half*>(S.Atl);
     __half* bt = reinterpret_cast<__half*>(S.Bt);
     __half* btl = reinterpret_cast<__half*>(S.Btl);
-    EWOS_CUDA_TRY(cudaMemsetAsync(S.scale, 0, sizeof(float) * 8, st));
-    ::ewos::note_launch(), absmax2_kernel<<<4 * 148, 256, 0, st>>>(Akm, (int64_t)K * M, Bkm, (int64_t)K * N, S.scale);
-    ::ewos::note_launch(), ab_scale_kernel<<<1, 32, 0, st>>>(S.scale);
+    // max |A| is kept between calls for the same operand (akey: the toolbox's serial)
+    const bool acached = akey != 0 && S.akey == akey;
+    EWOS_CUDA_TRY(cudaMemsetAsync(S.scale, 0, sizeof(float) * 5, st));
+    ::ewos::note_launch(), absmax2_kernel<<<4 * 148, 256, 0, st>>>(Akm, acached ? 0 : (int64_t)K * M, Bkm, (int64_t)K * N,
+                                                                  S.scale);
+    ::ewos::note_launch(), ab_scale_kernel<<<1, 32, 0, st>>>(S.scale, acached ? 1 : 0, akey != 0 ? 1 : 0);
+    if (akey != 0) S.akey = akey;
     const dim3 tb(32, 8);
     ::ewos::note_launch(), transpose_split16_kernel<<<dim3((M + 31) / 32, (Kp + 31) / 32), tb, 0, st>>>(Akm, K, M, at, atl, Kp,
                                                                                                      S.scale, 2);
@@ -963,8 +972,10 @@ static ewos_status tc_enqueue16(tc::Scratch& S, const float* Akm, const float* B
 
 static ewos_status tc_check(tc::Scratch& S, cudaStream_t st) {
     int herr = 0;
-    EWOS_CUDA_TRY(cudaMemcpyAsync(&herr, S.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    EWOS_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaError_t e = cudaMemcpyAsync(&herr, S.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || herr) S.pkey = S.akey = 0;      // the kept maxima may not have been written
+    EWOS_CUDA_TRY(e);
     if (herr) {
         set_error("tensor-core assembly: a pipeline wait timed out");
         return EWOS_ETIMEOUT;
@@ -1059,9 +1070,12 @@ __global__ void pq_absmax_kernel(const float* __restrict__ P, int64_t count, con
 }
 
 // powers of two s_P, s_Q with max |P| s_P and max |Q| s_Q in [2^13, 2^14) (|Q| <= max |P| times the
-// largest row sum of |M|, with a little room for the rounding of Q), and their inverse product
-__global__ void pq_scale_kernel(float* scale) {
+// largest row sum of |M|, with a little room for the rounding of Q), and their inverse product;
+// max |P| from scale[0], or from the kept scale[5] (cached), and kept there (keep)
+__global__ void pq_scale_kernel(float* scale, int cached, int keep) {
     if (threadIdx.x != 0) return;
+    if (cached) scale[0] = scale[5];
+    else if (keep) scale[5] = scale[0];
     const float mp = scale[0], mq = scale[0] * scale[1] * 1.0001f;
     auto pw = [](float mxv) {
         if (!(mxv > 0.f) || !isfinite(mxv)) return 1.0f;
@@ -1126,7 +1140,7 @@ __global__ void pq_split16_kernel(const float* __restrict__ P, const double* __r
 // three-product TF32 GEMM; waits for the launch (pipeline timeouts are reported)
 // The FP16 form of tc_assemble_pq (same operands in FP16 halves, twice the tensor-core rate)
 static ewos_status tc_assemble_pq16(tc::Scratch& S, const float* P, const double* Mc, int n, int m, int D, float* C,
-                                    cudaStream_t st, bool sym) {
+                                    cudaStream_t st, bool sym, uint64_t pkey = 0) {
     using namespace tc;
     const int E = D + 1, K = E * n;
     const int Kp = (K + 2 * BK - 1) / (2 * BK) * (2 * BK);          // halves, 128-byte rows
@@ -1151,13 +1165,16 @@ static ewos_status tc_assemble_pq16(tc::Scratch& S, const float* P, const double
         for (__half* b : {at, atl, bt, btl})
             EWOS_CUDA_TRY(cudaMemset2DAsync(b + K, sizeof(__half) * Kp, 0, sizeof(__half) * (Kp - K), m, st));
     }
-    EWOS_CUDA_TRY(cudaMemsetAsync(S.scale, 0, sizeof(float) * 8, st));
+    // max |P| is kept between calls for the same toolbox (pkey: its serial)
+    const bool pcached = pkey != 0 && S.pkey == pkey;
+    EWOS_CUDA_TRY(cudaMemsetAsync(S.scale, 0, sizeof(float) * 5, st));
     if (E != 3 && E != 4) {
         set_error("tensor-core assembly: dimension must be 2 or 3");
         return EWOS_EINVAL;
     }
-    ::ewos::note_launch(), pq_absmax_kernel<<<4 * 148, 256, 0, st>>>(P, (int64_t)E * n * m, Mc, n, E, S.scale);
-    ::ewos::note_launch(), pq_scale_kernel<<<1, 32, 0, st>>>(S.scale);
+    ::ewos::note_launch(), pq_absmax_kernel<<<4 * 148, 256, 0, st>>>(P, pcached ? 0 : (int64_t)E * n * m, Mc, n, E, S.scale);
+    ::ewos::note_launch(), pq_scale_kernel<<<1, 32, 0, st>>>(S.scale, pcached ? 1 : 0, pkey != 0 ? 1 : 0);
+    if (pkey != 0) S.pkey = pkey;
     const dim3 grid((unsigned)((m + 31) / 32), (unsigned)((n + 31) / 32)), tb(32, 8);
     ::ewos::note_launch();
     if (E == 3) pq_split16_kernel<3><<<grid, tb, 0, st>>>(P, Mc, n, m, at, atl, bt, btl, Kp, S.scale);
@@ -1184,11 +1201,11 @@ static ewos_status tc_assemble_pq16(tc::Scratch& S, const float* P, const double
 }
 
 ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D, float* C, cudaStream_t st,
-                           TcScratch** owned, bool sym = false, bool f16 = true) {
+                           TcScratch** owned, bool sym = false, bool f16 = true, uint64_t pkey = 0) {
     using namespace tc;
     if (!*owned) *owned = new TcScratch();
     Scratch& S = (*owned)->s;
-    if (f16) return tc_assemble_pq16(S, P, Mc, n, m, D, C, st, sym);
+    if (f16) return tc_assemble_pq16(S, P, Mc, n, m, D, C, st, sym, pkey);
     const int E = D + 1, K = E * n;
     const int Kp = (K + BK - 1) / BK * BK;
     const size_t need = (size_t)m * Kp;
@@ -1354,12 +1371,12 @@ ewos_status tc_update_check(TcScratch* t, cudaStream_t st) {
 // C [M][N] = A^T B for K-major FP32 operands A [K][M], B [K][N].  With a caller scratch the
 // call is reentrant across workspaces; without one the per-device scratch is used under a lock.
 ewos_status tc_assemble(const float* Akm, const float* Bkm, float* C, int M, int N, int K, cudaStream_t st,
-                        bool split, TcScratch** owned, bool sym = false, bool f16 = false) {
+                        bool split, TcScratch** owned, bool sym = false, bool f16 = false, uint64_t akey = 0) {
     int dev = 0;
     EWOS_CUDA_TRY(cudaGetDevice(&dev));
     if (owned) {
         if (!*owned) *owned = new TcScratch();
-        ewos_status s = f16 ? tc_enqueue16((*owned)->s, Akm, Bkm, C, M, N, K, st, sym)
+        ewos_status s = f16 ? tc_enqueue16((*owned)->s, Akm, Bkm, C, M, N, K, st, sym, akey)
                             : tc_enqueue((*owned)->s, Akm, Bkm, C, M, N, K, st, split, sym);
         if (s != EWOS_OK) return s;
         return tc_check((*owned)->s, st);
