@@ -819,11 +819,14 @@ __global__ void absmax2_kernel(const float* __restrict__ A, int64_t na, const fl
 }
 
 // powers of two s_A, s_B with max |A| s_A and max |B| s_B in [2^13, 2^14), and 1 / (s_A s_B);
-// max |A| from scale[0], or from the kept scale[6] (cached), and kept there (keep)
-__global__ void ab_scale_kernel(float* scale, int cached, int keep) {
+// max |A| from scale[0], or from the kept scale[6] (cached), and kept there (keep).  With bprod,
+// B = diag(d) A and scale[1] holds max |d|: max |B| is bounded by max |A| max |d| (a bound keeps
+// every scaled value below 2^14)
+__global__ void ab_scale_kernel(float* scale, int cached, int keep, int bprod = 0) {
     if (threadIdx.x != 0) return;
     if (cached) scale[0] = scale[6];
     else if (keep) scale[6] = scale[0];
+    if (bprod) scale[1] = scale[0] * scale[1] * 1.0001f;
     auto pw = [](float mxv) {
         if (!(mxv > 0.f) || !isfinite(mxv)) return 1.0f;
         int e;
@@ -839,6 +842,37 @@ __global__ void ab_scale_kernel(float* scale, int cached, int keep) {
 __device__ __forceinline__ void f16_split_tc(float v, __half& h, __half& l) {
     h = __float2half_rn(v);
     l = __float2half_rn(v - __half2float(h));
+}
+
+// hi/lo [C][Kp] halves of both s_A in^T and s_B (diag(d) in)^T for in [K][C] FP32 (row-major),
+// d [K]: the operands of G^T diag(d) G from one read of G (the product d_k g in FP32, as a
+// scaled copy of G would hold it); zero padding k in [K, Kp)
+__global__ void transpose_split16_ab_kernel(const float* __restrict__ in, const float* __restrict__ d, int K, int Ccols,
+                                            __half* __restrict__ ahi, __half* __restrict__ alo, __half* __restrict__ bhi,
+                                            __half* __restrict__ blo, int Kp, const float* __restrict__ scale) {
+    __shared__ float tile[32][33];
+    __shared__ float dk[32];
+    const float sa = scale[2], sb = scale[3];
+    const int c0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int k = k0 + r, c = c0 + threadIdx.x;
+        tile[r][threadIdx.x] = (k < K && c < Ccols) ? in[(int64_t)k * Ccols + c] : 0.f;
+    }
+    if (threadIdx.y == 0) dk[threadIdx.x] = k0 + (int)threadIdx.x < K ? d[k0 + threadIdx.x] : 0.f;
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int c = c0 + r, k = k0 + threadIdx.x;
+        if (c < Ccols && k < Kp) {
+            const float v = tile[threadIdx.x][r];
+            __half h, l;
+            f16_split_tc(v * sa, h, l);
+            ahi[(int64_t)c * Kp + k] = h;
+            alo[(int64_t)c * Kp + k] = l;
+            f16_split_tc((dk[threadIdx.x] * v) * sb, h, l);
+            bhi[(int64_t)c * Kp + k] = h;
+            blo[(int64_t)c * Kp + k] = l;
+        }
+    }
 }
 
 // hi/lo [C][Kp] halves of s * in^T for in [K][C] FP32 (row-major), zero padding k in [K, Kp);
@@ -921,8 +955,9 @@ static ewos_status tc_enqueue(tc::Scratch& S, const float* Akm, const float* Bkm
 // and split into FP16 halves, three kind::f16 products, unscaled in the epilogue): twice the TF32
 // rate; as accurate as the TF32 split while max |A| and max |B| do not exceed the other entries
 // by more than about 2^17 (below that an entry keeps an absolute error of 2^-39 of the largest).
+// dscale: B = diag(dscale) A (K values; Bkm unused, N = M): both operands from one pass over A
 static ewos_status tc_enqueue16(tc::Scratch& S, const float* Akm, const float* Bkm, float* C, int M, int N, int K,
-                                cudaStream_t st, bool sym, uint64_t akey = 0) {
+                                cudaStream_t st, bool sym, uint64_t akey = 0, const float* dscale = nullptr) {
     using namespace tc;
     using CF = Cfg<true, 0, true>;
     const int Kp = (K + 2 * BK - 1) / (2 * BK) * (2 * BK);
@@ -946,15 +981,21 @@ static ewos_status tc_enqueue16(tc::Scratch& S, const float* Akm, const float* B
     // max |A| is kept between calls for the same operand (akey: the toolbox's serial)
     const bool acached = akey != 0 && S.akey == akey;
     EWOS_CUDA_TRY(cudaMemsetAsync(S.scale, 0, sizeof(float) * 5, st));
-    ::ewos::note_launch(), absmax2_kernel<<<4 * 148, 256, 0, st>>>(Akm, acached ? 0 : (int64_t)K * M, Bkm, (int64_t)K * N,
+    ::ewos::note_launch(), absmax2_kernel<<<4 * 148, 256, 0, st>>>(Akm, acached ? 0 : (int64_t)K * M,
+                                                                  dscale ? dscale : Bkm, dscale ? (int64_t)K : (int64_t)K * N,
                                                                   S.scale);
-    ::ewos::note_launch(), ab_scale_kernel<<<1, 32, 0, st>>>(S.scale, acached ? 1 : 0, akey != 0 ? 1 : 0);
+    ::ewos::note_launch(), ab_scale_kernel<<<1, 32, 0, st>>>(S.scale, acached ? 1 : 0, akey != 0 ? 1 : 0, dscale ? 1 : 0);
     if (akey != 0) S.akey = akey;
     const dim3 tb(32, 8);
-    ::ewos::note_launch(), transpose_split16_kernel<<<dim3((M + 31) / 32, (Kp + 31) / 32), tb, 0, st>>>(Akm, K, M, at, atl, Kp,
-                                                                                                     S.scale, 2);
-    ::ewos::note_launch(), transpose_split16_kernel<<<dim3((N + 31) / 32, (Kp + 31) / 32), tb, 0, st>>>(Bkm, K, N, bt, btl, Kp,
-                                                                                                     S.scale, 3);
+    if (dscale) {
+        ::ewos::note_launch(), transpose_split16_ab_kernel<<<dim3((M + 31) / 32, (Kp + 31) / 32), tb, 0, st>>>(
+                                   Akm, dscale, K, M, at, atl, bt, btl, Kp, S.scale);
+    } else {
+        ::ewos::note_launch(), transpose_split16_kernel<<<dim3((M + 31) / 32, (Kp + 31) / 32), tb, 0, st>>>(Akm, K, M, at, atl,
+                                                                                                         Kp, S.scale, 2);
+        ::ewos::note_launch(), transpose_split16_kernel<<<dim3((N + 31) / 32, (Kp + 31) / 32), tb, 0, st>>>(Bkm, K, N, bt, btl,
+                                                                                                         Kp, S.scale, 3);
+    }
     EWOS_CUDA_TRY(cudaGetLastError());
     CUtensorMap ma, mb, mal, mbl;
     if (!(make_map16(&ma, at, M, Kp, BM) && make_map16(&mb, bt, N, Kp, CF::BN) && make_map16(&mal, atl, M, Kp, BM) &&
@@ -1371,19 +1412,25 @@ ewos_status tc_update_check(TcScratch* t, cudaStream_t st) {
 // C [M][N] = A^T B for K-major FP32 operands A [K][M], B [K][N].  With a caller scratch the
 // call is reentrant across workspaces; without one the per-device scratch is used under a lock.
 ewos_status tc_assemble(const float* Akm, const float* Bkm, float* C, int M, int N, int K, cudaStream_t st,
-                        bool split, TcScratch** owned, bool sym = false, bool f16 = false, uint64_t akey = 0) {
+                        bool split, TcScratch** owned, bool sym = false, bool f16 = false, uint64_t akey = 0,
+                        const float* dscale = nullptr) {
+    if (dscale && (!f16 || M != N)) {
+        set_error("tensor-core product: the row-scaled form needs the FP16 split and a square result");
+        return EWOS_EINVAL;
+    }
     int dev = 0;
     EWOS_CUDA_TRY(cudaGetDevice(&dev));
     if (owned) {
         if (!*owned) *owned = new TcScratch();
-        ewos_status s = f16 ? tc_enqueue16((*owned)->s, Akm, Bkm, C, M, N, K, st, sym, akey)
+        ewos_status s = f16 ? tc_enqueue16((*owned)->s, Akm, Bkm, C, M, N, K, st, sym, akey, dscale)
                             : tc_enqueue((*owned)->s, Akm, Bkm, C, M, N, K, st, split, sym);
         if (s != EWOS_OK) return s;
         return tc_check((*owned)->s, st);
     }
     std::lock_guard<std::mutex> lock(tc::g_mu);
     tc::Scratch& S = tc::g_scratch[dev & 63];
-    ewos_status s = f16 ? tc_enqueue16(S, Akm, Bkm, C, M, N, K, st, sym) : tc_enqueue(S, Akm, Bkm, C, M, N, K, st, split, sym);
+    ewos_status s = f16 ? tc_enqueue16(S, Akm, Bkm, C, M, N, K, st, sym, akey, dscale)
+                        : tc_enqueue(S, Akm, Bkm, C, M, N, K, st, split, sym);
     if (s != EWOS_OK) return s;
     return tc_check(S, st);
 }

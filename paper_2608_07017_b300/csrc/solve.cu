@@ -72,7 +72,8 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* b) {
 struct TcScratch;   // mixed.cu: operand transposes of one caller
 void tc_scratch_free(TcScratch* t);
 ewos_status tc_assemble(const float* A_km, const float* B_km, float* C, int M, int N, int K, cudaStream_t st,
-                        bool split, TcScratch** owned, bool sym = false, bool f16 = false, uint64_t akey = 0);
+                        bool split, TcScratch** owned, bool sym = false, bool f16 = false, uint64_t akey = 0,
+                        const float* dscale = nullptr);
 ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int M,
                               int N, int K, cudaStream_t st, TcScratch** owned, bool presplit = false, int a_off = 0,
                               int b_off = 0);
@@ -2401,6 +2402,16 @@ __global__ void add_shifted_kernel(float* __restrict__ LU, const float* __restri
     }
 }
 
+// d_i = lam_i N'(u_i) in FP64, stored in FP32 (the factor jac_scale32_kernel applies to row i of G)
+__global__ void jac_diag_kernel(const double* __restrict__ u, const double* __restrict__ lam, const double* __restrict__ nl,
+                                int nnl, float* __restrict__ d, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double dd = 0.0, pw = 1.0;
+    for (int t = 1; t < nnl; ++t) { dd += t * nl[t] * pw; pw *= u[i]; }
+    d[i] = (float)(lam[i] * dd);
+}
+
 template <typename TP>
 __global__ void jac_scale32_kernel(const TP* __restrict__ Gm, const double* __restrict__ u, const double* __restrict__ lam,
                                    const double* __restrict__ nl, int nnl, float* __restrict__ out, int n, int m,
@@ -3679,14 +3690,21 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                     }
                     have_factors = true;
                     const TP* Gm = (const TP*)tb->P + (size_t)C.D * C.n * C.m;
-                    ::ewos::note_launch(), jac_scale32_kernel<TP><<<(unsigned)C.n, 256, 0, C.st>>>(Gm, ws->u2, tb->lambda, nl, pb->nl_ncoef,
-                                                                                      ws->Jx32, (int)C.n, (int)C.m,
-                                                                                      (int)(C.m % 4 == 0 && aligned16(Gm) && aligned16(ws->Jx32)));
                     const float* Gm32 = P32 + (size_t)C.D * C.n * C.m;
-                    auto t1 = std::chrono::steady_clock::now();
                     // Jacobian Lambda + alpha I + G^T diag(lam N'(u)) G: the product on the tensor
-                    // cores (three products of FP16 halves, or of TF32 parts) when available
+                    // cores (three products of FP16 halves, or of TF32 parts) when available.  The
+                    // FP16 form takes d = lam N'(u) as a vector and splits G and diag(d) G in one pass
+                    // over G; the others scale a copy of G first
                     const bool tcj = tc_assemble_available();
+                    const bool jrow = tcj && pb->assembly != 1;
+                    if (jrow)
+                        ::ewos::note_launch(), jac_diag_kernel<<<(unsigned)((C.n + 255) / 256), 256, 0, C.st>>>(
+                                                   ws->u2, tb->lambda, nl, pb->nl_ncoef, ws->Jx32, (int)C.n);
+                    else
+                        ::ewos::note_launch(), jac_scale32_kernel<TP><<<(unsigned)C.n, 256, 0, C.st>>>(
+                                                   Gm, ws->u2, tb->lambda, nl, pb->nl_ncoef, ws->Jx32, (int)C.n, (int)C.m,
+                                                   (int)(C.m % 4 == 0 && aligned16(Gm) && aligned16(ws->Jx32)));
+                    auto t1 = std::chrono::steady_clock::now();
                     ewos_status tst = EWOS_OK;
                     ewos_status st = factor32_with(
                         C,
@@ -3694,8 +3712,10 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                             if (tcj) {
                                 DevSpan span(C.st, &rep->dev_ms_gemm);
                                 rep->gemm_flop += (double)C.m * (double)(C.m + 1) * (double)C.n;   // symmetric: lower triangle
-                                ewos_status e = tc_assemble(Gm32, ws->Jx32, ws->LU32, (int)C.m, (int)C.m, (int)C.n, C.st,
-                                                            kSplitTF32, &ws->tc, true, pb->assembly != 1, tb->serial);
+                                ewos_status e = jrow ? tc_assemble(Gm32, nullptr, ws->LU32, (int)C.m, (int)C.m, (int)C.n, C.st,
+                                                                   kSplitTF32, &ws->tc, true, true, tb->serial, ws->Jx32)
+                                                     : tc_assemble(Gm32, ws->Jx32, ws->LU32, (int)C.m, (int)C.m, (int)C.n, C.st,
+                                                                   kSplitTF32, &ws->tc, true, false, tb->serial);
                                 if (e != EWOS_OK) tst = e;
                                 const int64_t cnt = C.m * C.m;
                                 ::ewos::note_launch(), add_shifted_kernel<<<(int)std::min<int64_t>(65535, (cnt + 255) / 256), 256, 0, C.st>>>(
