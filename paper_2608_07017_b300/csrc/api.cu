@@ -64,6 +64,7 @@ static void release(ewos_toolbox* tb) {
     if (!tb) return;
     AllocStream as(tb->stream);
     ::ewos::dev_free(tb->P); ::ewos::dev_free(tb->KH); ::ewos::dev_free(tb->Hc); ::ewos::dev_free(tb->lambda);
+    ::ewos::dev_free(tb->pmax);
     ::ewos::dev_free(tb->x); ::ewos::dev_free(tb->z); ::ewos::dev_free(tb->y);
     ::ewos::dev_free(tb->rec_exit); ::ewos::dev_free(tb->rec_steps); ::ewos::dev_free(tb->rec_mass); ::ewos::dev_free(tb->rec_vhash);
     ::ewos::dev_free(tb->rec_xexit);
@@ -76,7 +77,10 @@ static ewos_status alloc_matrices(ewos_toolbox* tb, bool counts) {
     const int64_t d1 = tb->dim + 1;
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->P, e * d1 * tb->n * tb->m));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->KH, e * d1 * tb->n * tb->p));
-    if (counts) EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->Hc, sizeof(uint32_t) * tb->n * tb->p));
+    if (counts) {
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->Hc, sizeof(uint32_t) * tb->n * tb->p));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->pmax, 2 * sizeof(float)));
+    }
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->lambda, sizeof(double) * tb->n));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->x, sizeof(double) * tb->n * tb->dim));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&tb->z, sizeof(double) * tb->p * tb->dim));

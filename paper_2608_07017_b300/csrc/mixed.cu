@@ -957,7 +957,8 @@ static ewos_status tc_enqueue(tc::Scratch& S, const float* Akm, const float* Bkm
 // by more than about 2^17 (below that an entry keeps an absolute error of 2^-39 of the largest).
 // dscale: B = diag(dscale) A (K values; Bkm unused, N = M): both operands from one pass over A
 static ewos_status tc_enqueue16(tc::Scratch& S, const float* Akm, const float* Bkm, float* C, int M, int N, int K,
-                                cudaStream_t st, bool sym, uint64_t akey = 0, const float* dscale = nullptr) {
+                                cudaStream_t st, bool sym, uint64_t akey = 0, const float* dscale = nullptr,
+                                const float* amax = nullptr) {
     using namespace tc;
     using CF = Cfg<true, 0, true>;
     const int Kp = (K + 2 * BK - 1) / (2 * BK) * (2 * BK);
@@ -978,8 +979,13 @@ static ewos_status tc_enqueue16(tc::Scratch& S, const float* Akm, const float* B
     __half* atl = reinterpret_cast<__half*>(S.Atl);
     __half* bt = reinterpret_cast<__half*>(S.Bt);
     __half* btl = reinterpret_cast<__half*>(S.Btl);
-    // max |A| is kept between calls for the same operand (akey: the toolbox's serial)
-    const bool acached = akey != 0 && S.akey == akey;
+    // max |A| is kept between calls for the same operand (akey: the toolbox's serial), or given
+    // (amax, on the device)
+    if (amax) {
+        EWOS_CUDA_TRY(cudaMemcpyAsync(S.scale + 6, amax, sizeof(float), cudaMemcpyDeviceToDevice, st));
+        S.akey = akey;
+    }
+    const bool acached = amax != nullptr || (akey != 0 && S.akey == akey);
     EWOS_CUDA_TRY(cudaMemsetAsync(S.scale, 0, sizeof(float) * 5, st));
     ::ewos::note_launch(), absmax2_kernel<<<4 * 148, 256, 0, st>>>(Akm, acached ? 0 : (int64_t)K * M,
                                                                   dscale ? dscale : Bkm, dscale ? (int64_t)K : (int64_t)K * N,
@@ -1181,7 +1187,7 @@ __global__ void pq_split16_kernel(const float* __restrict__ P, const double* __r
 // three-product TF32 GEMM; waits for the launch (pipeline timeouts are reported)
 // The FP16 form of tc_assemble_pq (same operands in FP16 halves, twice the tensor-core rate)
 static ewos_status tc_assemble_pq16(tc::Scratch& S, const float* P, const double* Mc, int n, int m, int D, float* C,
-                                    cudaStream_t st, bool sym, uint64_t pkey = 0) {
+                                    cudaStream_t st, bool sym, uint64_t pkey = 0, const float* pmax = nullptr) {
     using namespace tc;
     const int E = D + 1, K = E * n;
     const int Kp = (K + 2 * BK - 1) / (2 * BK) * (2 * BK);          // halves, 128-byte rows
@@ -1206,8 +1212,13 @@ static ewos_status tc_assemble_pq16(tc::Scratch& S, const float* P, const double
         for (__half* b : {at, atl, bt, btl})
             EWOS_CUDA_TRY(cudaMemset2DAsync(b + K, sizeof(__half) * Kp, 0, sizeof(__half) * (Kp - K), m, st));
     }
-    // max |P| is kept between calls for the same toolbox (pkey: its serial)
-    const bool pcached = pkey != 0 && S.pkey == pkey;
+    // max |P| is kept between calls for the same toolbox (pkey: its serial), or given by the build
+    // that wrote P (pmax, on the device)
+    if (pmax) {
+        EWOS_CUDA_TRY(cudaMemcpyAsync(S.scale + 5, pmax, sizeof(float), cudaMemcpyDeviceToDevice, st));
+        S.pkey = pkey;
+    }
+    const bool pcached = pmax != nullptr || (pkey != 0 && S.pkey == pkey);
     EWOS_CUDA_TRY(cudaMemsetAsync(S.scale, 0, sizeof(float) * 5, st));
     if (E != 3 && E != 4) {
         set_error("tensor-core assembly: dimension must be 2 or 3");
@@ -1242,11 +1253,12 @@ static ewos_status tc_assemble_pq16(tc::Scratch& S, const float* P, const double
 }
 
 ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D, float* C, cudaStream_t st,
-                           TcScratch** owned, bool sym = false, bool f16 = true, uint64_t pkey = 0) {
+                           TcScratch** owned, bool sym = false, bool f16 = true, uint64_t pkey = 0,
+                           const float* pmax = nullptr) {
     using namespace tc;
     if (!*owned) *owned = new TcScratch();
     Scratch& S = (*owned)->s;
-    if (f16) return tc_assemble_pq16(S, P, Mc, n, m, D, C, st, sym, pkey);
+    if (f16) return tc_assemble_pq16(S, P, Mc, n, m, D, C, st, sym, pkey, pmax);
     const int E = D + 1, K = E * n;
     const int Kp = (K + BK - 1) / BK * BK;
     const size_t need = (size_t)m * Kp;
@@ -1413,7 +1425,7 @@ ewos_status tc_update_check(TcScratch* t, cudaStream_t st) {
 // call is reentrant across workspaces; without one the per-device scratch is used under a lock.
 ewos_status tc_assemble(const float* Akm, const float* Bkm, float* C, int M, int N, int K, cudaStream_t st,
                         bool split, TcScratch** owned, bool sym = false, bool f16 = false, uint64_t akey = 0,
-                        const float* dscale = nullptr) {
+                        const float* dscale = nullptr, const float* amax = nullptr) {
     if (dscale && (!f16 || M != N)) {
         set_error("tensor-core product: the row-scaled form needs the FP16 split and a square result");
         return EWOS_EINVAL;
@@ -1422,14 +1434,14 @@ ewos_status tc_assemble(const float* Akm, const float* Bkm, float* C, int M, int
     EWOS_CUDA_TRY(cudaGetDevice(&dev));
     if (owned) {
         if (!*owned) *owned = new TcScratch();
-        ewos_status s = f16 ? tc_enqueue16((*owned)->s, Akm, Bkm, C, M, N, K, st, sym, akey, dscale)
+        ewos_status s = f16 ? tc_enqueue16((*owned)->s, Akm, Bkm, C, M, N, K, st, sym, akey, dscale, amax)
                             : tc_enqueue((*owned)->s, Akm, Bkm, C, M, N, K, st, split, sym);
         if (s != EWOS_OK) return s;
         return tc_check((*owned)->s, st);
     }
     std::lock_guard<std::mutex> lock(tc::g_mu);
     tc::Scratch& S = tc::g_scratch[dev & 63];
-    ewos_status s = f16 ? tc_enqueue16(S, Akm, Bkm, C, M, N, K, st, sym, akey, dscale)
+    ewos_status s = f16 ? tc_enqueue16(S, Akm, Bkm, C, M, N, K, st, sym, akey, dscale, amax)
                         : tc_enqueue(S, Akm, Bkm, C, M, N, K, st, split, sym);
     if (s != EWOS_OK) return s;
     return tc_check(S, st);

@@ -73,13 +73,14 @@ struct TcScratch;   // mixed.cu: operand transposes of one caller
 void tc_scratch_free(TcScratch* t);
 ewos_status tc_assemble(const float* A_km, const float* B_km, float* C, int M, int N, int K, cudaStream_t st,
                         bool split, TcScratch** owned, bool sym = false, bool f16 = false, uint64_t akey = 0,
-                        const float* dscale = nullptr);
+                        const float* dscale = nullptr, const float* amax = nullptr);
 ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int M,
                               int N, int K, cudaStream_t st, TcScratch** owned, bool presplit = false, int a_off = 0,
                               int b_off = 0);
 ewos_status tc_update_reserve(int max_mn, int k, cudaStream_t st, TcScratch** owned);
 ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D, float* C, cudaStream_t st,
-                           TcScratch** owned, bool sym = false, bool f16 = true, uint64_t pkey = 0);
+                           TcScratch** owned, bool sym = false, bool f16 = true, uint64_t pkey = 0,
+                           const float* pmax = nullptr);
 void tc_update_operands(TcScratch* t, float** a_hi, float** a_lo, float** b_hi, float** b_lo);
 ewos_status tc_update_check(TcScratch* t, cudaStream_t st);
 bool tc_assemble_available();
@@ -3585,7 +3586,8 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                 rep->gemm_flop += (pb->b == nullptr ? (double)C.m * (double)(C.m + 1) : 2.0 * (double)C.m * (double)C.m) *
                                   (double)(C.E * C.n);
                 ewos_status st = tc_assemble_pq(P32, ws->M, (int)C.n, (int)C.m, C.D, ws->L32, C.st, &ws->tc,
-                                                    pb->b == nullptr, pb->assembly != 1, tb->serial);
+                                                    pb->b == nullptr, pb->assembly != 1, tb->serial,
+                                                    tb->pmax_valid ? tb->pmax : nullptr);
                 if (st != EWOS_OK) return st;
             } else {
                 assemble_mixed<TP>(C, P32);
@@ -3713,7 +3715,8 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                                 DevSpan span(C.st, &rep->dev_ms_gemm);
                                 rep->gemm_flop += (double)C.m * (double)(C.m + 1) * (double)C.n;   // symmetric: lower triangle
                                 ewos_status e = jrow ? tc_assemble(Gm32, nullptr, ws->LU32, (int)C.m, (int)C.m, (int)C.n, C.st,
-                                                                   kSplitTF32, &ws->tc, true, true, tb->serial, ws->Jx32)
+                                                                   kSplitTF32, &ws->tc, true, true, tb->serial, ws->Jx32,
+                                                                   tb->pmax_valid ? tb->pmax + 1 : nullptr)
                                                      : tc_assemble(Gm32, ws->Jx32, ws->LU32, (int)C.m, (int)C.m, (int)C.n, C.st,
                                                                    kSplitTF32, &ws->tc, true, false, tb->serial);
                                 if (e != EWOS_OK) tst = e;
@@ -3766,7 +3769,8 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                 rep->gemm_flop += (pb->b == nullptr ? (double)C.m * (double)(C.m + 1) : 2.0 * (double)C.m * (double)C.m) *
                                   (double)(C.E * C.n);
                     ewos_status st = tc_assemble_pq(P32, ws->M, (int)C.n, (int)C.m, C.D, ws->L32, C.st, &ws->tc,
-                                                    pb->b == nullptr, pb->assembly != 1, tb->serial);
+                                                    pb->b == nullptr, pb->assembly != 1, tb->serial,
+                                                    tb->pmax_valid ? tb->pmax : nullptr);
                     if (st != EWOS_OK) return st;
                 } else {
                     assemble_mixed<TP>(C, P32);

@@ -51,6 +51,11 @@ struct ewos_toolbox {
     void* P = nullptr;
     void* KH = nullptr;
     uint32_t* Hc = nullptr;          // [n][p] exit counts (empty for toolboxes made from matrices)
+    // max |P| and max |G| (FP32, device [2]) as the build wrote P: the scales of the FP16 assembly and
+    // Jacobian products without a pass over P; valid after a build (not for toolboxes made from
+    // matrices or read from files)
+    float* pmax = nullptr;
+    bool pmax_valid = false;
     double* lambda = nullptr;        // [n]
     double* x = nullptr;             // [n][d]
     double* z = nullptr;             // [p][d]

@@ -734,6 +734,7 @@ struct WalkArgs {
     T* P;              // [(D+1)][n][m]
     T* KH;             // [(D+1)][n][p]
     uint32_t* Hc;      // [n][p]
+    float* pmax;       // [2] max |P| and max |G| of the rows written (FP32 bits, atomic max; may be NULL)
     int* row_counter;
     unsigned long long* stat_steps;
     unsigned long long* stat_capped;
@@ -1132,6 +1133,7 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
         const T sGG = invN / (T(2) * r0);
         const T sKH = T(D) * invN / r0;
         const size_t nm = (size_t)a.n * a.m, np = (size_t)a.n * a.p;
+        float my_pmax = 0.f, my_gmax = 0.f;   // largest |value| of P (of G) this thread writes in the row
         for (int t = threadIdx.x; t < a.m; t += blockDim.x) {
             if constexpr (L2ACC) {
                 // the reductions of the row are complete at the barrier above; read past L1
@@ -1145,17 +1147,37 @@ __device__ __forceinline__ int walk_rows(const WalkArgs<T, D>& a, int g_first, i
                     for (int c = 0; c < 4; ++c) { v[c] = __ldcg(acc + (size_t)t * 4 + c); acc[(size_t)t * 4 + c] = T(0); }
                 }
 #pragma unroll
-                for (int c = 0; c < D; ++c) __stcs(a.P + c * nm + (size_t)row * a.m + t, v[1 + c] * sGG);
-                __stcs(a.P + D * nm + (size_t)row * a.m + t, v[0] * sG);
+                for (int c = 0; c < D; ++c) {
+                    const T o = v[1 + c] * sGG;
+                    __stcs(a.P + c * nm + (size_t)row * a.m + t, o);
+                    my_pmax = fmaxf(my_pmax, fabsf((float)o));
+                }
+                const T og = v[0] * sG;
+                __stcs(a.P + D * nm + (size_t)row * a.m + t, og);
+                my_gmax = fmaxf(my_gmax, fabsf((float)og));
             } else {
 #pragma unroll
                 for (int c = 0; c < D; ++c) {
-                    __stcs(a.P + c * nm + (size_t)row * a.m + t, acc[(size_t)c * a.m + t] * sGG);
+                    const T o = acc[(size_t)c * a.m + t] * sGG;
+                    __stcs(a.P + c * nm + (size_t)row * a.m + t, o);
+                    my_pmax = fmaxf(my_pmax, fabsf((float)o));
                     acc[(size_t)c * a.m + t] = T(0);
                 }
-                __stcs(a.P + D * nm + (size_t)row * a.m + t, acc[(size_t)D * a.m + t] * sG);
+                const T og = acc[(size_t)D * a.m + t] * sG;
+                __stcs(a.P + D * nm + (size_t)row * a.m + t, og);
+                my_gmax = fmaxf(my_gmax, fabsf((float)og));
                 acc[(size_t)D * a.m + t] = T(0);
             }
+        }
+        if (a.pmax) {                         // (non-negative floats compare as their bits)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                my_pmax = fmaxf(my_pmax, __shfl_xor_sync(0xffffffffu, my_pmax, o));
+                my_gmax = fmaxf(my_gmax, __shfl_xor_sync(0xffffffffu, my_gmax, o));
+            }
+            my_pmax = fmaxf(my_pmax, my_gmax);
+            if (lane == 0 && my_pmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(a.pmax), __float_as_uint(my_pmax));
+            if (lane == 0 && my_gmax > 0.f) atomicMax(reinterpret_cast<unsigned int*>(a.pmax + 1), __float_as_uint(my_gmax));
         }
         for (int t = threadIdx.x; t < a.p; t += blockDim.x) {
 #pragma unroll
@@ -1607,6 +1629,9 @@ static ewos_status prepare_walks(ewos_toolbox* tb, const ewos_domain* dom, const
     }
     a.Z = lookup_view<T, D>(ctx.Z);
     a.P = (T*)tb->P; a.KH = (T*)tb->KH; a.Hc = tb->Hc;
+    a.pmax = tb->pmax;
+    tb->pmax_valid = false;
+    if (tb->pmax) EWOS_CUDA_TRY(cudaMemsetAsync(tb->pmax, 0, 2 * sizeof(float), st));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_counter, sizeof(int)));
     EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&ctx.d_stats, 3 * sizeof(unsigned long long)));
     EWOS_CUDA_TRY(cudaMemsetAsync(ctx.d_counter, 0, sizeof(int), st));
@@ -1809,6 +1834,7 @@ static ewos_status build_typed(ewos_toolbox* tb, const ewos_domain* dom, const d
         set_error("walk kernel: " + std::to_string(stats[2]) + " out-of-range indexes found and skipped");
         return EWOS_ECUDA;
     }
+    tb->pmax_valid = tb->pmax != nullptr;     // every row written: the kernel's max |P| is complete
     float ms[4];
     cudaEventElapsedTime(&ms[0], ev[0], ev[4]);
     cudaEventElapsedTime(&ms[1], ev[0], ev[1]);
@@ -1993,6 +2019,7 @@ static ewos_status build_batch_kind(std::vector<ewos_toolbox*>& tbs, const std::
             set_error("batch walk kernel: " + std::to_string(stats[3 * k + 2]) + " out-of-range indexes found and skipped");
             return EWOS_ECUDA;
         }
+    for (int k = 0; k < nb; ++k) tbs[k]->pmax_valid = tbs[k]->pmax != nullptr;
     float ms_all = 0, ms_walk = 0;
     cudaEventElapsedTime(&ms_all, ev[0], ev[2]);
     cudaEventElapsedTime(&ms_walk, ev[1], ev[2]);
