@@ -2403,6 +2403,23 @@ __global__ void add_shifted_kernel(float* __restrict__ LU, const float* __restri
     }
 }
 
+// the same in 16-byte pieces (m a multiple of 4, both matrices 16-byte aligned): row i's diagonal
+// element sits in piece (i m + i) / 4
+__global__ void add_shifted4_kernel(float4* __restrict__ LU, const float4* __restrict__ L, int64_t count4, int m,
+                                    float alpha) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count4; t += (int64_t)gridDim.x * blockDim.x) {
+        float4 v = __ldcs(LU + t);
+        const float4 l = __ldcs(L + t);
+        v.x += l.x; v.y += l.y; v.z += l.z; v.w += l.w;
+        const int64_t e = 4 * t, row = e / m, col = e - row * m;
+        if (row >= col && row < col + 4) {
+            const int k = (int)(row - col);
+            if (k == 0) v.x += alpha; else if (k == 1) v.y += alpha; else if (k == 2) v.z += alpha; else v.w += alpha;
+        }
+        __stcs(LU + t, v);
+    }
+}
+
 // d_i = lam_i N'(u_i) in FP64, stored in FP32 (the factor jac_scale32_kernel applies to row i of G)
 __global__ void jac_diag_kernel(const double* __restrict__ u, const double* __restrict__ lam, const double* __restrict__ nl,
                                 int nnl, float* __restrict__ d, int n) {
@@ -3721,8 +3738,13 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                                                                    kSplitTF32, &ws->tc, true, false, tb->serial);
                                 if (e != EWOS_OK) tst = e;
                                 const int64_t cnt = C.m * C.m;
-                                ::ewos::note_launch(), add_shifted_kernel<<<(int)std::min<int64_t>(65535, (cnt + 255) / 256), 256, 0, C.st>>>(
-                                    ws->LU32, ws->L32, cnt, (int)C.m, alpha);
+                                if (C.m % 4 == 0 && aligned16(ws->LU32) && aligned16(ws->L32))
+                                    ::ewos::note_launch(), add_shifted4_kernel<<<4 * 148 * 8, 256, 0, C.st>>>(
+                                        reinterpret_cast<float4*>(ws->LU32), reinterpret_cast<const float4*>(ws->L32), cnt / 4,
+                                        (int)C.m, (float)alpha);
+                                else
+                                    ::ewos::note_launch(), add_shifted_kernel<<<(int)std::min<int64_t>(65535, (cnt + 255) / 256), 256, 0, C.st>>>(
+                                        ws->LU32, ws->L32, cnt, (int)C.m, alpha);
                             } else {
                                 cudaMemcpyAsync(ws->LU32, ws->L32, sizeof(float) * C.m * C.m, cudaMemcpyDeviceToDevice, C.st);
                                 sgemm<true>(C.st, (int)C.m, (int)C.m, (int)C.n, 1.f, Gm32, C.m, ws->Jx32, C.m, 1.f, ws->LU32, C.m);
