@@ -409,6 +409,13 @@ ewos_status ewos_debug_tc_gemm(const float* A, const float* B, float* C, int M, 
  * (three TF32 products); sym != 0 computes the tiles on and below the diagonal and mirrors them
  * (for symmetric M_i).  EWOS_EINVAL when the device has no sm_100-family tensor cores. */
 ewos_status ewos_debug_tc_assemble(const float* P, const double* M, int n, int m, int D, float* C, int sym, int f16);
+/* Test hook (no counterpart in the paper): the trailing update of the FP32 LU of the mixed-precision
+ * solve on the tensor cores, C [M][N] -= A [M][K] B [K][N] for host FP32 row-major arrays (C read
+ * and written in place).  f16 != 0: each row of A and each column of B scaled by a power of two
+ * and split into FP16 halves, three kind::f16 products (the form of the LU's rank-512 updates);
+ * f16 = 0: three TF32 products.  EWOS_EINVAL for M, N or K below 1, and when the device has no
+ * sm_100-family tensor cores. */
+ewos_status ewos_debug_tc_update(const float* A, const float* B, float* C, int M, int N, int K, int f16);
 
 /* Test hooks for the failure paths (no counterpart in the paper).
  * ewos_debug_set_flow_wait_limit: the flag waits of the dataflow triangular solves (mixed mode)

@@ -150,7 +150,9 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
                                                            int Kp, float* __restrict__ C, int64_t ldc,
                                                            int* __restrict__ err, int sub, int tri = 0,
                                                            const int* __restrict__ tiles = nullptr,
-                                                           const float* __restrict__ cscale = nullptr) {
+                                                           const float* __restrict__ cscale = nullptr,
+                                                           const float* __restrict__ rinv = nullptr,
+                                                           const float* __restrict__ cinv = nullptr) {
     using CF = Cfg<SPLIT, ST, F16>;
     constexpr int BN = CF::BN, STAGES = CF::STAGES, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
     constexpr int STAGE_BYTES = CF::STAGE_BYTES;
@@ -306,13 +308,22 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if constexpr (F16) {
-                // the operands were scaled by powers of two: undo it (exact)
-                const float sc = cscale ? *cscale : 1.0f;
-#pragma unroll
-                for (int q = 0; q < 32; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) * sc);
-            }
             const int col0 = n0 + c * 32;
+            if constexpr (F16) {
+                // the operands were scaled by powers of two: undo it (exact).  rinv, cinv: one
+                // scale per row of A and per column of B (1 / s_i, 1 / t_j), else one for all
+                if (rinv) {
+                    const float rs = row < M ? rinv[row] : 0.f;
+                    const float cl = col0 + lane < N ? cinv[col0 + lane] : 0.f;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        v[q] = __float_as_uint(__uint_as_float(v[q]) * rs * __shfl_sync(0xffffffffu, cl, q));
+                } else {
+                    const float sc = cscale ? *cscale : 1.0f;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) * sc);
+                }
+            }
             float4 ccur[8];
             if constexpr (CSM) {
                 const float4* cs4 = reinterpret_cast<const float4*>(Cs + (warp * 32 + lane) * kCsmLd + c * 32);
@@ -713,6 +724,8 @@ struct Scratch {
     float* scale = nullptr;        // FP16 forms: [0], [1] the maxima that set [2] s_A (s_P), [3] s_B (s_Q); [4] 1/(s_A s_B);
                                    // [5] max |P|, [6] max |A| kept for the operand of key pkey, akey
     uint64_t pkey = 0, akey = 0;   // (a toolbox's serial: its P, and the G plane of P, never change)
+    float* rcinv = nullptr;        // the FP16 update: 1 / s_i per row of A, 1 / t_j and max_k |B_kj| per column of B
+    size_t rccap = 0;
     int* tiles = nullptr;          // (tile row, tile column) per CTA, blocked order
     long long tiles_key = -1;      // shape the table was made for
     int tiles_count = 0;
@@ -794,7 +807,7 @@ struct TcScratch {
 void tc_scratch_free(TcScratch* t) {
     if (!t) return;
     ::ewos::dev_free(t->s.At); ::ewos::dev_free(t->s.Bt); ::ewos::dev_free(t->s.Atl); ::ewos::dev_free(t->s.Btl);
-    ::ewos::dev_free(t->s.err); ::ewos::dev_free(t->s.tiles); ::ewos::dev_free(t->s.scale);
+    ::ewos::dev_free(t->s.err); ::ewos::dev_free(t->s.tiles); ::ewos::dev_free(t->s.scale); ::ewos::dev_free(t->s.rcinv);
     delete t;
 }
 
@@ -894,6 +907,92 @@ __global__ void transpose_split16_kernel(const float* __restrict__ in, int K, in
             f16_split_tc(tile[threadIdx.x][r] * sc, h, l);
             hi[(int64_t)c * Kp + k] = h;
             lo[(int64_t)c * Kp + k] = l;
+        }
+    }
+}
+
+// the power of two s with mx s in [2^13, 2^14) (1 for a zero or non-finite mx; at most 2^127)
+__device__ __forceinline__ float pow2_scale(float mx) {
+    if (!(mx > 0.f) || !isfinite(mx)) return 1.0f;
+    int e;
+    frexpf(mx, &e);
+    return ldexpf(1.0f, min(14 - e, 127));
+}
+
+// FP16 halves [M][Kp] of s_i A_i for a row-major A [M][K] (row stride ld), s_i the power of two
+// that puts max_k |A_ik| in [2^13, 2^14); rinv[i] = 1 / s_i; zero padding k in [K, Kp).  One warp
+// per row (the LU's update operand: rows of the L block, K = the update's rank).
+__global__ void rows_split16_kernel(const float* __restrict__ in, int64_t ld, int M, int K, __half* __restrict__ hi,
+                                    __half* __restrict__ lo, int Kp, float* __restrict__ rinv) {
+    ::ewos::pdl_trigger();
+    ::ewos::pdl_wait();
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= M) return;
+    const float* a = in + (int64_t)i * ld;
+    float mx = 0.f;
+    for (int k = lane; k < K; k += 32) mx = fmaxf(mx, fabsf(a[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const float s = pow2_scale(mx);
+    __half2* h2 = reinterpret_cast<__half2*>(hi + (int64_t)i * Kp);
+    __half2* l2 = reinterpret_cast<__half2*>(lo + (int64_t)i * Kp);
+    for (int k = 2 * lane; k < Kp; k += 64) {       // (Kp is even: 4-byte pairs)
+        __half h0, l0, h1, l1;
+        f16_split_tc(k < K ? a[k] * s : 0.f, h0, l0);
+        f16_split_tc(k + 1 < K ? a[k + 1] * s : 0.f, h1, l1);
+        h2[k >> 1] = __halves2half2(h0, h1);
+        l2[k >> 1] = __halves2half2(l0, l1);
+    }
+    if (lane == 0) rinv[i] = 1.0f / s;
+}
+
+// cmax[j] = max_k |B_kj| for a row-major B [K][N] (row stride ld), as the bits of non-negative
+// floats (cmax zeroed first); 32 x 32 tiles, one atomic per column and tile
+__global__ void cols_absmax_kernel(const float* __restrict__ in, int64_t ld, int K, int N, float* __restrict__ cmax) {
+    __shared__ float red[8][32];
+    ::ewos::pdl_trigger();
+    ::ewos::pdl_wait();
+    const int c = blockIdx.x * 32 + threadIdx.x, k0 = blockIdx.y * 32;
+    float mx = 0.f;
+    if (c < N)
+        for (int r = threadIdx.y; r < 32; r += blockDim.y)
+            if (k0 + r < K) mx = fmaxf(mx, fabsf(in[(int64_t)(k0 + r) * ld + c]));
+    red[threadIdx.y][threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < N) {
+        for (int r = 1; r < (int)blockDim.y; ++r) mx = fmaxf(mx, red[r][threadIdx.x]);
+        atomicMax(reinterpret_cast<unsigned int*>(cmax + c), __float_as_uint(mx));
+    }
+}
+
+// FP16 halves [N][Kp] of t_j B_j for the columns of a row-major B [K][N] (row stride ld), t_j the
+// power of two that puts cmax[j] = max_k |B_kj| in [2^13, 2^14); cinv[j] = 1 / t_j; zero padding
+// k in [K, Kp).  32 x 32 tiles transposed through shared memory.
+__global__ void cols_split16_kernel(const float* __restrict__ in, int64_t ld, int K, int N, __half* __restrict__ hi,
+                                    __half* __restrict__ lo, int Kp, const float* __restrict__ cmax,
+                                    float* __restrict__ cinv) {
+    __shared__ float tile[32][33];
+    __shared__ float sc[32];
+    ::ewos::pdl_trigger();
+    ::ewos::pdl_wait();
+    const int c0 = blockIdx.x * 32, k0 = blockIdx.y * 32, c = c0 + threadIdx.x;
+    if (threadIdx.y == 0) {
+        const float t = pow2_scale(c < N ? cmax[c] : 0.f);
+        sc[threadIdx.x] = t;
+        if (blockIdx.y == 0 && c < N) cinv[c] = 1.0f / t;
+    }
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int k = k0 + r;
+        tile[r][threadIdx.x] = (k < K && c < N) ? in[(int64_t)k * ld + c] : 0.f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int cc = c0 + r, k = k0 + threadIdx.x;
+        if (cc < N && k < Kp) {
+            __half h, l;
+            f16_split_tc(tile[threadIdx.x][r] * sc[r], h, l);
+            hi[(int64_t)cc * Kp + k] = h;
+            lo[(int64_t)cc * Kp + k] = l;
         }
     }
 }
@@ -1335,16 +1434,88 @@ void tc_update_operands(TcScratch* t, float** a_hi, float** a_lo, float** b_hi, 
     *a_hi = t->s.At; *a_lo = t->s.Atl; *b_hi = t->s.Bt; *b_lo = t->s.Btl;
 }
 
+// The FP16 form of tc_update_enqueue (operands split here, one scale per row of A and column of B)
+static ewos_status tc_update_enqueue16(tc::Scratch& S, const float* A, int64_t lda, const float* B, int64_t ldb,
+                                       float* C, int64_t ldc, int M, int N, int K, cudaStream_t st) {
+    using namespace tc;
+    using CF = Cfg<true, 0, true>;
+    const int Kp = (K + 2 * BK - 1) / (2 * BK) * (2 * BK);
+    const size_t need_f = ((size_t)std::max(M, N) * Kp + 1) / 2;     // halves, in floats
+    if (S.cap < need_f || !S.Atl) {
+        ::ewos::dev_free(S.At); ::ewos::dev_free(S.Bt); ::ewos::dev_free(S.Atl); ::ewos::dev_free(S.Btl);
+        S.At = S.Bt = S.Atl = S.Btl = nullptr;
+        S.cap = 0;
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.At, sizeof(float) * need_f));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Bt, sizeof(float) * need_f));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Atl, sizeof(float) * need_f));
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.Btl, sizeof(float) * need_f));
+        S.cap = need_f;
+    }
+    if (S.rccap < (size_t)M + 2 * (size_t)N) {
+        ::ewos::dev_free(S.rcinv);
+        S.rcinv = nullptr;
+        S.rccap = 0;
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.rcinv, sizeof(float) * ((size_t)M + 2 * (size_t)N)));
+        S.rccap = (size_t)M + 2 * (size_t)N;
+    }
+    if (!S.err) {
+        EWOS_CUDA_TRY(::ewos::dev_alloc((void**)&S.err, sizeof(int)));
+        EWOS_CUDA_TRY(cudaMemsetAsync(S.err, 0, sizeof(int), st));
+    }
+    __half* at = reinterpret_cast<__half*>(S.At);
+    __half* atl = reinterpret_cast<__half*>(S.Atl);
+    __half* bt = reinterpret_cast<__half*>(S.Bt);
+    __half* btl = reinterpret_cast<__half*>(S.Btl);
+    float* rinv = S.rcinv;
+    float* cinv = S.rcinv + M;
+    float* cmax = S.rcinv + M + N;
+    EWOS_CUDA_TRY(cudaMemsetAsync(cmax, 0, sizeof(float) * N, st));
+    ::ewos::note_launch();
+    EWOS_CUDA_TRY(::ewos::launch_pdl(rows_split16_kernel, dim3((unsigned)((M + 7) / 8)), dim3(256), 0, st, A, lda, M, K, at,
+                                     atl, Kp, rinv));
+    ::ewos::note_launch();
+    EWOS_CUDA_TRY(::ewos::launch_pdl(cols_absmax_kernel, dim3((unsigned)((N + 31) / 32), (unsigned)((K + 31) / 32)),
+                                     dim3(32, 8), 0, st, B, ldb, K, N, cmax));
+    ::ewos::note_launch();
+    EWOS_CUDA_TRY(::ewos::launch_pdl(cols_split16_kernel, dim3((unsigned)((N + 31) / 32), (unsigned)(Kp / 32)), dim3(32, 8),
+                                     0, st, B, ldb, K, N, bt, btl, Kp, (const float*)cmax, cinv));
+    CUtensorMap ma, mb, mal, mbl;
+    if (!(make_map16(&ma, at, M, Kp, BM) && make_map16(&mb, bt, N, Kp, CF::BN) && make_map16(&mal, atl, M, Kp, BM) &&
+          make_map16(&mbl, btl, N, Kp, CF::BN))) {
+        set_error("tensor-core update: cuTensorMapEncodeTiled failed");
+        return EWOS_ECUDA;
+    }
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(gemm_tf32_kernel<true, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    CF::SMEM_BYTES);
+    });
+    EWOS_CUDA_TRY(attr);
+    const dim3 grid((N + CF::BN - 1) / CF::BN, (M + BM - 1) / BM);
+    ::ewos::note_launch();
+    EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true, 0, false, true>, grid, dim3(128), (size_t)CF::SMEM_BYTES, st,
+                                     ma, mb, mal, mbl, M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr,
+                                     (const float*)nullptr, (const float*)rinv, (const float*)cinv));
+    return EWOS_OK;
+}
+
 // C [M][N] (row stride ldc) -= A B for a row-major A [M][K] (stride lda) and B [K][N] (stride
 // ldb): the LU's trailing update on the tensor cores (three TF32 products).  With presplit the
 // operands are already in the scratch (tc_update_operands; A and B are not read), starting at
-// operand row a_off of A and b_off of B.  Enqueued only; a pipeline timeout sets the scratch's
-// error word, which tc_update_check reads (and clears).
+// operand row a_off of A and b_off of B.  Otherwise, with f16, the rows of A and the columns of B
+// are scaled by powers of two (s_i, t_j: the largest entry of each in [2^13, 2^14)) and split into
+// FP16 halves, three kind::f16 products at twice the TF32 rate, unscaled by 1 / (s_i t_j) in the
+// epilogue: an entry x keeps about 22 bits, or an absolute error of 2^-38 of its row's (column's)
+// largest, like the TF32 halves.  Enqueued only; a pipeline timeout sets the scratch's error
+// word, which tc_update_check reads (and clears).
 ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int M,
-                              int N, int K, cudaStream_t st, TcScratch** owned, bool presplit, int a_off, int b_off) {
+                              int N, int K, cudaStream_t st, TcScratch** owned, bool presplit, int a_off, int b_off,
+                              bool f16) {
     using namespace tc;
     if (!*owned) *owned = new TcScratch();
     Scratch& S = (*owned)->s;
+    if (!presplit && f16) return tc_update_enqueue16(S, A, lda, B, ldb, C, ldc, M, N, K, st);
     const int Kp = (K + BK - 1) / BK * BK;
     const size_t need = (size_t)std::max(M, N) * Kp;
     if (!presplit) a_off = b_off = 0;
@@ -1401,10 +1572,12 @@ ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64
     ::ewos::note_launch();
     if (csm)
         EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true, kUpd, true>, grid, dim3(128), kCsmSmem, st, ma, mb, mal, mbl,
-                                         M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr));
+                                         M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr,
+                                         (const float*)nullptr, (const float*)nullptr));
     else
         EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true>, grid, dim3(128), (size_t)Cfg<true>::SMEM_BYTES, st, ma, mb,
-                                         mal, mbl, M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr));
+                                         mal, mbl, M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr,
+                                         (const float*)nullptr, (const float*)nullptr));
     return EWOS_OK;
 }
 
@@ -1470,6 +1643,36 @@ extern "C" ewos_status ewos_debug_tc_gemm(const float* A, const float* B, float*
     if (s == EWOS_OK && cudaMemcpy(C, dC, sizeof(float) * (size_t)M * N, cudaMemcpyDeviceToHost) != cudaSuccess) s = EWOS_ECUDA;
     dev_free(dA); dev_free(dB); dev_free(dC);
     cudaDeviceSynchronize();
+    return s;
+}
+
+extern "C" ewos_status ewos_debug_tc_update(const float* A, const float* B, float* C, int M, int N, int K, int f16) {
+    using namespace ewos;
+    if (!A || !B || !C || M < 1 || N < 1 || K < 1) {
+        set_error("ewos_debug_tc_update: bad arguments");
+        return EWOS_EINVAL;
+    }
+    if (!tc_assemble_available()) { set_error("tensor cores (sm_100 family) not available"); return EWOS_EINVAL; }
+    AllocStream as(nullptr);
+    float *dA = nullptr, *dB = nullptr, *dC = nullptr;
+    TcScratch* owned = nullptr;
+    ewos_status s = EWOS_OK;
+    if (dev_alloc((void**)&dA, sizeof(float) * (size_t)M * K) != cudaSuccess ||
+        dev_alloc((void**)&dB, sizeof(float) * (size_t)K * N) != cudaSuccess ||
+        dev_alloc((void**)&dC, sizeof(float) * (size_t)M * N) != cudaSuccess) {
+        set_error("ewos_debug_tc_update: out of device memory");
+        s = EWOS_ENOMEM;
+    }
+    if (s == EWOS_OK && (cudaMemcpy(dA, A, sizeof(float) * (size_t)M * K, cudaMemcpyHostToDevice) != cudaSuccess ||
+                         cudaMemcpy(dB, B, sizeof(float) * (size_t)K * N, cudaMemcpyHostToDevice) != cudaSuccess ||
+                         cudaMemcpy(dC, C, sizeof(float) * (size_t)M * N, cudaMemcpyHostToDevice) != cudaSuccess))
+        s = EWOS_ECUDA;
+    if (s == EWOS_OK) s = tc_update_enqueue(dA, K, dB, N, dC, N, M, N, K, nullptr, &owned, false, 0, 0, f16 != 0);
+    if (s == EWOS_OK) s = tc_update_check(owned, nullptr);
+    if (s == EWOS_OK && cudaMemcpy(C, dC, sizeof(float) * (size_t)M * N, cudaMemcpyDeviceToHost) != cudaSuccess) s = EWOS_ECUDA;
+    cudaDeviceSynchronize();
+    tc_scratch_free(owned);
+    dev_free(dA); dev_free(dB); dev_free(dC);
     return s;
 }
 

@@ -76,7 +76,7 @@ ewos_status tc_assemble(const float* A_km, const float* B_km, float* C, int M, i
                         const float* dscale = nullptr, const float* amax = nullptr);
 ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64_t ldb, float* C, int64_t ldc, int M,
                               int N, int K, cudaStream_t st, TcScratch** owned, bool presplit = false, int a_off = 0,
-                              int b_off = 0);
+                              int b_off = 0, bool f16 = true);
 ewos_status tc_update_reserve(int max_mn, int k, cudaStream_t st, TcScratch** owned);
 ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D, float* C, cudaStream_t st,
                            TcScratch** owned, bool sym = false, bool f16 = true, uint64_t pkey = 0,
@@ -1422,8 +1422,9 @@ __global__ void iota_kernel(int* __restrict__ v, int m) {
 
 // Returns EWOS_OK with *accepted false when a multiplier exceeds 1 or a pivot is zero (the
 // caller then refactors the original matrix with interchanges).
-// Trailing updates of at least this many rows go to the tensor cores (FP32 factors, three TF32
-// products); smaller ones stay on the FP32 SIMT GEMM.
+// Trailing updates of at least this many rows go to the tensor cores (FP32 factors; three TF32
+// products on the halves the panel kernel splits, three FP16 products on per-row and per-column
+// scaled halves for the rank-512 updates); smaller ones stay on the FP32 SIMT GEMM.
 constexpr int kTcUpdateMin = 256;
 constexpr int kSuper = 8;           // 64-column panels per super panel of the unpivoted LU
 

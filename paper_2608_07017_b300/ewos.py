@@ -139,6 +139,7 @@ def lib():
         L.ewos_debug_green_radius.argtypes = [P, P, I64, I]
         L.ewos_debug_tc_gemm.argtypes = [P, P, P, I, I, I, I]
         L.ewos_debug_tc_assemble.argtypes = [P, P, I, I, I, P, I, I]
+        L.ewos_debug_tc_update.argtypes = [P, P, P, I, I, I, I]
         L.ewos_debug_set_flow_wait_limit.argtypes = [I64]
         L.ewos_debug_fail_allocations.argtypes = [I64]
         L.ewos_debug_fail_allocations.restype = None
@@ -159,7 +160,7 @@ def lib():
                                          ctypes.POINTER(AdamReport)]
         for fn in ("ewos_toolbox_build", "ewos_toolbox_build_noalloc", "ewos_toolbox_from_host", "ewos_toolbox_get", "ewos_toolbox_report",
                    "ewos_toolbox_shape", "ewos_solve", "ewos_debug_philox", "ewos_debug_green_radius",
-                   "ewos_debug_tc_gemm", "ewos_debug_tc_assemble", "ewos_server_create", "ewos_server_submit", "ewos_server_wait",
+                   "ewos_debug_tc_gemm", "ewos_debug_tc_assemble", "ewos_debug_tc_update", "ewos_server_create", "ewos_server_submit", "ewos_server_wait",
                    "ewos_server_query", "ewos_toolbox_build_batch", "ewos_toolbox_save", "ewos_toolbox_load",
                    "ewos_gradient", "ewos_minimize_adam", "ewos_operators"):
             getattr(L, fn).restype = I
@@ -451,6 +452,21 @@ def debug_tc_assemble(P, M, sym=False, f16=True):
     c = np.zeros((m, m), dtype=np.float32)
     _check(lib().ewos_debug_tc_assemble(p.ctypes.data, mm.ctypes.data, n, m, E - 1, c.ctypes.data,
                                         1 if sym else 0, 1 if f16 else 0), "tc assemble")
+    return c
+
+
+def debug_tc_update(A, B, C, f16=True):
+    """C - A B by the tensor-core trailing update of the LU (A [M][K], B [K][N], C [M][N]; FP32):
+    f16: rows of A and columns of B scaled by powers of two and split into FP16 halves (the
+    rank-512 updates), else three TF32 products."""
+    a = np.ascontiguousarray(A, dtype=np.float32)
+    b = np.ascontiguousarray(B, dtype=np.float32)
+    c = np.array(C, dtype=np.float32, order="C", copy=True)
+    M, K = a.shape
+    N = b.shape[1]
+    assert b.shape[0] == K and c.shape == (M, N)
+    _check(lib().ewos_debug_tc_update(a.ctypes.data, b.ctypes.data, c.ctypes.data, M, N, K, 1 if f16 else 0),
+           "tc update")
     return c
 
 

@@ -333,3 +333,33 @@ def test_ball8000_full_size_newton_mixed_and_fp64():
     e_d = S.errors(ud, pb.u_star, lam)["l2"]
     assert abs(e_m - e_d) <= 1e-3 * max(1e-3, e_d)
     assert e_m < 0.2 * math.sqrt(np.sum(lam * pb.u_star ** 2))
+
+
+def test_mixed_lu_with_rank512_fp16_update():
+    # m = 1100: the unpivoted FP32 LU's first super panel (512 columns) ends with the rank-512
+    # update of the trailing 588 x 588 matrix, on the FP16 tensor-core path (rows and columns
+    # scaled by powers of two); the refined solution is the oracle's, in few sweeps
+    rng = np.random.default_rng(11)
+    n = 1100
+    x = rng.uniform(0.05, 0.95, size=(n, 2))
+    z = W.square_boundary_nodes(8)
+    sc = 2.0 ** rng.uniform(-1, 1, size=n)
+    G = (rng.normal(size=(n, n)) * 0.05 + np.eye(n)) * sc
+    gradG = (rng.normal(size=(2, n, n)) * 0.05 + 2.0 * np.eye(n)[None]) * sc
+    H = rng.uniform(0, 1, (n, z.shape[0]))
+    H /= H.sum(1, keepdims=True)
+    gradH = rng.normal(size=(2, n, z.shape[0])) * 0.01
+    lam = np.full(n, 1.0 / n)
+    A = np.tile(np.eye(2), (n, 1, 1))
+    c = np.ones(n)
+    f = rng.normal(size=n)
+    g = rng.normal(size=z.shape[0])
+    gtb = ewos.toolbox_from_host(2, x, z, G, gradG, H, gradH, lam, precision=32)
+    u, _, rep = gtb.solve(A, f, g, c=c, mode="mixed")
+    gtb.close()
+    assert rep["converged"] and rep["factorizations"] == 1 and rep["pivoted_factorizations"] == 0
+    assert rep["refine_iters"] <= 4
+    f32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    tb = dict(G=f32(G), gradG=f32(gradG), H=f32(H), gradH=f32(gradH))
+    ref = S.solve_linear(tb, lam, A, None, c, f, g, alpha=rep["alpha"])
+    assert _rel(u, ref["u"]) < 1e-9

@@ -143,3 +143,42 @@ def test_tc_assemble_pq(n, m, D, sym, spread, f16):
     rel = np.linalg.norm(C - ref) / np.linalg.norm(ref)
     assert rel < 4e-6
     assert np.linalg.norm(C) < np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("f16", [True, False])
+@pytest.mark.parametrize("M,N,K", [(389, 300, 512), (1000, 777, 512), (256, 256, 100), (130, 1100, 64), (3, 5, 7)])
+def test_tc_update_per_row_and_column_scales(M, N, K, f16):
+    """The LU's trailing update C - A B on the tensor cores.  In the FP16 form every row of A and
+    every column of B gets its own power-of-two scale (largest entry in [2^13, 2^14)) before the
+    split into FP16 halves, so rows and columns whose magnitudes differ by 2^40 keep their
+    relative accuracy: per entry 2^-21 of sum |a b| from the halves, the truncating FP32
+    accumulation (at most 2^-24 of the partial sums per step), the FP16 subnormal floor of
+    2^-25 / s_i per entry of row i (2^-25 / t_j for column j), and the rounding of the result.
+    The TF32 form splits without scales (FP32's range) and has no floor."""
+    rng = np.random.default_rng(M * 7 + N + K)
+    A = rng.normal(size=(M, K)) * 2.0 ** rng.integers(-20, 21, size=(M, 1))
+    B = rng.normal(size=(K, N)) * 2.0 ** rng.integers(-20, 21, size=(1, N))
+    A[M // 2, :] = 0.0               # a zero row and a zero column (scale 1)
+    B[:, N // 2] = 0.0
+    A = A.astype(np.float32)
+    B = B.astype(np.float32)
+    C = (A.astype(np.float64) @ B.astype(np.float64) * rng.uniform(0.5, 1.5, size=(M, N))).astype(np.float32)
+    out = ewos.debug_tc_update(A, B, C, f16=f16).astype(np.float64)
+    A64, B64 = A.astype(np.float64), B.astype(np.float64)
+    ref = C.astype(np.float64) - A64 @ B64
+    absref = np.abs(A64) @ np.abs(B64)
+    bound = (2.0 ** -19 + K * 2.0 ** -24) * absref + 2.0 ** -23 * np.abs(ref)
+    if f16:
+        amax = np.abs(A64).max(axis=1, keepdims=True)
+        bmax = np.abs(B64).max(axis=0, keepdims=True)
+        s = np.where(amax > 0, 2.0 ** (13 - np.floor(np.log2(np.where(amax > 0, amax, 1.0)))), 1.0)
+        t = np.where(bmax > 0, 2.0 ** (13 - np.floor(np.log2(np.where(bmax > 0, bmax, 1.0)))), 1.0)
+        bound += 2.0 ** -24 / s * np.abs(B64).sum(axis=0, keepdims=True) + \
+            2.0 ** -24 / t * np.abs(A64).sum(axis=1, keepdims=True)
+    assert np.all(np.abs(out - ref) <= bound)
+    # the zero row and column leave C as it was
+    assert np.array_equal(out[M // 2, :], C[M // 2, :].astype(np.float64))
+    assert np.array_equal(out[:, N // 2], C[:, N // 2].astype(np.float64))
+    # relative accuracy of the rows and columns of smallest magnitude
+    i = int(np.argmin(np.where(np.abs(A64).max(axis=1) > 0, np.abs(A64).max(axis=1), np.inf)))
+    assert np.linalg.norm(out[i] - ref[i]) <= 1e-5 * np.linalg.norm(absref[i]) + 2.0 ** -23 * np.linalg.norm(ref[i])
