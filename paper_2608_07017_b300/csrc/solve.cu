@@ -2014,7 +2014,8 @@ static ewos_status ensure_workspace(const ewos_toolbox* tb, SolveWorkspace*& slo
 }
 
 template <typename T>
-static ewos_status lu_solve_device(const T* LU, int m, int lda, LuScratch& S, double* x, int nrhs, cudaStream_t st) {
+static ewos_status lu_solve_device(const T* LU, int m, int lda, LuScratch& S, double* x, int nrhs, cudaStream_t st,
+                                   bool check = true) {
     EWOS_CUDA_TRY(trsm_prepare<T>());
     T* X = reinterpret_cast<T*>(S.tmp);   // [m][nrhs] in the precision of the factors
     const int64_t cnt = (int64_t)m * nrhs;
@@ -2023,7 +2024,7 @@ static ewos_status lu_solve_device(const T* LU, int m, int lda, LuScratch& S, do
     trsm_flow<T>(LU, m, lda, (const T*)S.dinv, X, nrhs, S.flow, st);
     ::ewos::note_launch(), scatter_cols_kernel<T><<<nb, 256, 0, st>>>(X, x, m, nrhs);
     EWOS_CUDA_TRY(cudaGetLastError());
-    return flow_check(S.flow, st);
+    return check ? flow_check(S.flow, st) : EWOS_OK;
 }
 
 // ------------------------------------------------------------------ operator pieces
@@ -2148,11 +2149,14 @@ static void u_from_v(const Ctx& C, double* u) {
     cudaMemcpyAsync(u, C.ws->v + (size_t)C.D * C.n, sizeof(double) * C.n, cudaMemcpyDeviceToDevice, C.st);
 }
 
-static double norm2(const Ctx& C, const double* v, int64_t len) {
+// ||v||; with flag, the word *flag on the device is read in the same synchronisation (into *flag_h)
+static double norm2(const Ctx& C, const double* v, int64_t len, const unsigned int* flag = nullptr,
+                    unsigned int* flag_h = nullptr) {
     cudaMemsetAsync(C.ws->scal, 0, sizeof(double), C.st);
     ::ewos::note_launch(), sumsq_kernel<<<std::max<int64_t>(1, std::min<int64_t>(1024, (len + 255) / 256)), 256, 0, C.st>>>(v, len, C.ws->scal);
     double h = 0;
     cudaMemcpyAsync(&h, C.ws->scal, sizeof(double), cudaMemcpyDeviceToHost, C.st);
+    if (flag) cudaMemcpyAsync(flag_h, flag, sizeof(unsigned int), cudaMemcpyDeviceToHost, C.st);
     cudaStreamSynchronize(C.st);
     return std::sqrt(h);
 }
@@ -2507,23 +2511,31 @@ static void apply_op(const Ctx& C, const double* x, double alpha, const double* 
 // x <- solution of (A) x = b by the FP32 factors plus FP64 refinement; A applied by apply_op
 template <typename TP>
 static ewos_status refine(const Ctx& C, const double* b, double* x, double alpha, const double* u, const double* nl,
-                          int nnl, double rel_tol, int max_sweeps, int* sweeps, double* final_rel) {
+                          int nnl, double rel_tol, int max_sweeps, int* sweeps, double* final_rel, double b_norm = -1.0) {
     SolveWorkspace* ws = C.ws;
-    const double nb = norm2(C, b, C.m);
+    const double nb = b_norm >= 0.0 ? b_norm : norm2(C, b, C.m);
     cudaMemsetAsync(x, 0, sizeof(double) * C.m, C.st);
     cudaMemcpyAsync(ws->r, b, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
     double rel = 1.0;
     int it = 0;
     while (it < max_sweeps) {
         cudaMemcpyAsync(ws->dx, ws->r, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
-        ewos_status st = lu_solve_device<float>(ws->LU32, (int)C.m, (int)C.m, ws->lu, ws->dx, 1, C.st);
+        // the triangular solves' error word is read with the residual's norm (one synchronisation)
+        ewos_status st = lu_solve_device<float>(ws->LU32, (int)C.m, (int)C.m, ws->lu, ws->dx, 1, C.st, false);
         if (st != EWOS_OK) return st;
         ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, 1.0, ws->dx, x);
         apply_op<TP>(C, x, alpha, u, nl, nnl, ws->y);
         cudaMemcpyAsync(ws->r, b, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
         ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, -1.0, ws->y, ws->r);
         ++it;
-        rel = nb > 0 ? norm2(C, ws->r, C.m) / nb : 0.0;
+        unsigned int flow_err = 0;
+        const double nr = norm2(C, ws->r, C.m, ws->lu.flow + 1, &flow_err);
+        if (flow_err) {
+            cudaMemsetAsync(ws->lu.flow + 1, 0, sizeof(unsigned int), C.st);
+            set_error("triangular solve: a wait on a preceding row block timed out");
+            return EWOS_ETIMEOUT;
+        }
+        rel = nb > 0 ? nr / nb : 0.0;
         if (rel <= rel_tol) break;
     }
     *sweeps += it;
@@ -3696,7 +3708,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                         cudaMemcpyAsync(ws->rhs, ws->y, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
                         double rel = 1.0;
                         ewos_status st = refine<TP>(C, ws->rhs, ws->x, alpha, ws->u2, nl, pb->nl_ncoef, eta,
-                                                    kStaleSweeps, &sweeps, &rel);
+                                                    kStaleSweeps, &sweeps, &rel, rn);
                         if (st != EWOS_OK) return st;
                         if (rel <= eta) {
                             ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, -1.0, ws->x, s);
@@ -3758,7 +3770,7 @@ static ewos_status solve_mixed_t(ewos_toolbox* tb, SolveWorkspace* ws, const ewo
                     if (st != EWOS_OK) return st;
                     rep->ms_factor += elapsed_ms(t1);
                     cudaMemcpyAsync(ws->rhs, ws->y, sizeof(double) * C.m, cudaMemcpyDeviceToDevice, C.st);
-                    st = refine<TP>(C, ws->rhs, ws->x, alpha, ws->u2, nl, pb->nl_ncoef, eta, 8, &sweeps, nullptr);
+                    st = refine<TP>(C, ws->rhs, ws->x, alpha, ws->u2, nl, pb->nl_ncoef, eta, 8, &sweeps, nullptr, rn);
                     if (st != EWOS_OK) return st;
                     ::ewos::note_launch(), axpy_kernel<<<(int)((C.m + 255) / 256), 256, 0, C.st>>>(C.m, -1.0, ws->x, s);
                     residual<TP>(C, s, g, f, nl, pb->nl_ncoef, alpha, ws->y);
