@@ -512,8 +512,11 @@ def summarize(name, res, workload, peaks, peak_src, nsm, dtype):
     if lu_ms > 0:
         mm = line_m(name)
         nf = statistics.median(r["factorizations"] for r in solves)
-        rl["fp32_lu"] = tensor_roofline("FP32 LU (tensor-core trailing updates)", nf * 2.0 / 3.0 * mm ** 3, lu_ms, peaks,
-                                        peak_src)
+        # most of the LU's FLOPs are in the rank-512 trailing updates (FP16 halves); the 64-wide
+        # panel updates take TF32 halves: the FP16 peak, the higher of the two, is the bound
+        rl["fp32_lu"] = tensor_roofline("FP32 LU (tensor-core trailing updates: rank-512 on FP16 halves, panel "
+                                        "updates on TF32 halves)", nf * 2.0 / 3.0 * mm ** 3, lu_ms, peaks,
+                                        peak_src, dtype="f16")
     out["rooflines"] = rl
     return out
 
