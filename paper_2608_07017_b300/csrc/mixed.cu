@@ -150,9 +150,7 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
                                                            int Kp, float* __restrict__ C, int64_t ldc,
                                                            int* __restrict__ err, int sub, int tri = 0,
                                                            const int* __restrict__ tiles = nullptr,
-                                                           const float* __restrict__ cscale = nullptr,
-                                                           const float* __restrict__ rinv = nullptr,
-                                                           const float* __restrict__ cinv = nullptr) {
+                                                           const float* __restrict__ cscale = nullptr) {
     using CF = Cfg<SPLIT, ST, F16>;
     constexpr int BN = CF::BN, STAGES = CF::STAGES, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
     constexpr int STAGE_BYTES = CF::STAGE_BYTES;
@@ -310,19 +308,10 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int col0 = n0 + c * 32;
             if constexpr (F16) {
-                // the operands were scaled by powers of two: undo it (exact).  rinv, cinv: one
-                // scale per row of A and per column of B (1 / s_i, 1 / t_j), else one for all
-                if (rinv) {
-                    const float rs = row < M ? rinv[row] : 0.f;
-                    const float cl = col0 + lane < N ? cinv[col0 + lane] : 0.f;
+                // the operands were scaled by powers of two: undo it (exact)
+                const float sc = cscale ? *cscale : 1.0f;
 #pragma unroll
-                    for (int q = 0; q < 32; ++q)
-                        v[q] = __float_as_uint(__uint_as_float(v[q]) * rs * __shfl_sync(0xffffffffu, cl, q));
-                } else {
-                    const float sc = cscale ? *cscale : 1.0f;
-#pragma unroll
-                    for (int q = 0; q < 32; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) * sc);
-                }
+                for (int q = 0; q < 32; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) * sc);
             }
             float4 ccur[8];
             if constexpr (CSM) {
@@ -581,6 +570,221 @@ __global__ void __launch_bounds__(192, 1) gemm_drain_kernel(const __grid_constan
         } else {
             s_fail = 1;
         }
+    }
+    __syncwarp();
+    __syncthreads();
+    if (threadIdx.x == 0 && s_fail) atomicExch(err, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * BN));
+}
+
+// The LU's subtracting update C -= diag(1/s) (A_h B_h + A_h B_l + A_l B_h) diag(1/t) on FP16 halves
+// (the rank-512 updates), persistent: a CTA per SM takes output tiles b, b + G, .. (G CTAs) in
+// bands of kUpdBand tile rows, column by column inside a band (the CTAs that run together share
+// kUpdBand row panels of A and a run of column panels of B in L2).  Two TMEM accumulators: the
+// MMAs of a tile run into one while the four epilogue warps read the other's tile, subtract it
+// from C (read and written in HBM) and release it, so that the C traffic of one tile hides under
+// the next tile's MMAs instead of following them.  Warp roles: warps 0-3 epilogue (warp w reads
+// TMEM lanes 32 w .. 32 w + 31: a row of the tile per thread), warp 4 the TMA loads, warp 5 the
+// MMA issue.
+constexpr int kUpdBand = 8;
+
+__global__ void __launch_bounds__(192, 1) gemm_upd16_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                            const __grid_constant__ CUtensorMap mapB,
+                                                            const __grid_constant__ CUtensorMap mapAl,
+                                                            const __grid_constant__ CUtensorMap mapBl, int M, int N,
+                                                            int Kp, float* __restrict__ C, int64_t ldc,
+                                                            int* __restrict__ err, const float* __restrict__ rinv,
+                                                            const float* __restrict__ cinv) {
+    using CF = Cfg<true, 0, true>;
+    constexpr int BN = CF::BN, STAGES = CF::STAGES, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
+    constexpr int STAGE_BYTES = CF::STAGE_BYTES;
+    constexpr int NACC = 2;
+    static_assert(BN == 128 && BM == 128, "128 x 128 tiles");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* tfull = empty + STAGES;        // [NACC]: a tile's MMAs have completed into accumulator b
+    uint64_t* tempty = tfull + NACC;         // [NACC]: the epilogue warps have read accumulator b
+    uint64_t* done = tempty + NACC;          // every MMA of the CTA has completed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ int s_fail;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = (M + BM - 1) / BM, ntx = (N + BN - 1) / BN;
+    const int ntiles = mt * ntx;
+    const int nk = Kp / CF::KSTAGE;
+    // tile t of the order: band of kUpdBand tile rows, columns in turn inside the band
+    auto tile_of = [&](int t, int& m0, int& n0) {
+        const int by = (t / (kUpdBand * ntx)) * kUpdBand;
+        const int h = min(kUpdBand, mt - by);
+        const int r = t - by * ntx;
+        m0 = (by + r % h) * BM;
+        n0 = (r / h) * BN;
+    };
+    ::ewos::pdl_trigger();
+
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < NACC; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 4); }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(NACC * BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    ::ewos::pdl_wait();                       // operands and C come from the preceding launches
+
+    if (warp == 4) {
+        if (lane == 0) {
+            int s = 0, issued = 0;
+            uint32_t ph = 0;
+            for (int t = blockIdx.x; t < ntiles && !s_fail; t += gridDim.x) {
+                int m0, n0;
+                tile_of(t, m0, n0);
+                for (int kb = 0; kb < nk; ++kb) {
+                    if (!mbar_wait(&empty[s], ph ^ 1u)) { s_fail = 1; break; }
+                    unsigned char* st = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_2d(st, &mapA, &full[s], kb * CF::KSTAGE, m0);
+                    tma_load_2d(st + A_BYTES, &mapB, &full[s], kb * CF::KSTAGE, n0);
+                    tma_load_2d(st + A_BYTES + B_BYTES, &mapAl, &full[s], kb * CF::KSTAGE, m0);
+                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, &mapBl, &full[s], kb * CF::KSTAGE, n0);
+                    ++issued;
+                    if (++s == STAGES) { s = 0; ph ^= 1u; }
+                }
+            }
+            // after a failed wait, let the loads still in flight land before the CTA exits
+            if (s_fail)
+                for (int g = issued > STAGES ? issued - STAGES : 0; g < issued; ++g)
+                    mbar_wait(&full[g % STAGES], (uint32_t)((g / STAGES) & 1));
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            const uint64_t d0a = smem_desc(smem), d0b = smem_desc(smem + A_BYTES);
+            const uint64_t d0al = smem_desc(smem + A_BYTES + B_BYTES), d0bl = smem_desc(smem + 2 * A_BYTES + B_BYTES);
+            int s = 0, j = 0;
+            uint32_t ph = 0;
+            bool bad = false;
+            for (int t = blockIdx.x; t < ntiles && !bad; t += gridDim.x, ++j) {
+                const int b = j & (NACC - 1);
+                // accumulator b is free again once tile j - NACC has been read by the epilogue
+                if (j >= NACC && !mbar_wait(&tempty[b], (uint32_t)(((j >> 1) - 1) & 1))) { bad = true; break; }
+                const uint32_t d = tmem + (uint32_t)(b * BN);
+                for (int kb = 0; kb < nk; ++kb) {
+                    if (!mbar_wait(&full[s], ph)) { bad = true; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint64_t so = (uint64_t)(s * (STAGE_BYTES >> 4));
+#pragma unroll
+                    for (int k = 0; k < BK / 8; ++k) {
+                        const uint64_t ko = so + (uint64_t)(k * 2);
+                        const uint32_t acc = (kb > 0 || k > 0) ? 1u : 0u;
+                        mma_f16(d, d0a + ko, d0b + ko, CF::IDESC, acc);
+                        mma_f16(d, d0a + ko, d0bl + ko, CF::IDESC, 1u);
+                        mma_f16(d, d0al + ko, d0b + ko, CF::IDESC, 1u);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&empty[s]))
+                                 : "memory");
+                    if (++s == STAGES) { s = 0; ph ^= 1u; }
+                }
+                if (bad) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&tfull[b]))
+                             : "memory");
+            }
+            if (bad) s_fail = 1;
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(done))
+                         : "memory");
+        }
+    } else {
+        bool ok = true;
+        int j = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+            int m0, n0;
+            tile_of(t, m0, n0);
+            const int b = j & (NACC - 1);
+            const int row = m0 + warp * 32 + lane;
+            // the thread's row of C, a 32-column chunk ahead: the first one under the MMAs
+            auto fast = [&](int c) {
+                const int col0 = n0 + c * 32;
+                return row < M && col0 + 32 <= N && (ldc & 3) == 0 &&
+                       ((reinterpret_cast<uintptr_t>(C + (int64_t)row * ldc + col0) & 15) == 0);
+            };
+            float4 cpre[8];
+            auto fetch = [&](int c) {
+                if (fast(c)) {
+                    const float4* cp4 = reinterpret_cast<const float4*>(C + (int64_t)row * ldc + n0 + c * 32);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) cpre[q] = cp4[q];
+                }
+            };
+            fetch(0);
+            if (!mbar_wait_sleep(&tfull[b], (uint32_t)((j >> 1) & 1), EWOS_DRAIN_SLEEP) || s_fail) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float acc[BN];
+#pragma unroll
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * BN + c * 32);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                    "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 32; ++q) acc[c * 32 + q] = __uint_as_float(v[q]);
+            }
+            // the accumulator is free for tile j + NACC once the four warps have read it
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[b])) : "memory");
+            const float rs = row < M ? rinv[row] : 0.f;
+#pragma unroll
+            for (int c = 0; c < BN / 32; ++c) {
+                const int col0 = n0 + c * 32;
+                const float cl = col0 + lane < N ? cinv[col0 + lane] : 0.f;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) acc[c * 32 + q] = acc[c * 32 + q] * rs * __shfl_sync(0xffffffffu, cl, q);
+                const bool f = fast(c);
+                float4 ccur[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) ccur[q] = cpre[q];
+                if (c + 1 < BN / 32) fetch(c + 1);
+                if (row < M) {
+                    float* cp = C + (int64_t)row * ldc + col0;
+                    if (f) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            reinterpret_cast<float4*>(cp)[q] =
+                                make_float4(ccur[q].x - acc[c * 32 + 4 * q], ccur[q].y - acc[c * 32 + 4 * q + 1],
+                                            ccur[q].z - acc[c * 32 + 4 * q + 2], ccur[q].w - acc[c * 32 + 4 * q + 3]);
+                    } else {
+                        for (int q = 0; q < 32; ++q)
+                            if (col0 + q < N) cp[q] = cp[q] - acc[c * 32 + q];
+                    }
+                }
+            }
+        }
+        // every MMA has completed (also after a failed wait) before TMEM is released
+        if (!mbar_wait_sleep(done, 0, EWOS_DRAIN_SLEEP)) ok = false;
+        if (!ok) s_fail = 1;
     }
     __syncwarp();
     __syncthreads();
@@ -1434,7 +1638,8 @@ void tc_update_operands(TcScratch* t, float** a_hi, float** a_lo, float** b_hi, 
     *a_hi = t->s.At; *a_lo = t->s.Atl; *b_hi = t->s.Bt; *b_lo = t->s.Btl;
 }
 
-// The FP16 form of tc_update_enqueue (operands split here, one scale per row of A and column of B)
+// The FP16 form of tc_update_enqueue (operands split here, one scale per row of A and column of B;
+// the persistent gemm_upd16_kernel)
 static ewos_status tc_update_enqueue16(tc::Scratch& S, const float* A, int64_t lda, const float* B, int64_t ldb,
                                        float* C, int64_t ldc, int M, int N, int K, cudaStream_t st) {
     using namespace tc;
@@ -1487,16 +1692,19 @@ static ewos_status tc_update_enqueue16(tc::Scratch& S, const float* A, int64_t l
     }
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
+    static int nsm = 0;
     std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(gemm_tf32_kernel<true, 0, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    CF::SMEM_BYTES);
+        attr = cudaFuncSetAttribute(gemm_upd16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM_BYTES);
+        int dev = 0;
+        if (attr == cudaSuccess) attr = cudaGetDevice(&dev);
+        if (attr == cudaSuccess) attr = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     });
     EWOS_CUDA_TRY(attr);
-    const dim3 grid((N + CF::BN - 1) / CF::BN, (M + BM - 1) / BM);
+    const int ntiles = ((M + BM - 1) / BM) * ((N + CF::BN - 1) / CF::BN);
+    const int grid = std::max(1, std::min(ntiles, nsm));
     ::ewos::note_launch();
-    EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true, 0, false, true>, grid, dim3(128), (size_t)CF::SMEM_BYTES, st,
-                                     ma, mb, mal, mbl, M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr,
-                                     (const float*)nullptr, (const float*)rinv, (const float*)cinv));
+    EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_upd16_kernel, dim3(grid), dim3(192), (size_t)CF::SMEM_BYTES, st, ma, mb, mal, mbl,
+                                     M, N, Kp, C, ldc, S.err, (const float*)rinv, (const float*)cinv));
     return EWOS_OK;
 }
 
@@ -1572,12 +1780,10 @@ ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64
     ::ewos::note_launch();
     if (csm)
         EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true, kUpd, true>, grid, dim3(128), kCsmSmem, st, ma, mb, mal, mbl,
-                                         M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr,
-                                         (const float*)nullptr, (const float*)nullptr));
+                                         M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr));
     else
         EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true>, grid, dim3(128), (size_t)Cfg<true>::SMEM_BYTES, st, ma, mb,
-                                         mal, mbl, M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr,
-                                         (const float*)nullptr, (const float*)nullptr));
+                                         mal, mbl, M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr));
     return EWOS_OK;
 }
 
