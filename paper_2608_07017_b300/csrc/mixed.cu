@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
                                                            int Kp, float* __restrict__ C, int64_t ldc,
                                                            int* __restrict__ err, int sub, int tri = 0,
                                                            const int* __restrict__ tiles = nullptr,
-                                                           const float* __restrict__ cscale = nullptr) {
+                                                           const float* __restrict__ cscale = nullptr, int lband = -1) {
     using CF = Cfg<SPLIT, ST, F16>;
     constexpr int BN = CF::BN, STAGES = CF::STAGES, A_BYTES = CF::A_BYTES, B_BYTES = CF::B_BYTES;
     constexpr int STAGE_BYTES = CF::STAGE_BYTES;
@@ -178,7 +178,23 @@ __global__ void __launch_bounds__(128, 1) gemm_tf32_kernel(const __grid_constant
         tile_y = ty;
         tile_x = t - ty * (ty + 1) / 2;
     }
-    const int m0 = tile_y * BM, n0 = tile_x * BN;
+    int m0 = tile_y * BM, n0 = tile_x * BN;
+    if (lband >= 0) {
+        // L-shaped update (1D grid): rows [0, lband) x columns [0, N), then rows [lband, M) x
+        // columns [0, lband); each tile's bounds are those of its part
+        const int ntx1 = (N + BN - 1) / BN, t1 = ((lband + BM - 1) / BM) * ntx1;
+        const int t = blockIdx.x;
+        if (t < t1) {
+            m0 = (t / ntx1) * BM;
+            n0 = (t % ntx1) * BN;
+            M = lband;
+        } else {
+            const int ntx2 = (lband + BN - 1) / BN, t2 = t - t1;
+            m0 = lband + (t2 / ntx2) * BM;
+            n0 = (t2 % ntx2) * BN;
+            N = lband;
+        }
+    }
     const bool mirror = tri && tile_x != tile_y;
     const int nk = Kp / CF::KSTAGE;                // (Kp counts operand elements)
     ::ewos::pdl_trigger();
@@ -1780,10 +1796,51 @@ ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64
     ::ewos::note_launch();
     if (csm)
         EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true, kUpd, true>, grid, dim3(128), kCsmSmem, st, ma, mb, mal, mbl,
-                                         M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr));
+                                         M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr, -1));
     else
         EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true>, grid, dim3(128), (size_t)Cfg<true>::SMEM_BYTES, st, ma, mb,
-                                         mal, mbl, M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr));
+                                         mal, mbl, M, N, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr, (const float*)nullptr, -1));
+    return EWOS_OK;
+}
+
+// The two rank-64 updates of a panel in one launch, on the operands the panel kernel split
+// (tc_update_operands, rows from 0): with C the block right of and below the diagonal block (rest
+// x rest, row stride ldc), C[0, band) x [0, rest) and C[band, rest) x [0, band) -= A B, the rows
+// of the super panel's later panels across every column and the rows below it across the super
+// panel's later columns (the rest of C waits for the super panel's rank-512 update).
+ewos_status tc_update_lshape_enqueue(float* C, int64_t ldc, int rest, int band, int K, cudaStream_t st,
+                                     TcScratch** owned) {
+    using namespace tc;
+    if (!*owned) *owned = new TcScratch();
+    Scratch& S = (*owned)->s;
+    const int Kp = (K + BK - 1) / BK * BK;
+    constexpr int kUpd = 2;
+    constexpr int bn = Cfg<true>::BN;
+    if (rest <= 0 || band <= 0 || band > rest || S.cap < (size_t)rest * Kp || !S.Atl || !S.err || Kp > kUpd * BK ||
+        (ldc & 3) != 0 || (reinterpret_cast<uintptr_t>(C) & 15) != 0) {
+        set_error("tensor-core update: L-shaped update outside its preconditions");
+        return EWOS_EINVAL;
+    }
+    CUtensorMap ma, mb, mal, mbl;
+    if (!(make_map(&ma, S.At, rest, Kp, BM) && make_map(&mb, S.Bt, rest, Kp, bn) && make_map(&mal, S.Atl, rest, Kp, BM) &&
+          make_map(&mbl, S.Btl, rest, Kp, bn))) {
+        set_error("tensor-core update: cuTensorMapEncodeTiled failed");
+        return EWOS_ECUDA;
+    }
+    constexpr size_t kCsmSmem = (size_t)Cfg<true, kUpd>::SMEM_BYTES + kCsmBytes;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(gemm_tf32_kernel<true, kUpd, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kCsmSmem);
+    });
+    EWOS_CUDA_TRY(attr);
+    const int t1 = ((band + BM - 1) / BM) * ((rest + bn - 1) / bn);
+    const int t2 = ((rest - band + BM - 1) / BM) * ((band + bn - 1) / bn);
+    ::ewos::note_launch();
+    EWOS_CUDA_TRY(::ewos::launch_pdl(gemm_tf32_kernel<true, kUpd, true>, dim3((unsigned)(t1 + t2)), dim3(128), kCsmSmem, st,
+                                     ma, mb, mal, mbl, rest, rest, Kp, C, ldc, S.err, 1, 0, (const int*)nullptr,
+                                     (const float*)nullptr, band));
     return EWOS_OK;
 }
 

@@ -78,6 +78,8 @@ ewos_status tc_update_enqueue(const float* A, int64_t lda, const float* B, int64
                               int N, int K, cudaStream_t st, TcScratch** owned, bool presplit = false, int a_off = 0,
                               int b_off = 0, bool f16 = true);
 ewos_status tc_update_reserve(int max_mn, int k, cudaStream_t st, TcScratch** owned);
+ewos_status tc_update_lshape_enqueue(float* C, int64_t ldc, int rest, int band, int K, cudaStream_t st,
+                                     TcScratch** owned);
 ewos_status tc_assemble_pq(const float* P, const double* Mc, int n, int m, int D, float* C, cudaStream_t st,
                            TcScratch** owned, bool sym = false, bool f16 = true, uint64_t pkey = 0,
                            const float* pmax = nullptr);
@@ -1493,7 +1495,17 @@ static ewos_status lu_factor_nopiv(T* A, int m, int lda, LuScratch& S, cudaStrea
                                          lda, m, kb, (const T*)iblk, S.bar, tc_here ? tc_ops : TcOperands{}));
                 const int band = KE - (kb + nb);       // rows (and columns) of the super panel's later panels
                 const int below = m - KE;
-                ewos_status e = update(band, rest, nb, kb + nb, kb + nb, kb, kb, tc_here, 0, 0);
+                ewos_status e = EWOS_OK;
+                if constexpr (std::is_same<T, float>::value) {
+                    // on the tensor cores both updates are one launch over their L-shaped region
+                    if (tc_here && band > 0 && (lda & 3) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0) {
+                        e = tc_update_lshape_enqueue(reinterpret_cast<float*>(A + (size_t)(kb + nb) * lda + kb + nb), lda,
+                                                     rest, band, nb, st, tc);
+                        if (e != EWOS_OK) return e;
+                        continue;
+                    }
+                }
+                e = update(band, rest, nb, kb + nb, kb + nb, kb, kb, tc_here, 0, 0);
                 if (e == EWOS_OK) e = update(below, band, nb, KE, kb + nb, kb, kb, tc_here, band, 0);
                 if (e != EWOS_OK) return e;
             }
