@@ -3167,7 +3167,19 @@ static void multi_coltrans_f2(cudaStream_t st, const float* X, int64_t rows, int
 static bool coltrans_rows(const Ctx& C, const float* X, int64_t rows, int cols, const float* Whi, const float* Wlo,
                           double* Y) {
     if (cols % 4 != 0 || !aligned16(X) || rows < 1) return false;
-    const int64_t vchunk = 256;
+    // row chunks sized so that the grid is one full wave of resident CTAs: with fixed 256-row
+    // chunks the ball's 2000 CTAs made 1.13 waves, and the last 13 % took as long as a full wave
+    static int slots = 0;
+    if (slots == 0) {
+        int dev = 0, nsm = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coltrans_f2_vec_kernel<8>, 128, 0);
+        slots = std::max(1, nsm * std::max(1, per_sm));
+    }
+    const int gx = (cols / 4 + 127) / 128;
+    const int64_t want = std::max<int64_t>(1, slots / gx);
+    const int64_t vchunk = std::max<int64_t>(8, (rows + want - 1) / want);
     const int parts = (int)((rows + vchunk - 1) / vchunk);
     SolveWorkspace* ws = C.ws;
     if (ws->ctpart_cap < (int64_t)parts * cols) {
