@@ -130,8 +130,8 @@ def _dist():
 
 # ------------------------------------------------------------------ rooflines
 def walk_roofline(workload, steps_per_launch, ms_walk, nsm, peaks, peak_src, grid_scale=None):
-    """Walk-kernel roofline of the survey's measurement section: its fraction is max(fma-pipe,
-    xu-pipe) utilisation, with issue beside it, and beside those the resource the kernel is
+    """Walk-kernel roofline: the kernel is bound by plain arithmetic (FP32 and SFU pipes), so its
+    fraction is max(fma-pipe, xu-pipe) utilisation, with issue beside it, and beside those the resource the kernel is
     measured to be bound by (`binding_resource`: L1 data-pipe wavefronts per WoS step).
     The instructions per WoS step on each pipe come from the ncu counters committed in
     profiles/walk_counters.json for the same kernel source (sha of wos_build.cu and
