@@ -2871,7 +2871,7 @@ __device__ __forceinline__ void f2_add_prod4(float* hi, float* lo, const float4 
 
 // Vout[row] (+)= sum_c X[row][c] (Vhi[c] + Vlo[c])   (warp per row)
 template <int kU>
-__global__ void rowdot_f2_vec_kernel(const float* __restrict__ X, int64_t rows, int cols, const float* __restrict__ Vhi,
+__global__ void __launch_bounds__(256, 6) rowdot_f2_vec_kernel(const float* __restrict__ X, int64_t rows, int cols, const float* __restrict__ Vhi,
                                      const float* __restrict__ Vlo, double* __restrict__ Vout, int accumulate) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
